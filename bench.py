@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark: spectral-signature tensor evaluations per second on GB300.
+
+Workload (one "step"): the batched dictionary sweep -- 1000 synthetic reduced
+objects (shared basis, r drawn uniformly from 8..96, K_r spectrum in
+[1e-6, 1e2], C_r spectrum in [1e-3, 1], Gram blocks from a random N = 4096
+basis) x 2000 frequencies log-spaced in [1e1, 1e8] rad/s.  Every step runs the
+whole on-line path for all 2,000,000 (object, frequency) pairs: reduced solve
+(Eq. (17)), R (Eq. (18)), I (Eq. (19)) and the certificate Delta (Lemma 4.2),
+in float64, one persistent-kernel launch.
+
+value: evaluations/s with the reduced data already resident in HBM.
+e2e:   the same through the public API from pinned host buffers -- every step
+       uploads the dictionary, builds the objects and the plan, sweeps, and
+       reads R, I and Delta back.
+roofline: the sweep kernel against the FP64 pipe (GB300: 2 DFMA/clk/SM).
+cpu_baseline: the CPU oracle (numpy/LAPACK) on a bounded sample of objects.
+
+Multi-GPU (torchrun, N > 1): every rank sweeps its own 1000-object dictionary
+(weak scaling, no collective on the data path); value = all evaluations / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spectral-signature tensor evals/sec (objects x freqs), FP64, with certificate"
+UNIT = "evals/s"
+SM_COUNT_NOMINAL = 152
+DFMA_PER_CLK_PER_SM = 2           # measured: GB300 DFMA rate saturates at 4 flop/clk/SM
+FP64_MEASURED_TFLOPS = 1.189      # DFMA microbenchmark on this machine's GB300 (1.96 GHz)
+# DRAM traffic per sweep launch from an ncu capture of the current kernel (None until captured)
+SWEEP_DRAM_BYTES_PER_LAUNCH = None
+
+
+def flops_per_eval(r: int, cert: bool = True) -> float:
+    """FP64 flops of one (object, frequency) evaluation as the sweep kernel computes it.
+
+    FMA = 2 flops, multiply = 1.  Complex multiply-add = 4 FMA.
+    form A (2 FMA/entry), elimination of the augmented [A | 3 rhs] without pivoting,
+    3 back substitutions, y = K p, C p (3 rhs each), G~ formation (2x2 FMA/entry) and
+    G~ p, then the 36 length-r reductions of the quadratic forms.
+    """
+    r = int(r)
+    m = np.arange(1, r)
+    elim = 8.0 * np.sum(m * (m + 3)) + 6.0 * np.sum(m)    # updates + multipliers
+    back = 8.0 * 3 * r * (r - 1) / 2 + 6.0 * 3 * r
+    form = 4.0 * r * r
+    mats = 2 if not cert else 3
+    matvec = 8.0 * 3 * r * r * mats + (8.0 * r * r if cert else 0.0)
+    red = 4.0 * r * (18 if cert else 12) + 4.0 * r * 9 + (12.0 * r * 9 if cert else 0.0)
+    return elim + back + form + matvec + red
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join("/tmp", f"mrom_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self, device_index: int = 0):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != device_index:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dictionary(n_obj: int, seed: int):
+    from workloads import reduced_dictionary
+    return reduced_dictionary(n_obj, seed=seed)
+
+
+def oracle_sample_rate(objs, omegas, n_sample: int):
+    """Evaluations/s of the CPU oracle on n_sample objects spread over the dictionary."""
+    from oracle import certificate, rom
+    idx = np.linspace(0, len(objs) - 1, n_sample).round().astype(int)
+    t0 = time.perf_counter()
+    for k in idx:
+        model = rom.from_reduced_object(objs[k])
+        P = rom.reduced_solve(model, omegas)
+        rom.mm_tensors(model, omegas, P)
+        certificate.certificate(model, omegas, P)
+    dt = time.perf_counter() - t0
+    return n_sample * omegas.size / dt, dt, [int(objs[k].r) for k in idx]
+
+
+def blas_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        return int(max(n)) if n else os.cpu_count()
+    except Exception:
+        return os.cpu_count()
+
+
+def config(args):
+    return {"workload": f"batched dictionary sweep: {args.n_obj} reduced objects (r ~ U{{8..96}}, shared basis) "
+                        f"x {args.n_w} log-spaced omega in [1e1, 1e8] rad/s; R, I and certificate Delta",
+            "n_obj": args.n_obj, "n_w": args.n_w, "r_range": [8, 96], "omega_range": [1e1, 1e8],
+            "certificate": True, "precision": "fp64",
+            "l2": "inputs larger than L2: 0.39 GB reduced data read and 0.43 GB written per step"}
+
+
+def run_reference(args, world):
+    """The oracle as it stands, timed on the host cores (bounded sample per step)."""
+    from workloads import log_omegas
+    objs = dictionary(args.n_obj, 20230711)
+    wo = log_omegas(1e1, 1e8, args.n_w)
+    n_s = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_sample_rate(objs, wo, 1)
+    times = []
+    for _ in range(args.steps):
+        rate, dt, rs = oracle_sample_rate(objs, wo, n_s)
+        times.append(dt)
+    evals = n_s * args.n_w
+    value = evals * len(times) / sum(times)
+    cores = blas_threads()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config(args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n_s} objects (r = {rs}) x {args.n_w} frequencies per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-obj", type=int, default=1000)
+    ap.add_argument("--n-w", type=int, default=2000)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=int, default=20)
+    ap.add_argument("--ref-sample", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    import paper_2307_05590_gb300 as m
+    from workloads import log_omegas
+
+    objs = dictionary(args.n_obj, 20230711 + rank)
+    wo = log_omegas(1e1, 1e8, args.n_w)
+    rs = np.array([o.r for o in objs])
+    flops_launch = float(sum(flops_per_eval(r) for r in rs)) * args.n_w
+
+    stream = torch.cuda.Stream(dev)
+    h = m.Handle(local_rank, stream.cuda_stream)
+    roms = [m.ReducedObject.from_workload(h, o) for o in objs]
+    plan = m.Plan(h, roms, args.n_w)
+    om = torch.as_tensor(wo, dtype=torch.float64, device=dev)
+    shape = (args.n_obj, args.n_w, 3, 3)
+    R = torch.empty(shape, dtype=torch.float64, device=dev)
+    I = torch.empty_like(R)
+    D = torch.empty_like(R)
+
+    for _ in range(args.warmup):
+        plan.sweep(om, R, I, D)
+    h.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler()
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    n0 = h.launch_count()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        plan.sweep(om, R, I, D)
+        ev[k][1].record(stream)
+    h.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = h.launch_count() - n0
+    clk = clocks.stop(local_rank)
+    per_launch_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_ms = ev[0][0].elapsed_time(ev[-1][1])
+    t_step = torch.tensor([dev_ms / args.steps], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_step, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t_step.item())
+    evals_step = args.n_obj * args.n_w * world
+    value = evals_step / (ms_per_step * 1e-3)
+
+    # ---- end to end through the public API from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pinned = []
+        h2d = 0
+        for o in objs:
+            arrs = {}
+            for name in ("K", "C", "B", "G", "K_in"):
+                a = getattr(o, name)
+                t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                arrs[name] = t
+                h2d += t.numel() * t.element_size()
+            arrs["c00"] = torch.from_numpy(np.ascontiguousarray(o.c00)).pin_memory()
+            h2d += 72
+            pinned.append(arrs)
+        om_host = torch.from_numpy(wo.copy()).pin_memory()
+        h2d += om_host.numel() * 8
+        outs = [torch.empty(shape, dtype=torch.float64).pin_memory() for _ in range(3)]
+        d2h = 3 * int(np.prod(shape)) * 8
+
+        def e2e_step():
+            rr = [m.ReducedObject(h, o.r, p["K"], p["C"], p["B"], p["c00"], G=p["G"], K_in=p["K_in"],
+                                  alpha=o.alpha, alpha_lb=o.alpha_lb, vol_B=o.vol_B)
+                  for o, p in zip(objs, pinned)]
+            pl = m.Plan(h, rr, args.n_w)
+            omd = om_host.to(dev, non_blocking=True)
+            pl.sweep(omd, R, I, D)
+            with torch.cuda.stream(stream):
+                for dst, src in zip(outs, (R, I, D)):
+                    dst.copy_(src, non_blocking=True)
+            h.synchronize()
+            pl.close()
+            for x in rr:
+                x.close()
+
+        with torch.cuda.stream(stream):
+            e2e_step()
+            if world > 1:
+                dist.barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                e2e_step()
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            te = torch.tensor([(time.perf_counter() - t0) / args.e2e_steps], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": evals_step / float(te.item()), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * float(te.item())}
+
+    # ---- CPU oracle baseline (rank 0, single GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, srs = oracle_sample_rate(objs, wo, args.cpu_sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": f"{args.cpu_sample} objects spread over the dictionary (r = {srs}) x {args.n_w} "
+                         f"frequencies, {dt:.1f} s"}
+
+    mean_launch_ms = float(np.mean(per_launch_ms))
+    sm_mhz_max = (clk or {}).get("sm_max_mhz", 2070.0)
+    peak_tflops = SM_COUNT_NOMINAL * DFMA_PER_CLK_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
+    achieved = flops_launch / (mean_launch_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": SWEEP_DRAM_BYTES_PER_LAUNCH,
+                "kernel": "sweep_fp64_kernel", "flops_per_launch": flops_launch,
+                "peak_note": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 flop x max SM clock; "
+                             f"measured DFMA microbenchmark {FP64_MEASURED_TFLOPS} TFLOP/s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk, "wall_s_timed": wall, "per_launch_ms": per_launch_ms,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    for x in roms:
+        x.close()
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * mrom.h -- C ABI of the GB300 reduced-order MPT spectral-signature library.
+ *
+ * The library computes magnetic polarizability tensor (MPT) spectral
+ * signatures with the reduced-order "Matrix Method" of Elgy & Ledger,
+ * "Efficient Computation of Magnetic Polarizability Tensor Spectral
+ * Signatures for Object Characterisation in Metal Detection":
+ *   snapshots D_i (Sect. 4.1, Eq. (13)) -> truncated SVD (Eqs. (14), (15))
+ *   -> Galerkin projection of K and C (Eq. (17)) -> for many objects and
+ *   frequencies the reduced solves (Eq. (17)) and the tensor post-processing
+ *   R (Eq. (18)) and I (Eq. (19)) -> the a-posteriori certificate Delta
+ *   (Lemma 4.2, Eq. (20)) -> adaptive snapshot selection (Algorithm 1).
+ *
+ * Conventions used throughout
+ *  - Sign convention of the paper: A[omega] = K - i omega C + eps M, source
+ *    r_i = i omega C o_i (Sect. 3.1, Eq. (9)).  A solution written for the
+ *    conjugate convention (K + i omega C) alpha = i omega b is alpha = -conj(q).
+ *  - Complex numbers are interleaved (re, im) float64 pairs (complex128,
+ *    cuDoubleComplex); matrices are row-major.
+ *  - Tensor outputs are float64 arrays [n_obj][n_w][3][3], row-major.
+ *    R excludes N0 unless the object was given an N0 (then R~ = N0 + R).
+ *  - Unless stated otherwise, array arguments of compute calls are DEVICE
+ *    pointers owned by the caller; they must stay valid until the handle's
+ *    stream has reached the call.  Object-creation calls accept host or
+ *    device pointers (copied with cudaMemcpyDefault before returning).
+ *  - Every compute call is asynchronous on the handle's CUDA stream.  A call
+ *    returns MROM_EINVAL for invalid arguments (nothing is launched),
+ *    MROM_ECUDA for a failed launch, MROM_ENOMEM when device memory runs out.
+ *    Conditions detected on the device (a non-finite frequency, a zero or
+ *    non-finite pivot) are recorded in a device status word and returned by
+ *    the next mrom_synchronize() on the handle.  No call aborts the process.
+ *  - No call is thread-safe on the same handle.
+ */
+#ifndef MROM_H
+#define MROM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MROM_OK = 0,
+  MROM_EINVAL = 1,        /* bad argument (shape, null pointer, non-finite value) */
+  MROM_ENOMEM = 2,        /* device allocation failed */
+  MROM_ECUDA = 3,         /* CUDA runtime error (launch, copy) */
+  MROM_ESINGULAR = 4,     /* zero or non-finite pivot in a reduced solve */
+  MROM_ENOTCONVERGED = 5, /* iteration limit reached */
+  MROM_ETIMEOUT = 6,      /* a bounded device wait gave up */
+  MROM_ECALLBACK = 7,     /* a user callback returned an error */
+  MROM_ENOTSUP = 8        /* option not supported for this object */
+} mrom_status;
+
+typedef struct mrom_ctx* mrom_handle;
+typedef struct mrom_rom* mrom_rom_t;
+typedef struct mrom_plan_s* mrom_plan;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a handle on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to run on (NULL: the handle creates its own non-blocking stream).  The
+ * handle owns a small device status word and no other device memory. */
+mrom_status mrom_create(int device, void* cuda_stream, mrom_handle* out);
+mrom_status mrom_destroy(mrom_handle h);
+/* Replace the stream used by later calls (NULL: the handle's own stream). */
+mrom_status mrom_set_stream(mrom_handle h, void* cuda_stream);
+/* Wait for the handle's stream; returns the first CUDA error or the first
+ * device-detected condition since the previous mrom_synchronize, then clears it. */
+mrom_status mrom_synchronize(mrom_handle h);
+/* Human-readable description of the last error on this handle (never NULL). */
+const char* mrom_last_error(mrom_handle h);
+/* Number of kernels this library launched on the handle so far. */
+int64_t mrom_launch_count(mrom_handle h);
+
+/* ------------------------------------------------------- reduced objects */
+
+/* One reduced object with a single basis U (N x r) shared by the three
+ * directions (Remark 3.1 taken one step further: one space for all i).
+ * With this basis, Sect. 4.3 needs
+ *   K   = U^H K U        r x r complex128, Hermitian     (K_ij^M, Eq. (18))
+ *   C   = U^H C U        r x r complex128, Hermitian PD  (C_ij^M, Eq. (19))
+ *   Me  = U^H (eps M) U  r x r or NULL (added to A only; Eq. (17))
+ *   B   = [b_1 b_2 b_3]  r x 3 complex128, b_i = U^H C o_i, so that the
+ *         reduced source is U^H r_i = i omega b_i and the o^T C^(2) U p and
+ *         t^M p terms of Eq. (19) are b_i^H p_j
+ *   c00 = o_i^T C^(1) o_j + c_ij + s_i^T o_j + s_j^T o_i   (3 x 3 float64)
+ *   G   = Phi^H X^-1 Phi, (2r+3) x (2r+3) complex128 Hermitian, or NULL
+ *         (then no certificate), with the columns of Phi ordered
+ *         [C o_1, C o_2, C o_3 | (K + eps M) U | C U]  (Lemma 4.2)
+ *   K_in (r x r or NULL): the part of K scaled by a permeability scale s_mu,
+ *         K(s_mu) = (K - K_in) + K_in / s_mu.
+ *   N0  (9 float64 or NULL): added to R (Eq. (6a)).
+ *   alpha (object size), alpha_lb (stability lower bound of Lemma 4.2),
+ *   vol_B (|B|, so that |B_alpha| = alpha^3 vol_B).
+ * Pointers may be host or device memory; they are copied before return.
+ * Returns MROM_EINVAL for r < 1, r > MROM_MAX_R, a null required pointer or
+ * a non-finite scalar. */
+#define MROM_MAX_R 112
+typedef struct {
+  int32_t r;
+  const void* K;
+  const void* K_in;
+  const void* C;
+  const void* Me;
+  const void* B;
+  const double* c00;
+  const void* G;
+  const double* N0;
+  double alpha;
+  double alpha_lb;
+  double vol_B;
+} mrom_reduced_desc;
+
+mrom_status mrom_rom_from_reduced(mrom_handle h, const mrom_reduced_desc* desc, mrom_rom_t* out);
+/* Basis size r of an object (per direction); 0 on a null object. */
+int32_t mrom_rom_rank(mrom_rom_t rom);
+void mrom_rom_free(mrom_rom_t rom);
+
+/* ------------------------------------------------------------------ sweep */
+
+/* On-line stage of Algorithm 1 for a batch of objects (Sect. 4.3):
+ * for every object o and frequency omega = omega[o*omega_stride + k]
+ * (omega_stride = 0: one grid shared by all objects; n_w: one grid each),
+ * solve (K + Me - i omega C) p_i = i omega b_i for i = 1..3 (Eq. (17)) and write
+ *   R[o][k][i][j] = -alpha^3/4 Re(p_i^H K p_j) (+ N0_ij)              (Eq. (18))
+ *   I[o][k][i][j] =  omega alpha^3/4 (c00_ij + Re(p_i^H C p_j
+ *                    + b_i^H p_j + b_j^H p_i))                       (Eq. (19))
+ *   Delta[o][k][i][j] (if Delta != NULL; Lemma 4.2, Eq. (20)):
+ *     alpha^3/(8 alpha_lb) (||r_i||^2 + ||r_j||^2 + ||r_i - r_j||^2),
+ *     ||r_i||^2 = w_i^H G w_i, w_i = [i omega e_i ; -p_i ; i omega p_i].
+ * The reduced solves use LU factorisation without pivoting, which is stable
+ * here because A's Hermitian part after a pi/4 rotation, (K + omega C)/sqrt(2),
+ * is positive definite for omega > 0.  omega must be finite and > 0; a
+ * violation is reported by the next mrom_synchronize (outputs for that
+ * frequency are NaN).  Delta != NULL requires every object to have a Gram
+ * matrix (else MROM_EINVAL).  R, I, Delta are device pointers with room for
+ * n_obj * n_w * 9 doubles; omega holds n_w (stride 0) or n_obj * n_w values.
+ * s_sigma, s_mu (device, n_obj each, or NULL for 1): per-object conductivity
+ * and permeability scales; s_sigma acts as omega -> s_sigma omega (nu is
+ * linear in omega sigma); s_mu != 1 requires K_in and no Delta. */
+mrom_status mrom_sweep(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega,
+                       int32_t n_w, int32_t omega_stride, const double* s_sigma, const double* s_mu,
+                       double* R, double* I, double* Delta);
+
+/* Certificate only: Delta as in mrom_sweep, without writing R and I. */
+mrom_status mrom_certificate(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega,
+                             int32_t n_w, int32_t omega_stride, double* Delta);
+
+/* A plan fixes a batch of objects and a frequency count once (device object
+ * table, cost-sorted work list); mrom_plan_sweep then runs the same sweep as
+ * mrom_sweep with no host-side preparation.  The plan keeps pointers to the
+ * objects, which must outlive it. */
+mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int32_t n_w,
+                             mrom_plan* out);
+mrom_status mrom_plan_sweep(mrom_plan plan, const double* omega, int32_t omega_stride,
+                            double* R, double* I, double* Delta);
+mrom_status mrom_plan_destroy(mrom_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MROM_H */

@@ -1,0 +1,225 @@
+"""Python binding of libmrom (reduced-order MPT spectral signatures on GB300).
+
+Argument marshalling only: every computation runs in the CUDA library.  The
+functions keep the C names of include/mrom.h (mrom_create, mrom_sweep, ...);
+array arguments are torch tensors (device tensors for compute calls; host or
+device for object creation) or numpy arrays (object creation only).
+Importing this module does not load the library; the first call does, and it
+raises if libmrom.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _abi
+from ._abi import MromError, lib, mrom_reduced_desc  # noqa: F401
+
+__all__ = [
+    "MromError", "lib", "Handle", "ReducedObject", "Plan",
+    "mrom_create", "mrom_destroy", "mrom_synchronize", "mrom_last_error", "mrom_launch_count",
+    "mrom_rom_from_reduced", "mrom_rom_free", "mrom_rom_rank", "mrom_sweep", "mrom_certificate",
+    "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy",
+]
+
+
+def _ptr(x) -> int:
+    """Raw data pointer of a contiguous torch tensor or numpy array (0 for None)."""
+    if x is None:
+        return 0
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return x.data_ptr()
+
+
+class Handle:
+    """An mrom_handle bound to a CUDA device and stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self._h = ctypes.c_void_p()
+        _abi.check(lib().mrom_create(int(device), ctypes.c_void_p(stream), ctypes.byref(self._h)), None)
+        self.device = device
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def synchronize(self):
+        _abi.check(lib().mrom_synchronize(self._h), self._h)
+
+    def launch_count(self) -> int:
+        return int(lib().mrom_launch_count(self._h))
+
+    def close(self):
+        if self._h:
+            lib().mrom_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ReducedObject:
+    """An mrom_rom_t created from reduced data (mrom_rom_from_reduced)."""
+
+    def __init__(self, handle: Handle, r: int, K, C, B, c00, *, G=None, K_in=None, Me=None, N0=None,
+                 alpha: float = 1.0, alpha_lb: float = 1.0 / np.sqrt(2.0), vol_B: float = 1.0):
+        keep = [_as_c128(K), _as_c128(C), _as_c128(B), _as_f64(c00), _as_c128(G), _as_c128(K_in),
+                _as_c128(Me), _as_f64(N0)]
+        d = mrom_reduced_desc()
+        d.r = int(r)
+        d.K, d.C, d.B = _ptr(keep[0]), _ptr(keep[1]), _ptr(keep[2])
+        d.c00 = ctypes.cast(_ptr(keep[3]), ctypes.POINTER(ctypes.c_double))
+        d.G, d.K_in, d.Me = _ptr(keep[4]), _ptr(keep[5]), _ptr(keep[6])
+        d.N0 = ctypes.cast(_ptr(keep[7]), ctypes.POINTER(ctypes.c_double)) if N0 is not None else None
+        d.alpha, d.alpha_lb, d.vol_B = float(alpha), float(alpha_lb), float(vol_B)
+        self._rom = ctypes.c_void_p()
+        self.handle = handle
+        _abi.check(lib().mrom_rom_from_reduced(handle.ptr, ctypes.byref(d), ctypes.byref(self._rom)),
+                   handle.ptr)
+        self.r = int(r)
+        self.has_cert = G is not None
+
+    @classmethod
+    def from_workload(cls, handle: Handle, obj, *, with_cert: bool = True):
+        """Create from a workloads.dictionary.ReducedObject (host numpy data)."""
+        return cls(handle, obj.r, obj.K, obj.C, obj.B, obj.c00, G=obj.G if with_cert else None,
+                   K_in=obj.K_in, alpha=obj.alpha, alpha_lb=obj.alpha_lb, vol_B=obj.vol_B)
+
+    @property
+    def ptr(self):
+        return self._rom
+
+    def close(self):
+        if self._rom:
+            lib().mrom_rom_free(self._rom)
+            self._rom = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _as_c128(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return np.ascontiguousarray(x, dtype=np.complex128)
+    import torch
+    return x.to(torch.complex128).contiguous()
+
+
+def _as_f64(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return np.ascontiguousarray(x, dtype=np.float64)
+    import torch
+    return x.to(torch.float64).contiguous()
+
+
+def _rom_array(objs):
+    arr = (ctypes.c_void_p * len(objs))()
+    for k, o in enumerate(objs):
+        arr[k] = o.ptr.value
+    return arr
+
+
+class Plan:
+    """mrom_plan: a fixed batch of objects and frequency count (mrom_plan_create)."""
+
+    def __init__(self, handle: Handle, objs, n_w: int):
+        self.handle = handle
+        self.objs = list(objs)
+        self.n_w = int(n_w)
+        self._p = ctypes.c_void_p()
+        _abi.check(lib().mrom_plan_create(handle.ptr, _rom_array(self.objs), len(self.objs), self.n_w,
+                                          ctypes.byref(self._p)), handle.ptr)
+
+    def sweep(self, omega, R, I, Delta=None, omega_stride: int = 0):
+        _abi.check(lib().mrom_plan_sweep(self._p, _ptr(omega), int(omega_stride), _ptr(R), _ptr(I),
+                                         _ptr(Delta)), self.handle.ptr)
+
+    def close(self):
+        if self._p:
+            lib().mrom_plan_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- C names
+
+def mrom_create(device: int = 0, stream=None) -> Handle:
+    return Handle(device, stream)
+
+
+def mrom_destroy(h: Handle) -> None:
+    h.close()
+
+
+def mrom_synchronize(h: Handle) -> None:
+    h.synchronize()
+
+
+def mrom_last_error(h: Handle) -> str:
+    return lib().mrom_last_error(h.ptr).decode()
+
+
+def mrom_launch_count(h: Handle) -> int:
+    return h.launch_count()
+
+
+def mrom_rom_from_reduced(h: Handle, obj, with_cert: bool = True) -> ReducedObject:
+    return ReducedObject.from_workload(h, obj, with_cert=with_cert)
+
+
+def mrom_rom_free(rom: ReducedObject) -> None:
+    rom.close()
+
+
+def mrom_rom_rank(rom: ReducedObject) -> int:
+    return int(lib().mrom_rom_rank(rom.ptr))
+
+
+def mrom_sweep(h: Handle, objs, omega, n_w: int, R, I, Delta=None, *, omega_stride: int = 0,
+               s_sigma=None, s_mu=None) -> None:
+    """Device tensors in, device tensors out (R, I, Delta: float64, n_obj*n_w*9)."""
+    _abi.check(lib().mrom_sweep(h.ptr, _rom_array(objs), len(objs), _ptr(omega), int(n_w),
+                                int(omega_stride), _ptr(s_sigma), _ptr(s_mu), _ptr(R), _ptr(I),
+                                _ptr(Delta)), h.ptr)
+
+
+def mrom_certificate(h: Handle, objs, omega, n_w: int, Delta, *, omega_stride: int = 0) -> None:
+    _abi.check(lib().mrom_certificate(h.ptr, _rom_array(objs), len(objs), _ptr(omega), int(n_w),
+                                      int(omega_stride), _ptr(Delta)), h.ptr)
+
+
+def mrom_plan_create(h: Handle, objs, n_w: int) -> Plan:
+    return Plan(h, objs, n_w)
+
+
+def mrom_plan_sweep(plan: Plan, omega, R, I, Delta=None, omega_stride: int = 0) -> None:
+    plan.sweep(omega, R, I, Delta, omega_stride)
+
+
+def mrom_plan_destroy(plan: Plan) -> None:
+    plan.close()

@@ -1,0 +1,84 @@
+"""ctypes declarations of include/mrom.h and library loading."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmrom.so")
+_LIB = None
+
+STATUS = {0: "MROM_OK", 1: "MROM_EINVAL", 2: "MROM_ENOMEM", 3: "MROM_ECUDA", 4: "MROM_ESINGULAR",
+          5: "MROM_ENOTCONVERGED", 6: "MROM_ETIMEOUT", 7: "MROM_ECALLBACK", 8: "MROM_ENOTSUP"}
+
+# Every function the header declares (checked by tests/test_abi.py).
+EXPORTS = [
+    "mrom_create", "mrom_destroy", "mrom_set_stream", "mrom_synchronize", "mrom_last_error",
+    "mrom_launch_count", "mrom_rom_from_reduced", "mrom_rom_rank", "mrom_rom_free", "mrom_sweep",
+    "mrom_certificate", "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy",
+]
+
+
+class MromError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class mrom_reduced_desc(ctypes.Structure):
+    _fields_ = [
+        ("r", ctypes.c_int32),
+        ("K", ctypes.c_void_p),
+        ("K_in", ctypes.c_void_p),
+        ("C", ctypes.c_void_p),
+        ("Me", ctypes.c_void_p),
+        ("B", ctypes.c_void_p),
+        ("c00", ctypes.POINTER(ctypes.c_double)),
+        ("G", ctypes.c_void_p),
+        ("N0", ctypes.POINTER(ctypes.c_double)),
+        ("alpha", ctypes.c_double),
+        ("alpha_lb", ctypes.c_double),
+        ("vol_B", ctypes.c_double),
+    ]
+
+
+def _declare(L):
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    sig = {
+        "mrom_create": (ctypes.c_int, [ctypes.c_int, vp, ctypes.POINTER(vp)]),
+        "mrom_destroy": (ctypes.c_int, [vp]),
+        "mrom_set_stream": (ctypes.c_int, [vp, vp]),
+        "mrom_synchronize": (ctypes.c_int, [vp]),
+        "mrom_last_error": (ctypes.c_char_p, [vp]),
+        "mrom_launch_count": (i64, [vp]),
+        "mrom_rom_from_reduced": (ctypes.c_int, [vp, ctypes.POINTER(mrom_reduced_desc), ctypes.POINTER(vp)]),
+        "mrom_rom_rank": (i32, [vp]),
+        "mrom_rom_free": (None, [vp]),
+        "mrom_sweep": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, dp, i32, i32, dp, dp, dp, dp, dp]),
+        "mrom_certificate": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, dp, i32, i32, dp]),
+        "mrom_plan_create": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, i32, ctypes.POINTER(vp)]),
+        "mrom_plan_sweep": (ctypes.c_int, [vp, dp, i32, dp, dp, dp]),
+        "mrom_plan_destroy": (ctypes.c_int, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def lib():
+    """Load libmrom.so (built by paper_2307_05590_gb300/build.py); raise if it is missing."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise MromError(3, f"{LIB_PATH} not built; run paper_2307_05590_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        _declare(L)
+        _LIB = L
+    return _LIB
+
+
+def check(status: int, handle) -> None:
+    if status != 0:
+        msg = lib().mrom_last_error(handle).decode() if handle else ""
+        raise MromError(status, msg)

@@ -1,0 +1,264 @@
+// Handles, plans and the sweep entry points of the C ABI.
+#include "mrom_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+namespace mrom {
+
+mrom_status fail(mrom_ctx* h, mrom_status s, const std::string& msg) {
+  if (h) h->last_error = msg;
+  return s;
+}
+
+mrom_status cuda_fail(mrom_ctx* h, cudaError_t e, const char* what) {
+  if (h) h->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? MROM_ENOMEM : MROM_ECUDA;
+}
+
+}  // namespace mrom
+
+using namespace mrom;
+
+extern "C" mrom_status mrom_create(int device, void* cuda_stream, mrom_handle* out) {
+  if (!out) return MROM_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return MROM_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return MROM_ECUDA;
+  auto* h = new mrom_ctx();
+  h->device = device;
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  h->smem_optin = (size_t)optin;
+  if (cuda_stream) {
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return MROM_ECUDA;
+    }
+    h->stream = h->own_stream;
+  }
+  if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    if (h->d_status) cudaFree(h->d_status);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+    return MROM_ENOMEM;
+  }
+  *out = h;
+  return MROM_OK;
+}
+
+extern "C" mrom_status mrom_destroy(mrom_handle h) {
+  if (!h) return MROM_EINVAL;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  if (h->d_status) cudaFree(h->d_status);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  delete h;
+  return MROM_OK;
+}
+
+extern "C" mrom_status mrom_set_stream(mrom_handle h, void* cuda_stream) {
+  if (!h) return MROM_EINVAL;
+  h->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : h->own_stream;
+  if (!h->stream) {
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(h, MROM_ECUDA, "mrom_set_stream: stream creation failed");
+    h->stream = h->own_stream;
+  }
+  return MROM_OK;
+}
+
+extern "C" const char* mrom_last_error(mrom_handle h) {
+  return h ? h->last_error.c_str() : "null handle";
+}
+
+extern "C" int64_t mrom_launch_count(mrom_handle h) { return h ? h->launches : 0; }
+
+extern "C" mrom_status mrom_synchronize(mrom_handle h) {
+  if (!h) return MROM_EINVAL;
+  cudaSetDevice(h->device);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_synchronize");
+  int st = 0;
+  e = cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_synchronize: status read");
+  if (st) {
+    cudaMemset(h->d_status, 0, sizeof(int));
+    if (st & kStatusBadOmega) return fail(h, MROM_EINVAL, "a frequency was non-finite or <= 0");
+    if (st & kStatusSingular) return fail(h, MROM_ESINGULAR, "zero or non-finite pivot in a reduced solve");
+    if (st & kStatusTimeout) return fail(h, MROM_ETIMEOUT, "a bounded device wait gave up");
+  }
+  mrom_status p = h->pending;
+  h->pending = MROM_OK;
+  return p;
+}
+
+// ------------------------------------------------------------------ plans
+
+namespace {
+
+size_t sweep_budget(const mrom_ctx* h) {
+  // leave room for static shared memory and the per-CTA reservation
+  return std::min<size_t>(h->smem_optin, 227 * 1024) - 2048;
+}
+
+}  // namespace
+
+extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int32_t n_w,
+                                        mrom_plan* out) {
+  if (!h) return MROM_EINVAL;
+  if (!roms || !out || n_obj < 1 || n_w < 1) return fail(h, MROM_EINVAL, "mrom_plan_create: bad arguments");
+  *out = nullptr;
+  for (int o = 0; o < n_obj; ++o)
+    if (!roms[o] || roms[o]->ctx != h) return fail(h, MROM_EINVAL, "mrom_plan_create: invalid object");
+  cudaSetDevice(h->device);
+  const size_t budget = sweep_budget(h);
+  std::vector<RomDev> objs(n_obj);
+  std::vector<SweepTask> tasks;
+  std::vector<double> cost;
+  bool all_cert = true;
+  size_t smem = 0;
+  for (int o = 0; o < n_obj; ++o) {
+    const mrom_rom* m = roms[o];
+    RomDev& d = objs[o];
+    d.K = m->K;
+    d.C = m->C;
+    d.Me = m->Me;
+    d.B = m->B;
+    d.GKK = m->GKK;
+    d.GCC = m->GCC;
+    d.GSk = m->GSk;
+    d.gsK = m->gsK;
+    d.gsC = m->gsC;
+    std::memcpy(d.gss, m->gss, sizeof(d.gss));
+    std::memcpy(d.c00, m->c00, sizeof(d.c00));
+    std::memcpy(d.N0, m->N0, sizeof(d.N0));
+    d.alpha3 = m->alpha * m->alpha * m->alpha;
+    d.cert_scale = m->has_cert ? d.alpha3 / (4.0 * m->alpha_lb) : 0.0;
+    d.r = m->r;
+    d.has_cert = m->has_cert ? 1 : 0;
+    all_cert = all_cert && m->has_cert;
+    const size_t per = sweep_fp64_bytes_per_system(m->r);
+    if (per > budget) return fail(h, MROM_ENOTSUP, "mrom_plan_create: r too large for shared memory");
+    const int smax = (int)std::max<size_t>(1, budget / per);
+    const int S = std::min(n_w, smax);
+    const double r = m->r;
+    const double unit = 4.0 * r * r * r / 3.0 + 54.0 * r * r;
+    for (int w0 = 0; w0 < n_w; w0 += S) {
+      const int nw = std::min(S, n_w - w0);
+      tasks.push_back(SweepTask{o, w0, nw, 0});
+      cost.push_back(unit * nw);
+      smem = std::max(smem, per * nw);
+    }
+  }
+  // longest tasks first: CTAs pull from the front of the list
+  std::vector<int> order(tasks.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<SweepTask> sorted(tasks.size());
+  for (size_t k = 0; k < order.size(); ++k) sorted[k] = tasks[order[k]];
+
+  auto* plan = new mrom_plan_s();
+  plan->ctx = h;
+  plan->n_obj = n_obj;
+  plan->n_w = n_w;
+  plan->all_cert = all_cert;
+  plan->smem_bytes = smem;
+  plan->n_tasks = (int)sorted.size();
+  cudaError_t e = sweep_fp64_configure(smem);
+  int occ = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_fp64_symbol(), sweep_fp64_threads(), smem);
+  occ = std::max(occ, 1);
+  plan->grid = std::min(plan->n_tasks, h->num_sms * occ);
+  const size_t bytes = n_obj * sizeof(RomDev) + sorted.size() * sizeof(SweepTask) + 16;
+  void* blk = nullptr;
+  // stream-ordered allocation: the plan's tables are freed with cudaFreeAsync, so a
+  // one-shot mrom_sweep never blocks the host
+  if (e == cudaSuccess) e = cudaMallocAsync(&blk, bytes, h->stream);
+  if (e != cudaSuccess) {
+    delete plan;
+    return cuda_fail(h, e, "mrom_plan_create");
+  }
+  plan->d_objs = static_cast<RomDev*>(blk);
+  plan->d_tasks = reinterpret_cast<SweepTask*>(plan->d_objs + n_obj);
+  plan->d_counter = reinterpret_cast<int*>(plan->d_tasks + sorted.size());
+  e = cudaMemcpyAsync(plan->d_objs, objs.data(), n_obj * sizeof(RomDev), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(plan->d_tasks, sorted.data(), sorted.size() * sizeof(SweepTask),
+                        cudaMemcpyHostToDevice, h->stream);
+  // (copies from pageable host memory return once the source has been staged)
+  if (e != cudaSuccess) {
+    cudaFreeAsync(blk, h->stream);
+    delete plan;
+    return cuda_fail(h, e, "mrom_plan_create: upload");
+  }
+  *out = plan;
+  return MROM_OK;
+}
+
+extern "C" mrom_status mrom_plan_destroy(mrom_plan plan) {
+  if (!plan) return MROM_EINVAL;
+  cudaSetDevice(plan->ctx->device);
+  cudaFreeAsync(plan->d_objs, plan->ctx->stream);
+  delete plan;
+  return MROM_OK;
+}
+
+namespace {
+
+mrom_status run_plan(mrom_plan plan, const double* omega, int32_t omega_stride, const double* s_sigma,
+                     double* R, double* I, double* Delta) {
+  mrom_ctx* h = plan->ctx;
+  if (!omega) return fail(h, MROM_EINVAL, "sweep: omega is null");
+  if (omega_stride != 0 && omega_stride < plan->n_w)
+    return fail(h, MROM_EINVAL, "sweep: omega_stride must be 0 or >= n_w");
+  if (Delta && !plan->all_cert)
+    return fail(h, MROM_EINVAL, "sweep: Delta requested but an object has no Gram matrix");
+  if (!R && !I && !Delta) return MROM_OK;
+  cudaSetDevice(h->device);
+  cudaError_t e = cudaMemsetAsync(plan->d_counter, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess)
+    e = launch_sweep_fp64(plan->d_objs, plan->d_tasks, plan->n_tasks, plan->d_counter, omega, omega_stride,
+                          s_sigma, R, I, Delta, h->d_status, plan->n_w, plan->grid, plan->smem_bytes,
+                          h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sweep launch");
+  ++h->launches;
+  return MROM_OK;
+}
+
+}  // namespace
+
+extern "C" mrom_status mrom_plan_sweep(mrom_plan plan, const double* omega, int32_t omega_stride, double* R,
+                                       double* I, double* Delta) {
+  if (!plan) return MROM_EINVAL;
+  return run_plan(plan, omega, omega_stride, nullptr, R, I, Delta);
+}
+
+extern "C" mrom_status mrom_sweep(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega,
+                                  int32_t n_w, int32_t omega_stride, const double* s_sigma, const double* s_mu,
+                                  double* R, double* I, double* Delta) {
+  if (!h) return MROM_EINVAL;
+  if (s_mu) return fail(h, MROM_ENOTSUP, "mrom_sweep: s_mu scaling is supported by mrom_sweep_vjp only");
+  mrom_plan plan = nullptr;
+  mrom_status st = mrom_plan_create(h, roms, n_obj, n_w, &plan);
+  if (st != MROM_OK) return st;
+  st = run_plan(plan, omega, omega_stride, s_sigma, R, I, Delta);
+  mrom_plan_destroy(plan);
+  return st;
+}
+
+extern "C" mrom_status mrom_certificate(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj,
+                                        const double* omega, int32_t n_w, int32_t omega_stride, double* Delta) {
+  if (!h) return MROM_EINVAL;
+  if (!Delta) return fail(h, MROM_EINVAL, "mrom_certificate: Delta is null");
+  return mrom_sweep(h, roms, n_obj, omega, n_w, omega_stride, nullptr, nullptr, nullptr, nullptr, Delta);
+}

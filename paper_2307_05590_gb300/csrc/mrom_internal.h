@@ -1,0 +1,114 @@
+// Internal types shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mrom.h"
+
+namespace mrom {
+
+// Device status word bits (set by kernels with atomicOr, read by mrom_synchronize).
+enum : int {
+  kStatusBadOmega = 1,    // non-finite or non-positive frequency
+  kStatusSingular = 2,    // zero or non-finite pivot
+  kStatusTimeout = 4,     // a bounded wait gave up
+};
+
+// Per-object record read by the sweep kernels (device copy lives in a plan).
+// All matrices are row-major complex128 (double2).
+struct RomDev {
+  const double2* K;     // r x r, used in R (Eq. (18)) and in A
+  const double2* C;     // r x r
+  const double2* Me;    // r x r or nullptr: U^H (eps M) U, added to A only
+  const double2* B;     // r x 3: b_i in column i
+  const double2* GKK;   // r x r  Gram block [(K+eps M)U]^H X^-1 [(K+eps M)U]
+  const double2* GCC;   // r x r  Gram block (CU)^H X^-1 (CU)
+  const double2* GSk;   // r x r  G_CK - G_KC (skew-Hermitian)
+  const double2* gsK;   // 3 x r  rows of G: source column i against the K block
+  const double2* gsC;   // 3 x r  rows of G: source column i against the C block
+  double gss[9];        // Re G between source columns
+  double c00[9];
+  double N0[9];
+  double alpha3;        // alpha^3
+  double cert_scale;    // alpha^3 / (4 alpha_lb)
+  int r;
+  int has_cert;
+};
+
+// One unit of work: S consecutive frequencies of one object.
+struct SweepTask {
+  int obj;
+  int w0;
+  int nw;
+  int pad;
+};
+
+}  // namespace mrom
+
+// Opaque ABI objects.
+struct mrom_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  int* d_status = nullptr;        // device status word
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  int64_t launches = 0;
+  mrom_status pending = MROM_OK;  // host-detected asynchronous error
+  std::string last_error;
+};
+
+struct mrom_rom {
+  mrom_ctx* ctx = nullptr;
+  int r = 0;
+  double alpha = 1.0, alpha_lb = 0.0, vol_B = 0.0;
+  // device storage (one allocation, views below)
+  void* d_block = nullptr;
+  double2 *K = nullptr, *Kin = nullptr, *C = nullptr, *Me = nullptr, *B = nullptr;
+  double2 *GKK = nullptr, *GCC = nullptr, *GSk = nullptr, *gsK = nullptr, *gsC = nullptr;
+  double2* G = nullptr;          // full Gram, kept for certificate-only consumers
+  double gss[9] = {0};
+  double c00[9] = {0};
+  double N0[9] = {0};
+  bool has_cert = false;
+  bool has_kin = false;
+};
+
+struct mrom_plan_s {
+  mrom_ctx* ctx = nullptr;
+  int n_obj = 0, n_w = 0;
+  bool all_cert = false;
+  size_t smem_bytes = 0;
+  int n_tasks = 0;
+  int grid = 0;
+  mrom::RomDev* d_objs = nullptr;
+  mrom::SweepTask* d_tasks = nullptr;
+  int* d_counter = nullptr;
+};
+
+namespace mrom {
+
+// Set the handle's last error message and return the status.
+mrom_status fail(mrom_ctx* h, mrom_status s, const std::string& msg);
+mrom_status cuda_fail(mrom_ctx* h, cudaError_t e, const char* what);
+
+// Sweep kernel launcher (sweep_fp64.cu).
+size_t sweep_fp64_bytes_per_system(int r);
+int sweep_fp64_threads();
+cudaError_t sweep_fp64_configure(size_t smem_bytes);
+const void* sweep_fp64_symbol();
+cudaError_t launch_sweep_fp64(const RomDev* objs, const SweepTask* tasks, int n_tasks, int* counter,
+                              const double* omega, int omega_stride, const double* s_sigma,
+                              double* R, double* I, double* Delta, int* status, int n_w, int grid,
+                              size_t smem_bytes, cudaStream_t stream);
+
+// Certificate pre-processing of a Gram matrix (rom.cu).
+cudaError_t launch_split_gram(const double2* G, int r, double2* GKK, double2* GCC, double2* GSk,
+                              double2* gsK, double2* gsC, cudaStream_t stream);
+// Sets *flag (device int) to 1 when any of the n doubles at x is not finite.
+cudaError_t launch_nonfinite(const double* x, size_t n, int* flag, cudaStream_t stream);
+
+}  // namespace mrom

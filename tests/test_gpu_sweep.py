@@ -1,0 +1,134 @@
+"""GPU parity of mrom_sweep (reduced solves, Eqs. (17)-(19), certificate of Lemma 4.2)
+against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def mrom():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_05590_gb300 import build
+    build.build()
+    import paper_2307_05590_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def handle(mrom):
+    return mrom.Handle(0)
+
+
+def _run(mrom, handle, objs, omega, n_w, with_delta=True, omega_stride=0, s_sigma=None):
+    import torch
+    dev = torch.device("cuda", 0)
+    roms = [mrom.ReducedObject.from_workload(handle, o) for o in objs]
+    n = len(objs)
+    om = torch.as_tensor(np.ascontiguousarray(omega), dtype=torch.float64, device=dev)
+    R = torch.full((n, n_w, 3, 3), np.nan, dtype=torch.float64, device=dev)
+    I = torch.full_like(R, np.nan)
+    D = torch.full_like(R, np.nan) if with_delta else None
+    ss = torch.as_tensor(s_sigma, dtype=torch.float64, device=dev) if s_sigma is not None else None
+    mrom.mrom_sweep(handle, roms, om, n_w, R, I, D, omega_stride=omega_stride, s_sigma=ss)
+    handle.synchronize()
+    out = (R.cpu().numpy(), I.cpu().numpy(), D.cpu().numpy() if with_delta else None)
+    for r in roms:
+        r.close()
+    return out
+
+
+def test_sweep_matches_oracle_across_tile_boundaries(mrom, handle):
+    """r spans warp/tile boundaries; 250 frequencies make ragged frequency chunks."""
+    from workloads import log_omegas, reduced_object
+    from gpu_common import oracle_sweep, rel_errors
+    rs = [1, 2, 3, 8, 17, 31, 32, 33, 64, 95, 96, 112]
+    objs = [reduced_object(20230711, 100 + k, r) for k, r in enumerate(rs)]
+    wo = log_omegas(1e1, 1e8, 250)
+    Rg, Ig, Dg = _run(mrom, handle, objs, wo, wo.size)
+    for k, obj in enumerate(objs):
+        R, I, Dl, sI, sD = oracle_sweep(obj, wo)
+        eR, eI, eD = rel_errors(Rg[k], Ig[k], Dg[k], R, I, Dl, sI, sD)
+        assert eR <= TOL and eI <= TOL and eD <= TOL, (obj.r, eR, eI, eD)
+
+
+def test_per_object_grids_and_conductivity_scale(mrom, handle):
+    from workloads import log_omegas, reduced_object
+    from gpu_common import oracle_sweep, rel_errors
+    objs = [reduced_object(5, k, r) for k, r in enumerate([9, 40, 77])]
+    n_w = 41
+    grids = np.stack([log_omegas(10.0 ** (1 + k), 1e7, n_w) for k in range(3)])
+    ss = np.array([0.5, 1.0, 2.0])
+    Rg, Ig, Dg = _run(mrom, handle, objs, grids, n_w, omega_stride=n_w, s_sigma=ss)
+    for k, obj in enumerate(objs):
+        R, I, Dl, sI, sD = oracle_sweep(obj, grids[k], s_sigma=ss[k])
+        eR, eI, eD = rel_errors(Rg[k], Ig[k], Dg[k], R, I, Dl, sI, sD)
+        assert eR <= TOL and eI <= TOL and eD <= TOL, (obj.r, eR, eI, eD)
+
+
+def test_certificate_only_and_no_certificate(mrom, handle):
+    import torch
+    from workloads import log_omegas, reduced_object
+    from gpu_common import oracle_sweep
+    obj = reduced_object(9, 0, 20)
+    wo = log_omegas(1e1, 1e8, 30)
+    rom = mrom.ReducedObject.from_workload(handle, obj)
+    om = torch.as_tensor(wo, device="cuda")
+    D = torch.empty(30 * 9, dtype=torch.float64, device="cuda")
+    mrom.mrom_certificate(handle, [rom], om, 30, D)
+    handle.synchronize()
+    _, _, Dl, _, sD = oracle_sweep(obj, wo)
+    err = np.abs(D.cpu().numpy().reshape(30, 3, 3) - Dl).reshape(30, -1).max(1) / sD
+    assert err.max() <= TOL
+    # an object without a Gram matrix: R and I work, Delta is refused
+    rom2 = mrom.ReducedObject.from_workload(handle, obj, with_cert=False)
+    R = torch.empty(30 * 9, dtype=torch.float64, device="cuda")
+    I = torch.empty_like(R)
+    mrom.mrom_sweep(handle, [rom2], om, 30, R, I)
+    handle.synchronize()
+    with pytest.raises(mrom.MromError) as ei:
+        mrom.mrom_sweep(handle, [rom2], om, 30, R, I, D)
+    assert ei.value.status == 1
+
+
+def test_device_detected_bad_frequency(mrom, handle):
+    import torch
+    from workloads import reduced_object
+    rom = mrom.ReducedObject.from_workload(handle, reduced_object(9, 1, 10))
+    om = torch.tensor([10.0, -5.0, 100.0], dtype=torch.float64, device="cuda")
+    R = torch.empty(27, dtype=torch.float64, device="cuda")
+    I = torch.empty_like(R)
+    mrom.mrom_sweep(handle, [rom], om, 3, R, I)
+    with pytest.raises(mrom.MromError) as ei:
+        handle.synchronize()
+    assert ei.value.status == 1
+    handle.synchronize()  # status cleared
+
+
+def test_invalid_objects_rejected(mrom, handle):
+    from workloads import reduced_object
+    obj = reduced_object(9, 2, 6)
+    K = obj.K.copy()
+    K[1, 2] = np.nan
+    with pytest.raises(mrom.MromError) as ei:
+        mrom.ReducedObject(handle, 6, K, obj.C, obj.B, obj.c00)
+    assert ei.value.status == 1
+    with pytest.raises(mrom.MromError):
+        mrom.ReducedObject(handle, 113, np.zeros((113, 113)), np.zeros((113, 113)), np.zeros((113, 3)),
+                           obj.c00)
+
+
+def test_launch_count_increases(mrom, handle):
+    import torch
+    from workloads import reduced_object
+    rom = mrom.ReducedObject.from_workload(handle, reduced_object(9, 3, 12))
+    om = torch.tensor([10.0, 20.0], dtype=torch.float64, device="cuda")
+    R = torch.empty(18, dtype=torch.float64, device="cuda")
+    before = handle.launch_count()
+    mrom.mrom_sweep(handle, [rom], om, 2, R, torch.empty_like(R))
+    handle.synchronize()
+    assert handle.launch_count() == before + 1
