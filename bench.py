@@ -46,20 +46,23 @@ SWEEP_DRAM_BYTES_PER_LAUNCH = None
 def flops_per_eval(r: int, cert: bool = True) -> float:
     """FP64 flops of one (object, frequency) evaluation as the sweep kernel computes it.
 
-    FMA = 2 flops, multiply = 1.  Complex multiply-add = 4 FMA.
-    form A (2 FMA/entry), elimination of the augmented [A | 3 rhs] without pivoting,
-    3 back substitutions, y = K p, C p (3 rhs each), G~ formation (2x2 FMA/entry) and
-    G~ p, then the 36 length-r reductions of the quadratic forms.
+    FMA = 2 flops, multiply = 1; a complex multiply-add is 4 FMA (8 flops).
+      form A                      2 FMA per entry                       4 r^2
+      elimination, no pivoting    sum_m [m (m+3) updates + m multipliers]
+      back substitution           3 right-hand sides
+      forms y = (L + D/2) p       3 rhs x r(r+1)/2 per Hermitian matrix (K, C, G~)
+      G~(omega) entries           4 FMA per lower-triangle entry
+      reductions                  45 length-r dot products
     """
     r = int(r)
     m = np.arange(1, r)
-    elim = 8.0 * np.sum(m * (m + 3)) + 6.0 * np.sum(m)    # updates + multipliers
-    back = 8.0 * 3 * r * (r - 1) / 2 + 6.0 * 3 * r
+    elim = 8.0 * np.sum(m * (m + 3)) + 6.0 * np.sum(m)
+    back = 3 * (8.0 * r * (r - 1) / 2 + 6.0 * r)
     form = 4.0 * r * r
-    mats = 2 if not cert else 3
-    matvec = 8.0 * 3 * r * r * mats + (8.0 * r * r if cert else 0.0)
-    red = 4.0 * r * (18 if cert else 12) + 4.0 * r * 9 + (12.0 * r * 9 if cert else 0.0)
-    return elim + back + form + matvec + red
+    mats = 3 if cert else 2
+    forms = 12.0 * r * (r + 1) * mats + (4.0 * r * (r + 1) if cert else 0.0)
+    red = (108.0 + 36.0 + 90.0) * r if cert else (72.0 + 36.0) * r
+    return float(elim + back + form + forms + red)
 
 
 class ClockSampler:

@@ -105,9 +105,13 @@ extern "C" mrom_status mrom_synchronize(mrom_handle h) {
 
 namespace {
 
+// Dynamic shared memory per CTA: half of an SM's shared memory, so that two CTAs
+// co-reside and fill each other's barrier waits (minus the per-CTA reservation).
 size_t sweep_budget(const mrom_ctx* h) {
-  // leave room for static shared memory and the per-CTA reservation
-  return std::min<size_t>(h->smem_optin, 227 * 1024) - 2048;
+  int per_sm = 0;
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
+  const size_t half = (size_t)per_sm / 2;
+  return std::min<size_t>(h->smem_optin, half) - 2048;
 }
 
 }  // namespace
@@ -125,7 +129,7 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
   std::vector<SweepTask> tasks;
   std::vector<double> cost;
   bool all_cert = true;
-  size_t smem = 0;
+  size_t smem = 0, ws_elems = 0;
   for (int o = 0; o < n_obj; ++o) {
     const mrom_rom* m = roms[o];
     RomDev& d = objs[o];
@@ -146,15 +150,18 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
     d.r = m->r;
     d.has_cert = m->has_cert ? 1 : 0;
     all_cert = all_cert && m->has_cert;
-    const size_t per = sweep_fp64_bytes_per_system(m->r);
-    if (per > budget) return fail(h, MROM_ENOTSUP, "mrom_plan_create: r too large for shared memory");
-    const int smax = (int)std::max<size_t>(1, budget / per);
-    const int S = std::min(n_w, smax);
+    // matrices in shared memory when at least one system fits the budget, otherwise
+    // in the CTA's slice of an L2-resident global workspace (one system per task)
+    const size_t per_s = sweep_fp64_bytes_per_system(m->r, true);
+    const bool in_smem = per_s <= budget;
+    const size_t per = in_smem ? per_s : sweep_fp64_bytes_per_system(m->r, false);
+    const int S = in_smem ? std::min<int>(n_w, (int)(budget / per_s)) : 1;
+    if (!in_smem) ws_elems = std::max(ws_elems, sweep_fp64_matrix_elems(m->r));
     const double r = m->r;
-    const double unit = 4.0 * r * r * r / 3.0 + 54.0 * r * r;
+    const double unit = 4.0 * r * r * r / 3.0 + 30.0 * r * r;
     for (int w0 = 0; w0 < n_w; w0 += S) {
       const int nw = std::min(S, n_w - w0);
-      tasks.push_back(SweepTask{o, w0, nw, 0});
+      tasks.push_back(SweepTask{o, w0, nw, in_smem ? 0 : 1});
       cost.push_back(unit * nw);
       smem = std::max(smem, per * nw);
     }
@@ -179,7 +186,9 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_fp64_symbol(), sweep_fp64_threads(), smem);
   occ = std::max(occ, 1);
   plan->grid = std::min(plan->n_tasks, h->num_sms * occ);
-  const size_t bytes = n_obj * sizeof(RomDev) + sorted.size() * sizeof(SweepTask) + 16;
+  plan->ws_elems = ws_elems;
+  const size_t ws_bytes = ws_elems * sizeof(double2) * (size_t)plan->grid;
+  const size_t bytes = ws_bytes + n_obj * sizeof(RomDev) + sorted.size() * sizeof(SweepTask) + 16;
   void* blk = nullptr;
   // stream-ordered allocation: the plan's tables are freed with cudaFreeAsync, so a
   // one-shot mrom_sweep never blocks the host
@@ -188,7 +197,8 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
     delete plan;
     return cuda_fail(h, e, "mrom_plan_create");
   }
-  plan->d_objs = static_cast<RomDev*>(blk);
+  plan->d_workspace = ws_elems ? static_cast<double2*>(blk) : nullptr;
+  plan->d_objs = reinterpret_cast<RomDev*>(static_cast<char*>(blk) + ws_bytes);
   plan->d_tasks = reinterpret_cast<SweepTask*>(plan->d_objs + n_obj);
   plan->d_counter = reinterpret_cast<int*>(plan->d_tasks + sorted.size());
   e = cudaMemcpyAsync(plan->d_objs, objs.data(), n_obj * sizeof(RomDev), cudaMemcpyHostToDevice, h->stream);
@@ -208,7 +218,8 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
 extern "C" mrom_status mrom_plan_destroy(mrom_plan plan) {
   if (!plan) return MROM_EINVAL;
   cudaSetDevice(plan->ctx->device);
-  cudaFreeAsync(plan->d_objs, plan->ctx->stream);
+  cudaFreeAsync(plan->d_workspace ? static_cast<void*>(plan->d_workspace) : static_cast<void*>(plan->d_objs),
+                plan->ctx->stream);
   delete plan;
   return MROM_OK;
 }
@@ -225,11 +236,12 @@ mrom_status run_plan(mrom_plan plan, const double* omega, int32_t omega_stride, 
     return fail(h, MROM_EINVAL, "sweep: Delta requested but an object has no Gram matrix");
   if (!R && !I && !Delta) return MROM_OK;
   cudaSetDevice(h->device);
-  cudaError_t e = cudaMemsetAsync(plan->d_counter, 0, sizeof(int), h->stream);
+  cudaError_t e = sweep_fp64_configure(plan->smem_bytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(plan->d_counter, 0, sizeof(int), h->stream);
   if (e == cudaSuccess)
     e = launch_sweep_fp64(plan->d_objs, plan->d_tasks, plan->n_tasks, plan->d_counter, omega, omega_stride,
                           s_sigma, R, I, Delta, h->d_status, plan->n_w, plan->grid, plan->smem_bytes,
-                          h->stream);
+                          plan->d_workspace, plan->ws_elems, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "sweep launch");
   ++h->launches;
   return MROM_OK;

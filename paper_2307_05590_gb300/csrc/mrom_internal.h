@@ -87,6 +87,8 @@ struct mrom_plan_s {
   mrom::RomDev* d_objs = nullptr;
   mrom::SweepTask* d_tasks = nullptr;
   int* d_counter = nullptr;
+  double2* d_workspace = nullptr;   // grid x ws_elems complex128, for tasks whose matrices are global
+  size_t ws_elems = 0;
 };
 
 namespace mrom {
@@ -95,15 +97,17 @@ namespace mrom {
 mrom_status fail(mrom_ctx* h, mrom_status s, const std::string& msg);
 mrom_status cuda_fail(mrom_ctx* h, cudaError_t e, const char* what);
 
-// Sweep kernel launcher (sweep_fp64.cu).
-size_t sweep_fp64_bytes_per_system(int r);
+// Sweep kernel launcher (sweep_fp64.cu).  A task's matrices live in shared memory
+// (SweepTask.pad bit 0 clear) or in the CTA's slice of a global workspace (bit 0 set).
+size_t sweep_fp64_matrix_elems(int r);
+size_t sweep_fp64_bytes_per_system(int r, bool matrix_in_smem);
 int sweep_fp64_threads();
 cudaError_t sweep_fp64_configure(size_t smem_bytes);
 const void* sweep_fp64_symbol();
 cudaError_t launch_sweep_fp64(const RomDev* objs, const SweepTask* tasks, int n_tasks, int* counter,
                               const double* omega, int omega_stride, const double* s_sigma,
                               double* R, double* I, double* Delta, int* status, int n_w, int grid,
-                              size_t smem_bytes, cudaStream_t stream);
+                              size_t smem_bytes, double2* workspace, size_t ws_elems, cudaStream_t stream);
 
 // Certificate pre-processing of a Gram matrix (rom.cu).
 cudaError_t launch_split_gram(const double2* G, int r, double2* GKK, double2* GCC, double2* GSk,

@@ -8,15 +8,19 @@
 //   2. eliminates without pivoting (A is sectorial: e^{i pi/4} A has the
 //      positive definite Hermitian part (K + omega C)/sqrt(2), which bounds the
 //      growth of Gaussian elimination);
-//   3. back-substitutes the three right-hand sides;
-//   4. forms y = M p for M in {K, C, G~(omega)} and the quadratic forms of
-//      Eq. (18) (R), Eq. (19) (I) and, for the certificate of Lemma 4.2,
+//   3. back-substitutes the three right-hand sides (one warp per system and
+//      right-hand side, warp-synchronous);
+//   4. forms y = (L + D/2) p for the Hermitian M = L + D + L^H in
+//      {K, C, G~(omega)}, so that Re(p_i^H M p_j) = Re(p_i^H y_j) + Re(p_j^H y_i)
+//      at half the cost of M p, and reduces the quadratic forms of Eq. (18)
+//      (R), Eq. (19) (I) and, for the certificate of Lemma 4.2,
 //      w_i^H G w_j = omega^2 Re G_ss + 2 Re(...) + p_i^H G~(omega) p_j with
 //      G~(omega) = G_KK + omega^2 G_CC + i omega (G_CK - G_KC);
 //   5. writes R, I and Delta.
-// The FP64 pipe is the roofline of this kernel (GB300 executes two DFMA per
-// clock per SM), so every phase spreads its work over all threads of the CTA,
-// and all indexing runs on the integer pipes.  CTAs pull tasks from a
+// The FP64 pipe is the roofline (GB300: two DFMA per clock per SM).  Two CTAs
+// share an SM so that one CTA's barrier waits are filled by the other's
+// arithmetic; systems too large for half an SM's shared memory keep their
+// matrices in an L2-resident global workspace.  CTAs pull tasks from a
 // cost-sorted list through an atomic counter (no waits).
 #include "mrom_internal.h"
 
@@ -24,7 +28,8 @@ namespace mrom {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kRed = 36;  // reduced scalars per system
+constexpr int kWarps = kThreads / 32;
+constexpr int kRed = 45;  // reduced scalars per system
 
 __device__ __forceinline__ double2 c_mac(double2 c, double2 a, double2 b) {   // c + a b
   return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
@@ -47,23 +52,16 @@ __device__ __forceinline__ double2 c_recip(double2 a, int* status) {
   return make_double2(ax / d, -ay / d);
 }
 
-__device__ __forceinline__ void pair_ij(int q, int& i, int& j) {
-  // (0,0) (0,1) (0,2) (1,1) (1,2) (2,2)
-  const int ti[6] = {0, 0, 0, 1, 1, 2};
-  const int tj[6] = {0, 1, 2, 1, 2, 2};
-  i = ti[q];
-  j = tj[q];
-}
-
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__ tasks, int n_tasks,
                   int* __restrict__ counter, const double* __restrict__ omega, int omega_stride,
                   const double* __restrict__ s_sigma, double* __restrict__ Rout,
                   double* __restrict__ Iout, double* __restrict__ Dout, int* __restrict__ status,
-                  int n_w) {
+                  int n_w, double2* __restrict__ workspace, size_t ws_elems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_task;
   const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
 
   for (;;) {
     if (tid == 0) s_task = atomicAdd(counter, 1);
@@ -76,13 +74,23 @@ sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__
     const RomDev& ob = objs[task.obj];
     const int r = ob.r, S = task.nw, ld = r + 3;
     const bool want_cert = (Dout != nullptr) && ob.has_cert;
+    const bool in_global = (task.pad & 1) != 0;
 
+    // buffers: matrices (shared memory, or this CTA's slice of the global workspace),
+    // then solutions, pivot inverses, frequencies and reductions in shared memory
     const int am_elems = max(r * ld, 9 * r);
-    double2* Am = reinterpret_cast<double2*>(smem_raw);          // S * am_elems
-    double2* Pm = Am + (size_t)S * am_elems;                      // S * r * 3
-    double2* Inv = Pm + (size_t)S * r * 3;                        // S * r
-    double* Ws = reinterpret_cast<double*>(Inv + (size_t)S * r);  // S
-    double* Red = Ws + S;                                         // S * kRed
+    double2* sp = reinterpret_cast<double2*>(smem_raw);
+    double2* Am;
+    if (in_global) {
+      Am = workspace + (size_t)blockIdx.x * ws_elems;
+    } else {
+      Am = sp;
+      sp += (size_t)S * am_elems;
+    }
+    double2* Pm = sp;
+    double2* Inv = Pm + (size_t)S * r * 3;
+    double* Ws = reinterpret_cast<double*>(Inv + (size_t)S * r);
+    double* Red = Ws + S;
 
     // ---- frequencies (s_sigma acts as omega -> s_sigma omega)
     const double ssig = s_sigma ? s_sigma[task.obj] : 1.0;
@@ -120,7 +128,7 @@ sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__
     }
     __syncthreads();
 
-    // ---- 2. elimination without pivoting (right-looking, RHS carried along)
+    // ---- 2. elimination without pivoting (right-looking, right-hand sides carried along)
     for (int k = 0; k < r - 1; ++k) {
       const int m = r - k - 1;
       for (int idx = tid; idx < S * m; idx += kThreads) {
@@ -132,111 +140,115 @@ sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__
       __syncthreads();
       const int nc = ld - k - 1;
       const int per = m * nc;
-      for (int idx = tid; idx < S * per; idx += kThreads) {
-        const int s = idx / per;
-        const int e = idx - s * per;
-        const int ii = e / nc;
-        const int jj = e - ii * nc;
-        const int i = k + 1 + ii, j = k + 1 + jj;
-        double2* a = Am + (size_t)s * am_elems;
-        const double2 v = c_msub(a[i * ld + j], a[i * ld + k], a[k * ld + j]);
-        a[i * ld + j] = v;
-        if (e == 0) Inv[(size_t)s * r + k + 1] = c_recip(v, status);
+      const int total = S * per;
+      // two independent elements per iteration: all loads are issued before either store
+      for (int idx = tid; idx < total; idx += 2 * kThreads) {
+        const int idx2 = idx + kThreads;
+        const bool two = idx2 < total;
+        const int s1 = idx / per;
+        const int e1 = idx - s1 * per;
+        const int i1 = k + 1 + e1 / nc, j1 = k + 1 + (e1 - (e1 / nc) * nc);
+        const int s2 = two ? idx2 / per : s1;
+        const int e2 = two ? idx2 - s2 * per : e1;
+        const int i2 = k + 1 + e2 / nc, j2 = k + 1 + (e2 - (e2 / nc) * nc);
+        double2* a1 = Am + (size_t)s1 * am_elems;
+        double2* a2 = Am + (size_t)s2 * am_elems;
+        const double2 x1 = a1[i1 * ld + j1], l1 = a1[i1 * ld + k], u1 = a1[k * ld + j1];
+        const double2 x2 = a2[i2 * ld + j2], l2 = a2[i2 * ld + k], u2 = a2[k * ld + j2];
+        const double2 v1 = c_msub(x1, l1, u1);
+        const double2 v2 = c_msub(x2, l2, u2);
+        a1[i1 * ld + j1] = v1;
+        if (two) a2[i2 * ld + j2] = v2;
+        if (e1 == 0) Inv[(size_t)s1 * r + k + 1] = c_recip(v1, status);
+        if (two && e2 == 0) Inv[(size_t)s2 * r + k + 1] = c_recip(v2, status);
       }
       __syncthreads();
     }
 
-    // ---- 3. back substitution, three right-hand sides
-    for (int k = r - 1; k >= 0; --k) {
-      for (int idx = tid; idx < S * 3; idx += kThreads) {
-        const int s = idx / 3;
-        const int j = idx - s * 3;
-        const double2* a = Am + (size_t)s * am_elems;
-        Pm[((size_t)s * r + k) * 3 + j] = c_mul(a[k * ld + r + j], Inv[(size_t)s * r + k]);
-      }
-      __syncthreads();
-      if (k > 0) {
-        const int per = k * 3;
-        for (int idx = tid; idx < S * per; idx += kThreads) {
-          const int s = idx / per;
-          const int e = idx - s * per;
-          const int i = e / 3;
-          const int j = e - i * 3;
-          double2* a = Am + (size_t)s * am_elems;
-          a[i * ld + r + j] = c_msub(a[i * ld + r + j], a[i * ld + k], Pm[((size_t)s * r + k) * 3 + j]);
-        }
-        __syncthreads();
+    // ---- 3. back substitution: one warp per (system, right-hand side), warp-synchronous
+    for (int sj = warp; sj < S * 3; sj += kWarps) {
+      const int s = sj / 3, j = sj - (sj / 3) * 3;
+      double2* a = Am + (size_t)s * am_elems;
+      const double2* inv = Inv + (size_t)s * r;
+      double2* p = Pm + (size_t)s * r * 3;
+      for (int k = r - 1; k >= 0; --k) {
+        const double2 x = c_mul(a[k * ld + r + j], inv[k]);  // every lane reads the same y_k
+        for (int i = lane; i < k; i += 32) a[i * ld + r + j] = c_msub(a[i * ld + r + j], a[i * ld + k], x);
+        if (lane == 0) p[k * 3 + j] = x;
+        __syncwarp();
       }
     }
+    __syncthreads();
 
-    // ---- 4a. y = M p for M in {K, C, G~(omega)}; Y overwrites the factors.
-    // M is Hermitian, so M[a][b] = conj(M[b][a]) is read along a (coalesced).
+    // ---- 4a. y = (L + D/2) p for M in {K, C, G~(omega)}; rows a and r-1-a share a task so
+    // every task touches r+1 entries.  M[a][b] = conj(M[b][a]) is read along a (coalesced).
     const int nm = want_cert ? 3 : 2;
+    const int half = (r + 1) / 2;
     double2* Y = Am;  // Y[s][mm][a][j] at ((s*3 + mm)*r + a)*3 + j
-    for (int idx = tid; idx < S * nm * r; idx += kThreads) {
-      const int s = idx / (nm * r);
-      const int e = idx - s * nm * r;
-      const int mm = e / r;
-      const int a = e - mm * r;
+    for (int idx = tid; idx < S * nm * half; idx += kThreads) {
+      const int s = idx / (nm * half);
+      const int e = idx - s * nm * half;
+      const int mm = e / half;
+      const int pr = e - mm * half;
       const double2* p = Pm + (size_t)s * r * 3;
-      double2 y0 = make_double2(0.0, 0.0), y1 = y0, y2 = y0;
-      if (mm < 2) {
-        const double2* M = (mm == 0) ? ob.K : ob.C;
-        for (int b = 0; b < r; ++b) {
-          double2 g = M[b * r + a];
-          g.y = -g.y;
+      const double w = Ws[s], w2 = w * w;
+      for (int side = 0; side < 2; ++side) {
+        const int a = side == 0 ? pr : r - 1 - pr;
+        if (side == 1 && a == pr) break;
+        double2 y0 = make_double2(0.0, 0.0), y1 = y0, y2 = y0;
+        for (int b = 0; b <= a; ++b) {
+          double2 g;
+          if (mm < 2) {
+            g = ((mm == 0) ? ob.K : ob.C)[b * r + a];
+            g.y = -g.y;
+          } else {
+            const double2 gk = ob.GKK[b * r + a];
+            const double2 gc = ob.GCC[b * r + a];
+            const double2 sk = ob.GSk[b * r + a];
+            g = make_double2(fma(w2, gc.x, fma(-w, sk.y, gk.x)), fma(-w2, gc.y, fma(-w, sk.x, -gk.y)));
+          }
+          if (b == a) {
+            g.x *= 0.5;
+            g.y *= 0.5;
+          }
           y0 = c_mac(y0, g, p[b * 3 + 0]);
           y1 = c_mac(y1, g, p[b * 3 + 1]);
           y2 = c_mac(y2, g, p[b * 3 + 2]);
         }
-      } else {
-        const double w = Ws[s], w2 = w * w;
-        for (int b = 0; b < r; ++b) {
-          const double2 g = ob.GKK[b * r + a];
-          const double2 c = ob.GCC[b * r + a];
-          const double2 sk = ob.GSk[b * r + a];
-          const double2 gt = make_double2(fma(w2, c.x, fma(-w, sk.y, g.x)),
-                                          fma(-w2, c.y, fma(-w, sk.x, -g.y)));
-          y0 = c_mac(y0, gt, p[b * 3 + 0]);
-          y1 = c_mac(y1, gt, p[b * 3 + 1]);
-          y2 = c_mac(y2, gt, p[b * 3 + 2]);
-        }
+        double2* yo = Y + (((size_t)s * 3 + mm) * r + a) * 3;
+        yo[0] = y0;
+        yo[1] = y1;
+        yo[2] = y2;
       }
-      double2* yo = Y + (((size_t)s * 3 + mm) * r + a) * 3;
-      yo[0] = y0;
-      yo[1] = y1;
-      yo[2] = y2;
     }
     __syncthreads();
 
-    // ---- 4b. reductions over the basis index a
-    //  q 0..5  : Re(p_i^H K p_j)      q 6..11 : Re(p_i^H C p_j)
-    //  q 12..17: Re(p_i^H G~ p_j)     q 18..26: Re(b_i^H p_j)
-    //  q 27..35: Re((i w gsK_i + w^2 gsC_i) p_j)
-    // without a certificate only the K and C forms (12) and Re(b_i^H p_j) (9) are needed
-    const int nq = want_cert ? kRed : 21;
+    // ---- 4b. reductions over the basis index a (all nine (i, j); symmetrised in step 5)
+    //  q  0.. 8: Re(p_i^H y^K_j)   q  9..17: Re(p_i^H y^C_j)   q 18..26: Re(p_i^H y^G_j)
+    //  q 27..35: Re(b_i^H p_j)     q 36..44: Re((i w gsK_i + w^2 gsC_i) p_j)
+    // without a certificate only q 0..17 and 27..35 are formed
+    const int nq = want_cert ? kRed : 27;
     for (int idx = tid; idx < S * nq; idx += kThreads) {
       const int s = idx / nq;
       int q = idx - s * nq;
-      if (!want_cert && q >= 12) q += 6;  // skip the G~ block
+      if (!want_cert && q >= 18) q += 9;
       const double2* p = Pm + (size_t)s * r * 3;
       double acc = 0.0;
-      if (q < 18) {
-        int i, j;
-        pair_ij(q % 6, i, j);
-        const double2* y = Y + ((size_t)s * 3 + q / 6) * r * 3;
+      if (q < 27) {
+        const int i = (q % 9) / 3, j = q % 3;
+        const double2* y = Y + ((size_t)s * 3 + q / 9) * r * 3;
         for (int a = 0; a < r; ++a) {
           const double2 pa = p[a * 3 + i], ya = y[a * 3 + j];
           acc = fma(pa.x, ya.x, fma(pa.y, ya.y, acc));
         }
-      } else if (q < 27) {
-        const int i = (q - 18) / 3, j = (q - 18) % 3;
+      } else if (q < 36) {
+        const int i = (q - 27) / 3, j = (q - 27) % 3;
         for (int a = 0; a < r; ++a) {
           const double2 b = ob.B[a * 3 + i], pa = p[a * 3 + j];
           acc = fma(b.x, pa.x, fma(b.y, pa.y, acc));
         }
       } else {
-        const int i = (q - 27) / 3, j = (q - 27) % 3;
+        const int i = (q - 36) / 3, j = (q - 36) % 3;
         const double w = Ws[s], w2 = w * w;
         for (int a = 0; a < r; ++a) {
           const double2 gk = ob.gsK[i * r + a], gc = ob.gsC[i * r + a], pa = p[a * 3 + j];
@@ -254,27 +266,26 @@ sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__
       const int s = idx / 9;
       const int ij = idx - s * 9;
       const int i = ij / 3, j = ij - (ij / 3) * 3;
-      const int lo = min(i, j), hi = max(i, j);
-      const int q = (lo == 0) ? hi : (lo == 1 ? 2 + hi : 5);
+      const int ji = j * 3 + i;
       const double* red = Red + (size_t)s * kRed;
       const double w = Ws[s];
       const size_t o = ((size_t)task.obj * n_w + task.w0 + s) * 9 + ij;
-      if (Rout) Rout[o] = fma(-0.25 * ob.alpha3, red[q], ob.N0[ij]);
-      if (Iout) Iout[o] = 0.25 * ob.alpha3 * w * (ob.c00[ij] + red[6 + q] + red[18 + ij] + red[18 + j * 3 + i]);
+      if (Rout) Rout[o] = fma(-0.25 * ob.alpha3, red[ij] + red[ji], ob.N0[ij]);
+      if (Iout)
+        Iout[o] = 0.25 * ob.alpha3 * w * (ob.c00[ij] + red[9 + ij] + red[9 + ji] + red[27 + ij] + red[27 + ji]);
       if (Dout) {
         if (want_cert) {
           const double w2 = w * w;
-          const double cij = fma(w2, ob.gss[ij], red[12 + q] + red[27 + ij] + red[27 + j * 3 + i]);
-          const int qi = (i == 0) ? 0 : (i == 1 ? 3 : 5), qj = (j == 0) ? 0 : (j == 1 ? 3 : 5);
-          const double ni = fma(w2, ob.gss[i * 4], red[12 + qi] + 2.0 * red[27 + i * 4]);
-          const double nj = fma(w2, ob.gss[j * 4], red[12 + qj] + 2.0 * red[27 + j * 4]);
+          const double cij = fma(w2, ob.gss[ij], red[18 + ij] + red[18 + ji] + red[36 + ij] + red[36 + ji]);
+          const double ni = fma(w2, ob.gss[i * 4], 2.0 * (red[18 + i * 4] + red[36 + i * 4]));
+          const double nj = fma(w2, ob.gss[j * 4], 2.0 * (red[18 + j * 4] + red[36 + j * 4]));
           Dout[o] = ob.cert_scale * (ni + nj - cij);
         } else {
           Dout[o] = __longlong_as_double(0x7ff8000000000000LL);
         }
       }
     }
-    // the next iteration's first barrier orders these reads before smem is reused
+    // the next iteration's first barrier orders these reads before the buffers are reused
   }
 }
 
@@ -284,8 +295,10 @@ int sweep_fp64_threads() { return kThreads; }
 
 const void* sweep_fp64_symbol() { return reinterpret_cast<const void*>(&sweep_fp64_kernel); }
 
-size_t sweep_fp64_bytes_per_system(int r) {
-  const size_t am = (size_t)(r * (r + 3) > 9 * r ? r * (r + 3) : 9 * r);
+size_t sweep_fp64_matrix_elems(int r) { return (size_t)(r * (r + 3) > 9 * r ? r * (r + 3) : 9 * r); }
+
+size_t sweep_fp64_bytes_per_system(int r, bool matrix_in_smem) {
+  const size_t am = matrix_in_smem ? sweep_fp64_matrix_elems(r) : 0;
   return 16 * (am + 3 * (size_t)r + (size_t)r) + 8 * (1 + kRed);
 }
 
@@ -297,10 +310,10 @@ cudaError_t sweep_fp64_configure(size_t smem_bytes) {
 cudaError_t launch_sweep_fp64(const RomDev* objs, const SweepTask* tasks, int n_tasks, int* counter,
                               const double* omega, int omega_stride, const double* s_sigma,
                               double* R, double* I, double* Delta, int* status, int n_w, int grid,
-                              size_t smem_bytes, cudaStream_t stream) {
+                              size_t smem_bytes, double2* workspace, size_t ws_elems, cudaStream_t stream) {
   sweep_fp64_kernel<<<grid, kThreads, smem_bytes, stream>>>(objs, tasks, n_tasks, counter, omega,
                                                             omega_stride, s_sigma, R, I, Delta,
-                                                            status, n_w);
+                                                            status, n_w, workspace, ws_elems);
   return cudaGetLastError();
 }
 
