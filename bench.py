@@ -218,6 +218,7 @@ def main():
     stream = torch.cuda.Stream(dev)
     h = m.Handle(local_rank, stream.cuda_stream)
     roms = [m.ReducedObject.from_workload(h, o) for o in objs]
+    sweep_cfg = m.mrom_tune(h, roms, args.n_w)
     plan = m.Plan(h, roms, args.n_w)
     om = torch.as_tensor(wo, dtype=torch.float64, device=dev)
     shape = (args.n_obj, args.n_w, 3, 3)
@@ -332,7 +333,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk, "wall_s_timed": wall, "per_launch_ms": per_launch_ms,
+            "clocks": clk, "wall_s_timed": wall, "per_launch_ms": per_launch_ms, "sweep_config": sweep_cfg,
         }
         print(json.dumps(line), flush=True)
     plan.close()

@@ -58,12 +58,12 @@ typedef struct mrom_plan_s* mrom_plan;
 
 /* ---------------------------------------------------------------- context */
 
-/* Create a handle on CUDA device `device`.  `cuda_stream` is a cudaStream_t
- * to run on (NULL: the handle creates its own non-blocking stream).  The
+/* Create a handle on CUDA device `device`.  `cuda_stream` is the cudaStream_t
+ * every call of this handle runs on (NULL: CUDA's default stream).  The
  * handle owns a small device status word and no other device memory. */
 mrom_status mrom_create(int device, void* cuda_stream, mrom_handle* out);
 mrom_status mrom_destroy(mrom_handle h);
-/* Replace the stream used by later calls (NULL: the handle's own stream). */
+/* Replace the stream used by later calls (NULL: CUDA's default stream). */
 mrom_status mrom_set_stream(mrom_handle h, void* cuda_stream);
 /* Wait for the handle's stream; returns the first CUDA error or the first
  * device-detected condition since the previous mrom_synchronize, then clears it. */
@@ -156,6 +156,13 @@ mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, int32_t n_ob
 mrom_status mrom_plan_sweep(mrom_plan plan, const double* omega, int32_t omega_stride,
                             double* R, double* I, double* Delta);
 mrom_status mrom_plan_destroy(mrom_plan plan);
+
+/* Autotuner: time every sweep launch configuration (threads per CTA x CTAs per
+ * SM) on a sample of this batch (up to 96 objects x 200 frequencies) and make
+ * the fastest the handle's configuration for later plans.  Blocks until done;
+ * allocates and frees a scratch buffer.  *chosen (may be NULL) receives the
+ * configuration index. */
+mrom_status mrom_tune(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int32_t n_w, int32_t* chosen);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,7 @@ __all__ = [
     "MromError", "lib", "Handle", "ReducedObject", "Plan",
     "mrom_create", "mrom_destroy", "mrom_synchronize", "mrom_last_error", "mrom_launch_count",
     "mrom_rom_from_reduced", "mrom_rom_free", "mrom_rom_rank", "mrom_sweep", "mrom_certificate",
-    "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy",
+    "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune",
 ]
 
 
@@ -223,3 +223,10 @@ def mrom_plan_sweep(plan: Plan, omega, R, I, Delta=None, omega_stride: int = 0) 
 
 def mrom_plan_destroy(plan: Plan) -> None:
     plan.close()
+
+
+def mrom_tune(h: Handle, objs, n_w: int) -> int:
+    """Pick the fastest sweep launch configuration for this batch; returns its index."""
+    chosen = ctypes.c_int32(-1)
+    _abi.check(lib().mrom_tune(h.ptr, _rom_array(objs), len(objs), int(n_w), ctypes.byref(chosen)), h.ptr)
+    return int(chosen.value)

@@ -15,7 +15,7 @@ STATUS = {0: "MROM_OK", 1: "MROM_EINVAL", 2: "MROM_ENOMEM", 3: "MROM_ECUDA", 4: 
 EXPORTS = [
     "mrom_create", "mrom_destroy", "mrom_set_stream", "mrom_synchronize", "mrom_last_error",
     "mrom_launch_count", "mrom_rom_from_reduced", "mrom_rom_rank", "mrom_rom_free", "mrom_sweep",
-    "mrom_certificate", "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy",
+    "mrom_certificate", "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune",
 ]
 
 
@@ -59,6 +59,7 @@ def _declare(L):
         "mrom_plan_create": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, i32, ctypes.POINTER(vp)]),
         "mrom_plan_sweep": (ctypes.c_int, [vp, dp, i32, dp, dp, dp]),
         "mrom_plan_destroy": (ctypes.c_int, [vp]),
+        "mrom_tune": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, i32, ctypes.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

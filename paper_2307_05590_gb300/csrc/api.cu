@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <numeric>
 
 namespace mrom {
@@ -34,15 +35,8 @@ extern "C" mrom_status mrom_create(int device, void* cuda_stream, mrom_handle* o
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   h->smem_optin = (size_t)optin;
-  if (cuda_stream) {
-    h->stream = static_cast<cudaStream_t>(cuda_stream);
-  } else {
-    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
-      delete h;
-      return MROM_ECUDA;
-    }
-    h->stream = h->own_stream;
-  }
+  // NULL is CUDA's default stream, as everywhere in the runtime API
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
   if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
       cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -67,12 +61,7 @@ extern "C" mrom_status mrom_destroy(mrom_handle h) {
 
 extern "C" mrom_status mrom_set_stream(mrom_handle h, void* cuda_stream) {
   if (!h) return MROM_EINVAL;
-  h->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : h->own_stream;
-  if (!h->stream) {
-    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
-      return fail(h, MROM_ECUDA, "mrom_set_stream: stream creation failed");
-    h->stream = h->own_stream;
-  }
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
   return MROM_OK;
 }
 
@@ -105,13 +94,23 @@ extern "C" mrom_status mrom_synchronize(mrom_handle h) {
 
 namespace {
 
-// Dynamic shared memory per CTA: half of an SM's shared memory, so that two CTAs
-// co-reside and fill each other's barrier waits (minus the per-CTA reservation).
-size_t sweep_budget(const mrom_ctx* h) {
+// Dynamic shared memory per CTA: an SM's shared memory divided by the CTAs that
+// co-reside, so that they fill each other's barrier waits (minus the reservation).
+size_t sweep_budget(const mrom_ctx* h, int cfg) {
   int per_sm = 0;
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
-  const size_t half = (size_t)per_sm / 2;
-  return std::min<size_t>(h->smem_optin, half) - 2048;
+  const size_t share = (size_t)per_sm / sweep_fp64_ctas_per_sm(cfg);
+  return std::min<size_t>(h->smem_optin, share) - 2048;
+}
+
+int default_config(const mrom_ctx* h) {
+  if (h->sweep_cfg >= 0) return h->sweep_cfg;
+  const char* env = std::getenv("MROM_SWEEP_CONFIG");
+  if (env) {
+    const int c = std::atoi(env);
+    if (c >= 0 && c < sweep_fp64_num_configs()) return c;
+  }
+  return 1;  // 128 threads x 4 CTAs per SM: fastest on the 8..96 dictionary mix
 }
 
 }  // namespace
@@ -124,7 +123,8 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
   for (int o = 0; o < n_obj; ++o)
     if (!roms[o] || roms[o]->ctx != h) return fail(h, MROM_EINVAL, "mrom_plan_create: invalid object");
   cudaSetDevice(h->device);
-  const size_t budget = sweep_budget(h);
+  const int cfg = default_config(h);
+  const size_t budget = sweep_budget(h, cfg);
   std::vector<RomDev> objs(n_obj);
   std::vector<SweepTask> tasks;
   std::vector<double> cost;
@@ -175,15 +175,16 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
 
   auto* plan = new mrom_plan_s();
   plan->ctx = h;
+  plan->cfg = cfg;
   plan->n_obj = n_obj;
   plan->n_w = n_w;
   plan->all_cert = all_cert;
   plan->smem_bytes = smem;
   plan->n_tasks = (int)sorted.size();
-  cudaError_t e = sweep_fp64_configure(smem);
+  cudaError_t e = sweep_fp64_configure(cfg, smem);
   int occ = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_fp64_symbol(), sweep_fp64_threads(), smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_fp64_symbol(cfg), sweep_fp64_threads(cfg), smem);
   occ = std::max(occ, 1);
   plan->grid = std::min(plan->n_tasks, h->num_sms * occ);
   plan->ws_elems = ws_elems;
@@ -236,10 +237,10 @@ mrom_status run_plan(mrom_plan plan, const double* omega, int32_t omega_stride, 
     return fail(h, MROM_EINVAL, "sweep: Delta requested but an object has no Gram matrix");
   if (!R && !I && !Delta) return MROM_OK;
   cudaSetDevice(h->device);
-  cudaError_t e = sweep_fp64_configure(plan->smem_bytes);
+  cudaError_t e = sweep_fp64_configure(plan->cfg, plan->smem_bytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(plan->d_counter, 0, sizeof(int), h->stream);
   if (e == cudaSuccess)
-    e = launch_sweep_fp64(plan->d_objs, plan->d_tasks, plan->n_tasks, plan->d_counter, omega, omega_stride,
+    e = launch_sweep_fp64(plan->cfg, plan->d_objs, plan->d_tasks, plan->n_tasks, plan->d_counter, omega, omega_stride,
                           s_sigma, R, I, Delta, h->d_status, plan->n_w, plan->grid, plan->smem_bytes,
                           plan->d_workspace, plan->ws_elems, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "sweep launch");
@@ -273,4 +274,59 @@ extern "C" mrom_status mrom_certificate(mrom_handle h, const mrom_rom_t* roms, i
   if (!h) return MROM_EINVAL;
   if (!Delta) return fail(h, MROM_EINVAL, "mrom_certificate: Delta is null");
   return mrom_sweep(h, roms, n_obj, omega, n_w, omega_stride, nullptr, nullptr, nullptr, nullptr, Delta);
+}
+
+extern "C" mrom_status mrom_tune(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int32_t n_w,
+                                 int32_t* chosen) {
+  if (!h) return MROM_EINVAL;
+  if (!roms || n_obj < 1 || n_w < 1) return fail(h, MROM_EINVAL, "mrom_tune: bad arguments");
+  cudaSetDevice(h->device);
+  // a sample spread over the batch: up to 96 objects and 200 frequencies
+  const int ns = std::min<int>(n_obj, 96), nw = std::min<int>(n_w, 200);
+  std::vector<mrom_rom_t> sample(ns);
+  for (int k = 0; k < ns; ++k) sample[k] = roms[(int64_t)k * n_obj / ns];
+  std::vector<double> om(nw);
+  for (int k = 0; k < nw; ++k) om[k] = std::pow(10.0, 1.0 + 7.0 * k / std::max(1, nw - 1));
+  const size_t out = (size_t)ns * nw * 9;
+  double* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, (3 * out + nw) * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_tune: scratch allocation");
+  double* d_om = buf + 3 * out;
+  e = cudaMemcpyAsync(d_om, om.data(), nw * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  bool cert = true;
+  for (auto* r : sample) cert = cert && r->has_cert;
+  const int saved = h->sweep_cfg;
+  int best = -1;
+  float best_ms = 0.f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int cfg = 0; cfg < sweep_fp64_num_configs() && e == cudaSuccess; ++cfg) {
+    h->sweep_cfg = cfg;
+    mrom_plan plan = nullptr;
+    if (mrom_plan_create(h, sample.data(), ns, nw, &plan) != MROM_OK) continue;
+    mrom_plan_sweep(plan, d_om, 0, buf, buf + out, cert ? buf + 2 * out : nullptr);  // warm-up
+    cudaEventRecord(e0, h->stream);
+    mrom_plan_sweep(plan, d_om, 0, buf, buf + out, cert ? buf + 2 * out : nullptr);
+    cudaEventRecord(e1, h->stream);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best < 0 || ms < best_ms) {
+      best = cfg;
+      best_ms = ms;
+    }
+    mrom_plan_destroy(plan);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(h->stream);
+  cudaFree(buf);
+  if (e != cudaSuccess) {
+    h->sweep_cfg = saved;
+    return cuda_fail(h, e, "mrom_tune");
+  }
+  h->sweep_cfg = best < 0 ? saved : best;
+  if (chosen) *chosen = h->sweep_cfg;
+  return MROM_OK;
 }

@@ -57,6 +57,7 @@ struct mrom_ctx {
   int num_sms = 0;
   size_t smem_optin = 0;
   int64_t launches = 0;
+  int sweep_cfg = -1;             // launch configuration for sweeps (-1: default)
   mrom_status pending = MROM_OK;  // host-detected asynchronous error
   std::string last_error;
 };
@@ -79,6 +80,7 @@ struct mrom_rom {
 
 struct mrom_plan_s {
   mrom_ctx* ctx = nullptr;
+  int cfg = 0;                      // sweep launch configuration
   int n_obj = 0, n_w = 0;
   bool all_cert = false;
   size_t smem_bytes = 0;
@@ -99,12 +101,15 @@ mrom_status cuda_fail(mrom_ctx* h, cudaError_t e, const char* what);
 
 // Sweep kernel launcher (sweep_fp64.cu).  A task's matrices live in shared memory
 // (SweepTask.pad bit 0 clear) or in the CTA's slice of a global workspace (bit 0 set).
+// Launch configurations differ in threads per CTA and CTAs per SM.
+int sweep_fp64_num_configs();
+int sweep_fp64_threads(int cfg);
+int sweep_fp64_ctas_per_sm(int cfg);
+const void* sweep_fp64_symbol(int cfg);
 size_t sweep_fp64_matrix_elems(int r);
 size_t sweep_fp64_bytes_per_system(int r, bool matrix_in_smem);
-int sweep_fp64_threads();
-cudaError_t sweep_fp64_configure(size_t smem_bytes);
-const void* sweep_fp64_symbol();
-cudaError_t launch_sweep_fp64(const RomDev* objs, const SweepTask* tasks, int n_tasks, int* counter,
+cudaError_t sweep_fp64_configure(int cfg, size_t smem_bytes);
+cudaError_t launch_sweep_fp64(int cfg, const RomDev* objs, const SweepTask* tasks, int n_tasks, int* counter,
                               const double* omega, int omega_stride, const double* s_sigma,
                               double* R, double* I, double* Delta, int* status, int n_w, int grid,
                               size_t smem_bytes, double2* workspace, size_t ws_elems, cudaStream_t stream);

@@ -132,3 +132,26 @@ def test_launch_count_increases(mrom, handle):
     mrom.mrom_sweep(handle, [rom], om, 2, R, torch.empty_like(R))
     handle.synchronize()
     assert handle.launch_count() == before + 1
+
+
+def test_autotuner_picks_a_valid_configuration(mrom, handle):
+    """mrom_tune times every launch configuration; results after tuning are unchanged."""
+    import torch
+    from workloads import log_omegas, reduced_object
+    from gpu_common import oracle_sweep, rel_errors
+    objs = [reduced_object(77, k, r) for k, r in enumerate([12, 50, 90])]
+    roms = [mrom.ReducedObject.from_workload(handle, o) for o in objs]
+    cfg = mrom.mrom_tune(handle, roms, 60)
+    assert cfg in (0, 1)
+    wo = log_omegas(1e1, 1e8, 60)
+    om = torch.as_tensor(wo, device="cuda")
+    R = torch.empty((3, 60, 3, 3), dtype=torch.float64, device="cuda")
+    I = torch.empty_like(R)
+    D = torch.empty_like(R)
+    plan = mrom.Plan(handle, roms, 60)
+    plan.sweep(om, R, I, D)
+    handle.synchronize()
+    for k, obj in enumerate(objs):
+        ref = oracle_sweep(obj, wo)
+        errs = rel_errors(R[k].cpu().numpy(), I[k].cpu().numpy(), D[k].cpu().numpy(), *ref)
+        assert max(errs) <= TOL, errs
