@@ -164,6 +164,33 @@ mrom_status mrom_plan_destroy(mrom_plan plan);
  * configuration index. */
 mrom_status mrom_tune(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int32_t n_w, int32_t* chosen);
 
+/* ------------------------------------------------------- allocation-free */
+
+/* mrom_sweep without any device allocation.  Some callers cannot allocate
+ * device memory while they run: a service that reserves its whole GPU memory
+ * budget at start-up and forbids later allocations, an application whose own
+ * allocator already owns the device memory, or a latency-critical loop in which
+ * cudaMalloc / cudaFree would synchronise the device.  For them this entry point
+ * computes exactly what mrom_sweep computes (same kernel arithmetic, same
+ * outputs) and allocates nothing: the object table, the task table, the work
+ * counter and the workspace of systems too large for shared memory all live in
+ * one fixed array of MROM_NOALLOC_SCRATCH_BYTES (64 MiB) of device memory inside
+ * this library, which every GPU that loads the library holds until the process
+ * exits.  The paper has no counterpart to this entry point.
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress); make this first call before any stream capture.
+ *  - Every call reuses the same array (it keeps the previous call's contents):
+ *    calls whose work overlaps on the GPU -- on different streams or handles of
+ *    the same device -- race and corrupt each other's results; serialise them.
+ *  - Arguments and output layout are those of mrom_sweep (without s_sigma and
+ *    s_mu).  A batch whose tables and workspace do not fit the array is refused
+ *    with MROM_EINVAL and a message giving the bytes needed; nothing is launched.
+ *    The workspace shrinks the grid when needed, so only the tables (about 330
+ *    bytes per object) bound the batch size. */
+#define MROM_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+mrom_status mrom_sweep_noalloc(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega,
+                               int32_t n_w, int32_t omega_stride, double* R, double* I, double* Delta);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ __all__ = [
     "MromError", "lib", "Handle", "ReducedObject", "Plan",
     "mrom_create", "mrom_destroy", "mrom_synchronize", "mrom_last_error", "mrom_launch_count",
     "mrom_rom_from_reduced", "mrom_rom_free", "mrom_rom_rank", "mrom_sweep", "mrom_certificate",
-    "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune",
+    "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune", "mrom_sweep_noalloc",
 ]
 
 
@@ -230,3 +230,14 @@ def mrom_tune(h: Handle, objs, n_w: int) -> int:
     chosen = ctypes.c_int32(-1)
     _abi.check(lib().mrom_tune(h.ptr, _rom_array(objs), len(objs), int(n_w), ctypes.byref(chosen)), h.ptr)
     return int(chosen.value)
+
+
+def mrom_sweep_noalloc(h: Handle, objs, omega, n_w: int, R, I, Delta=None, *, omega_stride: int = 0) -> None:
+    """mrom_sweep for callers that cannot allocate device memory while they run.
+
+    Same arguments and results as mrom_sweep (device tensors); all scratch lives in
+    a fixed 64 MiB array inside the library.  Calls share that array, so calls
+    whose GPU work overlaps must be serialised.
+    """
+    _abi.check(lib().mrom_sweep_noalloc(h.ptr, _rom_array(objs), len(objs), _ptr(omega), int(n_w),
+                                        int(omega_stride), _ptr(R), _ptr(I), _ptr(Delta)), h.ptr)

@@ -16,6 +16,7 @@ EXPORTS = [
     "mrom_create", "mrom_destroy", "mrom_set_stream", "mrom_synchronize", "mrom_last_error",
     "mrom_launch_count", "mrom_rom_from_reduced", "mrom_rom_rank", "mrom_rom_free", "mrom_sweep",
     "mrom_certificate", "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune",
+    "mrom_sweep_noalloc",
 ]
 
 
@@ -60,6 +61,7 @@ def _declare(L):
         "mrom_plan_sweep": (ctypes.c_int, [vp, dp, i32, dp, dp, dp]),
         "mrom_plan_destroy": (ctypes.c_int, [vp]),
         "mrom_tune": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, i32, ctypes.POINTER(i32)]),
+        "mrom_sweep_noalloc": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, dp, i32, i32, dp, dp, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -115,6 +115,35 @@ int default_config(const mrom_ctx* h) {
 
 }  // namespace
 
+namespace mrom {
+
+size_t sweep_budget_bytes(const mrom_ctx* h, int cfg) { return sweep_budget(h, cfg); }
+
+int sweep_config(const mrom_ctx* h) { return default_config(h); }
+
+RomDev rom_record(const mrom_rom* m) {
+  RomDev d;
+  d.K = m->K;
+  d.C = m->C;
+  d.Me = m->Me;
+  d.B = m->B;
+  d.GKK = m->GKK;
+  d.GCC = m->GCC;
+  d.GSk = m->GSk;
+  d.gsK = m->gsK;
+  d.gsC = m->gsC;
+  std::memcpy(d.gss, m->gss, sizeof(d.gss));
+  std::memcpy(d.c00, m->c00, sizeof(d.c00));
+  std::memcpy(d.N0, m->N0, sizeof(d.N0));
+  d.alpha3 = m->alpha * m->alpha * m->alpha;
+  d.cert_scale = m->has_cert ? d.alpha3 / (4.0 * m->alpha_lb) : 0.0;
+  d.r = m->r;
+  d.has_cert = m->has_cert ? 1 : 0;
+  return d;
+}
+
+}  // namespace mrom
+
 extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int32_t n_w,
                                         mrom_plan* out) {
   if (!h) return MROM_EINVAL;

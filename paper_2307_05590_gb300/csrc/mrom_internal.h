@@ -114,6 +114,18 @@ cudaError_t launch_sweep_fp64(int cfg, const RomDev* objs, const SweepTask* task
                               double* R, double* I, double* Delta, int* status, int n_w, int grid,
                               size_t smem_bytes, double2* workspace, size_t ws_elems, cudaStream_t stream);
 
+// Same sweep with the task list replaced by a compact per-object table (see
+// implicit_task in sweep_fp64.cu); used by the allocation-free entry point.
+cudaError_t launch_sweep_fp64_implicit(int cfg, const RomDev* objs, const SweepTask* table, int n_tasks,
+                                       int* counter, const double* omega, int omega_stride, double* R,
+                                       double* I, double* Delta, int* status, int n_w, int grid,
+                                       size_t smem_bytes, double2* workspace, size_t ws_elems,
+                                       cudaStream_t stream);
+// Builds the RomDev record of an object (api.cu).
+RomDev rom_record(const mrom_rom* m);
+size_t sweep_budget_bytes(const mrom_ctx* h, int cfg);
+int sweep_config(const mrom_ctx* h);
+
 // Certificate pre-processing of a Gram matrix (rom.cu).
 cudaError_t launch_split_gram(const double2* G, int r, double2* GKK, double2* GCC, double2* GSk,
                               double2* gsK, double2* gsC, cudaStream_t stream);

@@ -59,7 +59,22 @@ __host__ __device__ __forceinline__ int matrix_elems(int r) {
   return aug > forms ? aug : forms;
 }
 
-template <int THREADS, int MINB>
+// Compact task table: entry 0 is a header whose .obj holds the object count n; entries
+// 1..n (objects in cost order) hold {object, frequencies per task S, first task index,
+// matrices-in-global flag}.  Task t is chunk t - first of the entry whose range holds t.
+__device__ __forceinline__ SweepTask implicit_task(const SweepTask* __restrict__ table, int n_w, int t) {
+  const int n = table[0].obj;
+  int lo = 1, hi = n + 1;  // table[lo].w0 <= t, and t < table[hi].w0 when hi <= n
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (table[mid].w0 <= t) lo = mid; else hi = mid;
+  }
+  const SweepTask e = table[lo];
+  const int w0 = (t - e.w0) * e.nw;
+  return SweepTask{e.obj, w0, min(e.nw, n_w - w0), e.pad & 1};
+}
+
+template <int THREADS, int MINB, bool IMPLICIT = false>
 __global__ void __launch_bounds__(THREADS, MINB)
 sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__ tasks, int n_tasks,
                   int* __restrict__ counter, const double* __restrict__ omega, int omega_stride,
@@ -79,7 +94,12 @@ sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__
     __syncthreads();
     if (t >= n_tasks) break;
 
-    const SweepTask task = tasks[t];
+    SweepTask task;
+    if constexpr (IMPLICIT) {
+      task = implicit_task(tasks, n_w, t);
+    } else {
+      task = tasks[t];
+    }
     const RomDev& ob = objs[task.obj];
     const int r = ob.r, S = task.nw, ld = r + 3;
     const bool want_cert = (Dout != nullptr) && ob.has_cert;
@@ -335,6 +355,28 @@ const Config kConfigs[] = {
 };
 
 }  // namespace
+
+cudaError_t launch_sweep_fp64_implicit(int cfg, const RomDev* objs, const SweepTask* table, int n_tasks,
+                                       int* counter, const double* omega, int omega_stride, double* R,
+                                       double* I, double* Delta, int* status, int n_w, int grid,
+                                       size_t smem_bytes, double2* workspace, size_t ws_elems,
+                                       cudaStream_t stream) {
+  cudaError_t e;
+  if (cfg == 0) {
+    e = cudaFuncSetAttribute(sweep_fp64_kernel<256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    sweep_fp64_kernel<256, 2, true><<<grid, 256, smem_bytes, stream>>>(
+        objs, table, n_tasks, counter, omega, omega_stride, nullptr, R, I, Delta, status, n_w, workspace, ws_elems);
+  } else {
+    e = cudaFuncSetAttribute(sweep_fp64_kernel<128, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    sweep_fp64_kernel<128, 4, true><<<grid, 128, smem_bytes, stream>>>(
+        objs, table, n_tasks, counter, omega, omega_stride, nullptr, R, I, Delta, status, n_w, workspace, ws_elems);
+  }
+  return cudaGetLastError();
+}
 
 int sweep_fp64_num_configs() { return (int)(sizeof(kConfigs) / sizeof(kConfigs[0])); }
 int sweep_fp64_threads(int cfg) { return kConfigs[cfg].threads; }
