@@ -117,6 +117,63 @@ mrom_status mrom_rom_from_reduced(mrom_handle h, const mrom_reduced_desc* desc, 
 int32_t mrom_rom_rank(mrom_rom_t rom);
 void mrom_rom_free(mrom_rom_t rom);
 
+/* ------------------------------------------------ off-line stage (project) */
+
+/* The full-order problem of Sect. 3.1 as the projection needs it (all DEVICE
+ * pointers, caller-owned, float64):
+ *   K (Eq. (10a)): n x n CSR, int32 row pointers (n+1) and column indices, values;
+ *   C (Eq. (10b)) and M (Eq. (10c)): lumped (diagonal) matrices, n values each
+ *     (M may be NULL); eps scales M in A = K - i omega C + eps M;
+ *   o: 3 x n, row i = coefficients of the total theta_i^(0) = theta~_i^(0) + e_i x xi
+ *     (so the source is r_i = i omega C o_i, Eq. (9));
+ *   X_diag: n positive values of a diagonal inner-product matrix X for the
+ *     certificate's Riesz norm ||r||^2 = r^H X^-1 r (Lemma 4.2), or NULL for no
+ *     certificate.  With X = eps M + omega_min C, |a(v, v)| >= ||v||_X^2 / sqrt(2)
+ *     for omega >= omega_min, so alpha_lb = 1/sqrt(2) is valid (a looser bound
+ *     than with X = K + eps M + omega_min C);
+ *   alpha, alpha_lb, vol_B, N0 (9 or NULL) as in mrom_reduced_desc. */
+typedef struct {
+  int64_t n;
+  const int32_t* K_rowptr;
+  const int32_t* K_col;
+  const double* K_val;
+  const double* C_diag;
+  const double* M_diag;
+  double eps;
+  const double* o;
+  const double* X_diag;
+  double alpha;
+  double alpha_lb;
+  double vol_B;
+  const double* N0;
+} mrom_fom;
+
+#define MROM_MAX_SNAPSHOTS 192
+
+/* Off-line stage of Algorithm 1 with one basis for the three directions:
+ * truncated SVD of the snapshot matrix [D_1 D_2 D_3] (Sect. 4.1, Eqs. (13)-(15))
+ * and Galerkin projection (Sects. 4.2-4.3), producing a reduced object for
+ * mrom_sweep.  D holds n_cols complex128 snapshot columns of length n, column c
+ * at D + c * ldd (device, ldd >= n, n_cols <= MROM_MAX_SNAPSHOTS).  The SVD is
+ * computed from the Hermitian Gram D^H D with a Jacobi eigensolver, so singular
+ * values below about 1e-8 s_1 are not resolved; the retained rank is
+ * r = #{s_k / s_1 >= tol_sigma}, capped at r_max (if > 0) and MROM_MAX_R.
+ * basis_in (device, n x r_in complex128 row-major, or NULL) skips the SVD and
+ * projects onto the given basis.  sigma_out (host, n_cols values, or NULL)
+ * receives the singular values; r_out (host, or NULL) the rank.  Synchronous:
+ * allocates and frees its temporaries (about (3 r + 3) n complex values, plus
+ * (2 r + 3) n when X_diag is given).  MROM_ENOTCONVERGED if the eigensolver
+ * did not converge. */
+mrom_status mrom_project(mrom_handle h, const mrom_fom* fom, const void* D, int64_t ldd, int32_t n_cols,
+                         double tol_sigma, int32_t r_max, const void* basis_in, int32_t r_in, mrom_rom_t* out,
+                         double* sigma_out, int32_t* r_out);
+
+/* Copy an object's reduced data to caller buffers (host or device; any may be
+ * NULL): K, C, Me (r x r complex128; zeros when the object has no Me), B
+ * (r x 3), c00 (9 float64, host), G ((2r+3)^2; MROM_EINVAL if the object has
+ * no Gram matrix).  Synchronous. */
+mrom_status mrom_rom_get(mrom_rom_t rom, void* K, void* C, void* Me, void* B, double* c00, void* G);
+
 /* ------------------------------------------------------------------ sweep */
 
 /* On-line stage of Algorithm 1 for a batch of objects (Sect. 4.3):

@@ -22,6 +22,7 @@ __all__ = [
     "mrom_create", "mrom_destroy", "mrom_synchronize", "mrom_last_error", "mrom_launch_count",
     "mrom_rom_from_reduced", "mrom_rom_free", "mrom_rom_rank", "mrom_sweep", "mrom_certificate",
     "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune", "mrom_sweep_noalloc",
+    "FullOrder", "mrom_project", "mrom_rom_get",
 ]
 
 
@@ -91,6 +92,15 @@ class ReducedObject:
                    handle.ptr)
         self.r = int(r)
         self.has_cert = G is not None
+
+    @classmethod
+    def _wrap(cls, handle: Handle, ptr, r: int, has_cert: bool):
+        self = cls.__new__(cls)
+        self._rom = ptr
+        self.handle = handle
+        self.r = int(r)
+        self.has_cert = has_cert
+        return self
 
     @classmethod
     def from_workload(cls, handle: Handle, obj, *, with_cert: bool = True):
@@ -241,3 +251,72 @@ def mrom_sweep_noalloc(h: Handle, objs, omega, n_w: int, R, I, Delta=None, *, om
     """
     _abi.check(lib().mrom_sweep_noalloc(h.ptr, _rom_array(objs), len(objs), _ptr(omega), int(n_w),
                                         int(omega_stride), _ptr(R), _ptr(I), _ptr(Delta)), h.ptr)
+
+
+class FullOrder:
+    """Device copy of a full-order problem for mrom_project (torch tensors, caller-owned).
+
+    K: CSR (int32 rowptr, int32 col, float64 val); C, M, X: lumped diagonals (float64);
+    o: (3, n) float64 total theta^(0) coefficients.
+    """
+
+    def __init__(self, K_rowptr, K_col, K_val, C, o, *, M=None, eps=0.0, X=None, alpha=1.0,
+                 alpha_lb=1.0 / np.sqrt(2.0), vol_B=1.0, N0=None):
+        self.keep = [K_rowptr, K_col, K_val, C, o, M, X, N0]
+        f = _abi.mrom_fom()
+        f.n = int(C.numel())
+        f.K_rowptr, f.K_col, f.K_val = _ptr(K_rowptr), _ptr(K_col), _ptr(K_val)
+        f.C_diag, f.M_diag, f.eps = _ptr(C), _ptr(M), float(eps)
+        f.o, f.X_diag = _ptr(o), _ptr(X)
+        f.alpha, f.alpha_lb, f.vol_B = float(alpha), float(alpha_lb), float(vol_B)
+        f.N0 = _ptr(N0)
+        self.desc = f
+
+    @classmethod
+    def from_fit(cls, problem, device="cuda", *, X=None, alpha_lb=1.0 / np.sqrt(2.0)):
+        """Upload a workloads.FitProblem (K, C, M, o, eps, alpha, |B|, N0) to the device."""
+        import torch
+        K = problem.K.tocsr()
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)
+        return cls(t(K.indptr, torch.int32), t(K.indices, torch.int32), t(K.data, torch.float64),
+                   t(problem.C, torch.float64), t(problem.o, torch.float64), M=t(problem.M, torch.float64),
+                   eps=problem.eps, X=None if X is None else t(X, torch.float64), alpha=problem.alpha,
+                   alpha_lb=alpha_lb, vol_B=problem.vol_B, N0=t(problem.N0.ravel(), torch.float64))
+
+
+def mrom_project(h: Handle, fom: FullOrder, D=None, *, tol_sigma: float = 1e-6, r_max: int = 0, basis=None):
+    """Off-line stage: TSVD of the snapshot columns D (device (n_cols, n) complex128) and
+    projection, or projection onto a given basis (device (n, r) complex128).
+
+    Returns (ReducedObject, singular values (numpy, or None with a basis), rank r).
+    """
+    rom = ctypes.c_void_p()
+    r_out = ctypes.c_int32(0)
+    if basis is not None:
+        _abi.check(lib().mrom_project(h.ptr, ctypes.byref(fom.desc), None, 0, 0, 0.0, 0, _ptr(basis),
+                                      int(basis.shape[1]), ctypes.byref(rom), None, ctypes.byref(r_out)), h.ptr)
+        sig = None
+    else:
+        n_cols = int(D.shape[0])
+        sig = np.zeros(n_cols)
+        _abi.check(lib().mrom_project(h.ptr, ctypes.byref(fom.desc), _ptr(D), int(D.shape[1]), n_cols,
+                                      float(tol_sigma), int(r_max), None, 0, ctypes.byref(rom),
+                                      sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      ctypes.byref(r_out)), h.ptr)
+    return ReducedObject._wrap(h, rom, r_out.value, fom.desc.X_diag is not None), sig, int(r_out.value)
+
+
+def mrom_rom_get(rom: ReducedObject, with_gram: bool = True) -> dict:
+    """Host copies of an object's reduced data: K, C, Me, B, c00, G (numpy)."""
+    r = rom.r
+    out = {k: np.zeros((r, r), dtype=np.complex128) for k in ("K", "C", "Me")}
+    out["B"] = np.zeros((r, 3), dtype=np.complex128)
+    out["c00"] = np.zeros(9)
+    G = np.zeros((2 * r + 3, 2 * r + 3), dtype=np.complex128) if with_gram else None
+    _abi.check(lib().mrom_rom_get(rom.ptr, out["K"].ctypes.data, out["C"].ctypes.data, out["Me"].ctypes.data,
+                                  out["B"].ctypes.data,
+                                  out["c00"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  G.ctypes.data if G is not None else None), rom.handle.ptr)
+    out["c00"] = out["c00"].reshape(3, 3)
+    out["G"] = G
+    return out

@@ -16,7 +16,7 @@ EXPORTS = [
     "mrom_create", "mrom_destroy", "mrom_set_stream", "mrom_synchronize", "mrom_last_error",
     "mrom_launch_count", "mrom_rom_from_reduced", "mrom_rom_rank", "mrom_rom_free", "mrom_sweep",
     "mrom_certificate", "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune",
-    "mrom_sweep_noalloc",
+    "mrom_sweep_noalloc", "mrom_project", "mrom_rom_get",
 ]
 
 
@@ -24,6 +24,24 @@ class MromError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class mrom_fom(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("K_rowptr", ctypes.c_void_p),
+        ("K_col", ctypes.c_void_p),
+        ("K_val", ctypes.c_void_p),
+        ("C_diag", ctypes.c_void_p),
+        ("M_diag", ctypes.c_void_p),
+        ("eps", ctypes.c_double),
+        ("o", ctypes.c_void_p),
+        ("X_diag", ctypes.c_void_p),
+        ("alpha", ctypes.c_double),
+        ("alpha_lb", ctypes.c_double),
+        ("vol_B", ctypes.c_double),
+        ("N0", ctypes.c_void_p),
+    ]
 
 
 class mrom_reduced_desc(ctypes.Structure):
@@ -62,6 +80,10 @@ def _declare(L):
         "mrom_plan_destroy": (ctypes.c_int, [vp]),
         "mrom_tune": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, i32, ctypes.POINTER(i32)]),
         "mrom_sweep_noalloc": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, dp, i32, i32, dp, dp, dp]),
+        "mrom_project": (ctypes.c_int, [vp, ctypes.POINTER(mrom_fom), vp, i64, i32, ctypes.c_double, i32, vp, i32,
+                                        ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(i32)]),
+        "mrom_rom_get": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

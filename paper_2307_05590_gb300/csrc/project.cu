@@ -1,0 +1,618 @@
+// Off-line stage on the GPU: snapshot TSVD and Galerkin projection (Sects. 4.1-4.3).
+//
+//   G_D = D^H D                                  tall Gram (split over rows)
+//   G_D = V Lambda V^H                           Hermitian Jacobi eigensolver (one CTA)
+//   s_k = sqrt(lambda_k), r = #{s_k / s_1 >= TOL_Sigma} (capped)     (Eq. (15))
+//   U   = D V_r diag(1/s_r)                      left singular vectors (Eq. (14))
+//   Y   = K U                                    CSR SpMM
+//   K_r = U^H Y, C_r = U^H diag(c) U, Me = U^H diag(eps m) U,
+//   b_i = U^H (c o_i), c00 = o^T diag(c) o                             (Eqs. (17)-(19))
+//   G   = Phi^H diag(1/x) Phi, Phi = [c o_i | Y + eps m U | c U]      (Lemma 4.2)
+// Everything is float64 / complex128.  These kernels are FP64-pipe bound on GB300
+// (the snapshot and basis streams are re-read from L2), so they are written for
+// full FP64 utilisation with register tiles rather than for HBM streaming.
+#include "mrom_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+namespace mrom {
+namespace {
+
+__device__ __forceinline__ double2 c_conj_mac(double2 c, double2 a, double2 b) {  // c + conj(a) b
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 c_mac(double2 c, double2 a, double2 b) {  // c + a b
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+
+// ------------------------------------------------------------------ tall Gram
+// part[split][a][b] = sum_{n in split} conj(A[n][a]) * wgt(n) * B[n][b]
+// Element (n, c) of A is A[n * rsA + c * csA] (any layout).  One CTA computes a
+// kGT x kGT output tile over its row range; 256 threads hold 2 x 2 outputs each.
+constexpr int kGT = 32;
+constexpr int kGR = 32;
+
+__global__ void __launch_bounds__(256)
+gram_partial_kernel(const double2* __restrict__ A, int64_t rsA, int64_t csA, int ma,
+                    const double2* __restrict__ B, int64_t rsB, int64_t csB, int mb,
+                    const double* __restrict__ w, int wmode, int64_t n, int64_t rows_per_split,
+                    const int2* __restrict__ tiles, double2* __restrict__ part) {
+  __shared__ double2 As[kGR][kGT + 1];
+  __shared__ double2 Bs[kGR][kGT + 1];
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+  const int2 tile = tiles[blockIdx.y];
+  const int a_base = tile.x * kGT, b_base = tile.y * kGT;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_split;
+  const int64_t r1 = min(n, r0 + rows_per_split);
+  double2 acc[2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
+  for (int64_t row0 = r0; row0 < r1; row0 += kGR) {
+    for (int idx = tid; idx < kGR * kGT; idx += 256) {
+      int rr, cc;
+      if (csA == 1) { rr = idx / kGT; cc = idx % kGT; } else { cc = idx / kGR; rr = idx % kGR; }
+      const int64_t nr = row0 + rr;
+      const int col = a_base + cc;
+      As[rr][cc] = (nr < r1 && col < ma) ? A[nr * rsA + col * csA] : make_double2(0.0, 0.0);
+      if (csB == 1) { rr = idx / kGT; cc = idx % kGT; } else { cc = idx / kGR; rr = idx % kGR; }
+      const int64_t nb = row0 + rr;
+      const int colb = b_base + cc;
+      double2 v = make_double2(0.0, 0.0);
+      if (nb < r1 && colb < mb) {
+        v = B[nb * rsB + colb * csB];
+        if (wmode) {
+          const double s = (wmode == 1) ? w[nb] : 1.0 / w[nb];
+          v.x *= s;
+          v.y *= s;
+        }
+      }
+      Bs[rr][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < kGR; ++rr) {
+      const double2 a0 = As[rr][ty * 2], a1 = As[rr][ty * 2 + 1];
+      const double2 b0 = Bs[rr][tx * 2], b1 = Bs[rr][tx * 2 + 1];
+      acc[0][0] = c_conj_mac(acc[0][0], a0, b0);
+      acc[0][1] = c_conj_mac(acc[0][1], a0, b1);
+      acc[1][0] = c_conj_mac(acc[1][0], a1, b0);
+      acc[1][1] = c_conj_mac(acc[1][1], a1, b1);
+    }
+    __syncthreads();
+  }
+  double2* out = part + (size_t)blockIdx.x * ma * mb;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int a = a_base + ty * 2 + i, b = b_base + tx * 2 + j;
+      if (a < ma && b < mb) out[(size_t)a * mb + b] = acc[i][j];
+    }
+}
+
+// G[a][b] = sum over splits (fixed order).  Hermitian: only tiles with b-tile >= a-tile
+// were computed; the rest is mirrored and the diagonal made real.
+__global__ void gram_reduce_kernel(const double2* __restrict__ part, int nsplit, int ma, int mb, int hermitian,
+                                   double2* __restrict__ G, int64_t ldg) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)ma * mb;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / mb), b = (int)(idx % mb);
+    int sa = a, sb = b;
+    bool conj = false;
+    if (hermitian && (b / kGT) < (a / kGT)) {
+      sa = b;
+      sb = a;
+      conj = true;
+    }
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < nsplit; ++k) {
+      const double2 v = part[(size_t)k * ma * mb + (size_t)sa * mb + sb];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    if (conj) s.y = -s.y;
+    if (hermitian && a == b) s.y = 0.0;
+    G[(int64_t)a * ldg + b] = s;
+  }
+}
+
+// ---------------------------------------------------------- Jacobi eigensolver
+// Cyclic Jacobi for a Hermitian m x m matrix with the round-robin (circle) ordering:
+// every round rotates m/2 disjoint pairs in parallel, A <- J^H A J (columns, then
+// rows), V <- V J.  For the pair (p, q): tau = (a_qq - a_pp) / (2 |a_pq|),
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1+t^2), z = t c a_pq/|a_pq|,
+// A[:,p] <- c A[:,p] - conj(z) A[:,q], A[:,q] <- z A[:,p] + c A[:,q] (rows: with z).
+// One CTA; A and V live in global memory (L2-resident).  A bounded number of sweeps;
+// *status gets kStatusTimeout if the off-diagonal norm did not converge.
+__global__ void __launch_bounds__(1024)
+jacobi_eig_kernel(double2* __restrict__ A, double2* __restrict__ V, int m, int max_sweeps, double tol,
+                  double* __restrict__ lam, int* __restrict__ status) {
+  __shared__ int sp[128], sq[128];
+  __shared__ double sc[128];
+  __shared__ double2 sz[128];
+  __shared__ double red[2][32];
+  __shared__ int s_done;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int64_t idx = tid; idx < (int64_t)m * m; idx += nt) {
+    const int i = (int)(idx / m), j = (int)(idx % m);
+    V[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  const int n = m + (m & 1), half = n / 2;
+  bool converged = false;
+  for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
+    // off-diagonal and total Frobenius norms
+    double off = 0.0, tot = 0.0;
+    for (int64_t idx = tid; idx < (int64_t)m * m; idx += nt) {
+      const double2 v = A[idx];
+      const double s2 = v.x * v.x + v.y * v.y;
+      tot += s2;
+      if (idx / m != idx % m) off += s2;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = off;
+      red[1][tid >> 5] = tot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double o2 = 0.0, t2 = 0.0;
+      for (int k = 0; k < nt / 32; ++k) {
+        o2 += red[0][k];
+        t2 += red[1][k];
+      }
+      s_done = (o2 <= tol * tol * t2) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_done) {
+      converged = true;
+      break;
+    }
+    if (sweep == max_sweeps) break;
+    for (int t = 0; t < n - 1; ++t) {
+      if (tid < half) {
+        const int k = tid;
+        const int i1 = (k == 0) ? 0 : 1 + ((k - 1 + t) % (n - 1));
+        const int kk = n - 1 - k;
+        const int i2 = 1 + ((kk - 1 + t) % (n - 1));
+        const int p = min(i1, i2), q = max(i1, i2);
+        double c = 1.0;
+        double2 z = make_double2(0.0, 0.0);
+        if (q < m) {
+          const double2 apq = A[(int64_t)p * m + q];
+          const double g = hypot(apq.x, apq.y);
+          if (g > 0.0) {
+            const double app = A[(int64_t)p * m + p].x, aqq = A[(int64_t)q * m + q].x;
+            const double tau = (aqq - app) / (2.0 * g);
+            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + tt * tt);
+            const double s = tt * c;
+            z = make_double2(s * apq.x / g, s * apq.y / g);
+          }
+        }
+        sp[k] = p;
+        sq[k] = q;
+        sc[k] = c;
+        sz[k] = z;
+      }
+      __syncthreads();
+      // columns p, q of A and V (rows i of every pair; pairs are disjoint)
+      for (int64_t idx = tid; idx < (int64_t)m * half; idx += nt) {
+        const int i = (int)(idx / half), k = (int)(idx % half);
+        const int p = sp[k], q = sq[k];
+        if (q >= m) continue;
+        const double c = sc[k];
+        const double2 z = sz[k];
+        const double2 ap = A[(int64_t)i * m + p], aq = A[(int64_t)i * m + q];
+        // c ap - conj(z) aq ; z ap + c aq
+        A[(int64_t)i * m + p] = make_double2(c * ap.x - (z.x * aq.x + z.y * aq.y), c * ap.y - (z.x * aq.y - z.y * aq.x));
+        A[(int64_t)i * m + q] = make_double2(z.x * ap.x - z.y * ap.y + c * aq.x, z.x * ap.y + z.y * ap.x + c * aq.y);
+        const double2 vp = V[(int64_t)i * m + p], vq = V[(int64_t)i * m + q];
+        V[(int64_t)i * m + p] = make_double2(c * vp.x - (z.x * vq.x + z.y * vq.y), c * vp.y - (z.x * vq.y - z.y * vq.x));
+        V[(int64_t)i * m + q] = make_double2(z.x * vp.x - z.y * vp.y + c * vq.x, z.x * vp.y + z.y * vp.x + c * vq.y);
+      }
+      __syncthreads();
+      // rows p, q of A: A[p,:] <- c A[p,:] - z A[q,:], A[q,:] <- conj(z) A[p,:] + c A[q,:]
+      for (int64_t idx = tid; idx < (int64_t)m * half; idx += nt) {
+        const int k = (int)(idx / m), j = (int)(idx % m);
+        const int p = sp[k], q = sq[k];
+        if (q >= m) continue;
+        const double c = sc[k];
+        const double2 z = sz[k];
+        const double2 ap = A[(int64_t)p * m + j], aq = A[(int64_t)q * m + j];
+        A[(int64_t)p * m + j] = make_double2(c * ap.x - (z.x * aq.x - z.y * aq.y), c * ap.y - (z.x * aq.y + z.y * aq.x));
+        A[(int64_t)q * m + j] = make_double2(z.x * ap.x + z.y * ap.y + c * aq.x, z.x * ap.y - z.y * ap.x + c * aq.y);
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < m; i += nt) lam[i] = A[(int64_t)i * m + i].x;
+  if (tid == 0 && !converged) atomicOr(status, kStatusTimeout);
+}
+
+// ------------------------------------------------------------- basis apply
+// U[row][k] = sum_c D(row, c) W[c][k]; D(row, c) = D[row * rsD + c * csD]; U row-major (ldu).
+constexpr int kAR = 32;   // rows per CTA
+constexpr int kAC = 32;   // output columns per pass
+__global__ void __launch_bounds__(256)
+apply_basis_kernel(const double2* __restrict__ D, int64_t rsD, int64_t csD, int m, int64_t n,
+                   const double2* __restrict__ W, int r, double2* __restrict__ U, int64_t ldu) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* Dt = reinterpret_cast<double2*>(smem_raw);   // kAR x (m + 1)
+  double2* Wt = Dt + (size_t)kAR * (m + 1);             // m x kAC
+  const int tid = threadIdx.x;
+  const int64_t row0 = (int64_t)blockIdx.x * kAR;
+  for (int idx = tid; idx < kAR * m; idx += 256) {
+    int rr, c;
+    if (rsD == 1) { c = idx / kAR; rr = idx % kAR; } else { rr = idx / m; c = idx % m; }
+    const int64_t nr = row0 + rr;
+    Dt[rr * (m + 1) + c] = nr < n ? D[nr * rsD + c * csD] : make_double2(0.0, 0.0);
+  }
+  const int rr = tid % kAR, kq = tid / kAR;  // 8 groups of 4 columns
+  for (int k0 = 0; k0 < r; k0 += kAC) {
+    __syncthreads();
+    for (int idx = tid; idx < m * kAC; idx += 256) {
+      const int c = idx / kAC, kk = idx % kAC;
+      Wt[idx] = (k0 + kk < r) ? W[(size_t)c * r + k0 + kk] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    double2 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int c = 0; c < m; ++c) {
+      const double2 d = Dt[rr * (m + 1) + c];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j] = c_mac(acc[j], d, Wt[c * kAC + kq * 4 + j]);
+    }
+    const int64_t nr = row0 + rr;
+    if (nr < n) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = k0 + kq * 4 + j;
+        if (k < r) U[nr * ldu + k] = acc[j];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------- SpMM
+// Y[row][:] = sum_k K_val[k] U[K_col[k]][:] (+ e[row] U[row][:]); one warp per row.
+__global__ void __launch_bounds__(256)
+spmm_csr_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                const double* __restrict__ val, int64_t n, const double2* __restrict__ U, int r,
+                const double* __restrict__ e, double2* __restrict__ Y) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double2 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  for (int k = rowptr[row]; k < rowptr[row + 1]; ++k) {
+    const int64_t j = col[k];
+    const double v = val[k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = lane + 32 * q;
+      if (c < r) {
+        const double2 u = U[j * r + c];
+        acc[q].x = fma(v, u.x, acc[q].x);
+        acc[q].y = fma(v, u.y, acc[q].y);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = lane + 32 * q;
+    if (c < r) {
+      double2 y = acc[q];
+      if (e) {
+        const double2 u = U[row * r + c];
+        y.x = fma(e[row], u.x, y.x);
+        y.y = fma(e[row], u.y, y.y);
+      }
+      Y[row * r + c] = y;
+    }
+  }
+}
+
+// Oc[row][i] = o[i][row] + 0i (3 directions)
+__global__ void complexify_o_kernel(const double* __restrict__ o, int64_t n, double2* __restrict__ Oc) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 3 * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / 3;
+    const int i = (int)(idx % 3);
+    Oc[idx] = make_double2(o[(int64_t)i * n + row], 0.0);
+  }
+}
+
+// Phi[row] = [c o_1, c o_2, c o_3 | Y + eps m U | c U]  (width 2r + 3)
+__global__ void build_phi_kernel(const double* __restrict__ o, const double* __restrict__ cdiag,
+                                 const double* __restrict__ mdiag, double eps, const double2* __restrict__ Y,
+                                 const double2* __restrict__ U, int r, int64_t n, double2* __restrict__ Phi) {
+  const int wdt = 2 * r + 3;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)wdt * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / wdt;
+    const int k = (int)(idx % wdt);
+    const double c = cdiag[row];
+    double2 v;
+    if (k < 3) {
+      v = make_double2(c * o[(int64_t)k * n + row], 0.0);
+    } else if (k < 3 + r) {
+      const double2 y = Y[row * r + (k - 3)];
+      const double2 u = U[row * r + (k - 3)];
+      const double em = mdiag ? eps * mdiag[row] : 0.0;
+      v = make_double2(fma(em, u.x, y.x), fma(em, u.y, y.y));
+    } else {
+      const double2 u = U[row * r + (k - 3 - r)];
+      v = make_double2(c * u.x, c * u.y);
+    }
+    Phi[idx] = v;
+  }
+}
+
+__global__ void scale_kernel(const double* __restrict__ x, double a, int64_t n, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+__global__ void symmetrize_kernel(double2* __restrict__ G, int m) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m * m; idx += gridDim.x * blockDim.x) {
+    const int a = idx / m, b = idx % m;
+    if (a > b) continue;
+    const double2 x = G[a * m + b], y = G[b * m + a];
+    const double2 s = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y - y.y));
+    G[a * m + b] = s;
+    G[b * m + a] = make_double2(s.x, -s.y);
+    if (a == b) G[a * m + b].y = 0.0;
+  }
+}
+
+// Device buffers released at scope exit.
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+}  // namespace
+
+// G (ma x mb, row-major, ldg) = A^H diag(w) B over n rows; see gram_partial_kernel.
+cudaError_t tall_gram(mrom_ctx* h, const double2* A, int64_t rsA, int64_t csA, int ma, const double2* B,
+                      int64_t rsB, int64_t csB, int mb, const double* w, int wmode, int64_t n, bool hermitian,
+                      double2* G, int64_t ldg) {
+  const int ta = (ma + kGT - 1) / kGT, tb = (mb + kGT - 1) / kGT;
+  std::vector<int2> tl;
+  for (int i = 0; i < ta; ++i)
+    for (int j = hermitian ? i : 0; j < tb; ++j) tl.push_back(make_int2(i, j));
+  const int ntiles = (int)tl.size();
+  // split the rows so that about 4 CTAs per SM run, each over at least 1024 rows
+  int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>((4LL * h->num_sms + ntiles - 1) / ntiles,
+                                                          (n + 1023) / 1024));
+  nsplit = std::min<int64_t>(nsplit, 65535);
+  const int64_t per = ((n + nsplit - 1) / nsplit + kGR - 1) / kGR * kGR;
+  nsplit = (n + per - 1) / per;
+  if (nsplit < 1) nsplit = 1;
+  DevBuf part, tiles;
+  cudaError_t e = cudaMalloc(&part.p, (size_t)nsplit * ma * mb * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&tiles.p, tl.size() * sizeof(int2));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tiles.p, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)nsplit, (unsigned)ntiles);
+  gram_partial_kernel<<<grid, 256, 0, h->stream>>>(A, rsA, csA, ma, B, rsB, csB, mb, w, wmode, n, per,
+                                                  static_cast<int2*>(tiles.p), static_cast<double2*>(part.p));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int rb = (int)std::min<int64_t>(4096, ((int64_t)ma * mb + 255) / 256);
+  gram_reduce_kernel<<<std::max(rb, 1), 256, 0, h->stream>>>(static_cast<double2*>(part.p), (int)nsplit, ma, mb,
+                                                              hermitian ? 1 : 0, G, ldg);
+  e = cudaGetLastError();
+  h->launches += 2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // part/tiles are freed on return
+  return e;
+}
+
+}  // namespace mrom
+
+using namespace mrom;
+
+extern "C" mrom_status mrom_project(mrom_handle h, const mrom_fom* fom, const void* D, int64_t ldd, int32_t n_cols,
+                                    double tol_sigma, int32_t r_max, const void* basis_in, int32_t r_in,
+                                    mrom_rom_t* out, double* sigma_out, int32_t* r_out) {
+  if (!h) return MROM_EINVAL;
+  if (!fom || !out) return fail(h, MROM_EINVAL, "mrom_project: null argument");
+  *out = nullptr;
+  const int64_t n = fom->n;
+  if (n < 1 || !fom->K_rowptr || !fom->K_col || !fom->K_val || !fom->C_diag || !fom->o)
+    return fail(h, MROM_EINVAL, "mrom_project: n, K, C_diag and o are required");
+  if (!(fom->alpha > 0) || !std::isfinite(fom->alpha) || !std::isfinite(fom->eps))
+    return fail(h, MROM_EINVAL, "mrom_project: alpha must be finite and > 0, eps finite");
+  if (fom->X_diag && !(fom->alpha_lb > 0))
+    return fail(h, MROM_EINVAL, "mrom_project: a certificate needs alpha_lb > 0");
+  if (!basis_in) {
+    if (!D || n_cols < 1 || n_cols > MROM_MAX_SNAPSHOTS || ldd < n)
+      return fail(h, MROM_EINVAL, "mrom_project: D needs 1..MROM_MAX_SNAPSHOTS columns and ldd >= n");
+    if (!(tol_sigma >= 0.0) || !std::isfinite(tol_sigma))
+      return fail(h, MROM_EINVAL, "mrom_project: tol_sigma must be finite and >= 0");
+  } else if (r_in < 1 || r_in > MROM_MAX_R) {
+    return fail(h, MROM_EINVAL, "mrom_project: r_in must be in [1, MROM_MAX_R]");
+  }
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: cudaSetDevice");
+  cudaStream_t st = h->stream;
+  auto launch_grid = [](int64_t work) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(65535 * 4, (work + 255) / 256)); };
+
+  // ---- basis U (row-major n x r)
+  DevBuf Ubuf;
+  const double2* U = nullptr;
+  int r = 0;
+  if (basis_in) {
+    U = static_cast<const double2*>(basis_in);
+    r = r_in;
+  } else {
+    const int m = n_cols;
+    const auto* Dp = static_cast<const double2*>(D);
+    DevBuf g, vbuf, lam;
+    e = cudaMalloc(&g.p, (size_t)m * m * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&vbuf.p, (size_t)m * m * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&lam.p, (size_t)m * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: allocation");
+    // D(row, c) = D[row + c * ldd]
+    e = tall_gram(h, Dp, 1, ldd, m, Dp, 1, ldd, m, nullptr, 0, n, true, static_cast<double2*>(g.p), m);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: snapshot Gram");
+    jacobi_eig_kernel<<<1, 1024, 0, st>>>(static_cast<double2*>(g.p), static_cast<double2*>(vbuf.p), m, 60, 1e-15,
+                                          static_cast<double*>(lam.p), h->d_status);
+    ++h->launches;
+    std::vector<double> lh(m);
+    std::vector<double2> vh((size_t)m * m);
+    e = cudaMemcpyAsync(lh.data(), lam.p, m * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(vh.data(), vbuf.p, vh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: eigensolver");
+    int stw = 0;
+    cudaMemcpy(&stw, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (stw & kStatusTimeout) {
+      cudaMemset(h->d_status, 0, sizeof(int));
+      return fail(h, MROM_ENOTCONVERGED, "mrom_project: Jacobi eigensolver did not converge");
+    }
+    std::vector<int> order(m);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lh[a] > lh[b]; });
+    std::vector<double> s(m);
+    for (int k = 0; k < m; ++k) s[k] = std::sqrt(std::max(lh[order[k]], 0.0));
+    if (sigma_out) std::copy(s.begin(), s.end(), sigma_out);
+    // truncation rule (Eq. (15) reading): keep s_k / s_1 >= TOL_Sigma, at most r_max and MROM_MAX_R
+    for (int k = 0; k < m; ++k)
+      if (s[0] > 0 && s[k] > 0 && s[k] / s[0] >= tol_sigma) r = k + 1;
+    if (r_max > 0) r = std::min(r, (int)r_max);
+    r = std::min(r, MROM_MAX_R);
+    if (r < 1) return fail(h, MROM_EINVAL, "mrom_project: snapshots have no nonzero singular value");
+    std::vector<double2> wh((size_t)m * r);
+    for (int c = 0; c < m; ++c)
+      for (int k = 0; k < r; ++k) {
+        const double2 v = vh[(size_t)c * m + order[k]];
+        wh[(size_t)c * r + k] = make_double2(v.x / s[k], v.y / s[k]);
+      }
+    DevBuf wbuf;
+    e = cudaMalloc(&wbuf.p, wh.size() * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&Ubuf.p, (size_t)n * r * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(wbuf.p, wh.data(), wh.size() * sizeof(double2), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: basis allocation");
+    const size_t smem = ((size_t)kAR * (m + 1) + (size_t)m * kAC) * sizeof(double2);
+    e = cudaFuncSetAttribute(apply_basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: basis kernel attribute");
+    apply_basis_kernel<<<(unsigned)((n + kAR - 1) / kAR), 256, smem, st>>>(Dp, 1, ldd, m, n,
+                                                                           static_cast<double2*>(wbuf.p), r,
+                                                                           static_cast<double2*>(Ubuf.p), r);
+    ++h->launches;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: basis");
+    U = static_cast<const double2*>(Ubuf.p);
+  }
+  if (r_out) *r_out = r;
+
+  // ---- projections
+  const int ng = 2 * r + 3;
+  DevBuf Y, Oc, small, phi, winv;
+  e = cudaMalloc(&Y.p, (size_t)n * r * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&Oc.p, (size_t)n * 3 * sizeof(double2));
+  // small: Kr, Cr, Me (r x r each), B (r x 3), c00c (3 x 3), G (ng x ng)
+  const size_t nsmall = 3 * (size_t)r * r + 3 * (size_t)r + 9 + (size_t)ng * ng;
+  if (e == cudaSuccess) e = cudaMalloc(&small.p, nsmall * sizeof(double2));
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: allocation");
+  double2* Kr = static_cast<double2*>(small.p);
+  double2* Cr = Kr + (size_t)r * r;
+  double2* Me = Cr + (size_t)r * r;
+  double2* Bm = Me + (size_t)r * r;
+  double2* c00c = Bm + 3 * (size_t)r;
+  double2* Gm = c00c + 9;
+  spmm_csr_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(fom->K_rowptr, fom->K_col, fom->K_val, n, U, r,
+                                                                    nullptr, static_cast<double2*>(Y.p));
+  complexify_o_kernel<<<launch_grid(3 * n), 256, 0, st>>>(fom->o, n, static_cast<double2*>(Oc.p));
+  h->launches += 2;
+  e = cudaGetLastError();
+  const double2* Yp = static_cast<const double2*>(Y.p);
+  const double2* Op = static_cast<const double2*>(Oc.p);
+  // K_r = U^H (K U), symmetrised (K is symmetric)
+  if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, Yp, r, 1, r, nullptr, 0, n, false, Kr, r);
+  if (e == cudaSuccess) {
+    symmetrize_kernel<<<(r * r + 255) / 256, 256, 0, st>>>(Kr, r);
+    ++h->launches;
+  }
+  if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, U, r, 1, r, fom->C_diag, 1, n, true, Cr, r);
+  DevBuf em;
+  if (e == cudaSuccess && fom->M_diag && fom->eps != 0.0) {
+    e = cudaMalloc(&em.p, n * sizeof(double));
+    if (e == cudaSuccess) {
+      scale_kernel<<<launch_grid(n), 256, 0, st>>>(fom->M_diag, fom->eps, n, static_cast<double*>(em.p));
+      ++h->launches;
+      e = cudaGetLastError();
+    }
+    // Me = U^H diag(eps m) U  (added to the reduced system only, Eq. (17))
+    if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, U, r, 1, r, static_cast<double*>(em.p), 1, n, true, Me, r);
+  }
+  if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, Op, 3, 1, 3, fom->C_diag, 1, n, false, Bm, 3);
+  if (e == cudaSuccess) e = tall_gram(h, Op, 3, 1, 3, Op, 3, 1, 3, fom->C_diag, 1, n, true, c00c, 3);
+  bool cert = fom->X_diag != nullptr;
+  if (e == cudaSuccess && cert) {
+    e = cudaMalloc(&phi.p, (size_t)n * ng * sizeof(double2));
+    if (e == cudaSuccess) {
+      build_phi_kernel<<<launch_grid((int64_t)ng * n), 256, 0, st>>>(fom->o, fom->C_diag, fom->M_diag, fom->eps, Yp, U,
+                                                                     r, n, static_cast<double2*>(phi.p));
+      ++h->launches;
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = tall_gram(h, static_cast<double2*>(phi.p), ng, 1, ng, static_cast<double2*>(phi.p), ng, 1, ng,
+                    fom->X_diag, 2, n, true, Gm, ng);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: projection");
+  std::vector<double2> c00h(9);
+  e = cudaMemcpy(c00h.data(), c00c, 9 * sizeof(double2), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: read-back");
+  double c00[9];
+  for (int k = 0; k < 9; ++k) c00[k] = c00h[k].x;
+  mrom_reduced_desc d{};
+  d.r = r;
+  d.K = Kr;
+  d.C = Cr;
+  d.Me = (fom->M_diag && fom->eps != 0.0) ? Me : nullptr;
+  d.B = Bm;
+  d.c00 = c00;
+  d.G = cert ? Gm : nullptr;
+  d.N0 = fom->N0;
+  d.alpha = fom->alpha;
+  d.alpha_lb = cert ? fom->alpha_lb : 0.0;
+  d.vol_B = fom->vol_B;
+  return mrom_rom_from_reduced(h, &d, out);
+}
+
+extern "C" mrom_status mrom_rom_get(mrom_rom_t rom, void* K, void* C, void* Me, void* B, double* c00, void* G) {
+  if (!rom) return MROM_EINVAL;
+  mrom_ctx* h = rom->ctx;
+  const size_t rr = (size_t)rom->r * rom->r;
+  const size_t ng = (size_t)(2 * rom->r + 3);
+  cudaSetDevice(h->device);
+  cudaError_t e = cudaSuccess;
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    if (dst && e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyDefault);
+  };
+  cp(K, rom->K, rr * 16);
+  cp(C, rom->C, rr * 16);
+  if (Me) {
+    if (rom->Me) {
+      cp(Me, rom->Me, rr * 16);
+    } else {
+      const std::vector<double2> zeros(rr, make_double2(0.0, 0.0));
+      cp(Me, zeros.data(), rr * 16);
+    }
+  }
+  cp(B, rom->B, 3 * (size_t)rom->r * 16);
+  if (c00) std::copy(rom->c00, rom->c00 + 9, c00);
+  if (G) {
+    if (!rom->G) return fail(h, MROM_EINVAL, "mrom_rom_get: object has no Gram matrix");
+    cp(G, rom->G, ng * ng * 16);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_rom_get");
+  return MROM_OK;
+}

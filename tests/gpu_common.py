@@ -6,22 +6,29 @@ from oracle import certificate, rom
 
 def oracle_sweep(obj, omegas, s_sigma=1.0):
     """R, I, Delta and the per-(omega) term scales from the CPU oracle."""
+    return oracle_model_sweep(rom.from_reduced_object(obj), omegas, s_sigma)
+
+
+def oracle_model_sweep(model, omegas, s_sigma=1.0):
+    """As oracle_sweep, for a shared-basis oracle ReducedModel."""
     w = np.asarray(omegas, dtype=np.float64) * s_sigma
-    model = rom.from_reduced_object(obj)
     P = rom.reduced_solve(model, w)
     R, I = rom.mm_tensors(model, w, P)
-    Dl = certificate.certificate(model, w, P)
-    a3 = obj.alpha ** 3
+    Dl = certificate.certificate(model, w, P) if model.gram is not None else None
+    a3 = model.alpha ** 3
     sI = np.empty(w.size)
     sD = np.empty(w.size)
-    absG = np.abs(obj.G)
+    absG = np.abs(model.gram) if model.gram is not None else None
+    C = model.C[0][0]
+    B = np.stack([model.b(i) for i in range(3)], 1)
     for n in range(w.size):
         Pm = np.stack([P[i][n] for i in range(3)], 1)
-        hc = np.abs(Pm.conj().T @ obj.C @ Pm).max()
-        bp = np.abs(obj.B.conj().T @ Pm).max()
-        sI[n] = w[n] * a3 / 4 * (np.abs(obj.c00).max() + hc + 2 * bp)
-        W = certificate.residual_weights(model, w[n], [P[i][n] for i in range(3)])
-        sD[n] = a3 / (4 * obj.alpha_lb) * max(np.abs(x) @ absG @ np.abs(x) for x in W)
+        hc = np.abs(Pm.conj().T @ C @ Pm).max()
+        bp = np.abs(B.conj().T @ Pm).max()
+        sI[n] = w[n] * a3 / 4 * (np.abs(model.c00).max() + hc + 2 * bp)
+        if absG is not None:
+            W = certificate.residual_weights(model, w[n], [P[i][n] for i in range(3)])
+            sD[n] = a3 / (4 * model.alpha_lb) * max(np.abs(x) @ absG @ np.abs(x) for x in W)
     return R, I, Dl, sI, sD
 
 
