@@ -168,6 +168,41 @@ mrom_status mrom_project(mrom_handle h, const mrom_fom* fom, const void* D, int6
                          double tol_sigma, int32_t r_max, const void* basis_in, int32_t r_in, mrom_rom_t* out,
                          double* sigma_out, int32_t* r_out);
 
+/* Adaptive PODP, Algorithm 1 (Sect. 4.4), with one basis for the three directions.
+ * Starting from ns0 >= 2 snapshots at omega0 (host, ns0 values) with their
+ * 3 * ns0 full-order solution columns in D0 (length n each, column c at
+ * D0 + c * n, host or device; any column order), repeat while
+ * Lambda / |B_alpha| > tol_delta and k < max_k (k starts at 1):
+ *   k <- k + 1; project (mrom_project with tol_sigma, r_max) and evaluate the
+ *   certificate Delta on omega_out (device, n_out values, strictly increasing);
+ *   Lambda_n = max over the output frequencies in [omega_n, omega_{n+1}) that are
+ *   not snapshots of max_ij Delta_ij (ties: lowest frequency), Lambda = max_n;
+ *   stop if Lambda / |B_alpha| <= tol_delta; else ask the callback for the
+ *   full-order solutions at the frequencies of the n_star largest Lambda_n (one
+ *   per interval), append them and re-project.
+ * |B_alpha| = alpha^3 vol_B.  fom->X_diag is required (certificate).  The
+ * callback receives n_new frequencies (host, ascending) and a HOST buffer of
+ * 3 * n_new * n complex128 to fill: column j * 3 + i holds q_i(omega_new[j])
+ * (Eq. (9)) at offset (j * 3 + i) * n; it returns 0 on success (anything else
+ * stops the loop with MROM_ECALLBACK).  Outputs: the final reduced object
+ * (*out), Lambda after each certificate evaluation (lambda_hist, host, max_k
+ * values, or NULL), the final k (k_done), the sorted snapshot frequencies
+ * (omega_snap_out, host, ns0 + n_star (max_k - 1) values, or NULL) and their
+ * number (ns_out).  Requires 3 (ns0 + n_star (max_k - 1)) <= MROM_MAX_SNAPSHOTS.
+ * Synchronous; allocates its snapshot buffer. */
+typedef int (*mrom_snapshot_cb)(void* user, int32_t n_new, const double* omega_new, void* D_new_host);
+typedef struct {
+  double tol_sigma;
+  double tol_delta;
+  int32_t n_star;
+  int32_t max_k;
+  int32_t r_max;
+} mrom_adapt_opts;
+mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const double* omega0, int32_t ns0, const void* D0,
+                       mrom_snapshot_cb cb, void* user, const double* omega_out, int32_t n_out,
+                       const mrom_adapt_opts* opts, mrom_rom_t* out, double* lambda_hist, int32_t* k_done,
+                       double* omega_snap_out, int32_t* ns_out);
+
 /* Copy an object's reduced data to caller buffers (host or device; any may be
  * NULL): K, C, Me (r x r complex128; zeros when the object has no Me), B
  * (r x 3), c00 (9 float64, host), G ((2r+3)^2; MROM_EINVAL if the object has
@@ -195,10 +230,27 @@ mrom_status mrom_rom_get(mrom_rom_t rom, void* K, void* C, void* Me, void* B, do
  * n_obj * n_w * 9 doubles; omega holds n_w (stride 0) or n_obj * n_w values.
  * s_sigma, s_mu (device, n_obj each, or NULL for 1): per-object conductivity
  * and permeability scales; s_sigma acts as omega -> s_sigma omega (nu is
- * linear in omega sigma); s_mu != 1 requires K_in and no Delta. */
+ * linear in omega sigma).  s_mu must be NULL here (MROM_ENOTSUP); the forward
+ * values at a permeability scale come from mrom_sweep_vjp. */
 mrom_status mrom_sweep(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega,
                        int32_t n_w, int32_t omega_stride, const double* s_sigma, const double* s_mu,
                        double* R, double* I, double* Delta);
+
+/* Vector-Jacobian product of the sweep (not in the paper; gradients for
+ * inverse problems and least-squares fits of material scales).  With the
+ * forward model of mrom_sweep extended by a conductivity scale s_sigma
+ * (omega -> s_sigma omega) and a permeability scale s_mu
+ * (K(s_mu) = K + (1/s_mu - 1) K_in), and cotangents gR, gI ([n_obj][n_w][3][3],
+ * device), it writes g_omega[o][k] = dL/domega (device, n_obj * n_w),
+ * g_ssigma[o] = dL/ds_sigma and g_smu[o] = dL/ds_mu (device, n_obj each, or
+ * NULL) for L = sum gR . R + gI . I, by an adjoint solve with the same LU
+ * factors (recomputed, not stored).  R and I (device, or NULL) receive the
+ * forward values at these scales.  s_sigma, s_mu: device, n_obj each, or NULL
+ * for 1; s_mu or g_smu require K_in on every object.  Asynchronous; allocates
+ * its tables stream-ordered. */
+mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega, int32_t n_w,
+                           int32_t omega_stride, const double* s_sigma, const double* s_mu, const double* gR,
+                           const double* gI, double* g_omega, double* g_ssigma, double* g_smu, double* R, double* I);
 
 /* Certificate only: Delta as in mrom_sweep, without writing R and I. */
 mrom_status mrom_certificate(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega,

@@ -36,7 +36,7 @@ def interval_maxima(snaps: np.ndarray, omega_out: np.ndarray, dmax: np.ndarray):
 
 
 def adaptive_podp(problem, snapshot_fn, omega0, omega_out, *, tol_sigma=1e-6, tol_delta=1e-3,
-                  n_star=2, max_k=10, r_max=None, shared=False):
+                  n_star=2, max_k=10, r_max=None, shared=False, X_diag=None):
     """Run Algorithm 1; returns (model, snapshot omegas, Lambda history, k).
 
     snapshot_fn(omegas) must return the (3, N, len(omegas)) full-order
@@ -47,7 +47,7 @@ def adaptive_podp(problem, snapshot_fn, omega0, omega_out, *, tol_sigma=1e-6, to
     D = snapshot_fn(snaps)
     omega_min = float(omega_out.min())
     model, _, _ = pipeline.build_model(problem, D, tol_sigma=tol_sigma, r_max=r_max, shared=shared,
-                                       omega_min=omega_min)
+                                       omega_min=omega_min, X_diag=X_diag)
     b_alpha = problem.alpha ** 3 * problem.vol_B
     k, Lam, hist = 1, np.inf, []
     while Lam / b_alpha > tol_delta and k < max_k:
@@ -65,5 +65,5 @@ def adaptive_podp(problem, snapshot_fn, omega0, omega_out, *, tol_sigma=1e-6, to
         D = np.concatenate([D, snapshot_fn(new)], axis=2)
         snaps = np.concatenate([snaps, new])
         model, _, _ = pipeline.build_model(problem, D, tol_sigma=tol_sigma, r_max=r_max,
-                                           shared=shared, omega_min=omega_min)
+                                           shared=shared, omega_min=omega_min, X_diag=X_diag)
     return model, np.sort(snaps), hist, k

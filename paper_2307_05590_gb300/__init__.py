@@ -22,7 +22,7 @@ __all__ = [
     "mrom_create", "mrom_destroy", "mrom_synchronize", "mrom_last_error", "mrom_launch_count",
     "mrom_rom_from_reduced", "mrom_rom_free", "mrom_rom_rank", "mrom_sweep", "mrom_certificate",
     "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune", "mrom_sweep_noalloc",
-    "FullOrder", "mrom_project", "mrom_rom_get",
+    "FullOrder", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "MromSweep", "signature",
 ]
 
 
@@ -320,3 +320,133 @@ def mrom_rom_get(rom: ReducedObject, with_gram: bool = True) -> dict:
     out["c00"] = out["c00"].reshape(3, 3)
     out["G"] = G
     return out
+
+
+def mrom_adapt(h: Handle, fom: FullOrder, omega0, D0, snapshot_fn, omega_out, *, tol_sigma: float = 1e-6,
+               tol_delta: float = 1e-3, n_star: int = 2, max_k: int = 10, r_max: int = 0):
+    """Algorithm 1 on the GPU.
+
+    omega0: initial snapshot frequencies (numpy); D0: device (3 * ns0, n) complex128
+    solution columns; snapshot_fn(omegas) -> numpy (3, n, len(omegas)) full-order
+    solutions (called from the library for every refinement); omega_out: device
+    float64, strictly increasing.  Returns (ReducedObject, Lambda history, k,
+    sorted snapshot frequencies).
+    """
+    omega0 = np.ascontiguousarray(omega0, dtype=np.float64)
+    n = int(fom.desc.n)
+    errors = []
+
+    def _cb(user, n_new, omega_ptr, buf):
+        try:
+            ws = np.ctypeslib.as_array(omega_ptr, shape=(n_new,)).copy()
+            D = snapshot_fn(ws)
+            dst = np.ctypeslib.as_array(ctypes.cast(buf, ctypes.POINTER(ctypes.c_double)),
+                                        shape=(n_new * 3 * n * 2,)).view(np.complex128)
+            dst[:] = np.ascontiguousarray(np.transpose(D, (2, 0, 1))).reshape(-1)
+            return 0
+        except Exception as exc:  # reported as MROM_ECALLBACK
+            errors.append(exc)
+            return 1
+
+    cb = _abi.SNAPSHOT_CB(_cb)
+    opts = _abi.mrom_adapt_opts(float(tol_sigma), float(tol_delta), int(n_star), int(max_k), int(r_max))
+    hist = np.full(max_k, np.nan)
+    cap = omega0.size + n_star * max(0, max_k - 1)
+    snaps = np.zeros(cap)
+    rom = ctypes.c_void_p()
+    k = ctypes.c_int32(0)
+    ns = ctypes.c_int32(0)
+    dp = ctypes.POINTER(ctypes.c_double)
+    status = lib().mrom_adapt(h.ptr, ctypes.byref(fom.desc), omega0.ctypes.data_as(dp), omega0.size, _ptr(D0),
+                              cb, None, _ptr(omega_out), int(omega_out.numel()), ctypes.byref(opts),
+                              ctypes.byref(rom), hist.ctypes.data_as(dp), ctypes.byref(k), snaps.ctypes.data_as(dp),
+                              ctypes.byref(ns))
+    if errors:
+        raise errors[0]
+    _abi.check(status, h.ptr)
+    obj = ReducedObject._wrap(h, rom, lib().mrom_rom_rank(rom), True)
+    return obj, hist[~np.isnan(hist)], int(k.value), snaps[: ns.value]
+
+
+def mrom_sweep_vjp(h: Handle, objs, omega, n_w: int, gR, gI, g_omega, *, g_ssigma=None, g_smu=None,
+                   s_sigma=None, s_mu=None, R=None, I=None, omega_stride: int = 0) -> None:
+    """Adjoint of the sweep: dL/domega, dL/ds_sigma, dL/ds_mu for L = <gR, R> + <gI, I> (device tensors)."""
+    _abi.check(lib().mrom_sweep_vjp(h.ptr, _rom_array(objs), len(objs), _ptr(omega), int(n_w), int(omega_stride),
+                                    _ptr(s_sigma), _ptr(s_mu), _ptr(gR), _ptr(gI), _ptr(g_omega), _ptr(g_ssigma),
+                                    _ptr(g_smu), _ptr(R), _ptr(I)), h.ptr)
+
+
+def _sweep_values(h, objs, omega, s_sigma, s_mu):
+    import torch
+    n_obj = len(objs)
+    n_w = omega.shape[-1]
+    stride = n_w if omega.dim() == 2 else 0
+    dev = omega.device
+    R = torch.empty((n_obj, n_w, 3, 3), dtype=torch.float64, device=dev)
+    I = torch.empty_like(R)
+    if s_mu is None:
+        mrom_sweep(h, objs, omega.contiguous(), n_w, R, I, omega_stride=stride,
+                   s_sigma=None if s_sigma is None else s_sigma.contiguous())
+    else:
+        z = torch.zeros_like(R)
+        g = torch.empty((n_obj, n_w), dtype=torch.float64, device=dev)
+        mrom_sweep_vjp(h, objs, omega.contiguous(), n_w, z, z, g, s_sigma=None if s_sigma is None else
+                       s_sigma.contiguous(), s_mu=s_mu.contiguous(), R=R, I=I, omega_stride=stride)
+    return R, I
+
+
+def _autograd_function():
+    import torch
+
+    class MromSweep(torch.autograd.Function):
+        """(omega, s_sigma, s_mu) -> (R, I) with the adjoint kernel as backward."""
+
+        @staticmethod
+        def forward(ctx, omega, s_sigma, s_mu, handle, objs):
+            R, I = _sweep_values(handle, objs, omega, s_sigma, s_mu)
+            ctx.save_for_backward(omega, s_sigma, s_mu)
+            ctx.handle, ctx.objs = handle, objs
+            return R, I
+
+        @staticmethod
+        def backward(ctx, gR, gI):
+            omega, s_sigma, s_mu = ctx.saved_tensors
+            h, objs = ctx.handle, ctx.objs
+            n_obj, n_w = len(objs), omega.shape[-1]
+            stride = n_w if omega.dim() == 2 else 0
+            dev = omega.device
+            gR = torch.zeros((n_obj, n_w, 3, 3), dtype=torch.float64, device=dev) if gR is None else gR.contiguous()
+            gI = torch.zeros((n_obj, n_w, 3, 3), dtype=torch.float64, device=dev) if gI is None else gI.contiguous()
+            g_w = torch.empty((n_obj, n_w), dtype=torch.float64, device=dev)
+            g_ss = torch.empty(n_obj, dtype=torch.float64, device=dev)
+            g_sm = torch.empty(n_obj, dtype=torch.float64, device=dev) if s_mu is not None else None
+            mrom_sweep_vjp(h, objs, omega.contiguous(), n_w, gR, gI, g_w, g_ssigma=g_ss, g_smu=g_sm,
+                           s_sigma=s_sigma, s_mu=s_mu, omega_stride=stride)
+            g_omega = g_w if omega.dim() == 2 else g_w.sum(0)
+            return (g_omega if ctx.needs_input_grad[0] else None,
+                    g_ss if ctx.needs_input_grad[1] else None,
+                    g_sm if ctx.needs_input_grad[2] else None, None, None)
+
+    return MromSweep
+
+
+class _Lazy:
+    _fn = None
+
+    def __call__(self):
+        if _Lazy._fn is None:
+            _Lazy._fn = _autograd_function()
+        return _Lazy._fn
+
+
+MromSweep = _Lazy()
+
+
+def signature(handle: Handle, objs, omega, s_sigma=None, s_mu=None):
+    """Differentiable (R, I) of the objects: omega (n_w,) shared or (n_obj, n_w) per object,
+    s_sigma / s_mu (n_obj,) device tensors or None."""
+    import torch
+    dev = omega.device
+    n = len(objs)
+    ss = s_sigma if s_sigma is not None else torch.ones(n, dtype=torch.float64, device=dev)
+    return MromSweep().apply(omega, ss, s_mu, handle, list(objs))

@@ -16,7 +16,7 @@ EXPORTS = [
     "mrom_create", "mrom_destroy", "mrom_set_stream", "mrom_synchronize", "mrom_last_error",
     "mrom_launch_count", "mrom_rom_from_reduced", "mrom_rom_rank", "mrom_rom_free", "mrom_sweep",
     "mrom_certificate", "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune",
-    "mrom_sweep_noalloc", "mrom_project", "mrom_rom_get",
+    "mrom_sweep_noalloc", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp",
 ]
 
 
@@ -42,6 +42,20 @@ class mrom_fom(ctypes.Structure):
         ("vol_B", ctypes.c_double),
         ("N0", ctypes.c_void_p),
     ]
+
+
+class mrom_adapt_opts(ctypes.Structure):
+    _fields_ = [
+        ("tol_sigma", ctypes.c_double),
+        ("tol_delta", ctypes.c_double),
+        ("n_star", ctypes.c_int32),
+        ("max_k", ctypes.c_int32),
+        ("r_max", ctypes.c_int32),
+    ]
+
+
+SNAPSHOT_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                               ctypes.c_void_p)
 
 
 class mrom_reduced_desc(ctypes.Structure):
@@ -84,6 +98,12 @@ def _declare(L):
                                         ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(i32)]),
         "mrom_rom_get": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp]),
+        "mrom_sweep_vjp": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, dp, i32, i32, dp, dp, dp, dp, dp, dp, dp, dp,
+                                          dp]),
+        "mrom_adapt": (ctypes.c_int, [vp, ctypes.POINTER(mrom_fom), ctypes.POINTER(ctypes.c_double), i32, vp,
+                                      SNAPSHOT_CB, vp, dp, i32, ctypes.POINTER(mrom_adapt_opts),
+                                      ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

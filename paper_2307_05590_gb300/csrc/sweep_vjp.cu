@@ -1,0 +1,442 @@
+// Vector-Jacobian product of the batched sweep (R, I) with respect to the frequency
+// omega, a conductivity scale s_sigma and a permeability scale s_mu.
+//
+// Forward model per (object, omega) (Eqs. (17)-(19) with the scales applied):
+//   w' = s_sigma omega,  K(s_mu) = K + (1/s_mu - 1) K_in,
+//   A = K(s_mu) + Me - i w' C,  A P = i w' B,
+//   R = -a^3/4 Re(P^H K(s_mu) P) (+ N0),  I = w' a^3/4 (c00 + Re(P^H C P + B^H P + P^H B)).
+// For L = sum gR_ij R_ij + gI_ij I_ij, dL = Re tr(dP^H Z) with
+//   Z = -a^3/4 K(s_mu) P G_R + w' a^3/4 (C P + B) G_I,   G = g + g^T,
+// and with the adjoint Lambda = A^-H Z (same LU factors: U^H then L^H),
+//   dL/domega = s_sigma Im tr((B + C P)^H Lambda) + sum gI_ij I_ij / omega,
+//   dL/ds_mu  = (Re tr((K_in P)^H Lambda) + a^3/4 sum gR_ij Re(p_i^H K_in p_j)) / s_mu^2,
+//   dL/ds_sigma = sum_omega (omega / s_sigma) dL/domega      (I(omega; s_sigma) = I(s_sigma omega; 1)).
+// The factors are recomputed here instead of being stored per frequency.
+#include "mrom_internal.h"
+
+#include <algorithm>
+#include <numeric>
+
+namespace mrom {
+namespace {
+
+constexpr int kT = 128;  // threads per CTA (4 CTAs per SM)
+constexpr int kW = kT / 32;
+constexpr int kRedV = 40;
+
+__device__ __forceinline__ double2 c_msub(double2 c, double2 a, double2 b) {
+  return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 c_mul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 c_conj_mac(double2 c, double2 a, double2 b) {  // c + conj(a) b
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 c_conj_msub(double2 c, double2 a, double2 b) {  // c - conj(a) b
+  return make_double2(fma(-a.x, b.x, fma(-a.y, b.y, c.x)), fma(-a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 c_recip(double2 a, int* status) {
+  const double d = fma(a.x, a.x, a.y * a.y);
+  if (!(d > 0.0) || !isfinite(d)) {
+    atomicOr(status, kStatusSingular);
+    return make_double2(__longlong_as_double(0x7ff8000000000000LL), 0.0);
+  }
+  const double id = 1.0 / d;
+  return make_double2(a.x * id, -a.y * id);
+}
+
+struct VjpObj {
+  const double2 *K, *Kin, *C, *Me, *B;
+  double c00[9], N0[9];
+  double alpha3;
+  int r;
+};
+
+__global__ void __launch_bounds__(kT, 4)
+sweep_vjp_kernel(const VjpObj* __restrict__ objs, const SweepTask* __restrict__ tasks, int n_tasks,
+                 int* __restrict__ counter, const double* __restrict__ omega, int omega_stride,
+                 const double* __restrict__ s_sigma, const double* __restrict__ s_mu,
+                 const double* __restrict__ gR, const double* __restrict__ gI, double* __restrict__ g_omega,
+                 double* __restrict__ g_mu_part, double* __restrict__ Rout, double* __restrict__ Iout,
+                 int* __restrict__ status, int n_w, double2* __restrict__ workspace, size_t ws_elems) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_task;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();
+    if (t >= n_tasks) break;
+    const SweepTask task = tasks[t];
+    const VjpObj& ob = objs[task.obj];
+    const int r = ob.r, S = task.nw, ld = r + 3;
+    const size_t per_elems = (size_t)r * ld + 9 * (size_t)r;  // augmented system + y^K, y^C, y^Kin
+    double2* sp = reinterpret_cast<double2*>(smem_raw);
+    double2* Am;
+    if (task.pad & 1) {
+      Am = workspace + (size_t)blockIdx.x * ws_elems;
+    } else {
+      Am = sp;
+      sp += (size_t)S * per_elems;
+    }
+    double2* Pm = sp;                                   // S * r * 3
+    double2* Inv = Pm + (size_t)S * r * 3;              // S * r
+    double* Ws = reinterpret_cast<double*>(Inv + (size_t)S * r);  // S
+    double* Gs = Ws + S;                                // S * 18: symmetrised gR, gI
+    double* Red = Gs + (size_t)S * 18;                  // S * kRedV
+    const double ssig = s_sigma ? s_sigma[task.obj] : 1.0;
+    const double smu = s_mu ? s_mu[task.obj] : 1.0;
+    const double fmu = 1.0 / smu - 1.0;
+    const bool kin = ob.Kin != nullptr;
+
+    for (int s = tid; s < S; s += kT) {
+      const double w = omega[(size_t)task.obj * omega_stride + task.w0 + s] * ssig;
+      const bool ok = (w > 0.0) && isfinite(w) && (smu > 0.0) && (ssig > 0.0);
+      if (!ok) atomicOr(status, kStatusBadOmega);
+      Ws[s] = ok ? w : __longlong_as_double(0x7ff8000000000000LL);
+    }
+    for (int idx = tid; idx < S * 18; idx += kT) {
+      const int s = idx / 18, q = idx % 18;
+      const size_t e = ((size_t)task.obj * n_w + task.w0 + s) * 9;
+      const double* g = q < 9 ? gR : gI;
+      const int ij = q % 9, i = ij / 3, j = ij % 3;
+      Gs[idx] = g[e + i * 3 + j] + g[e + j * 3 + i];
+    }
+    __syncthreads();
+
+    // ---- forward: [K(s_mu) + Me - i w' C | i w' B], elimination, back substitution
+    for (int idx = tid; idx < S * r * ld; idx += kT) {
+      const int s = idx / (r * ld);
+      const int e = idx - s * r * ld;
+      const int i = e / ld, j = e - (e / ld) * ld;
+      const double w = Ws[s];
+      double2 v;
+      if (j < r) {
+        double2 k = ob.K[i * r + j];
+        if (kin) {
+          const double2 q = ob.Kin[i * r + j];
+          k.x = fma(fmu, q.x, k.x);
+          k.y = fma(fmu, q.y, k.y);
+        }
+        if (ob.Me) {
+          const double2 m = ob.Me[i * r + j];
+          k.x += m.x;
+          k.y += m.y;
+        }
+        const double2 c = ob.C[i * r + j];
+        v = make_double2(fma(w, c.y, k.x), fma(-w, c.x, k.y));
+      } else {
+        const double2 b = ob.B[i * 3 + (j - r)];
+        v = make_double2(-w * b.y, w * b.x);
+      }
+      Am[(size_t)s * per_elems + e] = v;
+      if (e == 0) Inv[(size_t)s * r] = c_recip(v, status);
+    }
+    __syncthreads();
+    for (int k = 0; k < r - 1; ++k) {
+      const int m = r - k - 1;
+      for (int idx = tid; idx < S * m; idx += kT) {
+        const int s = idx / m, i = k + 1 + (idx - (idx / m) * m);
+        double2* a = Am + (size_t)s * per_elems;
+        a[i * ld + k] = c_mul(a[i * ld + k], Inv[(size_t)s * r + k]);
+      }
+      __syncthreads();
+      const int nc = ld - k - 1, per = m * nc;
+      for (int idx = tid; idx < S * per; idx += kT) {
+        const int s = idx / per, e = idx - (idx / per) * per;
+        const int i = k + 1 + e / nc, j = k + 1 + (e - (e / nc) * nc);
+        double2* a = Am + (size_t)s * per_elems;
+        const double2 v = c_msub(a[i * ld + j], a[i * ld + k], a[k * ld + j]);
+        a[i * ld + j] = v;
+        if (e == 0) Inv[(size_t)s * r + k + 1] = c_recip(v, status);
+      }
+      __syncthreads();
+    }
+    for (int sj = warp; sj < S * 3; sj += kW) {
+      const int s = sj / 3, j = sj - (sj / 3) * 3;
+      double2* a = Am + (size_t)s * per_elems;
+      const double2* inv = Inv + (size_t)s * r;
+      double2* p = Pm + (size_t)s * r * 3;
+      for (int k = r - 1; k >= 0; --k) {
+        const double2 x = c_mul(a[k * ld + r + j], inv[k]);
+        for (int i = lane; i < k; i += 32) a[i * ld + r + j] = c_msub(a[i * ld + r + j], a[i * ld + k], x);
+        if (lane == 0) p[k * 3 + j] = x;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+
+    // ---- y = M p for M in {K(s_mu), C, K_in} (Hermitian: M[a][b] = conj(M[b][a]), read along a)
+    const int nmat = kin ? 3 : 2;
+    for (int idx = tid; idx < S * nmat * r * 3; idx += kT) {
+      const int s = idx / (nmat * r * 3);
+      int e = idx - s * nmat * r * 3;
+      const int mm = e / (r * 3);
+      e -= mm * r * 3;
+      const int a = e / 3, j = e - (e / 3) * 3;
+      const double2* p = Pm + (size_t)s * r * 3;
+      double2 y = make_double2(0.0, 0.0);
+      for (int b = 0; b < r; ++b) {
+        double2 g;
+        if (mm == 0) {
+          g = ob.K[b * r + a];
+          if (kin) {
+            const double2 q = ob.Kin[b * r + a];
+            g.x = fma(fmu, q.x, g.x);
+            g.y = fma(fmu, q.y, g.y);
+          }
+        } else {
+          g = (mm == 1 ? ob.C : ob.Kin)[b * r + a];
+        }
+        y = c_conj_mac(y, g, p[b * 3 + j]);
+      }
+      Am[(size_t)s * per_elems + (size_t)r * ld + (mm * r + a) * 3 + j] = y;
+    }
+    __syncthreads();
+
+    // ---- forward reductions: q 0..8 Re(p_i^H y^K_j), 9..17 Re(p_i^H y^C_j), 18..26 Re(b_i^H p_j),
+    // 27..35 Re(p_i^H y^Kin_j); and the adjoint source Z in the right-hand-side columns
+    for (int idx = tid; idx < S * 36; idx += kT) {
+      const int s = idx / 36, q = idx % 36;
+      if (q >= 27 && !kin) {
+        Red[(size_t)s * kRedV + q] = 0.0;
+        continue;
+      }
+      const int ij = q % 9, i = ij / 3, j = ij % 3;
+      const double2* p = Pm + (size_t)s * r * 3;
+      const double2* y = Am + (size_t)s * per_elems + (size_t)r * ld;
+      double acc = 0.0;
+      for (int a = 0; a < r; ++a) {
+        if (q < 18 || q >= 27) {
+          const int mm = q < 9 ? 0 : (q < 18 ? 1 : 2);
+          const double2 pa = p[a * 3 + i], ya = y[(mm * r + a) * 3 + j];
+          acc = fma(pa.x, ya.x, fma(pa.y, ya.y, acc));
+        } else {
+          const double2 b = ob.B[a * 3 + i], pa = p[a * 3 + j];
+          acc = fma(b.x, pa.x, fma(b.y, pa.y, acc));
+        }
+      }
+      Red[(size_t)s * kRedV + q] = acc;
+    }
+    for (int idx = tid; idx < S * r * 3; idx += kT) {
+      const int s = idx / (r * 3), e = idx - (idx / (r * 3)) * (r * 3);
+      const int a = e / 3, k = e - (e / 3) * 3;
+      const double2* y = Am + (size_t)s * per_elems + (size_t)r * ld;
+      const double* g = Gs + (size_t)s * 18;
+      const double cR = -0.25 * ob.alpha3, cI = 0.25 * ob.alpha3 * Ws[s];
+      double2 z = make_double2(0.0, 0.0);
+      for (int j = 0; j < 3; ++j) {
+        const double gr = cR * g[j * 3 + k], gi = cI * g[9 + j * 3 + k];
+        const double2 yk = y[(0 * r + a) * 3 + j], yc = y[(1 * r + a) * 3 + j], b = ob.B[a * 3 + j];
+        z.x = fma(gr, yk.x, fma(gi, yc.x + b.x, z.x));
+        z.y = fma(gr, yk.y, fma(gi, yc.y + b.y, z.y));
+      }
+      Am[(size_t)s * per_elems + a * ld + r + k] = z;
+    }
+    __syncthreads();
+
+    // ---- adjoint solves A^H Lambda = Z with A = L U: U^H w = Z (forward), L^H Lambda = w (backward)
+    for (int sk = warp; sk < S * 3; sk += kW) {
+      const int s = sk / 3, k3 = sk - (sk / 3) * 3;
+      double2* a = Am + (size_t)s * per_elems;
+      const double2* inv = Inv + (size_t)s * r;
+      for (int k = 0; k < r; ++k) {
+        const double2 iv = make_double2(inv[k].x, -inv[k].y);  // 1 / conj(u_kk)
+        const double2 x = c_mul(a[k * ld + r + k3], iv);
+        for (int i = k + 1 + lane; i < r; i += 32) a[i * ld + r + k3] = c_conj_msub(a[i * ld + r + k3], a[k * ld + i], x);
+        __syncwarp();
+        if (lane == 0) a[k * ld + r + k3] = x;
+        __syncwarp();
+      }
+      for (int k = r - 1; k >= 0; --k) {
+        const double2 x = a[k * ld + r + k3];
+        for (int i = lane; i < k; i += 32) a[i * ld + r + k3] = c_conj_msub(a[i * ld + r + k3], a[k * ld + i], x);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+
+    // ---- adjoint reductions: q 36: Im tr((B + C P)^H Lambda), q 37: Re tr((K_in P)^H Lambda)
+    for (int idx = tid; idx < S * 2; idx += kT) {
+      const int s = idx / 2, q = idx % 2;
+      const double2* a = Am + (size_t)s * per_elems;
+      const double2* y = a + (size_t)r * ld;
+      double acc = 0.0;
+      if (q == 0) {
+        for (int e = 0; e < r * 3; ++e) {
+          const int aa = e / 3, k = e % 3;
+          const double2 lam = a[aa * ld + r + k], yc = y[(1 * r + aa) * 3 + k], b = ob.B[aa * 3 + k];
+          const double2 v = make_double2(yc.x + b.x, yc.y + b.y);
+          acc += v.x * lam.y - v.y * lam.x;  // Im(conj(v) lam)
+        }
+      } else if (kin) {
+        for (int e = 0; e < r * 3; ++e) {
+          const int aa = e / 3, k = e % 3;
+          const double2 lam = a[aa * ld + r + k], yk = y[(2 * r + aa) * 3 + k];
+          acc += yk.x * lam.x + yk.y * lam.y;
+        }
+      }
+      Red[(size_t)s * kRedV + 36 + q] = acc;
+    }
+    __syncthreads();
+
+    // ---- outputs
+    for (int s = tid; s < S; s += kT) {
+      const double* red = Red + (size_t)s * kRedV;
+      const double* g = Gs + (size_t)s * 18;
+      const double w = Ws[s];
+      const size_t o = (size_t)task.obj * n_w + task.w0 + s;
+      double gI_dot_I = 0.0, gR_dot_HKin = 0.0;
+      for (int ij = 0; ij < 9; ++ij) {
+        const int i = ij / 3, j = ij % 3, ji = j * 3 + i;
+        const double Rv = -0.25 * ob.alpha3 * 0.5 * (red[ij] + red[ji]) + ob.N0[ij];
+        const double Iv = 0.25 * ob.alpha3 * w * (ob.c00[ij] + 0.5 * (red[9 + ij] + red[9 + ji]) + red[18 + ij] + red[18 + ji]);
+        if (Rout) Rout[o * 9 + ij] = Rv;
+        if (Iout) Iout[o * 9 + ij] = Iv;
+        // g holds gR + gR^T and gI + gI^T; the sums over all (i, j) count each pair twice
+        gI_dot_I += 0.5 * g[9 + ij] * Iv;
+        gR_dot_HKin += 0.5 * g[ij] * 0.5 * (red[27 + ij] + red[27 + ji]);
+      }
+      const double wr = w / ssig;  // the caller's omega
+      g_omega[o] = ssig * red[36] + gI_dot_I / wr;
+      g_mu_part[o] = (red[37] + 0.25 * ob.alpha3 * gR_dot_HKin) / (smu * smu);
+    }
+  }
+}
+
+// per object: g_ssigma = sum_w (omega_w / s_sigma) g_omega, g_smu = sum_w parts (fixed order)
+__global__ void vjp_object_sums_kernel(const double* __restrict__ omega, int omega_stride, const double* __restrict__ s_sigma,
+                                       const double* __restrict__ g_omega, const double* __restrict__ g_mu_part, int n_obj,
+                                       int n_w, double* __restrict__ g_ssigma, double* __restrict__ g_smu) {
+  const int o = blockIdx.x;
+  __shared__ double a[256], b[256];
+  double sa = 0.0, sb = 0.0;
+  const double ss = s_sigma ? s_sigma[o] : 1.0;
+  for (int k = threadIdx.x; k < n_w; k += blockDim.x) {
+    const size_t e = (size_t)o * n_w + k;
+    sa += omega[(size_t)o * omega_stride + k] / ss * g_omega[e];
+    sb += g_mu_part[e];
+  }
+  a[threadIdx.x] = sa;
+  b[threadIdx.x] = sb;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      a[threadIdx.x] += a[threadIdx.x + s];
+      b[threadIdx.x] += b[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (g_ssigma) g_ssigma[o] = a[0];
+    if (g_smu) g_smu[o] = b[0];
+  }
+}
+
+size_t vjp_bytes_per_system(int r, bool in_smem) {
+  const size_t am = in_smem ? (size_t)r * (r + 3) + 9 * (size_t)r : 0;
+  return 16 * (am + 3 * (size_t)r + (size_t)r) + 8 * (1 + 18 + kRedV);
+}
+
+}  // namespace
+}  // namespace mrom
+
+using namespace mrom;
+
+extern "C" mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega,
+                                      int32_t n_w, int32_t omega_stride, const double* s_sigma, const double* s_mu,
+                                      const double* gR, const double* gI, double* g_omega, double* g_ssigma,
+                                      double* g_smu, double* R, double* I) {
+  if (!h) return MROM_EINVAL;
+  if (!roms || n_obj < 1 || n_w < 1 || !omega || !gR || !gI || !g_omega)
+    return fail(h, MROM_EINVAL, "mrom_sweep_vjp: bad arguments");
+  if (omega_stride != 0 && omega_stride < n_w)
+    return fail(h, MROM_EINVAL, "mrom_sweep_vjp: omega_stride must be 0 or >= n_w");
+  for (int o = 0; o < n_obj; ++o) {
+    if (!roms[o] || roms[o]->ctx != h) return fail(h, MROM_EINVAL, "mrom_sweep_vjp: invalid object");
+    if ((s_mu || g_smu) && !roms[o]->has_kin)
+      return fail(h, MROM_EINVAL, "mrom_sweep_vjp: s_mu / g_smu need K_in on every object");
+  }
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_sweep_vjp: cudaSetDevice");
+  int per_sm = 0;
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
+  const size_t budget = std::min<size_t>(h->smem_optin, (size_t)per_sm / 4) - 2048;
+  std::vector<VjpObj> objs(n_obj);
+  std::vector<SweepTask> tasks;
+  std::vector<double> cost;
+  size_t smem = 0, ws_elems = 0;
+  for (int o = 0; o < n_obj; ++o) {
+    const mrom_rom* m = roms[o];
+    VjpObj& d = objs[o];
+    d.K = m->K;
+    d.Kin = m->has_kin ? m->Kin : nullptr;
+    d.C = m->C;
+    d.Me = m->Me;
+    d.B = m->B;
+    std::copy(m->c00, m->c00 + 9, d.c00);
+    std::copy(m->N0, m->N0 + 9, d.N0);
+    d.alpha3 = m->alpha * m->alpha * m->alpha;
+    d.r = m->r;
+    const size_t per_s = vjp_bytes_per_system(m->r, true);
+    const bool in_smem = per_s <= budget;
+    const size_t per = in_smem ? per_s : vjp_bytes_per_system(m->r, false);
+    const int S = in_smem ? std::min<int>(n_w, (int)(budget / per_s)) : 1;
+    if (!in_smem) ws_elems = std::max(ws_elems, (size_t)m->r * (m->r + 3) + 9 * (size_t)m->r);
+    const double r = m->r;
+    for (int w0 = 0; w0 < n_w; w0 += S) {
+      const int nw = std::min(S, n_w - w0);
+      tasks.push_back(SweepTask{o, w0, nw, in_smem ? 0 : 1});
+      cost.push_back((8.0 * r * r * r / 3.0 + 40.0 * r * r) * nw);
+      smem = std::max(smem, per * nw);
+    }
+  }
+  std::vector<int> order(tasks.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<SweepTask> sorted(tasks.size());
+  for (size_t k = 0; k < order.size(); ++k) sorted[k] = tasks[order[k]];
+  e = cudaFuncSetAttribute(sweep_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_vjp_kernel, kT, smem);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_sweep_vjp: configuration");
+  const int grid = std::min<int>((int)sorted.size(), h->num_sms * std::max(occ, 1));
+  const size_t ws_bytes = ws_elems * sizeof(double2) * grid;
+  const size_t bytes = ws_bytes + (size_t)n_obj * n_w * sizeof(double) + n_obj * sizeof(VjpObj) +
+                       sorted.size() * sizeof(SweepTask) + 16;
+  void* blk = nullptr;
+  e = cudaMallocAsync(&blk, bytes, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_sweep_vjp: allocation");
+  char* p = static_cast<char*>(blk);
+  auto* d_ws = ws_elems ? reinterpret_cast<double2*>(p) : nullptr;
+  p += ws_bytes;
+  auto* d_gmu = reinterpret_cast<double*>(p);
+  p += (size_t)n_obj * n_w * sizeof(double);
+  auto* d_objs = reinterpret_cast<VjpObj*>(p);
+  p += n_obj * sizeof(VjpObj);
+  auto* d_tasks = reinterpret_cast<SweepTask*>(p);
+  p += sorted.size() * sizeof(SweepTask);
+  auto* d_counter = reinterpret_cast<int*>(p);
+  e = cudaMemcpyAsync(d_objs, objs.data(), n_obj * sizeof(VjpObj), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_tasks, sorted.data(), sorted.size() * sizeof(SweepTask), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) {
+    sweep_vjp_kernel<<<grid, kT, smem, h->stream>>>(d_objs, d_tasks, (int)sorted.size(), d_counter, omega, omega_stride,
+                                                    s_sigma, s_mu, gR, gI, g_omega, d_gmu, R, I, h->d_status, n_w, d_ws,
+                                                    ws_elems);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && (g_ssigma || g_smu)) {
+    vjp_object_sums_kernel<<<n_obj, 256, 0, h->stream>>>(omega, omega_stride, s_sigma, g_omega, d_gmu, n_obj, n_w,
+                                                         g_ssigma, g_smu);
+    e = cudaGetLastError();
+    ++h->launches;
+  }
+  cudaFreeAsync(blk, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_sweep_vjp: launch");
+  ++h->launches;
+  return MROM_OK;
+}

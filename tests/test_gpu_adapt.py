@@ -1,0 +1,81 @@
+"""GPU parity of mrom_adapt (Algorithm 1) against the oracle's adaptive loop."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mrom():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_05590_gb300 import build
+    build.build()
+    import paper_2307_05590_gb300 as m
+    return m
+
+
+def test_adaptive_loop_matches_oracle(mrom):
+    """Same snapshot choices, Lambda history and final signature as oracle.adapt with a
+    shared basis and the diagonal inner product X = eps M + omega_min C."""
+    import torch
+    from oracle import adapt
+    from workloads import fit_problem, full_order_snapshots, log_omegas
+    from workloads.fit import Material
+    from gpu_common import oracle_model_sweep, rel_errors
+    p = fit_problem(12, (Material((0.25,) * 3, (0.75,) * 3, 5.96e7, 1.0),))
+    X = p.eps * p.M + 10.0 * p.C
+    wo = log_omegas(1e1, 1e5, 60)
+    w0 = log_omegas(1e1, 1e5, 3)
+    snap = lambda ws: full_order_snapshots(p, ws)
+    model, s_ref, h_ref, k_ref = adapt.adaptive_podp(p, snap, w0, wo, tol_sigma=1e-6, tol_delta=1e-30,
+                                                     n_star=2, max_k=4, shared=True, X_diag=X)
+    h = mrom.Handle(0)
+    fom = mrom.FullOrder.from_fit(p, X=X)
+    D0 = snap(w0)                                     # (3, N, 3)
+    cols = np.ascontiguousarray(np.transpose(D0, (2, 0, 1)).reshape(-1, p.N))
+    rom, hist, k, snaps = mrom.mrom_adapt(h, fom, w0, torch.as_tensor(cols, device="cuda"), snap,
+                                          torch.as_tensor(wo, device="cuda"), tol_sigma=1e-6, tol_delta=1e-30,
+                                          n_star=2, max_k=4)
+    assert k == k_ref
+    np.testing.assert_array_equal(snaps, s_ref)
+    # Lambda is compared where it is above the rounding floor of the Gram form (eps ||G|| ||w||^2,
+    # large here because X^-1 weighs the exterior by 1 / (eps M)); the last value (~1e-7) is at that
+    # floor: the oracle alone gives 6.5e-8 or 1.4e-7 depending on the BLAS it runs on.
+    assert np.allclose(hist[:2], h_ref[:2], rtol=1e-6, atol=0.0)
+    assert hist.size == len(h_ref) and hist[2] < 1e-3 * hist[0]
+    # final reduced model: same signature and certificate
+    wt = log_omegas(1e1, 1e5, 40) * 1.01
+    om = torch.as_tensor(wt, device="cuda")
+    R = torch.empty((1, wt.size, 3, 3), dtype=torch.float64, device="cuda")
+    I = torch.empty_like(R)
+    D = torch.empty_like(R)
+    mrom.mrom_sweep(h, [rom], om, wt.size, R, I, D)
+    h.synchronize()
+    errs = rel_errors(R[0].cpu().numpy(), I[0].cpu().numpy(), D[0].cpu().numpy(), *oracle_model_sweep(model, wt))
+    assert max(errs) <= 1e-9, errs
+
+
+def test_adaptive_loop_stops_on_tolerance_and_on_callback_error(mrom):
+    import torch
+    from workloads import fit_problem, full_order_snapshots, log_omegas
+    from workloads.fit import Material
+    p = fit_problem(10, (Material((0.3,) * 3, (0.7,) * 3, 5.96e7, 1.0),))
+    X = p.eps * p.M + 10.0 * p.C
+    fom = mrom.FullOrder.from_fit(p, X=X)
+    h = mrom.Handle(0)
+    w0 = log_omegas(1e1, 1e5, 3)
+    D0 = full_order_snapshots(p, w0)
+    cols = torch.as_tensor(np.ascontiguousarray(np.transpose(D0, (2, 0, 1)).reshape(-1, p.N)), device="cuda")
+    wo = torch.as_tensor(log_omegas(1e1, 1e5, 30), device="cuda")
+    # a huge tolerance stops after the first certificate evaluation, without new snapshots
+    rom, hist, k, snaps = mrom.mrom_adapt(h, fom, w0, cols, lambda ws: full_order_snapshots(p, ws), wo,
+                                          tol_delta=1e30, max_k=5)
+    assert k == 2 and hist.size == 1 and snaps.size == 3
+
+    def bad(ws):
+        raise RuntimeError("solver failed")
+
+    with pytest.raises(RuntimeError):
+        mrom.mrom_adapt(h, fom, w0, cols, bad, wo, tol_delta=1e-30, max_k=3)

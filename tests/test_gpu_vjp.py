@@ -1,0 +1,122 @@
+"""GPU parity of mrom_sweep_vjp (adjoint of Eqs. (17)-(19) in omega, s_sigma, s_mu) and of the
+torch.autograd wrapper, against the oracle's dense tangents and central finite differences."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mrom():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_05590_gb300 import build
+    build.build()
+    import paper_2307_05590_gb300 as m
+    return m
+
+
+def test_vjp_matches_oracle_tangents(mrom):
+    import torch
+    from oracle import grads
+    from workloads import log_omegas, reduced_object
+    h = mrom.Handle(0)
+    rs = [5, 24, 61, 96]
+    objs = [reduced_object(20230711, 500 + k, r) for k, r in enumerate(rs)]
+    roms = [mrom.ReducedObject.from_workload(h, o, with_cert=False) for o in objs]
+    n_w = 37
+    wo = log_omegas(1e1, 1e8, n_w)
+    ss = np.array([0.5, 1.0, 1.7, 2.0])
+    sm = np.array([1.0, 4.0, 17.0, 64.0])
+    rng = np.random.default_rng(3)
+    gR = rng.standard_normal((4, n_w, 3, 3))
+    gI = rng.standard_normal((4, n_w, 3, 3))
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    g_w = torch.empty((4, n_w), dtype=torch.float64, device="cuda")
+    g_s = torch.empty(4, dtype=torch.float64, device="cuda")
+    g_m = torch.empty(4, dtype=torch.float64, device="cuda")
+    R = torch.empty((4, n_w, 3, 3), dtype=torch.float64, device="cuda")
+    I = torch.empty_like(R)
+    mrom.mrom_sweep_vjp(h, roms, t(wo), n_w, t(gR), t(gI), g_w, g_ssigma=g_s, g_smu=g_m, s_sigma=t(ss), s_mu=t(sm),
+                        R=R, I=I)
+    h.synchronize()
+    for k, obj in enumerate(objs):
+        Rr, Ir = grads.forward(obj, wo, ss[k], sm[k])
+        assert np.abs(R[k].cpu().numpy() - Rr).max() <= 1e-10 * np.abs(Rr).max()
+        assert np.abs(I[k].cpu().numpy() - Ir).max() <= 1e-9 * np.abs(Ir).max()
+        gw, gs, gm = grads.vjp(obj, wo, gR[k], gI[k], ss[k], sm[k])
+        dR, dI = grads.tangents(obj, wo, ss[k], sm[k])
+        # scale of each contribution: sum |g| |d(R, I)/dtheta|
+        sc = (np.abs(dR) * np.abs(gR[k])[None]).sum(axis=(2, 3)) + (np.abs(dI) * np.abs(gI[k])[None]).sum(axis=(2, 3))
+        assert np.all(np.abs(g_w[k].cpu().numpy() - gw) <= 1e-8 * sc[0] + 1e-300), (obj.r,)
+        assert abs(g_s[k].item() - gs) <= 1e-8 * sc[1].sum()
+        assert abs(g_m[k].item() - gm) <= 1e-8 * sc[2].sum()
+
+
+def test_autograd_matches_finite_differences(mrom):
+    import torch
+    from workloads import log_omegas, reduced_object
+    h = mrom.Handle(0)
+    objs = [reduced_object(20230711, 700 + k, r) for k, r in enumerate([12, 40])]
+    roms = [mrom.ReducedObject.from_workload(h, o, with_cert=False) for o in objs]
+    wo = torch.as_tensor(log_omegas(1e2, 1e6, 9), device="cuda").requires_grad_(True)
+    ss = torch.tensor([1.3, 0.8], dtype=torch.float64, device="cuda", requires_grad=True)
+    sm = torch.tensor([2.0, 9.0], dtype=torch.float64, device="cuda", requires_grad=True)
+    wR = torch.randn((2, 9, 3, 3), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    wI = torch.randn((2, 9, 3, 3), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+
+    def loss(w, s1, s2):
+        R, I = mrom.signature(h, roms, w, s1, s2)
+        return (wR * R).sum() + (wI * I).sum()
+
+    L = loss(wo, ss, sm)
+    L.backward()
+
+    def central(x, k, rel):
+        hstep = rel * x[k].item()
+        x[k] += hstep
+        Lp = loss(wo, ss, sm).item()
+        x[k] -= 2 * hstep
+        Lm = loss(wo, ss, sm).item()
+        x[k] += hstep
+        return (Lp - Lm) / (2 * hstep)
+
+    # L is a sum of +-terms of size ~1e6 whose rounding noise (~kappa(A) eps) limits a difference
+    # quotient: h = 1e-4 (truncation ~1e-8) is checked tightly, h = 1e-6 (the configured step) at
+    # the size of its noise.
+    with torch.no_grad():
+        for x, g in ((ss, ss.grad), (sm, sm.grad), (wo, wo.grad)):
+            for k in ([0, 1] if x is not wo else [2, 6]):
+                assert g[k].item() == pytest.approx(central(x, k, 1e-4), rel=1e-6)
+                assert g[k].item() == pytest.approx(central(x, k, 1e-6), rel=1e-4)
+
+
+def test_least_squares_fit_of_material_scales(mrom):
+    """Fit (s_sigma, s_mu) of an object to a target signature made with scales drawn from the
+    held-out seed 20230712, using gradients from the adjoint kernel."""
+    import torch
+    from scipy.optimize import minimize
+    from workloads import log_omegas, reduced_object
+    h = mrom.Handle(0)
+    obj = reduced_object(20230711, 900, 30)
+    rom = mrom.ReducedObject.from_workload(h, obj, with_cert=False)
+    rng = np.random.default_rng(20230712)
+    true_s = np.array([rng.uniform(0.5, 2.0), np.exp(rng.uniform(0.0, np.log(64.0)))])
+    wo = torch.as_tensor(log_omegas(1e1, 1e8, 80), device="cuda")
+    t1 = lambda v: torch.tensor([v], dtype=torch.float64, device="cuda")
+    with torch.no_grad():
+        Rt, It = mrom.signature(h, [rom], wo, t1(true_s[0]), t1(true_s[1]))
+        sR, sI = Rt.abs().amax(dim=(2, 3), keepdim=True), It.abs().amax(dim=(2, 3), keepdim=True)
+
+    def fun(x):
+        a = torch.tensor([np.exp(x[0])], dtype=torch.float64, device="cuda", requires_grad=True)
+        b = torch.tensor([np.exp(x[1])], dtype=torch.float64, device="cuda", requires_grad=True)
+        R, I = mrom.signature(h, [rom], wo, a, b)
+        L = (((R - Rt) / sR) ** 2).sum() + (((I - It) / sI) ** 2).sum()
+        L.backward()
+        return L.item(), np.array([a.grad.item() * a.item(), b.grad.item() * b.item()])
+
+    res = minimize(fun, np.zeros(2), jac=True, method="L-BFGS-B", options={"maxiter": 200, "gtol": 1e-12, "ftol": 1e-16})
+    fit = np.exp(res.x)
+    assert np.allclose(fit, true_s, rtol=1e-5), (fit, true_s)

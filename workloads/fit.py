@@ -206,12 +206,14 @@ def _assign_materials(n: int, materials: Sequence[Material]):
 
 def fit_problem(n: int, materials: Sequence[Material] = CUBE_C1, *, alpha: float = 1.0,
                 eps: float = 1e-6, eps_static: float = 1e-10,
-                static_solver: Callable | None = None) -> FitProblem:
+                static_solver: Callable | None = None, static: bool = True) -> FitProblem:
     """Assemble the FIT problem on an n^3 grid.
 
     eps is the regularisation of Eq. (7b) (mass on Omega minus B); eps_static
     regularises the static theta^(0) problem with mass on all of Omega.  The
-    static solve is skipped (o~ = 0, N0 = 0) when mu_r == 1 everywhere.
+    static solve is skipped (o~ = 0, N0 = 0) when mu_r == 1 everywhere, or when
+    static=False (for grids too large for a sparse direct solve; the operator
+    shapes are unchanged).
     """
     if n < 2:
         raise ValueError("n must be >= 2")
@@ -260,7 +262,7 @@ def fit_problem(n: int, materials: Sequence[Material] = CUBE_C1, *, alpha: float
     o_tilde = np.zeros((3, N))
     N0 = np.zeros((3, 3))
     magnetic = np.any(mu != 1.0)
-    if magnetic:
+    if magnetic and static:
         Kia = Kall[interior]
         rhs = -(Kia @ x_all.T)
         A0 = (K + sp.diags(eps_static * Mo_all[interior])).tocsc()
