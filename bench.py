@@ -141,6 +141,42 @@ def blas_threads() -> int:
         return os.cpu_count()
 
 
+def project_flops(n: int, nnz: int, m: int, r: int, cert: bool = True) -> float:
+    """Algorithmic FP64 flops of mrom_project: snapshot Gram (Hermitian half), basis
+    apply, SpMM, K_r, C_r, eps M_r (Hermitian half), b, c00 and the certificate Gram."""
+    ng = 2 * r + 3
+    fl = 4.0 * n * m * m + 8.0 * n * m * r + 4.0 * nnz * r + 8.0 * n * r * r + 2 * 4.0 * n * r * r
+    fl += 8.0 * n * r * 3 + 4.0 * n * 9
+    if cert:
+        fl += 4.0 * n * ng * ng
+    return fl
+
+
+def measure_projection(m, h, n_grid: int = 96, n_s: int = 32):
+    """mrom_project on the 96^3 FIT grid (N = 2.6M) with 3 x 32 synthetic snapshot columns."""
+    import torch
+    from workloads import CUBE_C2, fit_problem, synthetic_snapshot_matrix
+    p = fit_problem(n_grid, CUBE_C2, static=False)
+    D = synthetic_snapshot_matrix(p.N, n_s, 20230711)
+    Dd = torch.from_numpy(np.ascontiguousarray(D.transpose(0, 2, 1).reshape(3 * n_s, p.N))).to("cuda")
+    del D
+    fom = m.FullOrder.from_fit(p, X=p.eps * p.M + 10.0 * p.C)
+    rom, sig, r = m.mrom_project(h, fom, Dd, tol_sigma=1e-6)  # warm-up
+    rom.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rom, sig, r = m.mrom_project(h, fom, Dd, tol_sigma=1e-6)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rom.close()
+    fl = project_flops(p.N, p.K.nnz, 3 * n_s, r)
+    return {"workload": f"mrom_project: 96^3 FIT grid (N = {p.N}, {p.K.nnz} nnz), 3 x {n_s} snapshot columns, "
+                        f"TOL_Sigma 1e-6 -> r = {r}, certificate Gram with diagonal X",
+            "seconds": dt, "r": r, "flops": fl, "achieved_tflops": fl / dt / 1e12,
+            "bound": "alu", "fp64_frac": fl / dt / 1e12 / (SM_COUNT_NOMINAL * DFMA_PER_CLK_PER_SM * 2 * 2.07e9 / 1e12),
+            "hbm_gb_moved_min": (3 * n_s * p.N * 16 * 2 + p.N * r * 16 * 4 + p.K.nnz * 12) / 1e9}
+
+
 def config(args):
     return {"workload": f"batched dictionary sweep: {args.n_obj} reduced objects (r ~ U{{8..96}}, shared basis) "
                         f"x {args.n_w} log-spaced omega in [1e1, 1e8] rad/s; R, I and certificate Delta",
@@ -188,6 +224,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=20)
     ap.add_argument("--ref-sample", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mixed", action=argparse.BooleanOptionalAction, default=True)
+    ap.add_argument("--projection", action=argparse.BooleanOptionalAction, default=True)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -257,6 +295,30 @@ def main():
     ms_per_step = float(t_step.item())
     evals_step = args.n_obj * args.n_w * world
     value = evals_step / (ms_per_step * 1e-3)
+
+    # ---- mixed precision (complex64 elimination + one float64 refinement step), same dictionary
+    mixed = None
+    if args.mixed:
+        Rm, Im, Dm = torch.empty_like(R), torch.empty_like(R), torch.empty_like(R)
+        for _ in range(2):
+            m.mrom_sweep_mixed(h, roms, om, args.n_w, Rm, Im, Dm, n_refine=1)
+        h.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            m.mrom_sweep_mixed(h, roms, om, args.n_w, Rm, Im, Dm, n_refine=1)
+        e1.record(stream)
+        h.synchronize()
+        ms_mixed = e0.elapsed_time(e1) / args.steps
+        # error against the float64 sweep, normwise per tensor (R: max|R|, I and Delta: max of both)
+        def rel(a, b):
+            sc = torch.clamp(b.abs().amax(dim=(2, 3), keepdim=True), min=1e-300)
+            return float(((a - b).abs() / sc).max().item())
+        mixed = {"value": args.n_obj * args.n_w / (ms_mixed * 1e-3), "unit": UNIT, "ms_per_step": ms_mixed,
+                 "n_refine": 1, "max_rel_err_vs_fp64": {"R": rel(Rm, R), "I": rel(Im, I), "Delta": rel(Dm, D)}}
+        del Rm, Im, Dm
+
+    proj = measure_projection(m, h) if args.projection else None
 
     # ---- end to end through the public API from pinned host buffers
     e2e = None
@@ -334,6 +396,7 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "wall_s_timed": wall, "per_launch_ms": per_launch_ms, "sweep_config": sweep_cfg,
+            "mixed_precision": mixed, "projection": proj,
         }
         print(json.dumps(line), flush=True)
     plan.close()

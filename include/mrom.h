@@ -252,6 +252,18 @@ mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj,
                            int32_t omega_stride, const double* s_sigma, const double* s_mu, const double* gR,
                            const double* gI, double* g_omega, double* g_ssigma, double* g_smu, double* R, double* I);
 
+/* Mixed-precision sweep: the same outputs as mrom_sweep (no s_sigma, s_mu), with
+ * the reduced systems eliminated in complex64 and refined n_refine times
+ * (0..8) in float64: res = i omega B - (K + Me - i omega C) X in float64,
+ * correction through the complex64 factors, X += d.  The quadratic forms of
+ * Eqs. (18)-(19) and the certificate stay float64.  Each refinement step
+ * multiplies the solution error by about kappa(A) * 6e-8; for the dictionary
+ * spectra one step gives about 1e-7 relative and two give float64 accuracy.
+ * Objects up to r = 96 (MROM_ENOTSUP above).  Asynchronous; allocates its task
+ * tables stream-ordered. */
+mrom_status mrom_sweep_mixed(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega, int32_t n_w,
+                             int32_t omega_stride, int32_t n_refine, double* R, double* I, double* Delta);
+
 /* Certificate only: Delta as in mrom_sweep, without writing R and I. */
 mrom_status mrom_certificate(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega,
                              int32_t n_w, int32_t omega_stride, double* Delta);

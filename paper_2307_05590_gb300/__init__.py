@@ -23,6 +23,7 @@ __all__ = [
     "mrom_rom_from_reduced", "mrom_rom_free", "mrom_rom_rank", "mrom_sweep", "mrom_certificate",
     "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune", "mrom_sweep_noalloc",
     "FullOrder", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "MromSweep", "signature",
+    "mrom_sweep_mixed",
 ]
 
 
@@ -450,3 +451,10 @@ def signature(handle: Handle, objs, omega, s_sigma=None, s_mu=None):
     n = len(objs)
     ss = s_sigma if s_sigma is not None else torch.ones(n, dtype=torch.float64, device=dev)
     return MromSweep().apply(omega, ss, s_mu, handle, list(objs))
+
+
+def mrom_sweep_mixed(h: Handle, objs, omega, n_w: int, R, I, Delta=None, *, n_refine: int = 1,
+                     omega_stride: int = 0) -> None:
+    """mrom_sweep with complex64 elimination and n_refine float64 refinement steps."""
+    _abi.check(lib().mrom_sweep_mixed(h.ptr, _rom_array(objs), len(objs), _ptr(omega), int(n_w),
+                                      int(omega_stride), int(n_refine), _ptr(R), _ptr(I), _ptr(Delta)), h.ptr)

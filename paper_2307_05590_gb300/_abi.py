@@ -16,7 +16,7 @@ EXPORTS = [
     "mrom_create", "mrom_destroy", "mrom_set_stream", "mrom_synchronize", "mrom_last_error",
     "mrom_launch_count", "mrom_rom_from_reduced", "mrom_rom_rank", "mrom_rom_free", "mrom_sweep",
     "mrom_certificate", "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune",
-    "mrom_sweep_noalloc", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp",
+    "mrom_sweep_noalloc", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "mrom_sweep_mixed",
 ]
 
 
@@ -98,6 +98,7 @@ def _declare(L):
                                         ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(i32)]),
         "mrom_rom_get": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp]),
+        "mrom_sweep_mixed": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, dp, i32, i32, i32, dp, dp, dp]),
         "mrom_sweep_vjp": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, dp, i32, i32, dp, dp, dp, dp, dp, dp, dp, dp,
                                           dp]),
         "mrom_adapt": (ctypes.c_int, [vp, ctypes.POINTER(mrom_fom), ctypes.POINTER(ctypes.c_double), i32, vp,
