@@ -93,6 +93,11 @@ int64_t mrom_launch_count(mrom_handle h);
  *   N0  (9 float64 or NULL): added to R (Eq. (6a)).
  *   alpha (object size), alpha_lb (stability lower bound of Lemma 4.2),
  *   vol_B (|B|, so that |B_alpha| = alpha^3 vol_B).
+ *   r_dirs: all 0 for one basis shared by the three directions, or the sizes
+ *   r_1 + r_2 + r_3 = r of one basis per direction (Sect. 4.1, the paper's
+ *   PODP): the basis is W = [U_1 U_2 U_3], K, C, Me and G are the full
+ *   W-space matrices (K_ij = U_i^H K U_j, Eq. (18)), column i of B is W^H C o_i,
+ *   and the sweep solves direction i with the diagonal block only (Eq. (17)).
  * Pointers may be host or device memory; they are copied before return.
  * Returns MROM_EINVAL for r < 1, r > MROM_MAX_R, a null required pointer or
  * a non-finite scalar. */
@@ -110,6 +115,7 @@ typedef struct {
   double alpha;
   double alpha_lb;
   double vol_B;
+  int32_t r_dirs[3];
 } mrom_reduced_desc;
 
 mrom_status mrom_rom_from_reduced(mrom_handle h, const mrom_reduced_desc* desc, mrom_rom_t* out);
@@ -202,6 +208,18 @@ mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const double* omega0,
                        mrom_snapshot_cb cb, void* user, const double* omega_out, int32_t n_out,
                        const mrom_adapt_opts* opts, mrom_rom_t* out, double* lambda_hist, int32_t* k_done,
                        double* omega_snap_out, int32_t* ns_out);
+
+/* As mrom_project with one basis per direction, the paper's PODP (Sect. 4.1:
+ * a TSVD of each D_i).  D holds 3 * n_s columns: n_s snapshots of direction 1,
+ * then direction 2, then direction 3 (column c at D + c * ldd).  Each direction
+ * is truncated with tol_sigma and r_max; r_1 + r_2 + r_3 <= MROM_MAX_R.  Or
+ * basis_in (device, n x (r_1 + r_2 + r_3) complex128 row-major, columns
+ * [U_1 U_2 U_3]) with r_dirs_in (host, 3).  sigma_out (host, 3 n_s, or NULL):
+ * singular values per direction; r_dirs_out (host, 3, or NULL): the ranks.
+ * The object's cross blocks give R_ij, I_ij of Eqs. (18)-(19) for i != j. */
+mrom_status mrom_project_dirs(mrom_handle h, const mrom_fom* fom, const void* D, int64_t ldd, int32_t n_s,
+                              double tol_sigma, int32_t r_max, const void* basis_in, const int32_t* r_dirs_in,
+                              mrom_rom_t* out, double* sigma_out, int32_t* r_dirs_out);
 
 /* Copy an object's reduced data to caller buffers (host or device; any may be
  * NULL): K, C, Me (r x r complex128; zeros when the object has no Me), B

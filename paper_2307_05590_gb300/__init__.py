@@ -23,7 +23,7 @@ __all__ = [
     "mrom_rom_from_reduced", "mrom_rom_free", "mrom_rom_rank", "mrom_sweep", "mrom_certificate",
     "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune", "mrom_sweep_noalloc",
     "FullOrder", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "MromSweep", "signature",
-    "mrom_sweep_mixed",
+    "mrom_sweep_mixed", "mrom_project_dirs",
 ]
 
 
@@ -77,7 +77,7 @@ class ReducedObject:
     """An mrom_rom_t created from reduced data (mrom_rom_from_reduced)."""
 
     def __init__(self, handle: Handle, r: int, K, C, B, c00, *, G=None, K_in=None, Me=None, N0=None,
-                 alpha: float = 1.0, alpha_lb: float = 1.0 / np.sqrt(2.0), vol_B: float = 1.0):
+                 alpha: float = 1.0, alpha_lb: float = 1.0 / np.sqrt(2.0), vol_B: float = 1.0, r_dirs=(0, 0, 0)):
         keep = [_as_c128(K), _as_c128(C), _as_c128(B), _as_f64(c00), _as_c128(G), _as_c128(K_in),
                 _as_c128(Me), _as_f64(N0)]
         d = mrom_reduced_desc()
@@ -87,6 +87,8 @@ class ReducedObject:
         d.G, d.K_in, d.Me = _ptr(keep[4]), _ptr(keep[5]), _ptr(keep[6])
         d.N0 = ctypes.cast(_ptr(keep[7]), ctypes.POINTER(ctypes.c_double)) if N0 is not None else None
         d.alpha, d.alpha_lb, d.vol_B = float(alpha), float(alpha_lb), float(vol_B)
+        for i in range(3):
+            d.r_dirs[i] = int(r_dirs[i])
         self._rom = ctypes.c_void_p()
         self.handle = handle
         _abi.check(lib().mrom_rom_from_reduced(handle.ptr, ctypes.byref(d), ctypes.byref(self._rom)),
@@ -458,3 +460,26 @@ def mrom_sweep_mixed(h: Handle, objs, omega, n_w: int, R, I, Delta=None, *, n_re
     """mrom_sweep with complex64 elimination and n_refine float64 refinement steps."""
     _abi.check(lib().mrom_sweep_mixed(h.ptr, _rom_array(objs), len(objs), _ptr(omega), int(n_w),
                                       int(omega_stride), int(n_refine), _ptr(R), _ptr(I), _ptr(Delta)), h.ptr)
+
+
+def mrom_project_dirs(h: Handle, fom: FullOrder, D=None, *, n_s: int = 0, tol_sigma: float = 1e-6, r_max: int = 0,
+                      basis=None, r_dirs=None):
+    """One basis per direction (the paper's PODP): D is device (3 * n_s, n) complex128 with the
+    snapshots of direction 1, then 2, then 3; or basis (device (n, r1+r2+r3)) with r_dirs.
+    Returns (ReducedObject, singular values (3, n_s) or None, (r1, r2, r3))."""
+    rom = ctypes.c_void_p()
+    rd_out = (ctypes.c_int32 * 3)()
+    if basis is not None:
+        rd_in = (ctypes.c_int32 * 3)(*[int(x) for x in r_dirs])
+        _abi.check(lib().mrom_project_dirs(h.ptr, ctypes.byref(fom.desc), None, 0, 0, 0.0, 0, _ptr(basis), rd_in,
+                                           ctypes.byref(rom), None, rd_out), h.ptr)
+        sig = None
+    else:
+        n_s = int(D.shape[0]) // 3
+        sig = np.zeros(3 * n_s)
+        _abi.check(lib().mrom_project_dirs(h.ptr, ctypes.byref(fom.desc), _ptr(D), int(D.shape[1]), n_s,
+                                           float(tol_sigma), int(r_max), None, None, ctypes.byref(rom),
+                                           sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), rd_out), h.ptr)
+        sig = sig.reshape(3, n_s)
+    rd = tuple(int(x) for x in rd_out)
+    return ReducedObject._wrap(h, rom, sum(rd), fom.desc.X_diag is not None), sig, rd

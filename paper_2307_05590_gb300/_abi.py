@@ -17,6 +17,7 @@ EXPORTS = [
     "mrom_launch_count", "mrom_rom_from_reduced", "mrom_rom_rank", "mrom_rom_free", "mrom_sweep",
     "mrom_certificate", "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune",
     "mrom_sweep_noalloc", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "mrom_sweep_mixed",
+    "mrom_project_dirs",
 ]
 
 
@@ -72,6 +73,7 @@ class mrom_reduced_desc(ctypes.Structure):
         ("alpha", ctypes.c_double),
         ("alpha_lb", ctypes.c_double),
         ("vol_B", ctypes.c_double),
+        ("r_dirs", ctypes.c_int32 * 3),
     ]
 
 
@@ -97,6 +99,9 @@ def _declare(L):
         "mrom_project": (ctypes.c_int, [vp, ctypes.POINTER(mrom_fom), vp, i64, i32, ctypes.c_double, i32, vp, i32,
                                         ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(i32)]),
+        "mrom_project_dirs": (ctypes.c_int, [vp, ctypes.POINTER(mrom_fom), vp, i64, i32, ctypes.c_double, i32, vp,
+                                             ctypes.POINTER(i32), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(i32)]),
         "mrom_rom_get": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp]),
         "mrom_sweep_mixed": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, dp, i32, i32, i32, dp, dp, dp]),
         "mrom_sweep_vjp": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, dp, i32, i32, dp, dp, dp, dp, dp, dp, dp, dp,

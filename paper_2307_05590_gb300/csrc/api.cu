@@ -139,6 +139,13 @@ RomDev rom_record(const mrom_rom* m) {
   d.cert_scale = m->has_cert ? d.alpha3 / (4.0 * m->alpha_lb) : 0.0;
   d.r = m->r;
   d.has_cert = m->has_cert ? 1 : 0;
+  d.per_dir = (m->r_dirs[0] + m->r_dirs[1] + m->r_dirs[2]) > 0 ? 1 : 0;
+  int off = 0;
+  for (int i = 0; i < 3; ++i) {
+    d.blk_lo[i] = d.per_dir ? off : 0;
+    d.blk_hi[i] = d.per_dir ? off + m->r_dirs[i] : m->r;
+    off += m->r_dirs[i];
+  }
   return d;
 }
 
@@ -161,23 +168,7 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
   size_t smem = 0, ws_elems = 0;
   for (int o = 0; o < n_obj; ++o) {
     const mrom_rom* m = roms[o];
-    RomDev& d = objs[o];
-    d.K = m->K;
-    d.C = m->C;
-    d.Me = m->Me;
-    d.B = m->B;
-    d.GKK = m->GKK;
-    d.GCC = m->GCC;
-    d.GSk = m->GSk;
-    d.gsK = m->gsK;
-    d.gsC = m->gsC;
-    std::memcpy(d.gss, m->gss, sizeof(d.gss));
-    std::memcpy(d.c00, m->c00, sizeof(d.c00));
-    std::memcpy(d.N0, m->N0, sizeof(d.N0));
-    d.alpha3 = m->alpha * m->alpha * m->alpha;
-    d.cert_scale = m->has_cert ? d.alpha3 / (4.0 * m->alpha_lb) : 0.0;
-    d.r = m->r;
-    d.has_cert = m->has_cert ? 1 : 0;
+    objs[o] = rom_record(m);
     all_cert = all_cert && m->has_cert;
     // matrices in shared memory when at least one system fits the budget, otherwise
     // in the CTA's slice of an L2-resident global workspace (one system per task)

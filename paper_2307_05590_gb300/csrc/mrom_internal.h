@@ -36,6 +36,12 @@ struct RomDev {
   double cert_scale;    // alpha^3 / (4 alpha_lb)
   int r;
   int has_cert;
+  // Direction blocks of the basis W = [U_1 U_2 U_3] (Sect. 4.1: one TSVD per direction):
+  // direction i's solution lives in rows [blk_lo[i], blk_hi[i]) and the reduced system uses
+  // only the diagonal block A_ii.  A basis shared by the directions has [0, r) for all i.
+  int per_dir;
+  int blk_lo[3];
+  int blk_hi[3];
 };
 
 // One unit of work: S consecutive frequencies of one object.
@@ -76,6 +82,7 @@ struct mrom_rom {
   double N0[9] = {0};
   bool has_cert = false;
   bool has_kin = false;
+  int r_dirs[3] = {0, 0, 0};  // per-direction basis sizes (all 0: one shared basis)
 };
 
 struct mrom_plan_s {

@@ -416,107 +416,86 @@ cudaError_t tall_gram(mrom_ctx* h, const double2* A, int64_t rsA, int64_t csA, i
 
 using namespace mrom;
 
-extern "C" mrom_status mrom_project(mrom_handle h, const mrom_fom* fom, const void* D, int64_t ldd, int32_t n_cols,
-                                    double tol_sigma, int32_t r_max, const void* basis_in, int32_t r_in,
-                                    mrom_rom_t* out, double* sigma_out, int32_t* r_out) {
-  if (!h) return MROM_EINVAL;
-  if (!fom || !out) return fail(h, MROM_EINVAL, "mrom_project: null argument");
-  *out = nullptr;
-  const int64_t n = fom->n;
-  if (n < 1 || !fom->K_rowptr || !fom->K_col || !fom->K_val || !fom->C_diag || !fom->o)
-    return fail(h, MROM_EINVAL, "mrom_project: n, K, C_diag and o are required");
-  if (!(fom->alpha > 0) || !std::isfinite(fom->alpha) || !std::isfinite(fom->eps))
-    return fail(h, MROM_EINVAL, "mrom_project: alpha must be finite and > 0, eps finite");
-  if (fom->X_diag && !(fom->alpha_lb > 0))
-    return fail(h, MROM_EINVAL, "mrom_project: a certificate needs alpha_lb > 0");
-  if (!basis_in) {
-    if (!D || n_cols < 1 || n_cols > MROM_MAX_SNAPSHOTS || ldd < n)
-      return fail(h, MROM_EINVAL, "mrom_project: D needs 1..MROM_MAX_SNAPSHOTS columns and ldd >= n");
-    if (!(tol_sigma >= 0.0) || !std::isfinite(tol_sigma))
-      return fail(h, MROM_EINVAL, "mrom_project: tol_sigma must be finite and >= 0");
-  } else if (r_in < 1 || r_in > MROM_MAX_R) {
-    return fail(h, MROM_EINVAL, "mrom_project: r_in must be in [1, MROM_MAX_R]");
+namespace mrom {
+namespace {
+
+// Snapshot Gram, Jacobi eigensolver and truncation for the m columns of D (column c at
+// D + c * ldd): returns the rank r, the singular values (host) and W = V_r diag(1/s_r)
+// (host, m x r, row-major) such that U = D W.
+mrom_status gram_eig(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, int m, double tol_sigma, int r_cap,
+                     int* r_out, std::vector<double>& s, std::vector<double2>& wh) {
+  cudaStream_t st = h->stream;
+  DevBuf g, vbuf, lam;
+  cudaError_t e = cudaMalloc(&g.p, (size_t)m * m * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&vbuf.p, (size_t)m * m * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&lam.p, (size_t)m * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: allocation");
+  e = tall_gram(h, Dp, 1, ldd, m, Dp, 1, ldd, m, nullptr, 0, n, true, static_cast<double2*>(g.p), m);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: snapshot Gram");
+  jacobi_eig_kernel<<<1, 1024, 0, st>>>(static_cast<double2*>(g.p), static_cast<double2*>(vbuf.p), m, 60, 1e-15,
+                                        static_cast<double*>(lam.p), h->d_status);
+  ++h->launches;
+  std::vector<double> lh(m);
+  std::vector<double2> vh((size_t)m * m);
+  e = cudaMemcpyAsync(lh.data(), lam.p, m * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(vh.data(), vbuf.p, vh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: eigensolver");
+  int stw = 0;
+  cudaMemcpy(&stw, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (stw & kStatusTimeout) {
+    cudaMemset(h->d_status, 0, sizeof(int));
+    return fail(h, MROM_ENOTCONVERGED, "mrom_project: Jacobi eigensolver did not converge");
   }
-  cudaError_t e = cudaSetDevice(h->device);
-  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: cudaSetDevice");
+  std::vector<int> order(m);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lh[a] > lh[b]; });
+  s.assign(m, 0.0);
+  for (int k = 0; k < m; ++k) s[k] = std::sqrt(std::max(lh[order[k]], 0.0));
+  // truncation rule (Eq. (15) reading): keep s_k / s_1 >= TOL_Sigma, at most r_cap
+  int r = 0;
+  for (int k = 0; k < m; ++k)
+    if (s[0] > 0 && s[k] > 0 && s[k] / s[0] >= tol_sigma) r = k + 1;
+  r = std::min(r, r_cap);
+  if (r < 1) return fail(h, MROM_EINVAL, "mrom_project: snapshots have no nonzero singular value");
+  wh.assign((size_t)m * r, make_double2(0.0, 0.0));
+  for (int c = 0; c < m; ++c)
+    for (int k = 0; k < r; ++k) {
+      const double2 v = vh[(size_t)c * m + order[k]];
+      wh[(size_t)c * r + k] = make_double2(v.x / s[k], v.y / s[k]);
+    }
+  *r_out = r;
+  return MROM_OK;
+}
+
+// U[:, off : off + r] (row-major, leading dimension ldu) = D W
+mrom_status apply_basis(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, int m, const std::vector<double2>& wh,
+                        int r, double2* U, int ldu) {
+  DevBuf wbuf;
+  cudaError_t e = cudaMalloc(&wbuf.p, wh.size() * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(wbuf.p, wh.data(), wh.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream);
+  const size_t smem = ((size_t)kAR * (m + 1) + (size_t)m * kAC) * sizeof(double2);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply_basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: basis");
+  apply_basis_kernel<<<(unsigned)((n + kAR - 1) / kAR), 256, smem, h->stream>>>(Dp, 1, ldd, m, n,
+                                                                                 static_cast<double2*>(wbuf.p), r, U, ldu);
+  ++h->launches;
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: basis");
+  return MROM_OK;
+}
+
+// Galerkin projection onto the basis U (n x Rt row-major; r_dirs = per-direction column
+// blocks, or all zero for one shared basis) and creation of the reduced object.
+mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, int r, const int32_t* r_dirs,
+                          mrom_rom_t* out) {
+  const int64_t n = fom->n;
   cudaStream_t st = h->stream;
   auto launch_grid = [](int64_t work) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(65535 * 4, (work + 255) / 256)); };
-
-  // ---- basis U (row-major n x r)
-  DevBuf Ubuf;
-  const double2* U = nullptr;
-  int r = 0;
-  if (basis_in) {
-    U = static_cast<const double2*>(basis_in);
-    r = r_in;
-  } else {
-    const int m = n_cols;
-    const auto* Dp = static_cast<const double2*>(D);
-    DevBuf g, vbuf, lam;
-    e = cudaMalloc(&g.p, (size_t)m * m * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMalloc(&vbuf.p, (size_t)m * m * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMalloc(&lam.p, (size_t)m * sizeof(double));
-    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: allocation");
-    // D(row, c) = D[row + c * ldd]
-    e = tall_gram(h, Dp, 1, ldd, m, Dp, 1, ldd, m, nullptr, 0, n, true, static_cast<double2*>(g.p), m);
-    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: snapshot Gram");
-    jacobi_eig_kernel<<<1, 1024, 0, st>>>(static_cast<double2*>(g.p), static_cast<double2*>(vbuf.p), m, 60, 1e-15,
-                                          static_cast<double*>(lam.p), h->d_status);
-    ++h->launches;
-    std::vector<double> lh(m);
-    std::vector<double2> vh((size_t)m * m);
-    e = cudaMemcpyAsync(lh.data(), lam.p, m * sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(vh.data(), vbuf.p, vh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: eigensolver");
-    int stw = 0;
-    cudaMemcpy(&stw, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
-    if (stw & kStatusTimeout) {
-      cudaMemset(h->d_status, 0, sizeof(int));
-      return fail(h, MROM_ENOTCONVERGED, "mrom_project: Jacobi eigensolver did not converge");
-    }
-    std::vector<int> order(m);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lh[a] > lh[b]; });
-    std::vector<double> s(m);
-    for (int k = 0; k < m; ++k) s[k] = std::sqrt(std::max(lh[order[k]], 0.0));
-    if (sigma_out) std::copy(s.begin(), s.end(), sigma_out);
-    // truncation rule (Eq. (15) reading): keep s_k / s_1 >= TOL_Sigma, at most r_max and MROM_MAX_R
-    for (int k = 0; k < m; ++k)
-      if (s[0] > 0 && s[k] > 0 && s[k] / s[0] >= tol_sigma) r = k + 1;
-    if (r_max > 0) r = std::min(r, (int)r_max);
-    r = std::min(r, MROM_MAX_R);
-    if (r < 1) return fail(h, MROM_EINVAL, "mrom_project: snapshots have no nonzero singular value");
-    std::vector<double2> wh((size_t)m * r);
-    for (int c = 0; c < m; ++c)
-      for (int k = 0; k < r; ++k) {
-        const double2 v = vh[(size_t)c * m + order[k]];
-        wh[(size_t)c * r + k] = make_double2(v.x / s[k], v.y / s[k]);
-      }
-    DevBuf wbuf;
-    e = cudaMalloc(&wbuf.p, wh.size() * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMalloc(&Ubuf.p, (size_t)n * r * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMemcpyAsync(wbuf.p, wh.data(), wh.size() * sizeof(double2), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: basis allocation");
-    const size_t smem = ((size_t)kAR * (m + 1) + (size_t)m * kAC) * sizeof(double2);
-    e = cudaFuncSetAttribute(apply_basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: basis kernel attribute");
-    apply_basis_kernel<<<(unsigned)((n + kAR - 1) / kAR), 256, smem, st>>>(Dp, 1, ldd, m, n,
-                                                                           static_cast<double2*>(wbuf.p), r,
-                                                                           static_cast<double2*>(Ubuf.p), r);
-    ++h->launches;
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: basis");
-    U = static_cast<const double2*>(Ubuf.p);
-  }
-  if (r_out) *r_out = r;
-
-  // ---- projections
   const int ng = 2 * r + 3;
-  DevBuf Y, Oc, small, phi, winv;
-  e = cudaMalloc(&Y.p, (size_t)n * r * sizeof(double2));
+  DevBuf Y, Oc, small, phi, em;
+  cudaError_t e = cudaMalloc(&Y.p, (size_t)n * r * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc(&Oc.p, (size_t)n * 3 * sizeof(double2));
-  // small: Kr, Cr, Me (r x r each), B (r x 3), c00c (3 x 3), G (ng x ng)
   const size_t nsmall = 3 * (size_t)r * r + 3 * (size_t)r + 9 + (size_t)ng * ng;
   if (e == cudaSuccess) e = cudaMalloc(&small.p, nsmall * sizeof(double2));
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: allocation");
@@ -540,8 +519,8 @@ extern "C" mrom_status mrom_project(mrom_handle h, const mrom_fom* fom, const vo
     ++h->launches;
   }
   if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, U, r, 1, r, fom->C_diag, 1, n, true, Cr, r);
-  DevBuf em;
-  if (e == cudaSuccess && fom->M_diag && fom->eps != 0.0) {
+  const bool has_me = fom->M_diag && fom->eps != 0.0;
+  if (e == cudaSuccess && has_me) {
     e = cudaMalloc(&em.p, n * sizeof(double));
     if (e == cudaSuccess) {
       scale_kernel<<<launch_grid(n), 256, 0, st>>>(fom->M_diag, fom->eps, n, static_cast<double*>(em.p));
@@ -553,7 +532,7 @@ extern "C" mrom_status mrom_project(mrom_handle h, const mrom_fom* fom, const vo
   }
   if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, Op, 3, 1, 3, fom->C_diag, 1, n, false, Bm, 3);
   if (e == cudaSuccess) e = tall_gram(h, Op, 3, 1, 3, Op, 3, 1, 3, fom->C_diag, 1, n, true, c00c, 3);
-  bool cert = fom->X_diag != nullptr;
+  const bool cert = fom->X_diag != nullptr;
   if (e == cudaSuccess && cert) {
     e = cudaMalloc(&phi.p, (size_t)n * ng * sizeof(double2));
     if (e == cudaSuccess) {
@@ -576,7 +555,7 @@ extern "C" mrom_status mrom_project(mrom_handle h, const mrom_fom* fom, const vo
   d.r = r;
   d.K = Kr;
   d.C = Cr;
-  d.Me = (fom->M_diag && fom->eps != 0.0) ? Me : nullptr;
+  d.Me = has_me ? Me : nullptr;
   d.B = Bm;
   d.c00 = c00;
   d.G = cert ? Gm : nullptr;
@@ -584,7 +563,113 @@ extern "C" mrom_status mrom_project(mrom_handle h, const mrom_fom* fom, const vo
   d.alpha = fom->alpha;
   d.alpha_lb = cert ? fom->alpha_lb : 0.0;
   d.vol_B = fom->vol_B;
+  for (int i = 0; i < 3; ++i) d.r_dirs[i] = r_dirs ? r_dirs[i] : 0;
   return mrom_rom_from_reduced(h, &d, out);
+}
+
+mrom_status check_fom(mrom_ctx* h, const mrom_fom* fom) {
+  if (!fom) return fail(h, MROM_EINVAL, "mrom_project: null argument");
+  if (fom->n < 1 || !fom->K_rowptr || !fom->K_col || !fom->K_val || !fom->C_diag || !fom->o)
+    return fail(h, MROM_EINVAL, "mrom_project: n, K, C_diag and o are required");
+  if (!(fom->alpha > 0) || !std::isfinite(fom->alpha) || !std::isfinite(fom->eps))
+    return fail(h, MROM_EINVAL, "mrom_project: alpha must be finite and > 0, eps finite");
+  if (fom->X_diag && !(fom->alpha_lb > 0)) return fail(h, MROM_EINVAL, "mrom_project: a certificate needs alpha_lb > 0");
+  return MROM_OK;
+}
+
+}  // namespace
+}  // namespace mrom
+
+extern "C" mrom_status mrom_project(mrom_handle h, const mrom_fom* fom, const void* D, int64_t ldd, int32_t n_cols,
+                                    double tol_sigma, int32_t r_max, const void* basis_in, int32_t r_in,
+                                    mrom_rom_t* out, double* sigma_out, int32_t* r_out) {
+  if (!h) return MROM_EINVAL;
+  if (!out) return fail(h, MROM_EINVAL, "mrom_project: null argument");
+  *out = nullptr;
+  mrom_status st = check_fom(h, fom);
+  if (st != MROM_OK) return st;
+  const int64_t n = fom->n;
+  if (!basis_in) {
+    if (!D || n_cols < 1 || n_cols > MROM_MAX_SNAPSHOTS || ldd < n)
+      return fail(h, MROM_EINVAL, "mrom_project: D needs 1..MROM_MAX_SNAPSHOTS columns and ldd >= n");
+    if (!(tol_sigma >= 0.0) || !std::isfinite(tol_sigma))
+      return fail(h, MROM_EINVAL, "mrom_project: tol_sigma must be finite and >= 0");
+  } else if (r_in < 1 || r_in > MROM_MAX_R) {
+    return fail(h, MROM_EINVAL, "mrom_project: r_in must be in [1, MROM_MAX_R]");
+  }
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: cudaSetDevice");
+  if (basis_in) {
+    if (r_out) *r_out = r_in;
+    return project_basis(h, fom, static_cast<const double2*>(basis_in), r_in, nullptr, out);
+  }
+  const auto* Dp = static_cast<const double2*>(D);
+  int r = 0;
+  std::vector<double> s;
+  std::vector<double2> wh;
+  st = gram_eig(h, Dp, ldd, n, n_cols, tol_sigma, std::min<int>(r_max > 0 ? r_max : MROM_MAX_R, MROM_MAX_R), &r, s, wh);
+  if (st != MROM_OK) return st;
+  if (sigma_out) std::copy(s.begin(), s.end(), sigma_out);
+  if (r_out) *r_out = r;
+  DevBuf Ubuf;
+  e = cudaMalloc(&Ubuf.p, (size_t)n * r * sizeof(double2));
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: basis allocation");
+  st = apply_basis(h, Dp, ldd, n, n_cols, wh, r, static_cast<double2*>(Ubuf.p), r);
+  if (st != MROM_OK) return st;
+  return project_basis(h, fom, static_cast<const double2*>(Ubuf.p), r, nullptr, out);
+}
+
+extern "C" mrom_status mrom_project_dirs(mrom_handle h, const mrom_fom* fom, const void* D, int64_t ldd, int32_t n_s,
+                                         double tol_sigma, int32_t r_max, const void* basis_in,
+                                         const int32_t* r_dirs_in, mrom_rom_t* out, double* sigma_out,
+                                         int32_t* r_dirs_out) {
+  if (!h) return MROM_EINVAL;
+  if (!out) return fail(h, MROM_EINVAL, "mrom_project_dirs: null argument");
+  *out = nullptr;
+  mrom_status st = check_fom(h, fom);
+  if (st != MROM_OK) return st;
+  const int64_t n = fom->n;
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project_dirs: cudaSetDevice");
+  int32_t rd[3] = {0, 0, 0};
+  if (basis_in) {
+    if (!r_dirs_in) return fail(h, MROM_EINVAL, "mrom_project_dirs: a basis needs r_dirs_in");
+    int rt = 0;
+    for (int i = 0; i < 3; ++i) {
+      if (r_dirs_in[i] < 1) return fail(h, MROM_EINVAL, "mrom_project_dirs: every direction needs r >= 1");
+      rd[i] = r_dirs_in[i];
+      rt += rd[i];
+    }
+    if (rt > MROM_MAX_R) return fail(h, MROM_EINVAL, "mrom_project_dirs: r_1 + r_2 + r_3 exceeds MROM_MAX_R");
+    if (r_dirs_out) std::copy(rd, rd + 3, r_dirs_out);
+    return project_basis(h, fom, static_cast<const double2*>(basis_in), rt, rd, out);
+  }
+  if (!D || n_s < 1 || 3 * n_s > MROM_MAX_SNAPSHOTS || ldd < n)
+    return fail(h, MROM_EINVAL, "mrom_project_dirs: D needs 3 x n_s columns (3 n_s <= MROM_MAX_SNAPSHOTS), ldd >= n");
+  if (!(tol_sigma >= 0.0) || !std::isfinite(tol_sigma))
+    return fail(h, MROM_EINVAL, "mrom_project_dirs: tol_sigma must be finite and >= 0");
+  const auto* Dp = static_cast<const double2*>(D);
+  std::vector<double2> wh[3];
+  for (int i = 0; i < 3; ++i) {
+    std::vector<double> s;
+    const int cap = std::min<int>(r_max > 0 ? r_max : MROM_MAX_R, MROM_MAX_R);
+    st = gram_eig(h, Dp + (size_t)i * n_s * ldd, ldd, n, n_s, tol_sigma, cap, &rd[i], s, wh[i]);
+    if (st != MROM_OK) return st;
+    if (sigma_out) std::copy(s.begin(), s.end(), sigma_out + (size_t)i * n_s);
+  }
+  const int rt = rd[0] + rd[1] + rd[2];
+  if (rt > MROM_MAX_R) return fail(h, MROM_EINVAL, "mrom_project_dirs: r_1 + r_2 + r_3 exceeds MROM_MAX_R");
+  if (r_dirs_out) std::copy(rd, rd + 3, r_dirs_out);
+  DevBuf Ubuf;
+  e = cudaMalloc(&Ubuf.p, (size_t)n * rt * sizeof(double2));
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project_dirs: basis allocation");
+  int off = 0;
+  for (int i = 0; i < 3; ++i) {
+    st = apply_basis(h, Dp + (size_t)i * n_s * ldd, ldd, n, n_s, wh[i], rd[i], static_cast<double2*>(Ubuf.p) + off, rt);
+    if (st != MROM_OK) return st;
+    off += rd[i];
+  }
+  return project_basis(h, fom, static_cast<const double2*>(Ubuf.p), rt, rd, out);
 }
 
 extern "C" mrom_status mrom_rom_get(mrom_rom_t rom, void* K, void* C, void* Me, void* B, double* c00, void* G) {

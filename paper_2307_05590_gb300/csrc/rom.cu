@@ -71,6 +71,9 @@ extern "C" mrom_status mrom_rom_from_reduced(mrom_handle h, const mrom_reduced_d
     return fail(h, MROM_EINVAL, "mrom_rom_from_reduced: alpha must be finite and > 0");
   if (d->G && !(d->alpha_lb > 0 && std::isfinite(d->alpha_lb)))
     return fail(h, MROM_EINVAL, "mrom_rom_from_reduced: a Gram matrix needs alpha_lb > 0");
+  const int rd_sum = d->r_dirs[0] + d->r_dirs[1] + d->r_dirs[2];
+  if (rd_sum != 0 && (rd_sum != r || d->r_dirs[0] < 1 || d->r_dirs[1] < 1 || d->r_dirs[2] < 1))
+    return fail(h, MROM_EINVAL, "mrom_rom_from_reduced: r_dirs must be all 0 or positive with sum r");
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
 
@@ -153,6 +156,7 @@ extern "C" mrom_status mrom_rom_from_reduced(mrom_handle h, const mrom_reduced_d
     rom->has_cert = true;
   }
   rom->has_kin = d->K_in != nullptr;
+  for (int i = 0; i < 3; ++i) rom->r_dirs[i] = d->r_dirs[i];
   if (!d->Me) rom->Me = nullptr;
   *out = rom;
   return MROM_OK;

@@ -131,35 +131,45 @@ sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__
     }
     __syncthreads();
 
-    // ---- 1. augmented systems [K + Me - i w C | i w B]
+    // ---- 1. augmented systems [K + Me - i w C | i w B]; with one basis per direction only the
+    // diagonal blocks A_ii are kept and source i is restricted to block i (Eq. (17) per direction)
+    const bool per_dir = ob.per_dir != 0;
+    auto block_of = [&](int i) { return (int)(i >= ob.blk_lo[1]) + (int)(i >= ob.blk_lo[2]); };
     for (int idx = tid; idx < S * r * ld; idx += THREADS) {
       const int s = idx / (r * ld);
       const int e = idx - s * r * ld;
       const int i = e / ld;
       const int j = e - i * ld;
       const double w = Ws[s];
-      double2 v;
+      double2 v = make_double2(0.0, 0.0);
       if (j < r) {
-        double2 k = ob.K[i * r + j];
-        const double2 c = ob.C[i * r + j];
-        if (ob.Me) {
-          const double2 m = ob.Me[i * r + j];
-          k.x += m.x;
-          k.y += m.y;
+        if (!per_dir || block_of(i) == block_of(j)) {
+          double2 k = ob.K[i * r + j];
+          const double2 c = ob.C[i * r + j];
+          if (ob.Me) {
+            const double2 m = ob.Me[i * r + j];
+            k.x += m.x;
+            k.y += m.y;
+          }
+          v = make_double2(fma(w, c.y, k.x), fma(-w, c.x, k.y));
         }
-        v = make_double2(fma(w, c.y, k.x), fma(-w, c.x, k.y));
-      } else {
+      } else if (!per_dir || (i >= ob.blk_lo[j - r] && i < ob.blk_hi[j - r])) {
         const double2 b = ob.B[i * 3 + (j - r)];
         v = make_double2(-w * b.y, w * b.x);
       }
       Am[(size_t)s * am_elems + e] = v;
-      if (e == 0) Inv[(size_t)s * r] = c_recip(v, status);
+      // first pivot of the matrix and, per direction, of every block
+      if (e == 0 || (per_dir && i == j && (i == ob.blk_lo[1] || i == ob.blk_lo[2])))
+        Inv[(size_t)s * r + i] = c_recip(v, status);
     }
     __syncthreads();
 
-    // ---- 2. elimination without pivoting (right-looking, right-hand sides carried along)
+    // ---- 2. elimination without pivoting (right-looking, right-hand sides carried along);
+    // rows and columns of the pivot's direction block only (all of them for a shared basis)
     for (int k = 0; k < r - 1; ++k) {
-      const int m = r - k - 1;
+      const int hi = per_dir ? (k < ob.blk_hi[0] ? ob.blk_hi[0] : (k < ob.blk_hi[1] ? ob.blk_hi[1] : ob.blk_hi[2])) : r;
+      const int m = hi - k - 1;
+      if (m == 0) continue;  // last pivot of a block (uniform across the CTA)
       for (int idx = tid; idx < S * m; idx += THREADS) {
         const int s = idx / m;
         const int i = k + 1 + (idx - s * m);
@@ -167,7 +177,7 @@ sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__
         a[i * ld + k] = c_mul(a[i * ld + k], Inv[(size_t)s * r + k]);
       }
       __syncthreads();
-      const int nc = ld - k - 1;
+      const int nc = m + 3;  // the block's columns right of the pivot, then the three sources
       const int per = m * nc;
       const int total = S * per;
       // two independent elements per iteration: all loads are issued before either store
@@ -176,10 +186,12 @@ sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__
         const bool two = idx2 < total;
         const int s1 = idx / per;
         const int e1 = idx - s1 * per;
-        const int i1 = k + 1 + e1 / nc, j1 = k + 1 + (e1 - (e1 / nc) * nc);
+        const int c1 = e1 - (e1 / nc) * nc;
+        const int i1 = k + 1 + e1 / nc, j1 = c1 < m ? k + 1 + c1 : r + (c1 - m);
         const int s2 = two ? idx2 / per : s1;
         const int e2 = two ? idx2 - s2 * per : e1;
-        const int i2 = k + 1 + e2 / nc, j2 = k + 1 + (e2 - (e2 / nc) * nc);
+        const int c2 = e2 - (e2 / nc) * nc;
+        const int i2 = k + 1 + e2 / nc, j2 = c2 < m ? k + 1 + c2 : r + (c2 - m);
         double2* a1 = Am + (size_t)s1 * am_elems;
         double2* a2 = Am + (size_t)s2 * am_elems;
         const double2 x1 = a1[i1 * ld + j1], l1 = a1[i1 * ld + k], u1 = a1[k * ld + j1];
@@ -194,15 +206,19 @@ sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__
       __syncthreads();
     }
 
-    // ---- 3. back substitution: one warp per (system, right-hand side), warp-synchronous
+    // ---- 3. back substitution: one warp per (system, right-hand side), warp-synchronous; the
+    // solution of direction j is zero outside its block
     for (int sj = warp; sj < S * 3; sj += kWarps) {
       const int s = sj / 3, j = sj - (sj / 3) * 3;
       double2* a = Am + (size_t)s * am_elems;
       const double2* inv = Inv + (size_t)s * r;
       double2* p = Pm + (size_t)s * r * 3;
-      for (int k = r - 1; k >= 0; --k) {
+      const int lo = ob.blk_lo[j], hi = ob.blk_hi[j];
+      for (int k = lane; k < r; k += 32)
+        if (k < lo || k >= hi) p[k * 3 + j] = make_double2(0.0, 0.0);
+      for (int k = hi - 1; k >= lo; --k) {
         const double2 x = c_mul(a[k * ld + r + j], inv[k]);  // every lane reads the same y_k
-        for (int i = lane; i < k; i += 32) a[i * ld + r + j] = c_msub(a[i * ld + r + j], a[i * ld + k], x);
+        for (int i = lo + lane; i < k; i += 32) a[i * ld + r + j] = c_msub(a[i * ld + r + j], a[i * ld + k], x);
         if (lane == 0) p[k * 3 + j] = x;
         __syncwarp();
       }

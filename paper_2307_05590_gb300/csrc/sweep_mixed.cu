@@ -320,6 +320,8 @@ extern "C" mrom_status mrom_sweep_mixed(mrom_handle h, const mrom_rom_t* roms, i
     return fail(h, MROM_EINVAL, "mrom_sweep_mixed: omega_stride must be 0 or >= n_w");
   for (int o = 0; o < n_obj; ++o) {
     if (!roms[o] || roms[o]->ctx != h) return fail(h, MROM_EINVAL, "mrom_sweep_mixed: invalid object");
+    if (roms[o]->r_dirs[0] + roms[o]->r_dirs[1] + roms[o]->r_dirs[2] > 0)
+      return fail(h, MROM_ENOTSUP, "mrom_sweep_mixed: objects with one basis per direction are swept by mrom_sweep");
     if (Delta && !roms[o]->has_cert)
       return fail(h, MROM_EINVAL, "mrom_sweep_mixed: Delta requested but an object has no Gram matrix");
   }

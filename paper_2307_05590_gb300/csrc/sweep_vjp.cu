@@ -356,6 +356,8 @@ extern "C" mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int
     return fail(h, MROM_EINVAL, "mrom_sweep_vjp: omega_stride must be 0 or >= n_w");
   for (int o = 0; o < n_obj; ++o) {
     if (!roms[o] || roms[o]->ctx != h) return fail(h, MROM_EINVAL, "mrom_sweep_vjp: invalid object");
+    if (roms[o]->r_dirs[0] + roms[o]->r_dirs[1] + roms[o]->r_dirs[2] > 0)
+      return fail(h, MROM_ENOTSUP, "mrom_sweep_vjp: objects with one basis per direction are swept by mrom_sweep");
     if ((s_mu || g_smu) && !roms[o]->has_kin)
       return fail(h, MROM_EINVAL, "mrom_sweep_vjp: s_mu / g_smu need K_in on every object");
   }

@@ -108,3 +108,43 @@ def test_project_rejects_bad_input(mrom, case):
         mrom.mrom_project(h, fom, torch.zeros((200, p.N), dtype=torch.complex128, device="cuda"))
     with pytest.raises(mrom.MromError):
         mrom.mrom_project(h, fom, basis=torch.zeros((p.N, 120), dtype=torch.complex128, device="cuda"))
+
+
+def test_per_direction_bases_match_oracle(mrom, case):
+    """The paper's PODP: one TSVD per direction (Sect. 4.1), cross blocks K_ij = U_i^H K U_j in
+    Eq. (18), I_ij of Eq. (19) and the certificate with Phi_i = [C o_i | (K+eps M)U_i | C U_i].
+    Both with the oracle's bases and with the GPU's own per-direction TSVDs."""
+    import torch
+    from oracle import certificate, rom, tsvd
+    from workloads import log_omegas
+    from gpu_common import rel_errors
+    p, Dcols, X = case
+    n_s = Dcols.shape[0] // 3
+    Us = [tsvd.truncated_svd(Dcols[i * n_s:(i + 1) * n_s].T, 1e-6)[0] for i in range(3)]
+    model = rom.project(p, Us)
+    certificate.attach_gram(model, p, Us, sp.diags(X).tocsc())
+    wo = log_omegas(1e1, 1e5, 48) * 1.07
+    P = rom.reduced_solve(model, wo)
+    Rr, Ir = rom.mm_tensors(model, wo, P)
+    Dr = certificate.certificate(model, wo, P)
+    a3 = model.alpha ** 3
+    # term scales (reading 10): I against w a^3/4 (|c00| + |forms|), Delta against |w|^T |G| |w|
+    sI = np.array([w * a3 / 4 * (np.abs(model.c00).max() + sum(np.abs(P[i][n]).sum() ** 2 for i in range(3)) *
+                                 max(np.abs(model.C[i][j]).max() for i in range(3) for j in range(3)) +
+                                 2 * max(np.abs(model.oCU[i][j]).max() for i in range(3) for j in range(3)) *
+                                 sum(np.abs(P[i][n]).sum() for i in range(3))) for n, w in enumerate(wo)])
+    absG = np.abs(model.gram)
+    sD = np.array([a3 / (4 * model.alpha_lb) * max(np.abs(x) @ absG @ np.abs(x) for x in
+                   certificate.residual_weights(model, w, [P[i][n] for i in range(3)])) for n, w in enumerate(wo)])
+    h = mrom.Handle(0)
+    fom = mrom.FullOrder.from_fit(p, X=X)
+    W = torch.as_tensor(np.ascontiguousarray(np.concatenate(Us, axis=1)), device="cuda")
+    rd = tuple(U.shape[1] for U in Us)
+    obj, _, rd_out = mrom.mrom_project_dirs(h, fom, basis=W, r_dirs=rd)
+    assert rd_out == rd
+    obj2, sig, rd2 = mrom.mrom_project_dirs(h, fom, torch.as_tensor(Dcols, device="cuda"), tol_sigma=1e-6)
+    assert rd2 == rd
+    for o in (obj, obj2):
+        Rg, Ig, Dg = _sweep(mrom, h, [o], wo)
+        errs = rel_errors(Rg[0], Ig[0], Dg[0], Rr, Ir, Dr, sI, sD)
+        assert max(errs) <= TOL, errs
