@@ -170,11 +170,23 @@ def measure_projection(m, h, n_grid: int = 96, n_s: int = 32):
     dt = time.perf_counter() - t0
     rom.close()
     fl = project_flops(p.N, p.K.nnz, 3 * n_s, r)
+    # single-precision products (K U and the K_r, C_r, eps M_r, b Gram products in complex64)
+    h.set_projection_precision(True)
+    rom, _, r32 = m.mrom_project(h, fom, Dd, tol_sigma=1e-6)  # warm-up
+    rom.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rom, _, r32 = m.mrom_project(h, fom, Dd, tol_sigma=1e-6)
+    torch.cuda.synchronize()
+    dt32 = time.perf_counter() - t0
+    rom.close()
+    h.set_projection_precision(False)
     return {"workload": f"mrom_project: 96^3 FIT grid (N = {p.N}, {p.K.nnz} nnz), 3 x {n_s} snapshot columns, "
                         f"TOL_Sigma 1e-6 -> r = {r}, certificate Gram with diagonal X",
             "seconds": dt, "r": r, "flops": fl, "achieved_tflops": fl / dt / 1e12,
             "bound": "alu", "fp64_frac": fl / dt / 1e12 / (SM_COUNT_NOMINAL * DFMA_PER_CLK_PER_SM * 2 * 2.07e9 / 1e12),
-            "hbm_gb_moved_min": (3 * n_s * p.N * 16 * 2 + p.N * r * 16 * 4 + p.K.nnz * 12) / 1e9}
+            "hbm_gb_moved_min": (3 * n_s * p.N * 16 * 2 + p.N * r * 16 * 4 + p.K.nnz * 12) / 1e9,
+            "mixed_seconds": dt32, "mixed_r": r32}
 
 
 def config(args):

@@ -52,6 +52,8 @@ typedef enum {
   MROM_ENOTSUP = 8        /* option not supported for this object */
 } mrom_status;
 
+typedef enum { MROM_FP64 = 0, MROM_MIXED = 1 } mrom_precision;
+
 typedef struct mrom_ctx* mrom_handle;
 typedef struct mrom_rom* mrom_rom_t;
 typedef struct mrom_plan_s* mrom_plan;
@@ -72,6 +74,12 @@ mrom_status mrom_synchronize(mrom_handle h);
 const char* mrom_last_error(mrom_handle h);
 /* Number of kernels this library launched on the handle so far. */
 int64_t mrom_launch_count(mrom_handle h);
+/* Precision of mrom_project / mrom_project_dirs on this handle.  MROM_FP64
+ * (default): every product in float64.  MROM_MIXED: the SpMM K U and the Gram
+ * products K_r, C_r, eps M_r and b in complex64 with complex64 accumulation
+ * over each CTA's rows (partials summed in float64); the TSVD and the
+ * certificate Gram stay float64. */
+mrom_status mrom_set_projection_precision(mrom_handle h, mrom_precision precision);
 
 /* ------------------------------------------------------- reduced objects */
 

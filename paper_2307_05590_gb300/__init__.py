@@ -61,6 +61,10 @@ class Handle:
     def launch_count(self) -> int:
         return int(lib().mrom_launch_count(self._h))
 
+    def set_projection_precision(self, mixed: bool) -> None:
+        """MROM_MIXED (complex64 SpMM and Gram products) or MROM_FP64 for mrom_project."""
+        _abi.check(lib().mrom_set_projection_precision(self._h, 1 if mixed else 0), self._h)
+
     def close(self):
         if self._h:
             lib().mrom_destroy(self._h)

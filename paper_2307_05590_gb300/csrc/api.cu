@@ -71,6 +71,14 @@ extern "C" const char* mrom_last_error(mrom_handle h) {
 
 extern "C" int64_t mrom_launch_count(mrom_handle h) { return h ? h->launches : 0; }
 
+extern "C" mrom_status mrom_set_projection_precision(mrom_handle h, mrom_precision precision) {
+  if (!h) return MROM_EINVAL;
+  if (precision != MROM_FP64 && precision != MROM_MIXED)
+    return fail(h, MROM_EINVAL, "mrom_set_projection_precision: MROM_FP64 or MROM_MIXED");
+  h->projection_precision = precision;
+  return MROM_OK;
+}
+
 extern "C" mrom_status mrom_synchronize(mrom_handle h) {
   if (!h) return MROM_EINVAL;
   cudaSetDevice(h->device);

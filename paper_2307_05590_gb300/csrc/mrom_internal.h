@@ -64,6 +64,7 @@ struct mrom_ctx {
   size_t smem_optin = 0;
   int64_t launches = 0;
   int sweep_cfg = -1;             // launch configuration for sweeps (-1: default)
+  int projection_precision = 0;   // MROM_FP64 or MROM_MIXED for mrom_project's K U and Gram products
   mrom_status pending = MROM_OK;  // host-detected asynchronous error
   std::string last_error;
 };

@@ -91,6 +91,119 @@ gram_partial_kernel(const double2* __restrict__ A, int64_t rsA, int64_t csA, int
     }
 }
 
+// Single-precision variant (complex64 operands, complex64 accumulation over the CTA's row
+// range); the partials are summed in float64 by gram_reduce_f32_kernel.
+__device__ __forceinline__ float2 f_conj_mac(float2 c, float2 a, float2 b) {  // c + conj(a) b
+  return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+
+__global__ void __launch_bounds__(256)
+gram_partial_f32_kernel(const float2* __restrict__ A, int64_t rsA, int ma, const float2* __restrict__ B, int64_t rsB,
+                        int mb, const float* __restrict__ w, int64_t n, int64_t rows_per_split,
+                        const int2* __restrict__ tiles, float2* __restrict__ part) {
+  __shared__ float2 As[kGR][kGT + 1];
+  __shared__ float2 Bs[kGR][kGT + 1];
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+  const int2 tile = tiles[blockIdx.y];
+  const int a_base = tile.x * kGT, b_base = tile.y * kGT;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_split;
+  const int64_t r1 = min(n, r0 + rows_per_split);
+  float2 acc[2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
+  for (int64_t row0 = r0; row0 < r1; row0 += kGR) {
+    for (int idx = tid; idx < kGR * kGT; idx += 256) {
+      const int rr = idx / kGT, cc = idx % kGT;
+      const int64_t nr = row0 + rr;
+      As[rr][cc] = (nr < r1 && a_base + cc < ma) ? A[nr * rsA + a_base + cc] : make_float2(0.f, 0.f);
+      float2 v = make_float2(0.f, 0.f);
+      if (nr < r1 && b_base + cc < mb) {
+        v = B[nr * rsB + b_base + cc];
+        if (w) {
+          v.x *= w[nr];
+          v.y *= w[nr];
+        }
+      }
+      Bs[rr][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < kGR; ++rr) {
+      const float2 a0 = As[rr][ty * 2], a1 = As[rr][ty * 2 + 1];
+      const float2 b0 = Bs[rr][tx * 2], b1 = Bs[rr][tx * 2 + 1];
+      acc[0][0] = f_conj_mac(acc[0][0], a0, b0);
+      acc[0][1] = f_conj_mac(acc[0][1], a0, b1);
+      acc[1][0] = f_conj_mac(acc[1][0], a1, b0);
+      acc[1][1] = f_conj_mac(acc[1][1], a1, b1);
+    }
+    __syncthreads();
+  }
+  float2* out = part + (size_t)blockIdx.x * ma * mb;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int a = a_base + ty * 2 + i, b = b_base + tx * 2 + j;
+      if (a < ma && b < mb) out[(size_t)a * mb + b] = acc[i][j];
+    }
+}
+
+__global__ void gram_reduce_f32_kernel(const float2* __restrict__ part, int nsplit, int ma, int mb, int hermitian,
+                                       double2* __restrict__ G, int64_t ldg) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)ma * mb;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / mb), b = (int)(idx % mb);
+    int sa = a, sb = b;
+    bool conj = false;
+    if (hermitian && (b / kGT) < (a / kGT)) {
+      sa = b;
+      sb = a;
+      conj = true;
+    }
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < nsplit; ++k) {
+      const float2 v = part[(size_t)k * ma * mb + (size_t)sa * mb + sb];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    if (conj) s.y = -s.y;
+    if (hermitian && a == b) s.y = 0.0;
+    G[(int64_t)a * ldg + b] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+spmm_csr_f32_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                    const float* __restrict__ val, int64_t n, const float2* __restrict__ U, int r,
+                    float2* __restrict__ Y) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  float2 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  for (int k = rowptr[row]; k < rowptr[row + 1]; ++k) {
+    const int64_t j = col[k];
+    const float v = val[k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = lane + 32 * q;
+      if (c < r) {
+        const float2 u = U[j * r + c];
+        acc[q].x = fmaf(v, u.x, acc[q].x);
+        acc[q].y = fmaf(v, u.y, acc[q].y);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = lane + 32 * q;
+    if (c < r) Y[row * r + c] = acc[q];
+  }
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ x, int64_t n, double scale, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)(scale * x[i]);
+}
+
 // G[a][b] = sum over splits (fixed order).  Hermitian: only tiles with b-tile >= a-tile
 // were computed; the rest is mirrored and the diagonal made real.
 __global__ void gram_reduce_kernel(const double2* __restrict__ part, int nsplit, int ma, int mb, int hermitian,
@@ -412,6 +525,36 @@ cudaError_t tall_gram(mrom_ctx* h, const double2* A, int64_t rsA, int64_t csA, i
   return e;
 }
 
+// Single-precision tall Gram (row-major operands): G = A^H diag(w) B, float64 output.
+cudaError_t tall_gram_f32(mrom_ctx* h, const float2* A, int64_t rsA, int ma, const float2* B, int64_t rsB, int mb,
+                          const float* w, int64_t n, bool hermitian, double2* G, int64_t ldg) {
+  const int ta = (ma + kGT - 1) / kGT, tb = (mb + kGT - 1) / kGT;
+  std::vector<int2> tl;
+  for (int i = 0; i < ta; ++i)
+    for (int j = hermitian ? i : 0; j < tb; ++j) tl.push_back(make_int2(i, j));
+  const int ntiles = (int)tl.size();
+  int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>((8LL * h->num_sms + ntiles - 1) / ntiles, (n + 1023) / 1024));
+  nsplit = std::min<int64_t>(nsplit, 65535);
+  const int64_t per = ((n + nsplit - 1) / nsplit + kGR - 1) / kGR * kGR;
+  nsplit = std::max<int64_t>(1, (n + per - 1) / per);
+  DevBuf part, tiles;
+  cudaError_t e = cudaMalloc(&part.p, (size_t)nsplit * ma * mb * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&tiles.p, tl.size() * sizeof(int2));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tiles.p, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return e;
+  gram_partial_f32_kernel<<<dim3((unsigned)nsplit, (unsigned)ntiles), 256, 0, h->stream>>>(
+      A, rsA, ma, B, rsB, mb, w, n, per, static_cast<int2*>(tiles.p), static_cast<float2*>(part.p));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int rb = (int)std::min<int64_t>(4096, ((int64_t)ma * mb + 255) / 256);
+  gram_reduce_f32_kernel<<<std::max(rb, 1), 256, 0, h->stream>>>(static_cast<float2*>(part.p), (int)nsplit, ma, mb,
+                                                                  hermitian ? 1 : 0, G, ldg);
+  e = cudaGetLastError();
+  h->launches += 2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e;
+}
+
 }  // namespace mrom
 
 using namespace mrom;
@@ -494,7 +637,9 @@ mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, in
   auto launch_grid = [](int64_t work) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(65535 * 4, (work + 255) / 256)); };
   const int ng = 2 * r + 3;
   DevBuf Y, Oc, small, phi, em;
-  cudaError_t e = cudaMalloc(&Y.p, (size_t)n * r * sizeof(double2));
+  // K U in float64 feeds the float64 products and the certificate's residual basis
+  const bool need_y64 = h->projection_precision != MROM_MIXED || fom->X_diag != nullptr;
+  cudaError_t e = need_y64 ? cudaMalloc(&Y.p, (size_t)n * r * sizeof(double2)) : cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&Oc.p, (size_t)n * 3 * sizeof(double2));
   const size_t nsmall = 3 * (size_t)r * r + 3 * (size_t)r + 9 + (size_t)ng * ng;
   if (e == cudaSuccess) e = cudaMalloc(&small.p, nsmall * sizeof(double2));
@@ -505,32 +650,74 @@ mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, in
   double2* Bm = Me + (size_t)r * r;
   double2* c00c = Bm + 3 * (size_t)r;
   double2* Gm = c00c + 9;
-  spmm_csr_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(fom->K_rowptr, fom->K_col, fom->K_val, n, U, r,
-                                                                    nullptr, static_cast<double2*>(Y.p));
+  if (need_y64) {
+    spmm_csr_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(fom->K_rowptr, fom->K_col, fom->K_val, n, U, r,
+                                                                      nullptr, static_cast<double2*>(Y.p));
+    ++h->launches;
+  }
   complexify_o_kernel<<<launch_grid(3 * n), 256, 0, st>>>(fom->o, n, static_cast<double2*>(Oc.p));
-  h->launches += 2;
+  ++h->launches;
   e = cudaGetLastError();
   const double2* Yp = static_cast<const double2*>(Y.p);
   const double2* Op = static_cast<const double2*>(Oc.p);
-  // K_r = U^H (K U), symmetrised (K is symmetric)
-  if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, Yp, r, 1, r, nullptr, 0, n, false, Kr, r);
-  if (e == cudaSuccess) {
-    symmetrize_kernel<<<(r * r + 255) / 256, 256, 0, st>>>(Kr, r);
-    ++h->launches;
-  }
-  if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, U, r, 1, r, fom->C_diag, 1, n, true, Cr, r);
   const bool has_me = fom->M_diag && fom->eps != 0.0;
-  if (e == cudaSuccess && has_me) {
-    e = cudaMalloc(&em.p, n * sizeof(double));
+  if (h->projection_precision == MROM_MIXED) {
+    // K U, K_r, C_r, eps M_r and b in single precision (complex64 SpMM and Gram products with
+    // complex64 accumulation over each CTA's rows, partials summed in float64)
+    DevBuf U32, Y32, O32, K32, c32, m32;
+    int32_t nnz_host = 0;
+    e = cudaMemcpy(&nnz_host, fom->K_rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMalloc(&U32.p, (size_t)n * r * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&Y32.p, (size_t)n * r * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&O32.p, (size_t)n * 3 * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&K32.p, (size_t)nnz_host * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c32.p, (size_t)n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&m32.p, (size_t)n * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: single-precision buffers");
+    to_f32_kernel<<<launch_grid(2 * n * r), 256, 0, st>>>(reinterpret_cast<const double*>(U), 2 * n * r, 1.0,
+                                                          static_cast<float*>(U32.p));
+    to_f32_kernel<<<launch_grid(6 * n), 256, 0, st>>>(reinterpret_cast<const double*>(Op), 6 * n, 1.0,
+                                                      static_cast<float*>(O32.p));
+    to_f32_kernel<<<launch_grid(nnz_host), 256, 0, st>>>(fom->K_val, nnz_host, 1.0, static_cast<float*>(K32.p));
+    to_f32_kernel<<<launch_grid(n), 256, 0, st>>>(fom->C_diag, n, 1.0, static_cast<float*>(c32.p));
+    if (has_me)
+      to_f32_kernel<<<launch_grid(n), 256, 0, st>>>(fom->M_diag, n, fom->eps, static_cast<float*>(m32.p));
+    spmm_csr_f32_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(
+        fom->K_rowptr, fom->K_col, static_cast<float*>(K32.p), n, static_cast<float2*>(U32.p), r,
+        static_cast<float2*>(Y32.p));
+    h->launches += has_me ? 6 : 5;
+    e = cudaGetLastError();
+    const auto* u32 = static_cast<const float2*>(U32.p);
+    if (e == cudaSuccess) e = tall_gram_f32(h, u32, r, r, static_cast<float2*>(Y32.p), r, r, nullptr, n, false, Kr, r);
     if (e == cudaSuccess) {
-      scale_kernel<<<launch_grid(n), 256, 0, st>>>(fom->M_diag, fom->eps, n, static_cast<double*>(em.p));
+      symmetrize_kernel<<<(r * r + 255) / 256, 256, 0, st>>>(Kr, r);
       ++h->launches;
-      e = cudaGetLastError();
     }
-    // Me = U^H diag(eps m) U  (added to the reduced system only, Eq. (17))
-    if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, U, r, 1, r, static_cast<double*>(em.p), 1, n, true, Me, r);
+    if (e == cudaSuccess) e = tall_gram_f32(h, u32, r, r, u32, r, r, static_cast<float*>(c32.p), n, true, Cr, r);
+    if (e == cudaSuccess && has_me)
+      e = tall_gram_f32(h, u32, r, r, u32, r, r, static_cast<float*>(m32.p), n, true, Me, r);
+    if (e == cudaSuccess)
+      e = tall_gram_f32(h, u32, r, r, static_cast<float2*>(O32.p), 3, 3, static_cast<float*>(c32.p), n, false, Bm, 3);
+  } else {
+    // K_r = U^H (K U), symmetrised (K is symmetric)
+    if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, Yp, r, 1, r, nullptr, 0, n, false, Kr, r);
+    if (e == cudaSuccess) {
+      symmetrize_kernel<<<(r * r + 255) / 256, 256, 0, st>>>(Kr, r);
+      ++h->launches;
+    }
+    if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, U, r, 1, r, fom->C_diag, 1, n, true, Cr, r);
+    if (e == cudaSuccess && has_me) {
+      e = cudaMalloc(&em.p, n * sizeof(double));
+      if (e == cudaSuccess) {
+        scale_kernel<<<launch_grid(n), 256, 0, st>>>(fom->M_diag, fom->eps, n, static_cast<double*>(em.p));
+        ++h->launches;
+        e = cudaGetLastError();
+      }
+      // Me = U^H diag(eps m) U  (added to the reduced system only, Eq. (17))
+      if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, U, r, 1, r, static_cast<double*>(em.p), 1, n, true, Me, r);
+    }
+    if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, Op, 3, 1, 3, fom->C_diag, 1, n, false, Bm, 3);
   }
-  if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, Op, 3, 1, 3, fom->C_diag, 1, n, false, Bm, 3);
   if (e == cudaSuccess) e = tall_gram(h, Op, 3, 1, 3, Op, 3, 1, 3, fom->C_diag, 1, n, true, c00c, 3);
   const bool cert = fom->X_diag != nullptr;
   if (e == cudaSuccess && cert) {

@@ -148,3 +148,34 @@ def test_per_direction_bases_match_oracle(mrom, case):
         Rg, Ig, Dg = _sweep(mrom, h, [o], wo)
         errs = rel_errors(Rg[0], Ig[0], Dg[0], Rr, Ir, Dr, sI, sD)
         assert max(errs) <= TOL, errs
+
+
+def test_mixed_projection_matches_oracle(mrom, case):
+    """Single-precision projection products (K U, K_r, C_r, eps M_r, b in complex64 with float64
+    summation of the per-CTA partials; TSVD and certificate Gram in float64): the reduced
+    tensors stay within the mixed-precision tolerance of 1e-5 of the float64 oracle."""
+    import torch
+    from workloads import log_omegas
+    from gpu_common import oracle_model_sweep, rel_errors
+    p, Dcols, X = case
+    model, U, _ = _oracle_model(p, Dcols, X, 1e-6)
+    h = mrom.Handle(0)
+    h.set_projection_precision(True)
+    fom = mrom.FullOrder.from_fit(p, X=X)
+    Ud = torch.as_tensor(np.ascontiguousarray(U), device="cuda")
+    rom, _, r = mrom.mrom_project(h, fom, basis=Ud)
+    got = mrom.mrom_rom_get(rom)
+    # the certificate Gram is float64 whatever the projection precision
+    assert np.abs(got["G"] - model.gram).max() <= 1e-12 * np.abs(model.gram).max()
+    # complex64 products: entrywise error bounded by a few ulps of float32 times the
+    # magnitude sum |U|^H |A| |U| (row sums of up to a few thousand terms per partial)
+    absU = np.abs(U)
+    Kabs = abs(p.K)
+    for key, ref, mag in (("K", model.K[0][0], absU.T @ (Kabs @ absU)),
+                          ("C", model.C[0][0], absU.T @ (p.C[:, None] * absU))):
+        assert np.all(np.abs(got[key] - ref) <= 1e-5 * mag + 1e-300), key
+    wo = log_omegas(1e1, 1e5, 64) * 1.03
+    Rg, Ig, Dg = _sweep(mrom, h, [rom], wo)
+    eR, eI, eD = rel_errors(Rg[0], Ig[0], Dg[0], *oracle_model_sweep(model, wo))
+    assert max(eR, eI) <= 1e-5, (eR, eI)
+    assert eD <= 1e-4, eD
