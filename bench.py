@@ -7,13 +7,18 @@ objects (shared basis, r drawn uniformly from 8..96, K_r spectrum in
 basis) x 2000 frequencies log-spaced in [1e1, 1e8] rad/s.  Every step runs the
 whole on-line path for all 2,000,000 (object, frequency) pairs: reduced solve
 (Eq. (17)), R (Eq. (18)), I (Eq. (19)) and the certificate Delta (Lemma 4.2),
-in float64, one persistent-kernel launch.
+in float64: per object the Hermitian-pencil preparation (Cholesky, Householder
+tridiagonalisation, implicit QL, transformed Gram blocks), device-side routing,
+then the O(r^2)-per-frequency pencil sweep (objects failing the accuracy gate
+take the LU sweep in the same step).
 
 value: evaluations/s with the reduced data already resident in HBM.
 e2e:   the same through the public API from pinned host buffers -- every step
        uploads the dictionary, builds the objects and the plan, sweeps, and
        reads R, I and Delta back.
-roofline: the sweep kernel against the FP64 pipe (GB300: 2 DFMA/clk/SM).
+roofline: the pencil sweep kernel against the FP64 pipe (GB300: 2 DFMA/clk/SM),
+          timed per step with CUDA events around each stage; lu_route: the same
+          step with every object on the LU route, for comparison.
 cpu_baseline: the CPU oracle (numpy/LAPACK) on a bounded sample of objects.
 
 Multi-GPU (torchrun, N > 1): every rank sweeps its own 1000-object dictionary
@@ -63,6 +68,31 @@ def flops_per_eval(r: int, cert: bool = True) -> float:
     forms = 12.0 * r * (r + 1) * mats + (4.0 * r * (r + 1) if cert else 0.0)
     red = (108.0 + 36.0 + 90.0) * r if cert else (72.0 + 36.0) * r
     return float(elim + back + form + forms + red)
+
+
+def pencil_sweep_flops(r: int, cert: bool = True) -> float:
+    """FP64 flops of one (object, frequency) evaluation in the pencil sweep kernel.
+
+      z_kj = u_k beta_kj, u_k = i w / (lambda_k - i w)         26 per k
+      O(r) terms per row a (Lambda, identity, beta, gs forms)   162 per row (126 without certificate)
+      certificate form: G~_ab(w) (4 FMA) and three complex
+        multiply-adds for every b < a                          32 per pair
+      diagonal b = a (halved)                                  38 per row
+      outputs R, I, Delta                                      225
+    """
+    r = int(r)
+    if not cert:
+        return float(26 * r + 126 * r + 100)
+    return float(16 * r * (r - 1) + 38 * r + 162 * r + 26 * r + 225)
+
+
+def pencil_prep_flops(r: int) -> float:
+    """FP64 flops of one object's pencil preparation, counting complex multiply-adds (8 flops):
+    Cholesky r^3/6, L^-1 r^3/6, X = L^-1 K r^3/2, H (lower) r^3/6, Householder tridiagonalisation
+    r^3, Q1 accumulation 2 r^3/3, V = L^-H Z r^3/2, three transformed Gram blocks 3 x 3 r^3/2
+    (the QL rotations, about r^2 of them on 2r real rows, are not counted)."""
+    r = float(r)
+    return 8.0 * r ** 3 * (1 / 6 + 1 / 6 + 1 / 2 + 1 / 6 + 1 + 2 / 3 + 1 / 2 + 4.5) + 8.0 * 9 * r * r
 
 
 class ClockSampler:
@@ -237,6 +267,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mixed", action=argparse.BooleanOptionalAction, default=True)
+    ap.add_argument("--lu-route", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--projection", action=argparse.BooleanOptionalAction, default=True)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
@@ -263,13 +294,16 @@ def main():
     objs = dictionary(args.n_obj, 20230711 + rank)
     wo = log_omegas(1e1, 1e8, args.n_w)
     rs = np.array([o.r for o in objs])
-    flops_launch = float(sum(flops_per_eval(r) for r in rs)) * args.n_w
+    flops_lu = float(sum(flops_per_eval(r) for r in rs)) * args.n_w
+    flops_pen = float(sum(pencil_sweep_flops(r) for r in rs)) * args.n_w
+    flops_prep = float(sum(pencil_prep_flops(r) for r in rs))
 
     stream = torch.cuda.Stream(dev)
     h = m.Handle(local_rank, stream.cuda_stream)
     roms = [m.ReducedObject.from_workload(h, o) for o in objs]
     sweep_cfg = m.mrom_tune(h, roms, args.n_w)
     plan = m.Plan(h, roms, args.n_w)
+    plan.enable_timing()
     om = torch.as_tensor(wo, dtype=torch.float64, device=dev)
     shape = (args.n_obj, args.n_w, 3, 3)
     R = torch.empty(shape, dtype=torch.float64, device=dev)
@@ -286,12 +320,14 @@ def main():
     clocks = ClockSampler()
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stages = []
     n0 = h.launch_count()
     t0 = time.perf_counter()
     for k in range(args.steps):
         ev[k][0].record(stream)
         plan.sweep(om, R, I, D)
         ev[k][1].record(stream)
+        stages.append(plan.stage_ms())  # (prep, route, pencil sweep, LU sweep) of this step
     h.synchronize()
     if world > 1:
         dist.barrier()
@@ -307,6 +343,34 @@ def main():
     ms_per_step = float(t_step.item())
     evals_step = args.n_obj * args.n_w * world
     value = evals_step / (ms_per_step * 1e-3)
+
+    n_pen, n_lu = plan.solver_counts()
+
+    # ---- the same step with every object on the LU route (float64 elimination)
+    lu_route = None
+    if args.lu_route:
+        h.set_solver(lu=True)
+        plan_lu = m.Plan(h, roms, args.n_w)
+        R2, I2, D2 = torch.empty_like(R), torch.empty_like(R), torch.empty_like(R)
+        plan_lu.sweep(om, R2, I2, D2)
+        h.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            plan_lu.sweep(om, R2, I2, D2)
+        e1.record(stream)
+        h.synchronize()
+        ms_lu = e0.elapsed_time(e1) / 2
+
+        def rel_d(a, b):
+            sc = torch.clamp(b.abs().amax(dim=(2, 3), keepdim=True), min=1e-300)
+            return float(((a - b).abs() / sc).max().item())
+        lu_route = {"value": args.n_obj * args.n_w / (ms_lu * 1e-3), "unit": UNIT, "ms_per_step": ms_lu,
+                    "achieved_tflops": flops_lu / (ms_lu * 1e-3) / 1e12,
+                    "max_rel_diff_vs_pencil": {"R": rel_d(R2, R), "I": rel_d(I2, I), "Delta": rel_d(D2, D)}}
+        plan_lu.close()
+        h.set_solver(lu=False)
+        del R2, I2, D2
 
     # ---- mixed precision (complex64 elimination + one float64 refinement step), same dictionary
     mixed = None
@@ -391,15 +455,18 @@ def main():
                "sample": f"{args.cpu_sample} objects spread over the dictionary (r = {srs}) x {args.n_w} "
                          f"frequencies, {dt:.1f} s"}
 
-    mean_launch_ms = float(np.mean(per_launch_ms))
     sm_mhz_max = (clk or {}).get("sm_max_mhz", 2070.0)
     peak_tflops = SM_COUNT_NOMINAL * DFMA_PER_CLK_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
-    achieved = flops_launch / (mean_launch_ms * 1e-3) / 1e12
+    st = np.array(stages, dtype=np.float64).mean(axis=0)  # mean ms per stage over the timed steps
+    achieved = flops_pen / (st[2] * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": SWEEP_DRAM_BYTES_PER_LAUNCH,
-                "kernel": "sweep_fp64_kernel", "flops_per_launch": flops_launch,
+                "kernel": "pencil_sweep_kernel", "flops_per_launch": flops_pen,
                 "peak_note": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 flop x max SM clock; "
                              f"measured DFMA microbenchmark {FP64_MEASURED_TFLOPS} TFLOP/s"}
+    stage_info = {"prep_ms": st[0], "route_ms": st[1], "pencil_sweep_ms": st[2], "lu_sweep_ms": st[3],
+                  "prep_flops": flops_prep, "prep_tflops": flops_prep / (st[0] * 1e-3) / 1e12 if st[0] > 0 else None,
+                  "objects_pencil": n_pen, "objects_lu": n_lu}
 
     if rank == 0:
         line = {
@@ -408,7 +475,7 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "wall_s_timed": wall, "per_launch_ms": per_launch_ms, "sweep_config": sweep_cfg,
-            "mixed_precision": mixed, "projection": proj,
+            "stages": stage_info, "lu_route": lu_route, "mixed_precision": mixed, "projection": proj,
         }
         print(json.dumps(line), flush=True)
     plan.close()

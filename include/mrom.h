@@ -53,6 +53,7 @@ typedef enum {
 } mrom_status;
 
 typedef enum { MROM_FP64 = 0, MROM_MIXED = 1 } mrom_precision;
+typedef enum { MROM_SOLVER_AUTO = 0, MROM_SOLVER_LU = 1 } mrom_solver;
 
 typedef struct mrom_ctx* mrom_handle;
 typedef struct mrom_rom* mrom_rom_t;
@@ -247,7 +248,8 @@ mrom_status mrom_rom_get(mrom_rom_t rom, void* K, void* C, void* Me, void* B, do
  *   Delta[o][k][i][j] (if Delta != NULL; Lemma 4.2, Eq. (20)):
  *     alpha^3/(8 alpha_lb) (||r_i||^2 + ||r_j||^2 + ||r_i - r_j||^2),
  *     ||r_i||^2 = w_i^H G w_i, w_i = [i omega e_i ; -p_i ; i omega p_i].
- * The reduced solves use LU factorisation without pivoting, which is stable
+ * The reduced solves go through each object's Hermitian pencil or use LU
+ * factorisation without pivoting (see mrom_set_solver); the latter is stable
  * here because A's Hermitian part after a pi/4 rotation, (K + omega C)/sqrt(2),
  * is positive definite for omega > 0.  omega must be finite and > 0; a
  * violation is reported by the next mrom_synchronize (outputs for that
@@ -303,6 +305,33 @@ mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, int32_t n_ob
 mrom_status mrom_plan_sweep(mrom_plan plan, const double* omega, int32_t omega_stride,
                             double* R, double* I, double* Delta);
 mrom_status mrom_plan_destroy(mrom_plan plan);
+
+/* Solver of the reduced systems for plans created (and one-shot sweeps run) after
+ * this call.  MROM_SOLVER_AUTO (default): every object with one basis shared by
+ * the directions goes through its Hermitian pencil (K + Me, C) -- per sweep, once
+ * per object, C = L L^H, L^-1 (K + Me) L^-H = Z Lambda Z^H (Householder
+ * tridiagonalisation and implicit QL) and V = L^-H Z, after which each frequency
+ * costs O(r^2) instead of the O(r^3) elimination; same outputs up to rounding.
+ * An object stays on the LU route when C is not numerically positive definite,
+ * when ||C||_F ||L^-1||_F^2 > 1e6, when the error estimate
+ * eps ||L^-1 (K + Me) L^-H||_F / omega_min exceeds 1e-11, or when the QL
+ * iteration does not converge (decided on the device, per sweep).  Objects with
+ * one basis per direction always take the LU route.  MROM_SOLVER_LU: every
+ * object takes the LU route. */
+mrom_status mrom_set_solver(mrom_handle h, mrom_solver solver);
+
+/* Objects that the last mrom_plan_sweep of this plan sent through the pencil
+ * route (*n_pencil) and through LU elimination (*n_lu); either may be NULL.
+ * Synchronous (waits for the handle's stream). */
+mrom_status mrom_plan_solver_counts(mrom_plan plan, int32_t* n_pencil, int32_t* n_lu);
+
+/* Stage timing of a plan's sweeps (not in the paper; for profiling).  enable != 0
+ * creates CUDA events that every later mrom_plan_sweep records on the handle's
+ * stream around its stages.  With stage_ms != NULL (host, 4 floats), waits for the
+ * last sweep and writes the durations in ms of its pencil preparation, routing,
+ * pencil sweep and LU sweep kernels (a plan without pencil objects has only the
+ * last).  MROM_EINVAL when stage_ms is given and timing was never enabled. */
+mrom_status mrom_plan_timing(mrom_plan plan, int32_t enable, float* stage_ms);
 
 /* Autotuner: time every sweep launch configuration (threads per CTA x CTAs per
  * SM) on a sample of this batch (up to 96 objects x 200 frequencies) and make

@@ -61,6 +61,11 @@ class Handle:
     def launch_count(self) -> int:
         return int(lib().mrom_launch_count(self._h))
 
+    def set_solver(self, lu: bool) -> None:
+        """MROM_SOLVER_LU (every object by LU elimination) or MROM_SOLVER_AUTO (pencil route
+        where it is accurate) for plans and sweeps created afterwards."""
+        _abi.check(lib().mrom_set_solver(self._h, 1 if lu else 0), self._h)
+
     def set_projection_precision(self, mixed: bool) -> None:
         """MROM_MIXED (complex64 SpMM and Gram products) or MROM_FP64 for mrom_project."""
         _abi.check(lib().mrom_set_projection_precision(self._h, 1 if mixed else 0), self._h)
@@ -170,6 +175,22 @@ class Plan:
     def sweep(self, omega, R, I, Delta=None, omega_stride: int = 0):
         _abi.check(lib().mrom_plan_sweep(self._p, _ptr(omega), int(omega_stride), _ptr(R), _ptr(I),
                                          _ptr(Delta)), self.handle.ptr)
+
+    def enable_timing(self) -> None:
+        """Record CUDA events around the stages of every later sweep (mrom_plan_timing)."""
+        _abi.check(lib().mrom_plan_timing(self._p, 1, None), self.handle.ptr)
+
+    def stage_ms(self):
+        """(prep, route, pencil sweep, LU sweep) kernel durations of the last sweep, in ms."""
+        buf = (ctypes.c_float * 4)()
+        _abi.check(lib().mrom_plan_timing(self._p, 0, buf), self.handle.ptr)
+        return tuple(float(x) for x in buf)
+
+    def solver_counts(self):
+        """(objects on the pencil route, objects on the LU route) of the last sweep."""
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _abi.check(lib().mrom_plan_solver_counts(self._p, ctypes.byref(a), ctypes.byref(b)), self.handle.ptr)
+        return a.value, b.value
 
     def close(self):
         if self._p:

@@ -102,6 +102,13 @@ extern "C" mrom_status mrom_synchronize(mrom_handle h) {
 
 namespace {
 
+// Pencil route gates: the estimated forward error eps ||H||_F / omega_min must stay below
+// kPencilGate (1e-11: the measured error stays near or below this estimate, so a factor of
+// ten below the 1e-10 parity tolerance), and ||C||_F ||L^-1||_F^2 >= kappa_2(C) below
+// kPencilKappaMax; other objects take the LU route.
+constexpr double kPencilGate = 1e-11;
+constexpr double kPencilKappaMax = 1e6;
+
 // Dynamic shared memory per CTA: an SM's shared memory divided by the CTAs that
 // co-reside, so that they fill each other's barrier waits (minus the reservation).
 size_t sweep_budget(const mrom_ctx* h, int cfg) {
@@ -155,6 +162,111 @@ RomDev rom_record(const mrom_rom* m) {
     off += m->r_dirs[i];
   }
   return d;
+}
+
+// Pencil route of a plan: eligible objects (one basis shared by the directions), their
+// per-object data, the preparation workspace and the routing tables (see pencil.cu).
+mrom_status plan_pencil(mrom_ctx* h, mrom_plan plan, const std::vector<RomDev>& objs, size_t lu_budget) {
+  const int n_obj = plan->n_obj, n_w = plan->n_w;
+  std::vector<int> elig;
+  for (int o = 0; o < n_obj; ++o)
+    if (!objs[o].per_dir) elig.push_back(o);
+  if (elig.empty()) return MROM_OK;
+  std::stable_sort(elig.begin(), elig.end(), [&](int a, int b) { return objs[a].r > objs[b].r; });
+  // frequency groups of 32 per task: as many as the shared memory holds (one CTA per SM),
+  // a power of two up to 8, and no more than the frequencies need
+  const size_t budget = h->smem_optin - 4096;
+  int need = 1;
+  while (need < 8 && 32 * need < n_w) need *= 2;
+  std::vector<int> spen(elig.size());
+  std::vector<PencilDev> pens(n_obj);
+  std::memset(pens.data(), 0, n_obj * sizeof(PencilDev));
+  size_t data_elems = 0, smem = 0;
+  int rmax = 1;
+  std::vector<size_t> off(n_obj, 0);
+  for (size_t k = 0; k < elig.size(); ++k) {
+    const int o = elig[k], r = objs[o].r;
+    int F = 8;
+    while (F > 1 && (F > need || pencil_sweep_smem_bytes(r, F) > budget)) F /= 2;
+    spen[k] = 32 * F;
+    pens[o].F = F;
+    smem = std::max(smem, pencil_sweep_smem_bytes(r, F));
+    rmax = std::max(rmax, r);
+    off[o] = data_elems;
+    const size_t tri = (size_t)r * (r + 1) / 2;
+    data_elems += (size_t)(r + 1) / 2 + 3 * (size_t)r;            // lam (in complex slots), beta
+    if (objs[o].has_cert) data_elems += 6 * (size_t)r + 3 * tri;  // gsh, Gh
+    if (objs[o].Me) data_elems += tri;                            // Eh
+  }
+  // LU order (all objects, descending cost) with their LU task shapes
+  std::vector<int> order_lu(n_obj);
+  std::iota(order_lu.begin(), order_lu.end(), 0);
+  std::stable_sort(order_lu.begin(), order_lu.end(), [&](int a, int b) { return objs[a].r > objs[b].r; });
+  std::vector<int2> lu_info(n_obj);
+  for (int k = 0; k < n_obj; ++k) {
+    const int r = objs[order_lu[k]].r;
+    const size_t per_s = sweep_fp64_bytes_per_system(r, true);
+    const bool in_smem = per_s <= lu_budget;
+    const int S = in_smem ? std::max(1, std::min<int>(n_w, (int)(lu_budget / per_s))) : 1;
+    lu_info[k] = make_int2(S, in_smem ? 0 : 1);
+  }
+  plan->prep_grid = std::min<int>((int)elig.size(), 2 * h->num_sms);
+  plan->prep_ws_elems = 3 * (size_t)rmax * rmax;
+  plan->pen_grid = h->num_sms;
+  plan->pen_smem = smem;
+  // one allocation: pens, order_pen, spen, order_lu, lu_info, two tables, pen_ok,
+  // counters, per-object data, preparation workspace
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b_pens = al(n_obj * sizeof(PencilDev)), b_op = al(elig.size() * sizeof(int)),
+               b_sp = al(elig.size() * sizeof(int)), b_ol = al(n_obj * sizeof(int)),
+               b_li = al(n_obj * sizeof(int2)), b_tab = al((n_obj + 1) * sizeof(SweepTask)),
+               b_ok = al(n_obj * sizeof(int)), b_cnt = al(8 * sizeof(int)),
+               b_data = al(data_elems * sizeof(double2)),
+               b_ws = al(plan->prep_ws_elems * plan->prep_grid * sizeof(double2));
+  const size_t total = b_pens + b_op + b_sp + b_ol + b_li + 2 * b_tab + b_ok + b_cnt + b_data + b_ws;
+  void* blk = nullptr;
+  cudaError_t e = cudaMallocAsync(&blk, total, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_plan_create: pencil allocation");
+  plan->pen_block = blk;
+  char* p = static_cast<char*>(blk);
+  plan->d_pens = reinterpret_cast<PencilDev*>(p); p += b_pens;
+  plan->d_order_pen = reinterpret_cast<int*>(p); p += b_op;
+  plan->d_spen = reinterpret_cast<int*>(p); p += b_sp;
+  plan->d_order_lu = reinterpret_cast<int*>(p); p += b_ol;
+  plan->d_lu_info = reinterpret_cast<int2*>(p); p += b_li;
+  plan->d_table_pen = reinterpret_cast<SweepTask*>(p); p += b_tab;
+  plan->d_table_lu = reinterpret_cast<SweepTask*>(p); p += b_tab;
+  plan->d_pen_ok = reinterpret_cast<int*>(p); p += b_ok;
+  plan->d_counters = reinterpret_cast<int*>(p); p += b_cnt;
+  double2* data = reinterpret_cast<double2*>(p); p += b_data;
+  plan->d_prep_ws = reinterpret_cast<double2*>(p);
+  for (const int o : elig) {
+    const int r = objs[o].r;
+    const size_t tri = (size_t)r * (r + 1) / 2;
+    double2* q = data + off[o];
+    pens[o].lam = reinterpret_cast<double*>(q); q += (r + 1) / 2;
+    pens[o].beta = q; q += 3 * (size_t)r;
+    if (objs[o].has_cert) {
+      pens[o].gsh = q; q += 6 * (size_t)r;
+      pens[o].Gh = q; q += 3 * tri;
+    }
+    if (objs[o].Me) pens[o].Eh = q;
+  }
+  plan->n_pen = (int)elig.size();
+  e = cudaMemcpyAsync(plan->d_pens, pens.data(), n_obj * sizeof(PencilDev), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(plan->d_order_pen, elig.data(), elig.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(plan->d_spen, spen.data(), spen.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(plan->d_order_lu, order_lu.data(), n_obj * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(plan->d_lu_info, lu_info.data(), n_obj * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
+  // (pageable sources are staged before these calls return, so the host vectors may go)
+  if (e == cudaSuccess) e = cudaMemsetAsync(plan->d_pen_ok, 0, b_ok, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_plan_create: pencil upload");
+  return MROM_OK;
 }
 
 }  // namespace mrom
@@ -240,6 +352,13 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
     delete plan;
     return cuda_fail(h, e, "mrom_plan_create: upload");
   }
+  if (h->solver == MROM_SOLVER_AUTO) {
+    const mrom_status ps = plan_pencil(h, plan, objs, budget);
+    if (ps != MROM_OK) {
+      mrom_plan_destroy(plan);
+      return ps;
+    }
+  }
   *out = plan;
   return MROM_OK;
 }
@@ -247,6 +366,9 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
 extern "C" mrom_status mrom_plan_destroy(mrom_plan plan) {
   if (!plan) return MROM_EINVAL;
   cudaSetDevice(plan->ctx->device);
+  if (plan->pen_block) cudaFreeAsync(plan->pen_block, plan->ctx->stream);
+  for (auto& ev : plan->ev)
+    if (ev) cudaEventDestroy(ev);
   cudaFreeAsync(plan->d_workspace ? static_cast<void*>(plan->d_workspace) : static_cast<void*>(plan->d_objs),
                 plan->ctx->stream);
   delete plan;
@@ -265,18 +387,98 @@ mrom_status run_plan(mrom_plan plan, const double* omega, int32_t omega_stride, 
     return fail(h, MROM_EINVAL, "sweep: Delta requested but an object has no Gram matrix");
   if (!R && !I && !Delta) return MROM_OK;
   cudaSetDevice(h->device);
+  auto mark = [&](int k) {
+    if (plan->timing) cudaEventRecord(plan->ev[k], h->stream);
+  };
+  if (plan->n_pen > 0) {
+    // pencil route: per-object preparation, device-side routing, then both sweep kernels
+    // (each over its own table; an empty table ends the kernel at once)
+    cudaError_t e = cudaMemsetAsync(plan->d_counters, 0, 3 * sizeof(int), h->stream);
+    mark(0);
+    if (e == cudaSuccess)
+      e = launch_pencil_prep(plan->d_objs, plan->d_pens, plan->d_order_pen, plan->n_pen, plan->d_counters, omega,
+                             omega_stride, plan->n_w, s_sigma, plan->d_pen_ok, plan->d_prep_ws, plan->prep_ws_elems,
+                             plan->prep_grid, kPencilGate, kPencilKappaMax, h->stream);
+    mark(1);
+    if (e == cudaSuccess)
+      e = launch_pencil_route(plan->d_pen_ok, plan->d_order_pen, plan->d_spen, plan->n_pen, plan->d_order_lu,
+                              plan->d_lu_info, plan->n_obj, plan->n_w, plan->d_table_pen, plan->d_table_lu,
+                              plan->d_counters + 3, h->stream);
+    mark(2);
+    if (e == cudaSuccess)
+      e = launch_pencil_sweep(plan->d_objs, plan->d_pens, plan->d_table_pen, plan->d_counters + 1, omega,
+                              omega_stride, s_sigma, R, I, Delta, h->d_status, plan->n_w, plan->pen_grid,
+                              plan->pen_smem, h->stream);
+    mark(3);
+    if (e == cudaSuccess)
+      e = launch_sweep_fp64_routed(plan->cfg, plan->d_objs, plan->d_table_lu, plan->d_counters + 2, omega,
+                                   omega_stride, s_sigma, R, I, Delta, h->d_status, plan->n_w, plan->grid,
+                                   plan->smem_bytes, plan->d_workspace, plan->ws_elems, h->stream);
+    mark(4);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sweep launch");
+    h->launches += 4;
+    return MROM_OK;
+  }
+  mark(0);
+  mark(1);
+  mark(2);
+  mark(3);
   cudaError_t e = sweep_fp64_configure(plan->cfg, plan->smem_bytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(plan->d_counter, 0, sizeof(int), h->stream);
   if (e == cudaSuccess)
     e = launch_sweep_fp64(plan->cfg, plan->d_objs, plan->d_tasks, plan->n_tasks, plan->d_counter, omega, omega_stride,
                           s_sigma, R, I, Delta, h->d_status, plan->n_w, plan->grid, plan->smem_bytes,
                           plan->d_workspace, plan->ws_elems, h->stream);
+  mark(4);
   if (e != cudaSuccess) return cuda_fail(h, e, "sweep launch");
   ++h->launches;
   return MROM_OK;
 }
 
 }  // namespace
+
+extern "C" mrom_status mrom_plan_solver_counts(mrom_plan plan, int32_t* n_pencil, int32_t* n_lu) {
+  if (!plan) return MROM_EINVAL;
+  mrom_ctx* h = plan->ctx;
+  int c[2] = {0, plan->n_obj};
+  if (plan->n_pen > 0) {
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaMemcpyAsync(c, plan->d_counters + 3, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_plan_solver_counts");
+  }
+  if (n_pencil) *n_pencil = c[0];
+  if (n_lu) *n_lu = c[1];
+  return MROM_OK;
+}
+
+extern "C" mrom_status mrom_plan_timing(mrom_plan plan, int32_t enable, float* stage_ms) {
+  if (!plan) return MROM_EINVAL;
+  mrom_ctx* h = plan->ctx;
+  cudaSetDevice(h->device);
+  if (enable && !plan->timing) {
+    for (auto& ev : plan->ev) {
+      const cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return cuda_fail(h, e, "mrom_plan_timing: event");
+    }
+    plan->timing = true;
+    return MROM_OK;
+  }
+  if (!stage_ms) return MROM_OK;
+  if (!plan->timing) return fail(h, MROM_EINVAL, "mrom_plan_timing: timing is not enabled");
+  cudaError_t e = cudaEventSynchronize(plan->ev[4]);
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&stage_ms[k], plan->ev[k], plan->ev[k + 1]);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_plan_timing: elapsed time");
+  return MROM_OK;
+}
+
+extern "C" mrom_status mrom_set_solver(mrom_handle h, mrom_solver solver) {
+  if (!h) return MROM_EINVAL;
+  if (solver != MROM_SOLVER_AUTO && solver != MROM_SOLVER_LU)
+    return fail(h, MROM_EINVAL, "mrom_set_solver: MROM_SOLVER_AUTO or MROM_SOLVER_LU");
+  h->solver = solver;
+  return MROM_OK;
+}
 
 extern "C" mrom_status mrom_plan_sweep(mrom_plan plan, const double* omega, int32_t omega_stride, double* R,
                                        double* I, double* Delta) {
@@ -324,6 +526,8 @@ extern "C" mrom_status mrom_tune(mrom_handle h, const mrom_rom_t* roms, int32_t 
   bool cert = true;
   for (auto* r : sample) cert = cert && r->has_cert;
   const int saved = h->sweep_cfg;
+  const int saved_solver = h->solver;
+  h->solver = MROM_SOLVER_LU;  // the configurations are those of the LU kernel
   int best = -1;
   float best_ms = 0.f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -350,6 +554,7 @@ extern "C" mrom_status mrom_tune(mrom_handle h, const mrom_rom_t* roms, int32_t 
   cudaEventDestroy(e1);
   cudaStreamSynchronize(h->stream);
   cudaFree(buf);
+  h->solver = saved_solver;
   if (e != cudaSuccess) {
     h->sweep_cfg = saved;
     return cuda_fail(h, e, "mrom_tune");

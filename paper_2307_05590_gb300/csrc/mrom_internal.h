@@ -44,6 +44,22 @@ struct RomDev {
   int blk_hi[3];
 };
 
+// Per-object data of the pencil route (pencil.cu), computed on the device by the
+// preparation kernel of every sweep: eigenvalues lam (r), beta = V^H B (r x 3),
+// gsh[k][q] = (gs_q V)[k] for the certificate rows of G (r x 6, or null), the transformed
+// Gram blocks V^H G_X V for X = KK, CC, S interleaved per entry of the packed lower
+// triangle (3 r (r+1)/2, or null) and V^H Me V (packed lower, or null).  F: frequency
+// groups of 32 per sweep task.
+struct PencilDev {
+  double* lam;
+  double2* beta;
+  double2* gsh;
+  double2* Gh;
+  double2* Eh;
+  int F;
+  int pad;
+};
+
 // One unit of work: S consecutive frequencies of one object.
 struct SweepTask {
   int obj;
@@ -65,6 +81,7 @@ struct mrom_ctx {
   int64_t launches = 0;
   int sweep_cfg = -1;             // launch configuration for sweeps (-1: default)
   int projection_precision = 0;   // MROM_FP64 or MROM_MIXED for mrom_project's K U and Gram products
+  int solver = 0;                 // MROM_SOLVER_AUTO or MROM_SOLVER_LU for plans and sweeps
   mrom_status pending = MROM_OK;  // host-detected asynchronous error
   std::string last_error;
 };
@@ -99,6 +116,26 @@ struct mrom_plan_s {
   int* d_counter = nullptr;
   double2* d_workspace = nullptr;   // grid x ws_elems complex128, for tasks whose matrices are global
   size_t ws_elems = 0;
+  // pencil route (n_pen > 0): eligible objects, their data, routing tables and counters
+  int n_pen = 0;
+  void* pen_block = nullptr;        // one stream-ordered allocation for everything below
+  mrom::PencilDev* d_pens = nullptr;
+  int* d_order_pen = nullptr;       // eligible objects, descending r
+  int* d_spen = nullptr;            // frequencies per pencil task, same order
+  int* d_order_lu = nullptr;        // all objects in LU cost order
+  int2* d_lu_info = nullptr;        // {S, matrices-in-global} per LU-order entry
+  mrom::SweepTask* d_table_pen = nullptr;
+  mrom::SweepTask* d_table_lu = nullptr;
+  int* d_pen_ok = nullptr;
+  int* d_counters = nullptr;        // prep, pencil sweep, LU sweep, then the two route counts
+  double2* d_prep_ws = nullptr;
+  size_t prep_ws_elems = 0;
+  int prep_grid = 0;
+  int pen_grid = 0;
+  size_t pen_smem = 0;
+  // optional stage timing (mrom_plan_timing): events around prep, route, pencil sweep, LU sweep
+  bool timing = false;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace mrom {
@@ -129,6 +166,28 @@ cudaError_t launch_sweep_fp64_implicit(int cfg, const RomDev* objs, const SweepT
                                        double* I, double* Delta, int* status, int n_w, int grid,
                                        size_t smem_bytes, double2* workspace, size_t ws_elems,
                                        cudaStream_t stream);
+// Routed variant: the task table comes from the routing kernel and its header holds the
+// task count (table[0].w0); s_sigma as in launch_sweep_fp64.
+cudaError_t launch_sweep_fp64_routed(int cfg, const RomDev* objs, const SweepTask* table, int* counter,
+                                     const double* omega, int omega_stride, const double* s_sigma, double* R,
+                                     double* I, double* Delta, int* status, int n_w, int grid, size_t smem_bytes,
+                                     double2* workspace, size_t ws_elems, cudaStream_t stream);
+
+// Pencil route (pencil.cu).
+size_t pencil_sweep_smem_bytes(int r, int F);
+int pencil_threads();
+cudaError_t launch_pencil_prep(const RomDev* objs, const PencilDev* pens, const int* order, int n_elig,
+                               int* counter, const double* omega, int omega_stride, int n_w,
+                               const double* s_sigma, int* pen_ok, double2* ws, size_t ws_elems, int grid,
+                               double gate, double kappa_max, cudaStream_t stream);
+cudaError_t launch_pencil_route(const int* pen_ok, const int* order_pen, const int* spen, int n_pen,
+                                const int* order_lu, const int2* lu_info, int n_lu, int n_w, SweepTask* table_pen,
+                                SweepTask* table_lu, int* counts, cudaStream_t stream);
+cudaError_t launch_pencil_sweep(const RomDev* objs, const PencilDev* pens, const SweepTask* table, int* counter,
+                                const double* omega, int omega_stride, const double* s_sigma, double* R,
+                                double* I, double* Delta, int* status, int n_w, int grid, size_t smem_bytes,
+                                cudaStream_t stream);
+
 // Builds the RomDev record of an object (api.cu).
 RomDev rom_record(const mrom_rom* m);
 size_t sweep_budget_bytes(const mrom_ctx* h, int cfg);

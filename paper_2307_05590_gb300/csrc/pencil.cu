@@ -1,0 +1,789 @@
+// Batched sweep through the Hermitian pencil (K + Me, C) of each reduced object.
+//
+// The reduced system of Eq. (17), (K' - i omega C) p_i = i omega b_i with K' = K + Me
+// Hermitian positive semi-definite and C Hermitian positive definite, is diagonalised once
+// per object by the generalised eigenproblem K' V = C V Lambda, V^H C V = I:
+//   C = L L^H (Cholesky), H = L^-1 K' L^-H = Z Lambda Z^H (Householder tridiagonalisation,
+//   then implicit QL on the real symmetric tridiagonal matrix), V = L^-H Z.
+// Then for every frequency, with z_i = V^-1 p_i,
+//   z_ki = i omega beta_ki / (lambda_k - i omega),  beta = V^H B,
+// and the quadratic forms of Eq. (18), Eq. (19) and of the certificate (Lemma 4.2) become
+//   p_i^H K p_j       = z_i^H (Lambda - V^H Me V) z_j
+//   p_i^H C p_j       = z_i^H z_j
+//   b_i^H p_j         = beta_i^H z_j
+//   p_i^H G~(w) p_j   = z_i^H (Gh_KK + w^2 Gh_CC + i w Gh_S) z_j,  Gh_X = V^H G_X V,
+// so a frequency costs O(r^2) (the certificate's Hermitian form, halved) instead of the
+// O(r^3) elimination.  The results are those of the LU path up to rounding: the forward
+// error of the pencil route is about eps ||H|| / omega (the eigen-decomposition is backward
+// stable in H, and |lambda - i omega| >= omega), which the preparation kernel estimates per
+// object from ||H||_F and the smallest frequency of the sweep.  Objects whose estimate
+// exceeds the gate, whose C is not numerically positive definite, or whose QL iteration
+// does not converge are routed to the LU kernel instead (device-side routing, no host sync).
+#include "mrom_internal.h"
+
+#include <cfloat>
+
+namespace mrom {
+namespace {
+
+constexpr int kPT = 256;        // threads per CTA in the preparation and sweep kernels
+constexpr int kPW = kPT / 32;   // warps per CTA
+constexpr int kQlMaxIter = 60;  // QL iterations per eigenvalue before giving up
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cmac(double2 c, double2 a, double2 b) {  // c + a b
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 cmacc(double2 c, double2 a, double2 b) {  // c + conj(a) b
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 cmac_bc(double2 c, double2 a, double2 b) {  // c + a conj(b)
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.y, b.x, fma(-a.x, b.y, c.y)));
+}
+
+// CTA-wide sum / minimum of one value per thread (every thread gets the result; fixed order).
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kPW; ++k) s += red[k];
+  __syncthreads();
+  return s;
+}
+__device__ double block_min(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = red[0];
+#pragma unroll
+  for (int k = 1; k < kPW; ++k) s = fmin(s, red[k]);
+  __syncthreads();
+  return s;
+}
+
+// ------------------------------------------------------------------ preparation
+//
+// One CTA per object (persistent, objects in descending r).  Three r x r complex matrices
+// in the CTA's slice of a global workspace (L2-resident): W0, W1, W2.
+//   W0: C -> L (strictly lower; diagonal in sd) -> X = L^-1 K' -> Q1 -> Z -> G_X V
+//   W1: K' -> H (full Hermitian) -> Householder vectors below the subdiagonal -> V
+//   W2: L^-1 (lower)
+__global__ void __launch_bounds__(kPT)
+pencil_prep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__ pens,
+                   const int* __restrict__ order, int n_elig, int* __restrict__ counter,
+                   const double* __restrict__ omega, int omega_stride, int n_w,
+                   const double* __restrict__ s_sigma, int* __restrict__ pen_ok, double2* __restrict__ ws,
+                   size_t ws_elems, double gate, double kappa_max) {
+  __shared__ double sd[MROM_MAX_R], se[MROM_MAX_R], stau[MROM_MAX_R];
+  __shared__ double rc[MROM_MAX_R], rs[MROM_MAX_R];
+  __shared__ double2 salpha[MROM_MAX_R], sph[MROM_MAX_R];
+  __shared__ double red[kPW];
+  __shared__ int s_task, s_nrot, s_m, s_done, s_fail;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  double2* W0 = ws + (size_t)blockIdx.x * ws_elems;
+
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();
+    if (t >= n_elig) break;
+    const int o = order[t];
+    const RomDev& ob = objs[o];
+    const PencilDev& pd = pens[o];
+    const int r = ob.r, rr = r * r;
+    double2* W1 = W0 + rr;
+    double2* W2 = W1 + rr;
+
+    // ---- smallest frequency of this object's sweep (for the accuracy gate)
+    const double ssig = s_sigma ? s_sigma[o] : 1.0;
+    double wmin = INFINITY;
+    for (int k = tid; k < n_w; k += kPT) {
+      const double w = omega[(size_t)o * omega_stride + k] * ssig;
+      if (w > 0.0 && isfinite(w)) wmin = fmin(wmin, w);
+    }
+    wmin = block_min(wmin, red);
+
+    // ---- load C (W0) and K' = K + Me (W1)
+    double cn = 0.0;
+    for (int idx = tid; idx < rr; idx += kPT) {
+      const double2 c = ob.C[idx];
+      W0[idx] = c;
+      cn += c.x * c.x + c.y * c.y;
+      double2 k = ob.K[idx];
+      if (ob.Me) k = cadd(k, ob.Me[idx]);
+      W1[idx] = k;
+    }
+    cn = block_sum(cn, red);  // (its barriers publish W0, W1)
+
+    // ---- 1. Cholesky C = L L^H, right-looking; L strictly lower in W0, diagonal in sd
+    bool ok = true;
+    for (int k = 0; k < r; ++k) {
+      const double d = W0[k * r + k].x;
+      if (!(d > 0.0) || !isfinite(d)) {  // the same value for every thread
+        ok = false;
+        break;
+      }
+      const double l = sqrt(d), il = 1.0 / l;
+      if (tid == 0) sd[k] = l;
+      for (int i = k + 1 + tid; i < r; i += kPT) {
+        const double2 v = W0[i * r + k];
+        W0[i * r + k] = make_double2(v.x * il, v.y * il);
+      }
+      __syncthreads();
+      const int m = r - k - 1;
+      for (int idx = tid; idx < m * m; idx += kPT) {
+        const int i = k + 1 + idx / m, j = k + 1 + idx % m;
+        if (j > i) continue;
+        const double2 li = W0[i * r + k], lj = W0[j * r + k];
+        double2 a = W0[i * r + j];
+        // a - li conj(lj)
+        a.x -= fma(li.x, lj.x, li.y * lj.y);
+        a.y -= fma(li.y, lj.x, -li.x * lj.y);
+        W0[i * r + j] = a;
+      }
+      __syncthreads();
+    }
+
+    // ---- 2. L^-1 (lower) in W2, row by row
+    double ln = 0.0;
+    if (ok) {
+      for (int i = 0; i < r; ++i) {
+        const double idi = 1.0 / sd[i];
+        for (int j = tid; j <= i; j += kPT) {
+          double2 v;
+          if (j == i) {
+            v = make_double2(idi, 0.0);
+          } else {
+            double2 s = make_double2(0.0, 0.0);
+            for (int k = j; k < i; ++k) s = cmac(s, W0[i * r + k], W2[k * r + j]);
+            v = make_double2(-s.x * idi, -s.y * idi);
+          }
+          W2[i * r + j] = v;
+          ln += v.x * v.x + v.y * v.y;
+        }
+        __syncthreads();
+      }
+    }
+    ln = block_sum(ln, red);
+    ok = ok && (sqrt(cn) * ln <= kappa_max);
+
+    // ---- 3. X = L^-1 K' (W0)  and  4. H = X L^-H (W1, lower then mirrored)
+    double hn = 0.0;
+    if (ok) {
+      for (int idx = tid; idx < rr; idx += kPT) {
+        const int i = idx / r, j = idx - (idx / r) * r;
+        double2 s = make_double2(0.0, 0.0);
+        for (int k = 0; k <= i; ++k) s = cmac(s, W2[i * r + k], W1[k * r + j]);
+        W0[idx] = s;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < rr; idx += kPT) {
+        const int i = idx / r, j = idx - (idx / r) * r;
+        if (j > i) continue;
+        double2 s = make_double2(0.0, 0.0);
+        for (int k = 0; k <= j; ++k) s = cmac_bc(s, W0[i * r + k], W2[j * r + k]);
+        if (i == j) s.y = 0.0;
+        W1[idx] = s;
+        hn += (i == j ? 1.0 : 2.0) * (s.x * s.x + s.y * s.y);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < rr; idx += kPT) {
+        const int i = idx / r, j = idx - (idx / r) * r;
+        if (j > i) {
+          const double2 v = W1[j * r + i];
+          W1[idx] = make_double2(v.x, -v.y);
+        }
+      }
+    }
+    hn = block_sum(hn, red);
+    ok = ok && (DBL_EPSILON * sqrt(hn) <= gate * wmin);
+
+    // ---- 5. Householder tridiagonalisation of H (W1): for column k, x = H[k+1:, k],
+    // alpha = -phase(x_0) ||x||, v = x - alpha e_1, tau = 1 / (||x|| (||x|| + |x_0|)),
+    // P = I - tau v v^H; H_sub <- P H_sub P = H_sub - v w^H - w v^H with
+    // p = tau H_sub v, w = p - (tau/2)(v^H p) v.  v is kept in column k below the diagonal.
+    if (ok) {
+      double2* pv = W0;  // p (length r) in W0's first row; W0 is free until step 6
+      for (int k = 0; k + 2 < r; ++k) {
+        const int m = r - k - 1;
+        double nx2 = 0.0;
+        for (int i = tid; i < m; i += kPT) {
+          const double2 x = W1[(k + 1 + i) * r + k];
+          nx2 += x.x * x.x + x.y * x.y;
+        }
+        nx2 = block_sum(nx2, red);
+        if (tid == 0) sd[k] = W1[k * r + k].x;
+        if (!(nx2 > 0.0)) {  // column already reduced
+          if (tid == 0) {
+            stau[k] = 0.0;
+            salpha[k] = make_double2(0.0, 0.0);
+          }
+          continue;
+        }
+        const double nx = sqrt(nx2);
+        const double2 x0 = W1[(k + 1) * r + k];
+        const double a0 = hypot(x0.x, x0.y);
+        const double2 ph = a0 > 0.0 ? make_double2(x0.x / a0, x0.y / a0) : make_double2(1.0, 0.0);
+        const double tau = 1.0 / (nx * (nx + a0));
+        // v_0 = x_0 - alpha = ph (|x_0| + ||x||); the other entries of v are those of x
+        __syncthreads();  // every thread has read x_0 before it is overwritten
+        if (tid == 0) {
+          W1[(k + 1) * r + k] = make_double2(ph.x * (a0 + nx), ph.y * (a0 + nx));
+          stau[k] = tau;
+          salpha[k] = make_double2(-ph.x * nx, -ph.y * nx);
+        }
+        __syncthreads();
+        // p = tau H_sub v: one warp per row, lanes along the row
+        for (int i = warp; i < m; i += kPW) {
+          double2 s = make_double2(0.0, 0.0);
+          const double2* hrow = W1 + (size_t)(k + 1 + i) * r + (k + 1);
+          for (int j = lane; j < m; j += 32) s = cmac(s, hrow[j], W1[(k + 1 + j) * r + k]);
+          for (int off = 16; off > 0; off >>= 1) {
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+          }
+          if (lane == 0) pv[i] = make_double2(tau * s.x, tau * s.y);
+        }
+        __syncthreads();
+        // K = (tau/2) v^H p (real for Hermitian H_sub)
+        double kr = 0.0;
+        for (int i = tid; i < m; i += kPT) {
+          const double2 v = W1[(k + 1 + i) * r + k], p = pv[i];
+          kr += fma(v.x, p.x, v.y * p.y);
+        }
+        kr = 0.5 * tau * block_sum(kr, red);
+        // H_sub -= v w^H + w v^H, w = p - K v
+        for (int idx = tid; idx < m * m; idx += kPT) {
+          const int i = idx / m, j = idx - (idx / m) * m;
+          const double2 vi = W1[(k + 1 + i) * r + k], vj = W1[(k + 1 + j) * r + k];
+          const double2 pi = pv[i], pj = pv[j];
+          const double2 wi = make_double2(fma(-kr, vi.x, pi.x), fma(-kr, vi.y, pi.y));
+          const double2 wj = make_double2(fma(-kr, vj.x, pj.x), fma(-kr, vj.y, pj.y));
+          double2 a = W1[(k + 1 + i) * r + (k + 1 + j)];
+          // a - vi conj(wj) - wi conj(vj)
+          a.x -= fma(vi.x, wj.x, vi.y * wj.y) + fma(wi.x, vj.x, wi.y * vj.y);
+          a.y -= fma(vi.y, wj.x, -vi.x * wj.y) + fma(wi.y, vj.x, -wi.x * vj.y);
+          if (i == j) a.y = 0.0;
+          W1[(k + 1 + i) * r + (k + 1 + j)] = a;
+        }
+        __syncthreads();
+      }
+      // the last 2 x 2 block is already tridiagonal
+      if (tid == 0) {
+        for (int k = (r >= 2 ? r - 2 : 0); k < r; ++k) sd[k] = W1[k * r + k].x;
+        if (r >= 2) {
+          salpha[r - 2] = W1[(r - 1) * r + (r - 2)];
+          stau[r - 2] = 0.0;
+        }
+      }
+      __syncthreads();
+
+      // ---- 6. Q1 = P_0 P_1 ... P_{r-3} (W0), backward accumulation on the trailing block
+      for (int idx = tid; idx < rr; idx += kPT) {
+        const int i = idx / r, j = idx - (idx / r) * r;
+        W0[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      }
+      __syncthreads();
+      for (int k = r - 3; k >= 0; --k) {
+        const double tau = stau[k];
+        if (tau == 0.0) continue;
+        const int m = r - k - 1;
+        // u_j = sum_i conj(v_i) Q[k+1+i][k+1+j], then Q_sub -= tau v u
+        for (int j = tid; j < m; j += kPT) {
+          double2 s = make_double2(0.0, 0.0);
+          for (int i = 0; i < m; ++i) s = cmacc(s, W1[(k + 1 + i) * r + k], W0[(k + 1 + i) * r + (k + 1 + j)]);
+          sph[j] = make_double2(tau * s.x, tau * s.y);
+        }
+        __syncthreads();
+        for (int idx = tid; idx < m * m; idx += kPT) {
+          const int i = idx / m, j = idx - (idx / m) * m;
+          const double2 v = W1[(k + 1 + i) * r + k], u = sph[j];
+          double2 a = W0[(k + 1 + i) * r + (k + 1 + j)];
+          a.x -= fma(v.x, u.x, -v.y * u.y);
+          a.y -= fma(v.x, u.y, v.y * u.x);
+          W0[(k + 1 + i) * r + (k + 1 + j)] = a;
+        }
+        __syncthreads();
+      }
+
+      // ---- 7. phases: D_0 = 1, D_{k+1} = D_k e_k / |e_k| makes D^H T D real with
+      // off-diagonal |e_k|; Z = Q1 D
+      if (tid == 0) {
+        double2 D = make_double2(1.0, 0.0);
+        sph[0] = D;
+        for (int k = 0; k + 1 < r; ++k) {
+          const double2 e = salpha[k];
+          const double ae = hypot(e.x, e.y);
+          se[k] = ae;
+          if (ae > 0.0) {
+            const double2 u = make_double2(e.x / ae, e.y / ae);
+            D = make_double2(D.x * u.x - D.y * u.y, D.x * u.y + D.y * u.x);
+          }
+          sph[k + 1] = D;
+        }
+        se[r - 1] = 0.0;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < rr; idx += kPT) {
+        const int j = idx - (idx / r) * r;
+        const double2 a = W0[idx], D = sph[j];
+        W0[idx] = make_double2(a.x * D.x - a.y * D.y, a.x * D.y + a.y * D.x);
+      }
+      __syncthreads();
+
+      // ---- 8. implicit QL with Wilkinson-type shifts on (sd, se), se[i] coupling i and i+1.
+      // Thread 0 chases one bulge at a time and records its rotations; then every thread
+      // applies them to its rows of Z (real and imaginary parts independently).
+      int l = 0, iter = 0;  // thread 0's state
+      for (;;) {
+        if (tid == 0) {
+          s_nrot = 0;
+          s_done = 0;
+          s_fail = 0;
+          bool emitted = false;
+          while (!emitted) {
+            if (l >= r) {
+              s_done = 1;
+              break;
+            }
+            int m = l;
+            while (m < r - 1 && fabs(se[m]) > DBL_EPSILON * (fabs(sd[m]) + fabs(sd[m + 1]))) ++m;
+            if (m == l) {
+              ++l;
+              iter = 0;
+              continue;
+            }
+            if (++iter > kQlMaxIter) {
+              s_fail = 1;
+              s_done = 1;
+              break;
+            }
+            double g = (sd[l + 1] - sd[l]) / (2.0 * se[l]);
+            double h = hypot(g, 1.0);
+            g = sd[m] - sd[l] + se[l] / (g + (g >= 0.0 ? h : -h));
+            double s = 1.0, c = 1.0, p = 0.0;
+            int nrot = 0;
+            bool underflow = false;
+            for (int i = m - 1; i >= l; --i) {
+              const double f = s * se[i], b = c * se[i];
+              h = hypot(f, g);
+              se[i + 1] = h;
+              if (h == 0.0) {
+                sd[i + 1] -= p;
+                se[m] = 0.0;
+                underflow = true;
+                break;
+              }
+              s = f / h;
+              c = g / h;
+              g = sd[i + 1] - p;
+              h = (sd[i] - g) * s + 2.0 * c * b;
+              p = s * h;
+              sd[i + 1] = g + p;
+              g = c * h - b;
+              rc[nrot] = c;
+              rs[nrot] = s;
+              ++nrot;
+            }
+            if (!underflow) {
+              sd[l] -= p;
+              se[l] = g;
+              se[m] = 0.0;
+            }
+            s_nrot = nrot;
+            s_m = m;
+            emitted = nrot > 0;
+          }
+        }
+        __syncthreads();
+        if (s_done) break;
+        // rotation q acts on columns (i, i+1), i = m-1-q:
+        //   Z[:, i+1] <- s Z[:, i] + c Z[:, i+1],  Z[:, i] <- c Z[:, i] - s Z[:, i+1]
+        {
+          const int nrot = s_nrot, m = s_m;
+          double* Zr = reinterpret_cast<double*>(W0);
+          for (int rp = tid; rp < 2 * r; rp += kPT) {
+            const int row = rp >> 1, part = rp & 1;
+            double* zrow = Zr + (size_t)2 * row * r + part;
+            double hi = zrow[2 * m];  // column i+1 of the first rotation
+            for (int q = 0; q < nrot; ++q) {
+              const int i = m - 1 - q;
+              const double lo = zrow[2 * i];
+              const double c = rc[q], s = rs[q];
+              zrow[2 * (i + 1)] = fma(s, lo, c * hi);
+              hi = fma(c, lo, -s * hi);
+            }
+            zrow[2 * (m - nrot)] = hi;
+          }
+        }
+        __syncthreads();
+      }
+      ok = ok && !s_fail;
+      __syncthreads();
+    }
+
+    // ---- 9. V = L^-H Z (W1): V[i][j] = sum_{k >= i} conj(Linv[k][i]) Z[k][j]
+    if (ok) {
+      for (int idx = tid; idx < rr; idx += kPT) {
+        const int i = idx / r, j = idx - (idx / r) * r;
+        double2 s = make_double2(0.0, 0.0);
+        for (int k = i; k < r; ++k) s = cmacc(s, W2[k * r + i], W0[k * r + j]);
+        W1[idx] = s;
+      }
+      __syncthreads();
+      // ---- 10. transformed data
+      for (int k = tid; k < r; k += kPT) pd.lam[k] = sd[k];
+      for (int idx = tid; idx < 3 * r; idx += kPT) {
+        const int k = idx / 3, j = idx - (idx / 3) * 3;
+        double2 s = make_double2(0.0, 0.0);
+        for (int a = 0; a < r; ++a) s = cmacc(s, W1[a * r + k], ob.B[a * 3 + j]);
+        pd.beta[idx] = s;  // beta[k][j] = (V^H B)[k][j]
+      }
+      if (pd.gsh) {
+        for (int idx = tid; idx < 6 * r; idx += kPT) {
+          const int k = idx / 6, q = idx - (idx / 6) * 6;
+          const double2* g = q < 3 ? ob.gsK + (size_t)q * r : ob.gsC + (size_t)(q - 3) * r;
+          double2 s = make_double2(0.0, 0.0);
+          for (int a = 0; a < r; ++a) s = cmac(s, g[a], W1[a * r + k]);
+          pd.gsh[idx] = s;  // gsh[k][q]: (gs_q V)[k]
+        }
+      }
+      // Gh_X = V^H G_X V for X = KK, CC, S (interleaved, packed lower triangle) and E = V^H Me V
+      const int nmat = (pd.Gh ? 3 : 0) + (pd.Eh ? 1 : 0);
+      for (int x = 0; x < nmat; ++x) {
+        const bool gram = pd.Gh != nullptr && x < 3;
+        const double2* G = !gram ? ob.Me : (x == 0 ? ob.GKK : (x == 1 ? ob.GCC : ob.GSk));
+        // Y = G V (W0)
+        for (int idx = tid; idx < rr; idx += kPT) {
+          const int i = idx / r, j = idx - (idx / r) * r;
+          double2 s = make_double2(0.0, 0.0);
+          for (int c = 0; c < r; ++c) s = cmac(s, G[i * r + c], W1[c * r + j]);
+          W0[idx] = s;
+        }
+        __syncthreads();
+        const int ntri = r * (r + 1) / 2;
+        for (int e = tid; e < ntri; e += kPT) {
+          // packed lower triangle: row a holds columns 0..a
+          int a = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+          while ((a + 1) * (a + 2) / 2 <= e) ++a;
+          while (a * (a + 1) / 2 > e) --a;
+          const int b = e - a * (a + 1) / 2;
+          double2 s = make_double2(0.0, 0.0);
+          for (int c = 0; c < r; ++c) s = cmacc(s, W1[c * r + a], W0[c * r + b]);
+          if (gram)
+            pd.Gh[(size_t)e * 3 + x] = s;
+          else
+            pd.Eh[e] = s;
+        }
+        __syncthreads();
+      }
+    }
+    if (tid == 0) pen_ok[o] = ok ? 1 : 0;
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ routing
+//
+// One CTA.  Objects in the plan's cost order; each goes to the pencil table or to the LU
+// table (header entry 0: .obj = entries, .w0 = total tasks; then {object, frequencies per
+// task, first task index, flags}).
+__global__ void pencil_route_kernel(const int* __restrict__ pen_ok, const int* __restrict__ order_pen,
+                                    const int* __restrict__ spen, int n_pen, const int* __restrict__ order_lu,
+                                    const int2* __restrict__ lu_info, int n_lu, int n_w,
+                                    SweepTask* __restrict__ table_pen, SweepTask* __restrict__ table_lu,
+                                    int* __restrict__ counts) {
+  if (threadIdx.x != 0) return;
+  int np = 0, tp = 0;
+  for (int k = 0; k < n_pen; ++k) {
+    const int o = order_pen[k];
+    if (!pen_ok[o]) continue;
+    const int S = spen[k];
+    table_pen[1 + np] = SweepTask{o, tp, S, 0};
+    tp += (n_w + S - 1) / S;
+    ++np;
+  }
+  table_pen[0] = SweepTask{np, tp, 0, 0};
+  int nl = 0, tl = 0;
+  for (int k = 0; k < n_lu; ++k) {
+    const int o = order_lu[k];
+    if (pen_ok[o]) continue;
+    const int2 info = lu_info[k];  // {S, in_global}
+    table_lu[1 + nl] = SweepTask{o, tl, info.x, info.y};
+    tl += (n_w + info.x - 1) / info.x;
+    ++nl;
+  }
+  table_lu[0] = SweepTask{nl, tl, 0, 0};
+  counts[0] = np;
+  counts[1] = nl;
+}
+
+__device__ __forceinline__ SweepTask table_task(const SweepTask* __restrict__ table, int n_w, int t) {
+  const int n = table[0].obj;
+  int lo = 1, hi = n + 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (table[mid].w0 <= t) lo = mid; else hi = mid;
+  }
+  const SweepTask e = table[lo];
+  const int w0 = (t - e.w0) * e.nw;
+  return SweepTask{e.obj, w0, min(e.nw, n_w - w0), e.pad};
+}
+
+// ------------------------------------------------------------------ sweep
+//
+// A task is 32 F consecutive frequencies of one object (F frequency groups of 32, one
+// frequency per lane).  Warp w serves group w % F and the row pairs (a, r-1-a) with
+// pair index = w / F (mod 8 / F), so that every pair costs r + 1 row steps.  Shared
+// memory: z[g][b][j][lane] (the solution in eigen-coordinates), then, after a barrier,
+// the per-warp partial sums for the cross-warp reduction in the same space.
+constexpr int kNQ = 48;  // partial sums per lane: U 9, X 9, Ib 9, E 9, Rl 6, Iz 6
+
+__global__ void __launch_bounds__(kPT, 1)
+pencil_sweep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__ pens,
+                    const SweepTask* __restrict__ table, int* __restrict__ counter,
+                    const double* __restrict__ omega, int omega_stride, const double* __restrict__ s_sigma,
+                    double* __restrict__ Rout, double* __restrict__ Iout, double* __restrict__ Dout,
+                    int* __restrict__ status, int n_w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_task;
+  __shared__ double Ws[kPT];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n_tasks = table[0].w0;
+  double2* zs = reinterpret_cast<double2*>(smem_raw);
+  double* rbuf = reinterpret_cast<double*>(smem_raw);
+
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();
+    if (t >= n_tasks) break;
+    const SweepTask task = table_task(table, n_w, t);
+    const RomDev& ob = objs[task.obj];
+    const PencilDev& pd = pens[task.obj];
+    const int r = ob.r, S = task.nw;
+    const int F = pd.F;               // frequency groups of 32
+    const int wpg = kPW / F;          // warps per group
+    const bool cert = Dout != nullptr && ob.has_cert;
+    const bool has_e = pd.Eh != nullptr;
+    const double ssig = s_sigma ? s_sigma[task.obj] : 1.0;
+
+    // ---- frequencies and z_kj = i w beta_kj / (lambda_k - i w) = u_k beta_kj,
+    //      u = i w (lambda + i w) / (lambda^2 + w^2)
+    for (int s = tid; s < 32 * F; s += kPT) {
+      double w = __longlong_as_double(0x7ff8000000000000LL);
+      if (s < S) {
+        w = omega[(size_t)task.obj * omega_stride + task.w0 + s] * ssig;
+        if (!(w > 0.0) || !isfinite(w)) {
+          atomicOr(status, kStatusBadOmega);
+          w = __longlong_as_double(0x7ff8000000000000LL);
+        }
+      }
+      Ws[s] = w;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < r * 32 * F; idx += kPT) {
+      const int g = idx / (r * 32);
+      const int rem = idx - g * r * 32;
+      const int k = rem >> 5, ln = rem & 31;
+      const double w = Ws[g * 32 + ln];
+      const double lam = pd.lam[k];
+      const double den = 1.0 / fma(lam, lam, w * w);
+      const double2 u = make_double2(-w * w * den, w * lam * den);
+      double2* zk = zs + ((size_t)(g * r + k) * 3) * 32 + ln;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double2 b = pd.beta[k * 3 + j];
+        zk[j * 32] = make_double2(fma(u.x, b.x, -u.y * b.y), fma(u.x, b.y, u.y * b.x));
+      }
+    }
+    __syncthreads();
+
+    // ---- row pairs
+    const int g = warp % F;
+    const int q0 = warp / F;
+    const double w = Ws[g * 32 + lane], w2 = w * w;
+    const double2* zg = zs + (size_t)g * r * 3 * 32 + lane;
+    double aU[9], aX[9], aB[9], aE[9], aR[6], aI[6];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) aU[q] = aX[q] = aB[q] = aE[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) aR[q] = aI[q] = 0.0;
+    const int half = (r + 1) / 2;
+    for (int pr = q0; pr < half; pr += wpg) {
+      for (int side = 0; side < 2; ++side) {
+        const int a = side == 0 ? pr : r - 1 - pr;
+        if (side == 1 && a == pr) break;
+        double2 za[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) za[j] = zg[(a * 3 + j) * 32];
+        // O(r) terms of row a
+        const double lam = pd.lam[a];
+        {
+          int q = 0;
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = i; j < 3; ++j, ++q) {
+              const double v = fma(za[i].x, za[j].x, za[i].y * za[j].y);
+              aR[q] = fma(lam, v, aR[q]);
+              aI[q] += v;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const double2 b = pd.beta[a * 3 + i];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) aB[i * 3 + j] = fma(b.x, za[j].x, fma(b.y, za[j].y, aB[i * 3 + j]));
+        }
+        if (cert) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const double2 gk = pd.gsh[a * 6 + i], gc = pd.gsh[a * 6 + 3 + i];
+            // coefficient i w gk + w^2 gc; the real part of its product with z_j
+            const double cx = fma(-w, gk.y, w2 * gc.x), cy = fma(w, gk.x, w2 * gc.y);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) aX[i * 3 + j] = fma(cx, za[j].x, fma(-cy, za[j].y, aX[i * 3 + j]));
+          }
+        }
+        // Hermitian forms, halved: y_j = sum_{b<a} M_ab z_bj + M_aa z_aj / 2
+        if (cert || has_e) {
+          double2 y[3], ye[3];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) y[j] = ye[j] = make_double2(0.0, 0.0);
+          const size_t row0 = (size_t)a * (a + 1) / 2;
+          for (int b = 0; b <= a; ++b) {
+            double2 zb[3];
+            if (b < a) {
+#pragma unroll
+              for (int j = 0; j < 3; ++j) zb[j] = zg[(b * 3 + j) * 32];
+            } else {
+#pragma unroll
+              for (int j = 0; j < 3; ++j) zb[j] = make_double2(0.5 * za[j].x, 0.5 * za[j].y);
+            }
+            if (cert) {
+              const double2* gh = pd.Gh + (row0 + b) * 3;
+              const double2 kk = gh[0], cc = gh[1], sk = gh[2];
+              // G~_ab = KK + w^2 CC + i w S
+              const double2 gt = make_double2(fma(w2, cc.x, fma(-w, sk.y, kk.x)), fma(w2, cc.y, fma(w, sk.x, kk.y)));
+#pragma unroll
+              for (int j = 0; j < 3; ++j) y[j] = cmac(y[j], gt, zb[j]);
+            }
+            if (has_e) {
+              const double2 e = pd.Eh[row0 + b];
+#pragma unroll
+              for (int j = 0; j < 3; ++j) ye[j] = cmac(ye[j], e, zb[j]);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              aU[i * 3 + j] = fma(za[i].x, y[j].x, fma(za[i].y, y[j].y, aU[i * 3 + j]));
+              aE[i * 3 + j] = fma(za[i].x, ye[j].x, fma(za[i].y, ye[j].y, aE[i * 3 + j]));
+            }
+        }
+      }
+    }
+    __syncthreads();  // z is no longer read: its space takes the partial sums
+    {
+      double* rb = rbuf + (size_t)warp * kNQ * 32 + lane;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        rb[q * 32] = aU[q];
+        rb[(9 + q) * 32] = aX[q];
+        rb[(18 + q) * 32] = aB[q];
+        rb[(27 + q) * 32] = aE[q];
+      }
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        rb[(36 + q) * 32] = aR[q];
+        rb[(42 + q) * 32] = aI[q];
+      }
+    }
+    __syncthreads();
+    // ---- outputs: (frequency, ij) pairs; partial sums of the group's warps in fixed order
+    for (int idx = tid; idx < S * 9; idx += kPT) {
+      const int s = idx / 9, ij = idx - (idx / 9) * 9;
+      const int i = ij / 3, j = ij - (ij / 3) * 3;
+      const int gg = s >> 5, ln = s & 31;
+      auto sum = [&](int q) {
+        double v = 0.0;
+        for (int k = 0; k < wpg; ++k) v += rbuf[((size_t)(gg + k * F) * kNQ + q) * 32 + ln];
+        return v;
+      };
+      auto sym = [](int a, int b) {  // packed index of (min, max) in the 6 symmetric sums
+        const int lo = a < b ? a : b, hi = a < b ? b : a;
+        return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+      };
+      const double wv = Ws[s];
+      const size_t o = ((size_t)task.obj * n_w + task.w0 + s) * 9 + ij;
+      if (Rout) {
+        const double kf = sum(36 + sym(i, j)) - (sum(27 + i * 3 + j) + sum(27 + j * 3 + i));
+        Rout[o] = fma(-0.25 * ob.alpha3, kf, ob.N0[ij]);
+      }
+      if (Iout)
+        Iout[o] = 0.25 * ob.alpha3 * wv *
+                  (ob.c00[ij] + sum(42 + sym(i, j)) + sum(18 + i * 3 + j) + sum(18 + j * 3 + i));
+      if (Dout) {
+        if (cert) {
+          const double ww = wv * wv;
+          const double cij = fma(ww, ob.gss[ij], sum(i * 3 + j) + sum(j * 3 + i) + sum(9 + i * 3 + j) +
+                                                     sum(9 + j * 3 + i));
+          const double ni = fma(ww, ob.gss[i * 4], 2.0 * (sum(i * 4) + sum(9 + i * 4)));
+          const double nj = fma(ww, ob.gss[j * 4], 2.0 * (sum(j * 4) + sum(9 + j * 4)));
+          Dout[o] = ob.cert_scale * (ni + nj - cij);
+        } else {
+          Dout[o] = __longlong_as_double(0x7ff8000000000000LL);
+        }
+      }
+    }
+    // the next task's first barrier orders these reads before the space is rewritten
+  }
+}
+
+}  // namespace
+
+size_t pencil_sweep_smem_bytes(int r, int F) {
+  const size_t z = (size_t)32 * F * 3 * r * sizeof(double2);
+  const size_t red = (size_t)kPW * kNQ * 32 * sizeof(double);
+  return z > red ? z : red;
+}
+
+int pencil_threads() { return kPT; }
+
+cudaError_t launch_pencil_prep(const RomDev* objs, const PencilDev* pens, const int* order, int n_elig,
+                               int* counter, const double* omega, int omega_stride, int n_w,
+                               const double* s_sigma, int* pen_ok, double2* ws, size_t ws_elems, int grid,
+                               double gate, double kappa_max, cudaStream_t stream) {
+  pencil_prep_kernel<<<grid, kPT, 0, stream>>>(objs, pens, order, n_elig, counter, omega, omega_stride, n_w,
+                                               s_sigma, pen_ok, ws, ws_elems, gate, kappa_max);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pencil_route(const int* pen_ok, const int* order_pen, const int* spen, int n_pen,
+                                const int* order_lu, const int2* lu_info, int n_lu, int n_w, SweepTask* table_pen,
+                                SweepTask* table_lu, int* counts, cudaStream_t stream) {
+  pencil_route_kernel<<<1, 32, 0, stream>>>(pen_ok, order_pen, spen, n_pen, order_lu, lu_info, n_lu, n_w,
+                                            table_pen, table_lu, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pencil_sweep(const RomDev* objs, const PencilDev* pens, const SweepTask* table, int* counter,
+                                const double* omega, int omega_stride, const double* s_sigma, double* R,
+                                double* I, double* Delta, int* status, int n_w, int grid, size_t smem_bytes,
+                                cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(pencil_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  pencil_sweep_kernel<<<grid, kPT, smem_bytes, stream>>>(objs, pens, table, counter, omega, omega_stride, s_sigma,
+                                                         R, I, Delta, status, n_w);
+  return cudaGetLastError();
+}
+
+}  // namespace mrom

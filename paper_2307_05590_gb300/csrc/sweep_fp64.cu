@@ -86,6 +86,7 @@ sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__
   __shared__ int s_task;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
+  if (IMPLICIT && n_tasks < 0) n_tasks = tasks[0].w0;  // routed table: count in the header
 
   for (;;) {
     if (tid == 0) s_task = atomicAdd(counter, 1);
@@ -390,6 +391,27 @@ cudaError_t launch_sweep_fp64_implicit(int cfg, const RomDev* objs, const SweepT
     if (e != cudaSuccess) return e;
     sweep_fp64_kernel<128, 4, true><<<grid, 128, smem_bytes, stream>>>(
         objs, table, n_tasks, counter, omega, omega_stride, nullptr, R, I, Delta, status, n_w, workspace, ws_elems);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_fp64_routed(int cfg, const RomDev* objs, const SweepTask* table, int* counter,
+                                     const double* omega, int omega_stride, const double* s_sigma, double* R,
+                                     double* I, double* Delta, int* status, int n_w, int grid, size_t smem_bytes,
+                                     double2* workspace, size_t ws_elems, cudaStream_t stream) {
+  cudaError_t e;
+  if (cfg == 0) {
+    e = cudaFuncSetAttribute(sweep_fp64_kernel<256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    sweep_fp64_kernel<256, 2, true><<<grid, 256, smem_bytes, stream>>>(
+        objs, table, -1, counter, omega, omega_stride, s_sigma, R, I, Delta, status, n_w, workspace, ws_elems);
+  } else {
+    e = cudaFuncSetAttribute(sweep_fp64_kernel<128, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    sweep_fp64_kernel<128, 4, true><<<grid, 128, smem_bytes, stream>>>(
+        objs, table, -1, counter, omega, omega_stride, s_sigma, R, I, Delta, status, n_w, workspace, ws_elems);
   }
   return cudaGetLastError();
 }

@@ -19,9 +19,14 @@ def mrom():
     return m
 
 
-@pytest.fixture(scope="module")
-def handle(mrom):
-    return mrom.Handle(0)
+@pytest.fixture(scope="module", params=["auto", "lu"])
+def handle(mrom, request):
+    """Both solver routes: the Hermitian pencil where its error estimate allows (default),
+    and LU elimination without pivoting for every object."""
+    h = mrom.Handle(0)
+    h.set_solver(lu=request.param == "lu")
+    h.solver = request.param
+    return h
 
 
 def _run(mrom, handle, objs, omega, n_w, with_delta=True, omega_stride=0, s_sigma=None):
@@ -123,6 +128,8 @@ def test_invalid_objects_rejected(mrom, handle):
 
 
 def test_launch_count_increases(mrom, handle):
+    """LU route: one sweep kernel.  Pencil route: preparation, routing and the two sweep
+    kernels (the LU one over an empty table)."""
     import torch
     from workloads import reduced_object
     rom = mrom.ReducedObject.from_workload(handle, reduced_object(9, 3, 12))
@@ -131,7 +138,67 @@ def test_launch_count_increases(mrom, handle):
     before = handle.launch_count()
     mrom.mrom_sweep(handle, [rom], om, 2, R, torch.empty_like(R))
     handle.synchronize()
-    assert handle.launch_count() == before + 1
+    assert handle.launch_count() == before + (1 if handle.solver == "lu" else 4)
+
+
+def _plan_sweep(mrom, handle, objs, wo):
+    import torch
+    roms = [mrom.ReducedObject.from_workload(handle, o) for o in objs]
+    plan = mrom.Plan(handle, roms, wo.size)
+    om = torch.as_tensor(wo, device="cuda")
+    R = torch.empty((len(objs), wo.size, 3, 3), dtype=torch.float64, device="cuda")
+    I = torch.empty_like(R)
+    D = torch.empty_like(R)
+    plan.sweep(om, R, I, D)
+    handle.synchronize()
+    return plan.solver_counts(), (R.cpu().numpy(), I.cpu().numpy(), D.cpu().numpy())
+
+
+def test_routing_of_dictionary_and_ill_conditioned_objects(mrom, handle):
+    """Dictionary objects (K spectrum [1e-6, 1e2], C spectrum [1e-3, 1]) all pass the pencil
+    gate; an object with K up to 1e4 has an error estimate eps ||H|| / omega_min above 1e-11
+    and goes to LU elimination in the same batch.  Every object matches the oracle."""
+    from workloads import log_omegas, reduced_object
+    from gpu_common import oracle_sweep, rel_errors
+    objs = [reduced_object(31, k, r) for k, r in enumerate([10, 48, 90])]
+    objs.append(reduced_object(31, 7, 40, k_range=(-4.0, 4.0)))
+    wo = log_omegas(1e1, 1e8, 97)
+    (n_pen, n_lu), (Rg, Ig, Dg) = _plan_sweep(mrom, handle, objs, wo)
+    if handle.solver == "lu":
+        assert (n_pen, n_lu) == (0, 4)
+    else:
+        assert (n_pen, n_lu) == (3, 1)
+    for k, obj in enumerate(objs):
+        errs = rel_errors(Rg[k], Ig[k], Dg[k], *oracle_sweep(obj, wo))
+        assert max(errs) <= TOL, (obj.r, errs)
+
+
+def test_pencil_route_with_stiffness_regularisation(mrom, handle):
+    """An object with Me = U^H (eps M) U (added to the system only, not to R): the pencil
+    route carries V^H Me V as a separate Hermitian form."""
+    import torch
+    from workloads import log_omegas, reduced_object
+    from oracle import rom as orom
+    from gpu_common import oracle_model_sweep, rel_errors
+    obj = reduced_object(41, 0, 30)
+    rng = np.random.default_rng(5)
+    Z = (rng.standard_normal((30, 30)) + 1j * rng.standard_normal((30, 30))) * 1e-3
+    Me = Z @ Z.conj().T
+    model = orom.from_reduced_object(obj)
+    model.Me = [Me] * 3
+    wo = log_omegas(1e1, 1e8, 70)
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    ro = mrom.ReducedObject(handle, 30, t(obj.K), t(obj.C), t(obj.B), obj.c00, G=t(obj.G), Me=t(Me),
+                            alpha=obj.alpha, alpha_lb=obj.alpha_lb)
+    om = t(wo)
+    R = torch.empty((1, 70, 3, 3), dtype=torch.float64, device=dev)
+    I = torch.empty_like(R)
+    D = torch.empty_like(R)
+    mrom.mrom_sweep(handle, [ro], om, 70, R, I, D)
+    handle.synchronize()
+    errs = rel_errors(R[0].cpu().numpy(), I[0].cpu().numpy(), D[0].cpu().numpy(), *oracle_model_sweep(model, wo))
+    assert max(errs) <= TOL, errs
 
 
 def test_autotuner_picks_a_valid_configuration(mrom, handle):
