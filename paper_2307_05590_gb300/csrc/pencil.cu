@@ -37,8 +37,15 @@ __device__ __forceinline__ double2 cmac(double2 c, double2 a, double2 b) {  // c
 __device__ __forceinline__ double2 cmacc(double2 c, double2 a, double2 b) {  // c + conj(a) b
   return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
 }
-__device__ __forceinline__ double2 cmac_bc(double2 c, double2 a, double2 b) {  // c + a conj(b)
-  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.y, b.x, fma(-a.x, b.y, c.y)));
+
+// Row and column of entry e of a packed lower triangle (row i holds columns 0..i):
+// e = i (i + 1) / 2 + j.  Float square root, then exact integer correction.
+__device__ __forceinline__ void tri_rc(int e, int& i, int& j) {
+  int t = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while (t * (t + 1) / 2 > e) --t;
+  while ((t + 1) * (t + 2) / 2 <= e) ++t;
+  i = t;
+  j = e - t * (t + 1) / 2;
 }
 
 // CTA-wide sum / minimum of one value per thread (every thread gets the result; fixed order).
@@ -135,35 +142,47 @@ pencil_prep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict_
       }
       __syncthreads();
       const int m = r - k - 1;
-      for (int idx = tid; idx < m * m; idx += kPT) {
-        const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-        if (j > i) continue;
+      for (int e = tid; e < m * (m + 1) / 2; e += kPT) {
+        int i, j;
+        tri_rc(e, i, j);
+        i += k + 1;
+        j += k + 1;
         const double2 li = W0[i * r + k], lj = W0[j * r + k];
         double2 a = W0[i * r + j];
         // a - li conj(lj)
-        a.x -= fma(li.x, lj.x, li.y * lj.y);
-        a.y -= fma(li.y, lj.x, -li.x * lj.y);
+        a.x = fma(-li.x, lj.x, fma(-li.y, lj.y, a.x));
+        a.y = fma(-li.y, lj.x, fma(li.x, lj.y, a.y));
         W0[i * r + j] = a;
       }
       __syncthreads();
     }
 
-    // ---- 2. L^-1 (lower) in W2, row by row
+    // ---- 2. Y = L^-1 (lower) in W2, right-looking: for k = 0..r-1, row k of Y is divided
+    // by L_kk (it is then final), and L[i][k] Y[k][:] is subtracted from the rows i > k
     double ln = 0.0;
     if (ok) {
-      for (int i = 0; i < r; ++i) {
-        const double idi = 1.0 / sd[i];
-        for (int j = tid; j <= i; j += kPT) {
-          double2 v;
-          if (j == i) {
-            v = make_double2(idi, 0.0);
-          } else {
-            double2 s = make_double2(0.0, 0.0);
-            for (int k = j; k < i; ++k) s = cmac(s, W0[i * r + k], W2[k * r + j]);
-            v = make_double2(-s.x * idi, -s.y * idi);
-          }
-          W2[i * r + j] = v;
+      for (int idx = tid; idx < rr; idx += kPT) {
+        const int i = idx / r, j = idx - (idx / r) * r;
+        W2[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      }
+      __syncthreads();
+      for (int k = 0; k < r; ++k) {
+        const double idk = 1.0 / sd[k];
+        for (int j = tid; j <= k; j += kPT) {
+          double2 v = W2[k * r + j];
+          v = make_double2(v.x * idk, v.y * idk);
+          W2[k * r + j] = v;
           ln += v.x * v.x + v.y * v.y;
+        }
+        __syncthreads();
+        const int nc = k + 1;
+        for (int idx = tid; idx < (r - k - 1) * nc; idx += kPT) {
+          const int i = k + 1 + idx / nc, j = idx - (idx / nc) * nc;
+          const double2 l = W0[i * r + k], y = W2[k * r + j];
+          double2 a = W2[i * r + j];
+          a.x = fma(-l.x, y.x, fma(l.y, y.y, a.x));
+          a.y = fma(-l.x, y.y, fma(-l.y, y.x, a.y));
+          W2[i * r + j] = a;
         }
         __syncthreads();
       }
@@ -174,29 +193,25 @@ pencil_prep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict_
     // ---- 3. X = L^-1 K' (W0)  and  4. H = X L^-H (W1, lower then mirrored)
     double hn = 0.0;
     if (ok) {
+      // X = L^-1 K', stored conjugate-transposed: W0[j][i] = conj(X[i][j])
       for (int idx = tid; idx < rr; idx += kPT) {
         const int i = idx / r, j = idx - (idx / r) * r;
         double2 s = make_double2(0.0, 0.0);
         for (int k = 0; k <= i; ++k) s = cmac(s, W2[i * r + k], W1[k * r + j]);
-        W0[idx] = s;
+        W0[j * r + i] = make_double2(s.x, -s.y);
       }
       __syncthreads();
+      // H[i][j] = sum_{k <= j} X[i][k] conj(L^-1[j][k]) = conj(sum_k W0[k][i] L^-1[j][k]) for
+      // i >= j, lanes along i (one trip count per warp), mirrored into the upper triangle
       for (int idx = tid; idx < rr; idx += kPT) {
-        const int i = idx / r, j = idx - (idx / r) * r;
-        if (j > i) continue;
+        const int j = idx / r, i = idx - (idx / r) * r;
+        if (i < j) continue;
         double2 s = make_double2(0.0, 0.0);
-        for (int k = 0; k <= j; ++k) s = cmac_bc(s, W0[i * r + k], W2[j * r + k]);
+        for (int k = 0; k <= j; ++k) s = cmac(s, W0[k * r + i], W2[j * r + k]);
         if (i == j) s.y = 0.0;
-        W1[idx] = s;
+        W1[i * r + j] = make_double2(s.x, -s.y);
+        W1[j * r + i] = s;
         hn += (i == j ? 1.0 : 2.0) * (s.x * s.x + s.y * s.y);
-      }
-      __syncthreads();
-      for (int idx = tid; idx < rr; idx += kPT) {
-        const int i = idx / r, j = idx - (idx / r) * r;
-        if (j > i) {
-          const double2 v = W1[j * r + i];
-          W1[idx] = make_double2(v.x, -v.y);
-        }
       }
     }
     hn = block_sum(hn, red);
@@ -256,19 +271,25 @@ pencil_prep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict_
           kr += fma(v.x, p.x, v.y * p.y);
         }
         kr = 0.5 * tau * block_sum(kr, red);
-        // H_sub -= v w^H + w v^H, w = p - K v
-        for (int idx = tid; idx < m * m; idx += kPT) {
-          const int i = idx / m, j = idx - (idx / m) * m;
+        // w = p - K v (in place of p)
+        for (int i = tid; i < m; i += kPT) {
+          const double2 v = W1[(k + 1 + i) * r + k], p = pv[i];
+          pv[i] = make_double2(fma(-kr, v.x, p.x), fma(-kr, v.y, p.y));
+        }
+        __syncthreads();
+        // H_sub -= v w^H + w v^H on the lower triangle, mirrored into the upper one
+        for (int e = tid; e < m * (m + 1) / 2; e += kPT) {
+          int i, j;
+          tri_rc(e, i, j);
           const double2 vi = W1[(k + 1 + i) * r + k], vj = W1[(k + 1 + j) * r + k];
-          const double2 pi = pv[i], pj = pv[j];
-          const double2 wi = make_double2(fma(-kr, vi.x, pi.x), fma(-kr, vi.y, pi.y));
-          const double2 wj = make_double2(fma(-kr, vj.x, pj.x), fma(-kr, vj.y, pj.y));
+          const double2 wi = pv[i], wj = pv[j];
           double2 a = W1[(k + 1 + i) * r + (k + 1 + j)];
           // a - vi conj(wj) - wi conj(vj)
-          a.x -= fma(vi.x, wj.x, vi.y * wj.y) + fma(wi.x, vj.x, wi.y * vj.y);
-          a.y -= fma(vi.y, wj.x, -vi.x * wj.y) + fma(wi.y, vj.x, -wi.x * vj.y);
+          a.x = fma(-vi.x, wj.x, fma(-vi.y, wj.y, fma(-wi.x, vj.x, fma(-wi.y, vj.y, a.x))));
+          a.y = fma(-vi.y, wj.x, fma(vi.x, wj.y, fma(-wi.y, vj.x, fma(wi.x, vj.y, a.y))));
           if (i == j) a.y = 0.0;
           W1[(k + 1 + i) * r + (k + 1 + j)] = a;
+          if (i != j) W1[(k + 1 + j) * r + (k + 1 + i)] = make_double2(a.x, -a.y);
         }
         __syncthreads();
       }
@@ -303,8 +324,8 @@ pencil_prep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict_
           const int i = idx / m, j = idx - (idx / m) * m;
           const double2 v = W1[(k + 1 + i) * r + k], u = sph[j];
           double2 a = W0[(k + 1 + i) * r + (k + 1 + j)];
-          a.x -= fma(v.x, u.x, -v.y * u.y);
-          a.y -= fma(v.x, u.y, v.y * u.x);
+          a.x = fma(-v.x, u.x, fma(v.y, u.y, a.x));
+          a.y = fma(-v.x, u.y, fma(-v.y, u.x, a.y));
           W0[(k + 1 + i) * r + (k + 1 + j)] = a;
         }
         __syncthreads();
@@ -467,11 +488,8 @@ pencil_prep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict_
         __syncthreads();
         const int ntri = r * (r + 1) / 2;
         for (int e = tid; e < ntri; e += kPT) {
-          // packed lower triangle: row a holds columns 0..a
-          int a = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-          while ((a + 1) * (a + 2) / 2 <= e) ++a;
-          while (a * (a + 1) / 2 > e) --a;
-          const int b = e - a * (a + 1) / 2;
+          int a, b;  // packed lower triangle: row a holds columns 0..a
+          tri_rc(e, a, b);
           double2 s = make_double2(0.0, 0.0);
           for (int c = 0; c < r; ++c) s = cmacc(s, W1[c * r + a], W0[c * r + b]);
           if (gram)
@@ -535,13 +553,213 @@ __device__ __forceinline__ SweepTask table_task(const SweepTask* __restrict__ ta
 }
 
 // ------------------------------------------------------------------ sweep
-//
+
+constexpr int kNQ = 48;  // partial sums per lane: U 0..8, X 9..17, B 18..26, E 27..35, R 36..41, I 42..47
+
+// Row pairs (a, r-1-a) of one warp, lane = one frequency: accumulates, over its rows a,
+//   U_ij = Re(z_ai^* y_aj), y = (L + D/2) G~(w) z   (certificate form, halved)
+//   X_ij = Re((i w gsK_ia + w^2 gsC_ia) z_aj)
+//   B_ij = Re(beta_ai^* z_aj)
+//   E_ij = Re(z_ai^* ye_aj), ye = (L + D/2) (V^H Me V) z
+//   R_ij = lambda_a Re(z_ai^* z_aj), I_ij = Re(z_ai^* z_aj)   (i <= j)
+template <bool CERT, bool HAS_E>
+__device__ __forceinline__ void pencil_rows(const PencilDev& pd, int r, const double2* __restrict__ zg, double w,
+                                            int q0, int wpg, double (&acc)[kNQ]) {
+  const double w2 = w * w;
+  const int half = (r + 1) / 2;
+  for (int pr = q0; pr < half; pr += wpg) {
+    for (int side = 0; side < 2; ++side) {
+      const int a = side == 0 ? pr : r - 1 - pr;
+      if (side == 1 && a == pr) break;
+      double2 za[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) za[j] = zg[(a * 3 + j) * 32];
+      const double lam = pd.lam[a];
+      {
+        int q = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = i; j < 3; ++j, ++q) {
+            const double v = fma(za[i].x, za[j].x, za[i].y * za[j].y);
+            acc[36 + q] = fma(lam, v, acc[36 + q]);
+            acc[42 + q] += v;
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double2 b = pd.beta[a * 3 + i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) acc[18 + i * 3 + j] = fma(b.x, za[j].x, fma(b.y, za[j].y, acc[18 + i * 3 + j]));
+      }
+      if constexpr (CERT) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const double2 gk = pd.gsh[a * 6 + i], gc = pd.gsh[a * 6 + 3 + i];
+          // coefficient i w gk + w^2 gc; the real part of its product with z_j
+          const double cx = fma(-w, gk.y, w2 * gc.x), cy = fma(w, gk.x, w2 * gc.y);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) acc[9 + i * 3 + j] = fma(cx, za[j].x, fma(-cy, za[j].y, acc[9 + i * 3 + j]));
+        }
+      }
+      if constexpr (CERT || HAS_E) {
+        double2 y[3], ye[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) y[j] = ye[j] = make_double2(0.0, 0.0);
+        const size_t row0 = (size_t)a * (a + 1) / 2;
+        const double2* gh = CERT ? pd.Gh + row0 * 3 : nullptr;
+        const double2* eh = HAS_E ? pd.Eh + row0 : nullptr;
+        for (int b = 0; b < a; ++b) {
+          double2 zb[3];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) zb[j] = zg[(b * 3 + j) * 32];
+          if constexpr (CERT) {
+            const double2 kk = gh[3 * b], cc = gh[3 * b + 1], sk = gh[3 * b + 2];
+            // G~_ab = KK + w^2 CC + i w S
+            const double2 gt = make_double2(fma(w2, cc.x, fma(-w, sk.y, kk.x)), fma(w2, cc.y, fma(w, sk.x, kk.y)));
+#pragma unroll
+            for (int j = 0; j < 3; ++j) y[j] = cmac(y[j], gt, zb[j]);
+          }
+          if constexpr (HAS_E) {
+            const double2 e = eh[b];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) ye[j] = cmac(ye[j], e, zb[j]);
+          }
+        }
+        // diagonal term, halved
+        double2 zh[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) zh[j] = make_double2(0.5 * za[j].x, 0.5 * za[j].y);
+        if constexpr (CERT) {
+          const double2 kk = gh[3 * a], cc = gh[3 * a + 1], sk = gh[3 * a + 2];
+          const double2 gt = make_double2(fma(w2, cc.x, fma(-w, sk.y, kk.x)), fma(w2, cc.y, fma(w, sk.x, kk.y)));
+#pragma unroll
+          for (int j = 0; j < 3; ++j) y[j] = cmac(y[j], gt, zh[j]);
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) acc[i * 3 + j] = fma(za[i].x, y[j].x, fma(za[i].y, y[j].y, acc[i * 3 + j]));
+        }
+        if constexpr (HAS_E) {
+          const double2 e = eh[a];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) ye[j] = cmac(ye[j], e, zh[j]);
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+              acc[27 + i * 3 + j] = fma(za[i].x, ye[j].x, fma(za[i].y, ye[j].y, acc[27 + i * 3 + j]));
+        }
+      }
+    }
+  }
+}
+
 // A task is 32 F consecutive frequencies of one object (F frequency groups of 32, one
-// frequency per lane).  Warp w serves group w % F and the row pairs (a, r-1-a) with
-// pair index = w / F (mod 8 / F), so that every pair costs r + 1 row steps.  Shared
-// memory: z[g][b][j][lane] (the solution in eigen-coordinates), then, after a barrier,
-// the per-warp partial sums for the cross-warp reduction in the same space.
-constexpr int kNQ = 48;  // partial sums per lane: U 9, X 9, Ib 9, E 9, Rl 6, Iz 6
+// frequency per lane).  Warp w serves group w % F and the row pairs (a, r-1-a) with pair
+// index = w / F (mod 8 / F), so that every pair costs r + 1 row steps.  Shared memory:
+// z[g][b][j][lane] (the solutions in eigen-coordinates), then, after a barrier, the
+// per-warp partial sums, reduced once per (group, quantity, lane) into warp g's slot.
+template <bool CERT, bool HAS_E>
+__device__ __forceinline__ void pencil_task(const RomDev& ob, const PencilDev& pd, const SweepTask& task,
+                                            const double* __restrict__ omega, int omega_stride, double ssig,
+                                            double* __restrict__ Rout, double* __restrict__ Iout,
+                                            double* __restrict__ Dout, int* __restrict__ status, int n_w,
+                                            unsigned char* smem_raw, double* Ws) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double2* zs = reinterpret_cast<double2*>(smem_raw);
+  double* rbuf = reinterpret_cast<double*>(smem_raw);
+  const int r = ob.r, S = task.nw;
+  const int F = pd.F;       // frequency groups of 32
+  const int wpg = kPW / F;  // warps per group
+
+  // ---- frequencies and z_kj = i w beta_kj / (lambda_k - i w) = u_k beta_kj,
+  //      u = i w (lambda + i w) / (lambda^2 + w^2)
+  for (int s = tid; s < 32 * F; s += kPT) {
+    double w = __longlong_as_double(0x7ff8000000000000LL);
+    if (s < S) {
+      w = omega[(size_t)task.obj * omega_stride + task.w0 + s] * ssig;
+      if (!(w > 0.0) || !isfinite(w)) {
+        atomicOr(status, kStatusBadOmega);
+        w = __longlong_as_double(0x7ff8000000000000LL);
+      }
+    }
+    Ws[s] = w;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < r * 32 * F; idx += kPT) {
+    const int g = idx / (r * 32);
+    const int rem = idx - g * r * 32;
+    const int k = rem >> 5, ln = rem & 31;
+    const double w = Ws[g * 32 + ln];
+    const double lam = pd.lam[k];
+    const double den = 1.0 / fma(lam, lam, w * w);
+    const double2 u = make_double2(-w * w * den, w * lam * den);
+    double2* zk = zs + ((size_t)(g * r + k) * 3) * 32 + ln;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double2 b = pd.beta[k * 3 + j];
+      zk[j * 32] = make_double2(fma(u.x, b.x, -u.y * b.y), fma(u.x, b.y, u.y * b.x));
+    }
+  }
+  __syncthreads();
+
+  // ---- row pairs
+  double acc[kNQ];
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+  {
+    const int g = warp % F;
+    pencil_rows<CERT, HAS_E>(pd, r, zs + (size_t)g * r * 3 * 32 + lane, Ws[g * 32 + lane], warp / F, wpg, acc);
+  }
+  __syncthreads();  // z is no longer read: its space takes the partial sums
+  {
+    double* rb = rbuf + (size_t)warp * kNQ * 32 + lane;
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q) rb[q * 32] = acc[q];
+  }
+  __syncthreads();
+  if (wpg > 1) {  // totals of each group into the slot of its first warp (warp g)
+    for (int idx = tid; idx < F * kNQ * 32; idx += kPT) {
+      const int g = idx / (kNQ * 32);
+      const int rem = idx - g * kNQ * 32;
+      double v = rbuf[(size_t)g * kNQ * 32 + rem];
+      for (int k = 1; k < wpg; ++k) v += rbuf[(size_t)(g + k * F) * kNQ * 32 + rem];
+      rbuf[(size_t)g * kNQ * 32 + rem] = v;
+    }
+    __syncthreads();
+  }
+  // ---- outputs
+  for (int idx = tid; idx < S * 9; idx += kPT) {
+    const int s = idx / 9, ij = idx - (idx / 9) * 9;
+    const int i = ij / 3, j = ij - (ij / 3) * 3;
+    const double* tot = rbuf + (size_t)(s >> 5) * kNQ * 32 + (s & 31);
+    auto t = [tot](int q) { return tot[q * 32]; };
+    const int lo = i < j ? i : j, hi = i < j ? j : i;
+    const int sym = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);  // packed index of (lo, hi)
+    const double wv = Ws[s];
+    const size_t o = ((size_t)task.obj * n_w + task.w0 + s) * 9 + ij;
+    if (Rout) {
+      double kf = t(36 + sym);
+      if constexpr (HAS_E) kf -= t(27 + i * 3 + j) + t(27 + j * 3 + i);
+      Rout[o] = fma(-0.25 * ob.alpha3, kf, ob.N0[ij]);
+    }
+    if (Iout)
+      Iout[o] = 0.25 * ob.alpha3 * wv * (ob.c00[ij] + t(42 + sym) + t(18 + i * 3 + j) + t(18 + j * 3 + i));
+    if (Dout) {
+      if constexpr (CERT) {
+        const double ww = wv * wv;
+        const double cij = fma(ww, ob.gss[ij], t(i * 3 + j) + t(j * 3 + i) + t(9 + i * 3 + j) + t(9 + j * 3 + i));
+        const double ni = fma(ww, ob.gss[i * 4], 2.0 * (t(i * 4) + t(9 + i * 4)));
+        const double nj = fma(ww, ob.gss[j * 4], 2.0 * (t(j * 4) + t(9 + j * 4)));
+        Dout[o] = ob.cert_scale * (ni + nj - cij);
+      } else {
+        Dout[o] = __longlong_as_double(0x7ff8000000000000LL);
+      }
+    }
+  }
+  // the next task's first barrier orders these reads before the space is rewritten
+}
 
 __global__ void __launch_bounds__(kPT, 1)
 pencil_sweep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__ pens,
@@ -552,11 +770,8 @@ pencil_sweep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_task;
   __shared__ double Ws[kPT];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int n_tasks = table[0].w0;
-  double2* zs = reinterpret_cast<double2*>(smem_raw);
-  double* rbuf = reinterpret_cast<double*>(smem_raw);
-
   for (;;) {
     if (tid == 0) s_task = atomicAdd(counter, 1);
     __syncthreads();
@@ -566,184 +781,21 @@ pencil_sweep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict
     const SweepTask task = table_task(table, n_w, t);
     const RomDev& ob = objs[task.obj];
     const PencilDev& pd = pens[task.obj];
-    const int r = ob.r, S = task.nw;
-    const int F = pd.F;               // frequency groups of 32
-    const int wpg = kPW / F;          // warps per group
     const bool cert = Dout != nullptr && ob.has_cert;
     const bool has_e = pd.Eh != nullptr;
     const double ssig = s_sigma ? s_sigma[task.obj] : 1.0;
-
-    // ---- frequencies and z_kj = i w beta_kj / (lambda_k - i w) = u_k beta_kj,
-    //      u = i w (lambda + i w) / (lambda^2 + w^2)
-    for (int s = tid; s < 32 * F; s += kPT) {
-      double w = __longlong_as_double(0x7ff8000000000000LL);
-      if (s < S) {
-        w = omega[(size_t)task.obj * omega_stride + task.w0 + s] * ssig;
-        if (!(w > 0.0) || !isfinite(w)) {
-          atomicOr(status, kStatusBadOmega);
-          w = __longlong_as_double(0x7ff8000000000000LL);
-        }
-      }
-      Ws[s] = w;
+    if (cert) {
+      if (has_e)
+        pencil_task<true, true>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, status, n_w, smem_raw, Ws);
+      else
+        pencil_task<true, false>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, status, n_w, smem_raw, Ws);
+    } else {
+      if (has_e)
+        pencil_task<false, true>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, status, n_w, smem_raw, Ws);
+      else
+        pencil_task<false, false>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, status, n_w, smem_raw,
+                                  Ws);
     }
-    __syncthreads();
-    for (int idx = tid; idx < r * 32 * F; idx += kPT) {
-      const int g = idx / (r * 32);
-      const int rem = idx - g * r * 32;
-      const int k = rem >> 5, ln = rem & 31;
-      const double w = Ws[g * 32 + ln];
-      const double lam = pd.lam[k];
-      const double den = 1.0 / fma(lam, lam, w * w);
-      const double2 u = make_double2(-w * w * den, w * lam * den);
-      double2* zk = zs + ((size_t)(g * r + k) * 3) * 32 + ln;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const double2 b = pd.beta[k * 3 + j];
-        zk[j * 32] = make_double2(fma(u.x, b.x, -u.y * b.y), fma(u.x, b.y, u.y * b.x));
-      }
-    }
-    __syncthreads();
-
-    // ---- row pairs
-    const int g = warp % F;
-    const int q0 = warp / F;
-    const double w = Ws[g * 32 + lane], w2 = w * w;
-    const double2* zg = zs + (size_t)g * r * 3 * 32 + lane;
-    double aU[9], aX[9], aB[9], aE[9], aR[6], aI[6];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) aU[q] = aX[q] = aB[q] = aE[q] = 0.0;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) aR[q] = aI[q] = 0.0;
-    const int half = (r + 1) / 2;
-    for (int pr = q0; pr < half; pr += wpg) {
-      for (int side = 0; side < 2; ++side) {
-        const int a = side == 0 ? pr : r - 1 - pr;
-        if (side == 1 && a == pr) break;
-        double2 za[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) za[j] = zg[(a * 3 + j) * 32];
-        // O(r) terms of row a
-        const double lam = pd.lam[a];
-        {
-          int q = 0;
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = i; j < 3; ++j, ++q) {
-              const double v = fma(za[i].x, za[j].x, za[i].y * za[j].y);
-              aR[q] = fma(lam, v, aR[q]);
-              aI[q] += v;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const double2 b = pd.beta[a * 3 + i];
-#pragma unroll
-          for (int j = 0; j < 3; ++j) aB[i * 3 + j] = fma(b.x, za[j].x, fma(b.y, za[j].y, aB[i * 3 + j]));
-        }
-        if (cert) {
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            const double2 gk = pd.gsh[a * 6 + i], gc = pd.gsh[a * 6 + 3 + i];
-            // coefficient i w gk + w^2 gc; the real part of its product with z_j
-            const double cx = fma(-w, gk.y, w2 * gc.x), cy = fma(w, gk.x, w2 * gc.y);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) aX[i * 3 + j] = fma(cx, za[j].x, fma(-cy, za[j].y, aX[i * 3 + j]));
-          }
-        }
-        // Hermitian forms, halved: y_j = sum_{b<a} M_ab z_bj + M_aa z_aj / 2
-        if (cert || has_e) {
-          double2 y[3], ye[3];
-#pragma unroll
-          for (int j = 0; j < 3; ++j) y[j] = ye[j] = make_double2(0.0, 0.0);
-          const size_t row0 = (size_t)a * (a + 1) / 2;
-          for (int b = 0; b <= a; ++b) {
-            double2 zb[3];
-            if (b < a) {
-#pragma unroll
-              for (int j = 0; j < 3; ++j) zb[j] = zg[(b * 3 + j) * 32];
-            } else {
-#pragma unroll
-              for (int j = 0; j < 3; ++j) zb[j] = make_double2(0.5 * za[j].x, 0.5 * za[j].y);
-            }
-            if (cert) {
-              const double2* gh = pd.Gh + (row0 + b) * 3;
-              const double2 kk = gh[0], cc = gh[1], sk = gh[2];
-              // G~_ab = KK + w^2 CC + i w S
-              const double2 gt = make_double2(fma(w2, cc.x, fma(-w, sk.y, kk.x)), fma(w2, cc.y, fma(w, sk.x, kk.y)));
-#pragma unroll
-              for (int j = 0; j < 3; ++j) y[j] = cmac(y[j], gt, zb[j]);
-            }
-            if (has_e) {
-              const double2 e = pd.Eh[row0 + b];
-#pragma unroll
-              for (int j = 0; j < 3; ++j) ye[j] = cmac(ye[j], e, zb[j]);
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-              aU[i * 3 + j] = fma(za[i].x, y[j].x, fma(za[i].y, y[j].y, aU[i * 3 + j]));
-              aE[i * 3 + j] = fma(za[i].x, ye[j].x, fma(za[i].y, ye[j].y, aE[i * 3 + j]));
-            }
-        }
-      }
-    }
-    __syncthreads();  // z is no longer read: its space takes the partial sums
-    {
-      double* rb = rbuf + (size_t)warp * kNQ * 32 + lane;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        rb[q * 32] = aU[q];
-        rb[(9 + q) * 32] = aX[q];
-        rb[(18 + q) * 32] = aB[q];
-        rb[(27 + q) * 32] = aE[q];
-      }
-#pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        rb[(36 + q) * 32] = aR[q];
-        rb[(42 + q) * 32] = aI[q];
-      }
-    }
-    __syncthreads();
-    // ---- outputs: (frequency, ij) pairs; partial sums of the group's warps in fixed order
-    for (int idx = tid; idx < S * 9; idx += kPT) {
-      const int s = idx / 9, ij = idx - (idx / 9) * 9;
-      const int i = ij / 3, j = ij - (ij / 3) * 3;
-      const int gg = s >> 5, ln = s & 31;
-      auto sum = [&](int q) {
-        double v = 0.0;
-        for (int k = 0; k < wpg; ++k) v += rbuf[((size_t)(gg + k * F) * kNQ + q) * 32 + ln];
-        return v;
-      };
-      auto sym = [](int a, int b) {  // packed index of (min, max) in the 6 symmetric sums
-        const int lo = a < b ? a : b, hi = a < b ? b : a;
-        return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
-      };
-      const double wv = Ws[s];
-      const size_t o = ((size_t)task.obj * n_w + task.w0 + s) * 9 + ij;
-      if (Rout) {
-        const double kf = sum(36 + sym(i, j)) - (sum(27 + i * 3 + j) + sum(27 + j * 3 + i));
-        Rout[o] = fma(-0.25 * ob.alpha3, kf, ob.N0[ij]);
-      }
-      if (Iout)
-        Iout[o] = 0.25 * ob.alpha3 * wv *
-                  (ob.c00[ij] + sum(42 + sym(i, j)) + sum(18 + i * 3 + j) + sum(18 + j * 3 + i));
-      if (Dout) {
-        if (cert) {
-          const double ww = wv * wv;
-          const double cij = fma(ww, ob.gss[ij], sum(i * 3 + j) + sum(j * 3 + i) + sum(9 + i * 3 + j) +
-                                                     sum(9 + j * 3 + i));
-          const double ni = fma(ww, ob.gss[i * 4], 2.0 * (sum(i * 4) + sum(9 + i * 4)));
-          const double nj = fma(ww, ob.gss[j * 4], 2.0 * (sum(j * 4) + sum(9 + j * 4)));
-          Dout[o] = ob.cert_scale * (ni + nj - cij);
-        } else {
-          Dout[o] = __longlong_as_double(0x7ff8000000000000LL);
-        }
-      }
-    }
-    // the next task's first barrier orders these reads before the space is rewritten
   }
 }
 
