@@ -108,6 +108,9 @@ namespace {
 // kPencilKappaMax; other objects take the LU route.
 constexpr double kPencilGate = 1e-11;
 constexpr double kPencilKappaMax = 1e6;
+// QL rotation log per object (complex slots): rotations and sweep records
+constexpr size_t kRotCap(int r) { return 3 * (size_t)r * r + 64; }
+constexpr size_t kSweepCap(int r) { return 16 * (size_t)r + 16; }
 
 // Dynamic shared memory per CTA: an SM's shared memory divided by the CTAs that
 // co-reside, so that they fill each other's barrier waits (minus the reservation).
@@ -197,6 +200,8 @@ mrom_status plan_pencil(mrom_ctx* h, mrom_plan plan, const std::vector<RomDev>& 
     data_elems += (size_t)(r + 1) / 2 + 3 * (size_t)r;            // lam (in complex slots), beta
     if (objs[o].has_cert) data_elems += 6 * (size_t)r + 3 * tri;  // gsh, Gh
     if (objs[o].Me) data_elems += tri;                            // Eh
+    // preparation scratch: W, e, rotation log (QL takes about r^2 rotations in 2 r sweeps)
+    data_elems += (size_t)r * r + (size_t)(r + 1) / 2 + kRotCap(r) + (size_t)(kSweepCap(r) + 1) / 2;
   }
   // LU order (all objects, descending cost) with their LU task shapes
   std::vector<int> order_lu(n_obj);
@@ -217,18 +222,21 @@ mrom_status plan_pencil(mrom_ctx* h, mrom_plan plan, const std::vector<RomDev>& 
   // one allocation: pens, order_pen, spen, order_lu, lu_info, two tables, pen_ok,
   // counters, per-object data, preparation workspace
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b_scr = al(n_obj * sizeof(PencilScratch)), b_nsw = al(elig.size() * sizeof(int));
   const size_t b_pens = al(n_obj * sizeof(PencilDev)), b_op = al(elig.size() * sizeof(int)),
                b_sp = al(elig.size() * sizeof(int)), b_ol = al(n_obj * sizeof(int)),
                b_li = al(n_obj * sizeof(int2)), b_tab = al((n_obj + 1) * sizeof(SweepTask)),
                b_ok = al(n_obj * sizeof(int)), b_cnt = al(8 * sizeof(int)),
                b_data = al(data_elems * sizeof(double2)),
                b_ws = al(plan->prep_ws_elems * plan->prep_grid * sizeof(double2));
-  const size_t total = b_pens + b_op + b_sp + b_ol + b_li + 2 * b_tab + b_ok + b_cnt + b_data + b_ws;
+  const size_t total = b_scr + b_nsw + b_pens + b_op + b_sp + b_ol + b_li + 2 * b_tab + b_ok + b_cnt + b_data + b_ws;
   void* blk = nullptr;
   cudaError_t e = cudaMallocAsync(&blk, total, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_plan_create: pencil allocation");
   plan->pen_block = blk;
   char* p = static_cast<char*>(blk);
+  plan->d_scr = reinterpret_cast<PencilScratch*>(p); p += b_scr;
+  int* d_nsw = reinterpret_cast<int*>(p); p += b_nsw;
   plan->d_pens = reinterpret_cast<PencilDev*>(p); p += b_pens;
   plan->d_order_pen = reinterpret_cast<int*>(p); p += b_op;
   plan->d_spen = reinterpret_cast<int*>(p); p += b_sp;
@@ -240,7 +248,10 @@ mrom_status plan_pencil(mrom_ctx* h, mrom_plan plan, const std::vector<RomDev>& 
   plan->d_counters = reinterpret_cast<int*>(p); p += b_cnt;
   double2* data = reinterpret_cast<double2*>(p); p += b_data;
   plan->d_prep_ws = reinterpret_cast<double2*>(p);
-  for (const int o : elig) {
+  std::vector<PencilScratch> scr(n_obj);
+  std::memset(scr.data(), 0, n_obj * sizeof(PencilScratch));
+  for (size_t k = 0; k < elig.size(); ++k) {
+    const int o = elig[k];
     const int r = objs[o].r;
     const size_t tri = (size_t)r * (r + 1) / 2;
     double2* q = data + off[o];
@@ -250,10 +261,22 @@ mrom_status plan_pencil(mrom_ctx* h, mrom_plan plan, const std::vector<RomDev>& 
       pens[o].gsh = q; q += 6 * (size_t)r;
       pens[o].Gh = q; q += 3 * tri;
     }
-    if (objs[o].Me) pens[o].Eh = q;
+    if (objs[o].Me) {
+      pens[o].Eh = q; q += tri;
+    }
+    scr[o].W = q; q += (size_t)r * r;
+    scr[o].e = reinterpret_cast<double*>(q); q += (r + 1) / 2;
+    scr[o].rot = q; q += kRotCap(r);
+    scr[o].sweeps = reinterpret_cast<int2*>(q);
+    scr[o].cap_rot = (int)kRotCap(r);
+    scr[o].cap_sw = (int)kSweepCap(r);
+    scr[o].nsw = d_nsw + k;
   }
   plan->n_pen = (int)elig.size();
+  plan->pen_rmax = rmax;
   e = cudaMemcpyAsync(plan->d_pens, pens.data(), n_obj * sizeof(PencilDev), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(plan->d_scr, scr.data(), n_obj * sizeof(PencilScratch), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(plan->d_order_pen, elig.data(), elig.size() * sizeof(int), cudaMemcpyHostToDevice,
                         h->stream);
@@ -393,30 +416,31 @@ mrom_status run_plan(mrom_plan plan, const double* omega, int32_t omega_stride, 
   if (plan->n_pen > 0) {
     // pencil route: per-object preparation, device-side routing, then both sweep kernels
     // (each over its own table; an empty table ends the kernel at once)
-    cudaError_t e = cudaMemsetAsync(plan->d_counters, 0, 3 * sizeof(int), h->stream);
+    cudaError_t e = cudaMemsetAsync(plan->d_counters, 0, 4 * sizeof(int), h->stream);
     mark(0);
     if (e == cudaSuccess)
-      e = launch_pencil_prep(plan->d_objs, plan->d_pens, plan->d_order_pen, plan->n_pen, plan->d_counters, omega,
-                             omega_stride, plan->n_w, s_sigma, plan->d_pen_ok, plan->d_prep_ws, plan->prep_ws_elems,
-                             plan->prep_grid, kPencilGate, kPencilKappaMax, h->stream);
+      e = launch_pencil_prep(plan->d_objs, plan->d_pens, plan->d_scr, plan->d_order_pen, plan->n_pen, plan->d_counters,
+                             omega, omega_stride, plan->n_w, s_sigma, plan->d_pen_ok, plan->d_prep_ws,
+                             plan->prep_ws_elems, plan->prep_grid, plan->pen_rmax, kPencilGate, kPencilKappaMax,
+                             h->stream);
     mark(1);
     if (e == cudaSuccess)
       e = launch_pencil_route(plan->d_pen_ok, plan->d_order_pen, plan->d_spen, plan->n_pen, plan->d_order_lu,
                               plan->d_lu_info, plan->n_obj, plan->n_w, plan->d_table_pen, plan->d_table_lu,
-                              plan->d_counters + 3, h->stream);
+                              plan->d_counters + 4, h->stream);
     mark(2);
     if (e == cudaSuccess)
-      e = launch_pencil_sweep(plan->d_objs, plan->d_pens, plan->d_table_pen, plan->d_counters + 1, omega,
+      e = launch_pencil_sweep(plan->d_objs, plan->d_pens, plan->d_table_pen, plan->d_counters + 2, omega,
                               omega_stride, s_sigma, R, I, Delta, h->d_status, plan->n_w, plan->pen_grid,
                               plan->pen_smem, h->stream);
     mark(3);
     if (e == cudaSuccess)
-      e = launch_sweep_fp64_routed(plan->cfg, plan->d_objs, plan->d_table_lu, plan->d_counters + 2, omega,
+      e = launch_sweep_fp64_routed(plan->cfg, plan->d_objs, plan->d_table_lu, plan->d_counters + 3, omega,
                                    omega_stride, s_sigma, R, I, Delta, h->d_status, plan->n_w, plan->grid,
                                    plan->smem_bytes, plan->d_workspace, plan->ws_elems, h->stream);
     mark(4);
     if (e != cudaSuccess) return cuda_fail(h, e, "sweep launch");
-    h->launches += 4;
+    h->launches += 6;
     return MROM_OK;
   }
   mark(0);
@@ -443,7 +467,7 @@ extern "C" mrom_status mrom_plan_solver_counts(mrom_plan plan, int32_t* n_pencil
   int c[2] = {0, plan->n_obj};
   if (plan->n_pen > 0) {
     cudaSetDevice(h->device);
-    cudaError_t e = cudaMemcpyAsync(c, plan->d_counters + 3, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e = cudaMemcpyAsync(c, plan->d_counters + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "mrom_plan_solver_counts");
   }

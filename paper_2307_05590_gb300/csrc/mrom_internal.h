@@ -60,6 +60,18 @@ struct PencilDev {
   int pad;
 };
 
+// Per-object scratch of the pencil preparation: W = L^-H Q1 D (r x r), the tridiagonal's
+// off-diagonal e (r), and the QL rotation log (sweeps {m, rotations}, rotations (c, s)).
+struct PencilScratch {
+  double2* W;
+  double* e;
+  double2* rot;
+  int2* sweeps;
+  int* nsw;
+  int cap_rot;
+  int cap_sw;
+};
+
 // One unit of work: S consecutive frequencies of one object.
 struct SweepTask {
   int obj;
@@ -120,6 +132,8 @@ struct mrom_plan_s {
   int n_pen = 0;
   void* pen_block = nullptr;        // one stream-ordered allocation for everything below
   mrom::PencilDev* d_pens = nullptr;
+  mrom::PencilScratch* d_scr = nullptr;
+  int pen_rmax = 0;
   int* d_order_pen = nullptr;       // eligible objects, descending r
   int* d_spen = nullptr;            // frequencies per pencil task, same order
   int* d_order_lu = nullptr;        // all objects in LU cost order
@@ -127,7 +141,7 @@ struct mrom_plan_s {
   mrom::SweepTask* d_table_pen = nullptr;
   mrom::SweepTask* d_table_lu = nullptr;
   int* d_pen_ok = nullptr;
-  int* d_counters = nullptr;        // prep, pencil sweep, LU sweep, then the two route counts
+  int* d_counters = nullptr;        // tridiag, finish, pencil sweep, LU sweep, then the two route counts
   double2* d_prep_ws = nullptr;
   size_t prep_ws_elems = 0;
   int prep_grid = 0;
@@ -176,10 +190,12 @@ cudaError_t launch_sweep_fp64_routed(int cfg, const RomDev* objs, const SweepTas
 // Pencil route (pencil.cu).
 size_t pencil_sweep_smem_bytes(int r, int F);
 int pencil_threads();
-cudaError_t launch_pencil_prep(const RomDev* objs, const PencilDev* pens, const int* order, int n_elig,
-                               int* counter, const double* omega, int omega_stride, int n_w,
-                               const double* s_sigma, int* pen_ok, double2* ws, size_t ws_elems, int grid,
-                               double gate, double kappa_max, cudaStream_t stream);
+size_t pencil_finish_smem_bytes(int rmax);
+// Tridiagonalisation, QL and finishing kernels; counters[0..1] are their task counters.
+cudaError_t launch_pencil_prep(const RomDev* objs, const PencilDev* pens, const PencilScratch* scr,
+                               const int* order, int n_elig, int* counters, const double* omega, int omega_stride,
+                               int n_w, const double* s_sigma, int* pen_ok, double2* ws, size_t ws_elems, int grid,
+                               int rmax, double gate, double kappa_max, cudaStream_t stream);
 cudaError_t launch_pencil_route(const int* pen_ok, const int* order_pen, const int* spen, int n_pen,
                                 const int* order_lu, const int2* lu_info, int n_lu, int n_w, SweepTask* table_pen,
                                 SweepTask* table_lu, int* counts, cudaStream_t stream);

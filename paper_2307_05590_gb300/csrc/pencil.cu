@@ -21,7 +21,9 @@
 // does not converge are routed to the LU kernel instead (device-side routing, no host sync).
 #include "mrom_internal.h"
 
+#include <algorithm>
 #include <cfloat>
+#include <cstdlib>
 
 namespace mrom {
 namespace {
@@ -29,6 +31,7 @@ namespace {
 constexpr int kPT = 256;        // threads per CTA in the preparation and sweep kernels
 constexpr int kPW = kPT / 32;   // warps per CTA
 constexpr int kQlMaxIter = 60;  // QL iterations per eigenvalue before giving up
+constexpr int kQlLanes = 1;     // objects per warp in the QL kernel (MROM_QL_LANES overrides)
 
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 cmac(double2 c, double2 a, double2 b) {  // c + a b
@@ -72,22 +75,27 @@ __device__ double block_min(double v, double* red) {
 
 // ------------------------------------------------------------------ preparation
 //
-// One CTA per object (persistent, objects in descending r).  Three r x r complex matrices
-// in the CTA's slice of a global workspace (L2-resident): W0, W1, W2.
-//   W0: C -> L (strictly lower; diagonal in sd) -> X = L^-1 K' -> Q1 -> Z -> G_X V
-//   W1: K' -> H (full Hermitian) -> Householder vectors below the subdiagonal -> V
+// Three kernels per sweep: tridiagonalisation (one CTA per object), implicit QL (one lane
+// per object) and finishing (one CTA per object).
+//
+// Tridiagonalisation: persistent CTAs, objects in descending r.  Three r x r complex
+// matrices in the CTA's slice of a global workspace (L2-resident): W0, W1, W2.
+//   W0: C -> L (strictly lower; diagonal in sd) -> X^H, X = L^-1 K' -> Q1 -> Z = Q1 D
+//   W1: K' -> H (full Hermitian) -> Householder vectors below the subdiagonal
 //   W2: L^-1 (lower)
+// Output per object: the real tridiagonal D^H Q1^H H Q1 D (diagonal in lam, off-diagonal
+// in the scratch e) and W = L^-H Z; V = W Q2 once QL has diagonalised the tridiagonal.
 __global__ void __launch_bounds__(kPT)
-pencil_prep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__ pens,
-                   const int* __restrict__ order, int n_elig, int* __restrict__ counter,
+pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__ pens,
+                      const PencilScratch* __restrict__ scr, const int* __restrict__ order, int n_elig,
+                      int* __restrict__ counter,
                    const double* __restrict__ omega, int omega_stride, int n_w,
                    const double* __restrict__ s_sigma, int* __restrict__ pen_ok, double2* __restrict__ ws,
                    size_t ws_elems, double gate, double kappa_max) {
   __shared__ double sd[MROM_MAX_R], se[MROM_MAX_R], stau[MROM_MAX_R];
-  __shared__ double rc[MROM_MAX_R], rs[MROM_MAX_R];
   __shared__ double2 salpha[MROM_MAX_R], sph[MROM_MAX_R];
   __shared__ double red[kPW];
-  __shared__ int s_task, s_nrot, s_m, s_done, s_fail;
+  __shared__ int s_task;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   double2* W0 = ws + (size_t)blockIdx.x * ws_elems;
@@ -101,6 +109,7 @@ pencil_prep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict_
     const int o = order[t];
     const RomDev& ob = objs[o];
     const PencilDev& pd = pens[o];
+    const PencilScratch& ps = scr[o];
     const int r = ob.r, rr = r * r;
     double2* W1 = W0 + rr;
     double2* W2 = W1 + rr;
@@ -356,152 +365,229 @@ pencil_prep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict_
       }
       __syncthreads();
 
-      // ---- 8. implicit QL with Wilkinson-type shifts on (sd, se), se[i] coupling i and i+1.
-      // Thread 0 chases one bulge at a time and records its rotations; then every thread
-      // applies them to its rows of Z (real and imaginary parts independently).
-      int l = 0, iter = 0;  // thread 0's state
-      for (;;) {
-        if (tid == 0) {
-          s_nrot = 0;
-          s_done = 0;
-          s_fail = 0;
-          bool emitted = false;
-          while (!emitted) {
-            if (l >= r) {
-              s_done = 1;
-              break;
-            }
-            int m = l;
-            while (m < r - 1 && fabs(se[m]) > DBL_EPSILON * (fabs(sd[m]) + fabs(sd[m + 1]))) ++m;
-            if (m == l) {
-              ++l;
-              iter = 0;
-              continue;
-            }
-            if (++iter > kQlMaxIter) {
-              s_fail = 1;
-              s_done = 1;
-              break;
-            }
-            double g = (sd[l + 1] - sd[l]) / (2.0 * se[l]);
-            double h = hypot(g, 1.0);
-            g = sd[m] - sd[l] + se[l] / (g + (g >= 0.0 ? h : -h));
-            double s = 1.0, c = 1.0, p = 0.0;
-            int nrot = 0;
-            bool underflow = false;
-            for (int i = m - 1; i >= l; --i) {
-              const double f = s * se[i], b = c * se[i];
-              h = hypot(f, g);
-              se[i + 1] = h;
-              if (h == 0.0) {
-                sd[i + 1] -= p;
-                se[m] = 0.0;
-                underflow = true;
-                break;
-              }
-              s = f / h;
-              c = g / h;
-              g = sd[i + 1] - p;
-              h = (sd[i] - g) * s + 2.0 * c * b;
-              p = s * h;
-              sd[i + 1] = g + p;
-              g = c * h - b;
-              rc[nrot] = c;
-              rs[nrot] = s;
-              ++nrot;
-            }
-            if (!underflow) {
-              sd[l] -= p;
-              se[l] = g;
-              se[m] = 0.0;
-            }
-            s_nrot = nrot;
-            s_m = m;
-            emitted = nrot > 0;
-          }
-        }
-        __syncthreads();
-        if (s_done) break;
-        // rotation q acts on columns (i, i+1), i = m-1-q:
-        //   Z[:, i+1] <- s Z[:, i] + c Z[:, i+1],  Z[:, i] <- c Z[:, i] - s Z[:, i+1]
-        {
-          const int nrot = s_nrot, m = s_m;
-          double* Zr = reinterpret_cast<double*>(W0);
-          for (int rp = tid; rp < 2 * r; rp += kPT) {
-            const int row = rp >> 1, part = rp & 1;
-            double* zrow = Zr + (size_t)2 * row * r + part;
-            double hi = zrow[2 * m];  // column i+1 of the first rotation
-            for (int q = 0; q < nrot; ++q) {
-              const int i = m - 1 - q;
-              const double lo = zrow[2 * i];
-              const double c = rc[q], s = rs[q];
-              zrow[2 * (i + 1)] = fma(s, lo, c * hi);
-              hi = fma(c, lo, -s * hi);
-            }
-            zrow[2 * (m - nrot)] = hi;
-          }
-        }
-        __syncthreads();
-      }
-      ok = ok && !s_fail;
-      __syncthreads();
-    }
-
-    // ---- 9. V = L^-H Z (W1): V[i][j] = sum_{k >= i} conj(Linv[k][i]) Z[k][j]
-    if (ok) {
+      // ---- 8. W = L^-H Z (per-object buffer): W[i][j] = sum_{k >= i} conj(Linv[k][i]) Z[k][j];
+      // the real tridiagonal (sd, se) goes to the QL kernel, W to the finishing kernel
       for (int idx = tid; idx < rr; idx += kPT) {
         const int i = idx / r, j = idx - (idx / r) * r;
-        double2 s = make_double2(0.0, 0.0);
-        for (int k = i; k < r; ++k) s = cmacc(s, W2[k * r + i], W0[k * r + j]);
-        W1[idx] = s;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = i; k < r; ++k) acc = cmacc(acc, W2[k * r + i], W0[k * r + j]);
+        ps.W[idx] = acc;
       }
-      __syncthreads();
-      // ---- 10. transformed data
-      for (int k = tid; k < r; k += kPT) pd.lam[k] = sd[k];
-      for (int idx = tid; idx < 3 * r; idx += kPT) {
-        const int k = idx / 3, j = idx - (idx / 3) * 3;
-        double2 s = make_double2(0.0, 0.0);
-        for (int a = 0; a < r; ++a) s = cmacc(s, W1[a * r + k], ob.B[a * 3 + j]);
-        pd.beta[idx] = s;  // beta[k][j] = (V^H B)[k][j]
-      }
-      if (pd.gsh) {
-        for (int idx = tid; idx < 6 * r; idx += kPT) {
-          const int k = idx / 6, q = idx - (idx / 6) * 6;
-          const double2* g = q < 3 ? ob.gsK + (size_t)q * r : ob.gsC + (size_t)(q - 3) * r;
-          double2 s = make_double2(0.0, 0.0);
-          for (int a = 0; a < r; ++a) s = cmac(s, g[a], W1[a * r + k]);
-          pd.gsh[idx] = s;  // gsh[k][q]: (gs_q V)[k]
-        }
-      }
-      // Gh_X = V^H G_X V for X = KK, CC, S (interleaved, packed lower triangle) and E = V^H Me V
-      const int nmat = (pd.Gh ? 3 : 0) + (pd.Eh ? 1 : 0);
-      for (int x = 0; x < nmat; ++x) {
-        const bool gram = pd.Gh != nullptr && x < 3;
-        const double2* G = !gram ? ob.Me : (x == 0 ? ob.GKK : (x == 1 ? ob.GCC : ob.GSk));
-        // Y = G V (W0)
-        for (int idx = tid; idx < rr; idx += kPT) {
-          const int i = idx / r, j = idx - (idx / r) * r;
-          double2 s = make_double2(0.0, 0.0);
-          for (int c = 0; c < r; ++c) s = cmac(s, G[i * r + c], W1[c * r + j]);
-          W0[idx] = s;
-        }
-        __syncthreads();
-        const int ntri = r * (r + 1) / 2;
-        for (int e = tid; e < ntri; e += kPT) {
-          int a, b;  // packed lower triangle: row a holds columns 0..a
-          tri_rc(e, a, b);
-          double2 s = make_double2(0.0, 0.0);
-          for (int c = 0; c < r; ++c) s = cmacc(s, W1[c * r + a], W0[c * r + b]);
-          if (gram)
-            pd.Gh[(size_t)e * 3 + x] = s;
-          else
-            pd.Eh[e] = s;
-        }
-        __syncthreads();
+      for (int k = tid; k < r; k += kPT) {
+        pd.lam[k] = sd[k];
+        ps.e[k] = se[k];
       }
     }
     if (tid == 0) pen_ok[o] = ok ? 1 : 0;
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ implicit QL
+//
+// One lane per object (objects of a warp have similar r): implicit QL with Wilkinson-type
+// shifts on the real symmetric tridiagonal (d, e), e[i] coupling i and i+1.  Each chase is
+// recorded as a sweep {m, rotations} with the rotations (c, s) on columns (i, i+1),
+// i = m-1, m-2, ...; the finishing kernel applies them.  d becomes the eigenvalues.  A log
+// that would overflow its capacity, or an eigenvalue that needs more than kQlMaxIter
+// chases, clears the object's pencil flag (it then takes the LU route).
+__global__ void __launch_bounds__(32)
+pencil_ql_kernel(const int* __restrict__ order, int n_elig, const RomDev* __restrict__ objs,
+                 const PencilDev* __restrict__ pens, const PencilScratch* __restrict__ scr,
+                 int* __restrict__ pen_ok, int lpw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sdd = reinterpret_cast<double*>(smem_raw);  // d[k][lane], then e[k][lane]
+  double* see = sdd + MROM_MAX_R * lpw;
+  const int lane = threadIdx.x;
+  const int t = blockIdx.x * lpw + lane;
+  if (lane >= lpw || t >= n_elig) return;
+  const int o = order[t];
+  if (!pen_ok[o]) return;
+  const int r = objs[o].r;
+  const PencilDev pd = pens[o];
+  const PencilScratch ps = scr[o];
+  double* d = sdd + lane;  // d[k * lpw]
+  double* e = see + lane;
+  for (int k = 0; k < r; ++k) {
+    d[k * lpw] = pd.lam[k];
+    e[k * lpw] = ps.e[k];
+  }
+  int nsw = 0, nrot_total = 0;
+  bool fail = false;
+  for (int l = 0; l < r && !fail; ++l) {
+    int iter = 0;
+    for (;;) {
+      int m = l;
+      while (m < r - 1 && fabs(e[m * lpw]) > DBL_EPSILON * (fabs(d[m * lpw]) + fabs(d[(m + 1) * lpw]))) ++m;
+      if (m == l) break;
+      if (++iter > kQlMaxIter || nsw >= ps.cap_sw || nrot_total + (m - l) > ps.cap_rot) {
+        fail = true;
+        break;
+      }
+      double g = (d[(l + 1) * lpw] - d[l * lpw]) / (2.0 * e[l * lpw]);
+      double h = fabs(g) < 1e150 ? sqrt(fma(g, g, 1.0)) : fabs(g);
+      g = d[m * lpw] - d[l * lpw] + e[l * lpw] / (g + (g >= 0.0 ? h : -h));
+      double sn = 1.0, cs = 1.0, p = 0.0;
+      int nrot = 0;
+      bool underflow = false;
+      double2* rot = ps.rot + nrot_total;
+      for (int i = m - 1; i >= l; --i) {
+        const double ei = e[i * lpw];
+        const double f = sn * ei, b = cs * ei;
+        const double h2 = fma(f, f, g * g);
+        if (h2 > 1e-280 && h2 < 1e280) {
+          const double rh = rsqrt(h2);
+          h = h2 * rh;
+          sn = f * rh;
+          cs = g * rh;
+        } else {
+          h = hypot(f, g);
+          if (h == 0.0) {
+            e[(i + 1) * lpw] = 0.0;
+            d[(i + 1) * lpw] -= p;
+            e[m * lpw] = 0.0;
+            underflow = true;
+            break;
+          }
+          sn = f / h;
+          cs = g / h;
+        }
+        e[(i + 1) * lpw] = h;
+        g = d[(i + 1) * lpw] - p;
+        h = fma(d[i * lpw] - g, sn, 2.0 * cs * b);
+        p = sn * h;
+        d[(i + 1) * lpw] = g + p;
+        g = fma(cs, h, -b);
+        rot[nrot++] = make_double2(cs, sn);
+      }
+      if (!underflow) {
+        d[l * lpw] -= p;
+        e[l * lpw] = g;
+        e[m * lpw] = 0.0;
+      }
+      if (nrot > 0) {
+        ps.sweeps[nsw++] = make_int2(m, nrot);
+        nrot_total += nrot;
+      }
+    }
+  }
+  for (int k = 0; k < r; ++k) pd.lam[k] = d[k * lpw];
+  *ps.nsw = nsw;
+  if (fail) pen_ok[o] = 0;
+}
+
+// ------------------------------------------------------------------ finishing
+//
+// One CTA per object.  Q2 (real r x r, shared memory, odd row stride) = the product of the
+// logged rotations, one row per thread (rows are independent); V = W Q2 (the generalised
+// eigenvectors, V^H C V = I); then beta = V^H B, gs V and the transformed Gram blocks.
+// Workspace per CTA: V and Y (r x r complex each).
+__global__ void __launch_bounds__(kPT, 1)
+pencil_finish_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__ pens,
+                     const PencilScratch* __restrict__ scr, const int* __restrict__ order, int n_elig,
+                     int* __restrict__ counter, const int* __restrict__ pen_ok, double2* __restrict__ ws,
+                     size_t ws_elems) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_task;
+  double* Q2 = reinterpret_cast<double*>(smem_raw);
+  const int tid = threadIdx.x;
+  double2* W1 = ws + (size_t)blockIdx.x * ws_elems;
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();
+    if (t >= n_elig) break;
+    const int o = order[t];
+    if (!pen_ok[o]) continue;  // uniform across the CTA
+    const RomDev& ob = objs[o];
+    const PencilDev& pd = pens[o];
+    const PencilScratch& ps = scr[o];
+    const int r = ob.r, rr = r * r;
+    const int ldq = r | 1;
+    double2* W0 = W1 + rr;
+    for (int idx = tid; idx < r * ldq; idx += kPT) {
+      const int i = idx / ldq, j = idx - (idx / ldq) * ldq;
+      Q2[idx] = i == j ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    // rotation q of a sweep acts on columns (i, i+1), i = m-1-q:
+    //   Q[:, i+1] <- s Q[:, i] + c Q[:, i+1],  Q[:, i] <- c Q[:, i] - s Q[:, i+1]
+    const int nsw = *ps.nsw;
+    for (int row = tid; row < r; row += kPT) {
+      double* q = Q2 + (size_t)row * ldq;
+      const double2* rot = ps.rot;
+      for (int k = 0; k < nsw; ++k) {
+        const int2 sw = ps.sweeps[k];
+        const int m = sw.x, nrot = sw.y;
+        double hi = q[m];
+        for (int u = 0; u < nrot; ++u) {
+          const int i = m - 1 - u;
+          const double2 cs = rot[u];
+          const double lo = q[i];
+          q[i + 1] = fma(cs.y, lo, cs.x * hi);
+          hi = fma(cs.x, lo, -cs.y * hi);
+        }
+        q[m - nrot] = hi;
+        rot += nrot;
+      }
+    }
+    __syncthreads();
+    // V = W Q2 (W1)
+    for (int idx = tid; idx < rr; idx += kPT) {
+      const int i = idx / r, j = idx - (idx / r) * r;
+      double2 acc = make_double2(0.0, 0.0);
+      const double2* wrow = ps.W + (size_t)i * r;
+      for (int k = 0; k < r; ++k) {
+        const double qk = Q2[k * ldq + j];
+        const double2 w = wrow[k];
+        acc.x = fma(w.x, qk, acc.x);
+        acc.y = fma(w.y, qk, acc.y);
+      }
+      W1[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 3 * r; idx += kPT) {
+      const int k = idx / 3, j = idx - (idx / 3) * 3;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int a = 0; a < r; ++a) acc = cmacc(acc, W1[a * r + k], ob.B[a * 3 + j]);
+      pd.beta[idx] = acc;  // beta[k][j] = (V^H B)[k][j]
+    }
+    if (pd.gsh) {
+      for (int idx = tid; idx < 6 * r; idx += kPT) {
+        const int k = idx / 6, q = idx - (idx / 6) * 6;
+        const double2* g = q < 3 ? ob.gsK + (size_t)q * r : ob.gsC + (size_t)(q - 3) * r;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int a = 0; a < r; ++a) acc = cmac(acc, g[a], W1[a * r + k]);
+        pd.gsh[idx] = acc;  // gsh[k][q]: (gs_q V)[k]
+      }
+    }
+    // Gh_X = V^H G_X V for X = KK, CC, S (interleaved, packed lower triangle) and E = V^H Me V
+    const int nmat = (pd.Gh ? 3 : 0) + (pd.Eh ? 1 : 0);
+    for (int x = 0; x < nmat; ++x) {
+      const bool gram = pd.Gh != nullptr && x < 3;
+      const double2* G = !gram ? ob.Me : (x == 0 ? ob.GKK : (x == 1 ? ob.GCC : ob.GSk));
+      // Y = G V (W0)
+      for (int idx = tid; idx < rr; idx += kPT) {
+        const int i = idx / r, j = idx - (idx / r) * r;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int c = 0; c < r; ++c) acc = cmac(acc, G[i * r + c], W1[c * r + j]);
+        W0[idx] = acc;
+      }
+      __syncthreads();
+      const int ntri = r * (r + 1) / 2;
+      for (int e = tid; e < ntri; e += kPT) {
+        int a, b;  // packed lower triangle: row a holds columns 0..a
+        tri_rc(e, a, b);
+        double2 acc = make_double2(0.0, 0.0);
+        for (int c = 0; c < r; ++c) acc = cmacc(acc, W1[c * r + a], W0[c * r + b]);
+        if (gram)
+          pd.Gh[(size_t)e * 3 + x] = acc;
+        else
+          pd.Eh[e] = acc;
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -809,12 +895,36 @@ size_t pencil_sweep_smem_bytes(int r, int F) {
 
 int pencil_threads() { return kPT; }
 
-cudaError_t launch_pencil_prep(const RomDev* objs, const PencilDev* pens, const int* order, int n_elig,
-                               int* counter, const double* omega, int omega_stride, int n_w,
-                               const double* s_sigma, int* pen_ok, double2* ws, size_t ws_elems, int grid,
-                               double gate, double kappa_max, cudaStream_t stream) {
-  pencil_prep_kernel<<<grid, kPT, 0, stream>>>(objs, pens, order, n_elig, counter, omega, omega_stride, n_w,
-                                               s_sigma, pen_ok, ws, ws_elems, gate, kappa_max);
+size_t pencil_finish_smem_bytes(int rmax) { return (size_t)rmax * (size_t)(rmax | 1) * sizeof(double); }
+
+cudaError_t launch_pencil_prep(const RomDev* objs, const PencilDev* pens, const PencilScratch* scr,
+                               const int* order, int n_elig, int* counters, const double* omega, int omega_stride,
+                               int n_w, const double* s_sigma, int* pen_ok, double2* ws, size_t ws_elems, int grid,
+                               int rmax, double gate, double kappa_max, cudaStream_t stream) {
+  pencil_tridiag_kernel<<<grid, kPT, 0, stream>>>(objs, pens, scr, order, n_elig, counters, omega, omega_stride, n_w,
+                                                  s_sigma, pen_ok, ws, ws_elems, gate, kappa_max);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // objects per warp (lanes in use): one object per warp spreads the chases over all SMs
+  // (masked lanes shorten the FP64 issue time of a warp instruction)
+  int lpw = kQlLanes;
+  if (const char* v = std::getenv("MROM_QL_LANES")) lpw = std::max(1, std::min(32, std::atoi(v)));
+  // at most one QL warp per SM sub-partition: a chase is a chain of dependent FP64
+  // operations, and two chases on one sub-partition slow each other down
+  int dev = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const size_t ql_smem = std::max<size_t>(2 * (size_t)MROM_MAX_R * lpw * sizeof(double), (size_t)per_sm / 4 - 2048);
+  e = cudaFuncSetAttribute(pencil_ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ql_smem);
+  if (e != cudaSuccess) return e;
+  pencil_ql_kernel<<<(n_elig + lpw - 1) / lpw, 32, ql_smem, stream>>>(order, n_elig, objs, pens, scr, pen_ok, lpw);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = pencil_finish_smem_bytes(rmax);
+  e = cudaFuncSetAttribute(pencil_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  pencil_finish_kernel<<<grid, kPT, smem, stream>>>(objs, pens, scr, order, n_elig, counters + 1, pen_ok, ws,
+                                                    ws_elems);
   return cudaGetLastError();
 }
 

@@ -138,7 +138,7 @@ def test_launch_count_increases(mrom, handle):
     before = handle.launch_count()
     mrom.mrom_sweep(handle, [rom], om, 2, R, torch.empty_like(R))
     handle.synchronize()
-    assert handle.launch_count() == before + (1 if handle.solver == "lu" else 4)
+    assert handle.launch_count() == before + (1 if handle.solver == "lu" else 6)
 
 
 def _plan_sweep(mrom, handle, objs, wo):
