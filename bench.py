@@ -44,8 +44,10 @@ UNIT = "evals/s"
 SM_COUNT_NOMINAL = 152
 DFMA_PER_CLK_PER_SM = 2           # measured: GB300 DFMA rate saturates at 4 flop/clk/SM
 FP64_MEASURED_TFLOPS = 1.189      # DFMA microbenchmark on this machine's GB300 (1.96 GHz)
-# DRAM traffic per sweep launch from an ncu capture of the current kernel (None until captured)
-SWEEP_DRAM_BYTES_PER_LAUNCH = None
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one pencil_sweep_kernel launch on
+# this workload, from a one-pass ncu capture of the current kernel (99,694,080 + 371,092,736 bytes);
+# None once the kernel changes until it is captured again
+SWEEP_DRAM_BYTES_PER_LAUNCH = 470786816
 
 
 def flops_per_eval(r: int, cert: bool = True) -> float:
