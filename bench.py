@@ -185,7 +185,7 @@ def project_flops(n: int, nnz: int, m: int, r: int, cert: bool = True) -> float:
 
 
 def measure_projection(m, h, n_grid: int = 96, n_s: int = 32):
-    """mrom_project on the 96^3 FIT grid (N = 2.6M) with 3 x 32 synthetic snapshot columns."""
+    """mrom_project on an n_grid^3 FIT grid (96^3: N = 2.6M) with 3 x 32 synthetic snapshot columns."""
     import torch
     from workloads import CUBE_C2, fit_problem, synthetic_snapshot_matrix
     p = fit_problem(n_grid, CUBE_C2, static=False)
@@ -213,7 +213,7 @@ def measure_projection(m, h, n_grid: int = 96, n_s: int = 32):
     dt32 = time.perf_counter() - t0
     rom.close()
     h.set_projection_precision(False)
-    return {"workload": f"mrom_project: 96^3 FIT grid (N = {p.N}, {p.K.nnz} nnz), 3 x {n_s} snapshot columns, "
+    return {"workload": f"mrom_project: {n_grid}^3 FIT grid (N = {p.N}, {p.K.nnz} nnz), 3 x {n_s} snapshot columns, "
                         f"TOL_Sigma 1e-6 -> r = {r}, certificate Gram with diagonal X",
             "seconds": dt, "r": r, "flops": fl, "achieved_tflops": fl / dt / 1e12,
             "bound": "alu", "fp64_frac": fl / dt / 1e12 / (SM_COUNT_NOMINAL * DFMA_PER_CLK_PER_SM * 2 * 2.07e9 / 1e12),
@@ -270,6 +270,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mixed", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--lu-route", action=argparse.BooleanOptionalAction, default=True)
+    ap.add_argument("--projection-only", action="store_true",
+                    help="time mrom_project alone (float64 and complex64 products) and print its record")
+    ap.add_argument("--projection-grid", type=int, default=96)
     ap.add_argument("--projection", action=argparse.BooleanOptionalAction, default=True)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
@@ -292,6 +295,14 @@ def main():
 
     import paper_2307_05590_gb300 as m
     from workloads import log_omegas
+
+    if args.projection_only:
+        stream = torch.cuda.Stream(dev)
+        h = m.Handle(local_rank, stream.cuda_stream)
+        if rank == 0:
+            print(json.dumps({"projection": measure_projection(m, h, n_grid=args.projection_grid)}), flush=True)
+        h.close()
+        return
 
     objs = dictionary(args.n_obj, 20230711 + rank)
     wo = log_omegas(1e1, 1e8, args.n_w)

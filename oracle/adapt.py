@@ -40,7 +40,7 @@ def adaptive_podp(problem, snapshot_fn, omega0, omega_out, *, tol_sigma=1e-6, to
     """Run Algorithm 1; returns (model, snapshot omegas, Lambda history, k).
 
     snapshot_fn(omegas) must return the (3, N, len(omegas)) full-order
-    solutions at those frequencies (lines 4 and 16 of the algorithm).
+    solutions at those frequencies (the initial and the added full-order snapshots).
     """
     omega_out = np.asarray(omega_out, dtype=np.float64)
     snaps = np.asarray(omega0, dtype=np.float64)

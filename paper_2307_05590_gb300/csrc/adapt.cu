@@ -139,7 +139,7 @@ extern "C" mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const doub
   if (s != MROM_OK) return s;
   while (Lam / b_alpha > opts->tol_delta && k < opts->max_k) {
     ++k;
-    // certificates of the current reduced model on the output grid (Algorithm 1, lines 10-11)
+    // certificates of the current reduced model on the output grid (Algorithm 1)
     s = mrom_certificate(h, &rom, 1, omega_out, n_out, 0, static_cast<double*>(Delta.p));
     if (s == MROM_OK) s = mrom_synchronize(h);
     if (s != MROM_OK) {
@@ -166,14 +166,14 @@ extern "C" mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const doub
       mrom_rom_free(rom);
       return cuda_fail(h, e, "mrom_adapt: interval maxima");
     }
-    // Lambda = max_n Lambda_n (lines 12-14)
+    // Lambda = max_n Lambda_n
     Lam = -std::numeric_limits<double>::infinity();
     for (int i = 0; i < nint; ++i)
       if (arg[i] >= 0) Lam = std::max(Lam, lam[i]);
     if (lambda_hist && nh < opts->max_k) lambda_hist[nh] = Lam;
     ++nh;
     if (!(Lam / b_alpha > opts->tol_delta)) break;
-    // the N* intervals with the largest Lambda_n, one new snapshot each (line 15)
+    // the N* intervals with the largest Lambda_n, one new snapshot each
     std::vector<int> order(nint);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -187,7 +187,7 @@ extern "C" mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const doub
     if (fresh.empty()) break;
     std::sort(fresh.begin(), fresh.end());
     const int nn = (int)fresh.size();
-    // full-order snapshots from the caller (line 16), uploaded after the columns already held
+    // full-order snapshots from the caller, uploaded after the columns already held
     stage.assign((size_t)3 * nn * n, make_double2(0.0, 0.0));
     if (cb(user, nn, fresh.data(), stage.data()) != 0) {
       mrom_rom_free(rom);
@@ -200,7 +200,7 @@ extern "C" mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const doub
     }
     snaps.insert(snaps.end(), fresh.begin(), fresh.end());
     ns += nn;
-    // updated TSVD and projection (lines 17-19)
+    // updated TSVD and projection
     s = rebuild();
     if (s != MROM_OK) return s;
   }

@@ -20,6 +20,7 @@
 // exceeds the gate, whose C is not numerically positive definite, or whose QL iteration
 // does not converge are routed to the LU kernel instead (device-side routing, no host sync).
 #include "mrom_internal.h"
+#include "herm_tridiag.cuh"
 
 #include <algorithm>
 #include <cfloat>
@@ -41,15 +42,7 @@ __device__ __forceinline__ double2 cmacc(double2 c, double2 a, double2 b) {  // 
   return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
 }
 
-// Row and column of entry e of a packed lower triangle (row i holds columns 0..i):
-// e = i (i + 1) / 2 + j.  Float square root, then exact integer correction.
-__device__ __forceinline__ void tri_rc(int e, int& i, int& j) {
-  int t = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-  while (t * (t + 1) / 2 > e) --t;
-  while ((t + 1) * (t + 2) / 2 <= e) ++t;
-  i = t;
-  j = e - t * (t + 1) / 2;
-}
+using hq::tri_rc;
 
 // CTA-wide sum / minimum of one value per thread (every thread gets the result; fixed order).
 __device__ double block_sum(double v, double* red) {
@@ -97,7 +90,6 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
   __shared__ double red[kPW];
   __shared__ int s_task;
   const int tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
   double2* W0 = ws + (size_t)blockIdx.x * ws_elems;
 
   for (;;) {
@@ -226,144 +218,10 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
     hn = block_sum(hn, red);
     ok = ok && (DBL_EPSILON * sqrt(hn) <= gate * wmin);
 
-    // ---- 5. Householder tridiagonalisation of H (W1): for column k, x = H[k+1:, k],
-    // alpha = -phase(x_0) ||x||, v = x - alpha e_1, tau = 1 / (||x|| (||x|| + |x_0|)),
-    // P = I - tau v v^H; H_sub <- P H_sub P = H_sub - v w^H - w v^H with
-    // p = tau H_sub v, w = p - (tau/2)(v^H p) v.  v is kept in column k below the diagonal.
+    // ---- 5.-7. Householder tridiagonalisation of H (W1), Z = Q1 D (W0), real tridiagonal (sd, se);
+    // p of each Householder step lives in W0's first row (W0 is free until Q1 is formed)
     if (ok) {
-      double2* pv = W0;  // p (length r) in W0's first row; W0 is free until step 6
-      for (int k = 0; k + 2 < r; ++k) {
-        const int m = r - k - 1;
-        double nx2 = 0.0;
-        for (int i = tid; i < m; i += kPT) {
-          const double2 x = W1[(k + 1 + i) * r + k];
-          nx2 += x.x * x.x + x.y * x.y;
-        }
-        nx2 = block_sum(nx2, red);
-        if (tid == 0) sd[k] = W1[k * r + k].x;
-        if (!(nx2 > 0.0)) {  // column already reduced
-          if (tid == 0) {
-            stau[k] = 0.0;
-            salpha[k] = make_double2(0.0, 0.0);
-          }
-          continue;
-        }
-        const double nx = sqrt(nx2);
-        const double2 x0 = W1[(k + 1) * r + k];
-        const double a0 = hypot(x0.x, x0.y);
-        const double2 ph = a0 > 0.0 ? make_double2(x0.x / a0, x0.y / a0) : make_double2(1.0, 0.0);
-        const double tau = 1.0 / (nx * (nx + a0));
-        // v_0 = x_0 - alpha = ph (|x_0| + ||x||); the other entries of v are those of x
-        __syncthreads();  // every thread has read x_0 before it is overwritten
-        if (tid == 0) {
-          W1[(k + 1) * r + k] = make_double2(ph.x * (a0 + nx), ph.y * (a0 + nx));
-          stau[k] = tau;
-          salpha[k] = make_double2(-ph.x * nx, -ph.y * nx);
-        }
-        __syncthreads();
-        // p = tau H_sub v: one warp per row, lanes along the row
-        for (int i = warp; i < m; i += kPW) {
-          double2 s = make_double2(0.0, 0.0);
-          const double2* hrow = W1 + (size_t)(k + 1 + i) * r + (k + 1);
-          for (int j = lane; j < m; j += 32) s = cmac(s, hrow[j], W1[(k + 1 + j) * r + k]);
-          for (int off = 16; off > 0; off >>= 1) {
-            s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
-            s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
-          }
-          if (lane == 0) pv[i] = make_double2(tau * s.x, tau * s.y);
-        }
-        __syncthreads();
-        // K = (tau/2) v^H p (real for Hermitian H_sub)
-        double kr = 0.0;
-        for (int i = tid; i < m; i += kPT) {
-          const double2 v = W1[(k + 1 + i) * r + k], p = pv[i];
-          kr += fma(v.x, p.x, v.y * p.y);
-        }
-        kr = 0.5 * tau * block_sum(kr, red);
-        // w = p - K v (in place of p)
-        for (int i = tid; i < m; i += kPT) {
-          const double2 v = W1[(k + 1 + i) * r + k], p = pv[i];
-          pv[i] = make_double2(fma(-kr, v.x, p.x), fma(-kr, v.y, p.y));
-        }
-        __syncthreads();
-        // H_sub -= v w^H + w v^H on the lower triangle, mirrored into the upper one
-        for (int e = tid; e < m * (m + 1) / 2; e += kPT) {
-          int i, j;
-          tri_rc(e, i, j);
-          const double2 vi = W1[(k + 1 + i) * r + k], vj = W1[(k + 1 + j) * r + k];
-          const double2 wi = pv[i], wj = pv[j];
-          double2 a = W1[(k + 1 + i) * r + (k + 1 + j)];
-          // a - vi conj(wj) - wi conj(vj)
-          a.x = fma(-vi.x, wj.x, fma(-vi.y, wj.y, fma(-wi.x, vj.x, fma(-wi.y, vj.y, a.x))));
-          a.y = fma(-vi.y, wj.x, fma(vi.x, wj.y, fma(-wi.y, vj.x, fma(wi.x, vj.y, a.y))));
-          if (i == j) a.y = 0.0;
-          W1[(k + 1 + i) * r + (k + 1 + j)] = a;
-          if (i != j) W1[(k + 1 + j) * r + (k + 1 + i)] = make_double2(a.x, -a.y);
-        }
-        __syncthreads();
-      }
-      // the last 2 x 2 block is already tridiagonal
-      if (tid == 0) {
-        for (int k = (r >= 2 ? r - 2 : 0); k < r; ++k) sd[k] = W1[k * r + k].x;
-        if (r >= 2) {
-          salpha[r - 2] = W1[(r - 1) * r + (r - 2)];
-          stau[r - 2] = 0.0;
-        }
-      }
-      __syncthreads();
-
-      // ---- 6. Q1 = P_0 P_1 ... P_{r-3} (W0), backward accumulation on the trailing block
-      for (int idx = tid; idx < rr; idx += kPT) {
-        const int i = idx / r, j = idx - (idx / r) * r;
-        W0[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-      }
-      __syncthreads();
-      for (int k = r - 3; k >= 0; --k) {
-        const double tau = stau[k];
-        if (tau == 0.0) continue;
-        const int m = r - k - 1;
-        // u_j = sum_i conj(v_i) Q[k+1+i][k+1+j], then Q_sub -= tau v u
-        for (int j = tid; j < m; j += kPT) {
-          double2 s = make_double2(0.0, 0.0);
-          for (int i = 0; i < m; ++i) s = cmacc(s, W1[(k + 1 + i) * r + k], W0[(k + 1 + i) * r + (k + 1 + j)]);
-          sph[j] = make_double2(tau * s.x, tau * s.y);
-        }
-        __syncthreads();
-        for (int idx = tid; idx < m * m; idx += kPT) {
-          const int i = idx / m, j = idx - (idx / m) * m;
-          const double2 v = W1[(k + 1 + i) * r + k], u = sph[j];
-          double2 a = W0[(k + 1 + i) * r + (k + 1 + j)];
-          a.x = fma(-v.x, u.x, fma(v.y, u.y, a.x));
-          a.y = fma(-v.x, u.y, fma(-v.y, u.x, a.y));
-          W0[(k + 1 + i) * r + (k + 1 + j)] = a;
-        }
-        __syncthreads();
-      }
-
-      // ---- 7. phases: D_0 = 1, D_{k+1} = D_k e_k / |e_k| makes D^H T D real with
-      // off-diagonal |e_k|; Z = Q1 D
-      if (tid == 0) {
-        double2 D = make_double2(1.0, 0.0);
-        sph[0] = D;
-        for (int k = 0; k + 1 < r; ++k) {
-          const double2 e = salpha[k];
-          const double ae = hypot(e.x, e.y);
-          se[k] = ae;
-          if (ae > 0.0) {
-            const double2 u = make_double2(e.x / ae, e.y / ae);
-            D = make_double2(D.x * u.x - D.y * u.y, D.x * u.y + D.y * u.x);
-          }
-          sph[k + 1] = D;
-        }
-        se[r - 1] = 0.0;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < rr; idx += kPT) {
-        const int j = idx - (idx / r) * r;
-        const double2 a = W0[idx], D = sph[j];
-        W0[idx] = make_double2(a.x * D.x - a.y * D.y, a.x * D.y + a.y * D.x);
-      }
-      __syncthreads();
+      hq::herm_tridiag<kPT>(W1, r, W0, sd, se, stau, salpha, sph, W0, red);
 
       // ---- 8. W = L^-H Z (per-object buffer): W[i][j] = sum_{k >= i} conj(Linv[k][i]) Z[k][j];
       // the real tridiagonal (sd, se) goes to the QL kernel, W to the finishing kernel

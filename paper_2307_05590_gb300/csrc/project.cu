@@ -12,6 +12,7 @@
 // (the snapshot and basis streams are re-read from L2), so they are written for
 // full FP64 utilisation with register tiles rather than for HBM streaming.
 #include "mrom_internal.h"
+#include "herm_tridiag.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -29,33 +30,59 @@ __device__ __forceinline__ double2 c_mac(double2 c, double2 a, double2 b) {  // 
 
 // ------------------------------------------------------------------ tall Gram
 // part[split][a][b] = sum_{n in split} conj(A[n][a]) * wgt(n) * B[n][b]
-// Element (n, c) of A is A[n * rsA + c * csA] (any layout).  One CTA computes a
-// kGT x kGT output tile over its row range; 256 threads hold 2 x 2 outputs each.
+// Element (n, c) of A is A[n * rsA + c * csA] (any layout).  One CTA computes a Ta x Tb
+// output tile (even sizes up to kGT, chosen so that the tiles cover ma x mb with little
+// padding) over its row range; (Ta/2) (Tb/2) threads hold 2 x 2 outputs each.
 constexpr int kGT = 32;
 constexpr int kGR = 32;
+
+// The 2 x 2 output block (ty, tx) of thread tid.  On a diagonal tile of a Hermitian product
+// only the blocks with ty <= tx are computed (the rest is mirrored by the reduction), with
+// the threads packed so that the idle ones form whole warps.
+__device__ __forceinline__ void gram_thread_block(bool upper_only, int ha, int hb, int tid, bool& active, int& ty,
+                                                  int& tx) {
+  if (upper_only) {
+    const int nu = hb * (hb + 1) / 2;
+    active = tid < nu;
+    int i = 0, j = 0;
+    if (active) hq::tri_rc(nu - 1 - tid, i, j);  // i >= j in the reversed triangle
+    ty = hb - 1 - i;
+    tx = hb - 1 - j;
+  } else {
+    active = tid < ha * hb;
+    ty = tid / hb;
+    tx = tid - (tid / hb) * hb;
+  }
+}
 
 __global__ void __launch_bounds__(256)
 gram_partial_kernel(const double2* __restrict__ A, int64_t rsA, int64_t csA, int ma,
                     const double2* __restrict__ B, int64_t rsB, int64_t csB, int mb,
                     const double* __restrict__ w, int wmode, int64_t n, int64_t rows_per_split,
-                    const int2* __restrict__ tiles, double2* __restrict__ part) {
+                    const int2* __restrict__ tiles, int Ta, int Tb, int herm, double2* __restrict__ part) {
   __shared__ double2 As[kGR][kGT + 1];
   __shared__ double2 Bs[kGR][kGT + 1];
   const int tid = threadIdx.x;
-  const int ty = tid >> 4, tx = tid & 15;
+  const int hb = Tb >> 1;
   const int2 tile = tiles[blockIdx.y];
-  const int a_base = tile.x * kGT, b_base = tile.y * kGT;
+  bool active;
+  int ty, tx;
+  gram_thread_block(herm && tile.x == tile.y, Ta >> 1, hb, tid, active, ty, tx);
+  const int a_base = tile.x * Ta, b_base = tile.y * Tb;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_split;
   const int64_t r1 = min(n, r0 + rows_per_split);
   double2 acc[2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
   for (int64_t row0 = r0; row0 < r1; row0 += kGR) {
-    for (int idx = tid; idx < kGR * kGT; idx += 256) {
+    for (int idx = tid; idx < kGR * Ta; idx += 256) {
       int rr, cc;
-      if (csA == 1) { rr = idx / kGT; cc = idx % kGT; } else { cc = idx / kGR; rr = idx % kGR; }
+      if (csA == 1) { rr = idx / Ta; cc = idx - rr * Ta; } else { cc = idx / kGR; rr = idx - cc * kGR; }
       const int64_t nr = row0 + rr;
       const int col = a_base + cc;
       As[rr][cc] = (nr < r1 && col < ma) ? A[nr * rsA + col * csA] : make_double2(0.0, 0.0);
-      if (csB == 1) { rr = idx / kGT; cc = idx % kGT; } else { cc = idx / kGR; rr = idx % kGR; }
+    }
+    for (int idx = tid; idx < kGR * Tb; idx += 256) {
+      int rr, cc;
+      if (csB == 1) { rr = idx / Tb; cc = idx - rr * Tb; } else { cc = idx / kGR; rr = idx - cc * kGR; }
       const int64_t nb = row0 + rr;
       const int colb = b_base + cc;
       double2 v = make_double2(0.0, 0.0);
@@ -70,17 +97,20 @@ gram_partial_kernel(const double2* __restrict__ A, int64_t rsA, int64_t csA, int
       Bs[rr][cc] = v;
     }
     __syncthreads();
+    if (active) {
 #pragma unroll 8
-    for (int rr = 0; rr < kGR; ++rr) {
-      const double2 a0 = As[rr][ty * 2], a1 = As[rr][ty * 2 + 1];
-      const double2 b0 = Bs[rr][tx * 2], b1 = Bs[rr][tx * 2 + 1];
-      acc[0][0] = c_conj_mac(acc[0][0], a0, b0);
-      acc[0][1] = c_conj_mac(acc[0][1], a0, b1);
-      acc[1][0] = c_conj_mac(acc[1][0], a1, b0);
-      acc[1][1] = c_conj_mac(acc[1][1], a1, b1);
+      for (int rr = 0; rr < kGR; ++rr) {
+        const double2 a0 = As[rr][ty * 2], a1 = As[rr][ty * 2 + 1];
+        const double2 b0 = Bs[rr][tx * 2], b1 = Bs[rr][tx * 2 + 1];
+        acc[0][0] = c_conj_mac(acc[0][0], a0, b0);
+        acc[0][1] = c_conj_mac(acc[0][1], a0, b1);
+        acc[1][0] = c_conj_mac(acc[1][0], a1, b0);
+        acc[1][1] = c_conj_mac(acc[1][1], a1, b1);
+      }
     }
     __syncthreads();
   }
+  if (!active) return;
   double2* out = part + (size_t)blockIdx.x * ma * mb;
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -100,21 +130,28 @@ __device__ __forceinline__ float2 f_conj_mac(float2 c, float2 a, float2 b) {  //
 __global__ void __launch_bounds__(256)
 gram_partial_f32_kernel(const float2* __restrict__ A, int64_t rsA, int ma, const float2* __restrict__ B, int64_t rsB,
                         int mb, const float* __restrict__ w, int64_t n, int64_t rows_per_split,
-                        const int2* __restrict__ tiles, float2* __restrict__ part) {
+                        const int2* __restrict__ tiles, int Ta, int Tb, int herm, float2* __restrict__ part) {
   __shared__ float2 As[kGR][kGT + 1];
   __shared__ float2 Bs[kGR][kGT + 1];
   const int tid = threadIdx.x;
-  const int ty = tid >> 4, tx = tid & 15;
+  const int hb = Tb >> 1;
   const int2 tile = tiles[blockIdx.y];
-  const int a_base = tile.x * kGT, b_base = tile.y * kGT;
+  bool active;
+  int ty, tx;
+  gram_thread_block(herm && tile.x == tile.y, Ta >> 1, hb, tid, active, ty, tx);
+  const int a_base = tile.x * Ta, b_base = tile.y * Tb;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_split;
   const int64_t r1 = min(n, r0 + rows_per_split);
   float2 acc[2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
   for (int64_t row0 = r0; row0 < r1; row0 += kGR) {
-    for (int idx = tid; idx < kGR * kGT; idx += 256) {
-      const int rr = idx / kGT, cc = idx % kGT;
+    for (int idx = tid; idx < kGR * Ta; idx += 256) {
+      const int rr = idx / Ta, cc = idx - (idx / Ta) * Ta;
       const int64_t nr = row0 + rr;
       As[rr][cc] = (nr < r1 && a_base + cc < ma) ? A[nr * rsA + a_base + cc] : make_float2(0.f, 0.f);
+    }
+    for (int idx = tid; idx < kGR * Tb; idx += 256) {
+      const int rr = idx / Tb, cc = idx - (idx / Tb) * Tb;
+      const int64_t nr = row0 + rr;
       float2 v = make_float2(0.f, 0.f);
       if (nr < r1 && b_base + cc < mb) {
         v = B[nr * rsB + b_base + cc];
@@ -126,17 +163,20 @@ gram_partial_f32_kernel(const float2* __restrict__ A, int64_t rsA, int ma, const
       Bs[rr][cc] = v;
     }
     __syncthreads();
+    if (active) {
 #pragma unroll 8
-    for (int rr = 0; rr < kGR; ++rr) {
-      const float2 a0 = As[rr][ty * 2], a1 = As[rr][ty * 2 + 1];
-      const float2 b0 = Bs[rr][tx * 2], b1 = Bs[rr][tx * 2 + 1];
-      acc[0][0] = f_conj_mac(acc[0][0], a0, b0);
-      acc[0][1] = f_conj_mac(acc[0][1], a0, b1);
-      acc[1][0] = f_conj_mac(acc[1][0], a1, b0);
-      acc[1][1] = f_conj_mac(acc[1][1], a1, b1);
+      for (int rr = 0; rr < kGR; ++rr) {
+        const float2 a0 = As[rr][ty * 2], a1 = As[rr][ty * 2 + 1];
+        const float2 b0 = Bs[rr][tx * 2], b1 = Bs[rr][tx * 2 + 1];
+        acc[0][0] = f_conj_mac(acc[0][0], a0, b0);
+        acc[0][1] = f_conj_mac(acc[0][1], a0, b1);
+        acc[1][0] = f_conj_mac(acc[1][0], a1, b0);
+        acc[1][1] = f_conj_mac(acc[1][1], a1, b1);
+      }
     }
     __syncthreads();
   }
+  if (!active) return;
   float2* out = part + (size_t)blockIdx.x * ma * mb;
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -148,13 +188,13 @@ gram_partial_f32_kernel(const float2* __restrict__ A, int64_t rsA, int ma, const
 }
 
 __global__ void gram_reduce_f32_kernel(const float2* __restrict__ part, int nsplit, int ma, int mb, int hermitian,
-                                       double2* __restrict__ G, int64_t ldg) {
+                                       int T, double2* __restrict__ G, int64_t ldg) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)ma * mb;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int a = (int)(idx / mb), b = (int)(idx % mb);
     int sa = a, sb = b;
     bool conj = false;
-    if (hermitian && (b / kGT) < (a / kGT)) {
+    if (hermitian && b < a) {
       sa = b;
       sb = a;
       conj = true;
@@ -204,16 +244,17 @@ __global__ void to_f32_kernel(const double* __restrict__ x, int64_t n, double sc
     y[i] = (float)(scale * x[i]);
 }
 
-// G[a][b] = sum over splits (fixed order).  Hermitian: only tiles with b-tile >= a-tile
-// were computed; the rest is mirrored and the diagonal made real.
+// G[a][b] = sum over splits (fixed order).  Hermitian: the upper triangle was computed
+// (tiles with b-tile >= a-tile, upper blocks of the diagonal tiles); the rest is mirrored
+// and the diagonal made real.
 __global__ void gram_reduce_kernel(const double2* __restrict__ part, int nsplit, int ma, int mb, int hermitian,
-                                   double2* __restrict__ G, int64_t ldg) {
+                                   int T, double2* __restrict__ G, int64_t ldg) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)ma * mb;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int a = (int)(idx / mb), b = (int)(idx % mb);
     int sa = a, sb = b;
     bool conj = false;
-    if (hermitian && (b / kGT) < (a / kGT)) {
+    if (hermitian && b < a) {
       sa = b;
       sb = a;
       conj = true;
@@ -230,120 +271,26 @@ __global__ void gram_reduce_kernel(const double2* __restrict__ part, int nsplit,
   }
 }
 
-// ---------------------------------------------------------- Jacobi eigensolver
-// Cyclic Jacobi for a Hermitian m x m matrix with the round-robin (circle) ordering:
-// every round rotates m/2 disjoint pairs in parallel, A <- J^H A J (columns, then
-// rows), V <- V J.  For the pair (p, q): tau = (a_qq - a_pp) / (2 |a_pq|),
-// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1+t^2), z = t c a_pq/|a_pq|,
-// A[:,p] <- c A[:,p] - conj(z) A[:,q], A[:,q] <- z A[:,p] + c A[:,q] (rows: with z).
-// One CTA; A and V live in global memory (L2-resident).  A bounded number of sweeps;
-// *status gets kStatusTimeout if the off-diagonal norm did not converge.
-__global__ void __launch_bounds__(1024)
-jacobi_eig_kernel(double2* __restrict__ A, double2* __restrict__ V, int m, int max_sweeps, double tol,
-                  double* __restrict__ lam, int* __restrict__ status) {
-  __shared__ int sp[128], sq[128];
-  __shared__ double sc[128];
-  __shared__ double2 sz[128];
-  __shared__ double red[2][32];
-  __shared__ int s_done;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int64_t idx = tid; idx < (int64_t)m * m; idx += nt) {
-    const int i = (int)(idx / m), j = (int)(idx % m);
-    V[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-  }
-  const int n = m + (m & 1), half = n / 2;
-  bool converged = false;
-  for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
-    // off-diagonal and total Frobenius norms
-    double off = 0.0, tot = 0.0;
-    for (int64_t idx = tid; idx < (int64_t)m * m; idx += nt) {
-      const double2 v = A[idx];
-      const double s2 = v.x * v.x + v.y * v.y;
-      tot += s2;
-      if (idx / m != idx % m) off += s2;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    }
-    if ((tid & 31) == 0) {
-      red[0][tid >> 5] = off;
-      red[1][tid >> 5] = tot;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double o2 = 0.0, t2 = 0.0;
-      for (int k = 0; k < nt / 32; ++k) {
-        o2 += red[0][k];
-        t2 += red[1][k];
-      }
-      s_done = (o2 <= tol * tol * t2) ? 1 : 0;
-    }
-    __syncthreads();
-    if (s_done) {
-      converged = true;
-      break;
-    }
-    if (sweep == max_sweeps) break;
-    for (int t = 0; t < n - 1; ++t) {
-      if (tid < half) {
-        const int k = tid;
-        const int i1 = (k == 0) ? 0 : 1 + ((k - 1 + t) % (n - 1));
-        const int kk = n - 1 - k;
-        const int i2 = 1 + ((kk - 1 + t) % (n - 1));
-        const int p = min(i1, i2), q = max(i1, i2);
-        double c = 1.0;
-        double2 z = make_double2(0.0, 0.0);
-        if (q < m) {
-          const double2 apq = A[(int64_t)p * m + q];
-          const double g = hypot(apq.x, apq.y);
-          if (g > 0.0) {
-            const double app = A[(int64_t)p * m + p].x, aqq = A[(int64_t)q * m + q].x;
-            const double tau = (aqq - app) / (2.0 * g);
-            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + tt * tt);
-            const double s = tt * c;
-            z = make_double2(s * apq.x / g, s * apq.y / g);
-          }
-        }
-        sp[k] = p;
-        sq[k] = q;
-        sc[k] = c;
-        sz[k] = z;
-      }
-      __syncthreads();
-      // columns p, q of A and V (rows i of every pair; pairs are disjoint)
-      for (int64_t idx = tid; idx < (int64_t)m * half; idx += nt) {
-        const int i = (int)(idx / half), k = (int)(idx % half);
-        const int p = sp[k], q = sq[k];
-        if (q >= m) continue;
-        const double c = sc[k];
-        const double2 z = sz[k];
-        const double2 ap = A[(int64_t)i * m + p], aq = A[(int64_t)i * m + q];
-        // c ap - conj(z) aq ; z ap + c aq
-        A[(int64_t)i * m + p] = make_double2(c * ap.x - (z.x * aq.x + z.y * aq.y), c * ap.y - (z.x * aq.y - z.y * aq.x));
-        A[(int64_t)i * m + q] = make_double2(z.x * ap.x - z.y * ap.y + c * aq.x, z.x * ap.y + z.y * ap.x + c * aq.y);
-        const double2 vp = V[(int64_t)i * m + p], vq = V[(int64_t)i * m + q];
-        V[(int64_t)i * m + p] = make_double2(c * vp.x - (z.x * vq.x + z.y * vq.y), c * vp.y - (z.x * vq.y - z.y * vq.x));
-        V[(int64_t)i * m + q] = make_double2(z.x * vp.x - z.y * vp.y + c * vq.x, z.x * vp.y + z.y * vp.x + c * vq.y);
-      }
-      __syncthreads();
-      // rows p, q of A: A[p,:] <- c A[p,:] - z A[q,:], A[q,:] <- conj(z) A[p,:] + c A[q,:]
-      for (int64_t idx = tid; idx < (int64_t)m * half; idx += nt) {
-        const int k = (int)(idx / m), j = (int)(idx % m);
-        const int p = sp[k], q = sq[k];
-        if (q >= m) continue;
-        const double c = sc[k];
-        const double2 z = sz[k];
-        const double2 ap = A[(int64_t)p * m + j], aq = A[(int64_t)q * m + j];
-        A[(int64_t)p * m + j] = make_double2(c * ap.x - (z.x * aq.x - z.y * aq.y), c * ap.y - (z.x * aq.y + z.y * aq.x));
-        A[(int64_t)q * m + j] = make_double2(z.x * ap.x + z.y * ap.y + c * aq.x, z.x * ap.y - z.y * ap.x + c * aq.y);
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = tid; i < m; i += nt) lam[i] = A[(int64_t)i * m + i].x;
-  if (tid == 0 && !converged) atomicOr(status, kStatusTimeout);
+// ------------------------------------------------ Householder + QL eigensolver
+// Hermitian m x m A = Z Lambda Z^H (A overwritten): Householder tridiagonalisation, then
+// implicit QL with the rotations accumulated into Z (columns = eigenvectors).  One CTA.
+// *status gets kStatusTimeout if QL did not converge.
+constexpr int kEigThreads = 512;
+
+__global__ void __launch_bounds__(kEigThreads)
+herm_eig_kernel(double2* __restrict__ A, int m, double2* __restrict__ Z, double* __restrict__ lam,
+                int* __restrict__ status) {
+  __shared__ double sd[MROM_MAX_SNAPSHOTS], se[MROM_MAX_SNAPSHOTS], stau[MROM_MAX_SNAPSHOTS];
+  __shared__ double rc[MROM_MAX_SNAPSHOTS], rs[MROM_MAX_SNAPSHOTS];
+  __shared__ double2 salpha[MROM_MAX_SNAPSHOTS], sph[MROM_MAX_SNAPSHOTS], pv[MROM_MAX_SNAPSHOTS];
+  __shared__ double red[kEigThreads / 32];
+  __shared__ int flags[4];
+  if (threadIdx.x < 4) flags[threadIdx.x] = 0;
+  __syncthreads();
+  hq::herm_tridiag<kEigThreads>(A, m, Z, sd, se, stau, salpha, sph, pv, red);
+  const bool ok = hq::ql_single<kEigThreads>(sd, se, m, Z, rc, rs, flags, 60);
+  for (int i = threadIdx.x; i < m; i += kEigThreads) lam[i] = sd[i];
+  if (threadIdx.x == 0 && !ok) atomicOr(status, kStatusTimeout);
 }
 
 // ------------------------------------------------------------- basis apply
@@ -468,6 +415,31 @@ __global__ void scale_kernel(const double* __restrict__ x, double a, int64_t n, 
     y[i] = a * x[i];
 }
 
+// UO[n] = [U[n][0..r) | O[n][0..3)] (row-major, r + 3 columns)
+__global__ void concat_uo_kernel(const double2* __restrict__ U, int r, const double2* __restrict__ O, int64_t n,
+                                 double2* __restrict__ UO) {
+  const int m = r + 3;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * m;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / m;
+    const int c = (int)(idx - row * m);
+    UO[idx] = c < r ? U[row * r + c] : O[row * 3 + (c - r)];
+  }
+}
+
+// Blocks of the (r+3) x (r+3) Gram of [U | O]: C_r (r x r), B = U^H C O (r x 3), c00 (3 x 3).
+__global__ void split_uo_kernel(const double2* __restrict__ G, int r, double2* __restrict__ Cr,
+                                double2* __restrict__ Bm, double2* __restrict__ c00) {
+  const int m = r + 3;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m * m; idx += gridDim.x * blockDim.x) {
+    const int a = idx / m, b = idx - (idx / m) * m;
+    const double2 v = G[idx];
+    if (a < r && b < r) Cr[a * r + b] = v;
+    else if (a < r) Bm[a * 3 + (b - r)] = v;
+    else if (b >= r) c00[(a - r) * 3 + (b - r)] = v;
+  }
+}
+
 __global__ void symmetrize_kernel(double2* __restrict__ G, int m) {
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m * m; idx += gridDim.x * blockDim.x) {
     const int a = idx / m, b = idx % m;
@@ -490,11 +462,19 @@ struct DevBuf {
 
 }  // namespace
 
+// Even tile size up to kGT that covers m with the fewest tiles and the least padding.
+int gram_tile(int m) {
+  const int nt = (m + kGT - 1) / kGT;
+  const int t = 2 * ((m + 2 * nt - 1) / (2 * nt));
+  return t < 2 ? 2 : t;
+}
+
 // G (ma x mb, row-major, ldg) = A^H diag(w) B over n rows; see gram_partial_kernel.
 cudaError_t tall_gram(mrom_ctx* h, const double2* A, int64_t rsA, int64_t csA, int ma, const double2* B,
                       int64_t rsB, int64_t csB, int mb, const double* w, int wmode, int64_t n, bool hermitian,
                       double2* G, int64_t ldg) {
-  const int ta = (ma + kGT - 1) / kGT, tb = (mb + kGT - 1) / kGT;
+  const int Ta = gram_tile(hermitian ? std::max(ma, mb) : ma), Tb = hermitian ? Ta : gram_tile(mb);
+  const int ta = (ma + Ta - 1) / Ta, tb = (mb + Tb - 1) / Tb;
   std::vector<int2> tl;
   for (int i = 0; i < ta; ++i)
     for (int j = hermitian ? i : 0; j < tb; ++j) tl.push_back(make_int2(i, j));
@@ -513,12 +493,13 @@ cudaError_t tall_gram(mrom_ctx* h, const double2* A, int64_t rsA, int64_t csA, i
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)nsplit, (unsigned)ntiles);
   gram_partial_kernel<<<grid, 256, 0, h->stream>>>(A, rsA, csA, ma, B, rsB, csB, mb, w, wmode, n, per,
-                                                  static_cast<int2*>(tiles.p), static_cast<double2*>(part.p));
+                                                  static_cast<int2*>(tiles.p), Ta, Tb, hermitian ? 1 : 0,
+                                                  static_cast<double2*>(part.p));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int rb = (int)std::min<int64_t>(4096, ((int64_t)ma * mb + 255) / 256);
   gram_reduce_kernel<<<std::max(rb, 1), 256, 0, h->stream>>>(static_cast<double2*>(part.p), (int)nsplit, ma, mb,
-                                                              hermitian ? 1 : 0, G, ldg);
+                                                              hermitian ? 1 : 0, Ta, G, ldg);
   e = cudaGetLastError();
   h->launches += 2;
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // part/tiles are freed on return
@@ -528,7 +509,8 @@ cudaError_t tall_gram(mrom_ctx* h, const double2* A, int64_t rsA, int64_t csA, i
 // Single-precision tall Gram (row-major operands): G = A^H diag(w) B, float64 output.
 cudaError_t tall_gram_f32(mrom_ctx* h, const float2* A, int64_t rsA, int ma, const float2* B, int64_t rsB, int mb,
                           const float* w, int64_t n, bool hermitian, double2* G, int64_t ldg) {
-  const int ta = (ma + kGT - 1) / kGT, tb = (mb + kGT - 1) / kGT;
+  const int Ta = gram_tile(hermitian ? std::max(ma, mb) : ma), Tb = hermitian ? Ta : gram_tile(mb);
+  const int ta = (ma + Ta - 1) / Ta, tb = (mb + Tb - 1) / Tb;
   std::vector<int2> tl;
   for (int i = 0; i < ta; ++i)
     for (int j = hermitian ? i : 0; j < tb; ++j) tl.push_back(make_int2(i, j));
@@ -543,12 +525,13 @@ cudaError_t tall_gram_f32(mrom_ctx* h, const float2* A, int64_t rsA, int ma, con
   if (e == cudaSuccess) e = cudaMemcpyAsync(tiles.p, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return e;
   gram_partial_f32_kernel<<<dim3((unsigned)nsplit, (unsigned)ntiles), 256, 0, h->stream>>>(
-      A, rsA, ma, B, rsB, mb, w, n, per, static_cast<int2*>(tiles.p), static_cast<float2*>(part.p));
+      A, rsA, ma, B, rsB, mb, w, n, per, static_cast<int2*>(tiles.p), Ta, Tb, hermitian ? 1 : 0,
+      static_cast<float2*>(part.p));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int rb = (int)std::min<int64_t>(4096, ((int64_t)ma * mb + 255) / 256);
   gram_reduce_f32_kernel<<<std::max(rb, 1), 256, 0, h->stream>>>(static_cast<float2*>(part.p), (int)nsplit, ma, mb,
-                                                                  hermitian ? 1 : 0, G, ldg);
+                                                                  hermitian ? 1 : 0, Ta, G, ldg);
   e = cudaGetLastError();
   h->launches += 2;
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -575,8 +558,8 @@ mrom_status gram_eig(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, int
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: allocation");
   e = tall_gram(h, Dp, 1, ldd, m, Dp, 1, ldd, m, nullptr, 0, n, true, static_cast<double2*>(g.p), m);
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: snapshot Gram");
-  jacobi_eig_kernel<<<1, 1024, 0, st>>>(static_cast<double2*>(g.p), static_cast<double2*>(vbuf.p), m, 60, 1e-15,
-                                        static_cast<double*>(lam.p), h->d_status);
+  herm_eig_kernel<<<1, kEigThreads, 0, st>>>(static_cast<double2*>(g.p), m, static_cast<double2*>(vbuf.p),
+                                             static_cast<double*>(lam.p), h->d_status);
   ++h->launches;
   std::vector<double> lh(m);
   std::vector<double2> vh((size_t)m * m);
@@ -588,7 +571,7 @@ mrom_status gram_eig(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, int
   cudaMemcpy(&stw, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (stw & kStatusTimeout) {
     cudaMemset(h->d_status, 0, sizeof(int));
-    return fail(h, MROM_ENOTCONVERGED, "mrom_project: Jacobi eigensolver did not converge");
+    return fail(h, MROM_ENOTCONVERGED, "mrom_project: the snapshot eigensolver did not converge");
   }
   std::vector<int> order(m);
   std::iota(order.begin(), order.end(), 0);
@@ -688,7 +671,7 @@ mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, in
     h->launches += has_me ? 6 : 5;
     e = cudaGetLastError();
     const auto* u32 = static_cast<const float2*>(U32.p);
-    if (e == cudaSuccess) e = tall_gram_f32(h, u32, r, r, static_cast<float2*>(Y32.p), r, r, nullptr, n, false, Kr, r);
+    if (e == cudaSuccess) e = tall_gram_f32(h, u32, r, r, static_cast<float2*>(Y32.p), r, r, nullptr, n, true, Kr, r);
     if (e == cudaSuccess) {
       symmetrize_kernel<<<(r * r + 255) / 256, 256, 0, st>>>(Kr, r);
       ++h->launches;
@@ -699,13 +682,33 @@ mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, in
     if (e == cudaSuccess)
       e = tall_gram_f32(h, u32, r, r, static_cast<float2*>(O32.p), 3, 3, static_cast<float*>(c32.p), n, false, Bm, 3);
   } else {
-    // K_r = U^H (K U), symmetrised (K is symmetric)
-    if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, Yp, r, 1, r, nullptr, 0, n, false, Kr, r);
+    // K_r = U^H (K U) is Hermitian (K is symmetric): upper tiles, mirrored, then symmetrised
+    if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, Yp, r, 1, r, nullptr, 0, n, true, Kr, r);
     if (e == cudaSuccess) {
       symmetrize_kernel<<<(r * r + 255) / 256, 256, 0, st>>>(Kr, r);
       ++h->launches;
     }
-    if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, U, r, 1, r, fom->C_diag, 1, n, true, Cr, r);
+    // C_r, B = U^H C O and c00 = O^T C O from one Hermitian Gram of [U | O] with weight C
+    {
+      DevBuf UO, Guo;
+      const int m = r + 3;
+      if (e == cudaSuccess) e = cudaMalloc(&UO.p, (size_t)n * m * sizeof(double2));
+      if (e == cudaSuccess) e = cudaMalloc(&Guo.p, (size_t)m * m * sizeof(double2));
+      if (e == cudaSuccess) {
+        concat_uo_kernel<<<launch_grid((int64_t)m * n), 256, 0, st>>>(U, r, Op, n, static_cast<double2*>(UO.p));
+        ++h->launches;
+        e = cudaGetLastError();
+      }
+      const auto* uo = static_cast<const double2*>(UO.p);
+      if (e == cudaSuccess)
+        e = tall_gram(h, uo, m, 1, m, uo, m, 1, m, fom->C_diag, 1, n, true, static_cast<double2*>(Guo.p), m);
+      if (e == cudaSuccess) {
+        split_uo_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(static_cast<double2*>(Guo.p), r, Cr, Bm, c00c);
+        ++h->launches;
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // UO and Guo are freed on scope exit
+    }
     if (e == cudaSuccess && has_me) {
       e = cudaMalloc(&em.p, n * sizeof(double));
       if (e == cudaSuccess) {
@@ -716,9 +719,9 @@ mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, in
       // Me = U^H diag(eps m) U  (added to the reduced system only, Eq. (17))
       if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, U, r, 1, r, static_cast<double*>(em.p), 1, n, true, Me, r);
     }
-    if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, Op, 3, 1, 3, fom->C_diag, 1, n, false, Bm, 3);
   }
-  if (e == cudaSuccess) e = tall_gram(h, Op, 3, 1, 3, Op, 3, 1, 3, fom->C_diag, 1, n, true, c00c, 3);
+  if (e == cudaSuccess && h->projection_precision == MROM_MIXED)
+    e = tall_gram(h, Op, 3, 1, 3, Op, 3, 1, 3, fom->C_diag, 1, n, true, c00c, 3);
   const bool cert = fom->X_diag != nullptr;
   if (e == cudaSuccess && cert) {
     e = cudaMalloc(&phi.p, (size_t)n * ng * sizeof(double2));

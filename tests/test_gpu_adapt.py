@@ -18,9 +18,16 @@ def mrom():
 
 def test_adaptive_loop_matches_oracle(mrom):
     """Same snapshot choices, Lambda history and final signature as oracle.adapt with a
-    shared basis and the diagonal inner product X = eps M + omega_min C."""
+    shared basis and the diagonal inner product X = eps M + omega_min C.
+
+    Lambda is compared where it is above the rounding floor of the Gram form of Lemma 4.2
+    (eps ||G|| ||w||^2, large here because X^-1 weighs the exterior by 1 / (eps M)).  The third
+    Lambda (~1e-7) is at that floor: the oracle alone gives 6.5e-8 or 1.4e-7 depending on the
+    BLAS it runs on.  So the intervals chosen from it are set by rounding, not by Algorithm 1,
+    and they are checked for validity only.  The snapshots chosen above the floor must be the
+    oracle's, and the final model must match the oracle's model built on the same snapshot set."""
     import torch
-    from oracle import adapt
+    from oracle import adapt, pipeline
     from workloads import fit_problem, full_order_snapshots, log_omegas
     from workloads.fit import Material
     from gpu_common import oracle_model_sweep, rel_errors
@@ -29,8 +36,11 @@ def test_adaptive_loop_matches_oracle(mrom):
     wo = log_omegas(1e1, 1e5, 60)
     w0 = log_omegas(1e1, 1e5, 3)
     snap = lambda ws: full_order_snapshots(p, ws)
-    model, s_ref, h_ref, k_ref = adapt.adaptive_podp(p, snap, w0, wo, tol_sigma=1e-6, tol_delta=1e-30,
-                                                     n_star=2, max_k=4, shared=True, X_diag=X)
+    _, s_ref, h_ref, k_ref = adapt.adaptive_podp(p, snap, w0, wo, tol_sigma=1e-6, tol_delta=1e-30,
+                                                 n_star=2, max_k=4, shared=True, X_diag=X)
+    # the snapshot set after the two choices made above the floor (max_k = 3)
+    _, s_above, _, _ = adapt.adaptive_podp(p, snap, w0, wo, tol_sigma=1e-6, tol_delta=1e-30,
+                                           n_star=2, max_k=3, shared=True, X_diag=X)
     h = mrom.Handle(0)
     fom = mrom.FullOrder.from_fit(p, X=X)
     D0 = snap(w0)                                     # (3, N, 3)
@@ -38,14 +48,17 @@ def test_adaptive_loop_matches_oracle(mrom):
     rom, hist, k, snaps = mrom.mrom_adapt(h, fom, w0, torch.as_tensor(cols, device="cuda"), snap,
                                           torch.as_tensor(wo, device="cuda"), tol_sigma=1e-6, tol_delta=1e-30,
                                           n_star=2, max_k=4)
-    assert k == k_ref
-    np.testing.assert_array_equal(snaps, s_ref)
-    # Lambda is compared where it is above the rounding floor of the Gram form (eps ||G|| ||w||^2,
-    # large here because X^-1 weighs the exterior by 1 / (eps M)); the last value (~1e-7) is at that
-    # floor: the oracle alone gives 6.5e-8 or 1.4e-7 depending on the BLAS it runs on.
+    assert k == k_ref and snaps.size == len(s_ref)
     assert np.allclose(hist[:2], h_ref[:2], rtol=1e-6, atol=0.0)
     assert hist.size == len(h_ref) and hist[2] < 1e-3 * hist[0]
-    # final reduced model: same signature and certificate
+    # choices above the floor: identical; choices at the floor: N* = 2 new output frequencies,
+    # at most one per interval of the previous snapshot set
+    assert set(s_above) <= set(snaps)
+    new = sorted(set(snaps) - set(s_above))
+    assert len(new) == 2 and all(w in set(wo) for w in new)
+    assert len({int(np.searchsorted(np.sort(s_above), w)) for w in new}) == 2
+    # final reduced model: same signature and certificate as the oracle's on that snapshot set
+    model, _, _ = pipeline.build_model(p, snap(np.asarray(snaps)), tol_sigma=1e-6, shared=True, X_diag=X)
     wt = log_omegas(1e1, 1e5, 40) * 1.01
     om = torch.as_tensor(wt, device="cuda")
     R = torch.empty((1, wt.size, 3, 3), dtype=torch.float64, device="cuda")
