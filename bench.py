@@ -14,8 +14,8 @@ take the LU sweep in the same step).
 
 value: evaluations/s with the reduced data already resident in HBM.
 e2e:   the same through the public API from pinned host buffers -- every step
-       uploads the dictionary, builds the objects and the plan, sweeps, and
-       reads R, I and Delta back.
+       uploads the dictionary (mrom_rom_from_reduced_batch), builds the plan,
+       sweeps, and reads R, I and Delta back.
 roofline: the pencil sweep kernel against the FP64 pipe (GB300: 2 DFMA/clk/SM),
           timed per step with CUDA events around each stage; lu_route: the same
           step with every object on the LU route, for comparison.
@@ -430,9 +430,9 @@ def main():
         d2h = 3 * int(np.prod(shape)) * 8
 
         def e2e_step():
-            rr = [m.ReducedObject(h, o.r, p["K"], p["C"], p["B"], p["c00"], G=p["G"], K_in=p["K_in"],
-                                  alpha=o.alpha, alpha_lb=o.alpha_lb, vol_B=o.vol_B)
-                  for o, p in zip(objs, pinned)]
+            rr = m.ReducedObject.batch(h, [dict(r=o.r, K=p["K"], C=p["C"], B=p["B"], c00=p["c00"], G=p["G"],
+                                                K_in=p["K_in"], alpha=o.alpha, alpha_lb=o.alpha_lb, vol_B=o.vol_B)
+                                           for o, p in zip(objs, pinned)])
             pl = m.Plan(h, rr, args.n_w)
             omd = om_host.to(dev, non_blocking=True)
             pl.sweep(omd, R, I, D)

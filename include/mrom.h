@@ -128,6 +128,14 @@ typedef struct {
 } mrom_reduced_desc;
 
 mrom_status mrom_rom_from_reduced(mrom_handle h, const mrom_reduced_desc* desc, mrom_rom_t* out);
+/* Batched form of mrom_rom_from_reduced (not in the paper; for loading a dictionary):
+ * n_obj objects from descs (host array), handles written to out (host array of n_obj).
+ * The objects share one stream-ordered device allocation, released with the last of
+ * them (mrom_rom_free as usual); copies are asynchronous and the batch synchronises
+ * once.  Same checks and errors as mrom_rom_from_reduced; the message names the first
+ * failing object, and on any error no object is created.  1 <= n_obj <= 65535. */
+mrom_status mrom_rom_from_reduced_batch(mrom_handle h, int32_t n_obj, const mrom_reduced_desc* descs,
+                                        mrom_rom_t* out);
 /* Basis size r of an object (per direction); 0 on a null object. */
 int32_t mrom_rom_rank(mrom_rom_t rom);
 void mrom_rom_free(mrom_rom_t rom);

@@ -115,6 +115,40 @@ class ReducedObject:
         return self
 
     @classmethod
+    def batch(cls, handle: Handle, items):
+        """mrom_rom_from_reduced_batch: one object per dict of items (keys r, K, C, B, c00 and
+        optionally G, K_in, Me, N0, alpha, alpha_lb, vol_B, r_dirs), one device allocation."""
+        items = list(items)
+        descs = (mrom_reduced_desc * len(items))()
+        keep = []
+        for d, it in zip(descs, items):
+            arrs = [_as_c128(it["K"]), _as_c128(it["C"]), _as_c128(it["B"]), _as_f64(it["c00"]),
+                    _as_c128(it.get("G")), _as_c128(it.get("K_in")), _as_c128(it.get("Me")),
+                    _as_f64(it.get("N0"))]
+            keep.append(arrs)
+            d.r = int(it["r"])
+            d.K, d.C, d.B = _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2])
+            d.c00 = ctypes.cast(_ptr(arrs[3]), ctypes.POINTER(ctypes.c_double))
+            d.G, d.K_in, d.Me = _ptr(arrs[4]), _ptr(arrs[5]), _ptr(arrs[6])
+            d.N0 = ctypes.cast(_ptr(arrs[7]), ctypes.POINTER(ctypes.c_double)) if arrs[7] is not None else None
+            d.alpha = float(it.get("alpha", 1.0))
+            d.alpha_lb = float(it.get("alpha_lb", 1.0 / np.sqrt(2.0)))
+            d.vol_B = float(it.get("vol_B", 1.0))
+            for i, v in enumerate(it.get("r_dirs", (0, 0, 0))):
+                d.r_dirs[i] = int(v)
+        out = (ctypes.c_void_p * len(items))()
+        _abi.check(lib().mrom_rom_from_reduced_batch(handle.ptr, len(items), descs, out), handle.ptr)
+        return [cls._wrap(handle, ctypes.c_void_p(out[k]), int(items[k]["r"]), items[k].get("G") is not None)
+                for k in range(len(items))]
+
+    @classmethod
+    def from_workload_batch(cls, handle: Handle, objs, *, with_cert: bool = True):
+        """Batched from_workload (one device allocation for the whole dictionary)."""
+        return cls.batch(handle, [dict(r=o.r, K=o.K, C=o.C, B=o.B, c00=o.c00, G=o.G if with_cert else None,
+                                       K_in=o.K_in, alpha=o.alpha, alpha_lb=o.alpha_lb, vol_B=o.vol_B)
+                                  for o in objs])
+
+    @classmethod
     def from_workload(cls, handle: Handle, obj, *, with_cert: bool = True):
         """Create from a workloads.dictionary.ReducedObject (host numpy data)."""
         return cls(handle, obj.r, obj.K, obj.C, obj.B, obj.c00, G=obj.G if with_cert else None,

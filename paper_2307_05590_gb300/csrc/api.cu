@@ -309,6 +309,12 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
   std::vector<double> cost;
   bool all_cert = true;
   size_t smem = 0, ws_elems = 0;
+  int64_t n_tasks_all = 0;
+  // with pencil-route objects the LU kernel runs over the device-routed table, so the
+  // explicit task list is only built for a plan that is LU throughout
+  bool any_pencil = false;
+  for (int o = 0; o < n_obj && h->solver == MROM_SOLVER_AUTO; ++o)
+    any_pencil = any_pencil || (roms[o]->r_dirs[0] + roms[o]->r_dirs[1] + roms[o]->r_dirs[2]) == 0;
   for (int o = 0; o < n_obj; ++o) {
     const mrom_rom* m = roms[o];
     objs[o] = rom_record(m);
@@ -320,13 +326,15 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
     const size_t per = in_smem ? per_s : sweep_fp64_bytes_per_system(m->r, false);
     const int S = in_smem ? std::min<int>(n_w, (int)(budget / per_s)) : 1;
     if (!in_smem) ws_elems = std::max(ws_elems, sweep_fp64_matrix_elems(m->r));
+    smem = std::max(smem, per * std::min(S, n_w));
+    n_tasks_all += (n_w + S - 1) / S;
+    if (any_pencil) continue;
     const double r = m->r;
     const double unit = 4.0 * r * r * r / 3.0 + 30.0 * r * r;
     for (int w0 = 0; w0 < n_w; w0 += S) {
       const int nw = std::min(S, n_w - w0);
       tasks.push_back(SweepTask{o, w0, nw, in_smem ? 0 : 1});
       cost.push_back(unit * nw);
-      smem = std::max(smem, per * nw);
     }
   }
   // longest tasks first: CTAs pull from the front of the list
@@ -349,7 +357,7 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_fp64_symbol(cfg), sweep_fp64_threads(cfg), smem);
   occ = std::max(occ, 1);
-  plan->grid = std::min(plan->n_tasks, h->num_sms * occ);
+  plan->grid = (int)std::min<int64_t>(n_tasks_all, (int64_t)h->num_sms * occ);
   plan->ws_elems = ws_elems;
   const size_t ws_bytes = ws_elems * sizeof(double2) * (size_t)plan->grid;
   const size_t bytes = ws_bytes + n_obj * sizeof(RomDev) + sorted.size() * sizeof(SweepTask) + 16;

@@ -102,8 +102,14 @@ struct mrom_rom {
   mrom_ctx* ctx = nullptr;
   int r = 0;
   double alpha = 1.0, alpha_lb = 0.0, vol_B = 0.0;
-  // device storage (one allocation, views below)
+  // device storage (one allocation, views below); objects of one batch share an allocation,
+  // released (stream-ordered) with the last of them
   void* d_block = nullptr;
+  struct SharedBlock {
+    void* p = nullptr;
+    int refs = 0;
+    cudaStream_t stream = nullptr;
+  }* shared = nullptr;
   double2 *K = nullptr, *Kin = nullptr, *C = nullptr, *Me = nullptr, *B = nullptr;
   double2 *GKK = nullptr, *GCC = nullptr, *GSk = nullptr, *gsK = nullptr, *gsC = nullptr;
   double2* G = nullptr;          // full Gram, kept for certificate-only consumers

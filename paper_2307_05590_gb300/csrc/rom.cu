@@ -3,7 +3,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
+#include <string>
 
 namespace mrom {
 namespace {
@@ -166,6 +168,203 @@ extern "C" int32_t mrom_rom_rank(mrom_rom_t rom) { return rom ? rom->r : 0; }
 
 extern "C" void mrom_rom_free(mrom_rom_t rom) {
   if (!rom) return;
-  if (rom->d_block) cudaFree(rom->d_block);
+  if (rom->shared) {
+    if (--rom->shared->refs == 0) {
+      cudaFreeAsync(rom->shared->p, rom->shared->stream);
+      delete rom->shared;
+    }
+  } else if (rom->d_block) {
+    cudaFree(rom->d_block);
+  }
   delete rom;
+}
+
+namespace mrom {
+namespace {
+
+// Per object: flag[o] = 1 when any of its len[o] doubles at seg[o] is not finite.
+__global__ void nonfinite_batch_kernel(const double* const* __restrict__ seg, const size_t* __restrict__ len,
+                                       int* __restrict__ flag) {
+  const int o = blockIdx.y;
+  const double* x = seg[o];
+  const size_t n = len[o];
+  int bad = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (bad) atomicOr(&flag[o], 1);
+}
+
+// gss[o][i][j] = Re G_o[i][j], i, j < 3 (the source-source block of the certificate Gram).
+__global__ void gather_gss_kernel(const double2* const* __restrict__ G, const int* __restrict__ ng, int n,
+                                  double* __restrict__ gss) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 9 * n; idx += gridDim.x * blockDim.x) {
+    const int o = idx / 9, k = idx - (idx / 9) * 9;
+    gss[idx] = G[o] ? G[o][(size_t)(k / 3) * ng[o] + (k % 3)].x : 0.0;
+  }
+}
+
+mrom_status check_desc(mrom_ctx* h, const mrom_reduced_desc* d, const char* who) {
+  const std::string w(who);
+  const int r = d->r;
+  if (r < 1 || r > MROM_MAX_R) return fail(h, MROM_EINVAL, w + ": r must be in [1, MROM_MAX_R]");
+  if (!d->K || !d->C || !d->B || !d->c00) return fail(h, MROM_EINVAL, w + ": K, C, B and c00 are required");
+  if (!std::isfinite(d->alpha) || !(d->alpha > 0) || !std::isfinite(d->vol_B))
+    return fail(h, MROM_EINVAL, w + ": alpha must be finite and > 0");
+  if (d->G && !(d->alpha_lb > 0 && std::isfinite(d->alpha_lb)))
+    return fail(h, MROM_EINVAL, w + ": a Gram matrix needs alpha_lb > 0");
+  const int rd_sum = d->r_dirs[0] + d->r_dirs[1] + d->r_dirs[2];
+  if (rd_sum != 0 && (rd_sum != r || d->r_dirs[0] < 1 || d->r_dirs[1] < 1 || d->r_dirs[2] < 1))
+    return fail(h, MROM_EINVAL, w + ": r_dirs must be all 0 or positive with sum r");
+  return MROM_OK;
+}
+
+// 9 doubles from a host or device pointer
+cudaError_t read9(const double* src, double* dst) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, src) == cudaSuccess && at.type == cudaMemoryTypeDevice)
+    return cudaMemcpy(dst, src, 9 * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaGetLastError();  // clear a possible error from querying a plain host pointer
+  std::memcpy(dst, src, 9 * sizeof(double));
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace mrom
+
+extern "C" mrom_status mrom_rom_from_reduced_batch(mrom_handle h, int32_t n_obj, const mrom_reduced_desc* descs,
+                                                   mrom_rom_t* out) {
+  if (!h) return MROM_EINVAL;
+  if (n_obj < 1 || n_obj > 65535 || !descs || !out)
+    return fail(h, MROM_EINVAL, "mrom_rom_from_reduced_batch: 1 <= n_obj <= 65535 and non-null arrays required");
+  for (int o = 0; o < n_obj; ++o) {
+    out[o] = nullptr;
+    const mrom_status st = check_desc(h, &descs[o], "mrom_rom_from_reduced_batch");
+    if (st != MROM_OK) return fail(h, st, h->last_error + " (object " + std::to_string(o) + ")");
+  }
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+  cudaStream_t st = h->stream;
+  // layout per object as in mrom_rom_from_reduced: K, Kin, C, Me, B, [G, GKK, GCC, GSk, gsK, gsC]
+  std::vector<size_t> off(n_obj), cnt(n_obj);
+  size_t total = 0;
+  for (int o = 0; o < n_obj; ++o) {
+    const size_t r = descs[o].r, rr = r * r, ng = 2 * r + 3;
+    cnt[o] = rr * 4 + 3 * r + (descs[o].G ? ng * ng + 3 * rr + 6 * r : 0);
+    off[o] = total;
+    total += cnt[o];
+  }
+  // tail: per-object flags (int), gss (9 doubles), segment and Gram pointer tables
+  const size_t b_data = total * sizeof(double2);
+  const size_t b_flag = ((size_t)n_obj * sizeof(int) + 15) / 16 * 16;
+  const size_t b_gss = (size_t)n_obj * 9 * sizeof(double);
+  const size_t b_tab = (size_t)n_obj * (2 * sizeof(void*) + sizeof(size_t) + sizeof(int));
+  void* block = nullptr;
+  e = cudaMallocAsync(&block, b_data + b_flag + b_gss + b_tab + 64, st);
+  if (e != cudaSuccess) return fail(h, MROM_ENOMEM, "mrom_rom_from_reduced_batch: device allocation failed");
+  auto* shared = new mrom_rom::SharedBlock();
+  shared->p = block;
+  shared->stream = st;
+  char* base = static_cast<char*>(block);
+  int* d_flag = reinterpret_cast<int*>(base + b_data);
+  double* d_gss = reinterpret_cast<double*>(base + b_data + b_flag);
+  char* tab = base + b_data + b_flag + b_gss;
+  tab = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(tab) + 15) / 16 * 16);
+  auto** d_seg = reinterpret_cast<const double**>(tab);
+  auto** d_g = reinterpret_cast<const double2**>(tab + (size_t)n_obj * sizeof(void*));
+  auto* d_len = reinterpret_cast<size_t*>(tab + (size_t)n_obj * 2 * sizeof(void*));
+  auto* d_ng = reinterpret_cast<int*>(tab + (size_t)n_obj * (2 * sizeof(void*) + sizeof(size_t)));
+
+  std::vector<mrom_rom*> roms(n_obj, nullptr);
+  std::vector<const double*> seg(n_obj);
+  std::vector<const double2*> gp(n_obj);
+  std::vector<size_t> len(n_obj);
+  std::vector<int> ngv(n_obj);
+  auto cleanup = [&](mrom_status s, const std::string& msg) {
+    for (auto* m : roms) delete m;
+    cudaFreeAsync(block, st);
+    delete shared;
+    return fail(h, s, msg);
+  };
+  e = cudaMemsetAsync(block, 0, b_data + b_flag, st);
+  for (int o = 0; o < n_obj && e == cudaSuccess; ++o) {
+    const mrom_reduced_desc* d = &descs[o];
+    const size_t r = d->r, rr = r * r, ng = 2 * r + 3;
+    auto* rom = new mrom_rom();
+    roms[o] = rom;
+    rom->ctx = h;
+    rom->r = d->r;
+    rom->alpha = d->alpha;
+    rom->alpha_lb = d->alpha_lb;
+    rom->vol_B = d->vol_B;
+    rom->shared = shared;
+    double2* p = static_cast<double2*>(block) + off[o];
+    rom->K = p; p += rr;
+    rom->Kin = p; p += rr;
+    rom->C = p; p += rr;
+    rom->Me = p; p += rr;
+    rom->B = p; p += 3 * r;
+    if (d->G) {
+      rom->G = p; p += ng * ng;
+      rom->GKK = p; p += rr;
+      rom->GCC = p; p += rr;
+      rom->GSk = p; p += rr;
+      rom->gsK = p; p += 3 * r;
+      rom->gsC = p; p += 3 * r;
+    }
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st);
+    };
+    cp(rom->K, d->K, rr * 16);
+    if (d->K_in) cp(rom->Kin, d->K_in, rr * 16);
+    cp(rom->C, d->C, rr * 16);
+    if (d->Me) cp(rom->Me, d->Me, rr * 16);
+    cp(rom->B, d->B, 3 * r * 16);
+    if (d->G) cp(rom->G, d->G, ng * ng * 16);
+    if (e == cudaSuccess) e = read9(d->c00, rom->c00);
+    if (e == cudaSuccess && d->N0) e = read9(d->N0, rom->N0);
+    seg[o] = reinterpret_cast<const double*>(static_cast<double2*>(block) + off[o]);
+    len[o] = 2 * cnt[o];
+    gp[o] = rom->G;
+    ngv[o] = (int)ng;
+    rom->has_cert = d->G != nullptr;
+    rom->has_kin = d->K_in != nullptr;
+    for (int i = 0; i < 3; ++i) rom->r_dirs[i] = d->r_dirs[i];
+    if (!d->Me) rom->Me = nullptr;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_seg, seg.data(), n_obj * sizeof(void*), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_g, gp.data(), n_obj * sizeof(void*), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_len, len.data(), n_obj * sizeof(size_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ng, ngv.data(), n_obj * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cleanup(MROM_ECUDA, std::string("mrom_rom_from_reduced_batch: upload: ") +
+                                                     cudaGetErrorString(e));
+  // (the host staging vectors above are pageable: each copy has consumed its source on return)
+  nonfinite_batch_kernel<<<dim3(8, (unsigned)n_obj), 256, 0, st>>>(d_seg, d_len, d_flag);
+  gather_gss_kernel<<<std::max(1, std::min(1024, (9 * n_obj + 255) / 256)), 256, 0, st>>>(d_g, d_ng, n_obj, d_gss);
+  h->launches += 2;
+  for (int o = 0; o < n_obj && e == cudaSuccess; ++o)
+    if (roms[o]->G) {
+      e = launch_split_gram(roms[o]->G, roms[o]->r, roms[o]->GKK, roms[o]->GCC, roms[o]->GSk, roms[o]->gsK,
+                            roms[o]->gsC, st);
+      ++h->launches;
+    }
+  std::vector<int> flag(n_obj);
+  std::vector<double> gss((size_t)n_obj * 9);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(flag.data(), d_flag, n_obj * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(gss.data(), d_gss, gss.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cleanup(MROM_ECUDA, std::string("mrom_rom_from_reduced_batch: ") + cudaGetErrorString(e));
+  for (int o = 0; o < n_obj; ++o) {
+    bool bad = flag[o] != 0;
+    for (int k = 0; k < 9; ++k) bad = bad || !std::isfinite(roms[o]->c00[k]) || !std::isfinite(roms[o]->N0[k]);
+    if (bad)
+      return cleanup(MROM_EINVAL, "mrom_rom_from_reduced_batch: non-finite value in the reduced data (object " +
+                                      std::to_string(o) + ")");
+  }
+  shared->refs = n_obj;
+  for (int o = 0; o < n_obj; ++o) {
+    if (roms[o]->has_cert) std::memcpy(roms[o]->gss, &gss[(size_t)o * 9], 9 * sizeof(double));
+    out[o] = roms[o];
+  }
+  return MROM_OK;
 }

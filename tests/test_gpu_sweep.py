@@ -222,3 +222,41 @@ def test_autotuner_picks_a_valid_configuration(mrom, handle):
         ref = oracle_sweep(obj, wo)
         errs = rel_errors(R[k].cpu().numpy(), I[k].cpu().numpy(), D[k].cpu().numpy(), *ref)
         assert max(errs) <= TOL, errs
+
+
+def test_batched_object_creation(mrom, handle):
+    """mrom_rom_from_reduced_batch gives the same sweep as objects created one by one; a
+    non-finite entry is refused with the object named; the shared allocation outlives any
+    subset of its objects."""
+    import torch
+    from workloads import log_omegas, reduced_object
+    objs = [reduced_object(61, k, r) for k, r in enumerate([5, 30, 64])]
+    wo = log_omegas(1e1, 1e8, 50)
+    om = torch.as_tensor(wo, device="cuda")
+    single = [mrom.ReducedObject.from_workload(handle, o) for o in objs]
+    batch = mrom.ReducedObject.from_workload_batch(handle, objs)
+    out = []
+    for roms in (single, batch):
+        R = torch.empty((3, 50, 3, 3), dtype=torch.float64, device="cuda")
+        I = torch.empty_like(R)
+        D = torch.empty_like(R)
+        mrom.mrom_sweep(handle, roms, om, 50, R, I, D)
+        handle.synchronize()
+        out.append([x.cpu().numpy() for x in (R, I, D)])
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    batch[0].close()
+    batch[2].close()
+    R = torch.empty((1, 50, 3, 3), dtype=torch.float64, device="cuda")
+    mrom.mrom_sweep(handle, [batch[1]], om, 50, R, torch.empty_like(R))
+    handle.synchronize()
+    assert np.array_equal(R[0].cpu().numpy(), out[0][0][1])
+    batch[1].close()
+    bad = reduced_object(61, 9, 12)
+    C = bad.C.copy()
+    C[3, 4] = np.inf
+    items = [dict(r=o.r, K=o.K, C=o.C, B=o.B, c00=o.c00, G=o.G) for o in objs]
+    items.append(dict(r=12, K=bad.K, C=C, B=bad.B, c00=bad.c00, G=bad.G))
+    with pytest.raises(mrom.MromError) as ei:
+        mrom.ReducedObject.batch(handle, items)
+    assert ei.value.status == 1 and "object 3" in str(ei.value)
