@@ -270,6 +270,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mixed", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--lu-route", action=argparse.BooleanOptionalAction, default=True)
+    ap.add_argument("--gradients", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--projection-only", action="store_true",
                     help="time mrom_project alone (float64 and complex64 products) and print its record")
     ap.add_argument("--projection-grid", type=int, default=96)
@@ -409,6 +410,35 @@ def main():
 
     proj = measure_projection(m, h) if args.projection else None
 
+    # ---- gradients (adjoint sweep) on the same dictionary: dL/domega, dL/ds_sigma, dL/ds_mu for
+    # per-object scales s_sigma ~ U(0.5, 2), s_mu ~ U(1, 64) and random cotangents of R and I
+    grads = None
+    if args.gradients:
+        rng = np.random.default_rng(20230713)
+        ss = torch.as_tensor(rng.uniform(0.5, 2.0, args.n_obj), device=dev)
+        sm = torch.as_tensor(rng.uniform(1.0, 64.0, args.n_obj), device=dev)
+        gR = torch.as_tensor(rng.standard_normal(shape), device=dev)
+        gI = torch.as_tensor(rng.standard_normal(shape), device=dev)
+        g_w = torch.empty((args.n_obj, args.n_w), dtype=torch.float64, device=dev)
+        g_s = torch.empty(args.n_obj, dtype=torch.float64, device=dev)
+        g_m = torch.empty_like(g_s)
+
+        def vjp():
+            m.mrom_sweep_vjp(h, roms, om, args.n_w, gR, gI, g_w, g_ssigma=g_s, g_smu=g_m, s_sigma=ss, s_mu=sm,
+                             R=R, I=I)
+        vjp()
+        h.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            vjp()
+        e1.record(stream)
+        h.synchronize()
+        ms_vjp = e0.elapsed_time(e1) / 2
+        grads = {"value": args.n_obj * args.n_w / (ms_vjp * 1e-3), "unit": "gradient evals/s (R, I and their "
+                 "vector-Jacobian product w.r.t. omega, s_sigma, s_mu)", "ms_per_step": ms_vjp}
+        del gR, gI
+
     # ---- end to end through the public API from pinned host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -489,6 +519,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "wall_s_timed": wall, "per_launch_ms": per_launch_ms, "sweep_config": sweep_cfg,
             "stages": stage_info, "lu_route": lu_route, "mixed_precision": mixed, "projection": proj,
+            "gradients": grads,
         }
         print(json.dumps(line), flush=True)
     plan.close()

@@ -415,6 +415,11 @@ __global__ void scale_kernel(const double* __restrict__ x, double a, int64_t n, 
     y[i] = a * x[i];
 }
 
+__global__ void recip_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = 1.0 / x[i];
+}
+
 // UO[n] = [U[n][0..r) | O[n][0..3)] (row-major, r + 3 columns)
 __global__ void concat_uo_kernel(const double2* __restrict__ U, int r, const double2* __restrict__ O, int64_t n,
                                  double2* __restrict__ UO) {
@@ -731,9 +736,17 @@ mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, in
       ++h->launches;
       e = cudaGetLastError();
     }
+    // X^-1 once (the Gram kernel would otherwise divide for every staged element)
+    DevBuf xinv;
+    if (e == cudaSuccess) e = cudaMalloc(&xinv.p, (size_t)n * sizeof(double));
+    if (e == cudaSuccess) {
+      recip_kernel<<<launch_grid(n), 256, 0, st>>>(fom->X_diag, n, static_cast<double*>(xinv.p));
+      ++h->launches;
+      e = cudaGetLastError();
+    }
     if (e == cudaSuccess)
       e = tall_gram(h, static_cast<double2*>(phi.p), ng, 1, ng, static_cast<double2*>(phi.p), ng, 1, ng,
-                    fom->X_diag, 2, n, true, Gm, ng);
+                    static_cast<double*>(xinv.p), 1, n, true, Gm, ng);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: projection");
   std::vector<double2> c00h(9);
