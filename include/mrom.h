@@ -279,11 +279,15 @@ mrom_status mrom_sweep(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, con
  * (K(s_mu) = K + (1/s_mu - 1) K_in), and cotangents gR, gI ([n_obj][n_w][3][3],
  * device), it writes g_omega[o][k] = dL/domega (device, n_obj * n_w),
  * g_ssigma[o] = dL/ds_sigma and g_smu[o] = dL/ds_mu (device, n_obj each, or
- * NULL) for L = sum gR . R + gI . I, by an adjoint solve with the same LU
- * factors (recomputed, not stored).  R and I (device, or NULL) receive the
- * forward values at these scales.  s_sigma, s_mu: device, n_obj each, or NULL
- * for 1; s_mu or g_smu require K_in on every object.  Asynchronous; allocates
- * its tables stream-ordered. */
+ * NULL) for L = sum gR . R + gI . I, by an adjoint solve A^H Lambda = Z.  On the
+ * pencil route (mrom_set_solver) the adjoint is diagonal in each object's
+ * eigenbasis: Lambda = V (Lambda_K + i w)^-1 V^H Z, with V^H K_in V transformed
+ * once per object when g_smu is wanted; objects that fail the pencil route's
+ * accuracy gate, and every object on the LU route, use the same LU factors as
+ * the forward solve (recomputed, not stored).  R and I (device, or NULL)
+ * receive the forward values at these scales.  s_sigma, s_mu: device, n_obj
+ * each, or NULL for 1; s_mu or g_smu require K_in on every object.
+ * Asynchronous; allocates its tables stream-ordered. */
 mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega, int32_t n_w,
                            int32_t omega_stride, const double* s_sigma, const double* s_mu, const double* gR,
                            const double* gI, double* g_omega, double* g_ssigma, double* g_smu, double* R, double* I);
@@ -355,8 +359,10 @@ mrom_status mrom_tune(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int3
  * budget at start-up and forbids later allocations, an application whose own
  * allocator already owns the device memory, or a latency-critical loop in which
  * cudaMalloc / cudaFree would synchronise the device.  For them this entry point
- * computes exactly what mrom_sweep computes (same kernel arithmetic, same
- * outputs) and allocates nothing: the object table, the task table, the work
+ * computes exactly what mrom_sweep computes on the LU route (MROM_SOLVER_LU: same
+ * kernel arithmetic, same outputs; the pencil route needs per-object tables that
+ * scale with r^2 and is not offered here) and allocates nothing: the object
+ * table, the task table, the work
  * counter and the workspace of systems too large for shared memory all live in
  * one fixed array of MROM_NOALLOC_SCRATCH_BYTES (64 MiB) of device memory inside
  * this library, which every GPU that loads the library holds until the process
@@ -369,7 +375,7 @@ mrom_status mrom_tune(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int3
  *  - Arguments and output layout are those of mrom_sweep (without s_sigma and
  *    s_mu).  A batch whose tables and workspace do not fit the array is refused
  *    with MROM_EINVAL and a message giving the bytes needed; nothing is launched.
- *    The workspace shrinks the grid when needed, so only the tables (about 330
+ *    The workspace shrinks the grid when needed, so only the tables (about 340
  *    bytes per object) bound the batch size. */
 #define MROM_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 mrom_status mrom_sweep_noalloc(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega,

@@ -102,15 +102,7 @@ extern "C" mrom_status mrom_synchronize(mrom_handle h) {
 
 namespace {
 
-// Pencil route gates: the estimated forward error eps ||H||_F / omega_min must stay below
-// kPencilGate (1e-11: the measured error stays near or below this estimate, so a factor of
-// ten below the 1e-10 parity tolerance), and ||C||_F ||L^-1||_F^2 >= kappa_2(C) below
-// kPencilKappaMax; other objects take the LU route.
-constexpr double kPencilGate = 1e-11;
-constexpr double kPencilKappaMax = 1e6;
-// QL rotation log per object (complex slots): rotations and sweep records
-constexpr size_t kRotCap(int r) { return 3 * (size_t)r * r + 64; }
-constexpr size_t kSweepCap(int r) { return 16 * (size_t)r + 16; }
+
 
 // Dynamic shared memory per CTA: an SM's shared memory divided by the CTAs that
 // co-reside, so that they fill each other's barrier waits (minus the reservation).
@@ -142,6 +134,7 @@ int sweep_config(const mrom_ctx* h) { return default_config(h); }
 RomDev rom_record(const mrom_rom* m) {
   RomDev d;
   d.K = m->K;
+  d.Kin = m->has_kin ? m->Kin : nullptr;
   d.C = m->C;
   d.Me = m->Me;
   d.B = m->B;
@@ -167,43 +160,9 @@ RomDev rom_record(const mrom_rom* m) {
   return d;
 }
 
-// Pencil route of a plan: eligible objects (one basis shared by the directions), their
-// per-object data, the preparation workspace and the routing tables (see pencil.cu).
+// Pencil route of a plan: the LU kernel's task shapes for the routed table, then the tables.
 mrom_status plan_pencil(mrom_ctx* h, mrom_plan plan, const std::vector<RomDev>& objs, size_t lu_budget) {
   const int n_obj = plan->n_obj, n_w = plan->n_w;
-  std::vector<int> elig;
-  for (int o = 0; o < n_obj; ++o)
-    if (!objs[o].per_dir) elig.push_back(o);
-  if (elig.empty()) return MROM_OK;
-  std::stable_sort(elig.begin(), elig.end(), [&](int a, int b) { return objs[a].r > objs[b].r; });
-  // frequency groups of 32 per task: as many as the shared memory holds (one CTA per SM),
-  // a power of two up to 8, and no more than the frequencies need
-  const size_t budget = h->smem_optin - 4096;
-  int need = 1;
-  while (need < 8 && 32 * need < n_w) need *= 2;
-  std::vector<int> spen(elig.size());
-  std::vector<PencilDev> pens(n_obj);
-  std::memset(pens.data(), 0, n_obj * sizeof(PencilDev));
-  size_t data_elems = 0, smem = 0;
-  int rmax = 1;
-  std::vector<size_t> off(n_obj, 0);
-  for (size_t k = 0; k < elig.size(); ++k) {
-    const int o = elig[k], r = objs[o].r;
-    int F = 8;
-    while (F > 1 && (F > need || pencil_sweep_smem_bytes(r, F) > budget)) F /= 2;
-    spen[k] = 32 * F;
-    pens[o].F = F;
-    smem = std::max(smem, pencil_sweep_smem_bytes(r, F));
-    rmax = std::max(rmax, r);
-    off[o] = data_elems;
-    const size_t tri = (size_t)r * (r + 1) / 2;
-    data_elems += (size_t)(r + 1) / 2 + 3 * (size_t)r;            // lam (in complex slots), beta
-    if (objs[o].has_cert) data_elems += 6 * (size_t)r + 3 * tri;  // gsh, Gh
-    if (objs[o].Me) data_elems += tri;                            // Eh
-    // preparation scratch: W, e, rotation log (QL takes about r^2 rotations in 2 r sweeps)
-    data_elems += (size_t)r * r + (size_t)(r + 1) / 2 + kRotCap(r) + (size_t)(kSweepCap(r) + 1) / 2;
-  }
-  // LU order (all objects, descending cost) with their LU task shapes
   std::vector<int> order_lu(n_obj);
   std::iota(order_lu.begin(), order_lu.end(), 0);
   std::stable_sort(order_lu.begin(), order_lu.end(), [&](int a, int b) { return objs[a].r > objs[b].r; });
@@ -215,81 +174,7 @@ mrom_status plan_pencil(mrom_ctx* h, mrom_plan plan, const std::vector<RomDev>& 
     const int S = in_smem ? std::max(1, std::min<int>(n_w, (int)(lu_budget / per_s))) : 1;
     lu_info[k] = make_int2(S, in_smem ? 0 : 1);
   }
-  plan->prep_grid = std::min<int>((int)elig.size(), 2 * h->num_sms);
-  plan->prep_ws_elems = 3 * (size_t)rmax * rmax;
-  plan->pen_grid = h->num_sms;
-  plan->pen_smem = smem;
-  // one allocation: pens, order_pen, spen, order_lu, lu_info, two tables, pen_ok,
-  // counters, per-object data, preparation workspace
-  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t b_scr = al(n_obj * sizeof(PencilScratch)), b_nsw = al(elig.size() * sizeof(int));
-  const size_t b_pens = al(n_obj * sizeof(PencilDev)), b_op = al(elig.size() * sizeof(int)),
-               b_sp = al(elig.size() * sizeof(int)), b_ol = al(n_obj * sizeof(int)),
-               b_li = al(n_obj * sizeof(int2)), b_tab = al((n_obj + 1) * sizeof(SweepTask)),
-               b_ok = al(n_obj * sizeof(int)), b_cnt = al(8 * sizeof(int)),
-               b_data = al(data_elems * sizeof(double2)),
-               b_ws = al(plan->prep_ws_elems * plan->prep_grid * sizeof(double2));
-  const size_t total = b_scr + b_nsw + b_pens + b_op + b_sp + b_ol + b_li + 2 * b_tab + b_ok + b_cnt + b_data + b_ws;
-  void* blk = nullptr;
-  cudaError_t e = cudaMallocAsync(&blk, total, h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_plan_create: pencil allocation");
-  plan->pen_block = blk;
-  char* p = static_cast<char*>(blk);
-  plan->d_scr = reinterpret_cast<PencilScratch*>(p); p += b_scr;
-  int* d_nsw = reinterpret_cast<int*>(p); p += b_nsw;
-  plan->d_pens = reinterpret_cast<PencilDev*>(p); p += b_pens;
-  plan->d_order_pen = reinterpret_cast<int*>(p); p += b_op;
-  plan->d_spen = reinterpret_cast<int*>(p); p += b_sp;
-  plan->d_order_lu = reinterpret_cast<int*>(p); p += b_ol;
-  plan->d_lu_info = reinterpret_cast<int2*>(p); p += b_li;
-  plan->d_table_pen = reinterpret_cast<SweepTask*>(p); p += b_tab;
-  plan->d_table_lu = reinterpret_cast<SweepTask*>(p); p += b_tab;
-  plan->d_pen_ok = reinterpret_cast<int*>(p); p += b_ok;
-  plan->d_counters = reinterpret_cast<int*>(p); p += b_cnt;
-  double2* data = reinterpret_cast<double2*>(p); p += b_data;
-  plan->d_prep_ws = reinterpret_cast<double2*>(p);
-  std::vector<PencilScratch> scr(n_obj);
-  std::memset(scr.data(), 0, n_obj * sizeof(PencilScratch));
-  for (size_t k = 0; k < elig.size(); ++k) {
-    const int o = elig[k];
-    const int r = objs[o].r;
-    const size_t tri = (size_t)r * (r + 1) / 2;
-    double2* q = data + off[o];
-    pens[o].lam = reinterpret_cast<double*>(q); q += (r + 1) / 2;
-    pens[o].beta = q; q += 3 * (size_t)r;
-    if (objs[o].has_cert) {
-      pens[o].gsh = q; q += 6 * (size_t)r;
-      pens[o].Gh = q; q += 3 * tri;
-    }
-    if (objs[o].Me) {
-      pens[o].Eh = q; q += tri;
-    }
-    scr[o].W = q; q += (size_t)r * r;
-    scr[o].e = reinterpret_cast<double*>(q); q += (r + 1) / 2;
-    scr[o].rot = q; q += kRotCap(r);
-    scr[o].sweeps = reinterpret_cast<int2*>(q);
-    scr[o].cap_rot = (int)kRotCap(r);
-    scr[o].cap_sw = (int)kSweepCap(r);
-    scr[o].nsw = d_nsw + k;
-  }
-  plan->n_pen = (int)elig.size();
-  plan->pen_rmax = rmax;
-  e = cudaMemcpyAsync(plan->d_pens, pens.data(), n_obj * sizeof(PencilDev), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(plan->d_scr, scr.data(), n_obj * sizeof(PencilScratch), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(plan->d_order_pen, elig.data(), elig.size() * sizeof(int), cudaMemcpyHostToDevice,
-                        h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(plan->d_spen, spen.data(), spen.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(plan->d_order_lu, order_lu.data(), n_obj * sizeof(int), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(plan->d_lu_info, lu_info.data(), n_obj * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
-  // (pageable sources are staged before these calls return, so the host vectors may go)
-  if (e == cudaSuccess) e = cudaMemsetAsync(plan->d_pen_ok, 0, b_ok, h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_plan_create: pencil upload");
-  return MROM_OK;
+  return pencil_tables_create(h, objs, n_w, true, false, order_lu, lu_info, &plan->pen);
 }
 
 }  // namespace mrom
@@ -397,7 +282,7 @@ extern "C" mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, i
 extern "C" mrom_status mrom_plan_destroy(mrom_plan plan) {
   if (!plan) return MROM_EINVAL;
   cudaSetDevice(plan->ctx->device);
-  if (plan->pen_block) cudaFreeAsync(plan->pen_block, plan->ctx->stream);
+  pencil_tables_destroy(&plan->pen, plan->ctx->stream);
   for (auto& ev : plan->ev)
     if (ev) cudaEventDestroy(ev);
   cudaFreeAsync(plan->d_workspace ? static_cast<void*>(plan->d_workspace) : static_cast<void*>(plan->d_objs),
@@ -421,34 +306,26 @@ mrom_status run_plan(mrom_plan plan, const double* omega, int32_t omega_stride, 
   auto mark = [&](int k) {
     if (plan->timing) cudaEventRecord(plan->ev[k], h->stream);
   };
-  if (plan->n_pen > 0) {
-    // pencil route: per-object preparation, device-side routing, then both sweep kernels
+  if (plan->pen.n_pen > 0) {
+    // pencil route: per-object preparation and device-side routing, then both sweep kernels
     // (each over its own table; an empty table ends the kernel at once)
-    cudaError_t e = cudaMemsetAsync(plan->d_counters, 0, 4 * sizeof(int), h->stream);
+    const PencilTables& t = plan->pen;
     mark(0);
-    if (e == cudaSuccess)
-      e = launch_pencil_prep(plan->d_objs, plan->d_pens, plan->d_scr, plan->d_order_pen, plan->n_pen, plan->d_counters,
-                             omega, omega_stride, plan->n_w, s_sigma, plan->d_pen_ok, plan->d_prep_ws,
-                             plan->prep_ws_elems, plan->prep_grid, plan->pen_rmax, kPencilGate, kPencilKappaMax,
-                             h->stream);
+    cudaError_t e = pencil_tables_prepare(h, t, plan->d_objs, omega, omega_stride, s_sigma, nullptr);
     mark(1);
-    if (e == cudaSuccess)
-      e = launch_pencil_route(plan->d_pen_ok, plan->d_order_pen, plan->d_spen, plan->n_pen, plan->d_order_lu,
-                              plan->d_lu_info, plan->n_obj, plan->n_w, plan->d_table_pen, plan->d_table_lu,
-                              plan->d_counters + 4, h->stream);
+    if (e == cudaSuccess) e = pencil_tables_route(h, t);
     mark(2);
     if (e == cudaSuccess)
-      e = launch_pencil_sweep(plan->d_objs, plan->d_pens, plan->d_table_pen, plan->d_counters + 2, omega,
-                              omega_stride, s_sigma, R, I, Delta, h->d_status, plan->n_w, plan->pen_grid,
-                              plan->pen_smem, h->stream);
+      e = launch_pencil_sweep(plan->d_objs, t.d_pens, t.d_table_pen, t.d_counters + 2, omega, omega_stride, s_sigma,
+                              R, I, Delta, h->d_status, plan->n_w, t.pen_grid, t.pen_smem, h->stream);
     mark(3);
     if (e == cudaSuccess)
-      e = launch_sweep_fp64_routed(plan->cfg, plan->d_objs, plan->d_table_lu, plan->d_counters + 3, omega,
-                                   omega_stride, s_sigma, R, I, Delta, h->d_status, plan->n_w, plan->grid,
-                                   plan->smem_bytes, plan->d_workspace, plan->ws_elems, h->stream);
+      e = launch_sweep_fp64_routed(plan->cfg, plan->d_objs, t.d_table_lu, t.d_counters + 3, omega, omega_stride,
+                                   s_sigma, R, I, Delta, h->d_status, plan->n_w, plan->grid, plan->smem_bytes,
+                                   plan->d_workspace, plan->ws_elems, h->stream);
     mark(4);
     if (e != cudaSuccess) return cuda_fail(h, e, "sweep launch");
-    h->launches += 6;
+    h->launches += 2;
     return MROM_OK;
   }
   mark(0);
@@ -473,9 +350,9 @@ extern "C" mrom_status mrom_plan_solver_counts(mrom_plan plan, int32_t* n_pencil
   if (!plan) return MROM_EINVAL;
   mrom_ctx* h = plan->ctx;
   int c[2] = {0, plan->n_obj};
-  if (plan->n_pen > 0) {
+  if (plan->pen.n_pen > 0) {
     cudaSetDevice(h->device);
-    cudaError_t e = cudaMemcpyAsync(c, plan->d_counters + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e = cudaMemcpyAsync(c, plan->pen.d_counters + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "mrom_plan_solver_counts");
   }

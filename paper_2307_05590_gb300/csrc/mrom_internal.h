@@ -23,6 +23,7 @@ struct RomDev {
   const double2* K;     // r x r, used in R (Eq. (18)) and in A
   const double2* C;     // r x r
   const double2* Me;    // r x r or nullptr: U^H (eps M) U, added to A only
+  const double2* Kin;   // r x r or nullptr: the permeability-dependent part of K (K(s_mu) = K + (1/s_mu - 1) K_in)
   const double2* B;     // r x 3: b_i in column i
   const double2* GKK;   // r x r  Gram block [(K+eps M)U]^H X^-1 [(K+eps M)U]
   const double2* GCC;   // r x r  Gram block (CU)^H X^-1 (CU)
@@ -56,6 +57,7 @@ struct PencilDev {
   double2* gsh;
   double2* Gh;
   double2* Eh;
+  double2* Fh;  // V^H K_in V (packed lower, or null): the permeability gradient
   int F;
   int pad;
 };
@@ -78,6 +80,28 @@ struct SweepTask {
   int w0;
   int nw;
   int pad;
+};
+
+// Device tables of the pencil route for a batch of objects (pencil.cu): the eligible objects
+// (one basis shared by the directions) in descending r, their data and preparation scratch,
+// the routing tables and counters.  One stream-ordered allocation.
+struct PencilTables {
+  int n_pen = 0;                // eligible objects (0: no pencil route)
+  int n_obj = 0, n_w = 0, rmax = 0;
+  int prep_grid = 0, pen_grid = 0;
+  size_t prep_ws_elems = 0, pen_smem = 0;
+  void* block = nullptr;
+  PencilDev* d_pens = nullptr;
+  PencilScratch* d_scr = nullptr;
+  int* d_order_pen = nullptr;   // eligible objects, descending r
+  int* d_spen = nullptr;        // frequencies per pencil task, same order
+  int* d_order_lu = nullptr;    // all objects in LU cost order
+  int2* d_lu_info = nullptr;    // {S, matrices-in-global} of the LU kernel, per LU-order entry
+  SweepTask* d_table_pen = nullptr;
+  SweepTask* d_table_lu = nullptr;
+  int* d_pen_ok = nullptr;
+  int* d_counters = nullptr;    // tridiag, finish, pencil kernel, LU kernel, then the two route counts
+  double2* d_prep_ws = nullptr;
 };
 
 }  // namespace mrom
@@ -134,25 +158,7 @@ struct mrom_plan_s {
   int* d_counter = nullptr;
   double2* d_workspace = nullptr;   // grid x ws_elems complex128, for tasks whose matrices are global
   size_t ws_elems = 0;
-  // pencil route (n_pen > 0): eligible objects, their data, routing tables and counters
-  int n_pen = 0;
-  void* pen_block = nullptr;        // one stream-ordered allocation for everything below
-  mrom::PencilDev* d_pens = nullptr;
-  mrom::PencilScratch* d_scr = nullptr;
-  int pen_rmax = 0;
-  int* d_order_pen = nullptr;       // eligible objects, descending r
-  int* d_spen = nullptr;            // frequencies per pencil task, same order
-  int* d_order_lu = nullptr;        // all objects in LU cost order
-  int2* d_lu_info = nullptr;        // {S, matrices-in-global} per LU-order entry
-  mrom::SweepTask* d_table_pen = nullptr;
-  mrom::SweepTask* d_table_lu = nullptr;
-  int* d_pen_ok = nullptr;
-  int* d_counters = nullptr;        // tridiag, finish, pencil sweep, LU sweep, then the two route counts
-  double2* d_prep_ws = nullptr;
-  size_t prep_ws_elems = 0;
-  int prep_grid = 0;
-  int pen_grid = 0;
-  size_t pen_smem = 0;
+  mrom::PencilTables pen;           // pencil route (pen.n_pen > 0)
   // optional stage timing (mrom_plan_timing): events around prep, route, pencil sweep, LU sweep
   bool timing = false;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -196,15 +202,24 @@ cudaError_t launch_sweep_fp64_routed(int cfg, const RomDev* objs, const SweepTas
 // Pencil route (pencil.cu).
 size_t pencil_sweep_smem_bytes(int r, int F);
 int pencil_threads();
-size_t pencil_finish_smem_bytes(int rmax);
-// Tridiagonalisation, QL and finishing kernels; counters[0..1] are their task counters.
-cudaError_t launch_pencil_prep(const RomDev* objs, const PencilDev* pens, const PencilScratch* scr,
-                               const int* order, int n_elig, int* counters, const double* omega, int omega_stride,
-                               int n_w, const double* s_sigma, int* pen_ok, double2* ws, size_t ws_elems, int grid,
-                               int rmax, double gate, double kappa_max, cudaStream_t stream);
-cudaError_t launch_pencil_route(const int* pen_ok, const int* order_pen, const int* spen, int n_pen,
-                                const int* order_lu, const int2* lu_info, int n_lu, int n_w, SweepTask* table_pen,
-                                SweepTask* table_lu, int* counts, cudaStream_t stream);
+// Tables for objs (host records; the device copy is passed to the kernels).  gram: transform
+// the certificate blocks of objects that have them; kin: transform K_in (permeability
+// gradient).  order_lu / lu_info: every object in the LU kernel's cost order with its task
+// shape {S, matrices-in-global}.  No eligible object: t->n_pen = 0 and nothing allocated.
+mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, int n_w, bool gram, bool kin,
+                                 const std::vector<int>& order_lu, const std::vector<int2>& lu_info, PencilTables* t);
+void pencil_tables_destroy(PencilTables* t, cudaStream_t stream);
+// Preparation (tridiagonalisation, QL, finishing) for one sweep; s_mu scales K_in as
+// K + (1/s_mu - 1) K_in (NULL: no scale).  Resets the counters.  Then the routing kernel
+// (pencil_tables_route) fills the pencil and LU task tables.
+cudaError_t pencil_tables_prepare(mrom_ctx* h, const PencilTables& t, const RomDev* objs, const double* omega,
+                                  int omega_stride, const double* s_sigma, const double* s_mu);
+cudaError_t pencil_tables_route(mrom_ctx* h, const PencilTables& t);
+size_t pencil_vjp_smem_bytes(int r, int F);
+cudaError_t launch_pencil_vjp(const RomDev* objs, const PencilDev* pens, const SweepTask* table, int* counter,
+                              const double* omega, int omega_stride, const double* s_sigma, const double* s_mu,
+                              const double* gR, const double* gI, double* g_omega, double* g_mu_part, double* R,
+                              double* I, int* status, int n_w, int grid, size_t smem_bytes, cudaStream_t stream);
 cudaError_t launch_pencil_sweep(const RomDev* objs, const PencilDev* pens, const SweepTask* table, int* counter,
                                 const double* omega, int omega_stride, const double* s_sigma, double* R,
                                 double* I, double* Delta, int* status, int n_w, int grid, size_t smem_bytes,

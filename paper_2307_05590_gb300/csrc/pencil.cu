@@ -25,6 +25,8 @@
 #include <algorithm>
 #include <cfloat>
 #include <cstdlib>
+#include <cstring>
+#include <vector>
 
 namespace mrom {
 namespace {
@@ -83,8 +85,8 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
                       const PencilScratch* __restrict__ scr, const int* __restrict__ order, int n_elig,
                       int* __restrict__ counter,
                    const double* __restrict__ omega, int omega_stride, int n_w,
-                   const double* __restrict__ s_sigma, int* __restrict__ pen_ok, double2* __restrict__ ws,
-                   size_t ws_elems, double gate, double kappa_max) {
+                   const double* __restrict__ s_sigma, const double* __restrict__ s_mu, int* __restrict__ pen_ok,
+                   double2* __restrict__ ws, size_t ws_elems, double gate, double kappa_max) {
   __shared__ double sd[MROM_MAX_R], se[MROM_MAX_R], stau[MROM_MAX_R];
   __shared__ double2 salpha[MROM_MAX_R], sph[MROM_MAX_R];
   __shared__ double red[kPW];
@@ -115,7 +117,8 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
     }
     wmin = block_min(wmin, red);
 
-    // ---- load C (W0) and K' = K + Me (W1)
+    // ---- load C (W0) and K' = K(s_mu) + Me (W1)
+    const double fmu = (s_mu && ob.Kin) ? 1.0 / s_mu[o] - 1.0 : 0.0;
     double cn = 0.0;
     for (int idx = tid; idx < rr; idx += kPT) {
       const double2 c = ob.C[idx];
@@ -123,6 +126,11 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
       cn += c.x * c.x + c.y * c.y;
       double2 k = ob.K[idx];
       if (ob.Me) k = cadd(k, ob.Me[idx]);
+      if (fmu != 0.0) {
+        const double2 q = ob.Kin[idx];
+        k.x = fma(fmu, q.x, k.x);
+        k.y = fma(fmu, q.y, k.y);
+      }
       W1[idx] = k;
     }
     cn = block_sum(cn, red);  // (its barriers publish W0, W1)
@@ -420,11 +428,15 @@ pencil_finish_kernel(const RomDev* __restrict__ objs, const PencilDev* __restric
         pd.gsh[idx] = acc;  // gsh[k][q]: (gs_q V)[k]
       }
     }
-    // Gh_X = V^H G_X V for X = KK, CC, S (interleaved, packed lower triangle) and E = V^H Me V
-    const int nmat = (pd.Gh ? 3 : 0) + (pd.Eh ? 1 : 0);
+    // Gh_X = V^H G_X V for X = KK, CC, S (interleaved, packed lower triangle), E = V^H Me V and
+    // F = V^H K_in V (packed lower)
+    const int ng3 = pd.Gh ? 3 : 0;
+    const int nmat = ng3 + (pd.Eh ? 1 : 0) + (pd.Fh ? 1 : 0);
     for (int x = 0; x < nmat; ++x) {
-      const bool gram = pd.Gh != nullptr && x < 3;
-      const double2* G = !gram ? ob.Me : (x == 0 ? ob.GKK : (x == 1 ? ob.GCC : ob.GSk));
+      const bool gram = x < ng3;
+      const bool kin = !gram && (x == ng3 + (pd.Eh ? 1 : 0));
+      double2* dst = gram ? nullptr : (kin ? pd.Fh : pd.Eh);
+      const double2* G = gram ? (x == 0 ? ob.GKK : (x == 1 ? ob.GCC : ob.GSk)) : (kin ? ob.Kin : ob.Me);
       // Y = G V (W0)
       for (int idx = tid; idx < rr; idx += kPT) {
         const int i = idx / r, j = idx - (idx / r) * r;
@@ -442,7 +454,7 @@ pencil_finish_kernel(const RomDev* __restrict__ objs, const PencilDev* __restric
         if (gram)
           pd.Gh[(size_t)e * 3 + x] = acc;
         else
-          pd.Eh[e] = acc;
+          dst[e] = acc;
       }
       __syncthreads();
     }
@@ -743,6 +755,240 @@ pencil_sweep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict
   }
 }
 
+// ------------------------------------------------------------------ adjoint sweep
+//
+// Vector-Jacobian product of (R, I) on the pencil route (same task layout as the sweep: lane
+// = frequency, the object's rows split over the warps of its frequency group).  With
+// w' = s_sigma omega, K(s_mu) + Me = K', z = V^-1 P (z_aj = u_a beta_aj), E = V^H Me V,
+// F = V^H K_in V, and symmetrised cotangents G = g + g^T:
+//   R = N0 - a^3/4 Re(Z^H (Lambda - E) Z),   I = w' a^3/4 (c00 + Re(Z^H Z + beta^H Z + Z^H beta)),
+//   the adjoint Lambda_adj = A^-H Z_rhs = V Y with
+//   Y = (Lambda + i w')^-1 [-a^3/4 (Lambda - E) Z G_R + w' a^3/4 (Z + beta) G_I],
+//   S_w = Im tr((B + C P)^H Lambda_adj) = Im tr((beta + Z)^H Y),
+//   S_mu = Re tr((K_in P)^H Lambda_adj) = Re tr((F Z)^H Y),  HK = Re(Z^H F Z),
+//   dL/domega = s_sigma S_w + sum gI.I / omega,  dL/ds_mu part = (S_mu + a^3/4 sum gR.HK) / s_mu^2.
+// Per row a every term needs only row a of E Z and F Z, so rows are independent.
+constexpr int kNQV = 42;  // partial sums per lane: R 0..5, I 6..11, B 12..20, RE 21..29, HK 30..38, Sw 39, Smu 40
+
+__device__ __forceinline__ double2 herm_packed(const double2* __restrict__ M, int a, int b) {  // M[a][b]
+  if (b <= a) return M[(size_t)a * (a + 1) / 2 + b];
+  const double2 v = M[(size_t)b * (b + 1) / 2 + a];
+  return make_double2(v.x, -v.y);
+}
+
+template <bool HAS_E, bool HAS_F>
+__device__ __forceinline__ void pencil_vjp_rows(const PencilDev& pd, int r, const double2* __restrict__ zg, double w,
+                                                double alpha3, const double (&GR)[9], const double (&GI)[9], int q0,
+                                                int wpg, double (&acc)[kNQV]) {
+  const double cR = -0.25 * alpha3, cI = 0.25 * alpha3 * w;
+  for (int a = q0; a < r; a += wpg) {
+    double2 za[3], ez[3], fz[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      za[j] = zg[(a * 3 + j) * 32];
+      ez[j] = fz[j] = make_double2(0.0, 0.0);
+    }
+    if constexpr (HAS_E || HAS_F) {
+      for (int b = 0; b < r; ++b) {
+        double2 zb[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) zb[j] = zg[(b * 3 + j) * 32];
+        if constexpr (HAS_E) {
+          const double2 e = herm_packed(pd.Eh, a, b);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) ez[j] = cmac(ez[j], e, zb[j]);
+        }
+        if constexpr (HAS_F) {
+          const double2 f = herm_packed(pd.Fh, a, b);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) fz[j] = cmac(fz[j], f, zb[j]);
+        }
+      }
+    }
+    const double lam = pd.lam[a];
+    double2 be[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) be[j] = pd.beta[a * 3 + j];
+    {
+      int q = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j, ++q) {
+          const double v = fma(za[i].x, za[j].x, za[i].y * za[j].y);
+          acc[q] = fma(lam, v, acc[q]);
+          acc[6 + q] += v;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        acc[12 + i * 3 + j] = fma(be[i].x, za[j].x, fma(be[i].y, za[j].y, acc[12 + i * 3 + j]));
+        if constexpr (HAS_E) acc[21 + i * 3 + j] = fma(za[i].x, ez[j].x, fma(za[i].y, ez[j].y, acc[21 + i * 3 + j]));
+        if constexpr (HAS_F) acc[30 + i * 3 + j] = fma(za[i].x, fz[j].x, fma(za[i].y, fz[j].y, acc[30 + i * 3 + j]));
+      }
+    // adjoint row a: rhs_k = sum_j cR GR[j][k] (lam z_aj - (E z)_aj) + cI GI[j][k] (z_aj + beta_aj)
+    const double den = 1.0 / fma(lam, lam, w * w);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double2 rhs = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double gr = cR * GR[j * 3 + k], gi = cI * GI[j * 3 + k];
+        const double kx = fma(lam, za[j].x, -ez[j].x), ky = fma(lam, za[j].y, -ez[j].y);
+        rhs.x = fma(gr, kx, fma(gi, za[j].x + be[j].x, rhs.x));
+        rhs.y = fma(gr, ky, fma(gi, za[j].y + be[j].y, rhs.y));
+      }
+      // Y = rhs / (lam + i w) = rhs (lam - i w) / (lam^2 + w^2)
+      const double2 y = make_double2(fma(rhs.x, lam, rhs.y * w) * den, fma(rhs.y, lam, -rhs.x * w) * den);
+      const double vx = be[k].x + za[k].x, vy = be[k].y + za[k].y;
+      acc[39] += vx * y.y - vy * y.x;  // Im(conj(v) y)
+      if constexpr (HAS_F) acc[40] = fma(fz[k].x, y.x, fma(fz[k].y, y.y, acc[40]));
+    }
+  }
+}
+
+template <bool HAS_E, bool HAS_F>
+__device__ __forceinline__ void pencil_vjp_task(const RomDev& ob, const PencilDev& pd, const SweepTask& task,
+                                                const double* __restrict__ omega, int omega_stride, double ssig,
+                                                double smu, const double* __restrict__ gR,
+                                                const double* __restrict__ gI, double* __restrict__ g_omega,
+                                                double* __restrict__ g_mu_part, double* __restrict__ Rout,
+                                                double* __restrict__ Iout, int* __restrict__ status, int n_w,
+                                                unsigned char* smem_raw, double* Ws) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double2* zs = reinterpret_cast<double2*>(smem_raw);
+  double* rbuf = reinterpret_cast<double*>(smem_raw);
+  const int r = ob.r, S = task.nw;
+  const int F = pd.F, wpg = kPW / F;
+  for (int s = tid; s < 32 * F; s += kPT) {
+    double w = __longlong_as_double(0x7ff8000000000000LL);
+    if (s < S) {
+      w = omega[(size_t)task.obj * omega_stride + task.w0 + s] * ssig;
+      if (!(w > 0.0) || !isfinite(w) || !(smu > 0.0) || !(ssig > 0.0)) {
+        atomicOr(status, kStatusBadOmega);
+        w = __longlong_as_double(0x7ff8000000000000LL);
+      }
+    }
+    Ws[s] = w;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < r * 32 * F; idx += kPT) {
+    const int g = idx / (r * 32);
+    const int rem = idx - g * r * 32;
+    const int k = rem >> 5, ln = rem & 31;
+    const double w = Ws[g * 32 + ln];
+    const double lam = pd.lam[k];
+    const double den = 1.0 / fma(lam, lam, w * w);
+    const double2 u = make_double2(-w * w * den, w * lam * den);
+    double2* zk = zs + ((size_t)(g * r + k) * 3) * 32 + ln;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double2 b = pd.beta[k * 3 + j];
+      zk[j * 32] = make_double2(fma(u.x, b.x, -u.y * b.y), fma(u.x, b.y, u.y * b.x));
+    }
+  }
+  __syncthreads();
+  double acc[kNQV];
+#pragma unroll
+  for (int q = 0; q < kNQV; ++q) acc[q] = 0.0;
+  {
+    const int g = warp % F, s = g * 32 + lane;
+    double GR[9], GI[9];
+    const size_t e = ((size_t)task.obj * n_w + task.w0 + min(s, S - 1)) * 9;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        GR[i * 3 + j] = gR[e + i * 3 + j] + gR[e + j * 3 + i];
+        GI[i * 3 + j] = gI[e + i * 3 + j] + gI[e + j * 3 + i];
+      }
+    pencil_vjp_rows<HAS_E, HAS_F>(pd, r, zs + (size_t)g * r * 3 * 32 + lane, Ws[s], ob.alpha3, GR, GI, warp / F,
+                                  wpg, acc);
+  }
+  __syncthreads();
+  {
+    double* rb = rbuf + (size_t)warp * kNQV * 32 + lane;
+#pragma unroll
+    for (int q = 0; q < kNQV; ++q) rb[q * 32] = acc[q];
+  }
+  __syncthreads();
+  if (wpg > 1) {
+    for (int idx = tid; idx < F * kNQV * 32; idx += kPT) {
+      const int g = idx / (kNQV * 32);
+      const int rem = idx - g * kNQV * 32;
+      double v = rbuf[(size_t)g * kNQV * 32 + rem];
+      for (int k = 1; k < wpg; ++k) v += rbuf[(size_t)(g + k * F) * kNQV * 32 + rem];
+      rbuf[(size_t)g * kNQV * 32 + rem] = v;
+    }
+    __syncthreads();
+  }
+  for (int s = tid; s < S; s += kPT) {
+    const double* tot = rbuf + (size_t)(s >> 5) * kNQV * 32 + (s & 31);
+    auto t = [tot](int q) { return tot[q * 32]; };
+    const double wv = Ws[s];
+    const size_t o = (size_t)task.obj * n_w + task.w0 + s;
+    double gI_dot_I = 0.0, gR_dot_HK = 0.0;
+#pragma unroll
+    for (int ij = 0; ij < 9; ++ij) {
+      const int i = ij / 3, j = ij - (ij / 3) * 3;
+      const int lo = i < j ? i : j, hi = i < j ? j : i;
+      const int sym = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+      double kf = t(sym);
+      if constexpr (HAS_E) kf -= 0.5 * (t(21 + i * 3 + j) + t(21 + j * 3 + i));
+      const double Rv = fma(-0.25 * ob.alpha3, kf, ob.N0[ij]);
+      const double Iv = 0.25 * ob.alpha3 * wv * (ob.c00[ij] + t(6 + sym) + t(12 + i * 3 + j) + t(12 + j * 3 + i));
+      if (Rout) Rout[o * 9 + ij] = Rv;
+      if (Iout) Iout[o * 9 + ij] = Iv;
+      gI_dot_I = fma(gI[o * 9 + ij], Iv, gI_dot_I);
+      if constexpr (HAS_F) gR_dot_HK = fma(gR[o * 9 + ij], 0.5 * (t(30 + i * 3 + j) + t(30 + j * 3 + i)), gR_dot_HK);
+    }
+    const double wr = wv / ssig;  // the caller's omega
+    g_omega[o] = fma(ssig, t(39), gI_dot_I / wr);
+    g_mu_part[o] = HAS_F ? (t(40) + 0.25 * ob.alpha3 * gR_dot_HK) / (smu * smu) : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kPT, 1)
+pencil_vjp_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__ pens,
+                  const SweepTask* __restrict__ table, int* __restrict__ counter, const double* __restrict__ omega,
+                  int omega_stride, const double* __restrict__ s_sigma, const double* __restrict__ s_mu,
+                  const double* __restrict__ gR, const double* __restrict__ gI, double* __restrict__ g_omega,
+                  double* __restrict__ g_mu_part, double* __restrict__ Rout, double* __restrict__ Iout,
+                  int* __restrict__ status, int n_w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_task;
+  __shared__ double Ws[kPT];
+  const int tid = threadIdx.x;
+  const int n_tasks = table[0].w0;
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();
+    if (t >= n_tasks) break;
+    const SweepTask task = table_task(table, n_w, t);
+    const RomDev& ob = objs[task.obj];
+    const PencilDev& pd = pens[task.obj];
+    const double ssig = s_sigma ? s_sigma[task.obj] : 1.0;
+    const double smu = s_mu ? s_mu[task.obj] : 1.0;
+    const bool he = pd.Eh != nullptr, hf = pd.Fh != nullptr;
+    if (he && hf)
+      pencil_vjp_task<true, true>(ob, pd, task, omega, omega_stride, ssig, smu, gR, gI, g_omega, g_mu_part, Rout,
+                                  Iout, status, n_w, smem_raw, Ws);
+    else if (he)
+      pencil_vjp_task<true, false>(ob, pd, task, omega, omega_stride, ssig, smu, gR, gI, g_omega, g_mu_part, Rout,
+                                   Iout, status, n_w, smem_raw, Ws);
+    else if (hf)
+      pencil_vjp_task<false, true>(ob, pd, task, omega, omega_stride, ssig, smu, gR, gI, g_omega, g_mu_part, Rout,
+                                   Iout, status, n_w, smem_raw, Ws);
+    else
+      pencil_vjp_task<false, false>(ob, pd, task, omega, omega_stride, ssig, smu, gR, gI, g_omega, g_mu_part, Rout,
+                                    Iout, status, n_w, smem_raw, Ws);
+  }
+}
+
 }  // namespace
 
 size_t pencil_sweep_smem_bytes(int r, int F) {
@@ -755,12 +1001,15 @@ int pencil_threads() { return kPT; }
 
 size_t pencil_finish_smem_bytes(int rmax) { return (size_t)rmax * (size_t)(rmax | 1) * sizeof(double); }
 
+namespace {
+
 cudaError_t launch_pencil_prep(const RomDev* objs, const PencilDev* pens, const PencilScratch* scr,
                                const int* order, int n_elig, int* counters, const double* omega, int omega_stride,
-                               int n_w, const double* s_sigma, int* pen_ok, double2* ws, size_t ws_elems, int grid,
-                               int rmax, double gate, double kappa_max, cudaStream_t stream) {
+                               int n_w, const double* s_sigma, const double* s_mu, int* pen_ok, double2* ws,
+                               size_t ws_elems, int grid, int rmax, double gate, double kappa_max,
+                               cudaStream_t stream) {
   pencil_tridiag_kernel<<<grid, kPT, 0, stream>>>(objs, pens, scr, order, n_elig, counters, omega, omega_stride, n_w,
-                                                  s_sigma, pen_ok, ws, ws_elems, gate, kappa_max);
+                                                  s_sigma, s_mu, pen_ok, ws, ws_elems, gate, kappa_max);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // objects per warp (lanes in use): one object per warp spreads the chases over all SMs
@@ -794,6 +1043,26 @@ cudaError_t launch_pencil_route(const int* pen_ok, const int* order_pen, const i
   return cudaGetLastError();
 }
 
+}  // namespace
+
+size_t pencil_vjp_smem_bytes(int r, int F) {
+  const size_t z = (size_t)32 * F * 3 * r * sizeof(double2);
+  const size_t red = (size_t)kPW * kNQV * 32 * sizeof(double);
+  return z > red ? z : red;
+}
+
+cudaError_t launch_pencil_vjp(const RomDev* objs, const PencilDev* pens, const SweepTask* table, int* counter,
+                              const double* omega, int omega_stride, const double* s_sigma, const double* s_mu,
+                              const double* gR, const double* gI, double* g_omega, double* g_mu_part, double* R,
+                              double* I, int* status, int n_w, int grid, size_t smem_bytes, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(pencil_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  pencil_vjp_kernel<<<grid, kPT, smem_bytes, stream>>>(objs, pens, table, counter, omega, omega_stride, s_sigma, s_mu,
+                                                       gR, gI, g_omega, g_mu_part, R, I, status, n_w);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pencil_sweep(const RomDev* objs, const PencilDev* pens, const SweepTask* table, int* counter,
                                 const double* omega, int omega_stride, const double* s_sigma, double* R,
                                 double* I, double* Delta, int* status, int n_w, int grid, size_t smem_bytes,
@@ -804,6 +1073,158 @@ cudaError_t launch_pencil_sweep(const RomDev* objs, const PencilDev* pens, const
   pencil_sweep_kernel<<<grid, kPT, smem_bytes, stream>>>(objs, pens, table, counter, omega, omega_stride, s_sigma,
                                                          R, I, Delta, status, n_w);
   return cudaGetLastError();
+}
+
+namespace {
+
+// Accuracy gates of the pencil route: the estimated forward error eps ||H||_F / omega_min must
+// stay below kPencilGate (1e-11: the measured error stays near or below this estimate, so a
+// factor of ten below the 1e-10 parity tolerance), and ||C||_F ||L^-1||_F^2 >= kappa_2(C) below
+// kPencilKappaMax; other objects take the LU route.
+constexpr double kPencilGate = 1e-11;
+constexpr double kPencilKappaMax = 1e6;
+// QL rotation log per object (complex slots): rotations and sweep records (QL takes about r^2
+// rotations in 2 r sweeps)
+constexpr size_t rot_cap(int r) { return 3 * (size_t)r * r + 64; }
+constexpr size_t sweep_cap(int r) { return 16 * (size_t)r + 16; }
+
+}  // namespace
+
+mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, int n_w, bool gram, bool kin,
+                                 const std::vector<int>& order_lu, const std::vector<int2>& lu_info, PencilTables* t) {
+  *t = PencilTables();
+  const int n_obj = (int)objs.size();
+  t->n_obj = n_obj;
+  t->n_w = n_w;
+  std::vector<int> elig;
+  for (int o = 0; o < n_obj; ++o)
+    if (!objs[o].per_dir) elig.push_back(o);
+  if (elig.empty()) return MROM_OK;
+  std::stable_sort(elig.begin(), elig.end(), [&](int a, int b) { return objs[a].r > objs[b].r; });
+  // frequency groups of 32 per task: as many as the shared memory holds (one CTA per SM),
+  // a power of two up to 8, and no more than the frequencies need
+  const size_t budget = h->smem_optin - 4096;
+  int need = 1;
+  while (need < 8 && 32 * need < n_w) need *= 2;
+  std::vector<int> spen(elig.size());
+  std::vector<PencilDev> pens(n_obj);
+  std::memset(pens.data(), 0, n_obj * sizeof(PencilDev));
+  size_t data_elems = 0, smem = 0;
+  int rmax = 1;
+  std::vector<size_t> off(n_obj, 0);
+  for (size_t k = 0; k < elig.size(); ++k) {
+    const int o = elig[k], r = objs[o].r;
+    int F = 8;
+    while (F > 1 && (F > need || pencil_sweep_smem_bytes(r, F) > budget)) F /= 2;
+    spen[k] = 32 * F;
+    pens[o].F = F;
+    smem = std::max(smem, pencil_sweep_smem_bytes(r, F));
+    rmax = std::max(rmax, r);
+    off[o] = data_elems;
+    const size_t tri = (size_t)r * (r + 1) / 2;
+    data_elems += (size_t)(r + 1) / 2 + 3 * (size_t)r;                    // lam (in complex slots), beta
+    if (gram && objs[o].has_cert) data_elems += 6 * (size_t)r + 3 * tri;  // gsh, Gh
+    if (objs[o].Me) data_elems += tri;                                    // Eh
+    if (kin && objs[o].Kin) data_elems += tri;                            // Fh
+    data_elems += (size_t)r * r + (size_t)(r + 1) / 2 + rot_cap(r) + (sweep_cap(r) + 1) / 2;  // scratch
+  }
+  t->prep_grid = std::min<int>((int)elig.size(), 2 * h->num_sms);
+  t->prep_ws_elems = 3 * (size_t)rmax * rmax;
+  t->pen_grid = h->num_sms;
+  t->pen_smem = smem;
+  t->rmax = rmax;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b_scr = al(n_obj * sizeof(PencilScratch)), b_nsw = al(elig.size() * sizeof(int));
+  const size_t b_pens = al(n_obj * sizeof(PencilDev)), b_op = al(elig.size() * sizeof(int)),
+               b_sp = al(elig.size() * sizeof(int)), b_ol = al(n_obj * sizeof(int)),
+               b_li = al(n_obj * sizeof(int2)), b_tab = al((n_obj + 1) * sizeof(SweepTask)),
+               b_ok = al(n_obj * sizeof(int)), b_cnt = al(8 * sizeof(int)),
+               b_data = al(data_elems * sizeof(double2)),
+               b_ws = al(t->prep_ws_elems * t->prep_grid * sizeof(double2));
+  const size_t total = b_scr + b_nsw + b_pens + b_op + b_sp + b_ol + b_li + 2 * b_tab + b_ok + b_cnt + b_data + b_ws;
+  void* blk = nullptr;
+  cudaError_t e = cudaMallocAsync(&blk, total, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "pencil route: allocation");
+  t->block = blk;
+  char* p = static_cast<char*>(blk);
+  t->d_scr = reinterpret_cast<PencilScratch*>(p); p += b_scr;
+  int* d_nsw = reinterpret_cast<int*>(p); p += b_nsw;
+  t->d_pens = reinterpret_cast<PencilDev*>(p); p += b_pens;
+  t->d_order_pen = reinterpret_cast<int*>(p); p += b_op;
+  t->d_spen = reinterpret_cast<int*>(p); p += b_sp;
+  t->d_order_lu = reinterpret_cast<int*>(p); p += b_ol;
+  t->d_lu_info = reinterpret_cast<int2*>(p); p += b_li;
+  t->d_table_pen = reinterpret_cast<SweepTask*>(p); p += b_tab;
+  t->d_table_lu = reinterpret_cast<SweepTask*>(p); p += b_tab;
+  t->d_pen_ok = reinterpret_cast<int*>(p); p += b_ok;
+  t->d_counters = reinterpret_cast<int*>(p); p += b_cnt;
+  double2* data = reinterpret_cast<double2*>(p); p += b_data;
+  t->d_prep_ws = reinterpret_cast<double2*>(p);
+  std::vector<PencilScratch> scr(n_obj);
+  std::memset(scr.data(), 0, n_obj * sizeof(PencilScratch));
+  for (size_t k = 0; k < elig.size(); ++k) {
+    const int o = elig[k];
+    const int r = objs[o].r;
+    const size_t tri = (size_t)r * (r + 1) / 2;
+    double2* q = data + off[o];
+    pens[o].lam = reinterpret_cast<double*>(q); q += (r + 1) / 2;
+    pens[o].beta = q; q += 3 * (size_t)r;
+    if (gram && objs[o].has_cert) {
+      pens[o].gsh = q; q += 6 * (size_t)r;
+      pens[o].Gh = q; q += 3 * tri;
+    }
+    if (objs[o].Me) {
+      pens[o].Eh = q; q += tri;
+    }
+    if (kin && objs[o].Kin) {
+      pens[o].Fh = q; q += tri;
+    }
+    scr[o].W = q; q += (size_t)r * r;
+    scr[o].e = reinterpret_cast<double*>(q); q += (r + 1) / 2;
+    scr[o].rot = q; q += rot_cap(r);
+    scr[o].sweeps = reinterpret_cast<int2*>(q);
+    scr[o].cap_rot = (int)rot_cap(r);
+    scr[o].cap_sw = (int)sweep_cap(r);
+    scr[o].nsw = d_nsw + k;
+  }
+  t->n_pen = (int)elig.size();
+  cudaStream_t st = h->stream;
+  e = cudaMemcpyAsync(t->d_pens, pens.data(), n_obj * sizeof(PencilDev), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_scr, scr.data(), n_obj * sizeof(PencilScratch), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_order_pen, elig.data(), elig.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_spen, spen.data(), spen.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_order_lu, order_lu.data(), n_obj * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_lu_info, lu_info.data(), n_obj * sizeof(int2), cudaMemcpyHostToDevice, st);
+  // (pageable sources are staged before these calls return, so the host vectors may go)
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->d_pen_ok, 0, b_ok, st);
+  if (e != cudaSuccess) {
+    pencil_tables_destroy(t, st);
+    return cuda_fail(h, e, "pencil route: upload");
+  }
+  return MROM_OK;
+}
+
+void pencil_tables_destroy(PencilTables* t, cudaStream_t stream) {
+  if (t->block) cudaFreeAsync(t->block, stream);
+  *t = PencilTables();
+}
+
+cudaError_t pencil_tables_prepare(mrom_ctx* h, const PencilTables& t, const RomDev* objs, const double* omega,
+                                  int omega_stride, const double* s_sigma, const double* s_mu) {
+  cudaError_t e = cudaMemsetAsync(t.d_counters, 0, 4 * sizeof(int), h->stream);
+  if (e == cudaSuccess)
+    e = launch_pencil_prep(objs, t.d_pens, t.d_scr, t.d_order_pen, t.n_pen, t.d_counters, omega, omega_stride, t.n_w,
+                           s_sigma, s_mu, t.d_pen_ok, t.d_prep_ws, t.prep_ws_elems, t.prep_grid, t.rmax, kPencilGate,
+                           kPencilKappaMax, h->stream);
+  if (e == cudaSuccess) h->launches += 3;
+  return e;
+}
+
+cudaError_t pencil_tables_route(mrom_ctx* h, const PencilTables& t) {
+  const cudaError_t e = launch_pencil_route(t.d_pen_ok, t.d_order_pen, t.d_spen, t.n_pen, t.d_order_lu, t.d_lu_info,
+                                            t.n_obj, t.n_w, t.d_table_pen, t.d_table_lu, t.d_counters + 4, h->stream);
+  if (e == cudaSuccess) ++h->launches;
+  return e;
 }
 
 }  // namespace mrom

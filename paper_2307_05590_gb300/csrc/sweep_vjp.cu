@@ -11,7 +11,8 @@
 //   dL/domega = s_sigma Im tr((B + C P)^H Lambda) + sum gI_ij I_ij / omega,
 //   dL/ds_mu  = (Re tr((K_in P)^H Lambda) + a^3/4 sum gR_ij Re(p_i^H K_in p_j)) / s_mu^2,
 //   dL/ds_sigma = sum_omega (omega / s_sigma) dL/domega      (I(omega; s_sigma) = I(s_sigma omega; 1)).
-// The factors are recomputed here instead of being stored per frequency.
+// The factors are recomputed here instead of being stored per frequency.  This is the LU
+// route; the pencil route of the same product is pencil_vjp_kernel (pencil.cu).
 #include "mrom_internal.h"
 
 #include <algorithm>
@@ -53,6 +54,21 @@ struct VjpObj {
   int r;
 };
 
+// Task t of a routed table (header entry 0: .obj = entries, .w0 = total tasks; then {object,
+// frequencies per task, first task index, flags}).
+__device__ __forceinline__ SweepTask routed_task(const SweepTask* __restrict__ table, int n_w, int t) {
+  const int n = table[0].obj;
+  int lo = 1, hi = n + 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (table[mid].w0 <= t) lo = mid; else hi = mid;
+  }
+  const SweepTask e = table[lo];
+  const int w0 = (t - e.w0) * e.nw;
+  return SweepTask{e.obj, w0, min(e.nw, n_w - w0), e.pad};
+}
+
+template <bool ROUTED>
 __global__ void __launch_bounds__(kT, 4)
 sweep_vjp_kernel(const VjpObj* __restrict__ objs, const SweepTask* __restrict__ tasks, int n_tasks,
                  int* __restrict__ counter, const double* __restrict__ omega, int omega_stride,
@@ -63,13 +79,14 @@ sweep_vjp_kernel(const VjpObj* __restrict__ objs, const SweepTask* __restrict__ 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_task;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (ROUTED) n_tasks = tasks[0].w0;
   for (;;) {
     if (tid == 0) s_task = atomicAdd(counter, 1);
     __syncthreads();
     const int t = s_task;
     __syncthreads();
     if (t >= n_tasks) break;
-    const SweepTask task = tasks[t];
+    const SweepTask task = ROUTED ? routed_task(tasks, n_w, t) : tasks[t];
     const VjpObj& ob = objs[task.obj];
     const int r = ob.r, S = task.nw, ld = r + 3;
     const size_t per_elems = (size_t)r * ld + 9 * (size_t)r;  // augmented system + y^K, y^C, y^Kin
@@ -369,7 +386,10 @@ extern "C" mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int
   std::vector<VjpObj> objs(n_obj);
   std::vector<SweepTask> tasks;
   std::vector<double> cost;
+  std::vector<int2> lu_shape(n_obj);
   size_t smem = 0, ws_elems = 0;
+  int64_t n_tasks_all = 0;
+  const bool pencil = h->solver == MROM_SOLVER_AUTO;  // every object here has one shared basis
   for (int o = 0; o < n_obj; ++o) {
     const mrom_rom* m = roms[o];
     VjpObj& d = objs[o];
@@ -387,48 +407,91 @@ extern "C" mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int
     const size_t per = in_smem ? per_s : vjp_bytes_per_system(m->r, false);
     const int S = in_smem ? std::min<int>(n_w, (int)(budget / per_s)) : 1;
     if (!in_smem) ws_elems = std::max(ws_elems, (size_t)m->r * (m->r + 3) + 9 * (size_t)m->r);
+    smem = std::max(smem, per * std::min(S, n_w));
+    n_tasks_all += (n_w + S - 1) / S;
+    lu_shape[o] = make_int2(S, in_smem ? 0 : 1);
+    if (pencil) continue;  // the LU kernel runs over the device-routed table
     const double r = m->r;
     for (int w0 = 0; w0 < n_w; w0 += S) {
       const int nw = std::min(S, n_w - w0);
       tasks.push_back(SweepTask{o, w0, nw, in_smem ? 0 : 1});
       cost.push_back((8.0 * r * r * r / 3.0 + 40.0 * r * r) * nw);
-      smem = std::max(smem, per * nw);
     }
+  }
+  // pencil route: tables (V^H K_in V when the permeability gradient is wanted), then
+  // preparation and routing on the device
+  PencilTables pt;
+  std::vector<RomDev> recs;
+  if (pencil) {
+    recs.resize(n_obj);
+    for (int o = 0; o < n_obj; ++o) recs[o] = rom_record(roms[o]);
+    std::vector<int> order_lu(n_obj);
+    std::iota(order_lu.begin(), order_lu.end(), 0);
+    std::stable_sort(order_lu.begin(), order_lu.end(), [&](int a, int b) { return recs[a].r > recs[b].r; });
+    std::vector<int2> lu_info(n_obj);
+    for (int k = 0; k < n_obj; ++k) lu_info[k] = lu_shape[order_lu[k]];
+    const mrom_status ps = pencil_tables_create(h, recs, n_w, false, g_smu != nullptr, order_lu, lu_info, &pt);
+    if (ps != MROM_OK) return ps;
   }
   std::vector<int> order(tasks.size());
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   std::vector<SweepTask> sorted(tasks.size());
   for (size_t k = 0; k < order.size(); ++k) sorted[k] = tasks[order[k]];
-  e = cudaFuncSetAttribute(sweep_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const void* lu_fn = pencil ? reinterpret_cast<const void*>(&sweep_vjp_kernel<true>)
+                             : reinterpret_cast<const void*>(&sweep_vjp_kernel<false>);
+  e = cudaFuncSetAttribute(lu_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_vjp_kernel, kT, smem);
-  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_sweep_vjp: configuration");
-  const int grid = std::min<int>((int)sorted.size(), h->num_sms * std::max(occ, 1));
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lu_fn, kT, smem);
+  if (e != cudaSuccess) {
+    pencil_tables_destroy(&pt, h->stream);
+    return cuda_fail(h, e, "mrom_sweep_vjp: configuration");
+  }
+  const int grid = (int)std::min<int64_t>(n_tasks_all, (int64_t)h->num_sms * std::max(occ, 1));
   const size_t ws_bytes = ws_elems * sizeof(double2) * grid;
+  const size_t b_recs = pencil ? (n_obj * sizeof(RomDev) + 255) / 256 * 256 : 0;
   const size_t bytes = ws_bytes + (size_t)n_obj * n_w * sizeof(double) + n_obj * sizeof(VjpObj) +
-                       sorted.size() * sizeof(SweepTask) + 16;
+                       sorted.size() * sizeof(SweepTask) + 16 + b_recs + 256;
   void* blk = nullptr;
   e = cudaMallocAsync(&blk, bytes, h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_sweep_vjp: allocation");
+  if (e != cudaSuccess) {
+    pencil_tables_destroy(&pt, h->stream);
+    return cuda_fail(h, e, "mrom_sweep_vjp: allocation");
+  }
   char* p = static_cast<char*>(blk);
   auto* d_ws = ws_elems ? reinterpret_cast<double2*>(p) : nullptr;
   p += ws_bytes;
   auto* d_gmu = reinterpret_cast<double*>(p);
   p += (size_t)n_obj * n_w * sizeof(double);
+  auto* d_recs = reinterpret_cast<RomDev*>(p);
+  p += b_recs;
   auto* d_objs = reinterpret_cast<VjpObj*>(p);
   p += n_obj * sizeof(VjpObj);
   auto* d_tasks = reinterpret_cast<SweepTask*>(p);
   p += sorted.size() * sizeof(SweepTask);
   auto* d_counter = reinterpret_cast<int*>(p);
   e = cudaMemcpyAsync(d_objs, objs.data(), n_obj * sizeof(VjpObj), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && !pencil)
     e = cudaMemcpyAsync(d_tasks, sorted.data(), sorted.size() * sizeof(SweepTask), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(int), h->stream);
-  if (e == cudaSuccess) {
-    sweep_vjp_kernel<<<grid, kT, smem, h->stream>>>(d_objs, d_tasks, (int)sorted.size(), d_counter, omega, omega_stride,
-                                                    s_sigma, s_mu, gR, gI, g_omega, d_gmu, R, I, h->d_status, n_w, d_ws,
-                                                    ws_elems);
+  if (e == cudaSuccess && pencil) {
+    e = cudaMemcpyAsync(d_recs, recs.data(), n_obj * sizeof(RomDev), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = pencil_tables_prepare(h, pt, d_recs, omega, omega_stride, s_sigma, s_mu);
+    if (e == cudaSuccess) e = pencil_tables_route(h, pt);
+    if (e == cudaSuccess)
+      e = launch_pencil_vjp(d_recs, pt.d_pens, pt.d_table_pen, pt.d_counters + 2, omega, omega_stride, s_sigma, s_mu,
+                            gR, gI, g_omega, d_gmu, R, I, h->d_status, n_w, pt.pen_grid, pt.pen_smem, h->stream);
+    if (e == cudaSuccess) {
+      ++h->launches;
+      sweep_vjp_kernel<true><<<grid, kT, smem, h->stream>>>(d_objs, pt.d_table_lu, -1, pt.d_counters + 3, omega,
+                                                            omega_stride, s_sigma, s_mu, gR, gI, g_omega, d_gmu, R, I,
+                                                            h->d_status, n_w, d_ws, ws_elems);
+      e = cudaGetLastError();
+    }
+  } else if (e == cudaSuccess) {
+    sweep_vjp_kernel<false><<<grid, kT, smem, h->stream>>>(d_objs, d_tasks, (int)sorted.size(), d_counter, omega,
+                                                           omega_stride, s_sigma, s_mu, gR, gI, g_omega, d_gmu, R, I,
+                                                           h->d_status, n_w, d_ws, ws_elems);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && (g_ssigma || g_smu)) {
@@ -438,6 +501,7 @@ extern "C" mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int
     ++h->launches;
   }
   cudaFreeAsync(blk, h->stream);
+  pencil_tables_destroy(&pt, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_sweep_vjp: launch");
   ++h->launches;
   return MROM_OK;

@@ -17,11 +17,14 @@ def mrom():
     return m
 
 
-def test_vjp_matches_oracle_tangents(mrom):
+@pytest.mark.parametrize("lu", [False, True], ids=["pencil", "lu"])
+def test_vjp_matches_oracle_tangents(mrom, lu):
+    """Both routes: the adjoint in the eigenbasis of each object's pencil (default) and by LU."""
     import torch
     from oracle import grads
     from workloads import log_omegas, reduced_object
     h = mrom.Handle(0)
+    h.set_solver(lu=lu)
     rs = [5, 24, 61, 96]
     objs = [reduced_object(20230711, 500 + k, r) for k, r in enumerate(rs)]
     roms = [mrom.ReducedObject.from_workload(h, o, with_cert=False) for o in objs]
@@ -120,3 +123,44 @@ def test_least_squares_fit_of_material_scales(mrom):
     res = minimize(fun, np.zeros(2), jac=True, method="L-BFGS-B", options={"maxiter": 200, "gtol": 1e-12, "ftol": 1e-16})
     fit = np.exp(res.x)
     assert np.allclose(fit, true_s, rtol=1e-5), (fit, true_s)
+
+
+def test_vjp_routes_agree_with_regularisation_and_without_scales(mrom):
+    """An object with Me = U^H (eps M) U (V^H Me V enters R and the adjoint source) and calls
+    without s_mu / g_smu: the pencil route reproduces the LU route (itself pinned to the oracle)."""
+    import torch
+    from workloads import log_omegas, reduced_object
+    obj = reduced_object(77, 3, 40)
+    rng = np.random.default_rng(11)
+    Z = (rng.standard_normal((40, 40)) + 1j * rng.standard_normal((40, 40))) * 1e-3
+    Me = Z @ Z.conj().T
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    n_w = 45
+    wo = t(log_omegas(1e1, 1e8, n_w))
+    gR = t(rng.standard_normal((1, n_w, 3, 3)))
+    gI = t(rng.standard_normal((1, n_w, 3, 3)))
+    out = []
+    for lu in (False, True):
+        h = mrom.Handle(0)
+        h.set_solver(lu=lu)
+        ro = mrom.ReducedObject(h, 40, t(obj.K), t(obj.C), t(obj.B), obj.c00, K_in=t(obj.K_in), Me=t(Me))
+        res = []
+        for scales in (True, False):
+            g_w = torch.empty((1, n_w), dtype=torch.float64, device="cuda")
+            g_s = torch.empty(1, dtype=torch.float64, device="cuda")
+            g_m = torch.empty(1, dtype=torch.float64, device="cuda") if scales else None
+            R = torch.empty((1, n_w, 3, 3), dtype=torch.float64, device="cuda")
+            I = torch.empty_like(R)
+            kw = dict(s_sigma=t(np.array([1.3])), s_mu=t(np.array([7.0]))) if scales else {}
+            mrom.mrom_sweep_vjp(h, [ro], wo, n_w, gR, gI, g_w, g_ssigma=g_s, g_smu=g_m, R=R, I=I, **kw)
+            h.synchronize()
+            res.append([x.cpu().numpy() for x in (g_w, g_s, R, I)] + ([g_m.cpu().numpy()] if scales else []))
+        out.append(res)
+    for a, b in zip(out[0], out[1]):
+        gw_p, gw_l = a[0], b[0]
+        assert np.abs(gw_p - gw_l).max() <= 1e-8 * np.abs(gw_l).max()
+        assert np.allclose(a[1], b[1], rtol=1e-8)
+        assert np.abs(a[2] - b[2]).max() <= 1e-10 * np.abs(b[2]).max()
+        assert np.abs(a[3] - b[3]).max() <= 1e-9 * np.abs(b[3]).max()
+        if len(a) > 4:
+            assert np.allclose(a[4], b[4], rtol=1e-8)

@@ -43,6 +43,7 @@ def test_noalloc_sweep_matches_sweep_on_two_calls(mrom):
     import torch
     from workloads import log_omegas, reduced_object
     h = mrom.Handle(0)
+    h.set_solver(lu=True)  # the allocation-free sweep is the LU route; compare with the same route
     # sizes on both sides of the shared-memory limit, so the workspace part of the array is used
     batches = [
         ([reduced_object(31337, k, r) for k, r in enumerate([8, 40, 64, 90, 96])], log_omegas(1e1, 1e8, 120)),
