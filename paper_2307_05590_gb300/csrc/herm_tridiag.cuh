@@ -202,6 +202,15 @@ __device__ __forceinline__ void ql_givens(double f, double g, double& c, double&
   }
 }
 
+// Deflation test of QL: e_m is negligible when it is below eps times the neighbouring diagonal
+// entries (relative) or below eps ||T|| (absolute; a backward perturbation of the same order
+// as the Householder reduction's, and what lets clusters of eigenvalues at the rounding level
+// of ||T|| deflate).
+__device__ __forceinline__ bool ql_split(double e, double d0, double d1, double tn) {
+  const double a = fabs(e);
+  return a <= DBL_EPSILON * (fabs(d0) + fabs(d1)) || a <= DBL_EPSILON * tn;
+}
+
 // Implicit QL with Wilkinson-type shifts on the real symmetric tridiagonal (sd, se), se[i]
 // coupling i and i+1 (shared arrays).  Thread 0 chases one bulge at a time and records its
 // rotations in rc, rs (shared, r entries); then every thread applies them to the rows of Z
@@ -214,6 +223,9 @@ __device__ bool ql_single(double* sd, double* se, int r, double2* Z, double* rc,
                           int max_iter) {
   const int tid = threadIdx.x;
   int l = 0, iter = 0;  // thread 0's state
+  double tn = 0.0;      // max_i |d_i| + |e_i| (thread 0)
+  if (tid == 0)
+    for (int i = 0; i < r; ++i) tn = fmax(tn, fabs(sd[i]) + fabs(se[i]));
   for (;;) {
     if (tid == 0) {
       flags[0] = 0;  // rotations of this sweep
@@ -225,7 +237,7 @@ __device__ bool ql_single(double* sd, double* se, int r, double2* Z, double* rc,
           break;
         }
         int m = l;
-        while (m < r - 1 && fabs(se[m]) > DBL_EPSILON * (fabs(sd[m]) + fabs(sd[m + 1]))) ++m;
+        while (m < r - 1 && !ql_split(se[m], sd[m], sd[m + 1], tn)) ++m;
         if (m == l) {
           ++l;
           iter = 0;

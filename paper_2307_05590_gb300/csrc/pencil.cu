@@ -278,13 +278,15 @@ pencil_ql_kernel(const int* __restrict__ order, int n_elig, const RomDev* __rest
     d[k * lpw] = pd.lam[k];
     e[k * lpw] = ps.e[k];
   }
+  double tn = 0.0;  // max_i |d_i| + |e_i|
+  for (int k = 0; k < r; ++k) tn = fmax(tn, fabs(d[k * lpw]) + fabs(e[k * lpw]));
   int nsw = 0, nrot_total = 0;
   bool fail = false;
   for (int l = 0; l < r && !fail; ++l) {
     int iter = 0;
     for (;;) {
       int m = l;
-      while (m < r - 1 && fabs(e[m * lpw]) > DBL_EPSILON * (fabs(d[m * lpw]) + fabs(d[(m + 1) * lpw]))) ++m;
+      while (m < r - 1 && !hq::ql_split(e[m * lpw], d[m * lpw], d[(m + 1) * lpw], tn)) ++m;
       if (m == l) break;
       if (++iter > kQlMaxIter || nsw >= ps.cap_sw || nrot_total + (m - l) > ps.cap_rot) {
         fail = true;
