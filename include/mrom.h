@@ -352,6 +352,18 @@ mrom_status mrom_plan_timing(mrom_plan plan, int32_t enable, float* stage_ms);
  * configuration index. */
 mrom_status mrom_tune(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int32_t n_w, int32_t* chosen);
 
+/* ------------------------------------------------- rotation invariants */
+
+/* Rotation-invariant features of a signature (Sect. 1: under a rotation Q of
+ * the object each coefficient matrix becomes Q M Q^T, so its eigenvalues do
+ * not depend on the orientation; dictionary matching compares the eigenvalues
+ * of R~ = N0 + R and of I per frequency).  M: n real 3 x 3 matrices (device,
+ * [n][3][3] row-major, e.g. the R or I output of mrom_sweep); eig: n x 3
+ * eigenvalues of their symmetric parts in ascending order (device).  Cyclic
+ * Jacobi per matrix: absolute accuracy a few eps ||M||, repeated eigenvalues
+ * included.  Asynchronous; MROM_EINVAL for n < 0 or null arrays with n > 0. */
+mrom_status mrom_invariants(mrom_handle h, const double* M, int64_t n, double* eig);
+
 /* ------------------------------------------------------- allocation-free */
 
 /* mrom_sweep without any device allocation.  Some callers cannot allocate

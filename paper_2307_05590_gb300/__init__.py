@@ -23,7 +23,7 @@ __all__ = [
     "mrom_rom_from_reduced", "mrom_rom_free", "mrom_rom_rank", "mrom_sweep", "mrom_certificate",
     "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune", "mrom_sweep_noalloc",
     "FullOrder", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "MromSweep", "signature",
-    "mrom_sweep_mixed", "mrom_project_dirs",
+    "mrom_sweep_mixed", "mrom_project_dirs", "mrom_invariants",
 ]
 
 
@@ -436,6 +436,15 @@ def mrom_sweep_vjp(h: Handle, objs, omega, n_w: int, gR, gI, g_omega, *, g_ssigm
     _abi.check(lib().mrom_sweep_vjp(h.ptr, _rom_array(objs), len(objs), _ptr(omega), int(n_w), int(omega_stride),
                                     _ptr(s_sigma), _ptr(s_mu), _ptr(gR), _ptr(gI), _ptr(g_omega), _ptr(g_ssigma),
                                     _ptr(g_smu), _ptr(R), _ptr(I)), h.ptr)
+
+
+def mrom_invariants(h: Handle, M, eig) -> None:
+    """Eigenvalues (ascending) of the symmetric parts of the 3 x 3 matrices M (device,
+    [..., 3, 3]) into eig (device, [..., 3]): the rotation invariants of Sect. 1."""
+    n = M.numel() // 9
+    if eig.numel() != 3 * n:
+        raise ValueError("eig must hold 3 values per 3 x 3 matrix")
+    _abi.check(lib().mrom_invariants(h.ptr, _ptr(M), int(n), _ptr(eig)), h.ptr)
 
 
 def _sweep_values(h, objs, omega, s_sigma, s_mu):

@@ -18,7 +18,7 @@ EXPORTS = [
     "mrom_certificate", "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune",
     "mrom_sweep_noalloc", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "mrom_sweep_mixed",
     "mrom_project_dirs", "mrom_set_projection_precision", "mrom_set_solver", "mrom_plan_solver_counts",
-    "mrom_plan_timing", "mrom_rom_from_reduced_batch",
+    "mrom_plan_timing", "mrom_rom_from_reduced_batch", "mrom_invariants",
 ]
 
 
@@ -91,6 +91,7 @@ def _declare(L):
         "mrom_set_solver": (ctypes.c_int, [vp, ctypes.c_int]),
         "mrom_plan_timing": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
         "mrom_rom_from_reduced_batch": (ctypes.c_int, [vp, ctypes.c_int32, vp, vp]),
+        "mrom_invariants": (ctypes.c_int, [vp, vp, i64, vp]),
         "mrom_plan_solver_counts": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "mrom_rom_from_reduced": (ctypes.c_int, [vp, ctypes.POINTER(mrom_reduced_desc), ctypes.POINTER(vp)]),
         "mrom_rom_rank": (i32, [vp]),

@@ -99,6 +99,27 @@ def test_gpu_tsvd_matches_oracle(mrom, case):
     assert max(errs) <= TOL, errs
 
 
+def test_gpu_tsvd_of_a_rank_deficient_snapshot_set(mrom, case):
+    """Repeated and linearly combined snapshot columns: the snapshot Gram has a cluster of
+    eigenvalues at its rounding level (the eigensolver must still converge, and the retained
+    subspace is the oracle's); outputs agree with the oracle's model to 1e-10."""
+    import torch
+    from workloads import log_omegas
+    from gpu_common import oracle_model_sweep, rel_errors
+    p, Dcols, X = case
+    extra = np.stack([Dcols[0], 2.0 * Dcols[3] - 0.5j * Dcols[7], Dcols[11], Dcols[5] + Dcols[6]])
+    Dd_host = np.ascontiguousarray(np.concatenate([Dcols, extra, Dcols[:6]]))  # 28 columns, rank 18
+    model, U, _ = _oracle_model(p, Dd_host, X, 1e-6)
+    h = mrom.Handle(0)
+    fom = mrom.FullOrder.from_fit(p, X=X)
+    rom, sig, r = mrom.mrom_project(h, fom, torch.as_tensor(Dd_host, device="cuda"), tol_sigma=1e-6)
+    assert r == U.shape[1]
+    wo = log_omegas(1e1, 1e5, 48) * 1.03
+    Rg, Ig, Dg = _sweep(mrom, h, [rom], wo)
+    errs = rel_errors(Rg[0], Ig[0], Dg[0], *oracle_model_sweep(model, wo))
+    assert max(errs) <= TOL, errs
+
+
 def test_project_rejects_bad_input(mrom, case):
     import torch
     p, Dcols, X = case
