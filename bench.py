@@ -213,12 +213,57 @@ def measure_projection(m, h, n_grid: int = 96, n_s: int = 32):
     dt32 = time.perf_counter() - t0
     rom.close()
     h.set_projection_precision(False)
+    # the sweep of this object over 10^4 output frequencies (with certificate)
+    rom, _, _ = m.mrom_project(h, fom, Dd, tol_sigma=1e-6)
+    from workloads import log_omegas
+    om = torch.as_tensor(log_omegas(1e1, 1e8, 10000), device="cuda")
+    Rs = torch.empty((1, 10000, 3, 3), dtype=torch.float64, device="cuda")
+    Is, Ds = torch.empty_like(Rs), torch.empty_like(Rs)
+    m.mrom_sweep(h, [rom], om, 10000, Rs, Is, Ds)
+    h.synchronize()
+    t0 = time.perf_counter()
+    m.mrom_sweep(h, [rom], om, 10000, Rs, Is, Ds)
+    h.synchronize()
+    sweep_ms = 1e3 * (time.perf_counter() - t0)
+    rom.close()
     return {"workload": f"mrom_project: {n_grid}^3 FIT grid (N = {p.N}, {p.K.nnz} nnz), 3 x {n_s} snapshot columns, "
                         f"TOL_Sigma 1e-6 -> r = {r}, certificate Gram with diagonal X",
             "seconds": dt, "r": r, "flops": fl, "achieved_tflops": fl / dt / 1e12,
             "bound": "alu", "fp64_frac": fl / dt / 1e12 / (SM_COUNT_NOMINAL * DFMA_PER_CLK_PER_SM * 2 * 2.07e9 / 1e12),
             "hbm_gb_moved_min": (3 * n_s * p.N * 16 * 2 + p.N * r * 16 * 4 + p.K.nnz * 12) / 1e9,
-            "mixed_seconds": dt32, "mixed_r": r32}
+            "mixed_seconds": dt32, "mixed_r": r32, "sweep_10000_omega_ms": sweep_ms}
+
+
+def measure_c1_latency(m, h):
+    """Copper cube on the 16^3 FIT grid (N = 10,800): the paper's PODP with one TSVD per direction
+    from nine full-order snapshots in [1e1, 1e5] (computed on the host by sparse LU: the off-line
+    inputs), then 100 outputs with the certificate.  Wall time of project + sweep (latency)."""
+    import torch
+    from workloads import CUBE_C1, fit_problem, full_order_snapshots, log_omegas
+    p = fit_problem(16, CUBE_C1)
+    D = full_order_snapshots(p, log_omegas(1e1, 1e5, 9))
+    X = p.eps * p.M + 10.0 * p.C
+    fom = m.FullOrder.from_fit(p, X=X)
+    cols = torch.as_tensor(np.ascontiguousarray(np.concatenate([D[i].T for i in range(3)])), device="cuda")
+    om = torch.as_tensor(log_omegas(1e1, 1e5, 100), device="cuda")
+    R = torch.empty((1, 100, 3, 3), dtype=torch.float64, device="cuda")
+    I = torch.empty_like(R)
+    Dl = torch.empty_like(R)
+    times = []
+    for _ in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        obj, _, rd = m.mrom_project_dirs(h, fom, cols, tol_sigma=1e-6)
+        t1 = time.perf_counter()
+        m.mrom_sweep(h, [obj], om, 100, R, I, Dl)
+        h.synchronize()
+        t2 = time.perf_counter()
+        obj.close()
+        times.append((t1 - t0, t2 - t1))
+    tp, ts = np.median(np.array(times[1:]), axis=0)
+    return {"workload": "c1: 16^3 copper cube (N = 10800), 9 snapshots in [1e1, 1e5], one TSVD per direction, "
+                        "100 outputs with certificate", "r_dirs": list(rd), "project_ms": 1e3 * tp,
+            "sweep_ms": 1e3 * ts, "total_ms": 1e3 * (tp + ts)}
 
 
 def measure_adaptive(m, h, n_grid: int = 128, ns0: int = 9, n_star: int = 2, max_k: int = 28, n_out: int = 4096):
@@ -423,6 +468,21 @@ def main():
 
     n_pen, n_lu = plan.solver_counts()
 
+    # ---- rotation invariants (eigenvalues of R~ and I per frequency) of the step's outputs
+    eigs = torch.empty((args.n_obj, args.n_w, 3), dtype=torch.float64, device=dev)
+    m.mrom_invariants(h, R, eigs)
+    h.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    m.mrom_invariants(h, R, eigs)
+    m.mrom_invariants(h, I, eigs)
+    e1.record(stream)
+    h.synchronize()
+    ms_inv = e0.elapsed_time(e1)
+    inv = {"ms_for_R_and_I": ms_inv, "matrices": 2 * args.n_obj * args.n_w,
+           "achieved_gbs": 2 * args.n_obj * args.n_w * (72 + 24) / (ms_inv * 1e-3) / 1e9}
+    del eigs
+
     # ---- the same step with every object on the LU route (float64 elimination)
     lu_route = None
     if args.lu_route:
@@ -472,6 +532,7 @@ def main():
         del Rm, Im, Dm
 
     proj = measure_projection(m, h) if args.projection else None
+    c1 = measure_c1_latency(m, h) if args.projection else None
 
     # ---- gradients (adjoint sweep) on the same dictionary: dL/domega, dL/ds_sigma, dL/ds_mu for
     # per-object scales s_sigma ~ U(0.5, 2), s_mu ~ U(1, 64) and random cotangents of R and I
@@ -582,7 +643,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "wall_s_timed": wall, "per_launch_ms": per_launch_ms, "sweep_config": sweep_cfg,
             "stages": stage_info, "lu_route": lu_route, "mixed_precision": mixed, "projection": proj,
-            "gradients": grads,
+            "gradients": grads, "invariants": inv, "c1_latency": c1,
         }
         print(json.dumps(line), flush=True)
     plan.close()
