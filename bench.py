@@ -368,6 +368,8 @@ def main():
     ap.add_argument("--mixed", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--lu-route", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--gradients", action=argparse.BooleanOptionalAction, default=True)
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="N > 1: every rank its own dictionary (weak) or one dictionary split by cost (strong)")
     ap.add_argument("--projection-only", action="store_true",
                     help="time mrom_project alone (float64 and complex64 products) and print its record")
     ap.add_argument("--projection-grid", type=int, default=96)
@@ -413,7 +415,14 @@ def main():
         h.close()
         return
 
-    objs = dictionary(args.n_obj, 20230711 + rank)
+    from paper_2307_05590_gb300 import shard
+    if args.scaling == "weak" or world == 1:
+        objs = dictionary(args.n_obj, 20230711 + rank)   # every rank its own dictionary
+    else:                                                 # one dictionary split by cost
+        full = dictionary(args.n_obj, 20230711)
+        part = shard.balanced_split(shard.sweep_cost([o.r for o in full], args.n_w), world)[rank]
+        objs = [full[k] for k in part]
+        args.n_obj = len(objs)
     wo = log_omegas(1e1, 1e8, args.n_w)
     rs = np.array([o.r for o in objs])
     flops_lu = float(sum(flops_per_eval(r) for r in rs)) * args.n_w
@@ -459,11 +468,8 @@ def main():
     clk = clocks.stop(local_rank)
     per_launch_ms = [a.elapsed_time(b) for a, b in ev]
     dev_ms = ev[0][0].elapsed_time(ev[-1][1])
-    t_step = torch.tensor([dev_ms / args.steps], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_step, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t_step.item())
-    evals_step = args.n_obj * args.n_w * world
+    ms_per_step = shard.max_over_ranks(dev_ms / args.steps, device=dev)   # the slowest rank
+    evals_step = int(shard.sum_over_ranks(args.n_obj * args.n_w, device=dev))
     value = evals_step / (ms_per_step * 1e-3)
 
     n_pen, n_lu = plan.solver_counts()
@@ -638,7 +644,7 @@ def main():
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": args.scaling,
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "wall_s_timed": wall, "per_launch_ms": per_launch_ms, "sweep_config": sweep_cfg,
