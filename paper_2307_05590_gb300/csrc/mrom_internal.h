@@ -201,7 +201,6 @@ cudaError_t launch_sweep_fp64_routed(int cfg, const RomDev* objs, const SweepTas
 
 // Pencil route (pencil.cu).
 size_t pencil_sweep_smem_bytes(int r, int F);
-int pencil_threads();
 // Tables for objs (host records; the device copy is passed to the kernels).  gram: transform
 // the certificate blocks of objects that have them; kin: transform K_in (permeability
 // gradient).  order_lu / lu_info: every object in the LU kernel's cost order with its task

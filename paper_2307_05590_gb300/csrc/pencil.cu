@@ -999,8 +999,6 @@ size_t pencil_sweep_smem_bytes(int r, int F) {
   return z > red ? z : red;
 }
 
-int pencil_threads() { return kPT; }
-
 size_t pencil_finish_smem_bytes(int rmax) { return (size_t)rmax * (size_t)(rmax | 1) * sizeof(double); }
 
 namespace {
