@@ -45,9 +45,9 @@ SM_COUNT_NOMINAL = 152
 DFMA_PER_CLK_PER_SM = 2           # measured: GB300 DFMA rate saturates at 4 flop/clk/SM
 FP64_MEASURED_TFLOPS = 1.189      # DFMA microbenchmark on this machine's GB300 (1.96 GHz)
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one pencil_sweep_kernel launch on
-# this workload, from a one-pass ncu capture of the current kernel (99,694,080 + 371,092,736 bytes);
+# this workload, from a one-pass ncu capture of the current kernel (98,763,264 + 371,965,440 bytes);
 # None once the kernel changes until it is captured again
-SWEEP_DRAM_BYTES_PER_LAUNCH = 470786816
+SWEEP_DRAM_BYTES_PER_LAUNCH = 470728704
 
 
 def flops_per_eval(r: int, cert: bool = True) -> float:
@@ -76,16 +76,17 @@ def pencil_sweep_flops(r: int, cert: bool = True) -> float:
     """FP64 flops of one (object, frequency) evaluation in the pencil sweep kernel.
 
       z_kj = u_k beta_kj, u_k = i w / (lambda_k - i w)         26 per k
-      O(r) terms per row a (Lambda, identity, beta, gs forms)   162 per row (126 without certificate)
+      R and I: (-lambda Re u, Re u) x Re(beta_i^* beta_j)      25 per k
+      certificate source terms X_ij and form sums U_ij          90 per row
       certificate form: G~_ab(w) (4 FMA) and three complex
         multiply-adds for every b < a                          32 per pair
-      diagonal b = a (halved)                                  38 per row
+      diagonal b = a (stored halved)                           32 per row
       outputs R, I, Delta                                      225
     """
     r = int(r)
     if not cert:
-        return float(26 * r + 126 * r + 100)
-    return float(16 * r * (r - 1) + 38 * r + 162 * r + 26 * r + 225)
+        return float(51 * r + 100)
+    return float(16 * r * (r - 1) + 51 * r + 90 * r + 32 * r + 225)
 
 
 def pencil_prep_flops(r: int) -> float:

@@ -49,11 +49,13 @@ struct RomDev {
 // preparation kernel of every sweep: eigenvalues lam (r), beta = V^H B (r x 3),
 // gsh[k][q] = (gs_q V)[k] for the certificate rows of G (r x 6, or null), the transformed
 // Gram blocks V^H G_X V for X = KK, CC, S interleaved per entry of the packed lower
-// triangle (3 r (r+1)/2, or null) and V^H Me V (packed lower, or null).  F: frequency
+// triangle with the diagonal halved (3 r (r+1)/2, or null) and V^H Me V (packed lower, or
+// null).  F: frequency
 // groups of 32 per sweep task.
 struct PencilDev {
   double* lam;
   double2* beta;
+  double* bbr;  // r x 6: Re(beta_ki^* beta_kj), (i, j) = 00 01 02 11 12 22
   double2* gsh;
   double2* Gh;
   double2* Eh;

@@ -421,6 +421,13 @@ pencil_finish_kernel(const RomDev* __restrict__ objs, const PencilDev* __restric
       for (int a = 0; a < r; ++a) acc = cmacc(acc, W1[a * r + k], ob.B[a * 3 + j]);
       pd.beta[idx] = acc;  // beta[k][j] = (V^H B)[k][j]
     }
+    __syncthreads();
+    for (int idx = tid; idx < 6 * r; idx += kPT) {  // bbr[k][(i,j)] = Re(beta_ki^* beta_kj), i <= j
+      const int k = idx / 6, q = idx - (idx / 6) * 6;
+      const int i = q < 3 ? 0 : (q < 5 ? 1 : 2), j = q < 3 ? q : (q < 5 ? q - 2 : 2);
+      const double2 bi = pd.beta[k * 3 + i], bj = pd.beta[k * 3 + j];
+      pd.bbr[idx] = fma(bi.x, bj.x, bi.y * bj.y);
+    }
     if (pd.gsh) {
       for (int idx = tid; idx < 6 * r; idx += kPT) {
         const int k = idx / 6, q = idx - (idx / 6) * 6;
@@ -453,8 +460,8 @@ pencil_finish_kernel(const RomDev* __restrict__ objs, const PencilDev* __restric
         tri_rc(e, a, b);
         double2 acc = make_double2(0.0, 0.0);
         for (int c = 0; c < r; ++c) acc = cmacc(acc, W1[c * r + a], W0[c * r + b]);
-        if (gram)
-          pd.Gh[(size_t)e * 3 + x] = acc;
+        if (gram)  // the sweep's Hermitian forms use the diagonal halved
+          pd.Gh[(size_t)e * 3 + x] = a == b ? make_double2(0.5 * acc.x, 0.5 * acc.y) : acc;
         else
           dst[e] = acc;
       }
@@ -512,14 +519,14 @@ __device__ __forceinline__ SweepTask table_task(const SweepTask* __restrict__ ta
 
 // ------------------------------------------------------------------ sweep
 
-constexpr int kNQ = 48;  // partial sums per lane: U 0..8, X 9..17, B 18..26, E 27..35, R 36..41, I 42..47
+constexpr int kNQ = 39;  // partial sums per lane: U 0..8, X 9..17, E 18..26, R 27..32, I 33..38
 
 // Row pairs (a, r-1-a) of one warp, lane = one frequency: accumulates, over its rows a,
-//   U_ij = Re(z_ai^* y_aj), y = (L + D/2) G~(w) z   (certificate form, halved)
+//   U_ij = Re(z_ai^* y_aj), y = (L + D/2) G~(w) z   (certificate form, halved; the diagonal
+//          of the stored blocks is already halved)
 //   X_ij = Re((i w gsK_ia + w^2 gsC_ia) z_aj)
-//   B_ij = Re(beta_ai^* z_aj)
 //   E_ij = Re(z_ai^* ye_aj), ye = (L + D/2) (V^H Me V) z
-//   R_ij = lambda_a Re(z_ai^* z_aj), I_ij = Re(z_ai^* z_aj)   (i <= j)
+// (R and I need only O(1) per row and frequency; the z phase accumulates them.)
 template <bool CERT, bool HAS_E>
 __device__ __forceinline__ void pencil_rows(const PencilDev& pd, int r, const double2* __restrict__ zg, double w,
                                             int q0, int wpg, double (&acc)[kNQ]) {
@@ -532,24 +539,6 @@ __device__ __forceinline__ void pencil_rows(const PencilDev& pd, int r, const do
       double2 za[3];
 #pragma unroll
       for (int j = 0; j < 3; ++j) za[j] = zg[(a * 3 + j) * 32];
-      const double lam = pd.lam[a];
-      {
-        int q = 0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = i; j < 3; ++j, ++q) {
-            const double v = fma(za[i].x, za[j].x, za[i].y * za[j].y);
-            acc[36 + q] = fma(lam, v, acc[36 + q]);
-            acc[42 + q] += v;
-          }
-      }
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const double2 b = pd.beta[a * 3 + i];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) acc[18 + i * 3 + j] = fma(b.x, za[j].x, fma(b.y, za[j].y, acc[18 + i * 3 + j]));
-      }
       if constexpr (CERT) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -584,29 +573,25 @@ __device__ __forceinline__ void pencil_rows(const PencilDev& pd, int r, const do
             for (int j = 0; j < 3; ++j) ye[j] = cmac(ye[j], e, zb[j]);
           }
         }
-        // diagonal term, halved
-        double2 zh[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) zh[j] = make_double2(0.5 * za[j].x, 0.5 * za[j].y);
-        if constexpr (CERT) {
+        if constexpr (CERT) {  // diagonal term (stored halved)
           const double2 kk = gh[3 * a], cc = gh[3 * a + 1], sk = gh[3 * a + 2];
           const double2 gt = make_double2(fma(w2, cc.x, fma(-w, sk.y, kk.x)), fma(w2, cc.y, fma(w, sk.x, kk.y)));
 #pragma unroll
-          for (int j = 0; j < 3; ++j) y[j] = cmac(y[j], gt, zh[j]);
+          for (int j = 0; j < 3; ++j) y[j] = cmac(y[j], gt, za[j]);
 #pragma unroll
           for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j) acc[i * 3 + j] = fma(za[i].x, y[j].x, fma(za[i].y, y[j].y, acc[i * 3 + j]));
         }
-        if constexpr (HAS_E) {
+        if constexpr (HAS_E) {  // diagonal term, halved here
           const double2 e = eh[a];
 #pragma unroll
-          for (int j = 0; j < 3; ++j) ye[j] = cmac(ye[j], e, zh[j]);
+          for (int j = 0; j < 3; ++j) ye[j] = cmac(ye[j], make_double2(0.5 * e.x, 0.5 * e.y), za[j]);
 #pragma unroll
           for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j)
-              acc[27 + i * 3 + j] = fma(za[i].x, ye[j].x, fma(za[i].y, ye[j].y, acc[27 + i * 3 + j]));
+              acc[18 + i * 3 + j] = fma(za[i].x, ye[j].x, fma(za[i].y, ye[j].y, acc[18 + i * 3 + j]));
         }
       }
     }
@@ -645,31 +630,36 @@ __device__ __forceinline__ void pencil_task(const RomDev& ob, const PencilDev& p
     Ws[s] = w;
   }
   __syncthreads();
-  for (int idx = tid; idx < r * 32 * F; idx += kPT) {
-    const int g = idx / (r * 32);
-    const int rem = idx - g * r * 32;
-    const int k = rem >> 5, ln = rem & 31;
-    const double w = Ws[g * 32 + ln];
+  // Warp w serves group g = w % F and rows k = w / F (mod 8 / F).  Per row, with
+  // bb_ij = Re(beta_ki^* beta_kj): Re(z_i^H Lambda z_j) gets lambda |u|^2 bb = -lambda Re(u) bb and
+  // Re(z_i^H z_j + beta_i^H z_j + beta_j^H z_i) gets (|u|^2 + 2 Re u) bb = Re(u) bb.
+  double acc[kNQ];
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+  const int g = warp % F;
+  const double wl = Ws[g * 32 + lane];
+  for (int k = warp / F; k < r; k += wpg) {
     const double lam = pd.lam[k];
-    const double den = 1.0 / fma(lam, lam, w * w);
-    const double2 u = make_double2(-w * w * den, w * lam * den);
-    double2* zk = zs + ((size_t)(g * r + k) * 3) * 32 + ln;
+    const double den = 1.0 / fma(lam, lam, wl * wl);
+    const double2 u = make_double2(-wl * wl * den, wl * lam * den);
+    double2* zk = zs + ((size_t)(g * r + k) * 3) * 32 + lane;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const double2 b = pd.beta[k * 3 + j];
       zk[j * 32] = make_double2(fma(u.x, b.x, -u.y * b.y), fma(u.x, b.y, u.y * b.x));
     }
+    const double wr = -lam * u.x;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const double bb = pd.bbr[k * 6 + q];
+      acc[27 + q] = fma(wr, bb, acc[27 + q]);
+      acc[33 + q] = fma(u.x, bb, acc[33 + q]);
+    }
   }
   __syncthreads();
 
   // ---- row pairs
-  double acc[kNQ];
-#pragma unroll
-  for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
-  {
-    const int g = warp % F;
-    pencil_rows<CERT, HAS_E>(pd, r, zs + (size_t)g * r * 3 * 32 + lane, Ws[g * 32 + lane], warp / F, wpg, acc);
-  }
+  pencil_rows<CERT, HAS_E>(pd, r, zs + (size_t)g * r * 3 * 32 + lane, wl, warp / F, wpg, acc);
   __syncthreads();  // z is no longer read: its space takes the partial sums
   {
     double* rb = rbuf + (size_t)warp * kNQ * 32 + lane;
@@ -698,12 +688,11 @@ __device__ __forceinline__ void pencil_task(const RomDev& ob, const PencilDev& p
     const double wv = Ws[s];
     const size_t o = ((size_t)task.obj * n_w + task.w0 + s) * 9 + ij;
     if (Rout) {
-      double kf = t(36 + sym);
-      if constexpr (HAS_E) kf -= t(27 + i * 3 + j) + t(27 + j * 3 + i);
+      double kf = t(27 + sym);
+      if constexpr (HAS_E) kf -= t(18 + i * 3 + j) + t(18 + j * 3 + i);
       Rout[o] = fma(-0.25 * ob.alpha3, kf, ob.N0[ij]);
     }
-    if (Iout)
-      Iout[o] = 0.25 * ob.alpha3 * wv * (ob.c00[ij] + t(42 + sym) + t(18 + i * 3 + j) + t(18 + j * 3 + i));
+    if (Iout) Iout[o] = 0.25 * ob.alpha3 * wv * (ob.c00[ij] + t(33 + sym));
     if (Dout) {
       if constexpr (CERT) {
         const double ww = wv * wv;
@@ -1122,7 +1111,7 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
     rmax = std::max(rmax, r);
     off[o] = data_elems;
     const size_t tri = (size_t)r * (r + 1) / 2;
-    data_elems += (size_t)(r + 1) / 2 + 3 * (size_t)r;                    // lam (in complex slots), beta
+    data_elems += (size_t)(r + 1) / 2 + 6 * (size_t)r;                    // lam (in complex slots), beta, bbr
     if (gram && objs[o].has_cert) data_elems += 6 * (size_t)r + 3 * tri;  // gsh, Gh
     if (objs[o].Me) data_elems += tri;                                    // Eh
     if (kin && objs[o].Kin) data_elems += tri;                            // Fh
@@ -1169,6 +1158,7 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
     double2* q = data + off[o];
     pens[o].lam = reinterpret_cast<double*>(q); q += (r + 1) / 2;
     pens[o].beta = q; q += 3 * (size_t)r;
+    pens[o].bbr = reinterpret_cast<double*>(q); q += 3 * (size_t)r;
     if (gram && objs[o].has_cert) {
       pens[o].gsh = q; q += 6 * (size_t)r;
       pens[o].Gh = q; q += 3 * tri;
