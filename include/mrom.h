@@ -178,7 +178,8 @@ typedef struct {
  * and Galerkin projection (Sects. 4.2-4.3), producing a reduced object for
  * mrom_sweep.  D holds n_cols complex128 snapshot columns of length n, column c
  * at D + c * ldd (device, ldd >= n, n_cols <= MROM_MAX_SNAPSHOTS).  The SVD is
- * computed from the Hermitian Gram D^H D with a Jacobi eigensolver, so singular
+ * computed from the Hermitian Gram D^H D (Householder tridiagonalisation and
+ * implicit QL), so singular
  * values below about 1e-8 s_1 are not resolved; the retained rank is
  * r = #{s_k / s_1 >= tol_sigma}, capped at r_max (if > 0) and MROM_MAX_R.
  * basis_in (device, n x r_in complex128 row-major, or NULL) skips the SVD and

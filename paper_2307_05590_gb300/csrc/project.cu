@@ -1,14 +1,16 @@
 // Off-line stage on the GPU: snapshot TSVD and Galerkin projection (Sects. 4.1-4.3).
 //
 //   G_D = D^H D                                  tall Gram (split over rows)
-//   G_D = V Lambda V^H                           Hermitian Jacobi eigensolver (one CTA)
+//   G_D = V Lambda V^H                           Householder tridiagonalisation + implicit QL (one CTA)
 //   s_k = sqrt(lambda_k), r = #{s_k / s_1 >= TOL_Sigma} (capped)     (Eq. (15))
 //   U   = D V_r diag(1/s_r)                      left singular vectors (Eq. (14))
 //   Y   = K U                                    CSR SpMM
 //   K_r = U^H Y, C_r = U^H diag(c) U, Me = U^H diag(eps m) U,
 //   b_i = U^H (c o_i), c00 = o^T diag(c) o                             (Eqs. (17)-(19))
 //   G   = Phi^H diag(1/x) Phi, Phi = [c o_i | Y + eps m U | c U]      (Lemma 4.2)
-// Everything is float64 / complex128.  These kernels are FP64-pipe bound on GB300
+// Everything is float64 / complex128, except that the mixed projection mode forms K U and the
+// products K_r, C_r, eps M_r and b in complex64 (TSVD and certificate Gram stay float64).
+// The float64 kernels are FP64-pipe bound on GB300
 // (the snapshot and basis streams are re-read from L2), so they are written for
 // full FP64 utilisation with register tiles rather than for HBM streaming.
 #include "mrom_internal.h"
@@ -550,7 +552,7 @@ using namespace mrom;
 namespace mrom {
 namespace {
 
-// Snapshot Gram, Jacobi eigensolver and truncation for the m columns of D (column c at
+// Snapshot Gram, eigensolver and truncation for the m columns of D (column c at
 // D + c * ldd): returns the rank r, the singular values (host) and W = V_r diag(1/s_r)
 // (host, m x r, row-major) such that U = D W.
 mrom_status gram_eig(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, int m, double tol_sigma, int r_cap,
