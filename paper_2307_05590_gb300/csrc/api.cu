@@ -92,6 +92,7 @@ extern "C" mrom_status mrom_synchronize(mrom_handle h) {
     if (st & kStatusBadOmega) return fail(h, MROM_EINVAL, "a frequency was non-finite or <= 0");
     if (st & kStatusSingular) return fail(h, MROM_ESINGULAR, "zero or non-finite pivot in a reduced solve");
     if (st & kStatusTimeout) return fail(h, MROM_ETIMEOUT, "a bounded device wait gave up");
+    if (st & kStatusConfig) return fail(h, MROM_ECUDA, "internal: a kernel launch had too little shared memory");
   }
   mrom_status p = h->pending;
   h->pending = MROM_OK;

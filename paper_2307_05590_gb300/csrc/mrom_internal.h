@@ -15,6 +15,7 @@ enum : int {
   kStatusBadOmega = 1,    // non-finite or non-positive frequency
   kStatusSingular = 2,    // zero or non-finite pivot
   kStatusTimeout = 4,     // a bounded wait gave up
+  kStatusConfig = 8,      // a launch had less shared memory than a task needs (internal error)
 };
 
 // Per-object record read by the sweep kernels (device copy lives in a plan).
@@ -91,7 +92,7 @@ struct PencilTables {
   int n_pen = 0;                // eligible objects (0: no pencil route)
   int n_obj = 0, n_w = 0, rmax = 0;
   int prep_grid = 0, pen_grid = 0;
-  size_t prep_ws_elems = 0, pen_smem = 0;
+  size_t prep_ws_elems = 0, pen_smem = 0, pen_smem_vjp = 0;  // dynamic shared memory: sweep, adjoint
   void* block = nullptr;
   PencilDev* d_pens = nullptr;
   PencilScratch* d_scr = nullptr;

@@ -80,7 +80,7 @@ __device__ double block_min(double v, double* red) {
 //   W2: L^-1 (lower)
 // Output per object: the real tridiagonal D^H Q1^H H Q1 D (diagonal in lam, off-diagonal
 // in the scratch e) and W = L^-H Z; V = W Q2 once QL has diagonalised the tridiagonal.
-__global__ void __launch_bounds__(kPT)
+__global__ void __launch_bounds__(kPT, 2)
 pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__ pens,
                       const PencilScratch* __restrict__ scr, const int* __restrict__ order, int n_elig,
                       int* __restrict__ counter,
@@ -91,7 +91,7 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
   __shared__ double2 salpha[MROM_MAX_R], sph[MROM_MAX_R];
   __shared__ double red[kPW];
   __shared__ int s_task;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double2* W0 = ws + (size_t)blockIdx.x * ws_elems;
 
   for (;;) {
@@ -202,25 +202,27 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
     // ---- 3. X = L^-1 K' (W0)  and  4. H = X L^-H (W1, lower then mirrored)
     double hn = 0.0;
     if (ok) {
-      // X = L^-1 K', stored conjugate-transposed: W0[j][i] = conj(X[i][j])
-      for (int idx = tid; idx < rr; idx += kPT) {
-        const int i = idx / r, j = idx - (idx / r) * r;
-        double2 s = make_double2(0.0, 0.0);
-        for (int k = 0; k <= i; ++k) s = cmac(s, W2[i * r + k], W1[k * r + j]);
-        W0[j * r + i] = make_double2(s.x, -s.y);
+      // X = L^-1 K', stored conjugate-transposed: W0[j][i] = conj(X[i][j]); one warp per row i
+      // (one trip count per warp), lanes along j
+      for (int i = warp; i < r; i += kPW) {
+        for (int j = lane; j < r; j += 32) {
+          double2 s = make_double2(0.0, 0.0);
+          for (int k = 0; k <= i; ++k) s = cmac(s, W2[i * r + k], W1[k * r + j]);
+          W0[j * r + i] = make_double2(s.x, -s.y);
+        }
       }
       __syncthreads();
       // H[i][j] = sum_{k <= j} X[i][k] conj(L^-1[j][k]) = conj(sum_k W0[k][i] L^-1[j][k]) for
-      // i >= j, lanes along i (one trip count per warp), mirrored into the upper triangle
-      for (int idx = tid; idx < rr; idx += kPT) {
-        const int j = idx / r, i = idx - (idx / r) * r;
-        if (i < j) continue;
-        double2 s = make_double2(0.0, 0.0);
-        for (int k = 0; k <= j; ++k) s = cmac(s, W0[k * r + i], W2[j * r + k]);
-        if (i == j) s.y = 0.0;
-        W1[i * r + j] = make_double2(s.x, -s.y);
-        W1[j * r + i] = s;
-        hn += (i == j ? 1.0 : 2.0) * (s.x * s.x + s.y * s.y);
+      // i >= j: one warp per column j, lanes along i; mirrored into the upper triangle
+      for (int j = warp; j < r; j += kPW) {
+        for (int i = j + lane; i < r; i += 32) {
+          double2 s = make_double2(0.0, 0.0);
+          for (int k = 0; k <= j; ++k) s = cmac(s, W0[k * r + i], W2[j * r + k]);
+          if (i == j) s.y = 0.0;
+          W1[i * r + j] = make_double2(s.x, -s.y);
+          W1[j * r + i] = s;
+          hn += (i == j ? 1.0 : 2.0) * (s.x * s.x + s.y * s.y);
+        }
       }
     }
     hn = block_sum(hn, red);
@@ -233,11 +235,12 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
 
       // ---- 8. W = L^-H Z (per-object buffer): W[i][j] = sum_{k >= i} conj(Linv[k][i]) Z[k][j];
       // the real tridiagonal (sd, se) goes to the QL kernel, W to the finishing kernel
-      for (int idx = tid; idx < rr; idx += kPT) {
-        const int i = idx / r, j = idx - (idx / r) * r;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int k = i; k < r; ++k) acc = cmacc(acc, W2[k * r + i], W0[k * r + j]);
-        ps.W[idx] = acc;
+      for (int i = warp; i < r; i += kPW) {  // one warp per row i, lanes along j
+        for (int j = lane; j < r; j += 32) {
+          double2 acc = make_double2(0.0, 0.0);
+          for (int k = i; k < r; ++k) acc = cmacc(acc, W2[k * r + i], W0[k * r + j]);
+          ps.W[i * r + j] = acc;
+        }
       }
       for (int k = tid; k < r; k += kPT) {
         pd.lam[k] = sd[k];
@@ -519,6 +522,21 @@ __device__ __forceinline__ SweepTask table_task(const SweepTask* __restrict__ ta
 
 // ------------------------------------------------------------------ sweep
 
+// Dynamic shared memory of a sweep or adjoint task: the z tile (32 F frequencies x 3 columns x r
+// complex), then, reusing it, nq partial sums per lane of every warp.
+__host__ __device__ inline size_t pencil_task_smem(int r, int F, int nq) {
+  const size_t z = (size_t)32 * F * 3 * r * sizeof(double2);
+  const size_t red = (size_t)kPW * nq * 32 * sizeof(double);
+  return z > red ? z : red;
+}
+
+// Dynamic shared memory of this launch, in bytes.
+__device__ __forceinline__ unsigned dynamic_smem_bytes() {
+  unsigned v;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+  return v;
+}
+
 constexpr int kNQ = 39;  // partial sums per lane: U 0..8, X 9..17, E 18..26, R 27..32, I 33..38
 
 // Row pairs (a, r-1-a) of one warp, lane = one frequency: accumulates, over its rows a,
@@ -728,6 +746,10 @@ pencil_sweep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict
     const SweepTask task = table_task(table, n_w, t);
     const RomDev& ob = objs[task.obj];
     const PencilDev& pd = pens[task.obj];
+    if (pencil_task_smem(ob.r, pd.F, kNQ) > dynamic_smem_bytes()) {  // launch smaller than the task
+      if (tid == 0) atomicOr(status, kStatusConfig);
+      continue;
+    }
     const bool cert = Dout != nullptr && ob.has_cert;
     const bool has_e = pd.Eh != nullptr;
     const double ssig = s_sigma ? s_sigma[task.obj] : 1.0;
@@ -962,6 +984,10 @@ pencil_vjp_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__
     const SweepTask task = table_task(table, n_w, t);
     const RomDev& ob = objs[task.obj];
     const PencilDev& pd = pens[task.obj];
+    if (pencil_task_smem(ob.r, pd.F, kNQV) > dynamic_smem_bytes()) {  // launch smaller than the task
+      if (tid == 0) atomicOr(status, kStatusConfig);
+      continue;
+    }
     const double ssig = s_sigma ? s_sigma[task.obj] : 1.0;
     const double smu = s_mu ? s_mu[task.obj] : 1.0;
     const bool he = pd.Eh != nullptr, hf = pd.Fh != nullptr;
@@ -982,11 +1008,7 @@ pencil_vjp_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__
 
 }  // namespace
 
-size_t pencil_sweep_smem_bytes(int r, int F) {
-  const size_t z = (size_t)32 * F * 3 * r * sizeof(double2);
-  const size_t red = (size_t)kPW * kNQ * 32 * sizeof(double);
-  return z > red ? z : red;
-}
+size_t pencil_sweep_smem_bytes(int r, int F) { return pencil_task_smem(r, F, kNQ); }
 
 size_t pencil_finish_smem_bytes(int rmax) { return (size_t)rmax * (size_t)(rmax | 1) * sizeof(double); }
 
@@ -1034,11 +1056,7 @@ cudaError_t launch_pencil_route(const int* pen_ok, const int* order_pen, const i
 
 }  // namespace
 
-size_t pencil_vjp_smem_bytes(int r, int F) {
-  const size_t z = (size_t)32 * F * 3 * r * sizeof(double2);
-  const size_t red = (size_t)kPW * kNQV * 32 * sizeof(double);
-  return z > red ? z : red;
-}
+size_t pencil_vjp_smem_bytes(int r, int F) { return pencil_task_smem(r, F, kNQV); }
 
 cudaError_t launch_pencil_vjp(const RomDev* objs, const PencilDev* pens, const SweepTask* table, int* counter,
                               const double* omega, int omega_stride, const double* s_sigma, const double* s_mu,
@@ -1098,7 +1116,7 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
   std::vector<int> spen(elig.size());
   std::vector<PencilDev> pens(n_obj);
   std::memset(pens.data(), 0, n_obj * sizeof(PencilDev));
-  size_t data_elems = 0, smem = 0;
+  size_t data_elems = 0, smem = 0, smem_vjp = 0;
   int rmax = 1;
   std::vector<size_t> off(n_obj, 0);
   for (size_t k = 0; k < elig.size(); ++k) {
@@ -1108,6 +1126,7 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
     spen[k] = 32 * F;
     pens[o].F = F;
     smem = std::max(smem, pencil_sweep_smem_bytes(r, F));
+    smem_vjp = std::max(smem_vjp, pencil_vjp_smem_bytes(r, F));  // more partial sums per lane
     rmax = std::max(rmax, r);
     off[o] = data_elems;
     const size_t tri = (size_t)r * (r + 1) / 2;
@@ -1121,6 +1140,7 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
   t->prep_ws_elems = 3 * (size_t)rmax * rmax;
   t->pen_grid = h->num_sms;
   t->pen_smem = smem;
+  t->pen_smem_vjp = smem_vjp;
   t->rmax = rmax;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t b_scr = al(n_obj * sizeof(PencilScratch)), b_nsw = al(elig.size() * sizeof(int));

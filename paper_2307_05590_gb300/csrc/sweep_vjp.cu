@@ -480,7 +480,7 @@ extern "C" mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int
     if (e == cudaSuccess) e = pencil_tables_route(h, pt);
     if (e == cudaSuccess)
       e = launch_pencil_vjp(d_recs, pt.d_pens, pt.d_table_pen, pt.d_counters + 2, omega, omega_stride, s_sigma, s_mu,
-                            gR, gI, g_omega, d_gmu, R, I, h->d_status, n_w, pt.pen_grid, pt.pen_smem, h->stream);
+                            gR, gI, g_omega, d_gmu, R, I, h->d_status, n_w, pt.pen_grid, pt.pen_smem_vjp, h->stream);
     if (e == cudaSuccess) {
       ++h->launches;
       sweep_vjp_kernel<true><<<grid, kT, smem, h->stream>>>(d_objs, pt.d_table_lu, -1, pt.d_counters + 3, omega,
