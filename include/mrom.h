@@ -203,7 +203,10 @@ mrom_status mrom_project(mrom_handle h, const mrom_fom* fom, const void* D, int6
  *   not snapshots of max_ij Delta_ij (ties: lowest frequency), Lambda = max_n;
  *   stop if Lambda / |B_alpha| <= tol_delta; else ask the callback for the
  *   full-order solutions at the frequencies of the n_star largest Lambda_n (one
- *   per interval), append them and re-project.
+ *   per interval), append them and re-project.  With 0 < theta <= 1 (the variant
+ *   with a threshold described after Algorithm 1) the new frequencies are those of
+ *   every interval with Lambda_n >= theta Lambda, the largest first and at most
+ *   n_star per iteration; theta = 0 is the fixed n_star rule.
  * |B_alpha| = alpha^3 vol_B.  fom->X_diag is required (certificate).  The
  * callback receives n_new frequencies (host, ascending) and a HOST buffer of
  * 3 * n_new * n complex128 to fill: column j * 3 + i holds q_i(omega_new[j])
@@ -221,6 +224,7 @@ typedef struct {
   int32_t n_star;
   int32_t max_k;
   int32_t r_max;
+  double theta; /* 0, or a threshold in (0, 1] */
 } mrom_adapt_opts;
 mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const double* omega0, int32_t ns0, const void* D0,
                        mrom_snapshot_cb cb, void* user, const double* omega_out, int32_t n_out,

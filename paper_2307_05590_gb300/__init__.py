@@ -385,8 +385,9 @@ def mrom_rom_get(rom: ReducedObject, with_gram: bool = True) -> dict:
 
 
 def mrom_adapt(h: Handle, fom: FullOrder, omega0, D0, snapshot_fn, omega_out, *, tol_sigma: float = 1e-6,
-               tol_delta: float = 1e-3, n_star: int = 2, max_k: int = 10, r_max: int = 0):
-    """Algorithm 1 on the GPU.
+               tol_delta: float = 1e-3, n_star: int = 2, max_k: int = 10, r_max: int = 0, theta: float = 0.0):
+    """Algorithm 1 on the GPU (theta > 0: the variant with a threshold, at most n_star new
+    snapshots per iteration).
 
     omega0: initial snapshot frequencies (numpy); D0: device (3 * ns0, n) complex128
     solution columns; snapshot_fn(omegas) -> numpy (3, n, len(omegas)) full-order
@@ -411,7 +412,8 @@ def mrom_adapt(h: Handle, fom: FullOrder, omega0, D0, snapshot_fn, omega_out, *,
             return 1
 
     cb = _abi.SNAPSHOT_CB(_cb)
-    opts = _abi.mrom_adapt_opts(float(tol_sigma), float(tol_delta), int(n_star), int(max_k), int(r_max))
+    opts = _abi.mrom_adapt_opts(float(tol_sigma), float(tol_delta), int(n_star), int(max_k), int(r_max),
+                                  float(theta))
     hist = np.full(max_k, np.nan)
     cap = omega0.size + n_star * max(0, max_k - 1)
     snaps = np.zeros(cap)

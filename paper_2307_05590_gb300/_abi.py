@@ -53,6 +53,7 @@ class mrom_adapt_opts(ctypes.Structure):
         ("n_star", ctypes.c_int32),
         ("max_k", ctypes.c_int32),
         ("r_max", ctypes.c_int32),
+        ("theta", ctypes.c_double),
     ]
 
 

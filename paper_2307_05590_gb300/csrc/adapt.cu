@@ -98,6 +98,8 @@ extern "C" mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const doub
   if (!fom->X_diag) return fail(h, MROM_EINVAL, "mrom_adapt: the certificate needs fom->X_diag");
   if (opts->n_star < 1 || opts->max_k < 1 || !(opts->tol_delta >= 0.0))
     return fail(h, MROM_EINVAL, "mrom_adapt: n_star >= 1, max_k >= 1 and tol_delta >= 0 are required");
+  if (!(opts->theta >= 0.0 && opts->theta <= 1.0))
+    return fail(h, MROM_EINVAL, "mrom_adapt: theta must be 0 or in (0, 1]");
   *out = nullptr;
   const int64_t n = fom->n;
   const int ns_cap = ns0 + opts->n_star * std::max(0, opts->max_k - 1);
@@ -173,7 +175,8 @@ extern "C" mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const doub
     if (lambda_hist && nh < opts->max_k) lambda_hist[nh] = Lam;
     ++nh;
     if (!(Lam / b_alpha > opts->tol_delta)) break;
-    // the N* intervals with the largest Lambda_n, one new snapshot each
+    // the N* intervals with the largest Lambda_n, one new snapshot each; with a threshold,
+    // only intervals with Lambda_n >= theta Lambda (still at most N* per iteration)
     std::vector<int> order(nint);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -183,7 +186,8 @@ extern "C" mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const doub
     });
     std::vector<double> fresh;
     for (int i = 0; i < nint && (int)fresh.size() < opts->n_star; ++i)
-      if (arg[order[i]] >= 0) fresh.push_back(wout[arg[order[i]]]);
+      if (arg[order[i]] >= 0 && (opts->theta <= 0.0 || lam[order[i]] >= opts->theta * Lam))
+        fresh.push_back(wout[arg[order[i]]]);
     if (fresh.empty()) break;
     std::sort(fresh.begin(), fresh.end());
     const int nn = (int)fresh.size();

@@ -70,6 +70,35 @@ def test_adaptive_loop_matches_oracle(mrom):
     assert max(errs) <= 1e-9, errs
 
 
+def test_adaptive_loop_with_threshold_matches_oracle(mrom):
+    """The variant with a threshold (theta = 0.3, at most 5 per iteration): one new snapshot
+    after the first certificate evaluation and two after the second (Lambda_n / Lambda = 0.003,
+    then 1.0, 0.70 and 0.014 on this grid, far from the threshold), the oracle's choices."""
+    import torch
+    from oracle import adapt
+    from workloads import fit_problem, full_order_snapshots, log_omegas
+    from workloads.fit import Material
+    p = fit_problem(12, (Material((0.25,) * 3, (0.75,) * 3, 5.96e7, 1.0),))
+    X = p.eps * p.M + 10.0 * p.C
+    wo = log_omegas(1e1, 1e5, 60)
+    w0 = log_omegas(1e1, 1e5, 3)
+    snap = lambda ws: full_order_snapshots(p, ws)
+    _, s_ref, h_ref, k_ref = adapt.adaptive_podp(p, snap, w0, wo, tol_sigma=1e-6, tol_delta=1e-30, n_star=5,
+                                                 max_k=3, shared=True, X_diag=X, theta=0.3)
+    h = mrom.Handle(0)
+    fom = mrom.FullOrder.from_fit(p, X=X)
+    cols = np.ascontiguousarray(np.transpose(snap(w0), (2, 0, 1)).reshape(-1, p.N))
+    _, hist, k, snaps = mrom.mrom_adapt(h, fom, w0, torch.as_tensor(cols, device="cuda"), snap,
+                                        torch.as_tensor(wo, device="cuda"), tol_sigma=1e-6, tol_delta=1e-30,
+                                        n_star=5, max_k=3, theta=0.3)
+    assert k == k_ref == 3 and snaps.size == len(s_ref) == 6
+    assert snaps.tolist() == list(s_ref)
+    assert np.allclose(hist, h_ref, rtol=1e-6, atol=0.0)
+    with pytest.raises(Exception):
+        mrom.mrom_adapt(h, fom, w0, torch.as_tensor(cols, device="cuda"), snap, torch.as_tensor(wo, device="cuda"),
+                        theta=1.5)
+
+
 def test_adaptive_loop_stops_on_tolerance_and_on_callback_error(mrom):
     import torch
     from workloads import fit_problem, full_order_snapshots, log_omegas

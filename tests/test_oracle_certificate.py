@@ -83,6 +83,38 @@ def test_interval_maxima_brute_force():
     assert cand.tolist() == [5.0, 20.0, 500.0]
 
 
+def test_snapshot_selection_fixed_count_and_threshold():
+    """The fixed-N_* rule of Algorithm 1 and the variant with a threshold theta (Sect. 4.4):
+    empty intervals (Lambda_n = -inf) are never chosen, ties go to the lower interval."""
+    lam = np.array([0.4, 1.0, -np.inf, 0.6, 0.5, 0.6])
+    cand = np.array([15.0, 25.0, np.nan, 45.0, 55.0, 65.0])
+    # fixed count: the N_* largest, returned in ascending frequency
+    assert adapt.select_new(lam, cand, 1).tolist() == [25.0]
+    assert adapt.select_new(lam, cand, 3).tolist() == [25.0, 45.0, 65.0]
+    assert adapt.select_new(lam, cand, 10).tolist() == [15.0, 25.0, 45.0, 55.0, 65.0]
+    # threshold: Lambda_n >= theta Lambda (0.5 >= 0.5 included), capped at N_*
+    assert adapt.select_new(lam, cand, 10, theta=0.5).tolist() == [25.0, 45.0, 55.0, 65.0]
+    assert adapt.select_new(lam, cand, 10, theta=0.55).tolist() == [25.0, 45.0, 65.0]
+    assert adapt.select_new(lam, cand, 2, theta=0.5).tolist() == [25.0, 45.0]
+    assert adapt.select_new(lam, cand, 10, theta=1.0).tolist() == [25.0]
+    assert adapt.select_new(lam, cand, 10, theta=1e-9).tolist() == [15.0, 25.0, 45.0, 55.0, 65.0]
+
+
+def test_adaptive_loop_threshold_one_is_one_snapshot_per_iteration():
+    """theta = 1 keeps only the interval of the largest Lambda_n, so with a unique maximum it
+    makes the same choices as N_* = 1, whatever the cap."""
+    from workloads.fit import Material
+    p = fit_problem(8, (Material((0.25,) * 3, (0.75,) * 3, 5.96e7, 1.0),))
+    snap = lambda ws: full_order_snapshots(p, ws)
+    wo = log_omegas(1e1, 1e5, 40)
+    w0 = log_omegas(1e1, 1e5, 3)
+    _, s1, h1, k1 = adapt.adaptive_podp(p, snap, w0, wo, tol_sigma=1e-10, tol_delta=1e-30, n_star=1, max_k=3)
+    _, st, ht, kt = adapt.adaptive_podp(p, snap, w0, wo, tol_sigma=1e-10, tol_delta=1e-30, n_star=4, max_k=3,
+                                        theta=1.0)
+    assert k1 == kt and s1.tolist() == st.tolist()
+    assert np.allclose(h1, ht, rtol=1e-12, atol=0.0)
+
+
 def test_adaptive_loop_grows_and_reduces_lambda():
     """Algorithm 1 with N_* = 2: N grows by two per iteration (Sects. 7.1/7.2 report
     13, 15, 17, 19) and the maximum certificate falls."""

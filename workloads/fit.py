@@ -22,6 +22,11 @@ centre, which lies inside B):
   o~_i solving (K + eps_s M_Omega) o~_i = -K x_i, so that the total
   theta^(0) coefficients are o_i = x_i + o~_i (Sect. 3, below Eq. (5)).
 * N0 follows Eq. (6a) with the same lumped quadrature.
+* Optionally (mu_split=True) the part K_in of K carried by the cells of the
+  object B (the conducting cells), so that scaling mu_r on B by s gives
+  K(s) = (K - K_in) + K_in / s, with the matching parts of K x (boundary
+  columns included) for the static right-hand side; mu_scale and
+  sigma_scale build the problem at scaled material parameters.
 
 This is problem data (the discretised PDE), not the reduced-order method.
 """
@@ -80,6 +85,11 @@ class FitProblem:
     edge_mid: np.ndarray        # N x 3, edge mid-points in xi coordinates
     vol_B: float                # |B| (dimensionless volume of conducting cells)
     extra: dict = field(default_factory=dict)
+    eps_static: float = 1e-10   # regularisation of the static theta^(0) problem (mass on Omega)
+    K_in: sp.csr_matrix | None = None   # N x N part of K carried by the cells of B (mu_split)
+    kx: np.ndarray | None = None        # 3 x N, rows of K x with the boundary columns (mu_split)
+    kx_in: np.ndarray | None = None     # 3 x N, the part of kx carried by the cells of B (mu_split)
+    vol_B_mu: float = 0.0               # sum over the cells of B of |cell| / mu_r (mu_split)
 
     @property
     def N(self) -> int:
@@ -206,14 +216,16 @@ def _assign_materials(n: int, materials: Sequence[Material]):
 
 def fit_problem(n: int, materials: Sequence[Material] = CUBE_C1, *, alpha: float = 1.0,
                 eps: float = 1e-6, eps_static: float = 1e-10,
-                static_solver: Callable | None = None, static: bool = True) -> FitProblem:
+                static_solver: Callable | None = None, static: bool = True,
+                mu_scale: float = 1.0, sigma_scale: float = 1.0, mu_split: bool = False) -> FitProblem:
     """Assemble the FIT problem on an n^3 grid.
 
     eps is the regularisation of Eq. (7b) (mass on Omega minus B); eps_static
     regularises the static theta^(0) problem with mass on all of Omega.  The
     static solve is skipped (o~ = 0, N0 = 0) when mu_r == 1 everywhere, or when
     static=False (for grids too large for a sparse direct solve; the operator
-    shapes are unchanged).
+    shapes are unchanged).  mu_scale multiplies mu_r and sigma_scale sigma in
+    every conducting cell; mu_split adds K_in, kx, kx_in and vol_B_mu.
     """
     if n < 2:
         raise ValueError("n must be >= 2")
@@ -222,6 +234,9 @@ def fit_problem(n: int, materials: Sequence[Material] = CUBE_C1, *, alpha: float
     G, cA, cB = _curl_incidence(n, ids)
     ecells, mids, dirs = _edge_cells(n, ids)
     sigma, mu = _assign_materials(n, materials)
+    in_B = sigma > 0.0
+    sigma = sigma * sigma_scale
+    mu = np.where(in_B, mu * mu_scale, mu)
 
     # interior edges: mid-point strictly inside in the two transverse coordinates
     on_bnd = np.zeros(n_all, dtype=bool)
@@ -259,6 +274,18 @@ def fit_problem(n: int, materials: Sequence[Material] = CUBE_C1, *, alpha: float
         x_all[i] = v[np.arange(n_all), dirs]
 
     N = interior.size
+    split = {}
+    if mu_split:
+        # each face weight is the mean of its cells' mu_r^-1; the share of the cells of B
+        cnt = (cA >= 0).astype(np.float64) + (cB >= 0)
+        wA_in = np.where((cA >= 0) & in_B[np.maximum(cA, 0)], inv_mu[np.maximum(cA, 0)], 0.0)
+        wB_in = np.where((cB >= 0) & in_B[np.maximum(cB, 0)], inv_mu[np.maximum(cB, 0)], 0.0)
+        Kin_all = (G.T @ sp.diags(h * (wA_in + wB_in) / cnt) @ G).tocsr()
+        K_in = Kin_all[interior][:, interior].tocsr()
+        K_in.sum_duplicates()
+        split = dict(K_in=K_in, kx=np.asarray(Kall[interior] @ x_all.T).T.copy(),
+                     kx_in=np.asarray(Kin_all[interior] @ x_all.T).T.copy(),
+                     vol_B_mu=float(np.sum(inv_mu[in_B]) * h ** 3))
     o_tilde = np.zeros((3, N))
     N0 = np.zeros((3, 3))
     magnetic = np.any(mu != 1.0)
@@ -275,5 +302,5 @@ def fit_problem(n: int, materials: Sequence[Material] = CUBE_C1, *, alpha: float
         n=n, h=h, alpha=alpha, eps=eps, K=K, C=C_all[interior], M=M_all[interior],
         M_omega=Mo_all[interior], x=x_all[:, interior], o_tilde=o_tilde, N0=N0,
         cell_sigma=sigma, cell_mu=mu, edge_dir=dirs[interior], edge_mid=mids[interior],
-        vol_B=float(np.count_nonzero(sigma > 0) * h ** 3),
+        vol_B=float(np.count_nonzero(sigma > 0) * h ** 3), eps_static=eps_static, **split,
     )
