@@ -235,6 +235,84 @@ def measure_projection(m, h, n_grid: int = 96, n_s: int = 32):
             "mixed_seconds": dt32, "mixed_r": r32, "sweep_10000_omega_ms": sweep_ms}
 
 
+def measure_podp_mu(m, h, stream, n_grid=16, n_inst=1000, n_w=2000):
+    """PODP in mu_r: a magnetic cube (mu_r = 16 at s = 1) projected once from full-order snapshots
+    at 3 permeability scales x 4 frequencies (mrom_project_mu), then n_inst instances at
+    s_mu log-uniform in [1/4, 4] and s_sigma = 1 over n_w frequencies in [1e1, 1e6], values and
+    the permeability gradient (mrom_sweep_vjp, B, c00 and N0 following s_mu).  Accuracy: two
+    instances between the samples against full-order solves (the method's error, not parity)."""
+    import torch
+    from oracle import fom as ofom
+    from workloads import fit_problem, full_order_snapshots, log_omegas
+    from workloads.fit import Material
+    mat = (Material((0.375,) * 3, (0.625,) * 3, 5.96e6, 16.0),)
+    S = (0.25, 1.0, 4.0)
+    Ws = log_omegas(1e1, 1e6, 4)
+    probs = {s: fit_problem(n_grid, mat, mu_scale=s, mu_split=True) for s in S}
+    t0 = time.perf_counter()
+    D = [full_order_snapshots(probs[s], Ws) for s in S]
+    t_fom = time.perf_counter() - t0
+    p1 = probs[1.0]
+    O = np.concatenate([probs[s].o_tilde for s in S], axis=0)
+    cols = np.concatenate([np.transpose(Dl, (2, 0, 1)).reshape(-1, p1.N) for Dl in D], axis=0)
+    fom = m.FullOrder.from_fit(p1)
+    mu = m.PermeabilityData.from_fit(p1, O, tol_static=1e-8)
+    dcols = torch.as_tensor(np.ascontiguousarray(cols), device="cuda")
+    m.mrom_project_mu(h, fom, mu, dcols, tol_sigma=1e-8)[0].close()  # warm-up
+    t0 = time.perf_counter()
+    rom, r, mm = m.mrom_project_mu(h, fom, mu, dcols, tol_sigma=1e-8)
+    t_proj = time.perf_counter() - t0
+    rng = np.random.default_rng(20230714)
+    s_mu = np.exp(rng.uniform(np.log(0.25), np.log(4.0), n_inst))
+    s_mu[:2] = (0.5, 2.0)
+    wo = log_omegas(1e1, 1e6, n_w)
+    dev = torch.device("cuda")
+    om = torch.as_tensor(wo, device=dev)
+    sm = torch.as_tensor(s_mu, device=dev)
+    shape = (n_inst, n_w, 3, 3)
+    gR = torch.as_tensor(rng.standard_normal(shape), device=dev)
+    gI = torch.as_tensor(rng.standard_normal(shape), device=dev)
+    R = torch.empty(shape, dtype=torch.float64, device=dev)
+    I = torch.empty_like(R)
+    g_w = torch.empty((n_inst, n_w), dtype=torch.float64, device=dev)
+    g_m = torch.empty(n_inst, dtype=torch.float64, device=dev)
+    objs = [rom] * n_inst
+
+    def step():
+        m.mrom_sweep_vjp(h, objs, om, n_w, gR, gI, g_w, g_smu=g_m, s_mu=sm, R=R, I=I)
+
+    step()
+    h.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        step()
+    e1.record(stream)
+    h.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    # the method's error between the samples: full-order solves at s = 0.5 and 2 on a few frequencies
+    idx = np.array([0, n_w // 3, 2 * n_w // 3, n_w - 1])
+    err = []
+    for k, s in enumerate((0.5, 2.0)):
+        p = fit_problem(n_grid, mat, mu_scale=s)
+        Rf, If = ofom.fmm_signature(p, wo[idx])
+        Rf = Rf + p.N0[None]
+        Rg, Ig = R[k, idx].cpu().numpy(), I[k, idx].cpu().numpy()
+        o = p.x + p.o_tilde
+        sI = wo[idx] * p.alpha ** 3 / 4 * np.abs(o @ (p.C[:, None] * o.T)).max()
+        eR = np.abs(Rg - Rf).reshape(idx.size, -1).max(1) / np.abs(Rf).reshape(idx.size, -1).max(1)
+        eI = np.abs(Ig - If).reshape(idx.size, -1).max(1) / sI
+        err.append(float(max(eR.max(), eI.max())))
+    rom.close()
+    return {"workload": f"PODP in mu_r: {n_grid}^3 FIT cube (N = {p1.N}), mu_r = 16 x s, sigma = 5.96e6; "
+                        f"snapshots at s in {list(S)} x 4 omega in [1e1, 1e6]; {n_inst} instances with s_mu "
+                        f"log-uniform in [1/4, 4] x {n_w} omega in [1e1, 1e6], values and dL/ds_mu",
+            "r": r, "m_static": mm, "project_seconds": t_proj, "full_order_snapshot_seconds_cpu": t_fom,
+            "ms_per_step": ms, "value": n_inst * n_w / (ms * 1e-3),
+            "unit": "(s_mu, omega) evaluations/s with the permeability gradient",
+            "max_rel_error_vs_full_order_between_samples": max(err)}
+
+
 def measure_c1_latency(m, h):
     """Copper cube on the 16^3 FIT grid (N = 10,800): the paper's PODP with one TSVD per direction
     from nine full-order snapshots in [1e1, 1e5] (computed on the host by sparse LU: the off-line
@@ -378,6 +456,9 @@ def main():
                     help="time mrom_adapt (Algorithm 1) on the two-material grid and print its record")
     ap.add_argument("--adaptive-grid", type=int, default=128)
     ap.add_argument("--projection", action=argparse.BooleanOptionalAction, default=True)
+    ap.add_argument("--podp-mu", action=argparse.BooleanOptionalAction, default=True,
+                    help="PODP in mu_r section (projection with the static reduction, instances over s_mu)")
+    ap.add_argument("--podp-mu-only", action="store_true", help="run only the PODP in mu_r section")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -405,6 +486,15 @@ def main():
         h = m.Handle(local_rank, stream.cuda_stream)
         if rank == 0:
             print(json.dumps({"adaptive": measure_adaptive(m, h, n_grid=args.adaptive_grid)}), flush=True)
+        h.close()
+        return
+
+    if args.podp_mu_only:
+        stream = torch.cuda.Stream(dev)
+        h = m.Handle(local_rank, stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            if rank == 0:
+                print(json.dumps({"podp_mu": measure_podp_mu(m, h, stream)}), flush=True)
         h.close()
         return
 
@@ -544,6 +634,7 @@ def main():
         del Rm, Im, Dm
 
     proj = measure_projection(m, h) if args.projection else None
+    pmu = measure_podp_mu(m, h, stream) if args.podp_mu and rank == 0 else None
     c1 = measure_c1_latency(m, h) if args.projection else None
 
     # ---- gradients (adjoint sweep) on the same dictionary: dL/domega, dL/ds_sigma, dL/ds_mu for
@@ -655,7 +746,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "wall_s_timed": wall, "per_launch_ms": per_launch_ms, "sweep_config": sweep_cfg,
             "stages": stage_info, "lu_route": lu_route, "mixed_precision": mixed, "projection": proj,
-            "gradients": grads, "invariants": inv, "c1_latency": c1,
+            "gradients": grads, "invariants": inv, "c1_latency": c1, "podp_mu": pmu,
         }
         print(json.dumps(line), flush=True)
     plan.close()

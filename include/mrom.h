@@ -192,6 +192,52 @@ mrom_status mrom_project(mrom_handle h, const mrom_fom* fom, const void* D, int6
                          double tol_sigma, int32_t r_max, const void* basis_in, int32_t r_in, mrom_rom_t* out,
                          double* sigma_out, int32_t* r_out);
 
+/* PODP in the relative permeability.  Sect. 4.2 notes that the precomputation of
+ * Eqs. (17)-(19) carries over to parameters other than omega; here the parameter s
+ * scales mu_r in every cell of the object (mu_r -> s mu_r).  K is linear in mu_r^-1
+ * cell by cell (Eq. (10a)), so K(s) = (K - K_in) + K_in / s; theta~^(0) depends on s
+ * through the static problem (K(s) + M_s) o~ = -K(s) x (Eq. (5)), and with it b, c00
+ * and N0 (Eq. (6a)).  The conductivity needs no second parameter: it enters only
+ * through nu = alpha^2 mu_0 omega sigma, so a conductivity scale is the sweep's
+ * s_sigma.  All pointers are device pointers, owned by the caller. */
+#define MROM_MAX_STATIC 64
+typedef struct {
+  const int32_t* Kin_rowptr; /* K_in: CSR n x n, the part of K carried by the object's cells (s = 1) */
+  const int32_t* Kin_col;
+  const double* Kin_val;
+  const double* x;           /* 3 x n (row i at x + i n): the coefficients of e_i x xi */
+  const double* kx;          /* 3 x n: K x at s = 1, K's columns of eliminated boundary edges included */
+  const double* kx_in;       /* 3 x n: the part of kx carried by the object's cells */
+  const double* M_static;    /* n: diagonal of the static problem's regularisation M_s */
+  double vol_B_mu;           /* sum over the object's cells of |cell| / mu_r at s = 1 */
+  const double* O;           /* static snapshots o~_i(s_l), real: n_o columns, column c at O + c * ldo */
+  int64_t ldo;
+  int32_t n_o;
+  double tol_static;         /* truncation of the static snapshots' SVD, as tol_sigma */
+} mrom_fom_mu;
+
+/* As mrom_project (fom at s = 1; D holds snapshots q_i(omega_k, s_l) of the sampled
+ * parameters, one basis U for all of them), plus K_in^r = U^H K_in U and the reduced
+ * static problem: V from the SVD of O (rank m <= MROM_MAX_STATIC, r_out / m_out report
+ * r and m), S(s) = V^H (K(s) + M_s) V, V^H K(s) x, U^H C V, V^H C V and V^H C x, so that
+ * o~(s) ~= V y(s) with S(s) y = -V^H K(s) x.  The object's B, c00 and N0 are those of
+ * the reduced static problem at s = 1; mrom_sweep_vjp evaluates it at per-object s_mu
+ * with B, c00 and N0 following s_mu, and its dL/ds_mu includes their derivatives.
+ * The certificate (fom->X_diag) is that of s = 1.  MROM_EINVAL if O has no nonzero
+ * singular value.  Synchronous. */
+mrom_status mrom_project_mu(mrom_handle h, const mrom_fom* fom, const mrom_fom_mu* mu, const void* D, int64_t ldd,
+                            int32_t n_cols, double tol_sigma, int32_t r_max, mrom_rom_t* out, int32_t* r_out,
+                            int32_t* m_out);
+
+/* Rank m of an object's reduced static problem (0: none). */
+int32_t mrom_rom_static_rank(mrom_rom_t rom);
+
+/* The reduced static state of an object at the permeability scale s_mu (host outputs,
+ * each optional): B (r x 3 complex128 row-major), c00, N0 (3 x 3), and their
+ * derivatives with respect to s_mu.  Synchronous. */
+mrom_status mrom_rom_mu_state(mrom_rom_t rom, double s_mu, void* B, double* c00, double* N0, void* dB, double* dc00,
+                              double* dN0);
+
 /* Adaptive PODP, Algorithm 1 (Sect. 4.4), with one basis for the three directions.
  * Starting from ns0 >= 2 snapshots at omega0 (host, ns0 values) with their
  * 3 * ns0 full-order solution columns in D0 (length n each, column c at

@@ -23,7 +23,8 @@ __all__ = [
     "mrom_rom_from_reduced", "mrom_rom_free", "mrom_rom_rank", "mrom_sweep", "mrom_certificate",
     "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune", "mrom_sweep_noalloc",
     "FullOrder", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "MromSweep", "signature",
-    "mrom_sweep_mixed", "mrom_project_dirs", "mrom_invariants",
+    "mrom_sweep_mixed", "mrom_project_dirs", "mrom_invariants", "PermeabilityData", "mrom_project_mu",
+    "mrom_rom_mu_state",
 ]
 
 
@@ -344,6 +345,62 @@ class FullOrder:
                    t(problem.C, torch.float64), t(problem.o, torch.float64), M=t(problem.M, torch.float64),
                    eps=problem.eps, X=None if X is None else t(X, torch.float64), alpha=problem.alpha,
                    alpha_lb=alpha_lb, vol_B=problem.vol_B, N0=t(problem.N0.ravel(), torch.float64))
+
+
+class PermeabilityData:
+    """Device copy of the permeability data of a full-order problem (mrom_fom_mu): K_in
+    (CSR), x, K x and K_in x (3 x n), the static regularisation's diagonal, the sum over the
+    object of |cell| / mu_r, and the static snapshots O (n_o x n float64, one per row)."""
+
+    def __init__(self, Kin_rowptr, Kin_col, Kin_val, x, kx, kx_in, M_static, vol_B_mu, O, *, tol_static=1e-10):
+        self.keep = [Kin_rowptr, Kin_col, Kin_val, x, kx, kx_in, M_static, O]
+        d = _abi.mrom_fom_mu()
+        d.Kin_rowptr, d.Kin_col, d.Kin_val = _ptr(Kin_rowptr), _ptr(Kin_col), _ptr(Kin_val)
+        d.x, d.kx, d.kx_in, d.M_static = _ptr(x), _ptr(kx), _ptr(kx_in), _ptr(M_static)
+        d.vol_B_mu = float(vol_B_mu)
+        d.O, d.ldo, d.n_o = _ptr(O), int(O.shape[1]), int(O.shape[0])
+        d.tol_static = float(tol_static)
+        self.desc = d
+
+    @classmethod
+    def from_fit(cls, problem, O, device="cuda", *, tol_static=1e-10):
+        """From a workloads.FitProblem built with mu_split=True and static snapshots O
+        (numpy (n_o, n): rows o~_i(s_l))."""
+        import torch
+        Kin = problem.K_in.tocsr()
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)
+        return cls(t(Kin.indptr, torch.int32), t(Kin.indices, torch.int32), t(Kin.data, torch.float64),
+                   t(problem.x, torch.float64), t(problem.kx, torch.float64), t(problem.kx_in, torch.float64),
+                   t(problem.eps_static * problem.M_omega, torch.float64), problem.vol_B_mu,
+                   t(O, torch.float64), tol_static=tol_static)
+
+
+def mrom_project_mu(h: Handle, fom: FullOrder, mu: PermeabilityData, D, *, tol_sigma: float = 1e-6,
+                    r_max: int = 0):
+    """PODP in mu_r: projection onto the basis of the snapshot columns D (device (n_cols, n)
+    complex128, taken at sampled (omega, s_mu)) with the reduced static problem of mu.
+    Returns (ReducedObject, r, m)."""
+    rom = ctypes.c_void_p()
+    r_out, m_out = ctypes.c_int32(0), ctypes.c_int32(0)
+    _abi.check(lib().mrom_project_mu(h.ptr, ctypes.byref(fom.desc), ctypes.byref(mu.desc), _ptr(D),
+                                     int(D.shape[1]), int(D.shape[0]), float(tol_sigma), int(r_max),
+                                     ctypes.byref(rom), ctypes.byref(r_out), ctypes.byref(m_out)), h.ptr)
+    obj = ReducedObject._wrap(h, rom, r_out.value, fom.desc.X_diag is not None)
+    return obj, int(r_out.value), int(m_out.value)
+
+
+def mrom_rom_mu_state(rom, s_mu: float) -> dict:
+    """Reduced static state of an object at s_mu: B, c00, N0 and their derivatives (numpy)."""
+    r = rom.r
+    out = {k: np.zeros((r, 3), dtype=np.complex128) for k in ("B", "dB")}
+    for k in ("c00", "N0", "dc00", "dN0"):
+        out[k] = np.zeros(9)
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _abi.check(lib().mrom_rom_mu_state(rom.ptr, float(s_mu), out["B"].ctypes.data, dp(out["c00"]), dp(out["N0"]),
+                                       out["dB"].ctypes.data, dp(out["dc00"]), dp(out["dN0"])), rom.handle.ptr)
+    for k in ("c00", "N0", "dc00", "dN0"):
+        out[k] = out[k].reshape(3, 3)
+    return out
 
 
 def mrom_project(h: Handle, fom: FullOrder, D=None, *, tol_sigma: float = 1e-6, r_max: int = 0, basis=None):

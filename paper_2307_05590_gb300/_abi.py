@@ -18,7 +18,8 @@ EXPORTS = [
     "mrom_certificate", "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune",
     "mrom_sweep_noalloc", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "mrom_sweep_mixed",
     "mrom_project_dirs", "mrom_set_projection_precision", "mrom_set_solver", "mrom_plan_solver_counts",
-    "mrom_plan_timing", "mrom_rom_from_reduced_batch", "mrom_invariants",
+    "mrom_plan_timing", "mrom_rom_from_reduced_batch", "mrom_invariants", "mrom_project_mu",
+    "mrom_rom_static_rank", "mrom_rom_mu_state",
 ]
 
 
@@ -43,6 +44,23 @@ class mrom_fom(ctypes.Structure):
         ("alpha_lb", ctypes.c_double),
         ("vol_B", ctypes.c_double),
         ("N0", ctypes.c_void_p),
+    ]
+
+
+class mrom_fom_mu(ctypes.Structure):
+    _fields_ = [
+        ("Kin_rowptr", ctypes.c_void_p),
+        ("Kin_col", ctypes.c_void_p),
+        ("Kin_val", ctypes.c_void_p),
+        ("x", ctypes.c_void_p),
+        ("kx", ctypes.c_void_p),
+        ("kx_in", ctypes.c_void_p),
+        ("M_static", ctypes.c_void_p),
+        ("vol_B_mu", ctypes.c_double),
+        ("O", ctypes.c_void_p),
+        ("ldo", ctypes.c_int64),
+        ("n_o", ctypes.c_int32),
+        ("tol_static", ctypes.c_double),
     ]
 
 
@@ -96,6 +114,11 @@ def _declare(L):
         "mrom_plan_solver_counts": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "mrom_rom_from_reduced": (ctypes.c_int, [vp, ctypes.POINTER(mrom_reduced_desc), ctypes.POINTER(vp)]),
         "mrom_rom_rank": (i32, [vp]),
+        "mrom_rom_static_rank": (i32, [vp]),
+        "mrom_rom_mu_state": (ctypes.c_int, [vp, ctypes.c_double, vp, dp, dp, vp, dp, dp]),
+        "mrom_project_mu": (ctypes.c_int, [vp, ctypes.POINTER(mrom_fom), ctypes.POINTER(mrom_fom_mu), vp, i64, i32,
+                                           ctypes.c_double, i32, ctypes.POINTER(vp), ctypes.POINTER(i32),
+                                           ctypes.POINTER(i32)]),
         "mrom_rom_free": (None, [vp]),
         "mrom_sweep": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, dp, i32, i32, dp, dp, dp, dp, dp]),
         "mrom_certificate": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, dp, i32, i32, dp]),

@@ -76,12 +76,6 @@ interval_max_kernel(const double* __restrict__ Delta, const double* __restrict__
   }
 }
 
-struct DevBuf {
-  void* p = nullptr;
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
-};
 
 }  // namespace
 }  // namespace mrom

@@ -151,6 +151,9 @@ RomDev rom_record(const mrom_rom* m) {
   d.cert_scale = m->has_cert ? d.alpha3 / (4.0 * m->alpha_lb) : 0.0;
   d.r = m->r;
   d.has_cert = m->has_cert ? 1 : 0;
+  d.dB = nullptr;
+  std::fill(d.dc00, d.dc00 + 9, 0.0);
+  std::fill(d.dN0, d.dN0 + 9, 0.0);
   d.per_dir = (m->r_dirs[0] + m->r_dirs[1] + m->r_dirs[2]) > 0 ? 1 : 0;
   int off = 0;
   for (int i = 0; i < 3; ++i) {

@@ -44,6 +44,10 @@ struct RomDev {
   int per_dir;
   int blk_lo[3];
   int blk_hi[3];
+  // PODP in mu_r (per call, when the permeability gradient is wanted): d/ds_mu of B, c00 and N0
+  const double2* dB;  // r x 3 or nullptr
+  double dc00[9];
+  double dN0[9];
 };
 
 // Per-object data of the pencil route (pencil.cu), computed on the device by the
@@ -61,6 +65,7 @@ struct PencilDev {
   double2* Gh;
   double2* Eh;
   double2* Fh;  // V^H K_in V (packed lower, or null): the permeability gradient
+  double2* dbeta;  // r x 3: V^H dB/ds_mu (or null)
   int F;
   int pad;
 };
@@ -125,6 +130,44 @@ struct mrom_ctx {
   std::string last_error;
 };
 
+namespace mrom {
+
+// PODP in mu_r (a scale s of mu_r on the object): the reduced static problem of one object,
+// S(s) y = -(kout + kin / s) with S(s) = Sout + Sin / s + Mv (m x m Hermitian, row-major), and
+// the maps to B(s) = Bx + BV y, c00(s) = cxx + Re(cvx^H y + y^H cvx + y^H cvv y),
+// N0(s) = (nB - mB / s) I + alpha^3/4 Re(y^H (Sout + Sin / s) y).  Per call the host sets the
+// destinations of B(s) and dB/ds (r x 3) for the object.
+struct MuDev {
+  const double2 *Sout, *Sin, *Mv, *kout, *kin, *cvx, *cvv, *Bx, *BV;
+  double cxx[9];
+  double nB, mB, alpha3;
+  int m, r;
+  double2* Bdst;
+  double2* dBdst;
+};
+
+// Device buffer released at scope exit.
+struct DevBuf {
+  void* p = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+// Per-object record of the LU-route adjoint kernel.
+struct VjpDev {
+  const double2 *K, *Kin, *C, *Me, *B;
+  const double2* dB;  // d/ds_mu of B (PODP in mu_r) or nullptr
+  double c00[9], N0[9], dc00[9], dN0[9];
+  double alpha3;
+  int r;
+};
+
+}  // namespace mrom
+
 struct mrom_rom {
   mrom_ctx* ctx = nullptr;
   int r = 0;
@@ -146,6 +189,9 @@ struct mrom_rom {
   bool has_cert = false;
   bool has_kin = false;
   int r_dirs[3] = {0, 0, 0};  // per-direction basis sizes (all 0: one shared basis)
+  // PODP in mu_r: the reduced static problem (device views in mu_block; mu.m == 0: none)
+  mrom::MuDev mu{};
+  void* mu_block = nullptr;
 };
 
 struct mrom_plan_s {
@@ -229,6 +275,14 @@ cudaError_t launch_pencil_sweep(const RomDev* objs, const PencilDev* pens, const
 
 // Builds the RomDev record of an object (api.cu).
 RomDev rom_record(const mrom_rom* m);
+
+// PODP in mu_r (podp_mu.cu): for every object o with mus[o].m > 0, the static state at
+// s_mu[o] (1 if s_mu is null): B(s) into mus[o].Bdst, dB/ds into mus[o].dBdst (when deriv), and
+// c00, N0 (and dc00, dN0 when deriv) into recs[o] and vjp[o] (either array may be null).
+// A non-positive pivot of the static system sets kStatusSingular in *status.
+// m_max: the largest m in the batch (dynamic shared memory).
+cudaError_t launch_mu_instance(const MuDev* mus, int n_obj, int m_max, const double* s_mu, bool deriv, RomDev* recs,
+                               VjpDev* vjp, int* status, cudaStream_t stream);
 size_t sweep_budget_bytes(const mrom_ctx* h, int cfg);
 int sweep_config(const mrom_ctx* h);
 

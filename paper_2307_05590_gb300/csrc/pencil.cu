@@ -424,6 +424,14 @@ pencil_finish_kernel(const RomDev* __restrict__ objs, const PencilDev* __restric
       for (int a = 0; a < r; ++a) acc = cmacc(acc, W1[a * r + k], ob.B[a * 3 + j]);
       pd.beta[idx] = acc;  // beta[k][j] = (V^H B)[k][j]
     }
+    if (pd.dbeta) {
+      for (int idx = tid; idx < 3 * r; idx += kPT) {
+        const int k = idx / 3, j = idx - (idx / 3) * 3;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int a = 0; a < r; ++a) acc = cmacc(acc, W1[a * r + k], ob.dB[a * 3 + j]);
+        pd.dbeta[idx] = acc;  // (V^H dB/ds_mu)[k][j]
+      }
+    }
     __syncthreads();
     for (int idx = tid; idx < 6 * r; idx += kPT) {  // bbr[k][(i,j)] = Re(beta_ki^* beta_kj), i <= j
       const int k = idx / 6, q = idx - (idx / 6) * 6;
@@ -782,6 +790,9 @@ pencil_sweep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict
 //   dL/domega = s_sigma S_w + sum gI.I / omega,  dL/ds_mu part = (S_mu + a^3/4 sum gR.HK) / s_mu^2.
 // Per row a every term needs only row a of E Z and F Z, so rows are independent.
 constexpr int kNQV = 42;  // partial sums per lane: R 0..5, I 6..11, B 12..20, RE 21..29, HK 30..38, Sw 39, Smu 40
+// with the PODP in mu_r (dbeta = V^H dB/ds_mu): Re(dbeta_i^H z_j) 42..50, Im tr(dbeta^H Y) 51, and
+//   dL/ds_mu += w' a^3/4 sum_ij Re(db_i^H p_j) G_I,ij + w' Im tr(dbeta^H Y) + w' a^3/4 gI.dc00 + gR.dN0
+constexpr int kNQVB = 52;
 
 __device__ __forceinline__ double2 herm_packed(const double2* __restrict__ M, int a, int b) {  // M[a][b]
   if (b <= a) return M[(size_t)a * (a + 1) / 2 + b];
@@ -789,10 +800,10 @@ __device__ __forceinline__ double2 herm_packed(const double2* __restrict__ M, in
   return make_double2(v.x, -v.y);
 }
 
-template <bool HAS_E, bool HAS_F>
+template <bool HAS_E, bool HAS_F, bool HAS_DB, int NQ>
 __device__ __forceinline__ void pencil_vjp_rows(const PencilDev& pd, int r, const double2* __restrict__ zg, double w,
                                                 double alpha3, const double (&GR)[9], const double (&GI)[9], int q0,
-                                                int wpg, double (&acc)[kNQV]) {
+                                                int wpg, double (&acc)[NQ]) {
   const double cR = -0.25 * alpha3, cI = 0.25 * alpha3 * w;
   for (int a = q0; a < r; a += wpg) {
     double2 za[3], ez[3], fz[3];
@@ -819,9 +830,18 @@ __device__ __forceinline__ void pencil_vjp_rows(const PencilDev& pd, int r, cons
       }
     }
     const double lam = pd.lam[a];
-    double2 be[3];
+    double2 be[3], db[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) be[j] = pd.beta[a * 3 + j];
+    if constexpr (HAS_DB) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) db[j] = pd.dbeta[a * 3 + j];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          acc[42 + i * 3 + j] = fma(db[i].x, za[j].x, fma(db[i].y, za[j].y, acc[42 + i * 3 + j]));
+    }
     {
       int q = 0;
 #pragma unroll
@@ -858,11 +878,12 @@ __device__ __forceinline__ void pencil_vjp_rows(const PencilDev& pd, int r, cons
       const double vx = be[k].x + za[k].x, vy = be[k].y + za[k].y;
       acc[39] += vx * y.y - vy * y.x;  // Im(conj(v) y)
       if constexpr (HAS_F) acc[40] = fma(fz[k].x, y.x, fma(fz[k].y, y.y, acc[40]));
+      if constexpr (HAS_DB) acc[51] += db[k].x * y.y - db[k].y * y.x;  // Im(conj(db) y)
     }
   }
 }
 
-template <bool HAS_E, bool HAS_F>
+template <bool HAS_E, bool HAS_F, bool HAS_DB>
 __device__ __forceinline__ void pencil_vjp_task(const RomDev& ob, const PencilDev& pd, const SweepTask& task,
                                                 const double* __restrict__ omega, int omega_stride, double ssig,
                                                 double smu, const double* __restrict__ gR,
@@ -903,9 +924,10 @@ __device__ __forceinline__ void pencil_vjp_task(const RomDev& ob, const PencilDe
     }
   }
   __syncthreads();
-  double acc[kNQV];
+  constexpr int NQ = HAS_DB ? kNQVB : kNQV;
+  double acc[NQ];
 #pragma unroll
-  for (int q = 0; q < kNQV; ++q) acc[q] = 0.0;
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
   {
     const int g = warp % F, s = g * 32 + lane;
     double GR[9], GI[9];
@@ -917,28 +939,28 @@ __device__ __forceinline__ void pencil_vjp_task(const RomDev& ob, const PencilDe
         GR[i * 3 + j] = gR[e + i * 3 + j] + gR[e + j * 3 + i];
         GI[i * 3 + j] = gI[e + i * 3 + j] + gI[e + j * 3 + i];
       }
-    pencil_vjp_rows<HAS_E, HAS_F>(pd, r, zs + (size_t)g * r * 3 * 32 + lane, Ws[s], ob.alpha3, GR, GI, warp / F,
+    pencil_vjp_rows<HAS_E, HAS_F, HAS_DB, NQ>(pd, r, zs + (size_t)g * r * 3 * 32 + lane, Ws[s], ob.alpha3, GR, GI, warp / F,
                                   wpg, acc);
   }
   __syncthreads();
   {
-    double* rb = rbuf + (size_t)warp * kNQV * 32 + lane;
+    double* rb = rbuf + (size_t)warp * NQ * 32 + lane;
 #pragma unroll
-    for (int q = 0; q < kNQV; ++q) rb[q * 32] = acc[q];
+    for (int q = 0; q < NQ; ++q) rb[q * 32] = acc[q];
   }
   __syncthreads();
   if (wpg > 1) {
-    for (int idx = tid; idx < F * kNQV * 32; idx += kPT) {
-      const int g = idx / (kNQV * 32);
-      const int rem = idx - g * kNQV * 32;
-      double v = rbuf[(size_t)g * kNQV * 32 + rem];
-      for (int k = 1; k < wpg; ++k) v += rbuf[(size_t)(g + k * F) * kNQV * 32 + rem];
-      rbuf[(size_t)g * kNQV * 32 + rem] = v;
+    for (int idx = tid; idx < F * NQ * 32; idx += kPT) {
+      const int g = idx / (NQ * 32);
+      const int rem = idx - g * NQ * 32;
+      double v = rbuf[(size_t)g * NQ * 32 + rem];
+      for (int k = 1; k < wpg; ++k) v += rbuf[(size_t)(g + k * F) * NQ * 32 + rem];
+      rbuf[(size_t)g * NQ * 32 + rem] = v;
     }
     __syncthreads();
   }
   for (int s = tid; s < S; s += kPT) {
-    const double* tot = rbuf + (size_t)(s >> 5) * kNQV * 32 + (s & 31);
+    const double* tot = rbuf + (size_t)(s >> 5) * NQ * 32 + (s & 31);
     auto t = [tot](int q) { return tot[q * 32]; };
     const double wv = Ws[s];
     const size_t o = (size_t)task.obj * n_w + task.w0 + s;
@@ -959,7 +981,18 @@ __device__ __forceinline__ void pencil_vjp_task(const RomDev& ob, const PencilDe
     }
     const double wr = wv / ssig;  // the caller's omega
     g_omega[o] = fma(ssig, t(39), gI_dot_I / wr);
-    g_mu_part[o] = HAS_F ? (t(40) + 0.25 * ob.alpha3 * gR_dot_HK) / (smu * smu) : 0.0;
+    double gmu = HAS_F ? (t(40) + 0.25 * ob.alpha3 * gR_dot_HK) / (smu * smu) : 0.0;
+    if constexpr (HAS_DB) {
+      double src = 0.0, stat = 0.0;
+#pragma unroll
+      for (int ij = 0; ij < 9; ++ij) {
+        const int ji = (ij % 3) * 3 + ij / 3;
+        src = fma(t(42 + ij), gI[o * 9 + ij] + gI[o * 9 + ji], src);
+        stat = fma(gI[o * 9 + ij], 0.25 * ob.alpha3 * wv * ob.dc00[ij], fma(gR[o * 9 + ij], ob.dN0[ij], stat));
+      }
+      gmu += 0.25 * ob.alpha3 * wv * src + wv * t(51) + stat;
+    }
+    g_mu_part[o] = gmu;
   }
 }
 
@@ -984,25 +1017,29 @@ pencil_vjp_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__
     const SweepTask task = table_task(table, n_w, t);
     const RomDev& ob = objs[task.obj];
     const PencilDev& pd = pens[task.obj];
-    if (pencil_task_smem(ob.r, pd.F, kNQV) > dynamic_smem_bytes()) {  // launch smaller than the task
+    if (pencil_task_smem(ob.r, pd.F, kNQVB) > dynamic_smem_bytes()) {  // launch smaller than the task
       if (tid == 0) atomicOr(status, kStatusConfig);
       continue;
     }
     const double ssig = s_sigma ? s_sigma[task.obj] : 1.0;
     const double smu = s_mu ? s_mu[task.obj] : 1.0;
-    const bool he = pd.Eh != nullptr, hf = pd.Fh != nullptr;
-    if (he && hf)
-      pencil_vjp_task<true, true>(ob, pd, task, omega, omega_stride, ssig, smu, gR, gI, g_omega, g_mu_part, Rout,
-                                  Iout, status, n_w, smem_raw, Ws);
-    else if (he)
-      pencil_vjp_task<true, false>(ob, pd, task, omega, omega_stride, ssig, smu, gR, gI, g_omega, g_mu_part, Rout,
-                                   Iout, status, n_w, smem_raw, Ws);
-    else if (hf)
-      pencil_vjp_task<false, true>(ob, pd, task, omega, omega_stride, ssig, smu, gR, gI, g_omega, g_mu_part, Rout,
-                                   Iout, status, n_w, smem_raw, Ws);
-    else
-      pencil_vjp_task<false, false>(ob, pd, task, omega, omega_stride, ssig, smu, gR, gI, g_omega, g_mu_part, Rout,
-                                    Iout, status, n_w, smem_raw, Ws);
+    const bool he = pd.Eh != nullptr, hf = pd.Fh != nullptr, hdb = hf && pd.dbeta != nullptr;
+#define MROM_VJP_TASK(E, F, DB)                                                                              \
+  pencil_vjp_task<E, F, DB>(ob, pd, task, omega, omega_stride, ssig, smu, gR, gI, g_omega, g_mu_part, Rout, Iout, \
+                            status, n_w, smem_raw, Ws)
+    if (hdb) {
+      if (he) MROM_VJP_TASK(true, true, true);
+      else MROM_VJP_TASK(false, true, true);
+    } else if (he && hf) {
+      MROM_VJP_TASK(true, true, false);
+    } else if (he) {
+      MROM_VJP_TASK(true, false, false);
+    } else if (hf) {
+      MROM_VJP_TASK(false, true, false);
+    } else {
+      MROM_VJP_TASK(false, false, false);
+    }
+#undef MROM_VJP_TASK
   }
 }
 
@@ -1056,7 +1093,7 @@ cudaError_t launch_pencil_route(const int* pen_ok, const int* order_pen, const i
 
 }  // namespace
 
-size_t pencil_vjp_smem_bytes(int r, int F) { return pencil_task_smem(r, F, kNQV); }
+size_t pencil_vjp_smem_bytes(int r, int F) { return pencil_task_smem(r, F, kNQVB); }
 
 cudaError_t launch_pencil_vjp(const RomDev* objs, const PencilDev* pens, const SweepTask* table, int* counter,
                               const double* omega, int omega_stride, const double* s_sigma, const double* s_mu,
@@ -1134,6 +1171,7 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
     if (gram && objs[o].has_cert) data_elems += 6 * (size_t)r + 3 * tri;  // gsh, Gh
     if (objs[o].Me) data_elems += tri;                                    // Eh
     if (kin && objs[o].Kin) data_elems += tri;                            // Fh
+    if (objs[o].dB) data_elems += 3 * (size_t)r;                          // dbeta
     data_elems += (size_t)r * r + (size_t)(r + 1) / 2 + rot_cap(r) + (sweep_cap(r) + 1) / 2;  // scratch
   }
   t->prep_grid = std::min<int>((int)elig.size(), 2 * h->num_sms);
@@ -1188,6 +1226,9 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
     }
     if (kin && objs[o].Kin) {
       pens[o].Fh = q; q += tri;
+    }
+    if (objs[o].dB) {
+      pens[o].dbeta = q; q += 3 * (size_t)r;
     }
     scr[o].W = q; q += (size_t)r * r;
     scr[o].e = reinterpret_cast<double*>(q); q += (r + 1) / 2;

@@ -412,6 +412,23 @@ __global__ void build_phi_kernel(const double* __restrict__ o, const double* __r
   }
 }
 
+// Y[c * n + i] = X[c * ldx + i] + 0i for n_c columns
+__global__ void real_cols_kernel(const double* __restrict__ X, int64_t ldx, int64_t n, int n_c,
+                                 double2* __restrict__ Y) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * n_c;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = idx / n, i = idx - (idx / n) * n;
+    Y[idx] = make_double2(X[c * ldx + i], 0.0);
+  }
+}
+
+// Z = X - Y (n complex values)
+__global__ void csub_kernel(const double2* __restrict__ X, const double2* __restrict__ Y, int n,
+                            double2* __restrict__ Z) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+    Z[idx] = make_double2(X[idx].x - Y[idx].x, X[idx].y - Y[idx].y);
+}
+
 __global__ void scale_kernel(const double* __restrict__ x, double a, int64_t n, double* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i];
@@ -459,13 +476,6 @@ __global__ void symmetrize_kernel(double2* __restrict__ G, int m) {
   }
 }
 
-// Device buffers released at scope exit.
-struct DevBuf {
-  void* p = nullptr;
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
-};
 
 }  // namespace
 
@@ -621,7 +631,7 @@ mrom_status apply_basis(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, 
 // Galerkin projection onto the basis U (n x Rt row-major; r_dirs = per-direction column
 // blocks, or all zero for one shared basis) and creation of the reduced object.
 mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, int r, const int32_t* r_dirs,
-                          mrom_rom_t* out) {
+                          mrom_rom_t* out, const double2* Kin_r = nullptr) {
   const int64_t n = fom->n;
   cudaStream_t st = h->stream;
   auto launch_grid = [](int64_t work) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(65535 * 4, (work + 255) / 256)); };
@@ -762,6 +772,7 @@ mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, in
   d.C = Cr;
   d.Me = has_me ? Me : nullptr;
   d.B = Bm;
+  d.K_in = Kin_r;
   d.c00 = c00;
   d.G = cert ? Gm : nullptr;
   d.N0 = fom->N0;
@@ -904,5 +915,202 @@ extern "C" mrom_status mrom_rom_get(mrom_rom_t rom, void* K, void* C, void* Me, 
     cp(G, rom->G, ng * ng * 16);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_rom_get");
+  return MROM_OK;
+}
+
+extern "C" mrom_status mrom_project_mu(mrom_handle h, const mrom_fom* fom, const mrom_fom_mu* mu, const void* D,
+                                       int64_t ldd, int32_t n_cols, double tol_sigma, int32_t r_max,
+                                       mrom_rom_t* out, int32_t* r_out, int32_t* m_out) {
+  if (!h) return MROM_EINVAL;
+  if (!out || !mu) return fail(h, MROM_EINVAL, "mrom_project_mu: null argument");
+  *out = nullptr;
+  mrom_status st = check_fom(h, fom);
+  if (st != MROM_OK) return st;
+  const int64_t n = fom->n;
+  if (!D || n_cols < 1 || n_cols > MROM_MAX_SNAPSHOTS || ldd < n)
+    return fail(h, MROM_EINVAL, "mrom_project_mu: D needs 1..MROM_MAX_SNAPSHOTS columns and ldd >= n");
+  if (!(tol_sigma >= 0.0) || !std::isfinite(tol_sigma) || !(mu->tol_static >= 0.0) || !std::isfinite(mu->tol_static))
+    return fail(h, MROM_EINVAL, "mrom_project_mu: tolerances must be finite and >= 0");
+  if (!mu->Kin_rowptr || !mu->Kin_col || !mu->Kin_val || !mu->x || !mu->kx || !mu->kx_in || !mu->M_static || !mu->O)
+    return fail(h, MROM_EINVAL, "mrom_project_mu: K_in, x, kx, kx_in, M_static and O are required");
+  if (mu->n_o < 1 || mu->n_o > MROM_MAX_SNAPSHOTS || mu->ldo < n || !std::isfinite(mu->vol_B_mu))
+    return fail(h, MROM_EINVAL, "mrom_project_mu: O needs 1..MROM_MAX_SNAPSHOTS columns, ldo >= n, finite vol_B_mu");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project_mu: cudaSetDevice");
+  cudaStream_t str = h->stream;
+  auto grid_of = [](int64_t work) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(65535 * 4, (work + 255) / 256)); };
+  // dynamic basis U (n x r) from the snapshots at the sampled (omega, s)
+  const auto* Dp = static_cast<const double2*>(D);
+  int r = 0;
+  std::vector<double> sv;
+  std::vector<double2> wh;
+  st = gram_eig(h, Dp, ldd, n, n_cols, tol_sigma, std::min<int>(r_max > 0 ? r_max : MROM_MAX_R, MROM_MAX_R), &r, sv, wh);
+  if (st != MROM_OK) return st;
+  DevBuf Ubuf, Oc, Vbuf, Y, small;
+  e = cudaMalloc(&Ubuf.p, (size_t)n * r * sizeof(double2));
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project_mu: allocation");
+  st = apply_basis(h, Dp, ldd, n, n_cols, wh, r, static_cast<double2*>(Ubuf.p), r);
+  if (st != MROM_OK) return st;
+  const auto* U = static_cast<const double2*>(Ubuf.p);
+  // static basis V (n x m) from the static snapshots (real columns)
+  const int n_o = mu->n_o;
+  e = cudaMalloc(&Oc.p, (size_t)n * n_o * sizeof(double2));
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project_mu: allocation");
+  real_cols_kernel<<<grid_of(n * n_o), 256, 0, str>>>(mu->O, mu->ldo, n, n_o, static_cast<double2*>(Oc.p));
+  ++h->launches;
+  int m = 0;
+  st = gram_eig(h, static_cast<double2*>(Oc.p), n, n, n_o, mu->tol_static, MROM_MAX_STATIC, &m, sv, wh);
+  if (st != MROM_OK) return st;
+  e = cudaMalloc(&Vbuf.p, (size_t)n * m * sizeof(double2));
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project_mu: allocation");
+  st = apply_basis(h, static_cast<double2*>(Oc.p), n, n, n_o, wh, m, static_cast<double2*>(Vbuf.p), m);
+  if (st != MROM_OK) return st;
+  const auto* V = static_cast<const double2*>(Vbuf.p);
+  // K_in^r = U^H (K_in U)
+  const int wmax = std::max(r, m);
+  e = cudaMalloc(&Y.p, (size_t)n * wmax * sizeof(double2));
+  const size_t n_small = (size_t)r * r + (size_t)m * m + 3 * (size_t)m + 9;  // K_in^r, then V^H K V, V^H K x, x^T C x
+  if (e == cudaSuccess) e = cudaMalloc(&small.p, n_small * sizeof(double2));
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project_mu: allocation");
+  auto* Yp = static_cast<double2*>(Y.p);
+  auto* Kin_r = static_cast<double2*>(small.p);
+  spmm_csr_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, str>>>(mu->Kin_rowptr, mu->Kin_col, mu->Kin_val, n, U, r,
+                                                                     nullptr, Yp);
+  ++h->launches;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, Yp, r, 1, r, nullptr, 0, n, true, Kin_r, r);
+  if (e == cudaSuccess) {
+    symmetrize_kernel<<<(r * r + 255) / 256, 256, 0, str>>>(Kin_r, r);
+    ++h->launches;
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project_mu: K_in projection");
+  st = project_basis(h, fom, U, r, nullptr, out, Kin_r);
+  if (st != MROM_OK) return st;
+  mrom_rom* rom = *out;
+  auto bail = [&](cudaError_t err, const char* what) {
+    mrom_rom_free(rom);
+    *out = nullptr;
+    return cuda_fail(h, err, what);
+  };
+  // reduced static data, one device block owned by the object:
+  // Sout, Sin, Mv, cvv (m x m), kout, kin, cvx (m x 3), Bx (r x 3), BV (r x m)
+  const size_t mm = (size_t)m * m, m3 = 3 * (size_t)m;
+  const size_t n_mu = 4 * mm + 3 * m3 + 3 * (size_t)r + (size_t)r * m;
+  void* blk = nullptr;
+  e = cudaMalloc(&blk, n_mu * sizeof(double2));
+  if (e != cudaSuccess) return bail(e, "mrom_project_mu: allocation");
+  rom->mu_block = blk;
+  MuDev md{};
+  auto* q = static_cast<double2*>(blk);
+  double2* Sout = q; q += mm;
+  double2* Sin = q; q += mm;
+  double2* Mv = q; q += mm;
+  double2* cvv = q; q += mm;
+  double2* kout = q; q += m3;
+  double2* kin = q; q += m3;
+  double2* cvx = q; q += m3;
+  double2* Bx = q; q += 3 * (size_t)r;
+  double2* BV = q;
+  // scratch in the small block after K_in^r
+  double2* Sv = Kin_r + (size_t)r * r;        // m x m
+  double2* kv = Sv + mm;                     // m x 3
+  double2* cxx = kv + m3;                    // 3 x 3
+  DevBuf Xb, KXb, KXinb;
+  e = cudaMalloc(&Xb.p, (size_t)n * 3 * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&KXb.p, (size_t)n * 3 * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&KXinb.p, (size_t)n * 3 * sizeof(double2));
+  if (e != cudaSuccess) return bail(e, "mrom_project_mu: allocation");
+  auto* X3 = static_cast<double2*>(Xb.p);
+  auto* KX3 = static_cast<double2*>(KXb.p);
+  auto* KXin3 = static_cast<double2*>(KXinb.p);
+  complexify_o_kernel<<<grid_of(3 * n), 256, 0, str>>>(mu->x, n, X3);
+  complexify_o_kernel<<<grid_of(3 * n), 256, 0, str>>>(mu->kx, n, KX3);
+  complexify_o_kernel<<<grid_of(3 * n), 256, 0, str>>>(mu->kx_in, n, KXin3);
+  h->launches += 3;
+  e = cudaGetLastError();
+  // V^H K V and V^H K_in V (Hermitian), Sout = the difference
+  if (e == cudaSuccess) {
+    spmm_csr_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, str>>>(fom->K_rowptr, fom->K_col, fom->K_val, n, V, m,
+                                                                       nullptr, Yp);
+    ++h->launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = tall_gram(h, V, m, 1, m, Yp, m, 1, m, nullptr, 0, n, true, Sv, m);
+  if (e == cudaSuccess) {
+    spmm_csr_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, str>>>(mu->Kin_rowptr, mu->Kin_col, mu->Kin_val, n, V,
+                                                                       m, nullptr, Yp);
+    ++h->launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = tall_gram(h, V, m, 1, m, Yp, m, 1, m, nullptr, 0, n, true, Sin, m);
+  if (e == cudaSuccess) {
+    symmetrize_kernel<<<(int)((mm + 255) / 256), 256, 0, str>>>(Sv, m);
+    symmetrize_kernel<<<(int)((mm + 255) / 256), 256, 0, str>>>(Sin, m);
+    csub_kernel<<<(int)((mm + 255) / 256), 256, 0, str>>>(Sv, Sin, (int)mm, Sout);
+    h->launches += 3;
+    e = cudaGetLastError();
+  }
+  // V^H M_s V, V^H C V (Hermitian); V^H (K x), V^H (K_in x), V^H C x; U^H C x, U^H C V; x^T C x
+  if (e == cudaSuccess) e = tall_gram(h, V, m, 1, m, V, m, 1, m, mu->M_static, 1, n, true, Mv, m);
+  if (e == cudaSuccess) e = tall_gram(h, V, m, 1, m, V, m, 1, m, fom->C_diag, 1, n, true, cvv, m);
+  if (e == cudaSuccess) e = tall_gram(h, V, m, 1, m, KX3, 3, 1, 3, nullptr, 0, n, false, kv, 3);
+  if (e == cudaSuccess) e = tall_gram(h, V, m, 1, m, KXin3, 3, 1, 3, nullptr, 0, n, false, kin, 3);
+  if (e == cudaSuccess) {
+    csub_kernel<<<(int)((m3 + 255) / 256), 256, 0, str>>>(kv, kin, (int)m3, kout);
+    ++h->launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = tall_gram(h, V, m, 1, m, X3, 3, 1, 3, fom->C_diag, 1, n, false, cvx, 3);
+  if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, X3, 3, 1, 3, fom->C_diag, 1, n, false, Bx, 3);
+  if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, V, m, 1, m, fom->C_diag, 1, n, false, BV, m);
+  if (e == cudaSuccess) e = tall_gram(h, X3, 3, 1, 3, X3, 3, 1, 3, fom->C_diag, 1, n, true, cxx, 3);
+  std::vector<double2> cxx_h(9);
+  if (e == cudaSuccess) e = cudaMemcpy(cxx_h.data(), cxx, 9 * sizeof(double2), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bail(e, "mrom_project_mu: static projection");
+  const double a3 = fom->alpha * fom->alpha * fom->alpha;
+  md.Sout = Sout;
+  md.Sin = Sin;
+  md.Mv = Mv;
+  md.kout = kout;
+  md.kin = kin;
+  md.cvx = cvx;
+  md.cvv = cvv;
+  md.Bx = Bx;
+  md.BV = BV;
+  for (int k = 0; k < 9; ++k) md.cxx[k] = cxx_h[k].x;
+  md.nB = a3 * fom->vol_B;
+  md.mB = a3 * mu->vol_B_mu;
+  md.alpha3 = a3;
+  md.m = m;
+  md.r = r;
+  rom->mu = md;
+  // the object's B, c00 and N0 become those of the reduced static problem at s = 1
+  DevBuf inst;
+  e = cudaMalloc(&inst.p, sizeof(MuDev) + sizeof(RomDev) + 3 * (size_t)r * sizeof(double2) + 64);
+  if (e != cudaSuccess) return bail(e, "mrom_project_mu: allocation");
+  auto* dmu = static_cast<MuDev*>(inst.p);
+  auto* drec = reinterpret_cast<RomDev*>(dmu + 1);
+  auto* dscr = reinterpret_cast<double2*>(drec + 1);
+  MuDev md1 = md;
+  md1.Bdst = rom->B;
+  md1.dBdst = dscr;
+  e = cudaMemcpyAsync(dmu, &md1, sizeof(MuDev), cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess) e = launch_mu_instance(dmu, 1, m, nullptr, false, drec, nullptr, h->d_status, str);
+  RomDev rec{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&rec, drec, sizeof(RomDev), cudaMemcpyDeviceToHost, str);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(str);
+  if (e != cudaSuccess) return bail(e, "mrom_project_mu: static state at s = 1");
+  ++h->launches;
+  st = mrom_synchronize(h);
+  if (st != MROM_OK) {
+    mrom_rom_free(rom);
+    *out = nullptr;
+    return st;
+  }
+  std::copy(rec.c00, rec.c00 + 9, rom->c00);
+  std::copy(rec.N0, rec.N0 + 9, rom->N0);
+  if (r_out) *r_out = r;
+  if (m_out) *m_out = m;
   return MROM_OK;
 }

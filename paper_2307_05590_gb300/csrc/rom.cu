@@ -168,6 +168,7 @@ extern "C" int32_t mrom_rom_rank(mrom_rom_t rom) { return rom ? rom->r : 0; }
 
 extern "C" void mrom_rom_free(mrom_rom_t rom) {
   if (!rom) return;
+  if (rom->mu_block) cudaFree(rom->mu_block);
   if (rom->shared) {
     if (--rom->shared->refs == 0) {
       cudaFreeAsync(rom->shared->p, rom->shared->stream);

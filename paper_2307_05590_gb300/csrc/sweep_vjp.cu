@@ -11,6 +11,9 @@
 //   dL/domega = s_sigma Im tr((B + C P)^H Lambda) + sum gI_ij I_ij / omega,
 //   dL/ds_mu  = (Re tr((K_in P)^H Lambda) + a^3/4 sum gR_ij Re(p_i^H K_in p_j)) / s_mu^2,
 //   dL/ds_sigma = sum_omega (omega / s_sigma) dL/domega      (I(omega; s_sigma) = I(s_sigma omega; 1)).
+// With the PODP in mu_r, B, c00 and N0 depend on s_mu as well (dB, dc00, dN0 per object), adding
+//   Re tr(dB^H (w' a^3/4 P G_I - i w' Lambda)) + w' a^3/4 sum gI_ij dc00_ij + sum gR_ij dN0_ij
+// to dL/ds_mu (P is linear in B through A P = i w' B, and I holds B directly).
 // The factors are recomputed here instead of being stored per frequency.  This is the LU
 // route; the pencil route of the same product is pencil_vjp_kernel (pencil.cu).
 #include "mrom_internal.h"
@@ -23,7 +26,7 @@ namespace {
 
 constexpr int kT = 128;  // threads per CTA (4 CTAs per SM)
 constexpr int kW = kT / 32;
-constexpr int kRedV = 40;
+constexpr int kRedV = 48;
 
 __device__ __forceinline__ double2 c_msub(double2 c, double2 a, double2 b) {
   return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
@@ -47,13 +50,6 @@ __device__ __forceinline__ double2 c_recip(double2 a, int* status) {
   return make_double2(a.x * id, -a.y * id);
 }
 
-struct VjpObj {
-  const double2 *K, *Kin, *C, *Me, *B;
-  double c00[9], N0[9];
-  double alpha3;
-  int r;
-};
-
 // Task t of a routed table (header entry 0: .obj = entries, .w0 = total tasks; then {object,
 // frequencies per task, first task index, flags}).
 __device__ __forceinline__ SweepTask routed_task(const SweepTask* __restrict__ table, int n_w, int t) {
@@ -70,7 +66,7 @@ __device__ __forceinline__ SweepTask routed_task(const SweepTask* __restrict__ t
 
 template <bool ROUTED>
 __global__ void __launch_bounds__(kT, 4)
-sweep_vjp_kernel(const VjpObj* __restrict__ objs, const SweepTask* __restrict__ tasks, int n_tasks,
+sweep_vjp_kernel(const VjpDev* __restrict__ objs, const SweepTask* __restrict__ tasks, int n_tasks,
                  int* __restrict__ counter, const double* __restrict__ omega, int omega_stride,
                  const double* __restrict__ s_sigma, const double* __restrict__ s_mu,
                  const double* __restrict__ gR, const double* __restrict__ gI, double* __restrict__ g_omega,
@@ -87,7 +83,7 @@ sweep_vjp_kernel(const VjpObj* __restrict__ objs, const SweepTask* __restrict__ 
     __syncthreads();
     if (t >= n_tasks) break;
     const SweepTask task = ROUTED ? routed_task(tasks, n_w, t) : tasks[t];
-    const VjpObj& ob = objs[task.obj];
+    const VjpDev& ob = objs[task.obj];
     const int r = ob.r, S = task.nw, ld = r + 3;
     const size_t per_elems = (size_t)r * ld + 9 * (size_t)r;  // augmented system + y^K, y^C, y^Kin
     double2* sp = reinterpret_cast<double2*>(smem_raw);
@@ -275,13 +271,27 @@ sweep_vjp_kernel(const VjpObj* __restrict__ objs, const SweepTask* __restrict__ 
     }
     __syncthreads();
 
-    // ---- adjoint reductions: q 36: Im tr((B + C P)^H Lambda), q 37: Re tr((K_in P)^H Lambda)
-    for (int idx = tid; idx < S * 2; idx += kT) {
-      const int s = idx / 2, q = idx % 2;
+    // ---- adjoint reductions: q 36: Im tr((B + C P)^H Lambda), q 37: Re tr((K_in P)^H Lambda);
+    // with dB: q 38..46 Re(db_i^H p_j), q 47 Im tr(dB^H Lambda)
+    const int nq_adj = ob.dB ? 12 : 2;
+    for (int idx = tid; idx < S * nq_adj; idx += kT) {
+      const int s = idx / nq_adj, q = idx % nq_adj;
       const double2* a = Am + (size_t)s * per_elems;
       const double2* y = a + (size_t)r * ld;
       double acc = 0.0;
-      if (q == 0) {
+      if (q >= 2 && q < 11) {
+        const int i = (q - 2) / 3, j = (q - 2) % 3;
+        const double2* p = Pm + (size_t)s * r * 3;
+        for (int aa = 0; aa < r; ++aa) {
+          const double2 db = ob.dB[aa * 3 + i], pa = p[aa * 3 + j];
+          acc = fma(db.x, pa.x, fma(db.y, pa.y, acc));
+        }
+      } else if (q == 11) {
+        for (int e = 0; e < r * 3; ++e) {
+          const double2 lam = a[(e / 3) * ld + r + e % 3], db = ob.dB[e];
+          acc += db.x * lam.y - db.y * lam.x;  // Im(conj(db) lam)
+        }
+      } else if (q == 0) {
         for (int e = 0; e < r * 3; ++e) {
           const int aa = e / 3, k = e % 3;
           const double2 lam = a[aa * ld + r + k], yc = y[(1 * r + aa) * 3 + k], b = ob.B[aa * 3 + k];
@@ -318,7 +328,16 @@ sweep_vjp_kernel(const VjpObj* __restrict__ objs, const SweepTask* __restrict__ 
       }
       const double wr = w / ssig;  // the caller's omega
       g_omega[o] = ssig * red[36] + gI_dot_I / wr;
-      g_mu_part[o] = (red[37] + 0.25 * ob.alpha3 * gR_dot_HKin) / (smu * smu);
+      double gmu = (red[37] + 0.25 * ob.alpha3 * gR_dot_HKin) / (smu * smu);
+      if (ob.dB) {
+        double src = 0.0, stat = 0.0;
+        for (int ij = 0; ij < 9; ++ij) {
+          src = fma(red[38 + ij], g[9 + ij], src);
+          stat = fma(0.5 * g[9 + ij], 0.25 * ob.alpha3 * w * ob.dc00[ij], fma(0.5 * g[ij], ob.dN0[ij], stat));
+        }
+        gmu += 0.25 * ob.alpha3 * w * src + w * red[47] + stat;
+      }
+      g_mu_part[o] = gmu;
     }
   }
 }
@@ -383,7 +402,7 @@ extern "C" mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int
   int per_sm = 0;
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
   const size_t budget = std::min<size_t>(h->smem_optin, (size_t)per_sm / 4) - 2048;
-  std::vector<VjpObj> objs(n_obj);
+  std::vector<VjpDev> objs(n_obj);
   std::vector<SweepTask> tasks;
   std::vector<double> cost;
   std::vector<int2> lu_shape(n_obj);
@@ -392,7 +411,7 @@ extern "C" mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int
   const bool pencil = h->solver == MROM_SOLVER_AUTO;  // every object here has one shared basis
   for (int o = 0; o < n_obj; ++o) {
     const mrom_rom* m = roms[o];
-    VjpObj& d = objs[o];
+    VjpDev& d = objs[o];
     d.K = m->K;
     d.Kin = m->has_kin ? m->Kin : nullptr;
     d.C = m->C;
@@ -418,20 +437,65 @@ extern "C" mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int
       cost.push_back((8.0 * r * r * r / 3.0 + 40.0 * r * r) * nw);
     }
   }
+  // PODP in mu_r: objects with a reduced static problem get B(s_mu) (and dB/ds_mu when the
+  // permeability gradient is wanted) in per-call buffers, filled on the device below
+  const bool deriv = g_smu != nullptr;
+  std::vector<MuDev> mus(n_obj);
+  size_t mu_elems = 0;
+  int m_max = 0;
+  for (int o = 0; o < n_obj; ++o) {
+    if (roms[o]->mu.m > 0) {
+      mu_elems += (deriv ? 6 : 3) * (size_t)roms[o]->r;
+      m_max = std::max(m_max, roms[o]->mu.m);
+    }
+  }
+  void* mublk = nullptr;
+  MuDev* d_mus = nullptr;
+  if (m_max > 0) {
+    const size_t b_mus = (n_obj * sizeof(MuDev) + 255) / 256 * 256;
+    e = cudaMallocAsync(&mublk, b_mus + mu_elems * sizeof(double2), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_sweep_vjp: allocation");
+    d_mus = static_cast<MuDev*>(mublk);
+    auto* q = reinterpret_cast<double2*>(static_cast<char*>(mublk) + b_mus);
+    for (int o = 0; o < n_obj; ++o) {
+      if (roms[o]->mu.m <= 0) continue;
+      const int r = roms[o]->r;
+      mus[o] = roms[o]->mu;
+      mus[o].Bdst = q; q += 3 * (size_t)r;
+      mus[o].dBdst = deriv ? q : nullptr;
+      if (deriv) q += 3 * (size_t)r;
+      objs[o].B = mus[o].Bdst;
+      objs[o].dB = mus[o].dBdst;
+    }
+    e = cudaMemcpyAsync(d_mus, mus.data(), n_obj * sizeof(MuDev), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(mublk, h->stream);
+      return cuda_fail(h, e, "mrom_sweep_vjp: upload");
+    }
+  }
   // pencil route: tables (V^H K_in V when the permeability gradient is wanted), then
   // preparation and routing on the device
   PencilTables pt;
   std::vector<RomDev> recs;
   if (pencil) {
     recs.resize(n_obj);
-    for (int o = 0; o < n_obj; ++o) recs[o] = rom_record(roms[o]);
+    for (int o = 0; o < n_obj; ++o) {
+      recs[o] = rom_record(roms[o]);
+      if (roms[o]->mu.m > 0) {
+        recs[o].B = mus[o].Bdst;
+        recs[o].dB = mus[o].dBdst;
+      }
+    }
     std::vector<int> order_lu(n_obj);
     std::iota(order_lu.begin(), order_lu.end(), 0);
     std::stable_sort(order_lu.begin(), order_lu.end(), [&](int a, int b) { return recs[a].r > recs[b].r; });
     std::vector<int2> lu_info(n_obj);
     for (int k = 0; k < n_obj; ++k) lu_info[k] = lu_shape[order_lu[k]];
     const mrom_status ps = pencil_tables_create(h, recs, n_w, false, g_smu != nullptr, order_lu, lu_info, &pt);
-    if (ps != MROM_OK) return ps;
+    if (ps != MROM_OK) {
+      if (mublk) cudaFreeAsync(mublk, h->stream);
+      return ps;
+    }
   }
   std::vector<int> order(tasks.size());
   std::iota(order.begin(), order.end(), 0);
@@ -445,17 +509,19 @@ extern "C" mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lu_fn, kT, smem);
   if (e != cudaSuccess) {
     pencil_tables_destroy(&pt, h->stream);
+    if (mublk) cudaFreeAsync(mublk, h->stream);
     return cuda_fail(h, e, "mrom_sweep_vjp: configuration");
   }
   const int grid = (int)std::min<int64_t>(n_tasks_all, (int64_t)h->num_sms * std::max(occ, 1));
   const size_t ws_bytes = ws_elems * sizeof(double2) * grid;
   const size_t b_recs = pencil ? (n_obj * sizeof(RomDev) + 255) / 256 * 256 : 0;
-  const size_t bytes = ws_bytes + (size_t)n_obj * n_w * sizeof(double) + n_obj * sizeof(VjpObj) +
+  const size_t bytes = ws_bytes + (size_t)n_obj * n_w * sizeof(double) + n_obj * sizeof(VjpDev) +
                        sorted.size() * sizeof(SweepTask) + 16 + b_recs + 256;
   void* blk = nullptr;
   e = cudaMallocAsync(&blk, bytes, h->stream);
   if (e != cudaSuccess) {
     pencil_tables_destroy(&pt, h->stream);
+    if (mublk) cudaFreeAsync(mublk, h->stream);
     return cuda_fail(h, e, "mrom_sweep_vjp: allocation");
   }
   char* p = static_cast<char*>(blk);
@@ -465,17 +531,23 @@ extern "C" mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int
   p += (size_t)n_obj * n_w * sizeof(double);
   auto* d_recs = reinterpret_cast<RomDev*>(p);
   p += b_recs;
-  auto* d_objs = reinterpret_cast<VjpObj*>(p);
-  p += n_obj * sizeof(VjpObj);
+  auto* d_objs = reinterpret_cast<VjpDev*>(p);
+  p += n_obj * sizeof(VjpDev);
   auto* d_tasks = reinterpret_cast<SweepTask*>(p);
   p += sorted.size() * sizeof(SweepTask);
   auto* d_counter = reinterpret_cast<int*>(p);
-  e = cudaMemcpyAsync(d_objs, objs.data(), n_obj * sizeof(VjpObj), cudaMemcpyHostToDevice, h->stream);
+  e = cudaMemcpyAsync(d_objs, objs.data(), n_obj * sizeof(VjpDev), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess && !pencil)
     e = cudaMemcpyAsync(d_tasks, sorted.data(), sorted.size() * sizeof(SweepTask), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(int), h->stream);
-  if (e == cudaSuccess && pencil) {
+  if (e == cudaSuccess && pencil)
     e = cudaMemcpyAsync(d_recs, recs.data(), n_obj * sizeof(RomDev), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && d_mus) {  // B, c00, N0 (and derivatives) at each object's s_mu
+    e = launch_mu_instance(d_mus, n_obj, m_max, s_mu, deriv, pencil ? d_recs : nullptr, d_objs, h->d_status,
+                           h->stream);
+    ++h->launches;
+  }
+  if (e == cudaSuccess && pencil) {
     if (e == cudaSuccess) e = pencil_tables_prepare(h, pt, d_recs, omega, omega_stride, s_sigma, s_mu);
     if (e == cudaSuccess) e = pencil_tables_route(h, pt);
     if (e == cudaSuccess)
@@ -502,6 +574,7 @@ extern "C" mrom_status mrom_sweep_vjp(mrom_handle h, const mrom_rom_t* roms, int
   }
   cudaFreeAsync(blk, h->stream);
   pencil_tables_destroy(&pt, h->stream);
+  if (mublk) cudaFreeAsync(mublk, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_sweep_vjp: launch");
   ++h->launches;
   return MROM_OK;

@@ -1,0 +1,141 @@
+"""GPU parity of the PODP in mu_r (mrom_project_mu, mrom_sweep_vjp at per-object s_mu) with
+oracle/podp_mu.py.
+
+Both sides keep every snapshot direction (the smallest singular value ratios are 1e-5 for the
+12 dynamic and 2e-2 for the 6 static columns, far above the truncation), so the reduced spaces
+are the same and the signature, the static quantities and the gradients must agree to
+rounding at any (omega, s_mu), not only at the sampled ones; at the sampled ones both also
+reproduce the full-order model.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+S_SAMPLES = (1.0, 4.0)
+W_SAMPLES = (1e2, 1e4)
+
+
+@pytest.fixture(scope="module")
+def mrom():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_05590_gb300 import build
+    build.build()
+    import paper_2307_05590_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def case(mrom):
+    import torch
+    from oracle import podp_mu
+    from workloads import fit_problem, full_order_snapshots
+    from workloads.fit import Material
+    mat = (Material((0.25,) * 3, (0.75,) * 3, 5.96e7, 4.0),)
+    probs = {s: fit_problem(8, mat, mu_scale=s, mu_split=True) for s in S_SAMPLES}
+    D = [full_order_snapshots(probs[s], W_SAMPLES) for s in S_SAMPLES]
+    O = [probs[s].o_tilde for s in S_SAMPLES]
+    U, V = podp_mu.bases(D, O, tol_sigma=1e-7, tol_static=1e-7)
+    model = podp_mu.project(probs[1.0], U, V)
+    h = mrom.Handle(0)
+    p1 = probs[1.0]
+    fom = mrom.FullOrder.from_fit(p1)
+    mu = mrom.PermeabilityData.from_fit(p1, np.concatenate(O, axis=0), tol_static=1e-7)
+    cols = np.concatenate([np.transpose(Dl, (2, 0, 1)).reshape(-1, p1.N) for Dl in D], axis=0)
+    rom, r, m = mrom.mrom_project_mu(h, fom, mu, torch.as_tensor(np.ascontiguousarray(cols), device="cuda"),
+                                     tol_sigma=1e-7)
+    return dict(h=h, rom=rom, r=r, m=m, model=model, probs=probs, U=U, V=V)
+
+
+def test_ranks_match_oracle(case):
+    assert case["r"] == case["U"].shape[1] == 12
+    assert case["m"] == case["V"].shape[1] == 6
+
+
+def test_static_state_matches_oracle(mrom, case):
+    from oracle import podp_mu
+    for s in (0.6, 1.0, 2.2, 4.0, 11.0):
+        g = mrom.mrom_rom_mu_state(case["rom"], s)
+        o = podp_mu.static_state(case["model"], s)
+        for k in ("c00", "N0", "dc00", "dN0"):
+            sc = np.abs(o[k]).max()
+            assert np.abs(g[k] - o[k]).max() <= 1e-10 * sc, (s, k)
+        # B is basis-dependent; its Gram B^H C_r^-1 B is not
+        C = case["model"].C
+        sc = np.abs(o["B"].conj().T @ np.linalg.solve(C, o["B"])).max()
+        Cg = mrom.mrom_rom_get(case["rom"], with_gram=False)["C"]
+        dg = g["B"].conj().T @ np.linalg.solve(Cg, g["B"]) - o["B"].conj().T @ np.linalg.solve(C, o["B"])
+        assert np.abs(dg).max() <= 1e-8 * sc, s
+
+
+def _sweep(mrom, case, wo, s_mu, s_sigma, gR, gI, lu):
+    import torch
+    h = case["h"]
+    h.set_solver(lu=lu)
+    n = len(s_mu)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    R = torch.empty((n, wo.size, 3, 3), dtype=torch.float64, device="cuda")
+    I = torch.empty_like(R)
+    g_w = torch.empty((n, wo.size), dtype=torch.float64, device="cuda")
+    g_s = torch.empty(n, dtype=torch.float64, device="cuda")
+    g_m = torch.empty(n, dtype=torch.float64, device="cuda")
+    mrom.mrom_sweep_vjp(h, [case["rom"]] * n, t(wo), wo.size, t(gR), t(gI), g_w, g_ssigma=g_s, g_smu=g_m,
+                        s_sigma=t(s_sigma), s_mu=t(s_mu), R=R, I=I)
+    h.synchronize()
+    h.set_solver(lu=False)
+    return R.cpu().numpy(), I.cpu().numpy(), g_w.cpu().numpy(), g_s.cpu().numpy(), g_m.cpu().numpy()
+
+
+@pytest.mark.parametrize("lu", [False, True], ids=["auto", "lu"])
+def test_signature_and_gradients_match_oracle(mrom, case, lu):
+    from oracle import podp_mu
+    from workloads import log_omegas
+    model = case["model"]
+    wo = log_omegas(1e1, 1e5, 23)
+    s_mu = np.array([0.7, 1.0, 2.3, 4.0, 9.0])
+    s_sigma = np.array([1.0, 1.3, 0.8, 1.0, 2.0])
+    rng = np.random.default_rng(5)
+    gR = rng.standard_normal((s_mu.size, wo.size, 3, 3))
+    gI = rng.standard_normal((s_mu.size, wo.size, 3, 3))
+    R, I, g_w, g_s, g_m = _sweep(mrom, case, wo, s_mu, s_sigma, gR, gI, lu)
+    a3 = model.alpha ** 3
+    for k, (sm, ss) in enumerate(zip(s_mu, s_sigma)):
+        Rr, Ir = podp_mu.signature(model, wo, s_mu=sm, s_sigma=ss)
+        # per frequency: R against max |R~|, I against its term scale w' a^3/4 max |c00(s)|
+        # (I is a difference of terms of that size at high omega)
+        sR = np.abs(Rr).reshape(wo.size, -1).max(1)
+        sI = wo * ss * a3 / 4 * np.abs(podp_mu.static_state(model, sm)["c00"]).max()
+        eR = (np.abs(R[k] - Rr).reshape(wo.size, -1).max(1) / sR).max()
+        eI = (np.abs(I[k] - Ir).reshape(wo.size, -1).max(1) / sI).max()
+        assert eR <= 1e-10 and eI <= 1e-10, (k, eR, eI)
+        dR, dI = podp_mu.tangent_s_mu(model, wo, s_mu=sm, s_sigma=ss)
+        ref = float(np.sum(gR[k] * dR) + np.sum(gI[k] * dI))
+        scale = float(np.sum(np.abs(gR[k] * dR)) + np.sum(np.abs(gI[k] * dI)))
+        assert abs(g_m[k] - ref) <= 1e-8 * scale, (k, g_m[k], ref, scale)
+
+
+def test_sampled_parameters_reproduce_the_full_order_model(mrom, case):
+    from oracle import fom
+    wo = np.asarray(W_SAMPLES)
+    s_mu = np.asarray(S_SAMPLES)
+    z = np.zeros((s_mu.size, wo.size, 3, 3))
+    R, I, *_ = _sweep(mrom, case, wo, s_mu, np.ones(s_mu.size), z, z, False)
+    for k, s in enumerate(S_SAMPLES):
+        p = case["probs"][s]
+        Rf, If = fom.fmm_signature(p, wo)
+        Rf = Rf + p.N0[None]
+        sc = max(np.abs(Rf).max(), np.abs(If).max())
+        assert max(np.abs(R[k] - Rf).max(), np.abs(I[k] - If).max()) <= 1e-8 * sc
+
+
+def test_invalid_scale_is_refused(mrom, case):
+    import torch
+    with pytest.raises(mrom.MromError):
+        mrom.mrom_rom_mu_state(case["rom"], -1.0)
+    wo = np.array([1e3])
+    z = np.zeros((1, 1, 3, 3))
+    with pytest.raises(mrom.MromError):
+        _sweep(mrom, case, wo, np.array([0.0]), np.ones(1), z, z, True)
+    case["h"].set_solver(lu=False)
