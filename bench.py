@@ -345,6 +345,72 @@ def measure_c1_latency(m, h):
             "sweep_ms": 1e3 * ts, "total_ms": 1e3 * (tp + ts)}
 
 
+def measure_fom_solve(m, h, n_grid: int = 128, n_w: int = 2):
+    """mrom_fom_solve alone: the 3 n_w right-hand sides of n_w frequencies (log-spaced in
+    [1e1, 1e8]) on the n_grid^3 two-material grid, Jacobi-scaled residual 1e-12; per-iteration
+    rates from the iteration counts (the CSR K is read once per iteration for all columns)."""
+    import torch
+    from workloads import TWO_MATERIAL_C5, fit_problem, log_omegas
+    p = fit_problem(n_grid, TWO_MATERIAL_C5, static=False)
+    fom = m.FullOrder.from_fit(p)
+    ws = log_omegas(1e1, 1e8, n_w)
+    m.mrom_fom_solve(h, fom, ws[:1], tol=1e-6)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Q, its, res = m.mrom_fom_solve(h, fom, ws, tol=1e-12)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    nit = int(its.max())
+    nnz = int(p.K.nnz)
+    nc = 3 * n_w
+    flops = nit * nc * (4.0 * nnz + 40.0 * p.N)   # SpMV 4 per nonzero, ~40 per row in the vector kernels
+    return {"workload": f"mrom_fom_solve: {n_grid}^3 two-material FIT grid (N = {p.N}, nnz(K) = {nnz}), "
+                        f"{nc} right-hand sides at {n_w} frequencies in [1e1, 1e8]",
+            "seconds": sec, "iterations_max": nit, "iterations_min": int(its.min()),
+            "ms_per_iteration": sec * 1e3 / nit, "ms_per_column_iteration": sec * 1e3 / nit / nc,
+            "approx_fp64_tflops": flops / sec / 1e12, "scaled_residual_max": float(res.max())}
+
+
+def measure_adaptive_fom(m, h, n_grid: int = 128, ns0: int = 9, n_star: int = 2, max_k: int = 28,
+                         n_out: int = 4096):
+    """Algorithm 1 end to end on the device: mrom_adapt without a callback, so every full-order
+    snapshot of Eq. (9) is solved by mrom_fom_solve (COCG, Jacobi-scaled residual 1e-12), on the
+    n_grid^3 two-material grid (theta^(0) without the static correction, whose sparse solve at
+    this size is not built), 4096 outputs in [1e1, 1e8], shared basis, r <= 64.  Also times one
+    batched solve of the 3 x 9 initial right-hand sides."""
+    import torch
+    from workloads import TWO_MATERIAL_C5, fit_problem, log_omegas
+    p = fit_problem(n_grid, TWO_MATERIAL_C5, static=False)
+    wo = log_omegas(1e1, 1e8, n_out)
+    X = p.eps * p.M + wo[0] * p.C
+    fom = m.FullOrder.from_fit(p, X=X)
+    w0 = log_omegas(1e1, 1e8, ns0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Q, its, res = m.mrom_fom_solve(h, fom, w0, tol=1e-12)
+    t_solve = time.perf_counter() - t0
+    del Q
+    om = torch.as_tensor(wo, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rom, hist, k, snaps = m.mrom_adapt(h, fom, w0, None, None, om, tol_sigma=1e-6, tol_delta=1e-3,
+                                       n_star=n_star, max_k=max_k, r_max=64)
+    torch.cuda.synchronize()
+    total = time.perf_counter() - t0
+    r = rom.r
+    rom.close()
+    return {"workload": f"mrom_adapt with device snapshots: {n_grid}^3 two-material FIT grid (N = {p.N}), "
+                        f"{ns0} -> {len(snaps)} snapshots (+{n_star} per iteration), {n_out} output frequencies, "
+                        f"shared basis, r_max 64; full-order solves by mrom_fom_solve",
+            "iterations": int(k), "final_r": int(r), "seconds_total": total,
+            "seconds_per_iteration": total / max(1, k - 1),
+            "lambda_history": [float(x) for x in hist[~np.isnan(hist)]],
+            "lambda_over_B_last": float(hist[~np.isnan(hist)][-1]) / (p.alpha ** 3 * p.vol_B)
+            if np.any(~np.isnan(hist)) else None,
+            "initial_solve": {"rhs": 3 * ns0, "seconds": t_solve, "iterations_max": int(its.max()),
+                              "iterations_min": int(its.min()), "scaled_residual_max": float(res.max())}}
+
+
 def measure_adaptive(m, h, n_grid: int = 128, ns0: int = 9, n_star: int = 2, max_k: int = 28, n_out: int = 4096):
     """Algorithm 1 (mrom_adapt) on the n_grid^3 two-material FIT grid (128^3: N = 6.2M) with
     4096 output frequencies in [1e1, 1e8], shared basis, r <= 64.  The full-order solves are out
@@ -455,6 +521,11 @@ def main():
     ap.add_argument("--adaptive-only", action="store_true",
                     help="time mrom_adapt (Algorithm 1) on the two-material grid and print its record")
     ap.add_argument("--adaptive-grid", type=int, default=128)
+    ap.add_argument("--fom-solve-only", action="store_true", help="time mrom_fom_solve alone and print its record")
+    ap.add_argument("--fom-grid", type=int, default=128)
+    ap.add_argument("--fom-freqs", type=int, default=2)
+    ap.add_argument("--adaptive-fom", action="store_true",
+                    help="with --adaptive-only: solve the full-order snapshots on the device (no callback)")
     ap.add_argument("--projection", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--podp-mu", action=argparse.BooleanOptionalAction, default=True,
                     help="PODP in mu_r section (projection with the static reduction, instances over s_mu)")
@@ -485,7 +556,17 @@ def main():
         stream = torch.cuda.Stream(dev)
         h = m.Handle(local_rank, stream.cuda_stream)
         if rank == 0:
-            print(json.dumps({"adaptive": measure_adaptive(m, h, n_grid=args.adaptive_grid)}), flush=True)
+            fn = measure_adaptive_fom if args.adaptive_fom else measure_adaptive
+            print(json.dumps({"adaptive": fn(m, h, n_grid=args.adaptive_grid)}), flush=True)
+        h.close()
+        return
+
+    if args.fom_solve_only:
+        stream = torch.cuda.Stream(dev)
+        h = m.Handle(local_rank, stream.cuda_stream)
+        if rank == 0:
+            print(json.dumps({"fom_solve": measure_fom_solve(m, h, n_grid=args.fom_grid, n_w=args.fom_freqs)}),
+                  flush=True)
         h.close()
         return
 

@@ -238,6 +238,20 @@ int32_t mrom_rom_static_rank(mrom_rom_t rom);
 mrom_status mrom_rom_mu_state(mrom_rom_t rom, double s_mu, void* B, double* c00, double* N0, void* dB, double* dc00,
                               double* dN0);
 
+/* Full-order snapshots on the device: q_i(omega_k) solving Eq. (9),
+ * (K + eps M - i omega_k C) q_i = i omega_k C o_i, for i = 1..3 and the n_w frequencies omega
+ * (host), by the conjugate orthogonal conjugate gradient method (A is complex symmetric) with
+ * Jacobi preconditioning, all 3 n_w right-hand sides iterated together (3 n_w <=
+ * MROM_MAX_FOM_RHS).  Column 3 k + i of Q (device, complex128, column c at Q + c * ldq,
+ * ldq >= n) receives q_i(omega_k), the snapshot layout of mrom_project.  A column stops when
+ * ||D^-1/2 r|| <= tol ||D^-1/2 b|| (D = diag A); iters and res (host, 3 n_w each, or NULL)
+ * receive the iteration counts and final scaled residuals.  MROM_ENOTCONVERGED if a column
+ * did not reach tol within max_iter iterations or broke down (Q then holds the last iterates).
+ * Temporaries: 5 n (3 n_w) complex128 and n (3 n_w) float64.  Synchronous. */
+#define MROM_MAX_FOM_RHS 48
+mrom_status mrom_fom_solve(mrom_handle h, const mrom_fom* fom, const double* omega, int32_t n_w, double tol,
+                           int32_t max_iter, void* Q, int64_t ldq, int32_t* iters, double* res);
+
 /* Adaptive PODP, Algorithm 1 (Sect. 4.4), with one basis for the three directions.
  * Starting from ns0 >= 2 snapshots at omega0 (host, ns0 values) with their
  * 3 * ns0 full-order solution columns in D0 (length n each, column c at
@@ -257,7 +271,9 @@ mrom_status mrom_rom_mu_state(mrom_rom_t rom, double s_mu, void* B, double* c00,
  * callback receives n_new frequencies (host, ascending) and a HOST buffer of
  * 3 * n_new * n complex128 to fill: column j * 3 + i holds q_i(omega_new[j])
  * (Eq. (9)) at offset (j * 3 + i) * n; it returns 0 on success (anything else
- * stops the loop with MROM_ECALLBACK).  Outputs: the final reduced object
+ * stops the loop with MROM_ECALLBACK).  With cb NULL the library computes every
+ * full-order snapshot itself with mrom_fom_solve (tolerance 1e-12), and D0 may be NULL
+ * (then the initial snapshots are solved too).  Outputs: the final reduced object
  * (*out), Lambda after each certificate evaluation (lambda_hist, host, max_k
  * values, or NULL), the final k (k_done), the sorted snapshot frequencies
  * (omega_snap_out, host, ns0 + n_star (max_k - 1) values, or NULL) and their

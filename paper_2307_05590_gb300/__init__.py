@@ -24,7 +24,7 @@ __all__ = [
     "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune", "mrom_sweep_noalloc",
     "FullOrder", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "MromSweep", "signature",
     "mrom_sweep_mixed", "mrom_project_dirs", "mrom_invariants", "PermeabilityData", "mrom_project_mu",
-    "mrom_rom_mu_state",
+    "mrom_rom_mu_state", "mrom_fom_solve",
 ]
 
 
@@ -441,6 +441,22 @@ def mrom_rom_get(rom: ReducedObject, with_gram: bool = True) -> dict:
     return out
 
 
+def mrom_fom_solve(h: Handle, fom: FullOrder, omegas, *, tol: float = 1e-12, max_iter: int = 100000):
+    """Full-order snapshots q_i(omega_k) on the device (COCG, Jacobi preconditioning).
+    Returns (Q device (3 n_w, n) complex128 with row 3 k + i = q_i(omega_k), iterations, residuals)."""
+    import torch
+    w = np.ascontiguousarray(omegas, dtype=np.float64)
+    n = int(fom.desc.n)
+    Q = torch.empty((3 * w.size, n), dtype=torch.complex128, device="cuda")
+    its = np.zeros(3 * w.size, dtype=np.int32)
+    res = np.zeros(3 * w.size)
+    _abi.check(lib().mrom_fom_solve(h.ptr, ctypes.byref(fom.desc), w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    int(w.size), float(tol), int(max_iter), _ptr(Q), n,
+                                    its.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                    res.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), h.ptr)
+    return Q, its, res
+
+
 def mrom_adapt(h: Handle, fom: FullOrder, omega0, D0, snapshot_fn, omega_out, *, tol_sigma: float = 1e-6,
                tol_delta: float = 1e-3, n_star: int = 2, max_k: int = 10, r_max: int = 0, theta: float = 0.0):
     """Algorithm 1 on the GPU (theta > 0: the variant with a threshold, at most n_star new
@@ -448,7 +464,8 @@ def mrom_adapt(h: Handle, fom: FullOrder, omega0, D0, snapshot_fn, omega_out, *,
 
     omega0: initial snapshot frequencies (numpy); D0: device (3 * ns0, n) complex128
     solution columns; snapshot_fn(omegas) -> numpy (3, n, len(omegas)) full-order
-    solutions (called from the library for every refinement); omega_out: device
+    solutions (called from the library for every refinement), or None: the library solves
+    every snapshot itself (mrom_fom_solve) and D0 may be None too; omega_out: device
     float64, strictly increasing.  Returns (ReducedObject, Lambda history, k,
     sorted snapshot frequencies).
     """
@@ -468,7 +485,8 @@ def mrom_adapt(h: Handle, fom: FullOrder, omega0, D0, snapshot_fn, omega_out, *,
             errors.append(exc)
             return 1
 
-    cb = _abi.SNAPSHOT_CB(_cb)
+    # a NULL callback (SNAPSHOT_CB()): the library solves the snapshots itself (mrom_fom_solve)
+    cb = _abi.SNAPSHOT_CB(_cb) if snapshot_fn is not None else _abi.SNAPSHOT_CB()
     opts = _abi.mrom_adapt_opts(float(tol_sigma), float(tol_delta), int(n_star), int(max_k), int(r_max),
                                   float(theta))
     hist = np.full(max_k, np.nan)

@@ -19,7 +19,7 @@ EXPORTS = [
     "mrom_sweep_noalloc", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "mrom_sweep_mixed",
     "mrom_project_dirs", "mrom_set_projection_precision", "mrom_set_solver", "mrom_plan_solver_counts",
     "mrom_plan_timing", "mrom_rom_from_reduced_batch", "mrom_invariants", "mrom_project_mu",
-    "mrom_rom_static_rank", "mrom_rom_mu_state",
+    "mrom_rom_static_rank", "mrom_rom_mu_state", "mrom_fom_solve",
 ]
 
 
@@ -115,6 +115,9 @@ def _declare(L):
         "mrom_rom_from_reduced": (ctypes.c_int, [vp, ctypes.POINTER(mrom_reduced_desc), ctypes.POINTER(vp)]),
         "mrom_rom_rank": (i32, [vp]),
         "mrom_rom_static_rank": (i32, [vp]),
+        "mrom_fom_solve": (ctypes.c_int, [vp, ctypes.POINTER(mrom_fom), ctypes.POINTER(ctypes.c_double), i32,
+                                          ctypes.c_double, i32, vp, i64, ctypes.POINTER(i32),
+                                          ctypes.POINTER(ctypes.c_double)]),
         "mrom_rom_mu_state": (ctypes.c_int, [vp, ctypes.c_double, vp, dp, dp, vp, dp, dp]),
         "mrom_project_mu": (ctypes.c_int, [vp, ctypes.POINTER(mrom_fom), ctypes.POINTER(mrom_fom_mu), vp, i64, i32,
                                            ctypes.c_double, i32, ctypes.POINTER(vp), ctypes.POINTER(i32),

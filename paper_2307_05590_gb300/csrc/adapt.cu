@@ -10,6 +10,11 @@
 #include <numeric>
 
 namespace mrom {
+
+// Full-order solves of the adaptive loop when no callback is given: Jacobi-scaled residual
+// below 1e-12 (R and I then agree with a direct solve to about 1e-13 on the FIT grids)
+constexpr double kAdaptSolveTol = 1e-12;
+constexpr int kAdaptSolveMaxIter = 100000;
 namespace {
 
 __device__ __forceinline__ bool in_sorted(const double* __restrict__ a, int n, double x) {
@@ -87,7 +92,7 @@ extern "C" mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const doub
                                   int32_t n_out, const mrom_adapt_opts* opts, mrom_rom_t* out, double* lambda_hist,
                                   int32_t* k_done, double* omega_snap_out, int32_t* ns_out) {
   if (!h) return MROM_EINVAL;
-  if (!fom || !omega0 || ns0 < 2 || !D0 || !cb || !omega_out || n_out < 2 || !opts || !out)
+  if (!fom || !omega0 || ns0 < 2 || (!D0 && cb) || !omega_out || n_out < 2 || !opts || !out)
     return fail(h, MROM_EINVAL, "mrom_adapt: bad arguments");
   if (!fom->X_diag) return fail(h, MROM_EINVAL, "mrom_adapt: the certificate needs fom->X_diag");
   if (opts->n_star < 1 || opts->max_k < 1 || !(opts->tol_delta >= 0.0))
@@ -115,9 +120,24 @@ extern "C" mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const doub
   if (e == cudaSuccess) e = cudaMalloc(&snaps_d.p, ns_cap * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&lam_d.p, ns_cap * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&arg_d.p, ns_cap * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemcpyAsync(Dbuf.p, D0, (size_t)3 * ns0 * n * sizeof(double2), cudaMemcpyDefault, st);
+  if (e == cudaSuccess && D0)
+    e = cudaMemcpyAsync(Dbuf.p, D0, (size_t)3 * ns0 * n * sizeof(double2), cudaMemcpyDefault, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_adapt: allocation");
   auto* Dcols = static_cast<double2*>(Dbuf.p);
+  // without a callback the library solves the full-order snapshots itself (mrom_fom_solve)
+  auto gpu_snapshots = [&](const double* w, int nw, double2* dst) -> mrom_status {
+    for (int k0 = 0; k0 < nw; k0 += MROM_MAX_FOM_RHS / 3) {
+      const int nk = std::min(nw - k0, MROM_MAX_FOM_RHS / 3);
+      const mrom_status fs = fom_solve(h, fom, w + k0, nk, kAdaptSolveTol, kAdaptSolveMaxIter,
+                                       dst + (size_t)3 * k0 * n, n, nullptr, nullptr);
+      if (fs != MROM_OK) return fs;
+    }
+    return MROM_OK;
+  };
+  if (!D0) {
+    const mrom_status fs = gpu_snapshots(omega0, ns0, Dcols);
+    if (fs != MROM_OK) return fs;
+  }
   std::vector<double2> stage;  // host staging for the callback's snapshots
   std::vector<double> snaps(omega0, omega0 + ns0);
   const double b_alpha = fom->alpha * fom->alpha * fom->alpha * fom->vol_B;
@@ -186,15 +206,23 @@ extern "C" mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const doub
     std::sort(fresh.begin(), fresh.end());
     const int nn = (int)fresh.size();
     // full-order snapshots from the caller, uploaded after the columns already held
-    stage.assign((size_t)3 * nn * n, make_double2(0.0, 0.0));
-    if (cb(user, nn, fresh.data(), stage.data()) != 0) {
-      mrom_rom_free(rom);
-      return fail(h, MROM_ECALLBACK, "mrom_adapt: snapshot callback returned an error");
-    }
-    e = cudaMemcpy(Dcols + (size_t)3 * ns * n, stage.data(), stage.size() * sizeof(double2), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      mrom_rom_free(rom);
-      return cuda_fail(h, e, "mrom_adapt: snapshot upload");
+    if (!cb) {
+      const mrom_status fs = gpu_snapshots(fresh.data(), nn, Dcols + (size_t)3 * ns * n);
+      if (fs != MROM_OK) {
+        mrom_rom_free(rom);
+        return fs;
+      }
+    } else {
+      stage.assign((size_t)3 * nn * n, make_double2(0.0, 0.0));
+      if (cb(user, nn, fresh.data(), stage.data()) != 0) {
+        mrom_rom_free(rom);
+        return fail(h, MROM_ECALLBACK, "mrom_adapt: snapshot callback returned an error");
+      }
+      e = cudaMemcpy(Dcols + (size_t)3 * ns * n, stage.data(), stage.size() * sizeof(double2), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        mrom_rom_free(rom);
+        return cuda_fail(h, e, "mrom_adapt: snapshot upload");
+      }
     }
     snaps.insert(snaps.end(), fresh.begin(), fresh.end());
     ns += nn;

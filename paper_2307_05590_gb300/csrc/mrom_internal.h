@@ -276,6 +276,11 @@ cudaError_t launch_pencil_sweep(const RomDev* objs, const PencilDev* pens, const
 // Builds the RomDev record of an object (api.cu).
 RomDev rom_record(const mrom_rom* m);
 
+// Full-order snapshots by COCG (fom_solve.cu): columns 3 k + i of Q (column c at Q + c ldq)
+// receive q_i(omega[k]) for k < n_w (omega on the host).
+mrom_status fom_solve(mrom_ctx* h, const mrom_fom* fom, const double* omega_host, int n_w, double tol, int max_iter,
+                      double2* Q, int64_t ldq, int32_t* iters_out, double* res_out);
+
 // PODP in mu_r (podp_mu.cu): for every object o with mus[o].m > 0, the static state at
 // s_mu[o] (1 if s_mu is null): B(s) into mus[o].Bdst, dB/ds into mus[o].dBdst (when deriv), and
 // c00, N0 (and dc00, dN0 when deriv) into recs[o] and vjp[o] (either array may be null).
