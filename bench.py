@@ -237,27 +237,29 @@ def measure_projection(m, h, n_grid: int = 96, n_s: int = 32):
 
 def measure_podp_mu(m, h, stream, n_grid=16, n_inst=1000, n_w=2000):
     """PODP in mu_r: a magnetic cube (mu_r = 16 at s = 1) projected once from full-order snapshots
-    at 3 permeability scales x 4 frequencies (mrom_project_mu), then n_inst instances at
+    (solved on the device by mrom_fom_solve) at 3 permeability scales x 4 frequencies
+    (mrom_project_mu), then n_inst instances at
     s_mu log-uniform in [1/4, 4] and s_sigma = 1 over n_w frequencies in [1e1, 1e6], values and
     the permeability gradient (mrom_sweep_vjp, B, c00 and N0 following s_mu).  Accuracy: two
     instances between the samples against full-order solves (the method's error, not parity)."""
     import torch
     from oracle import fom as ofom
-    from workloads import fit_problem, full_order_snapshots, log_omegas
+    from workloads import fit_problem, log_omegas
     from workloads.fit import Material
     mat = (Material((0.375,) * 3, (0.625,) * 3, 5.96e6, 16.0),)
-    S = (0.25, 1.0, 4.0)
+    S = (0.25, 1.0, 4.0)  # sampled permeability scales
     Ws = log_omegas(1e1, 1e6, 4)
     probs = {s: fit_problem(n_grid, mat, mu_scale=s, mu_split=True) for s in S}
+    # dynamic snapshots by the device solver (mrom_fom_solve), one call per sampled scale
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    D = [full_order_snapshots(probs[s], Ws) for s in S]
+    dcols = torch.cat([m.mrom_fom_solve(h, m.FullOrder.from_fit(probs[s]), Ws, tol=1e-12)[0] for s in S], dim=0)
+    torch.cuda.synchronize()
     t_fom = time.perf_counter() - t0
     p1 = probs[1.0]
     O = np.concatenate([probs[s].o_tilde for s in S], axis=0)
-    cols = np.concatenate([np.transpose(Dl, (2, 0, 1)).reshape(-1, p1.N) for Dl in D], axis=0)
     fom = m.FullOrder.from_fit(p1)
     mu = m.PermeabilityData.from_fit(p1, O, tol_static=1e-8)
-    dcols = torch.as_tensor(np.ascontiguousarray(cols), device="cuda")
     m.mrom_project_mu(h, fom, mu, dcols, tol_sigma=1e-8)[0].close()  # warm-up
     t0 = time.perf_counter()
     rom, r, mm = m.mrom_project_mu(h, fom, mu, dcols, tol_sigma=1e-8)
@@ -307,7 +309,7 @@ def measure_podp_mu(m, h, stream, n_grid=16, n_inst=1000, n_w=2000):
     return {"workload": f"PODP in mu_r: {n_grid}^3 FIT cube (N = {p1.N}), mu_r = 16 x s, sigma = 5.96e6; "
                         f"snapshots at s in {list(S)} x 4 omega in [1e1, 1e6]; {n_inst} instances with s_mu "
                         f"log-uniform in [1/4, 4] x {n_w} omega in [1e1, 1e6], values and dL/ds_mu",
-            "r": r, "m_static": mm, "project_seconds": t_proj, "full_order_snapshot_seconds_cpu": t_fom,
+            "r": r, "m_static": mm, "project_seconds": t_proj, "full_order_snapshot_seconds_device": t_fom,
             "ms_per_step": ms, "value": n_inst * n_w / (ms * 1e-3),
             "unit": "(s_mu, omega) evaluations/s with the permeability gradient",
             "max_rel_error_vs_full_order_between_samples": max(err)}
@@ -750,27 +752,17 @@ def main():
     # ---- end to end through the public API from pinned host buffers
     e2e = None
     if args.e2e_steps > 0:
-        pinned = []
-        h2d = 0
-        for o in objs:
-            arrs = {}
-            for name in ("K", "C", "B", "G", "K_in"):
-                a = getattr(o, name)
-                t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-                arrs[name] = t
-                h2d += t.numel() * t.element_size()
-            arrs["c00"] = torch.from_numpy(np.ascontiguousarray(o.c00)).pin_memory()
-            h2d += 72
-            pinned.append(arrs)
+        # the dictionary in one pinned host buffer (mrom_rom_from_packed copies it in one transfer)
+        packed = m.PackedDictionary([dict(r=o.r, K=o.K, C=o.C, B=o.B, c00=o.c00, G=o.G, K_in=o.K_in,
+                                          alpha=o.alpha, alpha_lb=o.alpha_lb, vol_B=o.vol_B) for o in objs])
+        h2d = packed.nbytes + 72 * len(objs)
         om_host = torch.from_numpy(wo.copy()).pin_memory()
         h2d += om_host.numel() * 8
         outs = [torch.empty(shape, dtype=torch.float64).pin_memory() for _ in range(3)]
         d2h = 3 * int(np.prod(shape)) * 8
 
         def e2e_step():
-            rr = m.ReducedObject.batch(h, [dict(r=o.r, K=p["K"], C=p["C"], B=p["B"], c00=p["c00"], G=p["G"],
-                                                K_in=p["K_in"], alpha=o.alpha, alpha_lb=o.alpha_lb, vol_B=o.vol_B)
-                                           for o, p in zip(objs, pinned)])
+            rr = m.ReducedObject.from_packed(h, packed)
             pl = m.Plan(h, rr, args.n_w)
             omd = om_host.to(dev, non_blocking=True)
             pl.sweep(omd, R, I, D)

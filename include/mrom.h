@@ -136,6 +136,32 @@ mrom_status mrom_rom_from_reduced(mrom_handle h, const mrom_reduced_desc* desc, 
  * failing object, and on any error no object is created.  1 <= n_obj <= 65535. */
 mrom_status mrom_rom_from_reduced_batch(mrom_handle h, int32_t n_obj, const mrom_reduced_desc* descs,
                                         mrom_rom_t* out);
+
+/* One object of a packed dictionary (host record).  Its region at byte offset `offset`
+ * (a multiple of 16) of the packed buffer holds, complex128 row-major and back to back:
+ * K (r x r), K_in (r x r, if has_kin), C (r x r), Me (r x r, if has_me), B (r x 3),
+ * G ((2r+3)^2, if has_gram) -- the arrays of mrom_reduced_desc with one basis shared by the
+ * directions.  N0 all zero for none. */
+typedef struct {
+  int32_t r;
+  int32_t has_kin;
+  int32_t has_me;
+  int32_t has_gram;
+  int64_t offset;
+  double c00[9];
+  double N0[9];
+  double alpha;
+  double alpha_lb;
+  double vol_B;
+} mrom_packed_obj;
+
+/* As mrom_rom_from_reduced_batch for a dictionary held in one buffer (packed: host -- pinned
+ * for speed -- or device, `bytes` long): one copy of the whole buffer into one device
+ * allocation shared by the objects, the Gram splits of all objects in one launch and one
+ * validity check, so the cost does not grow with one copy per array.  Regions must lie inside
+ * the buffer.  Synchronous. */
+mrom_status mrom_rom_from_packed(mrom_handle h, int32_t n_obj, const mrom_packed_obj* objs, const void* packed,
+                                 size_t bytes, mrom_rom_t* out);
 /* Basis size r of an object (per direction); 0 on a null object. */
 int32_t mrom_rom_rank(mrom_rom_t rom);
 void mrom_rom_free(mrom_rom_t rom);

@@ -24,7 +24,7 @@ __all__ = [
     "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune", "mrom_sweep_noalloc",
     "FullOrder", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "MromSweep", "signature",
     "mrom_sweep_mixed", "mrom_project_dirs", "mrom_invariants", "PermeabilityData", "mrom_project_mu",
-    "mrom_rom_mu_state", "mrom_fom_solve",
+    "mrom_rom_mu_state", "mrom_fom_solve", "PackedDictionary",
 ]
 
 
@@ -143,6 +143,16 @@ class ReducedObject:
                 for k in range(len(items))]
 
     @classmethod
+    def from_packed(cls, handle: Handle, packed):
+        """mrom_rom_from_packed: the objects of a PackedDictionary (one copy of its buffer)."""
+        n = len(packed.entries)
+        out = (ctypes.c_void_p * n)()
+        _abi.check(lib().mrom_rom_from_packed(handle.ptr, n, packed.entries, _ptr(packed.buffer),
+                                              int(packed.nbytes), out), handle.ptr)
+        return [cls._wrap(handle, ctypes.c_void_p(out[k]), int(packed.entries[k].r), bool(packed.entries[k].has_gram))
+                for k in range(n)]
+
+    @classmethod
     def from_workload_batch(cls, handle: Handle, objs, *, with_cert: bool = True):
         """Batched from_workload (one device allocation for the whole dictionary)."""
         return cls.batch(handle, [dict(r=o.r, K=o.K, C=o.C, B=o.B, c00=o.c00, G=o.G if with_cert else None,
@@ -194,6 +204,54 @@ def _rom_array(objs):
     for k, o in enumerate(objs):
         arr[k] = o.ptr.value
     return arr
+
+
+class PackedDictionary:
+    """A dictionary laid out for mrom_rom_from_packed: every object's K, [K_in], C, [Me], B, [G]
+    (complex128 row-major) back to back at 16-byte aligned offsets of one host buffer (pinned
+    when pin=True and torch is available), with the per-object records."""
+
+    def __init__(self, items, *, pin: bool = True):
+        items = list(items)
+        self.entries = (_abi.mrom_packed_obj * len(items))()
+        parts, off = [], 0
+        for e, it in zip(self.entries, items):
+            r = int(it["r"])
+            arrs = [np.ascontiguousarray(it["K"], dtype=np.complex128)]
+            if it.get("K_in") is not None:
+                arrs.append(np.ascontiguousarray(it["K_in"], dtype=np.complex128))
+            arrs.append(np.ascontiguousarray(it["C"], dtype=np.complex128))
+            if it.get("Me") is not None:
+                arrs.append(np.ascontiguousarray(it["Me"], dtype=np.complex128))
+            arrs.append(np.ascontiguousarray(it["B"], dtype=np.complex128))
+            if it.get("G") is not None:
+                arrs.append(np.ascontiguousarray(it["G"], dtype=np.complex128))
+            e.r, e.offset = r, off
+            e.has_kin, e.has_me, e.has_gram = (int(it.get(k) is not None) for k in ("K_in", "Me", "G"))
+            e.c00[:] = [float(v) for v in np.asarray(it["c00"], dtype=np.float64).ravel()]
+            e.N0[:] = [float(v) for v in np.asarray(it.get("N0", np.zeros(9)), dtype=np.float64).ravel()]
+            e.alpha = float(it.get("alpha", 1.0))
+            e.alpha_lb = float(it.get("alpha_lb", 1.0 / np.sqrt(2.0)))
+            e.vol_B = float(it.get("vol_B", 1.0))
+            for a in arrs:
+                parts.append((off, a))
+                off += a.nbytes
+            off = (off + 15) // 16 * 16
+        self.nbytes = off
+        host = None
+        if pin:
+            try:
+                import torch
+                host = torch.empty(off, dtype=torch.uint8).pin_memory()
+                view = host.numpy()
+            except Exception:  # no torch / no CUDA for pinning: pageable buffer
+                host = None
+        if host is None:
+            view = np.empty(off, dtype=np.uint8)
+            host = view
+        for o, a in parts:
+            view[o:o + a.nbytes] = a.view(np.uint8).ravel()
+        self.buffer = host
 
 
 class Plan:

@@ -19,7 +19,7 @@ EXPORTS = [
     "mrom_sweep_noalloc", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "mrom_sweep_mixed",
     "mrom_project_dirs", "mrom_set_projection_precision", "mrom_set_solver", "mrom_plan_solver_counts",
     "mrom_plan_timing", "mrom_rom_from_reduced_batch", "mrom_invariants", "mrom_project_mu",
-    "mrom_rom_static_rank", "mrom_rom_mu_state", "mrom_fom_solve",
+    "mrom_rom_static_rank", "mrom_rom_mu_state", "mrom_fom_solve", "mrom_rom_from_packed",
 ]
 
 
@@ -44,6 +44,21 @@ class mrom_fom(ctypes.Structure):
         ("alpha_lb", ctypes.c_double),
         ("vol_B", ctypes.c_double),
         ("N0", ctypes.c_void_p),
+    ]
+
+
+class mrom_packed_obj(ctypes.Structure):
+    _fields_ = [
+        ("r", ctypes.c_int32),
+        ("has_kin", ctypes.c_int32),
+        ("has_me", ctypes.c_int32),
+        ("has_gram", ctypes.c_int32),
+        ("offset", ctypes.c_int64),
+        ("c00", ctypes.c_double * 9),
+        ("N0", ctypes.c_double * 9),
+        ("alpha", ctypes.c_double),
+        ("alpha_lb", ctypes.c_double),
+        ("vol_B", ctypes.c_double),
     ]
 
 
@@ -115,6 +130,8 @@ def _declare(L):
         "mrom_rom_from_reduced": (ctypes.c_int, [vp, ctypes.POINTER(mrom_reduced_desc), ctypes.POINTER(vp)]),
         "mrom_rom_rank": (i32, [vp]),
         "mrom_rom_static_rank": (i32, [vp]),
+        "mrom_rom_from_packed": (ctypes.c_int, [vp, i32, ctypes.POINTER(mrom_packed_obj), vp, ctypes.c_size_t,
+                                                ctypes.POINTER(vp)]),
         "mrom_fom_solve": (ctypes.c_int, [vp, ctypes.POINTER(mrom_fom), ctypes.POINTER(ctypes.c_double), i32,
                                           ctypes.c_double, i32, vp, i64, ctypes.POINTER(i32),
                                           ctypes.POINTER(ctypes.c_double)]),

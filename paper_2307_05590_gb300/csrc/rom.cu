@@ -204,6 +204,34 @@ __global__ void gather_gss_kernel(const double2* const* __restrict__ G, const in
   }
 }
 
+// Gram split of many objects in one launch (blockIdx.y = object; objects without G skip).
+struct SplitJob {
+  const double2* G;
+  double2 *GKK, *GCC, *GSk, *gsK, *gsC;
+  int r, pad;
+};
+
+__global__ void split_gram_batch_kernel(const SplitJob* __restrict__ jobs) {
+  const SplitJob j = jobs[blockIdx.y];
+  if (!j.G) return;
+  const int r = j.r, n = 2 * r + 3, total = r * r;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total + 3 * r; idx += gridDim.x * blockDim.x) {
+    if (idx < total) {
+      const int a = idx / r, b = idx - (idx / r) * r;
+      const int ka = 3 + a, kb = 3 + b, ca = 3 + r + a, cb = 3 + r + b;
+      j.GKK[idx] = j.G[(size_t)ka * n + kb];
+      j.GCC[idx] = j.G[(size_t)ca * n + cb];
+      const double2 ck = j.G[(size_t)ca * n + kb], kc = j.G[(size_t)ka * n + cb];
+      j.GSk[idx] = make_double2(ck.x - kc.x, ck.y - kc.y);
+    } else {
+      const int e = idx - total;
+      const int i = e / r, q = e - (e / r) * r;
+      j.gsK[e] = j.G[(size_t)i * n + 3 + q];
+      j.gsC[e] = j.G[(size_t)i * n + 3 + r + q];
+    }
+  }
+}
+
 mrom_status check_desc(mrom_ctx* h, const mrom_reduced_desc* d, const char* who) {
   const std::string w(who);
   const int r = d->r;
@@ -362,6 +390,141 @@ extern "C" mrom_status mrom_rom_from_reduced_batch(mrom_handle h, int32_t n_obj,
       return cleanup(MROM_EINVAL, "mrom_rom_from_reduced_batch: non-finite value in the reduced data (object " +
                                       std::to_string(o) + ")");
   }
+  shared->refs = n_obj;
+  for (int o = 0; o < n_obj; ++o) {
+    if (roms[o]->has_cert) std::memcpy(roms[o]->gss, &gss[(size_t)o * 9], 9 * sizeof(double));
+    out[o] = roms[o];
+  }
+  return MROM_OK;
+}
+
+extern "C" mrom_status mrom_rom_from_packed(mrom_handle h, int32_t n_obj, const mrom_packed_obj* objs,
+                                            const void* packed, size_t bytes, mrom_rom_t* out) {
+  if (!h) return MROM_EINVAL;
+  if (n_obj < 1 || n_obj > 65535 || !objs || !packed || !out)
+    return fail(h, MROM_EINVAL, "mrom_rom_from_packed: 1 <= n_obj <= 65535 and non-null arguments required");
+  // region sizes and checks (host only)
+  std::vector<size_t> reg(n_obj), der(n_obj);
+  size_t n_der = 0;
+  for (int o = 0; o < n_obj; ++o) {
+    out[o] = nullptr;
+    const mrom_packed_obj& d = objs[o];
+    const size_t r = (size_t)d.r, rr = r * r, ng = 2 * r + 3;
+    const std::string tag = " (object " + std::to_string(o) + ")";
+    if (d.r < 1 || d.r > MROM_MAX_R) return fail(h, MROM_EINVAL, "mrom_rom_from_packed: r must be in [1, MROM_MAX_R]" + tag);
+    if (!std::isfinite(d.alpha) || !(d.alpha > 0) || !std::isfinite(d.vol_B))
+      return fail(h, MROM_EINVAL, "mrom_rom_from_packed: alpha must be finite and > 0" + tag);
+    if (d.has_gram && !(d.alpha_lb > 0 && std::isfinite(d.alpha_lb)))
+      return fail(h, MROM_EINVAL, "mrom_rom_from_packed: a Gram matrix needs alpha_lb > 0" + tag);
+    reg[o] = (rr * (2 + (d.has_kin ? 1 : 0) + (d.has_me ? 1 : 0)) + 3 * r + (d.has_gram ? ng * ng : 0)) * 16;
+    if (d.offset < 0 || d.offset % 16 != 0 || (size_t)d.offset + reg[o] > bytes)
+      return fail(h, MROM_EINVAL, "mrom_rom_from_packed: region not 16-byte aligned or outside the buffer" + tag);
+    bool bad = false;
+    for (int k = 0; k < 9; ++k) bad = bad || !std::isfinite(d.c00[k]) || !std::isfinite(d.N0[k]);
+    if (bad) return fail(h, MROM_EINVAL, "mrom_rom_from_packed: non-finite c00 or N0" + tag);
+    der[o] = n_der;
+    if (d.has_gram) n_der += 3 * rr + 6 * r;
+  }
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+  cudaStream_t st = h->stream;
+  const size_t b_pack = (bytes + 255) / 256 * 256, b_der = n_der * sizeof(double2);
+  const size_t b_flag = ((size_t)n_obj * sizeof(int) + 15) / 16 * 16, b_gss = (size_t)n_obj * 9 * sizeof(double);
+  const size_t b_tab = (size_t)n_obj * (2 * sizeof(void*) + sizeof(size_t) + sizeof(int) + sizeof(SplitJob)) + 64;
+  void* block = nullptr;
+  e = cudaMallocAsync(&block, b_pack + b_der + b_flag + b_gss + b_tab, st);
+  if (e != cudaSuccess) return fail(h, MROM_ENOMEM, "mrom_rom_from_packed: device allocation failed");
+  char* base = static_cast<char*>(block);
+  auto* derived = reinterpret_cast<double2*>(base + b_pack);
+  int* d_flag = reinterpret_cast<int*>(base + b_pack + b_der);
+  double* d_gss = reinterpret_cast<double*>(base + b_pack + b_der + b_flag);
+  char* tab = base + b_pack + b_der + b_flag + b_gss;
+  tab = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(tab) + 15) / 16 * 16);
+  auto* d_jobs = reinterpret_cast<SplitJob*>(tab);
+  auto** d_seg = reinterpret_cast<const double**>(tab + (size_t)n_obj * sizeof(SplitJob));
+  auto** d_g = reinterpret_cast<const double2**>(d_seg + n_obj);
+  auto* d_len = reinterpret_cast<size_t*>(d_g + n_obj);
+  auto* d_ng = reinterpret_cast<int*>(d_len + n_obj);
+  auto* shared = new mrom_rom::SharedBlock();
+  shared->p = block;
+  shared->stream = st;
+  std::vector<mrom_rom*> roms(n_obj, nullptr);
+  auto cleanup = [&](mrom_status s, const std::string& msg) {
+    for (auto* m : roms) delete m;
+    cudaFreeAsync(block, st);
+    delete shared;
+    return fail(h, s, msg);
+  };
+  // the whole dictionary in one copy
+  e = cudaMemcpyAsync(block, packed, bytes, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_flag, 0, b_flag, st);
+  std::vector<SplitJob> jobs(n_obj);
+  std::vector<const double*> seg(n_obj);
+  std::vector<const double2*> gp(n_obj);
+  std::vector<size_t> len(n_obj);
+  std::vector<int> ngv(n_obj);
+  int rmax_g = 1;
+  for (int o = 0; o < n_obj; ++o) {
+    const mrom_packed_obj& d = objs[o];
+    const size_t r = (size_t)d.r, rr = r * r, ng = 2 * r + 3;
+    auto* rom = new mrom_rom();
+    roms[o] = rom;
+    rom->ctx = h;
+    rom->r = d.r;
+    rom->alpha = d.alpha;
+    rom->alpha_lb = d.alpha_lb;
+    rom->vol_B = d.vol_B;
+    rom->shared = shared;
+    auto* p = reinterpret_cast<double2*>(base + d.offset);
+    rom->K = p; p += rr;
+    if (d.has_kin) { rom->Kin = p; p += rr; }
+    rom->C = p; p += rr;
+    if (d.has_me) { rom->Me = p; p += rr; }
+    rom->B = p; p += 3 * r;
+    SplitJob j{};
+    if (d.has_gram) {
+      rom->G = p;
+      double2* q = derived + der[o];
+      rom->GKK = q; q += rr;
+      rom->GCC = q; q += rr;
+      rom->GSk = q; q += rr;
+      rom->gsK = q; q += 3 * r;
+      rom->gsC = q;
+      j = SplitJob{rom->G, rom->GKK, rom->GCC, rom->GSk, rom->gsK, rom->gsC, d.r, 0};
+      rmax_g = std::max(rmax_g, d.r);
+    }
+    jobs[o] = j;
+    std::copy(d.c00, d.c00 + 9, rom->c00);
+    std::copy(d.N0, d.N0 + 9, rom->N0);
+    rom->has_cert = d.has_gram != 0;
+    rom->has_kin = d.has_kin != 0;
+    seg[o] = reinterpret_cast<const double*>(base + d.offset);
+    len[o] = reg[o] / sizeof(double);
+    gp[o] = rom->G;
+    ngv[o] = (int)ng;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_jobs, jobs.data(), n_obj * sizeof(SplitJob), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_seg, seg.data(), n_obj * sizeof(void*), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_g, gp.data(), n_obj * sizeof(void*), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_len, len.data(), n_obj * sizeof(size_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ng, ngv.data(), n_obj * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cleanup(MROM_ECUDA, std::string("mrom_rom_from_packed: upload: ") + cudaGetErrorString(e));
+  nonfinite_batch_kernel<<<dim3(8, (unsigned)n_obj), 256, 0, st>>>(d_seg, d_len, d_flag);
+  gather_gss_kernel<<<std::max(1, std::min(1024, (9 * n_obj + 255) / 256)), 256, 0, st>>>(d_g, d_ng, n_obj, d_gss);
+  split_gram_batch_kernel<<<dim3((unsigned)std::max(1, std::min(64, (rmax_g * rmax_g + 3 * rmax_g + 255) / 256)),
+                                 (unsigned)n_obj), 256, 0, st>>>(d_jobs);
+  h->launches += 3;
+  std::vector<int> flag(n_obj);
+  std::vector<double> gss((size_t)n_obj * 9);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(flag.data(), d_flag, n_obj * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(gss.data(), d_gss, gss.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cleanup(MROM_ECUDA, std::string("mrom_rom_from_packed: ") + cudaGetErrorString(e));
+  for (int o = 0; o < n_obj; ++o)
+    if (flag[o])
+      return cleanup(MROM_EINVAL, "mrom_rom_from_packed: non-finite value in the reduced data (object " +
+                                      std::to_string(o) + ")");
   shared->refs = n_obj;
   for (int o = 0; o < n_obj; ++o) {
     if (roms[o]->has_cert) std::memcpy(roms[o]->gss, &gss[(size_t)o * 9], 9 * sizeof(double));

@@ -260,3 +260,43 @@ def test_batched_object_creation(mrom, handle):
     with pytest.raises(mrom.MromError) as ei:
         mrom.ReducedObject.batch(handle, items)
     assert ei.value.status == 1 and "object 3" in str(ei.value)
+
+
+def test_packed_dictionary_matches_batch(mrom):
+    """mrom_rom_from_packed (one copy of a packed buffer) gives the objects of
+    mrom_rom_from_reduced_batch: identical sweeps; bad regions and non-finite data are refused."""
+    import torch
+    from workloads import log_omegas, reduced_object
+    h = mrom.Handle(0)
+    objs = [reduced_object(20230711, 900 + k, r) for k, r in enumerate([7, 40, 96, 13])]
+    items = [dict(r=o.r, K=o.K, C=o.C, B=o.B, c00=o.c00, G=o.G if k != 1 else None, K_in=o.K_in,
+                  alpha=o.alpha, alpha_lb=o.alpha_lb, vol_B=o.vol_B) for k, o in enumerate(objs)]
+    pk = mrom.PackedDictionary(items)
+    a = mrom.ReducedObject.from_packed(h, pk)
+    b = mrom.ReducedObject.batch(h, items)
+    wo = torch.as_tensor(log_omegas(1e1, 1e8, 50), device="cuda")
+    outs = []
+    for roms in (a, b):
+        R = torch.empty((4, 50, 3, 3), dtype=torch.float64, device="cuda")
+        I = torch.empty_like(R)
+        mrom.mrom_sweep(h, roms, wo, 50, R, I)              # object 1 has no Gram matrix: no Delta
+        cert = [roms[k] for k in (0, 2, 3)]
+        D = torch.empty((3, 50, 3, 3), dtype=torch.float64, device="cuda")
+        R3, I3 = torch.empty_like(D), torch.empty_like(D)
+        mrom.mrom_sweep(h, cert, wo, 50, R3, I3, D)
+        h.synchronize()
+        outs.append((R.cpu().numpy(), I.cpu().numpy(), D.cpu().numpy()))
+    for x, y in zip(*outs):
+        assert np.array_equal(x, y)
+    bad = mrom.PackedDictionary(items)
+    bad.entries[2].offset += 8                       # not 16-byte aligned
+    with pytest.raises(mrom.MromError):
+        mrom.ReducedObject.from_packed(h, bad)
+    bad = mrom.PackedDictionary(items)
+    bad.entries[3].offset = bad.nbytes               # outside the buffer
+    with pytest.raises(mrom.MromError):
+        mrom.ReducedObject.from_packed(h, bad)
+    items[2]["K"] = objs[2].K.copy()
+    items[2]["K"][3, 5] = np.nan
+    with pytest.raises(mrom.MromError):
+        mrom.ReducedObject.from_packed(h, mrom.PackedDictionary(items))
