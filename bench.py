@@ -45,9 +45,9 @@ SM_COUNT_NOMINAL = 152
 DFMA_PER_CLK_PER_SM = 2           # measured: GB300 DFMA rate saturates at 4 flop/clk/SM
 FP64_MEASURED_TFLOPS = 1.189      # DFMA microbenchmark on this machine's GB300 (1.96 GHz)
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one pencil_sweep_kernel launch on
-# this workload, from a one-pass ncu capture of the current kernel (98,763,264 + 371,965,440 bytes);
+# this workload, from a --set full ncu capture of the current kernel (97,853,696 + 373,272,320 bytes);
 # None once the kernel changes until it is captured again
-SWEEP_DRAM_BYTES_PER_LAUNCH = 470728704
+SWEEP_DRAM_BYTES_PER_LAUNCH = 97_853_696 + 373_272_320
 
 
 def flops_per_eval(r: int, cert: bool = True) -> float:
