@@ -139,3 +139,45 @@ def test_invalid_scale_is_refused(mrom, case):
     with pytest.raises(mrom.MromError):
         _sweep(mrom, case, wo, np.array([0.0]), np.ones(1), z, z, True)
     case["h"].set_solver(lu=False)
+
+
+def test_two_material_object_matches_oracle(mrom):
+    """Shell (mu_r = 1) around a mu_r = 64 core, both scaled by s, snapshots at s = 0.5 and 2
+    (smallest singular value ratios 6e-5 dynamic, 0.3 static: both sides keep every direction)."""
+    import torch
+    from oracle import podp_mu
+    from workloads import TWO_MATERIAL_C5, fit_problem, full_order_snapshots, log_omegas
+    S = (0.5, 2.0)
+    probs = {s: fit_problem(8, TWO_MATERIAL_C5, mu_scale=s, mu_split=True) for s in S}
+    p1 = fit_problem(8, TWO_MATERIAL_C5, mu_split=True)
+    D = [full_order_snapshots(probs[s], W_SAMPLES) for s in S]
+    O = [probs[s].o_tilde for s in S]
+    U, V = podp_mu.bases(D, O, tol_sigma=1e-7, tol_static=1e-7)
+    model = podp_mu.project(p1, U, V)
+    h = mrom.Handle(0)
+    fom = mrom.FullOrder.from_fit(p1)
+    mu = mrom.PermeabilityData.from_fit(p1, np.concatenate(O, axis=0), tol_static=1e-7)
+    cols = np.concatenate([np.transpose(Dl, (2, 0, 1)).reshape(-1, p1.N) for Dl in D], axis=0)
+    rom, r, m = mrom.mrom_project_mu(h, fom, mu, torch.as_tensor(np.ascontiguousarray(cols), device="cuda"),
+                                     tol_sigma=1e-7)
+    assert r == U.shape[1] and m == V.shape[1]
+    case = dict(h=h, rom=rom)
+    wo = log_omegas(1e1, 1e5, 17)
+    s_mu = np.array([0.5, 0.9, 2.0, 3.1])
+    s_sigma = np.ones(s_mu.size)
+    rng = np.random.default_rng(11)
+    gR = rng.standard_normal((s_mu.size, wo.size, 3, 3))
+    gI = rng.standard_normal((s_mu.size, wo.size, 3, 3))
+    R, I, _, _, g_m = _sweep(mrom, case, wo, s_mu, s_sigma, gR, gI, False)
+    a3 = model.alpha ** 3
+    for k, sm in enumerate(s_mu):
+        Rr, Ir = podp_mu.signature(model, wo, s_mu=sm)
+        sR = np.abs(Rr).reshape(wo.size, -1).max(1)
+        sI = wo * a3 / 4 * np.abs(podp_mu.static_state(model, sm)["c00"]).max()
+        eR = (np.abs(R[k] - Rr).reshape(wo.size, -1).max(1) / sR).max()
+        eI = (np.abs(I[k] - Ir).reshape(wo.size, -1).max(1) / sI).max()
+        assert eR <= 1e-10 and eI <= 1e-10, (k, eR, eI)
+        dR, dI = podp_mu.tangent_s_mu(model, wo, s_mu=sm)
+        ref = float(np.sum(gR[k] * dR) + np.sum(gI[k] * dI))
+        scale = float(np.sum(np.abs(gR[k] * dR)) + np.sum(np.abs(gI[k] * dI)))
+        assert abs(g_m[k] - ref) <= 1e-8 * scale, (k, g_m[k], ref, scale)

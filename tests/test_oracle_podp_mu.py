@@ -92,6 +92,22 @@ def test_mu_one_object_reduces_to_the_scalar_reading():
         assert max(np.abs(R - Rf).max(), np.abs(I - If).max()) <= 1e-9 * scale
 
 
+def test_two_material_object_exact_at_sampled_parameters():
+    """Shell (mu_r = 1) around a mu_r = 64 core, both scaled by s: the faces between the two
+    materials and between the shell and the exterior split K_in by their cells' shares."""
+    from workloads import TWO_MATERIAL_C5
+    probs = {s: fit_problem(8, TWO_MATERIAL_C5, mu_scale=s, mu_split=True) for s in (0.5, 2.0)}
+    D = [full_order_snapshots(probs[s], W_SAMPLES) for s in probs]
+    U, V = podp_mu.bases(D, [probs[s].o_tilde for s in probs], 1e-13, 1e-13)
+    base = fit_problem(8, TWO_MATERIAL_C5, mu_split=True)
+    model = podp_mu.project(base, U, V)
+    for s, p in probs.items():
+        R, I = podp_mu.signature(model, W_SAMPLES, s_mu=s)
+        Rf, If = _fom(p, W_SAMPLES)
+        scale = max(np.abs(Rf).max(), np.abs(If).max())
+        assert max(np.abs(R - Rf).max(), np.abs(I - If).max()) <= 1e-9 * scale, s
+
+
 def test_static_derivatives_central_differences(setup):
     _, _, _, model = setup
     s, h = 1.9, 1e-5
