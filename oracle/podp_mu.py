@@ -31,6 +31,8 @@ from __future__ import annotations
 from dataclasses import dataclass
 
 import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from . import tsvd
 
@@ -54,6 +56,8 @@ class MuModel:
     nB: float           # alpha^3 |B|
     mB: float           # alpha^3 sum_B |cell| / mu_r
     alpha: float
+    G_ext: np.ndarray | None = None   # Gram of [C x | C V | (K_out + eps M) U | K_in U | C U] in X^-1
+    alpha_lb: float = 1.0 / np.sqrt(2.0)
 
     @property
     def r(self) -> int:
@@ -95,6 +99,57 @@ def project(problem, U: np.ndarray, V: np.ndarray) -> MuModel:
         kv_out=VH @ kx_out.T, kv_in=VH @ problem.kx_in.T,
         cxx=x @ (C[:, None] * x.T), cvx=VH @ (C[:, None] * x.T), cvv=VH @ (C[:, None] * V),
         nB=a3 * problem.vol_B, mB=a3 * problem.vol_B_mu, alpha=problem.alpha)
+
+
+def attach_extended_gram(model: MuModel, problem, U: np.ndarray, V: np.ndarray, X_diag: np.ndarray) -> None:
+    """The certificate of Lemma 4.2 at a permeability scale s.  The residual of direction i,
+    r_i = i w C o_i(s) - (K(s) + eps M - i w C) U p_i with the reduced o_i(s) = x_i + V y_i(s),
+    is Phi_ext w_i for Phi_ext = [C x | C V | (K_out + eps M) U | K_in U | C U] and
+    w_i = [i w e_i ; i w y_i ; -p_i ; -p_i / s ; i w p_i]; G_ext = Phi_ext^H X^-1 Phi_ext."""
+    C = problem.C
+    K_in = problem.K_in
+    K_out = problem.K - K_in
+    Phi = np.concatenate([C[:, None] * problem.x.T, C[:, None] * V,
+                          K_out @ U + (problem.eps * problem.M)[:, None] * U, K_in @ U, C[:, None] * U], axis=1)
+    model.G_ext = Phi.conj().T @ (Phi / np.asarray(X_diag)[:, None])
+
+
+def certificate(model: MuModel, omegas, s_mu: float = 1.0, s_sigma: float = 1.0) -> np.ndarray:
+    """(Delta[omega])_ij of Lemma 4.2 at the scale s_mu, shape (n_w, 3, 3):
+    ||r^_i||^2 = w_i^H G_ext w_i and Delta_ij = alpha^3 / (8 alpha_LB) (||r^_i||^2 + ||r^_j||^2
+    + ||r^_i - r^_j||^2)."""
+    w_all = np.asarray(omegas, dtype=np.float64) * s_sigma
+    st = static_state(model, s_mu)
+    K = model.K_out + model.K_in / s_mu
+    a3 = model.alpha ** 3
+    out = np.empty((w_all.size, 3, 3))
+    for n, w in enumerate(w_all):
+        P = np.linalg.solve(K + model.Me - 1j * w * model.C, 1j * w * st["B"])
+        W = [np.concatenate([1j * w * np.eye(3)[i], 1j * w * st["y"][:, i], -P[:, i], -P[:, i] / s_mu,
+                             1j * w * P[:, i]]) for i in range(3)]
+        GW = [model.G_ext @ W[j] for j in range(3)]
+        nrm = np.array([np.real(np.vdot(W[i], GW[i])) for i in range(3)])
+        for i in range(3):
+            for j in range(3):
+                diff = nrm[i] + nrm[j] - 2.0 * np.real(np.vdot(W[i], GW[j]))
+                out[n, i, j] = a3 / (8.0 * model.alpha_lb) * (nrm[i] + nrm[j] + diff)
+    return out
+
+
+def residual_norms_direct(model: MuModel, problem, U: np.ndarray, V: np.ndarray, X_diag: np.ndarray,
+                          omega: float, s_mu: float) -> np.ndarray:
+    """||r^_i||^2 from the full-order residual vector of the problem at scale s_mu (pin for the
+    Gram form): r_i = i w C (x_i + V y_i(s)) - A(w, s) U p_i."""
+    st = static_state(model, s_mu)
+    K = problem.K - problem.K_in + problem.K_in / s_mu
+    A = (sp.csc_matrix(K, dtype=np.complex128) + sp.diags(problem.eps * problem.M - 1j * omega * problem.C))
+    P = np.linalg.solve(model.K_out + model.K_in / s_mu + model.Me - 1j * omega * model.C, 1j * omega * st["B"])
+    o = problem.x + np.real(V @ st["y"]).T
+    out = np.empty(3)
+    for i in range(3):
+        rho = 1j * omega * problem.C * o[i] - A @ (U @ P[:, i])
+        out[i] = np.real(np.vdot(rho, rho / X_diag))
+    return out
 
 
 def static_state(model: MuModel, s: float):

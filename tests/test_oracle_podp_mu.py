@@ -147,3 +147,23 @@ def test_conductivity_scale_is_a_frequency_scale():
     model = podp_mu.project(p, U, V)
     R, I = podp_mu.signature(model, w, s_mu=1.0, s_sigma=t)
     assert max(np.abs(R - Rt).max(), np.abs(I - It).max()) <= 1e-9 * scale
+
+
+def test_certificate_gram_form_matches_the_full_order_residual(setup):
+    """w_i^H G_ext w_i equals the X^-1 norm of the explicit full-order residual at any (omega, s),
+    and Delta vanishes (to the Gram form's rounding floor) at the sampled parameters."""
+    probs, U, V, model = setup
+    p1 = probs[1.0]
+    X = p1.eps * p1.M + 10.0 * p1.C
+    podp_mu.attach_extended_gram(model, p1, U, V, X)
+    for w, s in ((3e2, 1.7), (4e3, 0.6), (2e3, 2.5)):
+        direct = podp_mu.residual_norms_direct(model, p1, U, V, X, w, s)
+        D = podp_mu.certificate(model, [w], s_mu=s)[0]
+        a = model.alpha ** 3 / (4.0 * model.alpha_lb)
+        assert np.allclose(np.diag(D), a * direct, rtol=1e-7, atol=1e-10 * a * direct.max()), (w, s)
+    # the Gram form's rounding floor grows like omega^2: compare at the same frequency
+    for s in S_SAMPLES:
+        D0 = podp_mu.certificate(model, W_SAMPLES, s_mu=s)
+        Dfar = podp_mu.certificate(model, W_SAMPLES, s_mu=1.6 * s)
+        for k in range(len(W_SAMPLES)):
+            assert np.abs(D0[k]).max() <= 1e-5 * np.abs(Dfar[k]).max(), (s, k)
