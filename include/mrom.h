@@ -247,10 +247,13 @@ typedef struct {
  * static problem: V from the SVD of O (rank m <= MROM_MAX_STATIC, r_out / m_out report
  * r and m), S(s) = V^H (K(s) + M_s) V, V^H K(s) x, U^H C V, V^H C V and V^H C x, so that
  * o~(s) ~= V y(s) with S(s) y = -V^H K(s) x.  The object's B, c00 and N0 are those of
- * the reduced static problem at s = 1; mrom_sweep_vjp evaluates it at per-object s_mu
- * with B, c00 and N0 following s_mu, and its dL/ds_mu includes their derivatives.
- * The certificate (fom->X_diag) is that of s = 1.  MROM_EINVAL if O has no nonzero
- * singular value.  Synchronous. */
+ * the reduced static problem at s = 1; mrom_sweep and mrom_sweep_vjp evaluate it at
+ * per-object s_mu with B, c00 and N0 following s_mu, and dL/ds_mu includes their
+ * derivatives.  With fom->X_diag the object also keeps the Gram of
+ * Phi_ext = [C x | C V | (K - K_in + eps M) U | K_in U | C U] in X^-1 (size 3 + m + 3 r), from
+ * which the certificate of Lemma 4.2 follows at any s (the residual's source is the reduced
+ * C (x + V y(s))); its stored certificate blocks are those of s = 1.  MROM_EINVAL if O has no
+ * nonzero singular value.  Synchronous. */
 mrom_status mrom_project_mu(mrom_handle h, const mrom_fom* fom, const mrom_fom_mu* mu, const void* D, int64_t ldd,
                             int32_t n_cols, double tol_sigma, int32_t r_max, mrom_rom_t* out, int32_t* r_out,
                             int32_t* m_out);
@@ -359,8 +362,11 @@ mrom_status mrom_rom_get(mrom_rom_t rom, void* K, void* C, void* Me, void* B, do
  * n_obj * n_w * 9 doubles; omega holds n_w (stride 0) or n_obj * n_w values.
  * s_sigma, s_mu (device, n_obj each, or NULL for 1): per-object conductivity
  * and permeability scales; s_sigma acts as omega -> s_sigma omega (nu is
- * linear in omega sigma).  s_mu must be NULL here (MROM_ENOTSUP); the forward
- * values at a permeability scale come from mrom_sweep_vjp. */
+ * linear in omega sigma).  With s_mu every object needs K_in: K(s) = K + (1/s - 1) K_in
+ * (formed per call), and objects from mrom_project_mu take B, c00 and N0 of their reduced
+ * static problem at s; Delta at s_mu needs objects from mrom_project_mu with a certificate
+ * inner product (their extended Gram gives Lemma 4.2's Gram at s; MROM_ENOTSUP otherwise).
+ * The per-call buffers of the scales take (r^2 + 5 r + 3 m + 2 r^2) complex128 per object. */
 mrom_status mrom_sweep(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega,
                        int32_t n_w, int32_t omega_stride, const double* s_sigma, const double* s_mu,
                        double* R, double* I, double* Delta);

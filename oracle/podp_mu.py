@@ -136,6 +136,23 @@ def certificate(model: MuModel, omegas, s_mu: float = 1.0, s_sigma: float = 1.0)
     return out
 
 
+def certificate_term_scale(model: MuModel, omegas, s_mu: float = 1.0, s_sigma: float = 1.0) -> np.ndarray:
+    """Per frequency alpha^3 / (4 alpha_LB) max_i |w_i|^T |G_ext| |w_i|: the size of the terms the
+    Gram form of the certificate sums (Delta cancels them at an accurate model), the scale its
+    rounding is measured against."""
+    w_all = np.asarray(omegas, dtype=np.float64) * s_sigma
+    st = static_state(model, s_mu)
+    K = model.K_out + model.K_in / s_mu
+    absG = np.abs(model.G_ext)
+    out = np.empty(w_all.size)
+    for n, w in enumerate(w_all):
+        P = np.linalg.solve(K + model.Me - 1j * w * model.C, 1j * w * st["B"])
+        W = [np.abs(np.concatenate([1j * w * np.eye(3)[i], 1j * w * st["y"][:, i], -P[:, i], -P[:, i] / s_mu,
+                                    1j * w * P[:, i]])) for i in range(3)]
+        out[n] = model.alpha ** 3 / (4.0 * model.alpha_lb) * max(x @ absG @ x for x in W)
+    return out
+
+
 def residual_norms_direct(model: MuModel, problem, U: np.ndarray, V: np.ndarray, X_diag: np.ndarray,
                           omega: float, s_mu: float) -> np.ndarray:
     """||r^_i||^2 from the full-order residual vector of the problem at scale s_mu (pin for the

@@ -399,15 +399,105 @@ extern "C" mrom_status mrom_plan_sweep(mrom_plan plan, const double* omega, int3
   return run_plan(plan, omega, omega_stride, nullptr, R, I, Delta);
 }
 
+namespace mrom {
+namespace {
+
+// A plan's objects at per-object permeability scales s_mu: K(s) = K + (1/s - 1) K_in of every
+// object into per-call buffers (the plan's sweeps then read K(s) as their K, and the pencil
+// preparation runs unscaled), and for objects with a reduced static problem B(s), c00(s), N0(s)
+// and, when the certificate is wanted, its Gram blocks at s.  *block receives the per-call
+// allocation (freed by the caller after the sweep, stream-ordered).
+mrom_status instantiate_scales(mrom_plan plan, const mrom_rom_t* roms, const double* s_mu, bool cert,
+                               void** block) {
+  mrom_ctx* h = plan->ctx;
+  const int n_obj = plan->n_obj;
+  cudaStream_t st = h->stream;
+  size_t elems = 0;
+  int m_max = 0, rmax = 1;
+  for (int o = 0; o < n_obj; ++o) {
+    const size_t r = roms[o]->r, m = roms[o]->mu.m;
+    elems += r * r;
+    rmax = std::max(rmax, (int)r);
+    if (m > 0) {
+      elems += 3 * r + 3 * m + (cert ? 2 * r * r + 6 * r : 0);
+      m_max = std::max(m_max, (int)m);
+    }
+  }
+  const size_t b_mus = (n_obj * sizeof(MuDev) + 255) / 256 * 256, b_jobs = (n_obj * sizeof(ScaleKJob) + 255) / 256 * 256;
+  void* blk = nullptr;
+  cudaError_t e = cudaMallocAsync(&blk, b_mus + b_jobs + elems * sizeof(double2), st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_sweep: allocation");
+  *block = blk;
+  auto* d_mus = static_cast<MuDev*>(blk);
+  auto* d_jobs = reinterpret_cast<ScaleKJob*>(static_cast<char*>(blk) + b_mus);
+  auto* q = reinterpret_cast<double2*>(static_cast<char*>(blk) + b_mus + b_jobs);
+  std::vector<MuDev> mus(n_obj);
+  std::vector<ScaleKJob> jobs(n_obj);
+  std::vector<RomDev> recs(n_obj);
+  for (int o = 0; o < n_obj; ++o) {
+    const mrom_rom* m = roms[o];
+    const size_t r = m->r, mm = m->mu.m;
+    recs[o] = rom_record(m);
+    jobs[o] = ScaleKJob{m->K, m->Kin, q, (int)r, 0};
+    recs[o].K = q;
+    q += r * r;
+    if (mm > 0) {
+      mus[o] = m->mu;
+      mus[o].Bdst = q; q += 3 * r;
+      mus[o].ydst = q; q += 3 * mm;
+      mus[o].dBdst = nullptr;
+      recs[o].B = mus[o].Bdst;
+      if (cert) {
+        mus[o].GKKdst = q; q += r * r;
+        mus[o].GSkdst = q; q += r * r;
+        mus[o].gsKdst = q; q += 3 * r;
+        mus[o].gsCdst = q; q += 3 * r;
+        recs[o].GKK = mus[o].GKKdst;
+        recs[o].GSk = mus[o].GSkdst;
+        recs[o].gsK = mus[o].gsKdst;
+        recs[o].gsC = mus[o].gsCdst;
+      } else {
+        mus[o].Gext = nullptr;
+      }
+    }
+  }
+  e = cudaMemcpyAsync(d_mus, mus.data(), n_obj * sizeof(MuDev), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_jobs, jobs.data(), n_obj * sizeof(ScaleKJob), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(plan->d_objs, recs.data(), n_obj * sizeof(RomDev), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_scale_k(d_jobs, n_obj, rmax, s_mu, st);
+  if (e == cudaSuccess && m_max > 0) e = launch_mu_instance(d_mus, n_obj, m_max, s_mu, false, plan->d_objs, nullptr,
+                                                            h->d_status, st);
+  if (e == cudaSuccess && m_max > 0 && cert) e = launch_mu_cert(d_mus, n_obj, s_mu, plan->d_objs, st);
+  h->launches += 1 + (m_max > 0 ? 1 + (cert ? 1 : 0) : 0);
+  // (pageable host vectors: each copy has consumed its source on return)
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_sweep: scales");
+  return MROM_OK;
+}
+
+}  // namespace
+}  // namespace mrom
+
 extern "C" mrom_status mrom_sweep(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, const double* omega,
                                   int32_t n_w, int32_t omega_stride, const double* s_sigma, const double* s_mu,
                                   double* R, double* I, double* Delta) {
   if (!h) return MROM_EINVAL;
-  if (s_mu) return fail(h, MROM_ENOTSUP, "mrom_sweep: s_mu scaling is supported by mrom_sweep_vjp only");
+  if (s_mu) {
+    if (!roms || n_obj < 1) return fail(h, MROM_EINVAL, "mrom_sweep: bad arguments");
+    for (int o = 0; o < n_obj; ++o) {
+      if (!roms[o] || !roms[o]->has_kin) return fail(h, MROM_EINVAL, "mrom_sweep: s_mu needs K_in on every object");
+      if (Delta && !roms[o]->mu.Gext)
+        return fail(h, MROM_ENOTSUP, "mrom_sweep: the certificate at s_mu needs objects from mrom_project_mu "
+                                     "with a certificate inner product");
+    }
+  }
   mrom_plan plan = nullptr;
   mrom_status st = mrom_plan_create(h, roms, n_obj, n_w, &plan);
   if (st != MROM_OK) return st;
-  st = run_plan(plan, omega, omega_stride, s_sigma, R, I, Delta);
+  void* inst = nullptr;
+  if (s_mu) st = instantiate_scales(plan, roms, s_mu, Delta != nullptr, &inst);
+  if (st == MROM_OK) st = run_plan(plan, omega, omega_stride, s_sigma, R, I, Delta);
+  if (inst) cudaFreeAsync(inst, h->stream);
   mrom_plan_destroy(plan);
   return st;
 }

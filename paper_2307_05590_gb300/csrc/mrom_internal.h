@@ -142,8 +142,16 @@ struct MuDev {
   double cxx[9];
   double nB, mB, alpha3;
   int m, r;
+  // certificate at s (or null): the Gram of Phi_ext = [C x | C V | (K_out + eps M) U | K_in U | C U]
+  // in the certificate's inner product, next = 3 + m + 3 r rows and columns
+  const double2* Gext;
+  int next, pad;
+  // per-call destinations (null where not wanted): B(s), dB/ds, y(s) (m x 3), and the
+  // certificate's blocks at s (the split of Lemma 4.2's Gram used by the sweeps)
   double2* Bdst;
   double2* dBdst;
+  double2* ydst;
+  double2 *GKKdst, *GSkdst, *gsKdst, *gsCdst;
 };
 
 // Device buffer released at scope exit.
@@ -288,6 +296,18 @@ mrom_status fom_solve(mrom_ctx* h, const mrom_fom* fom, const double* omega_host
 // m_max: the largest m in the batch (dynamic shared memory).
 cudaError_t launch_mu_instance(const MuDev* mus, int n_obj, int m_max, const double* s_mu, bool deriv, RomDev* recs,
                                VjpDev* vjp, int* status, cudaStream_t stream);
+// The certificate's Gram blocks of every object with mus[o].Gext at s_mu[o] (needs y(s) in
+// mus[o].ydst from launch_mu_instance): G_KK(s), G_CK(s) - G_KC(s), g_sK(s), g_sC(s) into the
+// destinations and gss(s) into recs[o].gss.
+cudaError_t launch_mu_cert(const MuDev* mus, int n_obj, const double* s_mu, RomDev* recs, cudaStream_t stream);
+// K(s) = K + (1/s - 1) K_in of each object with a K_in (jobs: {K, K_in, destination, r}).
+struct ScaleKJob {
+  const double2* K;
+  const double2* Kin;
+  double2* dst;
+  int r, pad;
+};
+cudaError_t launch_scale_k(const ScaleKJob* jobs, int n_obj, int rmax, const double* s_mu, cudaStream_t stream);
 size_t sweep_budget_bytes(const mrom_ctx* h, int cfg);
 int sweep_config(const mrom_ctx* h);
 

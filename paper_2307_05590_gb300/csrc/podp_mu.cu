@@ -148,6 +148,8 @@ mu_instance_kernel(const MuDev* __restrict__ mus, const double* __restrict__ s_m
     return;
   }
   chol_solve3(L, m, y);
+  if (mu.ydst)
+    for (int idx = tid; idx < 3 * m; idx += kMT) mu.ydst[idx] = y[idx];
   hmat3(mu.cvv, nullptr, 0.0, m, y, Cy);
   hmat3(mu.Sout, mu.Sin, is, m, y, Ky);
   hmat3(mu.Sin, nullptr, 0.0, m, y, Sy);
@@ -202,7 +204,88 @@ mu_instance_kernel(const MuDev* __restrict__ mus, const double* __restrict__ s_m
   }
 }
 
+// Certificate blocks at s from the extended Gram (indices: sources 0..2, V 3..3+m, K_out block
+// O = 3+m, K_in block I = O+r, C block Cb = I+r; G[u][v] = phi_u^H X^-1 phi_v):
+//   G_KK(s)[a][b] = G[O+a][O+b] + (G[O+a][I+b] + G[I+a][O+b]) / s + G[I+a][I+b] / s^2
+//   G_CK(s) - G_KC(s) = G[Cb+a][O+b] + G[Cb+a][I+b] / s - G[O+a][Cb+b] - G[I+a][Cb+b] / s
+//   g_sK(s)[i][a] = sum_u conj(T_ui) (G[u][O+a] + G[u][I+a] / s),  g_sC(s)[i][a] = sum_u conj(T_ui) G[u][Cb+a]
+//   gss(s)[i][j] = Re sum_uv conj(T_ui) G[u][v] T_vj,  T = [I_3 ; y(s)] (the sources C o_i(s) = C x_i + C V y_i).
+__global__ void __launch_bounds__(kMT)
+mu_cert_kernel(const MuDev* __restrict__ mus, const double* __restrict__ s_mu, RomDev* __restrict__ recs) {
+  const int o = blockIdx.x, tid = threadIdx.x;
+  const MuDev& mu = mus[o];
+  if (mu.m <= 0 || !mu.Gext || !mu.ydst) return;
+  const double s = s_mu ? s_mu[o] : 1.0;
+  if (!(s > 0.0) || !isfinite(s)) return;  // reported by the instance kernel
+  const double is = 1.0 / s, is2 = is * is;
+  const int m = mu.m, r = mu.r, n = mu.next;
+  const int V0 = 3, O0 = 3 + m, I0 = O0 + r, C0 = I0 + r;
+  const double2* G = mu.Gext;
+  const double2* y = mu.ydst;
+  auto g = [&](int u, int v) { return G[(size_t)u * n + v]; };
+  for (int idx = tid; idx < r * r; idx += kMT) {
+    const int a = idx / r, b = idx - (idx / r) * r;
+    const double2 oo = g(O0 + a, O0 + b), oi = g(O0 + a, I0 + b), io = g(I0 + a, O0 + b), ii = g(I0 + a, I0 + b);
+    mu.GKKdst[idx] = make_double2(oo.x + (oi.x + io.x) * is + ii.x * is2, oo.y + (oi.y + io.y) * is + ii.y * is2);
+    const double2 co = g(C0 + a, O0 + b), ci = g(C0 + a, I0 + b), oc = g(O0 + a, C0 + b), ic = g(I0 + a, C0 + b);
+    mu.GSkdst[idx] = make_double2(co.x + ci.x * is - oc.x - ic.x * is, co.y + ci.y * is - oc.y - ic.y * is);
+  }
+  // T_ui: 1 for u = i < 3, y[(u-3)*3 + i] for V rows
+  for (int idx = tid; idx < 3 * r; idx += kMT) {
+    const int i = idx / r, a = idx - (idx / r) * r;
+    double2 k = g(i, O0 + a), ki = g(i, I0 + a), c = g(i, C0 + a);
+    k.x += ki.x * is;
+    k.y += ki.y * is;
+    for (int q = 0; q < m; ++q) {
+      const double2 t = y[q * 3 + i];  // conj(t) * G
+      const double2 vo = g(V0 + q, O0 + a), vi = g(V0 + q, I0 + a), vc = g(V0 + q, C0 + a);
+      const double2 vk = make_double2(vo.x + vi.x * is, vo.y + vi.y * is);
+      k = cfma(k, make_double2(t.x, -t.y), vk);
+      c = cfma(c, make_double2(t.x, -t.y), vc);
+    }
+    mu.gsKdst[idx] = k;
+    mu.gsCdst[idx] = c;
+  }
+  if (tid < 9) {
+    const int i = tid / 3, j = tid % 3;
+    double2 acc = g(i, j);
+    for (int q = 0; q < m; ++q) {
+      const double2 yj = y[q * 3 + j], yi = y[q * 3 + i];
+      acc = cfma(acc, g(i, V0 + q), yj);                                   // G[i][V] y_j
+      acc = cfma(acc, make_double2(yi.x, -yi.y), g(V0 + q, j));            // conj(y_i) G[V][j]
+      double2 row = make_double2(0.0, 0.0);
+      for (int l = 0; l < m; ++l) row = cfma(row, g(V0 + q, V0 + l), y[l * 3 + j]);
+      acc = cfma(acc, make_double2(yi.x, -yi.y), row);                     // conj(y_i) G[V][V] y_j
+    }
+    recs[o].gss[tid] = acc.x;
+  }
+}
+
+__global__ void scale_k_kernel(const ScaleKJob* __restrict__ jobs, const double* __restrict__ s_mu) {
+  const ScaleKJob j = jobs[blockIdx.y];
+  if (!j.dst) return;
+  const double f = (s_mu ? 1.0 / s_mu[blockIdx.y] : 1.0) - 1.0;
+  const int rr = j.r * j.r;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < rr; idx += gridDim.x * blockDim.x) {
+    const double2 k = j.K[idx], q = j.Kin[idx];
+    j.dst[idx] = make_double2(fma(f, q.x, k.x), fma(f, q.y, k.y));
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_mu_cert(const MuDev* mus, int n_obj, const double* s_mu, RomDev* recs, cudaStream_t stream) {
+  if (n_obj <= 0) return cudaSuccess;
+  mu_cert_kernel<<<n_obj, kMT, 0, stream>>>(mus, s_mu, recs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_k(const ScaleKJob* jobs, int n_obj, int rmax, const double* s_mu, cudaStream_t stream) {
+  if (n_obj <= 0) return cudaSuccess;
+  scale_k_kernel<<<dim3((unsigned)std::max(1, std::min(64, (rmax * rmax + 255) / 256)), (unsigned)n_obj), 256, 0,
+                   stream>>>(jobs, s_mu);
+  return cudaGetLastError();
+}
 
 size_t mu_instance_smem_bytes(int m_max) { return ((size_t)m_max * m_max + 24 * (size_t)m_max) * sizeof(double2); }
 

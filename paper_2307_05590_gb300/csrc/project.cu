@@ -422,6 +422,41 @@ __global__ void real_cols_kernel(const double* __restrict__ X, int64_t ldx, int6
   }
 }
 
+// Phi_ext[row] = [c x_1..3 | c V | (K U - K_in U) + eps m U | K_in U | c U]  (width 3 + m + 3 r):
+// the residual basis of the certificate at a permeability scale
+__global__ void build_phi_ext_kernel(const double2* __restrict__ X3, const double2* __restrict__ V, int m,
+                                     const double2* __restrict__ U, const double2* __restrict__ KU,
+                                     const double2* __restrict__ KinU, int r, const double* __restrict__ cdiag,
+                                     const double* __restrict__ mdiag, double eps, int64_t n,
+                                     double2* __restrict__ Phi) {
+  const int w = 3 + m + 3 * r;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * w;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / w;
+    const int col = (int)(idx - row * w);
+    const double c = cdiag[row];
+    double2 v;
+    if (col < 3) {
+      const double2 x = X3[row * 3 + col];
+      v = make_double2(c * x.x, c * x.y);
+    } else if (col < 3 + m) {
+      const double2 x = V[row * m + col - 3];
+      v = make_double2(c * x.x, c * x.y);
+    } else if (col < 3 + m + r) {
+      const int k = col - 3 - m;
+      const double2 a = KU[row * r + k], b = KinU[row * r + k], u = U[row * r + k];
+      const double em = mdiag ? eps * mdiag[row] : 0.0;
+      v = make_double2(a.x - b.x + em * u.x, a.y - b.y + em * u.y);
+    } else if (col < 3 + m + 2 * r) {
+      v = KinU[row * r + col - 3 - m - r];
+    } else {
+      const double2 u = U[row * r + col - 3 - m - 2 * r];
+      v = make_double2(c * u.x, c * u.y);
+    }
+    Phi[idx] = v;
+  }
+}
+
 // Z = X - Y (n complex values)
 __global__ void csub_kernel(const double2* __restrict__ X, const double2* __restrict__ Y, int n,
                             double2* __restrict__ Z) {
@@ -996,7 +1031,9 @@ extern "C" mrom_status mrom_project_mu(mrom_handle h, const mrom_fom* fom, const
   // reduced static data, one device block owned by the object:
   // Sout, Sin, Mv, cvv (m x m), kout, kin, cvx (m x 3), Bx (r x 3), BV (r x m)
   const size_t mm = (size_t)m * m, m3 = 3 * (size_t)m;
-  const size_t n_mu = 4 * mm + 3 * m3 + 3 * (size_t)r + (size_t)r * m;
+  const bool cert = fom->X_diag != nullptr;
+  const int n_ext = 3 + m + 3 * r;
+  const size_t n_mu = 4 * mm + 3 * m3 + 3 * (size_t)r + (size_t)r * m + (cert ? (size_t)n_ext * n_ext : 0);
   void* blk = nullptr;
   e = cudaMalloc(&blk, n_mu * sizeof(double2));
   if (e != cudaSuccess) return bail(e, "mrom_project_mu: allocation");
@@ -1011,7 +1048,8 @@ extern "C" mrom_status mrom_project_mu(mrom_handle h, const mrom_fom* fom, const
   double2* kin = q; q += m3;
   double2* cvx = q; q += m3;
   double2* Bx = q; q += 3 * (size_t)r;
-  double2* BV = q;
+  double2* BV = q; q += (size_t)r * m;
+  double2* Gext = cert ? q : nullptr;
   // scratch in the small block after K_in^r
   double2* Sv = Kin_r + (size_t)r * r;        // m x m
   double2* kv = Sv + mm;                     // m x 3
@@ -1065,6 +1103,31 @@ extern "C" mrom_status mrom_project_mu(mrom_handle h, const mrom_fom* fom, const
   if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, X3, 3, 1, 3, fom->C_diag, 1, n, false, Bx, 3);
   if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, V, m, 1, m, fom->C_diag, 1, n, false, BV, m);
   if (e == cudaSuccess) e = tall_gram(h, X3, 3, 1, 3, X3, 3, 1, 3, fom->C_diag, 1, n, true, cxx, 3);
+  // certificate at a permeability scale: G_ext = Phi_ext^H X^-1 Phi_ext
+  if (e == cudaSuccess && cert) {
+    DevBuf KinUb, Phib, xinv;
+    e = cudaMalloc(&KinUb.p, (size_t)n * r * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&Phib.p, (size_t)n * n_ext * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&xinv.p, (size_t)n * sizeof(double));
+    if (e == cudaSuccess) {
+      spmm_csr_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, str>>>(fom->K_rowptr, fom->K_col, fom->K_val, n, U,
+                                                                         r, nullptr, Yp);
+      spmm_csr_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, str>>>(mu->Kin_rowptr, mu->Kin_col, mu->Kin_val, n,
+                                                                         U, r, nullptr,
+                                                                         static_cast<double2*>(KinUb.p));
+      build_phi_ext_kernel<<<grid_of((int64_t)n * n_ext), 256, 0, str>>>(
+          X3, V, m, U, Yp, static_cast<double2*>(KinUb.p), r, fom->C_diag, fom->M_diag, fom->eps, n,
+          static_cast<double2*>(Phib.p));
+      recip_kernel<<<grid_of(n), 256, 0, str>>>(fom->X_diag, n, static_cast<double*>(xinv.p));
+      h->launches += 4;
+      e = cudaGetLastError();
+    }
+    const auto* Phi = static_cast<const double2*>(Phib.p);
+    if (e == cudaSuccess)
+      e = tall_gram(h, Phi, n_ext, 1, n_ext, Phi, n_ext, 1, n_ext, static_cast<double*>(xinv.p), 1, n, true, Gext,
+                    n_ext);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(str);
+  }
   std::vector<double2> cxx_h(9);
   if (e == cudaSuccess) e = cudaMemcpy(cxx_h.data(), cxx, 9 * sizeof(double2), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return bail(e, "mrom_project_mu: static projection");
@@ -1084,10 +1147,12 @@ extern "C" mrom_status mrom_project_mu(mrom_handle h, const mrom_fom* fom, const
   md.alpha3 = a3;
   md.m = m;
   md.r = r;
+  md.Gext = Gext;
+  md.next = cert ? n_ext : 0;
   rom->mu = md;
   // the object's B, c00 and N0 become those of the reduced static problem at s = 1
   DevBuf inst;
-  e = cudaMalloc(&inst.p, sizeof(MuDev) + sizeof(RomDev) + 3 * (size_t)r * sizeof(double2) + 64);
+  e = cudaMalloc(&inst.p, sizeof(MuDev) + sizeof(RomDev) + (3 * (size_t)r + 3 * (size_t)m) * sizeof(double2) + 64);
   if (e != cudaSuccess) return bail(e, "mrom_project_mu: allocation");
   auto* dmu = static_cast<MuDev*>(inst.p);
   auto* drec = reinterpret_cast<RomDev*>(dmu + 1);
@@ -1095,8 +1160,21 @@ extern "C" mrom_status mrom_project_mu(mrom_handle h, const mrom_fom* fom, const
   MuDev md1 = md;
   md1.Bdst = rom->B;
   md1.dBdst = dscr;
+  md1.ydst = dscr + 3 * (size_t)r;
+  if (cert && rom->GKK) {  // the object's certificate blocks become those of G_ext at s = 1
+    md1.GKKdst = rom->GKK;
+    md1.GSkdst = rom->GSk;
+    md1.gsKdst = rom->gsK;
+    md1.gsCdst = rom->gsC;
+  } else {
+    md1.Gext = nullptr;
+  }
   e = cudaMemcpyAsync(dmu, &md1, sizeof(MuDev), cudaMemcpyHostToDevice, str);
   if (e == cudaSuccess) e = launch_mu_instance(dmu, 1, m, nullptr, false, drec, nullptr, h->d_status, str);
+  if (e == cudaSuccess && md1.Gext) {
+    e = launch_mu_cert(dmu, 1, nullptr, drec, str);
+    ++h->launches;
+  }
   RomDev rec{};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&rec, drec, sizeof(RomDev), cudaMemcpyDeviceToHost, str);
   if (e == cudaSuccess) e = cudaStreamSynchronize(str);
@@ -1110,6 +1188,7 @@ extern "C" mrom_status mrom_project_mu(mrom_handle h, const mrom_fom* fom, const
   }
   std::copy(rec.c00, rec.c00 + 9, rom->c00);
   std::copy(rec.N0, rec.N0 + 9, rom->N0);
+  if (md1.Gext) std::copy(rec.gss, rec.gss + 9, rom->gss);
   if (r_out) *r_out = r;
   if (m_out) *m_out = m;
   return MROM_OK;

@@ -181,3 +181,61 @@ def test_two_material_object_matches_oracle(mrom):
         ref = float(np.sum(gR[k] * dR) + np.sum(gI[k] * dI))
         scale = float(np.sum(np.abs(gR[k] * dR)) + np.sum(np.abs(gI[k] * dI)))
         assert abs(g_m[k] - ref) <= 1e-8 * scale, (k, g_m[k], ref, scale)
+
+
+@pytest.mark.parametrize("lu", [False, True], ids=["auto", "lu"])
+def test_sweep_with_certificate_at_scales_matches_oracle(mrom, lu):
+    """mrom_sweep at per-object s_mu: R, I and the certificate Delta of Lemma 4.2 at the scale
+    (extended Gram of [C x | C V | (K_out + eps M) U | K_in U | C U]) against the oracle; Delta
+    per frequency against its term scale (the Gram form cancels terms of that size)."""
+    import torch
+    from oracle import podp_mu
+    from workloads import fit_problem, full_order_snapshots, log_omegas
+    from workloads.fit import Material
+    mat = (Material((0.25,) * 3, (0.75,) * 3, 5.96e7, 4.0),)
+    probs = {s: fit_problem(8, mat, mu_scale=s, mu_split=True) for s in S_SAMPLES}
+    p1 = probs[1.0]
+    X = p1.eps * p1.M + 10.0 * p1.C
+    D = [full_order_snapshots(probs[s], W_SAMPLES) for s in S_SAMPLES]
+    O = [probs[s].o_tilde for s in S_SAMPLES]
+    U, V = podp_mu.bases(D, O, tol_sigma=1e-7, tol_static=1e-7)
+    model = podp_mu.project(p1, U, V)
+    podp_mu.attach_extended_gram(model, p1, U, V, X)
+    h = mrom.Handle(0)
+    h.set_solver(lu=lu)
+    fom = mrom.FullOrder.from_fit(p1, X=X)
+    mu = mrom.PermeabilityData.from_fit(p1, np.concatenate(O, axis=0), tol_static=1e-7)
+    cols = np.concatenate([np.transpose(Dl, (2, 0, 1)).reshape(-1, p1.N) for Dl in D], axis=0)
+    rom, r, m = mrom.mrom_project_mu(h, fom, mu, torch.as_tensor(np.ascontiguousarray(cols), device="cuda"),
+                                     tol_sigma=1e-7)
+    wo = log_omegas(1e1, 1e5, 19)
+    s_mu = np.array([0.7, 1.0, 2.3, 4.0, 9.0])
+    n = s_mu.size
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    R = torch.empty((n, wo.size, 3, 3), dtype=torch.float64, device="cuda")
+    I = torch.empty_like(R)
+    Dg = torch.empty_like(R)
+    mrom.mrom_sweep(h, [rom] * n, t(wo), wo.size, R, I, Dg, s_mu=t(s_mu))
+    h.synchronize()
+    R, I, Dg = R.cpu().numpy(), I.cpu().numpy(), Dg.cpu().numpy()
+    a3 = model.alpha ** 3
+    for k, sm in enumerate(s_mu):
+        Rr, Ir = podp_mu.signature(model, wo, s_mu=sm)
+        Dr = podp_mu.certificate(model, wo, s_mu=sm)
+        sR = np.abs(Rr).reshape(wo.size, -1).max(1)
+        sI = wo * a3 / 4 * np.abs(podp_mu.static_state(model, sm)["c00"]).max()
+        sD = podp_mu.certificate_term_scale(model, wo, s_mu=sm)
+        eR = (np.abs(R[k] - Rr).reshape(wo.size, -1).max(1) / sR).max()
+        eI = (np.abs(I[k] - Ir).reshape(wo.size, -1).max(1) / sI).max()
+        eD = (np.abs(Dg[k] - Dr).reshape(wo.size, -1).max(1) / sD).max()
+        assert eR <= 1e-10 and eI <= 1e-10 and eD <= 1e-10, (k, eR, eI, eD)
+    # at s = 1 the scaled sweep equals the plain one (the object's stored state is that of s = 1)
+    R1, I1, D1 = (torch.empty((1, wo.size, 3, 3), dtype=torch.float64, device="cuda") for _ in range(3))
+    mrom.mrom_sweep(h, [rom], t(wo), wo.size, R1, I1, D1)
+    h.synchronize()
+    sc = np.abs(D1.cpu().numpy()).max()
+    assert np.abs(D1.cpu().numpy()[0] - Dg[1]).max() <= 1e-12 * sc
+    h.set_solver(lu=False)
+    with pytest.raises(mrom.MromError):       # no extended Gram: no certificate at a scale
+        plain = mrom.ReducedObject.from_workload(h, __import__("workloads").reduced_object(20230711, 1, 12))
+        mrom.mrom_sweep(h, [plain], t(wo), wo.size, R1, I1, D1, s_mu=t([2.0]))
