@@ -789,8 +789,7 @@ def main():
                     dst.copy_(src, non_blocking=True)
             h.synchronize()
             pl.close()
-            for x in rr:
-                x.close()
+            m.ReducedObject.close_all(rr)
 
         with torch.cuda.stream(stream):
             e2e_step()

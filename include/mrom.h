@@ -166,6 +166,9 @@ mrom_status mrom_rom_from_packed(mrom_handle h, int32_t n_obj, const mrom_packed
 int32_t mrom_rom_rank(mrom_rom_t rom);
 void mrom_rom_free(mrom_rom_t rom);
 
+/* mrom_rom_free of n objects (host array, entries set to NULL; NULL entries are skipped). */
+void mrom_rom_free_batch(mrom_rom_t* roms, int32_t n);
+
 /* ------------------------------------------------ off-line stage (project) */
 
 /* The full-order problem of Sect. 3.1 as the projection needs it (all DEVICE

@@ -142,6 +142,16 @@ class ReducedObject:
         return [cls._wrap(handle, ctypes.c_void_p(out[k]), int(items[k]["r"]), items[k].get("G") is not None)
                 for k in range(len(items))]
 
+    @staticmethod
+    def close_all(objs):
+        """Release many objects with one library call (mrom_rom_free_batch)."""
+        live = [o for o in objs if o._rom]
+        arr = (ctypes.c_void_p * len(live))(*[o._rom.value if isinstance(o._rom, ctypes.c_void_p) else o._rom
+                                              for o in live])
+        lib().mrom_rom_free_batch(arr, len(live))
+        for o in live:
+            o._rom = ctypes.c_void_p()
+
     @classmethod
     def from_packed(cls, handle: Handle, packed):
         """mrom_rom_from_packed: the objects of a PackedDictionary (one copy of its buffer)."""

@@ -19,7 +19,7 @@ EXPORTS = [
     "mrom_sweep_noalloc", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "mrom_sweep_mixed",
     "mrom_project_dirs", "mrom_set_projection_precision", "mrom_set_solver", "mrom_plan_solver_counts",
     "mrom_plan_timing", "mrom_rom_from_reduced_batch", "mrom_invariants", "mrom_project_mu",
-    "mrom_rom_static_rank", "mrom_rom_mu_state", "mrom_fom_solve", "mrom_rom_from_packed",
+    "mrom_rom_static_rank", "mrom_rom_mu_state", "mrom_fom_solve", "mrom_rom_from_packed", "mrom_rom_free_batch",
 ]
 
 
@@ -130,6 +130,7 @@ def _declare(L):
         "mrom_rom_from_reduced": (ctypes.c_int, [vp, ctypes.POINTER(mrom_reduced_desc), ctypes.POINTER(vp)]),
         "mrom_rom_rank": (i32, [vp]),
         "mrom_rom_static_rank": (i32, [vp]),
+        "mrom_rom_free_batch": (None, [ctypes.POINTER(vp), i32]),
         "mrom_rom_from_packed": (ctypes.c_int, [vp, i32, ctypes.POINTER(mrom_packed_obj), vp, ctypes.c_size_t,
                                                 ctypes.POINTER(vp)]),
         "mrom_fom_solve": (ctypes.c_int, [vp, ctypes.POINTER(mrom_fom), ctypes.POINTER(ctypes.c_double), i32,

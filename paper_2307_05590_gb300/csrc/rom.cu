@@ -166,6 +166,14 @@ extern "C" mrom_status mrom_rom_from_reduced(mrom_handle h, const mrom_reduced_d
 
 extern "C" int32_t mrom_rom_rank(mrom_rom_t rom) { return rom ? rom->r : 0; }
 
+extern "C" void mrom_rom_free_batch(mrom_rom_t* roms, int32_t n) {
+  if (!roms) return;
+  for (int32_t k = 0; k < n; ++k) {
+    mrom_rom_free(roms[k]);
+    roms[k] = nullptr;
+  }
+}
+
 extern "C" void mrom_rom_free(mrom_rom_t rom) {
   if (!rom) return;
   if (rom->mu_block) cudaFree(rom->mu_block);

@@ -300,3 +300,16 @@ def test_packed_dictionary_matches_batch(mrom):
     items[2]["K"][3, 5] = np.nan
     with pytest.raises(mrom.MromError):
         mrom.ReducedObject.from_packed(h, mrom.PackedDictionary(items))
+
+
+def test_batch_release(mrom):
+    """ReducedObject.close_all releases objects of one packed allocation with one call."""
+    from workloads import reduced_object
+    h = mrom.Handle(0)
+    objs = [reduced_object(20230711, 950 + k, r) for k, r in enumerate([6, 9, 11])]
+    pk = mrom.PackedDictionary([dict(r=o.r, K=o.K, C=o.C, B=o.B, c00=o.c00, G=o.G, K_in=o.K_in) for o in objs])
+    roms = mrom.ReducedObject.from_packed(h, pk)
+    mrom.ReducedObject.close_all(roms)
+    assert all(not x._rom for x in roms)
+    mrom.ReducedObject.close_all(roms)          # already released: nothing to do
+    h.synchronize()
