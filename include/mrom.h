@@ -63,7 +63,11 @@ typedef struct mrom_plan_s* mrom_plan;
 
 /* Create a handle on CUDA device `device`.  `cuda_stream` is the cudaStream_t
  * every call of this handle runs on (NULL: CUDA's default stream).  The
- * handle owns a small device status word and no other device memory. */
+ * handle owns a small device status word and no other device memory.  The
+ * library's per-call buffers are stream-ordered allocations from the device's
+ * default memory pool; the first handle raises that pool's release threshold
+ * (a setting of this process) to 8 GiB, so that freed buffers stay mapped for
+ * the next call instead of returning to the driver at each synchronisation. */
 mrom_status mrom_create(int device, void* cuda_stream, mrom_handle* out);
 mrom_status mrom_destroy(mrom_handle h);
 /* Replace the stream used by later calls (NULL: CUDA's default stream). */

@@ -23,6 +23,10 @@ mrom_status cuda_fail(mrom_ctx* h, cudaError_t e, const char* what) {
 
 using namespace mrom;
 
+namespace {
+constexpr uint64_t kPoolKeepBytes = 8ull << 30;  // freed stream-ordered memory kept for reuse
+}  // namespace
+
 extern "C" mrom_status mrom_create(int device, void* cuda_stream, mrom_handle* out) {
   if (!out) return MROM_EINVAL;
   *out = nullptr;
@@ -37,6 +41,21 @@ extern "C" mrom_status mrom_create(int device, void* cuda_stream, mrom_handle* o
   h->smem_optin = (size_t)optin;
   // NULL is CUDA's default stream, as everywhere in the runtime API
   h->stream = static_cast<cudaStream_t>(cuda_stream);
+  // The library's per-call blocks are stream-ordered allocations from the device's default pool.
+  // With the pool's default release threshold (0) the memory goes back to the driver at every
+  // synchronisation and is mapped again by the next call; keep up to kPoolKeepBytes cached in
+  // this process instead (a process-local pool attribute, raised only if it is lower).
+  {
+    cudaMemPool_t pool = nullptr;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t cur = 0;
+      if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < kPoolKeepBytes) {
+        uint64_t keep = kPoolKeepBytes;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+    }
+    cudaGetLastError();
+  }
   if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
       cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
