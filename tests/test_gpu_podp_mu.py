@@ -209,22 +209,23 @@ def test_sweep_with_certificate_at_scales_matches_oracle(mrom, lu):
     rom, r, m = mrom.mrom_project_mu(h, fom, mu, torch.as_tensor(np.ascontiguousarray(cols), device="cuda"),
                                      tol_sigma=1e-7)
     wo = log_omegas(1e1, 1e5, 19)
-    s_mu = np.array([0.7, 1.0, 2.3, 4.0, 9.0])
+    s_mu = np.array([0.7, 1.0, 2.3, 4.0, 9.0, 1.8])
+    s_sigma = np.array([1.0, 1.0, 1.0, 1.0, 1.0, 1.6])   # the last instance scales sigma as well
     n = s_mu.size
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     R = torch.empty((n, wo.size, 3, 3), dtype=torch.float64, device="cuda")
     I = torch.empty_like(R)
     Dg = torch.empty_like(R)
-    mrom.mrom_sweep(h, [rom] * n, t(wo), wo.size, R, I, Dg, s_mu=t(s_mu))
+    mrom.mrom_sweep(h, [rom] * n, t(wo), wo.size, R, I, Dg, s_mu=t(s_mu), s_sigma=t(s_sigma))
     h.synchronize()
     R, I, Dg = R.cpu().numpy(), I.cpu().numpy(), Dg.cpu().numpy()
     a3 = model.alpha ** 3
-    for k, sm in enumerate(s_mu):
-        Rr, Ir = podp_mu.signature(model, wo, s_mu=sm)
-        Dr = podp_mu.certificate(model, wo, s_mu=sm)
+    for k, (sm, ss) in enumerate(zip(s_mu, s_sigma)):
+        Rr, Ir = podp_mu.signature(model, wo, s_mu=sm, s_sigma=ss)
+        Dr = podp_mu.certificate(model, wo, s_mu=sm, s_sigma=ss)
         sR = np.abs(Rr).reshape(wo.size, -1).max(1)
-        sI = wo * a3 / 4 * np.abs(podp_mu.static_state(model, sm)["c00"]).max()
-        sD = podp_mu.certificate_term_scale(model, wo, s_mu=sm)
+        sI = wo * ss * a3 / 4 * np.abs(podp_mu.static_state(model, sm)["c00"]).max()
+        sD = podp_mu.certificate_term_scale(model, wo, s_mu=sm, s_sigma=ss)
         eR = (np.abs(R[k] - Rr).reshape(wo.size, -1).max(1) / sR).max()
         eI = (np.abs(I[k] - Ir).reshape(wo.size, -1).max(1) / sI).max()
         eD = (np.abs(Dg[k] - Dr).reshape(wo.size, -1).max(1) / sD).max()
