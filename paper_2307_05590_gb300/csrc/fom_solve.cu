@@ -298,25 +298,50 @@ mrom_status fom_solve(mrom_ctx* h, const mrom_fom* fom, const double* omega_host
   e = cudaGetLastError();
   std::vector<CocgState> hs(nc);
   const int chunk = 25;
+  auto iteration = [&]() {
+    cocg_spmv_kernel<<<nblk, kFT, 0, st>>>(fom->K_rowptr, fom->K_col, fom->K_val, om, fom->C_diag, fom->M_diag,
+                                           fom->eps, n, nc, P, Q, part);
+    cocg_reduce_kernel<<<1, kRedT, 0, st>>>(part, nblk, nc, 1, tol * tol, sts);
+    cocg_update_kernel<<<nblk, kFT, 0, st>>>(n, nc, sts, Dinv, Wt, X, Rv, P, Q, part);
+    cocg_reduce_kernel<<<1, kRedT, 0, st>>>(part, nblk, nc, 2, tol * tol, sts);
+    cocg_direction_kernel<<<nblk, kFT, 0, st>>>(n, nc, sts, Dinv, Rv, P);
+  };
+  // One chunk of iterations captured once as a CUDA graph and replayed (the launches of a
+  // small problem cost more than its kernels); direct launches when the handle runs on the
+  // legacy default stream (which cannot be captured) or the capture fails.
+  cudaGraphExec_t chunk_exec = nullptr;
+  if (e == cudaSuccess && st != nullptr && max_iter >= chunk) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      for (int k = 0; k < chunk; ++k) iteration();
+      const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+      if (ce == cudaSuccess && graph && cudaGraphInstantiate(&chunk_exec, graph, 0) != cudaSuccess)
+        chunk_exec = nullptr;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();  // a failed capture leaves only the fallback
+  }
   int it = 0;
   bool done = false;
   while (e == cudaSuccess && !done && it < max_iter) {
-    const int k_end = std::min(max_iter, it + chunk);
-    for (; it < k_end && e == cudaSuccess; ++it) {
-      cocg_spmv_kernel<<<nblk, kFT, 0, st>>>(fom->K_rowptr, fom->K_col, fom->K_val, om, fom->C_diag, fom->M_diag,
-                                             fom->eps, n, nc, P, Q, part);
-      cocg_reduce_kernel<<<1, kRedT, 0, st>>>(part, nblk, nc, 1, tol * tol, sts);
-      cocg_update_kernel<<<nblk, kFT, 0, st>>>(n, nc, sts, Dinv, Wt, X, Rv, P, Q, part);
-      cocg_reduce_kernel<<<1, kRedT, 0, st>>>(part, nblk, nc, 2, tol * tol, sts);
-      cocg_direction_kernel<<<nblk, kFT, 0, st>>>(n, nc, sts, Dinv, Rv, P);
-      h->launches += 5;
-      e = cudaGetLastError();
+    if (chunk_exec && it + chunk <= max_iter) {
+      e = cudaGraphLaunch(chunk_exec, st);
+      it += chunk;
+      h->launches += 5 * chunk;
+    } else {
+      const int k_end = std::min(max_iter, it + chunk);
+      for (; it < k_end && e == cudaSuccess; ++it) {
+        iteration();
+        h->launches += 5;
+        e = cudaGetLastError();
+      }
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), sts, nc * sizeof(CocgState), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     done = true;
     for (int c = 0; c < nc && e == cudaSuccess; ++c) done = done && !hs[c].active;
   }
+  if (chunk_exec) cudaGraphExecDestroy(chunk_exec);
   if (e == cudaSuccess) {
     cocg_store_kernel<<<(unsigned)std::min<int64_t>(65535 * 4, (n * nc + 255) / 256), 256, 0, st>>>(X, n, nc, Qout, ldq);
     ++h->launches;
