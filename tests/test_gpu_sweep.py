@@ -313,3 +313,33 @@ def test_batch_release(mrom):
     assert all(not x._rom for x in roms)
     mrom.ReducedObject.close_all(roms)          # already released: nothing to do
     h.synchronize()
+
+
+@pytest.mark.parametrize("lu", [False, True], ids=["auto", "lu"])
+def test_sweep_at_permeability_scales_for_objects_without_static_reduction(mrom, lu):
+    """mrom_sweep with s_mu on objects that carry K_in but no reduced static problem: K(s) =
+    K + (1/s - 1) K_in with b and c00 fixed, as the oracle's forward model of the gradients."""
+    import torch
+    from oracle import grads
+    from workloads import log_omegas, reduced_object
+    h = mrom.Handle(0)
+    h.set_solver(lu=lu)
+    objs = [reduced_object(20230711, 960 + k, r) for k, r in enumerate([6, 30, 71])]
+    roms = [mrom.ReducedObject.from_workload(h, o) for o in objs]
+    wo = log_omegas(1e1, 1e8, 41)
+    ss = np.array([1.0, 0.7, 1.9])
+    sm = np.array([3.0, 0.5, 17.0])
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    R = torch.empty((3, wo.size, 3, 3), dtype=torch.float64, device="cuda")
+    I = torch.empty_like(R)
+    mrom.mrom_sweep(h, roms, t(wo), wo.size, R, I, s_sigma=t(ss), s_mu=t(sm))
+    h.synchronize()
+    for k, o in enumerate(objs):
+        Rr, Ir = grads.forward(o, wo, ss[k], sm[k])
+        assert np.abs(R[k].cpu().numpy() - Rr).max() <= 1e-10 * np.abs(Rr).max()
+        sI = wo * ss[k] * o.alpha ** 3 / 4 * np.abs(o.c00).max()
+        assert (np.abs(I[k].cpu().numpy() - Ir).reshape(wo.size, -1).max(1) / sI).max() <= 1e-10
+    D = torch.empty_like(R)
+    with pytest.raises(mrom.MromError):          # no extended Gram: no certificate at a scale
+        mrom.mrom_sweep(h, roms, t(wo), wo.size, R, I, D, s_mu=t(sm))
+    h.set_solver(lu=False)
