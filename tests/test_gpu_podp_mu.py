@@ -240,3 +240,27 @@ def test_sweep_with_certificate_at_scales_matches_oracle(mrom, lu):
     with pytest.raises(mrom.MromError):       # no extended Gram: no certificate at a scale
         plain = mrom.ReducedObject.from_workload(h, __import__("workloads").reduced_object(20230711, 1, 12))
         mrom.mrom_sweep(h, [plain], t(wo), wo.size, R1, I1, D1, s_mu=t([2.0]))
+
+
+def test_sweep_values_at_scales_without_certificate(mrom, case):
+    """mrom_sweep with s_mu (values only) on an object projected without a certificate inner
+    product gives the oracle's R and I at each scale, as mrom_sweep_vjp does."""
+    import torch
+    from oracle import podp_mu
+    from workloads import log_omegas
+    model = case["model"]
+    wo = log_omegas(1e1, 1e5, 13)
+    s_mu = np.array([0.6, 2.5, 7.0])
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    h = case["h"]
+    R = torch.empty((s_mu.size, wo.size, 3, 3), dtype=torch.float64, device="cuda")
+    I = torch.empty_like(R)
+    mrom.mrom_sweep(h, [case["rom"]] * s_mu.size, t(wo), wo.size, R, I, s_mu=t(s_mu))
+    h.synchronize()
+    a3 = model.alpha ** 3
+    for k, sm in enumerate(s_mu):
+        Rr, Ir = podp_mu.signature(model, wo, s_mu=sm)
+        eR = (np.abs(R[k].cpu().numpy() - Rr).reshape(wo.size, -1).max(1) / np.abs(Rr).reshape(wo.size, -1).max(1)).max()
+        sI = wo * a3 / 4 * np.abs(podp_mu.static_state(model, sm)["c00"]).max()
+        eI = (np.abs(I[k].cpu().numpy() - Ir).reshape(wo.size, -1).max(1) / sI).max()
+        assert eR <= 1e-10 and eI <= 1e-10, (k, eR, eI)

@@ -271,6 +271,7 @@ def test_packed_dictionary_matches_batch(mrom):
     objs = [reduced_object(20230711, 900 + k, r) for k, r in enumerate([7, 40, 96, 13])]
     items = [dict(r=o.r, K=o.K, C=o.C, B=o.B, c00=o.c00, G=o.G if k != 1 else None, K_in=o.K_in,
                   alpha=o.alpha, alpha_lb=o.alpha_lb, vol_B=o.vol_B) for k, o in enumerate(objs)]
+    items[3]["Me"] = 1e-4 * np.eye(objs[3].r, dtype=np.complex128)   # an Me block in the region
     pk = mrom.PackedDictionary(items)
     a = mrom.ReducedObject.from_packed(h, pk)
     b = mrom.ReducedObject.batch(h, items)
