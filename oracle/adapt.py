@@ -1,5 +1,7 @@
 """Adaptive snapshot selection, Algorithm 1 (Sect. 4.4).
 
+Test infrastructure: only tests, the smoke check and the benchmark's CPU baseline use it.
+
 Readings where the algorithm leaves details open:
 * certificates are evaluated on the output frequency grid;
 * interval n is [omega_n, omega_{n+1}) over the sorted snapshot frequencies,

@@ -1,5 +1,7 @@
 """A-posteriori error certificate, Lemma 4.2 (Eq. (20)).
 
+Test infrastructure: only tests, the smoke check and the benchmark's CPU baseline use it.
+
 The residual of direction i for the PODP solution q_i = U_i p_i is
 rho_i = r_i - A U_i p_i = i omega C o_i - (K + eps M) U_i p_i + i omega C U_i p_i
       = Phi_i w^(i),   Phi_i = [C o_i | (K + eps M) U_i | C U_i],

@@ -1,5 +1,7 @@
 """Full-order solutions and the Full Matrix Method (FMM), Sect. 3.1-3.2.
 
+Test infrastructure: only tests, the smoke check and the benchmark's CPU baseline use it.
+
 Notation: q_i[omega] are the full-order solution coefficients of direction i
 (Eq. (9)), o~_i the theta~^(0) coefficients, x_i the coefficients of
 e_i x xi, and alpha the object size.  With one discrete space for theta~^(0)

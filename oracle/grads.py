@@ -1,5 +1,7 @@
 """Derivatives of the reduced tensors with respect to omega, s_sigma and s_mu.
 
+Test infrastructure: only tests, the smoke check and the benchmark's CPU baseline use it.
+
 For a shared-basis reduced object with a conductivity scale s_sigma and a
 permeability scale s_mu (K(s_mu) = K_out + K_in / s_mu):
   A = K(s_mu) - i omega s_sigma C,  A P = i omega s_sigma B,

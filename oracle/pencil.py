@@ -1,5 +1,7 @@
 """Second, independent reduced sweep through the Hermitian pencil (K_r + eps M_r, C_r).
 
+Test infrastructure: only tests, the smoke check and the benchmark's CPU baseline use it.
+
 For one basis shared by the three directions, the generalized eigenproblem
 (K_r + eps M_r) v = lambda C_r v with V^H C_r V = I gives
 A(omega)^-1 = V (Lambda - i omega I)^-1 V^H, so

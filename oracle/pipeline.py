@@ -1,4 +1,7 @@
-"""Off-line stage of PODP end to end: snapshots -> TSVD -> projection -> Gram."""
+"""Off-line stage of PODP end to end: snapshots -> TSVD -> projection -> Gram.
+
+Test infrastructure: only tests, the smoke check and the benchmark's CPU baseline use it.
+"""
 from __future__ import annotations
 
 import numpy as np

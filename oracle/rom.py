@@ -1,5 +1,7 @@
 """Galerkin reduced-order model and the Matrix Method (Sects. 4.2-4.3).
 
+Test infrastructure: only tests, the smoke check and the benchmark's CPU baseline use it.
+
 A ReducedModel holds, for the three directions i = 1..3 with (possibly
 different) bases U_i, the omega-independent quantities the Matrix Method
 precomputes (Eqs. (17)-(19)):

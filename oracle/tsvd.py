@@ -1,4 +1,7 @@
-"""Snapshot SVD and truncation (Sect. 4.1, Eqs. (13)-(15))."""
+"""Snapshot SVD and truncation (Sect. 4.1, Eqs. (13)-(15)).
+
+Test infrastructure: only tests, the smoke check and the benchmark's CPU baseline use it.
+"""
 from __future__ import annotations
 
 import numpy as np
