@@ -417,7 +417,12 @@ mrom_status mrom_certificate(mrom_handle h, const mrom_rom_t* roms, int32_t n_ob
 /* A plan fixes a batch of objects and a frequency count once (device object
  * table, cost-sorted work list); mrom_plan_sweep then runs the same sweep as
  * mrom_sweep with no host-side preparation.  The plan keeps pointers to the
- * objects, which must outlive it. */
+ * objects, which must outlive it.  mrom_plan_sweep allocates nothing and does
+ * not wait on the host (stream-ordered memsets and kernel launches only), so a
+ * caller may capture it on the handle's stream into a CUDA graph and replay the
+ * graph (after one direct call, which sets the kernels' shared-memory limits);
+ * a replay reads omega and writes R, I, Delta at the captured addresses, and
+ * errors detected on the device surface at the next mrom_synchronize. */
 mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int32_t n_w,
                              mrom_plan* out);
 mrom_status mrom_plan_sweep(mrom_plan plan, const double* omega, int32_t omega_stride,

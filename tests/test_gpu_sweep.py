@@ -344,3 +344,42 @@ def test_sweep_at_permeability_scales_for_objects_without_static_reduction(mrom,
     with pytest.raises(mrom.MromError):          # no extended Gram: no certificate at a scale
         mrom.mrom_sweep(h, roms, t(wo), wo.size, R, I, D, s_mu=t(sm))
     h.set_solver(lu=False)
+
+
+def test_plan_sweep_replays_as_a_cuda_graph(mrom):
+    """A plan's sweep issues only stream-ordered work (no allocation, no host wait), so a caller
+    can capture it once into a CUDA graph and replay it; the replay gives the direct call's
+    outputs bit for bit, and follows new frequencies written in place."""
+    import torch
+    from workloads import log_omegas, reduced_object
+    s = torch.cuda.Stream()
+    h = mrom.Handle(0, s.cuda_stream)
+    objs = [reduced_object(20230711, 980 + k, r) for k, r in enumerate([9, 41, 77])]
+    roms = [mrom.ReducedObject.from_workload(h, o) for o in objs]
+    n_w = 60
+    plan = mrom.Plan(h, roms, n_w)
+    with torch.cuda.stream(s):
+        om = torch.as_tensor(log_omegas(1e1, 1e8, n_w), device="cuda")
+        R = torch.zeros((3, n_w, 3, 3), dtype=torch.float64, device="cuda")
+        I, D = torch.zeros_like(R), torch.zeros_like(R)
+    plan.sweep(om, R, I, D)
+    h.synchronize()
+    ref = [x.clone() for x in (R, I, D)]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        plan.sweep(om, R, I, D)
+    for x in (R, I, D):
+        x.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for x, y in zip((R, I, D), ref):
+        assert torch.equal(x, y)
+    with torch.cuda.stream(s):
+        om.mul_(1.5)                        # new frequencies in place, then replay
+    g.replay()
+    torch.cuda.synchronize()
+    plan.sweep(om, *ref)
+    h.synchronize()
+    for x, y in zip((R, I, D), ref):
+        assert torch.equal(x, y)
+    plan.close()
