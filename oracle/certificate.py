@@ -104,3 +104,22 @@ def residual_norms_direct(problem, U, omega: float, p: list, X) -> np.ndarray:
         z = lu.solve(rho.real) + 1j * lu.solve(rho.imag)
         out[i] = np.real(np.vdot(rho, z))
     return out
+
+
+def residual_differences_direct(problem, U, omega: float, p: list, X) -> np.ndarray:
+    """||r^_i - r^_j||^2 for every pair (i, j), from the explicit full-order residual vectors
+    rho_i = i omega C o_i - A U_i p_i and one sparse LU of X: (rho_i - rho_j)^H X^-1 (rho_i - rho_j).
+    Pin for the off-diagonal entries of Lemma 4.2, which the Gram form gets from a cross term."""
+    Us = list(U) if isinstance(U, (list, tuple)) else [U, U, U]
+    o = problem.o_tilde + problem.x
+    A = (sp.csc_matrix(problem.K, dtype=np.complex128)
+         + sp.diags(problem.eps * problem.M - 1j * omega * problem.C))
+    lu = spla.splu(sp.csc_matrix(X, dtype=np.float64))
+    rho = [1j * omega * problem.C * o[i] - A @ (Us[i] @ p[i]) for i in range(3)]
+    out = np.empty((3, 3))
+    for i in range(3):
+        for j in range(3):
+            d = rho[i] - rho[j]
+            z = lu.solve(d.real) + 1j * lu.solve(d.imag)
+            out[i, j] = np.real(np.vdot(d, z))
+    return out

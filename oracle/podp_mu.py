@@ -169,6 +169,24 @@ def residual_norms_direct(model: MuModel, problem, U: np.ndarray, V: np.ndarray,
     return out
 
 
+def residual_differences_direct(model: MuModel, problem, U: np.ndarray, V: np.ndarray, X_diag: np.ndarray,
+                                omega: float, s_mu: float) -> np.ndarray:
+    """||r^_i - r^_j||^2 for every pair (i, j) from the explicit full-order residual vectors of the
+    problem at scale s_mu (pin for the off-diagonal entries of Lemma 4.2)."""
+    st = static_state(model, s_mu)
+    K = problem.K - problem.K_in + problem.K_in / s_mu
+    A = (sp.csc_matrix(K, dtype=np.complex128) + sp.diags(problem.eps * problem.M - 1j * omega * problem.C))
+    P = np.linalg.solve(model.K_out + model.K_in / s_mu + model.Me - 1j * omega * model.C, 1j * omega * st["B"])
+    o = problem.x + np.real(V @ st["y"]).T
+    rho = [1j * omega * problem.C * o[i] - A @ (U @ P[:, i]) for i in range(3)]
+    out = np.empty((3, 3))
+    for i in range(3):
+        for j in range(3):
+            d = rho[i] - rho[j]
+            out[i, j] = np.real(np.vdot(d, d / X_diag))
+    return out
+
+
 def static_state(model: MuModel, s: float):
     """y(s), b(s), c00(s), N0(s) and their derivatives with respect to s.
 

@@ -30,6 +30,50 @@ def test_gram_form_equals_residual_norm(poor_rom):
         assert np.allclose(gram, direct, rtol=1e-6)
 
 
+@pytest.fixture(scope="module")
+def skew_rom():
+    """12^3 grid with an object of two overlapping boxes that has no mirror plane, so the three
+    directions' residuals are not orthogonal and the cross terms of Lemma 4.2 do not vanish;
+    two snapshots make a poor ROM whose residual is far above the Gram form's rounding floor."""
+    from workloads.fit import Material
+    mats = (Material((0.25, 0.25, 0.25), (0.5, 0.75, 0.5), 5.96e7, 1.0),
+            Material((0.5, 0.25, 0.4), (0.75, 0.5, 0.75), 5.96e7, 1.0))
+    p = fit_problem(12, mats)
+    D = full_order_snapshots(p, log_omegas(1e1, 1e5, 2))
+    model, U, _ = pipeline.build_model(p, D, tol_sigma=1e-6, omega_min=10.0)
+    return p, U, model
+
+
+def test_off_diagonal_certificate_matches_explicit_residual_differences(skew_rom):
+    """Delta_ij for i != j (Lemma 4.2) equals alpha^3/(8 alpha_LB)(||r_i||^2 + ||r_j||^2 + ||r_i - r_j||^2)
+    with every norm taken from explicit full-order residual vectors, not from the Gram form.
+    Tolerance: 1e-6 relative plus the Gram form's absolute rounding floor 1e-13 |w|^T |G| |w|.
+    A flipped sign of the cross term Re(w_i^H G w_j) would move Delta_ij by
+    4 alpha^3/(8 alpha_LB) Re(w_i^H G w_j); the test checks that this is far above the tolerance."""
+    p, U, model = skew_rom
+    X = certificate.inner_product_matrix(p, 10.0)
+    wo = np.array([13.7, 210.0, 1370.0])
+    P = rom.reduced_solve(model, wo)
+    Dl = certificate.certificate(model, wo, P)
+    a = model.alpha ** 3 / (8.0 * model.alpha_lb)
+    absG = np.abs(model.gram)
+    for n, w in enumerate(wo):
+        pn = [P[i][n] for i in range(3)]
+        nrm = certificate.residual_norms_direct(p, U, w, pn, X)
+        dif = certificate.residual_differences_direct(p, U, w, pn, X)
+        assert np.abs(np.diag(dif)).max() == 0.0
+        expect = a * (nrm[:, None] + nrm[None, :] + dif)
+        W = certificate.residual_weights(model, w, pn)
+        floor = 1e-13 * 2.0 * a * max(np.abs(x) @ absG @ np.abs(x) for x in W)
+        tol = 1e-6 * np.abs(expect) + floor
+        assert (np.abs(Dl[n] - expect) <= tol).all(), w
+        for i in range(3):
+            for j in range(3):
+                if i != j:
+                    cross = np.real(np.vdot(W[i], model.gram @ W[j]))
+                    assert 4.0 * a * abs(cross) > 100.0 * tol[i, j], (w, i, j)
+
+
 def test_certificate_structure(poor_rom):
     p, U, model = poor_rom
     wo = log_omegas(1e1, 1e5, 9) * 1.2

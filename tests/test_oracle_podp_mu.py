@@ -167,3 +167,24 @@ def test_certificate_gram_form_matches_the_full_order_residual(setup):
         Dfar = podp_mu.certificate(model, W_SAMPLES, s_mu=1.6 * s)
         for k in range(len(W_SAMPLES)):
             assert np.abs(D0[k]).max() <= 1e-5 * np.abs(Dfar[k]).max(), (s, k)
+
+
+def test_certificate_off_diagonal_matches_full_order_residual_differences(setup):
+    """Delta_ij for i != j at a scale s (Lemma 4.2) equals alpha^3/(8 alpha_LB)(||r_i||^2 + ||r_j||^2
+    + ||r_i - r_j||^2) with the three norms from explicit full-order residual vectors; a sign slip
+    in the extended Gram's cross term would move Delta_ij by 4 alpha^3/(8 alpha_LB) Re(w_i^H G w_j)."""
+    probs, U, V, model = setup
+    p1 = probs[1.0]
+    X = p1.eps * p1.M + 10.0 * p1.C
+    podp_mu.attach_extended_gram(model, p1, U, V, X)
+    a = model.alpha ** 3 / (8.0 * model.alpha_lb)
+    for w, s in ((3e2, 1.7), (4e3, 0.6), (2e3, 2.5)):
+        nrm = podp_mu.residual_norms_direct(model, p1, U, V, X, w, s)
+        dif = podp_mu.residual_differences_direct(model, p1, U, V, X, w, s)
+        D = podp_mu.certificate(model, [w], s_mu=s)[0]
+        expect = a * (nrm[:, None] + nrm[None, :] + dif)
+        assert np.allclose(D, expect, rtol=1e-7, atol=1e-10 * expect.max()), (w, s)
+        # the cross term is a sizeable part of every off-diagonal entry
+        cross = 0.5 * (nrm[:, None] + nrm[None, :] - dif)
+        off = ~np.eye(3, dtype=bool)
+        assert (4.0 * a * np.abs(cross[off]) > 1e-3 * expect[off]).all(), (w, s)
