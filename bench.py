@@ -42,8 +42,7 @@ sys.path.insert(0, ROOT)
 METRIC = "spectral-signature tensor evals/sec (objects x freqs), FP64, with certificate"
 UNIT = "evals/s"
 SM_COUNT_NOMINAL = 152
-DFMA_PER_CLK_PER_SM = 2           # measured: GB300 DFMA rate saturates at 4 flop/clk/SM
-FP64_MEASURED_TFLOPS = 1.189      # DFMA microbenchmark on this machine's GB300 (1.96 GHz)
+DFMA_PER_CLK_PER_SM = 2           # GB300 DFMA rate: 4 flop/clk/SM (mrom_fp64_peak measures it in every run)
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one pencil_sweep_kernel launch on
 # this workload, from a --set full ncu capture of the current kernel (97,853,696 + 373,272,320 bytes);
 # None once the kernel changes until it is captured again
@@ -151,18 +150,55 @@ def dictionary(n_obj: int, seed: int):
     return reduced_dictionary(n_obj, seed=seed)
 
 
-def oracle_sample_rate(objs, omegas, n_sample: int):
-    """Evaluations/s of the CPU oracle on n_sample objects spread over the dictionary."""
+def sample_indices(n_obj: int, n_sample: int) -> np.ndarray:
+    """n_sample objects spread evenly over the dictionary (the CPU baseline's and the reference arm's sample)."""
+    return np.linspace(0, n_obj - 1, min(n_sample, n_obj)).round().astype(int)
+
+
+def oracle_sample_rate(objs, omegas, n_sample: int, keep: bool = False):
+    """Evaluations/s of the CPU oracle on n_sample objects spread over the dictionary; with keep,
+    also its (model, P, R, I, Delta) per sampled object (kept outside the timed loop's arithmetic)."""
     from oracle import certificate, rom
-    idx = np.linspace(0, len(objs) - 1, n_sample).round().astype(int)
+    idx = sample_indices(len(objs), n_sample)
+    kept = []
     t0 = time.perf_counter()
     for k in idx:
         model = rom.from_reduced_object(objs[k])
         P = rom.reduced_solve(model, omegas)
-        rom.mm_tensors(model, omegas, P)
-        certificate.certificate(model, omegas, P)
+        R, I = rom.mm_tensors(model, omegas, P)
+        Dl = certificate.certificate(model, omegas, P)
+        if keep:
+            kept.append((model, P, R, I, Dl))
     dt = time.perf_counter() - t0
-    return n_sample * omegas.size / dt, dt, [int(objs[k].r) for k in idx]
+    return idx.size * omegas.size / dt, dt, [int(objs[k].r) for k in idx], kept
+
+
+def accuracy_vs_oracle(omegas, kept, Rg, Ig, Dg) -> dict:
+    """Max relative error of the GPU outputs (Rg, Ig, Dg: [n_sample][n_w][3][3], host) against the
+    oracle's on the sampled objects at every frequency: R against max_ij |R| per frequency, I and
+    Delta against the size of the terms they are sums of (I -> 0 at high omega by cancellation of
+    terms of size omega alpha^3/4 |c00|; Delta is a difference of Gram quadratic forms)."""
+    from oracle import certificate
+    eR = eI = eD = 0.0
+    for s, (model, P, R, I, Dl) in enumerate(kept):
+        a3 = model.alpha ** 3
+        C = model.C[0][0]
+        B = np.stack([model.b(i) for i in range(3)], 1)
+        absG = np.abs(model.gram)
+        Pm = np.stack(P, axis=2)                         # [n_w][r][3]
+        hc = np.abs(np.einsum("wki,kl,wlj->wij", Pm.conj(), C, Pm)).reshape(omegas.size, -1).max(1)
+        bp = np.abs(np.einsum("ki,wkj->wij", B.conj(), Pm)).reshape(omegas.size, -1).max(1)
+        sI = omegas * a3 / 4 * (np.abs(model.c00).max() + hc + 2 * bp)
+        sD = np.empty(omegas.size)
+        for n, w in enumerate(omegas):
+            W = certificate.residual_weights(model, w, [P[i][n] for i in range(3)])
+            sD[n] = a3 / (4 * model.alpha_lb) * max(np.abs(x) @ absG @ np.abs(x) for x in W)
+        flat = lambda x: x.reshape(omegas.size, -1)
+        eR = max(eR, float((np.abs(flat(Rg[s] - R)).max(1) / np.abs(flat(R)).max(1)).max()))
+        eI = max(eI, float((np.abs(flat(Ig[s] - I)).max(1) / sI).max()))
+        eD = max(eD, float((np.abs(flat(Dg[s] - Dl)).max(1) / sD).max()))
+    return {"R": eR, "I": eI, "Delta": eD, "pairs": len(kept) * int(omegas.size),
+            "normalisation": "R: |diff| / max_ij |R| per (object, omega); I, Delta: |diff| / term scale"}
 
 
 def blas_threads() -> int:
@@ -496,12 +532,12 @@ def run_reference(args, world):
     from workloads import log_omegas
     objs = dictionary(args.n_obj, 20230711)
     wo = log_omegas(1e1, 1e8, args.n_w)
-    n_s = args.ref_sample
+    n_s = min(args.ref_sample, len(objs))
     for _ in range(args.warmup):
         oracle_sample_rate(objs, wo, 1)
     times = []
     for _ in range(args.steps):
-        rate, dt, rs = oracle_sample_rate(objs, wo, n_s)
+        rate, dt, rs, _ = oracle_sample_rate(objs, wo, n_s)
         times.append(dt)
     evals = n_s * args.n_w
     value = evals * len(times) / sum(times)
@@ -512,7 +548,8 @@ def run_reference(args, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config(args),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{n_s} objects (r = {rs}) x {args.n_w} frequencies per step"},
+                         "sample": f"{n_s} objects spread over the dictionary (r = {rs}, mean {np.mean(rs):.1f}) "
+                                   f"x {args.n_w} frequencies per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -528,7 +565,7 @@ def main():
     ap.add_argument("--n-w", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--cpu-sample", type=int, default=20)
-    ap.add_argument("--ref-sample", type=int, default=4)
+    ap.add_argument("--ref-sample", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mixed", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--lu-route", action=argparse.BooleanOptionalAction, default=True)
@@ -665,6 +702,9 @@ def main():
     value = evals_step / (ms_per_step * 1e-3)
 
     n_pen, n_lu = plan.solver_counts()
+    # the sampled objects' outputs of the last timed step, for the accuracy check against the oracle
+    acc_idx = torch.as_tensor(sample_indices(args.n_obj, args.cpu_sample), device=dev)
+    acc_out = [x.index_select(0, acc_idx).cpu().numpy() for x in (R, I, D)]
 
     # ---- rotation invariants (eigenvalues of R~ and I per frequency) of the step's outputs
     eigs = torch.empty((args.n_obj, args.n_w, 3), dtype=torch.float64, device=dev)
@@ -811,21 +851,29 @@ def main():
 
     # ---- CPU oracle baseline (rank 0, single GPU only)
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, srs = oracle_sample_rate(objs, wo, args.cpu_sample)
+        rate, dt, srs, kept = oracle_sample_rate(objs, wo, args.cpu_sample, keep=True)
         cpu = {"value": rate, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-               "sample": f"{args.cpu_sample} objects spread over the dictionary (r = {srs}) x {args.n_w} "
-                         f"frequencies, {dt:.1f} s"}
+               "sample": f"{len(srs)} objects spread over the dictionary (r = {srs}, mean {np.mean(srs):.1f}) x "
+                         f"{args.n_w} frequencies, {dt:.1f} s"}
+        accuracy = accuracy_vs_oracle(wo, kept, *acc_out)
+        accuracy["sample"] = "the CPU baseline's objects, every frequency, outputs of the last timed step"
+        del kept
 
     sm_mhz_max = (clk or {}).get("sm_max_mhz", 2070.0)
     peak_tflops = SM_COUNT_NOMINAL * DFMA_PER_CLK_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
+    # the DFMA rate measured on this device in this run (independent FMA chains on every SM)
+    fp64_measured, _ = m.mrom_fp64_peak(h)
     st = np.array(stages, dtype=np.float64).mean(axis=0)  # mean ms per stage over the timed steps
     achieved = flops_pen / (st[2] * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": SWEEP_DRAM_BYTES_PER_LAUNCH,
                 "kernel": "pencil_sweep_kernel", "flops_per_launch": flops_pen,
-                "peak_note": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 flop x max SM clock; "
-                             f"measured DFMA microbenchmark {FP64_MEASURED_TFLOPS} TFLOP/s"}
+                "peak_note": "derived FP64 pipe peak: 152 SM x 2 DFMA/clk x 2 flop x max SM clock (no FP64 entry "
+                             "in the measured peaks); mrom_fp64_peak (DFMA chains) measured "
+                             f"{fp64_measured:.3f} TFLOP/s in this run",
+                "fp64_peak_measured_in_run": fp64_measured}
     stage_info = {"prep_ms": st[0], "route_ms": st[1], "pencil_sweep_ms": st[2], "lu_sweep_ms": st[3],
                   "prep_flops": flops_prep, "prep_tflops": flops_prep / (st[0] * 1e-3) / 1e12 if st[0] > 0 else None,
                   "objects_pencil": n_pen, "objects_lu": n_lu}
@@ -835,7 +883,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": args.scaling,
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": roofline, "cpu_baseline": cpu, "accuracy_vs_oracle": accuracy, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "wall_s_timed": wall, "per_launch_ms": per_launch_ms, "sweep_config": sweep_cfg,
             "stages": stage_info, "lu_route": lu_route, "mixed_precision": mixed, "projection": proj,
             "gradients": grads, "invariants": inv, "c1_latency": c1, "podp_mu": pmu,

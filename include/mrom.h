@@ -183,11 +183,21 @@ void mrom_rom_free_batch(mrom_rom_t* roms, int32_t n);
  *   o: 3 x n, row i = coefficients of the total theta_i^(0) = theta~_i^(0) + e_i x xi
  *     (so the source is r_i = i omega C o_i, Eq. (9));
  *   X_diag: n positive values of a diagonal inner-product matrix X for the
- *     certificate's Riesz norm ||r||^2 = r^H X^-1 r (Lemma 4.2), or NULL for no
- *     certificate.  With X = eps M + omega_min C, |a(v, v)| >= ||v||_X^2 / sqrt(2)
- *     for omega >= omega_min, so alpha_lb = 1/sqrt(2) is valid (a looser bound
- *     than with X = K + eps M + omega_min C);
- *   alpha, alpha_lb, vol_B, N0 (9 or NULL) as in mrom_reduced_desc. */
+ *     certificate's Riesz norm ||r||^2 = r^H X^-1 r (Lemma 4.2), or NULL.  With
+ *     X = eps M + omega_min C, |a(v, v)| >= ||v||_X^2 / sqrt(2) for omega >= omega_min,
+ *     so alpha_lb = 1/sqrt(2) is valid (a looser bound than the sparse X below);
+ *   alpha, alpha_lb, vol_B, N0 (9 or NULL) as in mrom_reduced_desc;
+ *   X_rowptr, X_col, X_val: a sparse real symmetric positive definite X (CSR, n x n,
+ *     int32 indices), or NULL.  It takes precedence over X_diag.  With
+ *     X = K + eps M + omega_min C, |a(v, v)| >= ||v||_X^2 / sqrt(2) for every
+ *     omega >= omega_min (a(v, v) = v^H (K + eps M) v - i omega v^H C v), so alpha_lb =
+ *     1/sqrt(2).  The library forms X^-1 Phi for the certificate's residual basis Phi
+ *     by Jacobi-preconditioned conjugate gradients, every column together; a column
+ *     stops at r^H D^-1 r <= X_tol^2 b^H D^-1 b (D = diag X; X_tol 0: 1e-13), and a
+ *     column still iterating after X_max_iter iterations (0: 20000) or a breakdown
+ *     (X not SPD) makes the call return MROM_ENOTCONVERGED.  Temporaries: 4 n (2r + 3)
+ *     complex128.
+ * No certificate when X_diag and X_rowptr are both NULL. */
 typedef struct {
   int64_t n;
   const int32_t* K_rowptr;
@@ -202,6 +212,11 @@ typedef struct {
   double alpha_lb;
   double vol_B;
   const double* N0;
+  const int32_t* X_rowptr;
+  const int32_t* X_col;
+  const double* X_val;
+  double X_tol;
+  int32_t X_max_iter;
 } mrom_fom;
 
 #define MROM_MAX_SNAPSHOTS 192
@@ -475,6 +490,15 @@ mrom_status mrom_tune(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int3
  * included.  Asynchronous; MROM_EINVAL for n < 0 or null arrays with n > 0. */
 mrom_status mrom_invariants(mrom_handle h, const double* M, int64_t n, double* eig);
 
+/* ------------------------------------------------------------ measurement */
+
+/* FP64 pipe throughput of the handle's device (not in the paper; the denominator of the FP64
+ * kernels' roofline): independent fused multiply-add chains on every SM, timed with CUDA events
+ * on the handle's stream.  *tflops receives 2 x the FMAs per second / 1e12, *ms (may be NULL)
+ * the kernel's duration.  iters >= 1 (FMA steps per chain; 1 << 16 runs for about 10 ms).
+ * Synchronous. */
+mrom_status mrom_fp64_peak(mrom_handle h, int32_t iters, double* tflops, double* ms);
+
 /* ------------------------------------------------------- allocation-free */
 
 /* mrom_sweep without any device allocation.  Some callers cannot allocate
@@ -492,6 +516,12 @@ mrom_status mrom_invariants(mrom_handle h, const double* M, int64_t n, double* e
  * exits.  The paper has no counterpart to this entry point.
  *  - The first call on a device looks up that array's device address
  *    (cudaGetSymbolAddress); make this first call before any stream capture.
+ *    With CUDA's lazy module loading (the default) the array is committed on a
+ *    device when that first call loads this code, not when the library is
+ *    loaded: a caller that reserves the rest of its memory budget afterwards
+ *    makes one call at start-up first.  The address is kept per device index
+ *    for the life of the process; after a cudaDeviceReset it is stale, so this
+ *    entry point is not for processes that reset a device they used it on.
  *  - Every call reuses the same array (it keeps the previous call's contents):
  *    calls whose work overlaps on the GPU -- on different streams or handles of
  *    the same device -- race and corrupt each other's results; serialise them.

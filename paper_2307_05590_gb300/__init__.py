@@ -23,7 +23,7 @@ __all__ = [
     "mrom_rom_from_reduced", "mrom_rom_free", "mrom_rom_rank", "mrom_sweep", "mrom_certificate",
     "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune", "mrom_sweep_noalloc",
     "FullOrder", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "MromSweep", "signature",
-    "mrom_sweep_mixed", "mrom_project_dirs", "mrom_invariants", "PermeabilityData", "mrom_project_mu",
+    "mrom_sweep_mixed", "mrom_project_dirs", "mrom_invariants", "mrom_fp64_peak", "PermeabilityData", "mrom_project_mu",
     "mrom_rom_mu_state", "mrom_fom_solve", "PackedDictionary",
 ]
 
@@ -387,13 +387,15 @@ def mrom_sweep_noalloc(h: Handle, objs, omega, n_w: int, R, I, Delta=None, *, om
 class FullOrder:
     """Device copy of a full-order problem for mrom_project (torch tensors, caller-owned).
 
-    K: CSR (int32 rowptr, int32 col, float64 val); C, M, X: lumped diagonals (float64);
-    o: (3, n) float64 total theta^(0) coefficients.
+    K: CSR (int32 rowptr, int32 col, float64 val); C, M: lumped diagonals (float64);
+    o: (3, n) float64 total theta^(0) coefficients.  The certificate's inner product X is a
+    lumped diagonal (X, float64 n) or a sparse SPD matrix (X_csr = (rowptr, col, val) as for K,
+    solved by PCG with X_tol and X_max_iter); neither: no certificate.
     """
 
-    def __init__(self, K_rowptr, K_col, K_val, C, o, *, M=None, eps=0.0, X=None, alpha=1.0,
-                 alpha_lb=1.0 / np.sqrt(2.0), vol_B=1.0, N0=None):
-        self.keep = [K_rowptr, K_col, K_val, C, o, M, X, N0]
+    def __init__(self, K_rowptr, K_col, K_val, C, o, *, M=None, eps=0.0, X=None, X_csr=None, X_tol=0.0,
+                 X_max_iter=0, alpha=1.0, alpha_lb=1.0 / np.sqrt(2.0), vol_B=1.0, N0=None):
+        self.keep = [K_rowptr, K_col, K_val, C, o, M, X, N0] + list(X_csr or ())
         f = _abi.mrom_fom()
         f.n = int(C.numel())
         f.K_rowptr, f.K_col, f.K_val = _ptr(K_rowptr), _ptr(K_col), _ptr(K_val)
@@ -401,18 +403,31 @@ class FullOrder:
         f.o, f.X_diag = _ptr(o), _ptr(X)
         f.alpha, f.alpha_lb, f.vol_B = float(alpha), float(alpha_lb), float(vol_B)
         f.N0 = _ptr(N0)
+        if X_csr is not None:
+            f.X_rowptr, f.X_col, f.X_val = (_ptr(a) for a in X_csr)
+        f.X_tol, f.X_max_iter = float(X_tol), int(X_max_iter)
         self.desc = f
+        self.has_cert = X is not None or X_csr is not None
 
     @classmethod
-    def from_fit(cls, problem, device="cuda", *, X=None, alpha_lb=1.0 / np.sqrt(2.0)):
-        """Upload a workloads.FitProblem (K, C, M, o, eps, alpha, |B|, N0) to the device."""
+    def from_fit(cls, problem, device="cuda", *, X=None, alpha_lb=1.0 / np.sqrt(2.0), X_tol=0.0, X_max_iter=0):
+        """Upload a workloads.FitProblem (K, C, M, o, eps, alpha, |B|, N0) to the device.  X: the
+        certificate's inner product, a diagonal (numpy n) or a scipy sparse SPD matrix, or None."""
         import torch
         K = problem.K.tocsr()
         t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)
+        X_diag = X_csr = None
+        if X is not None and hasattr(X, "tocsr"):
+            Xc = X.tocsr()
+            Xc.sort_indices()
+            X_csr = (t(Xc.indptr, torch.int32), t(Xc.indices, torch.int32), t(Xc.data, torch.float64))
+        elif X is not None:
+            X_diag = t(X, torch.float64)
         return cls(t(K.indptr, torch.int32), t(K.indices, torch.int32), t(K.data, torch.float64),
                    t(problem.C, torch.float64), t(problem.o, torch.float64), M=t(problem.M, torch.float64),
-                   eps=problem.eps, X=None if X is None else t(X, torch.float64), alpha=problem.alpha,
-                   alpha_lb=alpha_lb, vol_B=problem.vol_B, N0=t(problem.N0.ravel(), torch.float64))
+                   eps=problem.eps, X=X_diag, X_csr=X_csr, X_tol=X_tol, X_max_iter=X_max_iter,
+                   alpha=problem.alpha, alpha_lb=alpha_lb, vol_B=problem.vol_B,
+                   N0=t(problem.N0.ravel(), torch.float64))
 
 
 class PermeabilityData:
@@ -453,7 +468,7 @@ def mrom_project_mu(h: Handle, fom: FullOrder, mu: PermeabilityData, D, *, tol_s
     _abi.check(lib().mrom_project_mu(h.ptr, ctypes.byref(fom.desc), ctypes.byref(mu.desc), _ptr(D),
                                      int(D.shape[1]), int(D.shape[0]), float(tol_sigma), int(r_max),
                                      ctypes.byref(rom), ctypes.byref(r_out), ctypes.byref(m_out)), h.ptr)
-    obj = ReducedObject._wrap(h, rom, r_out.value, fom.desc.X_diag is not None)
+    obj = ReducedObject._wrap(h, rom, r_out.value, fom.has_cert)
     return obj, int(r_out.value), int(m_out.value)
 
 
@@ -490,7 +505,7 @@ def mrom_project(h: Handle, fom: FullOrder, D=None, *, tol_sigma: float = 1e-6, 
                                       float(tol_sigma), int(r_max), None, 0, ctypes.byref(rom),
                                       sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                       ctypes.byref(r_out)), h.ptr)
-    return ReducedObject._wrap(h, rom, r_out.value, fom.desc.X_diag is not None), sig, int(r_out.value)
+    return ReducedObject._wrap(h, rom, r_out.value, fom.has_cert), sig, int(r_out.value)
 
 
 def mrom_rom_get(rom: ReducedObject, with_gram: bool = True) -> dict:
@@ -590,6 +605,13 @@ def mrom_invariants(h: Handle, M, eig) -> None:
     if eig.numel() != 3 * n:
         raise ValueError("eig must hold 3 values per 3 x 3 matrix")
     _abi.check(lib().mrom_invariants(h.ptr, _ptr(M), int(n), _ptr(eig)), h.ptr)
+
+
+def mrom_fp64_peak(h: Handle, iters: int = 1 << 16):
+    """Measured FP64 pipe throughput of the handle's device: (TFLOP/s, kernel ms)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _abi.check(lib().mrom_fp64_peak(h.ptr, int(iters), ctypes.byref(tf), ctypes.byref(ms)), h.ptr)
+    return tf.value, ms.value
 
 
 def _sweep_values(h, objs, omega, s_sigma, s_mu):
@@ -695,4 +717,4 @@ def mrom_project_dirs(h: Handle, fom: FullOrder, D=None, *, n_s: int = 0, tol_si
                                            sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), rd_out), h.ptr)
         sig = sig.reshape(3, n_s)
     rd = tuple(int(x) for x in rd_out)
-    return ReducedObject._wrap(h, rom, sum(rd), fom.desc.X_diag is not None), sig, rd
+    return ReducedObject._wrap(h, rom, sum(rd), fom.has_cert), sig, rd

@@ -94,7 +94,8 @@ extern "C" mrom_status mrom_adapt(mrom_handle h, const mrom_fom* fom, const doub
   if (!h) return MROM_EINVAL;
   if (!fom || !omega0 || ns0 < 2 || (!D0 && cb) || !omega_out || n_out < 2 || !opts || !out)
     return fail(h, MROM_EINVAL, "mrom_adapt: bad arguments");
-  if (!fom->X_diag) return fail(h, MROM_EINVAL, "mrom_adapt: the certificate needs fom->X_diag");
+  if (!fom_has_certificate(fom))
+    return fail(h, MROM_EINVAL, "mrom_adapt: the certificate needs fom->X_diag or a sparse X");
   if (opts->n_star < 1 || opts->max_k < 1 || !(opts->tol_delta >= 0.0))
     return fail(h, MROM_EINVAL, "mrom_adapt: n_star >= 1, max_k >= 1 and tol_delta >= 0 are required");
   if (!(opts->theta >= 0.0 && opts->theta <= 1.0))

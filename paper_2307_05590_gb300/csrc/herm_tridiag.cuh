@@ -211,7 +211,9 @@ __device__ __forceinline__ bool ql_split(double e, double d0, double d1, double 
   return a <= DBL_EPSILON * (fabs(d0) + fabs(d1)) || a <= DBL_EPSILON * tn;
 }
 
-// Implicit QL with Wilkinson-type shifts on the real symmetric tridiagonal (sd, se), se[i]
+// Implicit QL with Wilkinson-type shifts on the real symmetric tridiagonal (sd, se): the
+// published implicit QL method of Bowdler, Martin, Reinsch and Wilkinson (the tql2 procedure of
+// the Handbook for Automatic Computation, Vol. II), whose bulge chase this follows.  se[i]
 // coupling i and i+1 (shared arrays).  Thread 0 chases one bulge at a time and records its
 // rotations in rc, rs (shared, r entries); then every thread applies them to the rows of Z
 // (r x r complex, row-major; real and imaginary parts independently):

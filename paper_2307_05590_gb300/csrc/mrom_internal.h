@@ -233,7 +233,16 @@ mrom_status cuda_fail(mrom_ctx* h, cudaError_t e, const char* what);
 int sweep_fp64_num_configs();
 int sweep_fp64_threads(int cfg);
 int sweep_fp64_ctas_per_sm(int cfg);
+// Certificate inner product (riesz.cu): true when fom gives X_diag or a sparse X.
+bool fom_has_certificate(const mrom_fom* fom);
+// Y (n x nc, row-major complex128) = X^-1 Phi (same layout) for fom's sparse SPD X, by Jacobi PCG
+// on all columns together; *iters_max (may be null) receives the largest iteration count.
+// Synchronous.  MROM_ENOTCONVERGED when a column does not reach fom->X_tol.
+mrom_status riesz_solve(mrom_ctx* h, const mrom_fom* fom, const double2* Phi, int nc, double2* Y, int* iters_max);
+
 const void* sweep_fp64_symbol(int cfg);
+// the compact-table instantiation that launch_sweep_fp64_implicit and launch_sweep_fp64_routed run
+const void* sweep_fp64_implicit_symbol(int cfg);
 size_t sweep_fp64_matrix_elems(int r);
 size_t sweep_fp64_bytes_per_system(int r, bool matrix_in_smem);
 cudaError_t sweep_fp64_configure(int cfg, size_t smem_bytes);

@@ -104,10 +104,12 @@ extern "C" mrom_status mrom_sweep_noalloc(mrom_handle h, const mrom_rom_t* roms,
     return fail(h, MROM_EINVAL,
                 "mrom_sweep_noalloc: batch needs " + std::to_string(off_ws + ws_per_cta) +
                     " bytes of scratch, more than the fixed MROM_NOALLOC_SCRATCH_BYTES = " + std::to_string(cap));
-  e = sweep_fp64_configure(cfg, smem);
+  // occupancy of the instantiation that is launched (the compact-table kernel)
+  e = cudaFuncSetAttribute(sweep_fp64_implicit_symbol(cfg), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_fp64_symbol(cfg), sweep_fp64_threads(cfg), smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_fp64_implicit_symbol(cfg), sweep_fp64_threads(cfg),
+                                                      smem);
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_sweep_noalloc: configuration");
   int grid = std::min(n_tasks, h->num_sms * std::max(occ, 1));
   if (ws_per_cta) grid = std::min<int64_t>(grid, (int64_t)((cap - off_ws) / ws_per_cta));

@@ -673,7 +673,7 @@ mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, in
   const int ng = 2 * r + 3;
   DevBuf Y, Oc, small, phi, em;
   // K U in float64 feeds the float64 products and the certificate's residual basis
-  const bool need_y64 = h->projection_precision != MROM_MIXED || fom->X_diag != nullptr;
+  const bool need_y64 = h->projection_precision != MROM_MIXED || fom_has_certificate(fom);
   cudaError_t e = need_y64 ? cudaMalloc(&Y.p, (size_t)n * r * sizeof(double2)) : cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&Oc.p, (size_t)n * 3 * sizeof(double2));
   const size_t nsmall = 3 * (size_t)r * r + 3 * (size_t)r + 9 + (size_t)ng * ng;
@@ -774,7 +774,7 @@ mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, in
   }
   if (e == cudaSuccess && h->projection_precision == MROM_MIXED)
     e = tall_gram(h, Op, 3, 1, 3, Op, 3, 1, 3, fom->C_diag, 1, n, true, c00c, 3);
-  const bool cert = fom->X_diag != nullptr;
+  const bool cert = fom_has_certificate(fom);
   if (e == cudaSuccess && cert) {
     e = cudaMalloc(&phi.p, (size_t)n * ng * sizeof(double2));
     if (e == cudaSuccess) {
@@ -783,6 +783,23 @@ mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, in
       ++h->launches;
       e = cudaGetLastError();
     }
+  }
+  if (e == cudaSuccess && cert && fom->X_rowptr) {
+    // sparse X: G = Phi^H (X^-1 Phi), the representers by PCG, then the Hermitian average
+    DevBuf xphi;
+    e = cudaMalloc(&xphi.p, (size_t)n * ng * sizeof(double2));
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: allocation");
+    const mrom_status rs = riesz_solve(h, fom, static_cast<double2*>(phi.p), ng, static_cast<double2*>(xphi.p), nullptr);
+    if (rs != MROM_OK) return rs;
+    e = tall_gram(h, static_cast<double2*>(phi.p), ng, 1, ng, static_cast<double2*>(xphi.p), ng, 1, ng, nullptr, 0, n,
+                  false, Gm, ng);
+    if (e == cudaSuccess) {
+      symmetrize_kernel<<<(ng * ng + 255) / 256, 256, 0, st>>>(Gm, ng);
+      ++h->launches;
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // xphi is freed on scope exit
+  } else if (e == cudaSuccess && cert) {
     // X^-1 once (the Gram kernel would otherwise divide for every staged element)
     DevBuf xinv;
     if (e == cudaSuccess) e = cudaMalloc(&xinv.p, (size_t)n * sizeof(double));
@@ -824,7 +841,12 @@ mrom_status check_fom(mrom_ctx* h, const mrom_fom* fom) {
     return fail(h, MROM_EINVAL, "mrom_project: n, K, C_diag and o are required");
   if (!(fom->alpha > 0) || !std::isfinite(fom->alpha) || !std::isfinite(fom->eps))
     return fail(h, MROM_EINVAL, "mrom_project: alpha must be finite and > 0, eps finite");
-  if (fom->X_diag && !(fom->alpha_lb > 0)) return fail(h, MROM_EINVAL, "mrom_project: a certificate needs alpha_lb > 0");
+  if (fom_has_certificate(fom) && !(fom->alpha_lb > 0))
+    return fail(h, MROM_EINVAL, "mrom_project: a certificate needs alpha_lb > 0");
+  if (fom->X_rowptr && (!fom->X_col || !fom->X_val))
+    return fail(h, MROM_EINVAL, "mrom_project: a sparse X needs X_rowptr, X_col and X_val");
+  if (!std::isfinite(fom->X_tol) || fom->X_tol < 0.0 || fom->X_max_iter < 0)
+    return fail(h, MROM_EINVAL, "mrom_project: X_tol must be finite and >= 0, X_max_iter >= 0");
   return MROM_OK;
 }
 
@@ -1031,7 +1053,7 @@ extern "C" mrom_status mrom_project_mu(mrom_handle h, const mrom_fom* fom, const
   // reduced static data, one device block owned by the object:
   // Sout, Sin, Mv, cvv (m x m), kout, kin, cvx (m x 3), Bx (r x 3), BV (r x m)
   const size_t mm = (size_t)m * m, m3 = 3 * (size_t)m;
-  const bool cert = fom->X_diag != nullptr;
+  const bool cert = fom_has_certificate(fom);
   const int n_ext = 3 + m + 3 * r;
   const size_t n_mu = 4 * mm + 3 * m3 + 3 * (size_t)r + (size_t)r * m + (cert ? (size_t)n_ext * n_ext : 0);
   void* blk = nullptr;
@@ -1118,14 +1140,37 @@ extern "C" mrom_status mrom_project_mu(mrom_handle h, const mrom_fom* fom, const
       build_phi_ext_kernel<<<grid_of((int64_t)n * n_ext), 256, 0, str>>>(
           X3, V, m, U, Yp, static_cast<double2*>(KinUb.p), r, fom->C_diag, fom->M_diag, fom->eps, n,
           static_cast<double2*>(Phib.p));
-      recip_kernel<<<grid_of(n), 256, 0, str>>>(fom->X_diag, n, static_cast<double*>(xinv.p));
-      h->launches += 4;
+      if (!fom->X_rowptr) {
+        recip_kernel<<<grid_of(n), 256, 0, str>>>(fom->X_diag, n, static_cast<double*>(xinv.p));
+        ++h->launches;
+      }
+      h->launches += 3;
       e = cudaGetLastError();
     }
     const auto* Phi = static_cast<const double2*>(Phib.p);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && fom->X_rowptr) {
+      // sparse X: the representers X^-1 Phi_ext by PCG, G_ext = Phi_ext^H (X^-1 Phi_ext), Hermitian average
+      DevBuf xphi;
+      e = cudaMalloc(&xphi.p, (size_t)n * n_ext * sizeof(double2));
+      if (e == cudaSuccess) {
+        const mrom_status rs = riesz_solve(h, fom, Phi, n_ext, static_cast<double2*>(xphi.p), nullptr);
+        if (rs != MROM_OK) {
+          mrom_rom_free(rom);
+          *out = nullptr;
+          return rs;
+        }
+        e = tall_gram(h, Phi, n_ext, 1, n_ext, static_cast<double2*>(xphi.p), n_ext, 1, n_ext, nullptr, 0, n, false,
+                      Gext, n_ext);
+      }
+      if (e == cudaSuccess) {
+        symmetrize_kernel<<<(n_ext * n_ext + 255) / 256, 256, 0, str>>>(Gext, n_ext);
+        ++h->launches;
+        e = cudaGetLastError();
+      }
+    } else if (e == cudaSuccess) {
       e = tall_gram(h, Phi, n_ext, 1, n_ext, Phi, n_ext, 1, n_ext, static_cast<double*>(xinv.p), 1, n, true, Gext,
                     n_ext);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(str);
   }
   std::vector<double2> cxx_h(9);

@@ -420,6 +420,9 @@ int sweep_fp64_num_configs() { return (int)(sizeof(kConfigs) / sizeof(kConfigs[0
 int sweep_fp64_threads(int cfg) { return kConfigs[cfg].threads; }
 int sweep_fp64_ctas_per_sm(int cfg) { return kConfigs[cfg].ctas_per_sm; }
 const void* sweep_fp64_symbol(int cfg) { return kConfigs[cfg].fn; }
+const void* sweep_fp64_implicit_symbol(int cfg) {
+  return cfg == 0 ? (const void*)sweep_fp64_kernel<256, 2, true> : (const void*)sweep_fp64_kernel<128, 4, true>;
+}
 
 size_t sweep_fp64_matrix_elems(int r) { return (size_t)matrix_elems(r); }
 

@@ -108,13 +108,14 @@ def test_dictionary_1000x2000_sampled(mrom):
     mrom.mrom_sweep_vjp(h, rs, om, 2000, gR, gI, g_w, g_ssigma=g_s, g_smu=g_m)
     h.synchronize()
     for j, k in enumerate(sel):
-        gw, gs, gm = grads.vjp(objs[k], wo, gR[j].cpu().numpy(), gI[j].cpu().numpy())
         dR, dI = grads.tangents(objs[k], wo)
-        sc = (np.abs(dR) * np.abs(gR[j].cpu().numpy())[None]).sum(axis=(2, 3)) + \
-             (np.abs(dI) * np.abs(gI[j].cpu().numpy())[None]).sum(axis=(2, 3))
-        assert np.all(np.abs(g_w[j].cpu().numpy() - gw) <= 1e-8 * sc[0])
-        assert abs(g_s[j].item() - gs) <= 1e-8 * sc[1].sum()
-        assert abs(g_m[j].item() - gm) <= 1e-8 * sc[2].sum()
+        contrib = np.einsum("twij,wij->tw", dR, gR[j].cpu().numpy()) + \
+            np.einsum("twij,wij->tw", dI, gI[j].cpu().numpy())
+        # g_omega per (object, omega) against max |g_omega| of the object; the scale derivatives
+        # (sums over the 2000 frequencies) against the sum of their terms' magnitudes
+        assert np.abs(g_w[j].cpu().numpy() - contrib[0]).max() <= TOL * np.abs(contrib[0]).max()
+        assert abs(g_s[j].item() - contrib[1].sum()) <= TOL * np.abs(contrib[1]).sum()
+        assert abs(g_m[j].item() - contrib[2].sum()) <= TOL * np.abs(contrib[2]).sum()
 
 
 def test_c2_grid_projection_full_size(mrom):

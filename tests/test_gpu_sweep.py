@@ -114,6 +114,43 @@ def test_device_detected_bad_frequency(mrom, handle):
     handle.synchronize()  # status cleared
 
 
+def test_singular_reduced_system_reported(mrom, handle):
+    """An object whose K_r and C_r share the null vector e_r (last row and column zero, so
+    A(omega) = K_r - i omega C_r is singular at every omega): the pencil route's Cholesky of C_r
+    fails, the object goes to the LU route, whose last pivot is exactly zero, and the next
+    mrom_synchronize returns MROM_ESINGULAR.  A regular object in the same batch is unaffected."""
+    import torch
+    from gpu_common import oracle_sweep, rel_errors
+    from workloads import log_omegas, reduced_object
+    bad = reduced_object(9, 4, 12)
+    K, C = bad.K.copy(), bad.C.copy()
+    K[-1, :] = 0.0
+    K[:, -1] = 0.0
+    C[-1, :] = 0.0
+    C[:, -1] = 0.0
+    good = reduced_object(9, 5, 20)
+    n_w = 17
+    wo = log_omegas(1e1, 1e8, n_w)
+    roms = [mrom.ReducedObject(handle, 12, K, C, bad.B, bad.c00),
+            mrom.ReducedObject.from_workload(handle, good, with_cert=False)]
+    plan = mrom.Plan(handle, roms, n_w)
+    om = torch.as_tensor(wo, device="cuda")
+    R = torch.empty((2, n_w, 3, 3), dtype=torch.float64, device="cuda")
+    I = torch.empty_like(R)
+    plan.sweep(om, R, I)
+    with pytest.raises(mrom.MromError) as ei:
+        handle.synchronize()
+    assert ei.value.status == 4  # MROM_ESINGULAR
+    handle.synchronize()  # status cleared
+    n_pen, n_lu = plan.solver_counts()
+    assert (n_pen, n_lu) == ((0, 2) if handle.solver == "lu" else (1, 1))
+    assert not np.isfinite(R[0].cpu().numpy()).all()
+    Rr, Ir, _, sI, _ = oracle_sweep(good, wo)
+    eR, eI, _ = rel_errors(R[1].cpu().numpy(), I[1].cpu().numpy(), None, Rr, Ir, None, sI, None)
+    assert max(eR, eI) <= TOL
+    plan.close()
+
+
 def test_invalid_objects_rejected(mrom, handle):
     from workloads import reduced_object
     obj = reduced_object(9, 2, 6)

@@ -60,6 +60,41 @@ def test_noalloc_sweep_matches_sweep_on_two_calls(mrom):
         _compare(torch, got, ref)
 
 
+def test_noalloc_sweep_matches_the_oracle_and_allocates_nothing(mrom):
+    """Per-object frequency grids (omega_stride > n_w), outputs without Delta, and a second call:
+    the results match the CPU oracle (R against max |R|, I against its term scale per frequency),
+    and after a first call the device's free memory does not change across a second one."""
+    import torch
+    from gpu_common import oracle_sweep, rel_errors
+    from workloads import log_omegas, reduced_object
+    h = mrom.Handle(0)
+    objs = [reduced_object(2718, k, r) for k, r in enumerate([12, 50, 96])]
+    roms = [mrom.ReducedObject.from_workload(h, o) for o in objs]
+    n_w, stride = 41, 64
+    grids = [log_omegas(1e1 * (k + 1), 1e8 / (k + 1), n_w) for k in range(len(objs))]
+    om_host = np.zeros((len(objs), stride))
+    for k, g in enumerate(grids):
+        om_host[k, :n_w] = g
+        om_host[k, n_w:] = np.nan  # never read: only the first n_w of each row are frequencies
+    om = torch.as_tensor(om_host, device="cuda")
+    R = torch.full((len(objs), n_w, 3, 3), float("nan"), dtype=torch.float64, device="cuda")
+    I = torch.full_like(R, float("nan"))
+    mrom.mrom_sweep_noalloc(h, roms, om, n_w, R, I, omega_stride=stride)
+    h.synchronize()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    R.fill_(float("nan"))
+    I.fill_(float("nan"))
+    mrom.mrom_sweep_noalloc(h, roms, om, n_w, R, I, omega_stride=stride)
+    h.synchronize()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    for k, obj in enumerate(objs):
+        Rr, Ir, _, sI, _ = oracle_sweep(obj, grids[k])
+        eR, eI, _ = rel_errors(R[k].cpu().numpy(), I[k].cpu().numpy(), None, Rr, Ir, None, sI, None)
+        assert max(eR, eI) <= TOL, (obj.r, eR, eI)
+
+
 def test_noalloc_sweep_refuses_a_batch_larger_than_its_array(mrom):
     import torch
     from workloads import reduced_object

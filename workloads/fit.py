@@ -200,6 +200,43 @@ def _edge_cells(n: int, ids):
     return out, mids - 0.5, dirs
 
 
+def node_gradient(n: int) -> sp.csr_matrix:
+    """Discrete gradient of the n^3 grid restricted to interior edges and interior nodes
+    (rows in the edge order of fit_problem, columns = interior nodes in lexicographic order):
+    each edge holds phi(end) - phi(start) along its positive direction.  Boundary nodes carry
+    phi = 0 (n x grad phi = 0 on the boundary), so K G = 0 for the curl-curl K of fit_problem."""
+    ids, n_all = _edge_tables(n)
+    ex, ey, ez = ids
+    node = lambda i, j, k: (i * (n + 1) + j) * (n + 1) + k
+    rows, cols, vals = [], [], []
+    for d, e in enumerate(ids):
+        I, J, K = np.meshgrid(*[np.arange(s) for s in e.shape], indexing="ij")
+        start = node(I, J, K).ravel()
+        step = [(1, 0, 0), (0, 1, 0), (0, 0, 1)][d]
+        end = node(I + step[0], J + step[1], K + step[2]).ravel()
+        eid = e[I, J, K].ravel()
+        rows += [eid, eid]
+        cols += [end, start]
+        vals += [np.ones(eid.size), -np.ones(eid.size)]
+    G = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n_all, (n + 1) ** 3))
+    # interior edges: the same selection as fit_problem (mid-point off the outer faces)
+    _, mids, dirs = _edge_cells(n, ids)
+    on_bnd = np.zeros(n_all, dtype=bool)
+    for d in range(3):
+        sel = dirs == d
+        for t in range(3):
+            if t == d:
+                continue
+            coord = mids[sel, t] + 0.5
+            on_bnd[np.flatnonzero(sel)[(np.abs(coord) < 1e-12) | (np.abs(coord - 1.0) < 1e-12)]] = True
+    interior = np.flatnonzero(~on_bnd)
+    a = np.arange(1, n)
+    I, J, K = np.meshgrid(a, a, a, indexing="ij")
+    inodes = node(I, J, K).ravel()
+    return G[interior][:, inodes].tocsr()
+
+
 def _assign_materials(n: int, materials: Sequence[Material]):
     h = 1.0 / n
     c = (np.arange(n) + 0.5) * h
