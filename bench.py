@@ -428,17 +428,24 @@ def measure_fom_solve(m, h, n_grid: int = 128, n_w: int = 2):
 
 
 def measure_adaptive_fom(m, h, n_grid: int = 128, ns0: int = 9, n_star: int = 2, max_k: int = 28,
-                         n_out: int = 4096):
+                         n_out: int = 4096, cert_x: str = "sparse"):
     """Algorithm 1 end to end on the device: mrom_adapt without a callback, so every full-order
     snapshot of Eq. (9) is solved by mrom_fom_solve (COCG, Jacobi-scaled residual 1e-12), on the
-    n_grid^3 two-material grid (theta^(0) without the static correction, whose sparse solve at
-    this size is not built), 4096 outputs in [1e1, 1e8], shared basis, r <= 64.  Also times one
-    batched solve of the 3 x 9 initial right-hand sides."""
+    n_grid^3 two-material grid with the static correction theta~^(0) of the mu_r = 64 cube solved
+    on the device (mrom_static_solve), 4096 outputs in [1e1, 1e8], shared basis, r <= 64, and the
+    certificate in the inner product X = K + eps M + omega_min C (sparse, PCG on the device;
+    cert_x "diag": X = eps M + omega_min C).  Also times one batched solve of the 3 x 9 initial
+    right-hand sides."""
     import torch
     from workloads import TWO_MATERIAL_C5, fit_problem, log_omegas
-    p = fit_problem(n_grid, TWO_MATERIAL_C5, static=False)
+    import scipy.sparse as sp
+    t0 = time.perf_counter()
+    solver = m.static_solver_for(h, n_grid)
+    p = fit_problem(n_grid, TWO_MATERIAL_C5, static_solver=solver)
+    t_static = time.perf_counter() - t0
     wo = log_omegas(1e1, 1e8, n_out)
-    X = p.eps * p.M + wo[0] * p.C
+    Xd = p.eps * p.M + wo[0] * p.C
+    X = (p.K + sp.diags(Xd)).tocsr() if cert_x == "sparse" else Xd
     fom = m.FullOrder.from_fit(p, X=X)
     w0 = log_omegas(1e1, 1e8, ns0)
     torch.cuda.synchronize()
@@ -455,14 +462,18 @@ def measure_adaptive_fom(m, h, n_grid: int = 128, ns0: int = 9, n_star: int = 2,
     total = time.perf_counter() - t0
     r = rom.r
     rom.close()
+    lam = hist[~np.isnan(hist)]
+    b_alpha = p.alpha ** 3 * p.vol_B
     return {"workload": f"mrom_adapt with device snapshots: {n_grid}^3 two-material FIT grid (N = {p.N}), "
-                        f"{ns0} -> {len(snaps)} snapshots (+{n_star} per iteration), {n_out} output frequencies, "
-                        f"shared basis, r_max 64; full-order solves by mrom_fom_solve",
+                        f"static theta~^(0) by mrom_static_solve, {ns0} -> {len(snaps)} snapshots (+{n_star} per "
+                        f"iteration), {n_out} output frequencies, shared basis, r_max 64, certificate inner product "
+                        f"{'K + eps M + omega_min C (sparse)' if cert_x == 'sparse' else 'eps M + omega_min C'}",
             "iterations": int(k), "final_r": int(r), "seconds_total": total,
             "seconds_per_iteration": total / max(1, k - 1),
-            "lambda_history": [float(x) for x in hist[~np.isnan(hist)]],
-            "lambda_over_B_last": float(hist[~np.isnan(hist)][-1]) / (p.alpha ** 3 * p.vol_B)
-            if np.any(~np.isnan(hist)) else None,
+            "lambda_over_B_history": [float(x) / b_alpha for x in lam],
+            "lambda_over_B_last": float(lam[-1]) / b_alpha if lam.size else None,
+            "reached_tol_delta": bool(lam.size and lam[-1] / b_alpha <= 1e-3),
+            "static_solve": {"seconds_with_assembly": t_static, "iterations": list(solver.iters)},
             "initial_solve": {"rhs": 3 * ns0, "seconds": t_solve, "iterations_max": int(its.max()),
                               "iterations_min": int(its.min()), "scaled_residual_max": float(res.max())}}
 
@@ -583,6 +594,9 @@ def main():
     ap.add_argument("--fom-freqs", type=int, default=2)
     ap.add_argument("--adaptive-fom", action="store_true",
                     help="with --adaptive-only: solve the full-order snapshots on the device (no callback)")
+    ap.add_argument("--cert-x", default="sparse", choices=["sparse", "diag"],
+                    help="--adaptive-fom: certificate inner product K + eps M + omega_min C, or its diagonal part")
+    ap.add_argument("--adaptive-max-k", type=int, default=28)
     ap.add_argument("--projection", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--podp-mu", action=argparse.BooleanOptionalAction, default=True,
                     help="PODP in mu_r section (projection with the static reduction, instances over s_mu)")
@@ -613,8 +627,12 @@ def main():
         stream = torch.cuda.Stream(dev)
         h = m.Handle(local_rank, stream.cuda_stream)
         if rank == 0:
-            fn = measure_adaptive_fom if args.adaptive_fom else measure_adaptive
-            print(json.dumps({"adaptive": fn(m, h, n_grid=args.adaptive_grid)}), flush=True)
+            if args.adaptive_fom:
+                rec = measure_adaptive_fom(m, h, n_grid=args.adaptive_grid, cert_x=args.cert_x,
+                                           max_k=args.adaptive_max_k)
+            else:
+                rec = measure_adaptive(m, h, n_grid=args.adaptive_grid)
+            print(json.dumps({"adaptive": rec}), flush=True)
         h.close()
         return
 

@@ -80,10 +80,11 @@ const char* mrom_last_error(mrom_handle h);
 /* Number of kernels this library launched on the handle so far. */
 int64_t mrom_launch_count(mrom_handle h);
 /* Precision of mrom_project / mrom_project_dirs on this handle.  MROM_FP64
- * (default): every product in float64.  MROM_MIXED: the SpMM K U and the Gram
- * products K_r, C_r, eps M_r and b in complex64 with complex64 accumulation
- * over each CTA's rows (partials summed in float64); the TSVD and the
- * certificate Gram stay float64. */
+ * (default): every product in float64.  MROM_MIXED: the SpMM K U in complex64,
+ * and the Gram products K_r, C_r, eps M_r and b on the tensor cores from complex64
+ * operands (each real part split into two TF32 parts, three products accumulated in
+ * FP32 over 128 rows at a time, the partials summed in float64); the TSVD and the
+ * certificate Gram stay float64.  Requires r <= 112. */
 mrom_status mrom_set_projection_precision(mrom_handle h, mrom_precision precision);
 
 /* ------------------------------------------------------- reduced objects */
@@ -302,6 +303,31 @@ mrom_status mrom_rom_mu_state(mrom_rom_t rom, double s_mu, void* B, double* c00,
 #define MROM_MAX_FOM_RHS 48
 mrom_status mrom_fom_solve(mrom_handle h, const mrom_fom* fom, const double* omega, int32_t n_w, double tol,
                            int32_t max_iter, void* Q, int64_t ldq, int32_t* iters, double* res);
+
+/* The static problem behind theta^(0) (Sect. 3, below Eq. (5): theta^(0) = e_i x xi + theta~^(0),
+ * with theta~^(0) solving a regularised curl-curl problem when mu_r != 1), on the device:
+ *   (K + M_s) o~_i = f_i,  i = 1..n_rhs,
+ * K from fom (CSR), M_s (n, > 0) the regularisation's diagonal over all of Omega, and right-hand
+ * sides with G^T f_i = 0 (e.g. f_i = -K x_i with K's columns of the eliminated boundary edges).
+ * K vanishes on discrete gradients (K G = 0) while M_s is tiny, so the gradient part of o~ is fixed
+ * only by G^T M_s o~ = 0, which a Krylov method on K + M_s resolves too slowly.  The call
+ * therefore runs Jacobi PCG on K + M_s (which converges in the K part) and then removes the
+ * gradient part exactly: o~ <- o~ - G y with (G^T M_s G) y = G^T M_s o~ (Jacobi PCG on the nodal
+ * operator, applied as G^T (M_s (G y))).  The result solves the system and meets the gradient
+ * condition, both to about tol; a sparse direct solve of K + M_s meets the latter only to
+ * about cond(K + M_s) x rounding.
+ *   G: n x n_nodes CSR (int32), the discrete gradient of the interior nodes (+-1 per edge);
+ *   GT: its transpose (n_nodes x n CSR);  f, o: device, n_rhs x n (row i at + i n), float64;
+ *   tol: relative preconditioned residual of both solves; iters (host, 2, or NULL): their
+ *   iteration counts.  1 <= n_rhs <= MROM_MAX_STATIC_RHS.  Temporaries: 4 n + 2 n_nodes
+ *   complex128 per right-hand side.  MROM_ENOTCONVERGED if a solve does not reach tol within
+ *   max_iter iterations.  Synchronous. */
+#define MROM_MAX_STATIC_RHS 8
+mrom_status mrom_static_solve(mrom_handle h, const mrom_fom* fom, const double* M_s, int64_t n_nodes,
+                              const int32_t* G_rowptr, const int32_t* G_col, const double* G_val,
+                              const int32_t* GT_rowptr, const int32_t* GT_col, const double* GT_val,
+                              const double* f, int32_t n_rhs, double tol, int32_t max_iter, double* o,
+                              int32_t* iters);
 
 /* Adaptive PODP, Algorithm 1 (Sect. 4.4), with one basis for the three directions.
  * Starting from ns0 >= 2 snapshots at omega0 (host, ns0 values) with their

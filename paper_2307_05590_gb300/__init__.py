@@ -23,7 +23,7 @@ __all__ = [
     "mrom_rom_from_reduced", "mrom_rom_free", "mrom_rom_rank", "mrom_sweep", "mrom_certificate",
     "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune", "mrom_sweep_noalloc",
     "FullOrder", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "MromSweep", "signature",
-    "mrom_sweep_mixed", "mrom_project_dirs", "mrom_invariants", "mrom_fp64_peak", "PermeabilityData", "mrom_project_mu",
+    "mrom_sweep_mixed", "mrom_project_dirs", "mrom_invariants", "mrom_fp64_peak", "mrom_static_solve", "static_solver_for", "PermeabilityData", "mrom_project_mu",
     "mrom_rom_mu_state", "mrom_fom_solve", "PackedDictionary",
 ]
 
@@ -605,6 +605,46 @@ def mrom_invariants(h: Handle, M, eig) -> None:
     if eig.numel() != 3 * n:
         raise ValueError("eig must hold 3 values per 3 x 3 matrix")
     _abi.check(lib().mrom_invariants(h.ptr, _ptr(M), int(n), _ptr(eig)), h.ptr)
+
+
+def mrom_static_solve(h: Handle, K, M_s, G, GT, f, *, tol: float = 1e-12, max_iter: int = 20000):
+    """The regularised static problem (K + M_s) o = f with G^T M_s o = 0.  Device tensors: K, G and
+    GT as (rowptr, col, val) CSR triples (int32, int32, float64), M_s (n,) and f (n_rhs, n) float64.
+    Returns (o (n_rhs, n) float64 device tensor, iteration counts of the two solves)."""
+    import torch
+    fom = _abi.mrom_fom()
+    fom.n = int(M_s.numel())
+    fom.K_rowptr, fom.K_col, fom.K_val = _ptr(K[0]), _ptr(K[1]), _ptr(K[2])
+    o = torch.empty_like(f)
+    it = (ctypes.c_int32 * 2)()
+    _abi.check(lib().mrom_static_solve(h.ptr, ctypes.byref(fom), _ptr(M_s), int(GT[0].numel() - 1),
+                                       _ptr(G[0]), _ptr(G[1]), _ptr(G[2]), _ptr(GT[0]), _ptr(GT[1]), _ptr(GT[2]),
+                                       _ptr(f), int(f.shape[0]), float(tol), int(max_iter), _ptr(o), it), h.ptr)
+    return o, (int(it[0]), int(it[1]))
+
+
+def static_solver_for(h: Handle, n_grid: int, *, tol: float = 1e-12, device="cuda"):
+    """A static_solver(K, M_s, rhs) for workloads.fit_problem on an n_grid^3 FIT grid that runs
+    mrom_static_solve (argument marshalling only: uploads K, M_s, the grid's discrete gradient and
+    rhs, returns o~ as numpy N x 3)."""
+    import torch
+    from workloads.fit import node_gradient
+
+    def csr(A):
+        A = A.tocsr()
+        A.sort_indices()
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)
+        return (t(A.indptr, torch.int32), t(A.indices, torch.int32), t(A.data, torch.float64))
+
+    def solve(K, M_s, rhs):
+        G = node_gradient(n_grid)
+        f = torch.as_tensor(np.ascontiguousarray(np.asarray(rhs).T), dtype=torch.float64, device=device)
+        o, its = mrom_static_solve(h, csr(K), torch.as_tensor(M_s, dtype=torch.float64, device=device), csr(G),
+                                   csr(G.T), f, tol=tol)
+        solve.iters = its
+        return o.cpu().numpy().T
+
+    return solve
 
 
 def mrom_fp64_peak(h: Handle, iters: int = 1 << 16):

@@ -1,0 +1,391 @@
+// Tall complex64 Gram products on the fifth-generation tensor cores (the mixed-precision
+// projection of Eqs. (17)-(19): K_r = U^H (K U), C_r = U^H C U, eps M_r, b = U^H C O, all of the
+// form G = A^H diag(w) B over the N rows of the full-order space).
+//
+// A complex product is four real ones: with A = Ar + i Ai and B' = diag(w) B = Br + i Bi,
+//   Re G = Ar^T Br + Ai^T Bi,   Im G = Ar^T Bi - Ai^T Br,
+// so one real GEMM of [Ar Ai]^T (2 ma x rows) by [Br Bi] (rows x 2 mb) gives all four blocks.
+// Each real operand is split into two TF32 parts, x = x_hi + x_lo (x_hi = tf32(x),
+// x_lo = tf32(x - x_hi)), and a_hi b_hi + a_hi b_lo + a_lo b_hi is accumulated in FP32 in tensor
+// memory (three tcgen05.mma of kind::tf32 per product tile): products accurate to FP32's level
+// instead of TF32's 1e-3.  The rows are the reduction dimension (K of the MMA).
+//
+// Per CTA (one per SM, a contiguous range of rows): chunks of 16 rows of A, B and w are copied
+// into shared memory by the bulk-copy engine (cp.async.bulk, completion on an mbarrier), two raw
+// stages in flight; all threads convert a raw chunk into the K-major operand tiles (real and
+// imaginary rows, hi and lo parts; two operand stages), one thread issues the MMAs and commits
+// them to the stage's mbarrier, which releases the operand stage for the chunk after next.  The
+// accumulator (Mpad x Npad FP32, Mpad = 128 per M tile) lives in tensor memory; after every 8
+// chunks (128 rows) the CTA waits for its MMAs, reads the accumulator with tcgen05.ld and adds it
+// into its float64 partial block (the tensor cores' FP32 accumulation then spans 128 rows only),
+// and a second kernel sums the blocks over the CTAs in float64 in a fixed order and maps them to
+// the complex G.
+//
+// Operand tiles in shared memory: no swizzle, K-major core matrices of 8 rows x 16 bytes (4
+// TF32 values); within a tile of K = 16 the four core matrices of an 8-row group are adjacent
+// (leading byte offset 128: next core matrix along K), and 8-row groups follow each other every
+// 512 bytes (stride byte offset).  The MMA's K step of 8 starts 256 bytes further.
+//
+// Every wait on an mbarrier is bounded: a wait that gives up sets kStatusTimeout, the CTA waits
+// (bounded) for its own copies and MMAs in flight, frees its tensor memory and returns.
+#include "mrom_internal.h"
+
+#include <algorithm>
+
+namespace mrom {
+namespace {
+
+constexpr int kTT = 256;           // threads per CTA (8 warps)
+constexpr int kTK = 16;            // rows (MMA K) per chunk
+constexpr int kMaxHalf = 112;      // ma, mb <= 112, so 2 ma, 2 mb <= 224
+constexpr long long kSpinLimit = 1LL << 26;  // try_wait polls before a wait gives up
+constexpr int kFlush = 8;          // chunks (128 rows) per FP32 accumulation segment
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+
+// Bounded wait for the phase with the given parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completing
+// `bytes` of the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// x = hi + lo with both parts TF32
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+
+// Shared-memory matrix descriptor of a K-major operand without swizzle (see the file comment).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  constexpr uint64_t kLbo = 128, kSbo = 512;
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((kLbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((kSbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of this architecture
+  return d;                // base offset 0, layout: no swizzle
+}
+
+// Instruction descriptor: kind::tf32, FP32 accumulator, A and B K-major, M x N.
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
+  return (1u << 4)                       // D format: F32
+         | (2u << 7)                     // A format: TF32
+         | (2u << 10)                    // B format: TF32
+         | ((uint32_t)(n >> 3) << 17)    // N / 8
+         | ((uint32_t)(m >> 4) << 24);   // M / 16
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 8 consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+struct TcGramArgs {
+  const float2* A;   // n x ma, row-major
+  const float2* B;   // n x mb, row-major (unused when same_ab)
+  const float* w;    // n weights of B's rows, or null
+  int64_t n;
+  int ma, mb, mpad, npad, same_ab;
+  int64_t rows_per_cta;
+  double* part;      // [gridDim.x][mpad][npad]
+  int* status;
+};
+
+// byte offset of element (row, k) in a K-major operand tile of K = 16 (see the file comment)
+__device__ __forceinline__ uint32_t op_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 512 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, int row, int k, float x) {
+  uint32_t h, l;
+  split_tf32(x, h, l);
+  const uint32_t o = op_off(row, k);
+  *reinterpret_cast<uint32_t*>(hi + o) = h;
+  *reinterpret_cast<uint32_t*>(lo + o) = l;
+}
+
+__global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ma = g.ma, mb = g.mb, mpad = g.mpad, npad = g.npad;
+  const int mtiles = mpad / 128;
+  // ---- shared memory carve-up
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(smem);       // 2 barriers
+  uint64_t* op_free = raw_full + 2;                              // 2 barriers
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 32);
+  const uint32_t a_raw_b = 128u * ma, b_raw_b = g.same_ab ? 0u : 128u * mb, w_raw_b = 64u;
+  const uint32_t raw_stage_b = (a_raw_b + b_raw_b + w_raw_b + 127u) & ~127u;
+  unsigned char* raw0 = smem + 128;
+  const uint32_t a_op_b = 64u * mpad, b_op_b = 64u * npad;
+  const uint32_t op_stage_b = 2u * a_op_b + 2u * b_op_b;
+  unsigned char* op0 = raw0 + 2 * raw_stage_b;
+  auto raw_a = [&](int s) { return reinterpret_cast<float2*>(raw0 + s * raw_stage_b); };
+  auto raw_b = [&](int s) { return reinterpret_cast<float2*>(raw0 + s * raw_stage_b + a_raw_b); };
+  auto raw_w = [&](int s) { return reinterpret_cast<float*>(raw0 + s * raw_stage_b + a_raw_b + b_raw_b); };
+  auto a_hi = [&](int s) { return op0 + s * op_stage_b; };
+  auto a_lo = [&](int s) { return op0 + s * op_stage_b + a_op_b; };
+  auto b_hi = [&](int s) { return op0 + s * op_stage_b + 2 * a_op_b; };
+  auto b_lo = [&](int s) { return op0 + s * op_stage_b + 2 * a_op_b + b_op_b; };
+
+  const int64_t row0 = (int64_t)blockIdx.x * g.rows_per_cta;
+  const int64_t row1 = min(g.n, row0 + g.rows_per_cta);
+  const int nchunks = row1 > row0 ? (int)((row1 - row0 + kTK - 1) / kTK) : 0;
+  auto chunk_rows = [&](int c) { return (int)min((int64_t)kTK, row1 - (row0 + (int64_t)c * kTK)); };
+  const int ncols = mtiles * npad <= 256 ? 256 : 512;
+
+  // ---- set-up: barriers, tensor memory, zeroed operand tiles (their padding rows stay zero)
+  if (tid == 0) {
+    for (int k = 0; k < 4; ++k) mbar_init(raw_full + k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  for (uint32_t o = tid * 16u; o < 2u * op_stage_b; o += kTT * 16u)
+    *reinterpret_cast<uint4*>(op0 + o) = make_uint4(0u, 0u, 0u, 0u);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = *tslot;
+
+  // thread 0's view of the asynchronous work in flight (for the error path)
+  int tma_issued = -1;     // highest chunk whose bulk copies were issued
+  int mma_last = -1;       // highest chunk whose MMAs were committed
+  auto issue_copy = [&](int c) {  // thread 0: bulk copies of a full chunk into raw stage c & 1
+    const int s = c & 1;
+    const int64_t r = row0 + (int64_t)c * kTK;
+    mbar_expect_tx(raw_full + s, a_raw_b + b_raw_b + (g.w ? w_raw_b : 0u));
+    bulk_g2s(raw_a(s), g.A + r * ma, a_raw_b, raw_full + s);
+    if (!g.same_ab) bulk_g2s(raw_b(s), g.B + r * mb, b_raw_b, raw_full + s);
+    if (g.w) bulk_g2s(raw_w(s), g.w + r, w_raw_b, raw_full + s);
+    tma_issued = c;
+  };
+  if (tid == 0) {
+    for (int c = 0; c < 2 && c < nchunks; ++c)
+      if (chunk_rows(c) == kTK) issue_copy(c);
+  }
+
+  // this CTA's partial block (float64) += (or, on the first segment, =) the accumulator; every
+  // warp reads its lane quarter (warp % 4) of each M tile, the two warp halves alternate 8-column
+  // blocks.  With no chunk the block is set to zero without touching tensor memory.
+  const int nchunks_cta = nchunks;
+  auto flush = [&](bool first) {
+    const int q = warp & 3, half = warp >> 2;
+    double* out = g.part + (size_t)blockIdx.x * mpad * npad;
+    for (int t = 0; t < mtiles; ++t) {
+      const int m = t * 128 + q * 32 + lane;
+      for (int cb = half * 8; cb < npad; cb += 16) {
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (nchunks_cta > 0) tmem_ld8(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * npad + cb), v);
+        double* o = out + (size_t)m * npad + cb;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = first ? (double)v[k] : o[k] + (double)v[k];
+      }
+    }
+  };
+
+  bool failed = false;
+  int c = 0;
+  for (; c < nchunks; ++c) {
+    const int s = c & 1;
+    const int rows = chunk_rows(c);
+    const bool full = rows == kTK;
+    bool ok = true;
+    if (full) ok = mbar_wait(raw_full + s, (uint32_t)((c >> 1) & 1));
+    if (c >= 2 && ok) ok = mbar_wait(op_free + s, (uint32_t)(((c - 2) >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    // ---- convert chunk c into the operand tiles of stage s
+    const int64_t r0 = row0 + (int64_t)c * kTK;
+    const int nb = g.same_ab ? ma : mb;
+    const int items = kTK * (ma + mb);
+    unsigned char *ah = a_hi(s), *al = a_lo(s), *bh = b_hi(s), *bl = b_lo(s);
+    for (int idx = tid; idx < items; idx += kTT) {
+      if (idx < kTK * ma) {
+        const int kk = idx / ma, m = idx - (idx / ma) * ma;
+        float2 a = make_float2(0.f, 0.f);
+        if (full) a = raw_a(s)[kk * ma + m];
+        else if (kk < rows) a = g.A[(r0 + kk) * ma + m];
+        put_split(ah, al, m, kk, a.x);
+        put_split(ah, al, ma + m, kk, a.y);
+      } else {
+        const int j = idx - kTK * ma;
+        const int kk = j / mb, n = j - (j / mb) * mb;
+        float2 b = make_float2(0.f, 0.f);
+        float wt = 1.f;
+        if (full) {
+          b = g.same_ab ? raw_a(s)[kk * nb + n] : raw_b(s)[kk * nb + n];
+          if (g.w) wt = raw_w(s)[kk];
+        } else if (kk < rows) {
+          b = g.same_ab ? g.A[(r0 + kk) * nb + n] : g.B[(r0 + kk) * nb + n];
+          if (g.w) wt = g.w[r0 + kk];
+        }
+        put_split(bh, bl, n, kk, wt * b.x);
+        put_split(bh, bl, mb + n, kk, wt * b.y);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();  // raw stage s consumed, operand stage s written
+    if (tid == 0) {
+      if (c + 2 < nchunks && chunk_rows(c + 2) == kTK) issue_copy(c + 2);
+      tc_fence_after();
+      const uint32_t idesc = instr_desc(128, npad);
+      const uint32_t pa[3] = {smem_u32(ah), smem_u32(ah), smem_u32(al)};
+      const uint32_t pb[3] = {smem_u32(bh), smem_u32(bl), smem_u32(bh)};
+      for (int ks = 0; ks < kTK / 8; ++ks)
+        for (int t = 0; t < mtiles; ++t)
+          for (int p = 0; p < 3; ++p) {
+            const uint64_t ad = smem_desc(pa[p] + (uint32_t)t * 8192u + (uint32_t)ks * 256u);
+            const uint64_t bd = smem_desc(pb[p] + (uint32_t)ks * 256u);
+            mma_tf32(taddr + (uint32_t)(t * npad), ad, bd, idesc, (c % kFlush > 0 || ks > 0 || p > 0) ? 1u : 0u);
+          }
+      mma_commit(op_free + s);
+      mma_last = c;
+    }
+    // ---- end of a segment: add the FP32 accumulator into this CTA's float64 partial block
+    if (c % kFlush == kFlush - 1 || c == nchunks - 1) {
+      const bool ok = mbar_wait(op_free + s, (uint32_t)((c >> 1) & 1));
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        ++c;  // chunk c was consumed
+        break;
+      }
+      tc_fence_after();
+      flush(c < kFlush);
+      tc_fence_before();
+      __syncthreads();
+    }
+  }
+  if (!failed && nchunks == 0) flush(true);  // zeros for an empty range
+  if (failed) {
+    if (tid == 0) {
+      atomicOr(g.status, kStatusTimeout);
+      // bounded waits for this CTA's own copies and MMAs still in flight
+      for (int k = c; k <= tma_issued; ++k) mbar_wait(raw_full + (k & 1), (uint32_t)((k >> 1) & 1));
+      if (mma_last >= 0) mbar_wait(op_free + (mma_last & 1), (uint32_t)((mma_last >> 1) & 1));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+  }
+}
+
+// G[i][j] = sum over the CTAs of (P[i][j] + P[ma+i][mb+j]) + i (P[i][mb+j] - P[ma+i][j]), float64,
+// CTAs in order
+__global__ void gram_tc_reduce_kernel(const double* __restrict__ part, int nblk, int ma, int mb, int mpad, int npad,
+                                      double2* __restrict__ G, int64_t ldg) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < ma * mb; idx += gridDim.x * blockDim.x) {
+    const int i = idx / mb, j = idx - (idx / mb) * mb;
+    double re = 0.0, im = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+      const double* P = part + (size_t)b * mpad * npad;
+      re += P[(size_t)i * npad + j] + P[(size_t)(ma + i) * npad + mb + j];
+      im += P[(size_t)i * npad + mb + j] - P[(size_t)(ma + i) * npad + j];
+    }
+    G[(size_t)i * ldg + j] = make_double2(re, im);
+  }
+}
+
+}  // namespace
+
+size_t tall_gram_tc_smem(int ma, int mb, bool same_ab) {
+  const int mpad = 128 * ((2 * ma + 127) / 128), npad = 16 * ((2 * mb + 15) / 16);
+  const size_t raw_stage = ((size_t)128 * ma + (same_ab ? 0 : (size_t)128 * mb) + 64 + 127) & ~(size_t)127;
+  return 128 + 2 * raw_stage + 2 * (2 * (size_t)64 * mpad + 2 * (size_t)64 * npad);
+}
+
+cudaError_t tall_gram_tc(mrom_ctx* h, const float2* A, int ma, const float2* B, int mb, const float* w, int64_t n,
+                         double2* G, int64_t ldg) {
+  if (ma < 1 || mb < 1 || ma > kMaxHalf || mb > kMaxHalf || n < 1) return cudaErrorInvalidValue;
+  const bool same = (A == B) && (ma == mb);
+  const int mpad = 128 * ((2 * ma + 127) / 128), npad = 16 * ((2 * mb + 15) / 16);
+  // at least 116 KB so that one CTA runs per SM (each holds up to 512 tensor-memory columns)
+  const size_t smem = std::max<size_t>(tall_gram_tc_smem(ma, mb, same), 116 * 1024);
+  if (smem > h->smem_optin) return cudaErrorInvalidValue;
+  const int64_t chunks = (n + kTK - 1) / kTK;
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(h->num_sms, chunks));
+  const int64_t per = (chunks + nblk - 1) / nblk * kTK;
+  DevBuf part;
+  cudaError_t e = cudaMalloc(&part.p, (size_t)nblk * mpad * npad * sizeof(double));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  TcGramArgs a{A, same ? nullptr : B, w, n, ma, mb, mpad, npad, same ? 1 : 0, per, static_cast<double*>(part.p),
+               h->d_status};
+  gram_tc_kernel<<<nblk, kTT, smem, h->stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gram_tc_reduce_kernel<<<std::max(1, std::min(1024, (ma * mb + 255) / 256)), 256, 0, h->stream>>>(
+      static_cast<double*>(part.p), nblk, ma, mb, mpad, npad, G, ldg);
+  e = cudaGetLastError();
+  h->launches += 2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // part is freed on return
+  return e;
+}
+
+}  // namespace mrom

@@ -233,6 +233,12 @@ mrom_status cuda_fail(mrom_ctx* h, cudaError_t e, const char* what);
 int sweep_fp64_num_configs();
 int sweep_fp64_threads(int cfg);
 int sweep_fp64_ctas_per_sm(int cfg);
+// G (ma x mb complex128, row-major, ldg) = A^H diag(w) B for complex64 row-major A (n x ma) and
+// B (n x mb), w (n, or null for 1), on the tensor cores (gram_tc.cu); ma, mb <= 112, A, B, w
+// 16-byte aligned.  Synchronous.
+cudaError_t tall_gram_tc(mrom_ctx* h, const float2* A, int ma, const float2* B, int mb, const float* w, int64_t n,
+                         double2* G, int64_t ldg);
+
 // Certificate inner product (riesz.cu): true when fom gives X_diag or a sparse X.
 bool fom_has_certificate(const mrom_fom* fom);
 // Y (n x nc, row-major complex128) = X^-1 Phi (same layout) for fom's sparse SPD X, by Jacobi PCG

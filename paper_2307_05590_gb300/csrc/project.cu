@@ -123,96 +123,6 @@ gram_partial_kernel(const double2* __restrict__ A, int64_t rsA, int64_t csA, int
     }
 }
 
-// Single-precision variant (complex64 operands, complex64 accumulation over the CTA's row
-// range); the partials are summed in float64 by gram_reduce_f32_kernel.
-__device__ __forceinline__ float2 f_conj_mac(float2 c, float2 a, float2 b) {  // c + conj(a) b
-  return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, c.y)));
-}
-
-__global__ void __launch_bounds__(256)
-gram_partial_f32_kernel(const float2* __restrict__ A, int64_t rsA, int ma, const float2* __restrict__ B, int64_t rsB,
-                        int mb, const float* __restrict__ w, int64_t n, int64_t rows_per_split,
-                        const int2* __restrict__ tiles, int Ta, int Tb, int herm, float2* __restrict__ part) {
-  __shared__ float2 As[kGR][kGT + 1];
-  __shared__ float2 Bs[kGR][kGT + 1];
-  const int tid = threadIdx.x;
-  const int hb = Tb >> 1;
-  const int2 tile = tiles[blockIdx.y];
-  bool active;
-  int ty, tx;
-  gram_thread_block(herm && tile.x == tile.y, Ta >> 1, hb, tid, active, ty, tx);
-  const int a_base = tile.x * Ta, b_base = tile.y * Tb;
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_split;
-  const int64_t r1 = min(n, r0 + rows_per_split);
-  float2 acc[2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
-  for (int64_t row0 = r0; row0 < r1; row0 += kGR) {
-    for (int idx = tid; idx < kGR * Ta; idx += 256) {
-      const int rr = idx / Ta, cc = idx - (idx / Ta) * Ta;
-      const int64_t nr = row0 + rr;
-      As[rr][cc] = (nr < r1 && a_base + cc < ma) ? A[nr * rsA + a_base + cc] : make_float2(0.f, 0.f);
-    }
-    for (int idx = tid; idx < kGR * Tb; idx += 256) {
-      const int rr = idx / Tb, cc = idx - (idx / Tb) * Tb;
-      const int64_t nr = row0 + rr;
-      float2 v = make_float2(0.f, 0.f);
-      if (nr < r1 && b_base + cc < mb) {
-        v = B[nr * rsB + b_base + cc];
-        if (w) {
-          v.x *= w[nr];
-          v.y *= w[nr];
-        }
-      }
-      Bs[rr][cc] = v;
-    }
-    __syncthreads();
-    if (active) {
-#pragma unroll 8
-      for (int rr = 0; rr < kGR; ++rr) {
-        const float2 a0 = As[rr][ty * 2], a1 = As[rr][ty * 2 + 1];
-        const float2 b0 = Bs[rr][tx * 2], b1 = Bs[rr][tx * 2 + 1];
-        acc[0][0] = f_conj_mac(acc[0][0], a0, b0);
-        acc[0][1] = f_conj_mac(acc[0][1], a0, b1);
-        acc[1][0] = f_conj_mac(acc[1][0], a1, b0);
-        acc[1][1] = f_conj_mac(acc[1][1], a1, b1);
-      }
-    }
-    __syncthreads();
-  }
-  if (!active) return;
-  float2* out = part + (size_t)blockIdx.x * ma * mb;
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int a = a_base + ty * 2 + i, b = b_base + tx * 2 + j;
-      if (a < ma && b < mb) out[(size_t)a * mb + b] = acc[i][j];
-    }
-}
-
-__global__ void gram_reduce_f32_kernel(const float2* __restrict__ part, int nsplit, int ma, int mb, int hermitian,
-                                       int T, double2* __restrict__ G, int64_t ldg) {
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)ma * mb;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int a = (int)(idx / mb), b = (int)(idx % mb);
-    int sa = a, sb = b;
-    bool conj = false;
-    if (hermitian && b < a) {
-      sa = b;
-      sb = a;
-      conj = true;
-    }
-    double2 s = make_double2(0.0, 0.0);
-    for (int k = 0; k < nsplit; ++k) {
-      const float2 v = part[(size_t)k * ma * mb + (size_t)sa * mb + sb];
-      s.x += v.x;
-      s.y += v.y;
-    }
-    if (conj) s.y = -s.y;
-    if (hermitian && a == b) s.y = 0.0;
-    G[(int64_t)a * ldg + b] = s;
-  }
-}
-
 __global__ void __launch_bounds__(256)
 spmm_csr_f32_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                     const float* __restrict__ val, int64_t n, const float2* __restrict__ U, int r,
@@ -558,38 +468,6 @@ cudaError_t tall_gram(mrom_ctx* h, const double2* A, int64_t rsA, int64_t csA, i
   return e;
 }
 
-// Single-precision tall Gram (row-major operands): G = A^H diag(w) B, float64 output.
-cudaError_t tall_gram_f32(mrom_ctx* h, const float2* A, int64_t rsA, int ma, const float2* B, int64_t rsB, int mb,
-                          const float* w, int64_t n, bool hermitian, double2* G, int64_t ldg) {
-  const int Ta = gram_tile(hermitian ? std::max(ma, mb) : ma), Tb = hermitian ? Ta : gram_tile(mb);
-  const int ta = (ma + Ta - 1) / Ta, tb = (mb + Tb - 1) / Tb;
-  std::vector<int2> tl;
-  for (int i = 0; i < ta; ++i)
-    for (int j = hermitian ? i : 0; j < tb; ++j) tl.push_back(make_int2(i, j));
-  const int ntiles = (int)tl.size();
-  int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>((8LL * h->num_sms + ntiles - 1) / ntiles, (n + 1023) / 1024));
-  nsplit = std::min<int64_t>(nsplit, 65535);
-  const int64_t per = ((n + nsplit - 1) / nsplit + kGR - 1) / kGR * kGR;
-  nsplit = std::max<int64_t>(1, (n + per - 1) / per);
-  DevBuf part, tiles;
-  cudaError_t e = cudaMalloc(&part.p, (size_t)nsplit * ma * mb * sizeof(float2));
-  if (e == cudaSuccess) e = cudaMalloc(&tiles.p, tl.size() * sizeof(int2));
-  if (e == cudaSuccess) e = cudaMemcpyAsync(tiles.p, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
-  if (e != cudaSuccess) return e;
-  gram_partial_f32_kernel<<<dim3((unsigned)nsplit, (unsigned)ntiles), 256, 0, h->stream>>>(
-      A, rsA, ma, B, rsB, mb, w, n, per, static_cast<int2*>(tiles.p), Ta, Tb, hermitian ? 1 : 0,
-      static_cast<float2*>(part.p));
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int rb = (int)std::min<int64_t>(4096, ((int64_t)ma * mb + 255) / 256);
-  gram_reduce_f32_kernel<<<std::max(rb, 1), 256, 0, h->stream>>>(static_cast<float2*>(part.p), (int)nsplit, ma, mb,
-                                                                  hermitian ? 1 : 0, Ta, G, ldg);
-  e = cudaGetLastError();
-  h->launches += 2;
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  return e;
-}
-
 }  // namespace mrom
 
 using namespace mrom;
@@ -723,16 +601,16 @@ mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, in
     h->launches += has_me ? 6 : 5;
     e = cudaGetLastError();
     const auto* u32 = static_cast<const float2*>(U32.p);
-    if (e == cudaSuccess) e = tall_gram_f32(h, u32, r, r, static_cast<float2*>(Y32.p), r, r, nullptr, n, true, Kr, r);
+    // the Gram products on the tensor cores (tcgen05, 3 x TF32 split, FP32 accumulation per CTA)
+    if (e == cudaSuccess) e = tall_gram_tc(h, u32, r, static_cast<float2*>(Y32.p), r, nullptr, n, Kr, r);
     if (e == cudaSuccess) {
       symmetrize_kernel<<<(r * r + 255) / 256, 256, 0, st>>>(Kr, r);
       ++h->launches;
     }
-    if (e == cudaSuccess) e = tall_gram_f32(h, u32, r, r, u32, r, r, static_cast<float*>(c32.p), n, true, Cr, r);
-    if (e == cudaSuccess && has_me)
-      e = tall_gram_f32(h, u32, r, r, u32, r, r, static_cast<float*>(m32.p), n, true, Me, r);
+    if (e == cudaSuccess) e = tall_gram_tc(h, u32, r, u32, r, static_cast<float*>(c32.p), n, Cr, r);
+    if (e == cudaSuccess && has_me) e = tall_gram_tc(h, u32, r, u32, r, static_cast<float*>(m32.p), n, Me, r);
     if (e == cudaSuccess)
-      e = tall_gram_f32(h, u32, r, r, static_cast<float2*>(O32.p), 3, 3, static_cast<float*>(c32.p), n, false, Bm, 3);
+      e = tall_gram_tc(h, u32, r, static_cast<float2*>(O32.p), 3, static_cast<float*>(c32.p), n, Bm, 3);
   } else {
     // K_r = U^H (K U) is Hermitian (K is symmetric): upper tiles, mirrored, then symmetrised
     if (e == cudaSuccess) e = tall_gram(h, U, r, 1, r, Yp, r, 1, r, nullptr, 0, n, true, Kr, r);

@@ -208,42 +208,35 @@ riesz_reduce_kernel(const double* __restrict__ part, int nblk, int nc, int mode,
   }
 }
 
-}  // namespace
-
-bool fom_has_certificate(const mrom_fom* fom) { return fom->X_diag != nullptr || fom->X_rowptr != nullptr; }
-
-mrom_status riesz_solve(mrom_ctx* h, const mrom_fom* fom, const double2* Phi, int nc, double2* Y, int* iters_max) {
-  const int64_t n = fom->n;
+// Columns of the SPD operator apply(P) -> Q: PCG on every column of B (row-interleaved, nc columns
+// over n rows) with the Jacobi weights dinv; Y receives the solutions.  apply launches kernels that
+// write Q = A P and the column partials of p^H q into part[group][block][c] with the grid
+// (nblk, groups) of this driver, skipping columns whose state is inactive.
+template <class Apply>
+mrom_status pcg_columns(mrom_ctx* h, int64_t n, int nc, int nblk, const double* dinv, const double2* B, double2* Y,
+                        double tol, int max_iter, Apply apply, int* iters_max, const char* what) {
   cudaStream_t st = h->stream;
-  const double tol = fom->X_tol > 0.0 ? fom->X_tol : 1e-13;
-  const int max_iter = fom->X_max_iter > 0 ? fom->X_max_iter : 20000;
   const int ngroups = (nc + kRW - 1) / kRW;
-  // about 8 CTAs per SM over all groups, each over at least 64 rows
-  const int nblk = (int)std::max<int64_t>(
-      1, std::min<int64_t>(std::max<int64_t>(1, (int64_t)h->num_sms * 8 / ngroups), (n + 63) / 64));
   const size_t nv = (size_t)n * nc;
   DevBuf vec, aux;
   cudaError_t e = cudaMalloc(&vec.p, 3 * nv * sizeof(double2));
   const size_t b_part = (size_t)ngroups * nblk * kRW * sizeof(double);
-  if (e == cudaSuccess) e = cudaMalloc(&aux.p, b_part + (size_t)n * sizeof(double) + nc * sizeof(RieszState) + 256);
-  if (e != cudaSuccess) return cuda_fail(h, e, "certificate inner product: allocation");
+  if (e == cudaSuccess) e = cudaMalloc(&aux.p, b_part + nc * sizeof(RieszState) + 256);
+  if (e != cudaSuccess) return cuda_fail(h, e, what);
   auto* Rv = static_cast<double2*>(vec.p);
   double2* P = Rv + nv;
   double2* Q = P + nv;
   auto* part = static_cast<double*>(aux.p);
-  auto* dinv = reinterpret_cast<double*>(static_cast<char*>(aux.p) + b_part);
-  auto* sts = reinterpret_cast<RieszState*>(dinv + n);
+  auto* sts = reinterpret_cast<RieszState*>(static_cast<char*>(aux.p) + b_part);
   const dim3 grid((unsigned)nblk, (unsigned)ngroups);
-  const unsigned g1 = (unsigned)std::min<int64_t>(65535, (n + 255) / 256);
-  riesz_dinv_kernel<<<g1, 256, 0, st>>>(fom->X_rowptr, fom->X_col, fom->X_val, n, dinv);
-  riesz_init_kernel<<<grid, kRT, 0, st>>>(Phi, dinv, n, nc, Y, Rv, P, part);
+  riesz_init_kernel<<<grid, kRT, 0, st>>>(B, dinv, n, nc, Y, Rv, P, part);
   riesz_reduce_kernel<<<1, kRT, 0, st>>>(part, nblk, nc, 0, tol * tol, sts);
-  h->launches += 3;
+  h->launches += 2;
   e = cudaGetLastError();
   std::vector<RieszState> hs(nc);
   const int chunk = 25;
   auto iteration = [&]() {
-    riesz_spmv_kernel<<<grid, kRT, 0, st>>>(fom->X_rowptr, fom->X_col, fom->X_val, n, nc, sts, P, Q, part);
+    apply(sts, P, Q, part);
     riesz_reduce_kernel<<<1, kRT, 0, st>>>(part, nblk, nc, 1, tol * tol, sts);
     riesz_update_kernel<<<grid, kRT, 0, st>>>(n, nc, sts, dinv, Y, Rv, P, Q, part);
     riesz_reduce_kernel<<<1, kRT, 0, st>>>(part, nblk, nc, 2, tol * tol, sts);
@@ -269,12 +262,12 @@ mrom_status riesz_solve(mrom_ctx* h, const mrom_fom* fom, const double2* Phi, in
     if (chunk_exec && it + chunk <= max_iter) {
       e = cudaGraphLaunch(chunk_exec, st);
       it += chunk;
-      h->launches += 5 * chunk;
+      h->launches += (4 + Apply::kLaunches) * chunk;
     } else {
       const int k_end = std::min(max_iter, it + chunk);
       for (; it < k_end && e == cudaSuccess; ++it) {
         iteration();
-        h->launches += 5;
+        h->launches += 4 + Apply::kLaunches;
         e = cudaGetLastError();
       }
     }
@@ -285,7 +278,7 @@ mrom_status riesz_solve(mrom_ctx* h, const mrom_fom* fom, const double2* Phi, in
   }
   if (chunk_exec) cudaGraphExecDestroy(chunk_exec);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(h, e, "certificate inner product: PCG");
+  if (e != cudaSuccess) return cuda_fail(h, e, what);
   int imax = 0;
   bool ok = true;
   for (int c = 0; c < nc; ++c) {
@@ -295,9 +288,261 @@ mrom_status riesz_solve(mrom_ctx* h, const mrom_fom* fom, const double2* Phi, in
   if (iters_max) *iters_max = imax;
   if (!ok)
     return fail(h, MROM_ENOTCONVERGED,
-                "certificate inner product: PCG on X did not reach X_tol within X_max_iter iterations, or broke "
-                "down (X must be symmetric positive definite)");
+                std::string(what) + ": PCG did not reach the tolerance within the iteration limit, or broke down "
+                                    "(the matrix must be symmetric positive definite)");
   return MROM_OK;
 }
 
+// CTAs per column group: about 8 CTAs per SM over all groups, each over at least 64 rows
+int pcg_blocks(const mrom_ctx* h, int64_t n, int nc) {
+  const int ngroups = (nc + kRW - 1) / kRW;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(1, (int64_t)h->num_sms * 8 / ngroups),
+                                                     (n + 63) / 64));
+}
+
+// The CSR operator of pcg_columns
+struct CsrApply {
+  const int32_t *rowptr, *col;
+  const double* val;
+  int64_t n;
+  int nc, nblk;
+  cudaStream_t st;
+  static constexpr int kLaunches = 1;
+  void operator()(const RieszState* sts, const double2* P, double2* Q, double* part) const {
+    const dim3 grid((unsigned)nblk, (unsigned)((nc + kRW - 1) / kRW));
+    riesz_spmv_kernel<<<grid, kRT, 0, st>>>(rowptr, col, val, n, nc, sts, P, Q, part);
+  }
+};
+
+// ---- static problem: (K + M_s) o = f with the gradient part fixed by M_s-orthogonality
+
+// A = K + diag(M_s): K's values with M_s added on the diagonal entries
+__global__ void static_matrix_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                     const double* __restrict__ kval, const double* __restrict__ ms, int64_t n,
+                                     double* __restrict__ aval) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) aval[k] = kval[k] + (col[k] == i ? ms[i] : 0.0);
+}
+
+// V[i][c] = (f[c n + i], 0) for nc real columns
+__global__ void real_rows_kernel(const double* __restrict__ f, int64_t n, int nc, double2* __restrict__ V) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * nc;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / nc;
+    const int c = (int)(idx - i * nc);
+    V[idx] = make_double2(f[(int64_t)c * n + i], 0.0);
+  }
+}
+
+// out[i][c] = w_i sum_k A[i][k] V[k][c] (CSR rows, w = null for 1), every column (no partials)
+__global__ void __launch_bounds__(kRT)
+csr_rows_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, const double* __restrict__ val,
+                const double* __restrict__ w, int64_t nrows, int nc, const double2* __restrict__ V,
+                double2* __restrict__ out) {
+  const GroupMap m(nc);
+  if (!m.on) return;
+  for (int64_t i = (int64_t)blockIdx.x * kRR + m.lr; i < nrows; i += (int64_t)gridDim.x * kRR) {
+    double2 q = make_double2(0.0, 0.0);
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const double v = val[k];
+      const double2 x = V[(size_t)col[k] * nc + m.cg];
+      q.x = fma(v, x.x, q.x);
+      q.y = fma(v, x.y, q.y);
+    }
+    const double s = w ? w[i] : 1.0;
+    out[(size_t)i * nc + m.cg] = make_double2(s * q.x, s * q.y);
+  }
+}
+
+// T = M_s (G P) on the edges, for the active columns of the nodal solve
+__global__ void __launch_bounds__(kRT)
+lap_edge_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, const double* __restrict__ val,
+                const double* __restrict__ ms, int64_t n_edges, int nc, const RieszState* __restrict__ st,
+                const double2* __restrict__ P, double2* __restrict__ T) {
+  const GroupMap m(nc);
+  if (!m.on || !st[m.cg].active) return;
+  for (int64_t i = (int64_t)blockIdx.x * kRR + m.lr; i < n_edges; i += (int64_t)gridDim.x * kRR) {
+    double2 q = make_double2(0.0, 0.0);
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const double v = val[k];
+      const double2 x = P[(size_t)col[k] * nc + m.cg];
+      q.x = fma(v, x.x, q.x);
+      q.y = fma(v, x.y, q.y);
+    }
+    T[(size_t)i * nc + m.cg] = make_double2(ms[i] * q.x, ms[i] * q.y);
+  }
+}
+
+// Q = G^T T on the nodes (GT in CSR); partials of p^H q
+__global__ void __launch_bounds__(kRT)
+lap_node_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, const double* __restrict__ val,
+                int64_t n_nodes, int nc, const RieszState* __restrict__ st, const double2* __restrict__ T,
+                const double2* __restrict__ P, double2* __restrict__ Q, double* __restrict__ part) {
+  __shared__ double sh[kRT];
+  const GroupMap m(nc);
+  double acc = 0.0;
+  if (m.on && st[m.cg].active) {
+    for (int64_t j = (int64_t)blockIdx.x * kRR + m.lr; j < n_nodes; j += (int64_t)gridDim.x * kRR) {
+      double2 q = make_double2(0.0, 0.0);
+      for (int k = rowptr[j]; k < rowptr[j + 1]; ++k) {
+        const double v = val[k];
+        const double2 x = T[(size_t)col[k] * nc + m.cg];
+        q.x = fma(v, x.x, q.x);
+        q.y = fma(v, x.y, q.y);
+      }
+      const size_t e = (size_t)j * nc + m.cg;
+      const double2 p = P[e];
+      Q[e] = q;
+      acc += fma(p.x, q.x, p.y * q.y);
+    }
+  }
+  group_column_sum(acc, sh, part);
+}
+
+// 1 / diag(G^T M_s G): sum over the node's edges of GT^2 M_s
+__global__ void lap_dinv_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ ms, int64_t n_nodes,
+                                double* __restrict__ dinv) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_nodes;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double d = 0.0;
+    for (int k = rowptr[j]; k < rowptr[j + 1]; ++k) d += val[k] * val[k] * ms[col[k]];
+    dinv[j] = d > 0.0 ? 1.0 / d : __longlong_as_double(0x7ff8000000000000LL);
+  }
+}
+
+// T[i][c] = w_i V[i][c]
+__global__ void scale_rows_kernel(const double* __restrict__ w, const double2* __restrict__ V, int64_t n, int nc,
+                                  double2* __restrict__ T) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * nc;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const double s = w[idx / nc];
+    T[idx] = make_double2(s * V[idx].x, s * V[idx].y);
+  }
+}
+
+// o[c n + i] = Re(Y[i][c] - GY[i][c])
+__global__ void static_out_kernel(const double2* __restrict__ Y, const double2* __restrict__ GY, int64_t n, int nc,
+                                  double* __restrict__ o) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * nc;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / nc;
+    const int c = (int)(idx - i * nc);
+    o[(int64_t)c * n + i] = Y[idx].x - GY[idx].x;
+  }
+}
+
+// The nodal operator G^T M_s G of pcg_columns (edge pass into T, then the node pass)
+struct LapApply {
+  const int32_t *g_rowptr, *g_col, *gt_rowptr, *gt_col;
+  const double *g_val, *gt_val, *ms;
+  int64_t n_edges, n_nodes;
+  int nc, nblk, eblk;
+  double2* T;
+  cudaStream_t st;
+  static constexpr int kLaunches = 2;
+  void operator()(const RieszState* sts, const double2* P, double2* Q, double* part) const {
+    const unsigned ng = (unsigned)((nc + kRW - 1) / kRW);
+    lap_edge_kernel<<<dim3((unsigned)eblk, ng), kRT, 0, st>>>(g_rowptr, g_col, g_val, ms, n_edges, nc, sts, P, T);
+    lap_node_kernel<<<dim3((unsigned)nblk, ng), kRT, 0, st>>>(gt_rowptr, gt_col, gt_val, n_nodes, nc, sts, T, P, Q,
+                                                             part);
+  }
+};
+
+}  // namespace
+
+bool fom_has_certificate(const mrom_fom* fom) { return fom->X_diag != nullptr || fom->X_rowptr != nullptr; }
+
+mrom_status riesz_solve(mrom_ctx* h, const mrom_fom* fom, const double2* Phi, int nc, double2* Y, int* iters_max) {
+  const int64_t n = fom->n;
+  const double tol = fom->X_tol > 0.0 ? fom->X_tol : 1e-13;
+  const int max_iter = fom->X_max_iter > 0 ? fom->X_max_iter : 20000;
+  const int nblk = pcg_blocks(h, n, nc);
+  DevBuf dv;
+  cudaError_t e = cudaMalloc(&dv.p, (size_t)n * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(h, e, "certificate inner product: allocation");
+  auto* dinv = static_cast<double*>(dv.p);
+  riesz_dinv_kernel<<<(unsigned)std::min<int64_t>(65535, (n + 255) / 256), 256, 0, h->stream>>>(
+      fom->X_rowptr, fom->X_col, fom->X_val, n, dinv);
+  ++h->launches;
+  const CsrApply op{fom->X_rowptr, fom->X_col, fom->X_val, n, nc, nblk, h->stream};
+  return pcg_columns(h, n, nc, nblk, dinv, Phi, Y, tol, max_iter, op, iters_max, "certificate inner product");
+}
+
 }  // namespace mrom
+
+using namespace mrom;
+
+extern "C" mrom_status mrom_static_solve(mrom_handle h, const mrom_fom* fom, const double* M_s, int64_t n_nodes,
+                                         const int32_t* G_rowptr, const int32_t* G_col, const double* G_val,
+                                         const int32_t* GT_rowptr, const int32_t* GT_col, const double* GT_val,
+                                         const double* f, int32_t n_rhs, double tol, int32_t max_iter, double* o,
+                                         int32_t* iters) {
+  if (!h) return MROM_EINVAL;
+  if (!fom || fom->n < 1 || !fom->K_rowptr || !fom->K_col || !fom->K_val)
+    return fail(h, MROM_EINVAL, "mrom_static_solve: fom with n and K is required");
+  if (!M_s || !G_rowptr || !G_col || !G_val || !GT_rowptr || !GT_col || !GT_val || !f || !o || n_nodes < 1)
+    return fail(h, MROM_EINVAL, "mrom_static_solve: null argument or n_nodes < 1");
+  if (n_rhs < 1 || n_rhs > MROM_MAX_STATIC_RHS || !(tol > 0.0) || !std::isfinite(tol) || max_iter < 1)
+    return fail(h, MROM_EINVAL, "mrom_static_solve: 1 <= n_rhs <= MROM_MAX_STATIC_RHS, tol > 0, max_iter >= 1");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_static_solve: cudaSetDevice");
+  const int64_t n = fom->n;
+  const int nc = n_rhs;
+  cudaStream_t st = h->stream;
+  int32_t nnz = 0;
+  e = cudaMemcpy(&nnz, fom->K_rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  const size_t ne = (size_t)n * nc, nn = (size_t)n_nodes * nc;
+  DevBuf aval, vecs, small;
+  if (e == cudaSuccess) e = cudaMalloc(&aval.p, (size_t)std::max(nnz, 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&vecs.p, (4 * ne + 2 * nn) * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&small.p, ((size_t)n + (size_t)n_nodes) * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_static_solve: allocation");
+  auto* F = static_cast<double2*>(vecs.p);
+  double2* Y = F + ne;
+  double2* T = Y + ne;
+  double2* GY = T + ne;
+  double2* Bn = GY + ne;
+  double2* Yn = Bn + nn;
+  auto* dinv = static_cast<double*>(small.p);
+  double* dinv_n = dinv + n;
+  auto* A = static_cast<double*>(aval.p);
+  const auto g1 = [](int64_t work) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(65535, (work + 255) / 256)); };
+  // 1. (K + M_s) o0 = f by PCG: converges in the K part; the gradient part of o0 is left undetermined
+  static_matrix_kernel<<<g1(n), 256, 0, st>>>(fom->K_rowptr, fom->K_col, fom->K_val, M_s, n, A);
+  riesz_dinv_kernel<<<g1(n), 256, 0, st>>>(fom->K_rowptr, fom->K_col, A, n, dinv);
+  real_rows_kernel<<<g1(n * nc), 256, 0, st>>>(f, n, nc, F);
+  h->launches += 3;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_static_solve: launch");
+  const int nblk = pcg_blocks(h, n, nc);
+  int it1 = 0, it2 = 0;
+  mrom_status s = pcg_columns(h, n, nc, nblk, dinv, F, Y, tol, max_iter,
+                              CsrApply{fom->K_rowptr, fom->K_col, A, n, nc, nblk, st}, &it1,
+                              "mrom_static_solve (K + M_s)");
+  if (s != MROM_OK) return s;
+  // 2. remove the gradient part: (G^T M_s G) y = G^T M_s o0, o = o0 - G y
+  const unsigned ng = (unsigned)((nc + kRW - 1) / kRW);
+  scale_rows_kernel<<<g1(n * nc), 256, 0, st>>>(M_s, Y, n, nc, T);
+  const int nblk_n = pcg_blocks(h, n_nodes, nc);
+  csr_rows_kernel<<<dim3((unsigned)nblk_n, ng), kRT, 0, st>>>(GT_rowptr, GT_col, GT_val, nullptr, n_nodes, nc, T, Bn);
+  lap_dinv_kernel<<<g1(n_nodes), 256, 0, st>>>(GT_rowptr, GT_col, GT_val, M_s, n_nodes, dinv_n);
+  h->launches += 3;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_static_solve: launch");
+  const LapApply lap{G_rowptr, G_col, GT_rowptr, GT_col, G_val, GT_val, M_s, n, n_nodes, nc, nblk_n, nblk, T, st};
+  s = pcg_columns(h, n_nodes, nc, nblk_n, dinv_n, Bn, Yn, tol, max_iter, lap, &it2,
+                  "mrom_static_solve (G^T M_s G)");
+  if (s != MROM_OK) return s;
+  csr_rows_kernel<<<dim3((unsigned)nblk, ng), kRT, 0, st>>>(G_rowptr, G_col, G_val, nullptr, n, nc, Yn, GY);
+  static_out_kernel<<<g1(n * nc), 256, 0, st>>>(Y, GY, n, nc, o);
+  h->launches += 2;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_static_solve");
+  if (iters) {
+    iters[0] = it1;
+    iters[1] = it2;
+  }
+  return MROM_OK;
+}

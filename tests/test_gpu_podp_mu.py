@@ -111,8 +111,12 @@ def test_signature_and_gradients_match_oracle(mrom, case, lu):
         eI = (np.abs(I[k] - Ir).reshape(wo.size, -1).max(1) / sI).max()
         assert eR <= 1e-10 and eI <= 1e-10, (k, eR, eI)
         dR, dI = podp_mu.tangent_s_mu(model, wo, s_mu=sm, s_sigma=ss)
-        ref = float(np.sum(gR[k] * dR) + np.sum(gI[k] * dI))
-        scale = float(np.sum(np.abs(gR[k] * dR)) + np.sum(np.abs(gI[k] * dI)))
+        # dL/ds_mu is a sum over the frequencies, compared relative to the sum of its terms'
+        # magnitudes.  Floor 1e-8 (measured 8.7e-9): the two sides' reduced models come from their
+        # own truncated SVDs and projections of the same snapshots, and the derivative through the
+        # reduced static state (dy/ds, dB/ds, dc00/ds, dN0/ds) amplifies their 1e-11 difference.
+        per_w = np.sum(gR[k] * dR, axis=(1, 2)) + np.sum(gI[k] * dI, axis=(1, 2))
+        ref, scale = float(per_w.sum()), float(np.abs(per_w).sum())
         assert abs(g_m[k] - ref) <= 1e-8 * scale, (k, g_m[k], ref, scale)
 
 
@@ -178,8 +182,8 @@ def test_two_material_object_matches_oracle(mrom):
         eI = (np.abs(I[k] - Ir).reshape(wo.size, -1).max(1) / sI).max()
         assert eR <= 1e-10 and eI <= 1e-10, (k, eR, eI)
         dR, dI = podp_mu.tangent_s_mu(model, wo, s_mu=sm)
-        ref = float(np.sum(gR[k] * dR) + np.sum(gI[k] * dI))
-        scale = float(np.sum(np.abs(gR[k] * dR)) + np.sum(np.abs(gI[k] * dI)))
+        per_w = np.sum(gR[k] * dR, axis=(1, 2)) + np.sum(gI[k] * dI, axis=(1, 2))
+        ref, scale = float(per_w.sum()), float(np.abs(per_w).sum())
         assert abs(g_m[k] - ref) <= 1e-8 * scale, (k, g_m[k], ref, scale)
 
 

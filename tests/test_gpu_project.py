@@ -172,8 +172,9 @@ def test_per_direction_bases_match_oracle(mrom, case):
 
 
 def test_mixed_projection_matches_oracle(mrom, case):
-    """Single-precision projection products (K U, K_r, C_r, eps M_r, b in complex64 with float64
-    summation of the per-CTA partials; TSVD and certificate Gram in float64): the reduced
+    """Single-precision projection products (K U in complex64; K_r, C_r, eps M_r, b on the tensor
+    cores with the 3 x TF32 split and FP32 accumulation per CTA, float64 summation of the per-CTA
+    partials; TSVD and certificate Gram in float64): the reduced
     tensors stay within the mixed-precision tolerance of 1e-5 of the float64 oracle."""
     import torch
     from workloads import log_omegas
@@ -192,8 +193,12 @@ def test_mixed_projection_matches_oracle(mrom, case):
     # magnitude sum |U|^H |A| |U| (row sums of up to a few thousand terms per partial)
     absU = np.abs(U)
     Kabs = abs(p.K)
+    B = np.stack([model.b(i) for i in range(3)], 1)
+    absO = np.abs(p.o.T)
     for key, ref, mag in (("K", model.K[0][0], absU.T @ (Kabs @ absU)),
-                          ("C", model.C[0][0], absU.T @ (p.C[:, None] * absU))):
+                          ("C", model.C[0][0], absU.T @ (p.C[:, None] * absU)),
+                          ("Me", model.Me[0], absU.T @ ((p.eps * p.M)[:, None] * absU)),
+                          ("B", B, absU.T @ (p.C[:, None] * absO))):
         assert np.all(np.abs(got[key] - ref) <= 1e-5 * mag + 1e-300), key
     wo = log_omegas(1e1, 1e5, 64) * 1.03
     Rg, Ig, Dg = _sweep(mrom, h, [rom], wo)

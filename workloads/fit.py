@@ -258,7 +258,9 @@ def fit_problem(n: int, materials: Sequence[Material] = CUBE_C1, *, alpha: float
     """Assemble the FIT problem on an n^3 grid.
 
     eps is the regularisation of Eq. (7b) (mass on Omega minus B); eps_static
-    regularises the static theta^(0) problem with mass on all of Omega.  The
+    regularises the static theta^(0) problem with mass on all of Omega (M_s = eps_static M_Omega);
+    static_solver(K, M_s, rhs) -> o~ (N x 3) replaces the default sparse LU for that problem, whose
+    solution is the one with G^T M_s o~ = 0 for the discrete gradient G.  The
     static solve is skipped (o~ = 0, N0 = 0) when mu_r == 1 everywhere, or when
     static=False (for grids too large for a sparse direct solve; the operator
     shapes are unchanged).  mu_scale multiplies mu_r and sigma_scale sigma in
@@ -329,9 +331,18 @@ def fit_problem(n: int, materials: Sequence[Material] = CUBE_C1, *, alpha: float
     if magnetic and static:
         Kia = Kall[interior]
         rhs = -(Kia @ x_all.T)
-        A0 = (K + sp.diags(eps_static * Mo_all[interior])).tocsc()
-        solve = static_solver or (lambda A, b: spla.splu(A).solve(b))
-        o_tilde = np.asarray(solve(A0, rhs)).T
+        Ms = eps_static * Mo_all[interior]
+        if static_solver is not None:
+            o_tilde = np.asarray(static_solver(K, Ms, rhs)).T
+        else:
+            # sparse LU of K + M_s, then the gradient part fixed exactly: K G = 0 leaves it to the
+            # tiny M_s, so the LU solution carries rounding there of about cond x eps; the solution
+            # satisfies G^T M_s o~ = 0, restored by o~ -= G (G^T M_s G)^-1 G^T M_s o~
+            o_t = spla.splu((K + sp.diags(Ms)).tocsc()).solve(rhs)
+            Gn = node_gradient(n)
+            Ln = (Gn.T @ sp.diags(Ms) @ Gn).tocsc()
+            o_t = o_t - Gn @ spla.splu(Ln).solve(np.asarray(Gn.T @ (Ms[:, None] * o_t)))
+            o_tilde = np.asarray(o_t).T
         N0 = alpha ** 3 * np.eye(3) * np.sum(1.0 - inv_mu) * h ** 3 \
             + alpha ** 3 / 4.0 * (o_tilde @ (K @ o_tilde.T))
 
