@@ -210,65 +210,96 @@ def blas_threads() -> int:
         return os.cpu_count()
 
 
-def project_flops(n: int, nnz: int, m: int, r: int, cert: bool = True) -> float:
+def project_flops(n: int, nnz: int, m: int, r: int, cert: bool = True, per_dir: bool = False) -> float:
     """Algorithmic FP64 flops of mrom_project: snapshot Gram (Hermitian half), basis
-    apply, SpMM, K_r, C_r, eps M_r (Hermitian half), b, c00 and the certificate Gram."""
+    apply, SpMM, K_r, C_r, eps M_r (Hermitian half), b, c00 and the certificate Gram.  per_dir
+    (mrom_project_dirs): three snapshot Grams of m / 3 columns, each direction's basis from its own."""
     ng = 2 * r + 3
-    fl = 4.0 * n * m * m + 8.0 * n * m * r + 4.0 * nnz * r + 8.0 * n * r * r + 2 * 4.0 * n * r * r
+    gram_apply = (3 * 4.0 * n * (m / 3) ** 2 + 8.0 * n * (m / 3) * r) if per_dir else (4.0 * n * m * m + 8.0 * n * m * r)
+    fl = gram_apply + 4.0 * nnz * r + 8.0 * n * r * r + 2 * 4.0 * n * r * r
     fl += 8.0 * n * r * 3 + 4.0 * n * 9
     if cert:
         fl += 4.0 * n * ng * ng
     return fl
 
 
-def measure_projection(m, h, n_grid: int = 96, n_s: int = 32):
-    """mrom_project on an n_grid^3 FIT grid (96^3: N = 2.6M) with 3 x 32 synthetic snapshot columns."""
+def measure_projection(m, h, n_grid: int = 96, n_s: int = 32, n_out: int = 10000):
+    """The 96^3 plain-vs-mixed configuration: a mu_r = 32, sigma = 1.5e6 cube on the n_grid^3 FIT
+    grid (N = 2.6M) with the static correction theta~^(0) solved on the device (mrom_static_solve),
+    n_s full-order snapshots per direction at log-spaced omega in [1e1, 1e8] solved on the device
+    (mrom_fom_solve, Eq. (9)), the paper's PODP with one TSVD per direction (mrom_project_dirs,
+    TOL_Sigma 1e-6, r_i <= n_s), projected in float64 and in the mixed mode (complex64 SpMM, Gram
+    products on the tensor cores), then n_out outputs of each object (mrom_sweep, float64).  The
+    mixed mode's error against the float64 mode per R~ and I entry (R~: |diff| / (max_ij |R~| +
+    max_ij |N0|) per frequency, the size of the terms R~ = N0 + R sums; I: |diff| / (omega alpha^3/4
+    max |c00|)), and the float64 mode's own projection roofline (FP64 flops)."""
     import torch
-    from workloads import CUBE_C2, fit_problem, synthetic_snapshot_matrix
-    p = fit_problem(n_grid, CUBE_C2, static=False)
-    D = synthetic_snapshot_matrix(p.N, n_s, 20230711)
-    Dd = torch.from_numpy(np.ascontiguousarray(D.transpose(0, 2, 1).reshape(3 * n_s, p.N))).to("cuda")
-    del D
-    fom = m.FullOrder.from_fit(p, X=p.eps * p.M + 10.0 * p.C)
-    rom, sig, r = m.mrom_project(h, fom, Dd, tol_sigma=1e-6)  # warm-up
-    rom.close()
+    from workloads import CUBE_C2, fit_problem, log_omegas
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rom, sig, r = m.mrom_project(h, fom, Dd, tol_sigma=1e-6)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    rom.close()
-    fl = project_flops(p.N, p.K.nnz, 3 * n_s, r)
-    # single-precision products (K U and the K_r, C_r, eps M_r, b Gram products in complex64)
-    h.set_projection_precision(True)
-    rom, _, r32 = m.mrom_project(h, fom, Dd, tol_sigma=1e-6)  # warm-up
-    rom.close()
+    solver = m.static_solver_for(h, n_grid)
+    p = fit_problem(n_grid, CUBE_C2, static_solver=solver)
+    t_static = time.perf_counter() - t0
+    fom = m.FullOrder.from_fit(p)
+    ws = log_omegas(1e1, 1e8, n_s)
+    per_call = max(1, 48 // 3)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rom, _, r32 = m.mrom_project(h, fom, Dd, tol_sigma=1e-6)
+    Qs, its = [], []
+    for k in range(0, n_s, per_call):
+        Q, it, _ = m.mrom_fom_solve(h, fom, ws[k:k + per_call], tol=1e-12)
+        Qs.append(Q)
+        its.append(int(it.max()))
+    Q = torch.cat(Qs)
     torch.cuda.synchronize()
-    dt32 = time.perf_counter() - t0
-    rom.close()
+    t_fom = time.perf_counter() - t0
+    Dd = Q.view(n_s, 3, p.N).transpose(0, 1).reshape(3 * n_s, p.N).contiguous()  # direction-major columns
+    del Q, Qs
+    res = {}
+    for mixed in (False, True):
+        h.set_projection_precision(mixed)
+        m.mrom_project_dirs(h, fom, Dd, tol_sigma=1e-6)[0].close()  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rom, _, rd = m.mrom_project_dirs(h, fom, Dd, tol_sigma=1e-6)
+        torch.cuda.synchronize()
+        res[mixed] = [rom, time.perf_counter() - t0, rd]
     h.set_projection_precision(False)
-    # the sweep of this object over 10^4 output frequencies (with certificate)
-    rom, _, _ = m.mrom_project(h, fom, Dd, tol_sigma=1e-6)
-    from workloads import log_omegas
-    om = torch.as_tensor(log_omegas(1e1, 1e8, 10000), device="cuda")
-    Rs = torch.empty((1, 10000, 3, 3), dtype=torch.float64, device="cuda")
-    Is, Ds = torch.empty_like(Rs), torch.empty_like(Rs)
-    m.mrom_sweep(h, [rom], om, 10000, Rs, Is, Ds)
-    h.synchronize()
-    t0 = time.perf_counter()
-    m.mrom_sweep(h, [rom], om, 10000, Rs, Is, Ds)
-    h.synchronize()
-    sweep_ms = 1e3 * (time.perf_counter() - t0)
-    rom.close()
-    return {"workload": f"mrom_project: {n_grid}^3 FIT grid (N = {p.N}, {p.K.nnz} nnz), 3 x {n_s} snapshot columns, "
-                        f"TOL_Sigma 1e-6 -> r = {r}, certificate Gram with diagonal X",
-            "seconds": dt, "r": r, "flops": fl, "achieved_tflops": fl / dt / 1e12,
-            "bound": "alu", "fp64_frac": fl / dt / 1e12 / (SM_COUNT_NOMINAL * DFMA_PER_CLK_PER_SM * 2 * 2.07e9 / 1e12),
-            "hbm_gb_moved_min": (3 * n_s * p.N * 16 * 2 + p.N * r * 16 * 4 + p.K.nnz * 12) / 1e9,
-            "mixed_seconds": dt32, "mixed_r": r32, "sweep_10000_omega_ms": sweep_ms}
+    wo = log_omegas(1e1, 1e8, n_out)
+    om = torch.as_tensor(wo, device="cuda")
+    out = {}
+    for mixed in (False, True):
+        R = torch.empty((1, n_out, 3, 3), dtype=torch.float64, device="cuda")
+        I = torch.empty_like(R)
+        m.mrom_sweep(h, [res[mixed][0]], om, n_out, R, I)
+        h.synchronize()
+        t0 = time.perf_counter()
+        m.mrom_sweep(h, [res[mixed][0]], om, n_out, R, I)
+        h.synchronize()
+        out[mixed] = (R[0].cpu().numpy(), I[0].cpu().numpy(), 1e3 * (time.perf_counter() - t0))
+    g64 = m.mrom_rom_get(res[False][0], with_gram=False)
+    c00 = np.asarray(g64["c00"])
+    sR = (np.abs(out[False][0]).reshape(n_out, -1).max(1) + np.abs(p.N0).max())[:, None, None]
+    sI = (wo * p.alpha ** 3 / 4 * np.abs(c00).max())[:, None, None]
+    eR = (np.abs(out[True][0] - out[False][0]) / sR).max(0)
+    eI = (np.abs(out[True][1] - out[False][1]) / sI).max(0)
+    rsum = int(sum(res[False][2]))
+    fl = project_flops(p.N, p.K.nnz, 3 * n_s, rsum, cert=False, per_dir=True)
+    dt = res[False][1]
+    for mixed in (False, True):
+        res[mixed][0].close()
+    return {"workload": f"{n_grid}^3 FIT grid (N = {p.N}, {p.K.nnz} nnz), mu_r = 32 cube with the static "
+                        f"correction, {n_s} device-solved snapshots per direction in [1e1, 1e8], one TSVD per "
+                        f"direction (TOL_Sigma 1e-6 -> r = {list(res[False][2])}), {n_out} outputs",
+            "static_solve_seconds_with_assembly": t_static, "static_iterations": list(solver.iters),
+            "snapshot_solve_seconds": t_fom, "snapshot_iterations_max": its,
+            "project_seconds": {"fp64": dt, "mixed": res[True][1]}, "r_dirs_mixed": list(res[True][2]),
+            "sweep_ms": {"fp64": out[False][2], "mixed": out[True][2]},
+            "fp64_project_flops": fl, "fp64_project_frac": fl / dt / 1e12 / (SM_COUNT_NOMINAL * DFMA_PER_CLK_PER_SM * 2 * 2.07e9 / 1e12),
+            "mixed_vs_fp64_per_entry": {"R": eR.round(12).tolist(), "I": eI.round(12).tolist(),
+                                        "max_R": float(eR.max()), "max_I": float(eI.max()),
+                                        "normalisation": "R~: |diff| / (max|R~| + max|N0|); I: |diff| / "
+                                                         "(omega alpha^3/4 max|c00|), per frequency"}}
 
 
 def measure_podp_mu(m, h, stream, n_grid=16, n_inst=1000, n_w=2000):
@@ -735,9 +766,22 @@ def main():
     e1.record(stream)
     h.synchronize()
     ms_inv = e0.elapsed_time(e1)
-    inv = {"ms_for_R_and_I": ms_inv, "matrices": 2 * args.n_obj * args.n_w,
-           "achieved_gbs": 2 * args.n_obj * args.n_w * (72 + 24) / (ms_inv * 1e-3) / 1e9}
     del eigs
+    # the same invariants fused into the sweep's epilogue (mrom_plan_sweep_invariants): the step's
+    # extra time over the plain step
+    E6 = torch.empty((args.n_obj, args.n_w, 6), dtype=torch.float64, device=dev)
+    plan.sweep(om, R, I, D, eig=E6)
+    h.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.sweep(om, R, I, D, eig=E6)
+    e1.record(stream)
+    h.synchronize()
+    ms_fused = e0.elapsed_time(e1) / args.steps
+    del E6
+    inv = {"standalone_ms_for_R_and_I": ms_inv, "matrices": 2 * args.n_obj * args.n_w,
+           "fused_step_ms": ms_fused, "fused_extra_ms": ms_fused - ms_per_step,
+           "method": "closed form (trigonometric outermost eigenvalue, deflation, 2 x 2), FP64"}
 
     # ---- end to end through the public API from pinned host buffers
     # (measured right after the timed device steps, in the same thermal and clock state; the later

@@ -469,6 +469,14 @@ mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, int32_t n_ob
 mrom_status mrom_plan_sweep(mrom_plan plan, const double* omega, int32_t omega_stride,
                             double* R, double* I, double* Delta);
 mrom_status mrom_plan_destroy(mrom_plan plan);
+/* mrom_plan_sweep that also writes the rotation invariants of every evaluation (Sect. 1: the
+ * eigenvalues of R~ = N0 + R and of I do not depend on the object's orientation), computed in the
+ * sweep kernels' epilogue from the values they hold, so the 3 x 3 outputs need not be read back:
+ * eig (device, [n_obj][n_w][6]): the eigenvalues of the symmetric part of R~ in ascending order,
+ * then those of I (closed form, as mrom_invariants).  R, I and Delta may be NULL (then only the
+ * invariants are written).  Same rules as mrom_plan_sweep otherwise. */
+mrom_status mrom_plan_sweep_invariants(mrom_plan plan, const double* omega, int32_t omega_stride, double* R,
+                                       double* I, double* Delta, double* eig);
 
 /* Solver of the reduced systems for plans created (and one-shot sweeps run) after
  * this call.  MROM_SOLVER_AUTO (default): every object with one basis shared by
@@ -511,8 +519,10 @@ mrom_status mrom_tune(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int3
  * not depend on the orientation; dictionary matching compares the eigenvalues
  * of R~ = N0 + R and of I per frequency).  M: n real 3 x 3 matrices (device,
  * [n][3][3] row-major, e.g. the R or I output of mrom_sweep); eig: n x 3
- * eigenvalues of their symmetric parts in ascending order (device).  Cyclic
- * Jacobi per matrix: absolute accuracy a few eps ||M||, repeated eigenvalues
+ * eigenvalues of their symmetric parts in ascending order (device).  Closed form
+ * per matrix (the trigonometric solution of the characteristic cubic for the
+ * eigenvalue farthest from the others, deflation by its eigenvector, a 2 x 2
+ * problem for the pair): absolute accuracy a few eps ||M||, repeated eigenvalues
  * included.  Asynchronous; MROM_EINVAL for n < 0 or null arrays with n > 0. */
 mrom_status mrom_invariants(mrom_handle h, const double* M, int64_t n, double* eig);
 

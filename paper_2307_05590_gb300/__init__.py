@@ -275,9 +275,15 @@ class Plan:
         _abi.check(lib().mrom_plan_create(handle.ptr, _rom_array(self.objs), len(self.objs), self.n_w,
                                           ctypes.byref(self._p)), handle.ptr)
 
-    def sweep(self, omega, R, I, Delta=None, omega_stride: int = 0):
-        _abi.check(lib().mrom_plan_sweep(self._p, _ptr(omega), int(omega_stride), _ptr(R), _ptr(I),
-                                         _ptr(Delta)), self.handle.ptr)
+    def sweep(self, omega, R, I, Delta=None, omega_stride: int = 0, eig=None):
+        """mrom_plan_sweep; with eig (device [n_obj][n_w][6]) mrom_plan_sweep_invariants, which also
+        writes the eigenvalues of R~ and I from the sweep's epilogue (R, I may then be None)."""
+        if eig is None:
+            _abi.check(lib().mrom_plan_sweep(self._p, _ptr(omega), int(omega_stride), _ptr(R), _ptr(I),
+                                             _ptr(Delta)), self.handle.ptr)
+        else:
+            _abi.check(lib().mrom_plan_sweep_invariants(self._p, _ptr(omega), int(omega_stride), _ptr(R), _ptr(I),
+                                                        _ptr(Delta), _ptr(eig)), self.handle.ptr)
 
     def enable_timing(self) -> None:
         """Record CUDA events around the stages of every later sweep (mrom_plan_timing)."""

@@ -20,7 +20,7 @@ EXPORTS = [
     "mrom_project_dirs", "mrom_set_projection_precision", "mrom_set_solver", "mrom_plan_solver_counts",
     "mrom_plan_timing", "mrom_rom_from_reduced_batch", "mrom_invariants", "mrom_project_mu",
     "mrom_rom_static_rank", "mrom_rom_mu_state", "mrom_fom_solve", "mrom_rom_from_packed", "mrom_rom_free_batch",
-    "mrom_fp64_peak", "mrom_static_solve",
+    "mrom_fp64_peak", "mrom_static_solve", "mrom_plan_sweep_invariants",
 ]
 
 
@@ -134,6 +134,7 @@ def _declare(L):
         "mrom_invariants": (ctypes.c_int, [vp, vp, i64, vp]),
         "mrom_static_solve": (ctypes.c_int, [vp, ctypes.POINTER(mrom_fom), vp, i64, vp, vp, vp, vp, vp, vp, vp, i32,
                                              ctypes.c_double, i32, vp, ctypes.POINTER(i32)]),
+        "mrom_plan_sweep_invariants": (ctypes.c_int, [vp, vp, i32, vp, vp, vp, vp]),
         "mrom_fp64_peak": (ctypes.c_int, [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "mrom_plan_solver_counts": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "mrom_rom_from_reduced": (ctypes.c_int, [vp, ctypes.POINTER(mrom_reduced_desc), ctypes.POINTER(vp)]),

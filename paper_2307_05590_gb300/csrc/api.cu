@@ -317,14 +317,14 @@ extern "C" mrom_status mrom_plan_destroy(mrom_plan plan) {
 namespace {
 
 mrom_status run_plan(mrom_plan plan, const double* omega, int32_t omega_stride, const double* s_sigma,
-                     double* R, double* I, double* Delta) {
+                     double* R, double* I, double* Delta, double* eig = nullptr) {
   mrom_ctx* h = plan->ctx;
   if (!omega) return fail(h, MROM_EINVAL, "sweep: omega is null");
   if (omega_stride != 0 && omega_stride < plan->n_w)
     return fail(h, MROM_EINVAL, "sweep: omega_stride must be 0 or >= n_w");
   if (Delta && !plan->all_cert)
     return fail(h, MROM_EINVAL, "sweep: Delta requested but an object has no Gram matrix");
-  if (!R && !I && !Delta) return MROM_OK;
+  if (!R && !I && !Delta && !eig) return MROM_OK;
   cudaSetDevice(h->device);
   auto mark = [&](int k) {
     if (plan->timing) cudaEventRecord(plan->ev[k], h->stream);
@@ -340,11 +340,11 @@ mrom_status run_plan(mrom_plan plan, const double* omega, int32_t omega_stride, 
     mark(2);
     if (e == cudaSuccess)
       e = launch_pencil_sweep(plan->d_objs, t.d_pens, t.d_table_pen, t.d_counters + 2, omega, omega_stride, s_sigma,
-                              R, I, Delta, h->d_status, plan->n_w, t.pen_grid, t.pen_smem, h->stream);
+                              R, I, Delta, eig, h->d_status, plan->n_w, t.pen_grid, t.pen_smem, h->stream);
     mark(3);
     if (e == cudaSuccess)
       e = launch_sweep_fp64_routed(plan->cfg, plan->d_objs, t.d_table_lu, t.d_counters + 3, omega, omega_stride,
-                                   s_sigma, R, I, Delta, h->d_status, plan->n_w, plan->grid, plan->smem_bytes,
+                                   s_sigma, R, I, Delta, eig, h->d_status, plan->n_w, plan->grid, plan->smem_bytes,
                                    plan->d_workspace, plan->ws_elems, h->stream);
     mark(4);
     if (e != cudaSuccess) return cuda_fail(h, e, "sweep launch");
@@ -359,7 +359,7 @@ mrom_status run_plan(mrom_plan plan, const double* omega, int32_t omega_stride, 
   if (e == cudaSuccess) e = cudaMemsetAsync(plan->d_counter, 0, sizeof(int), h->stream);
   if (e == cudaSuccess)
     e = launch_sweep_fp64(plan->cfg, plan->d_objs, plan->d_tasks, plan->n_tasks, plan->d_counter, omega, omega_stride,
-                          s_sigma, R, I, Delta, h->d_status, plan->n_w, plan->grid, plan->smem_bytes,
+                          s_sigma, R, I, Delta, eig, h->d_status, plan->n_w, plan->grid, plan->smem_bytes,
                           plan->d_workspace, plan->ws_elems, h->stream);
   mark(4);
   if (e != cudaSuccess) return cuda_fail(h, e, "sweep launch");
@@ -416,6 +416,12 @@ extern "C" mrom_status mrom_plan_sweep(mrom_plan plan, const double* omega, int3
                                        double* I, double* Delta) {
   if (!plan) return MROM_EINVAL;
   return run_plan(plan, omega, omega_stride, nullptr, R, I, Delta);
+}
+
+extern "C" mrom_status mrom_plan_sweep_invariants(mrom_plan plan, const double* omega, int32_t omega_stride,
+                                                  double* R, double* I, double* Delta, double* eig) {
+  if (!plan) return MROM_EINVAL;
+  return run_plan(plan, omega, omega_stride, nullptr, R, I, Delta, eig);
 }
 
 namespace mrom {

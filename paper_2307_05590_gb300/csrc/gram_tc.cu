@@ -10,7 +10,7 @@
 // memory (three tcgen05.mma of kind::tf32 per product tile): products accurate to FP32's level
 // instead of TF32's 1e-3.  The rows are the reduction dimension (K of the MMA).
 //
-// Per CTA (one per SM, a contiguous range of rows): chunks of 16 rows of A, B and w are copied
+// Per CTA (one per SM, 16 warps, a contiguous range of rows): chunks of 16 rows of A, B and w are copied
 // into shared memory by the bulk-copy engine (cp.async.bulk, completion on an mbarrier), two raw
 // stages in flight; all threads convert a raw chunk into the K-major operand tiles (real and
 // imaginary rows, hi and lo parts; two operand stages), one thread issues the MMAs and commits
@@ -35,7 +35,7 @@
 namespace mrom {
 namespace {
 
-constexpr int kTT = 256;           // threads per CTA (8 warps)
+constexpr int kTT = 512;           // threads per CTA (16 warps)
 constexpr int kTK = 16;            // rows (MMA K) per chunk
 constexpr int kMaxHalf = 112;      // ma, mb <= 112, so 2 ma, 2 mb <= 224
 constexpr long long kSpinLimit = 1LL << 26;  // try_wait polls before a wait gives up
@@ -231,16 +231,20 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
   // blocks.  With no chunk the block is set to zero without touching tensor memory.
   const int nchunks_cta = nchunks;
   auto flush = [&](bool first) {
-    const int q = warp & 3, half = warp >> 2;
+    const int q = warp & 3, cg = warp >> 2;
+    constexpr int kCG = kTT / 128;  // warp sets sharing the lane quarters
     double* out = g.part + (size_t)blockIdx.x * mpad * npad;
     for (int t = 0; t < mtiles; ++t) {
       const int m = t * 128 + q * 32 + lane;
-      for (int cb = half * 8; cb < npad; cb += 16) {
+      for (int cb = cg * 8; cb < npad; cb += 8 * kCG) {
         float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (nchunks_cta > 0) tmem_ld8(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * npad + cb), v);
-        double* o = out + (size_t)m * npad + cb;
+        // partial block stored [column][row]: the 32 lanes of a warp write 32 consecutive rows
 #pragma unroll
-        for (int k = 0; k < 8; ++k) o[k] = first ? (double)v[k] : o[k] + (double)v[k];
+        for (int k = 0; k < 8; ++k) {
+          double* o = out + (size_t)(cb + k) * mpad + m;
+          *o = first ? (double)v[k] : *o + (double)v[k];
+        }
       }
     }
   };
@@ -251,40 +255,54 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
     const int s = c & 1;
     const int rows = chunk_rows(c);
     const bool full = rows == kTK;
+    // thread 0 polls (bounded); after the barrier every other thread observes the completed
+    // phases with one try_wait each, which makes the copied bytes visible to it
     bool ok = true;
-    if (full) ok = mbar_wait(raw_full + s, (uint32_t)((c >> 1) & 1));
-    if (c >= 2 && ok) ok = mbar_wait(op_free + s, (uint32_t)(((c - 2) >> 1) & 1));
+    if (tid == 0) {
+      if (full) ok = mbar_wait(raw_full + s, (uint32_t)((c >> 1) & 1));
+      if (c >= 2 && ok) ok = mbar_wait(op_free + s, (uint32_t)(((c - 2) >> 1) & 1));
+    }
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
     }
+    if (tid != 0 && full) mbar_wait(raw_full + s, (uint32_t)((c >> 1) & 1));
     // ---- convert chunk c into the operand tiles of stage s
     const int64_t r0 = row0 + (int64_t)c * kTK;
     const int nb = g.same_ab ? ma : mb;
-    const int items = kTK * (ma + mb);
+    // one core matrix (8 operand rows x 4 k) per warp step: lane -> (row 8 g + lane / 4,
+    // k = 4 q + lane % 4), so the 32 lanes store one contiguous 128-byte core matrix (no bank
+    // conflicts); A's units first, then B's
+    const int ga = (ma + 7) >> 3, gb = (mb + 7) >> 3;
+    const int units = 4 * (ga + gb);
+    const int ml = lane >> 2, kl = lane & 3;
     unsigned char *ah = a_hi(s), *al = a_lo(s), *bh = b_hi(s), *bl = b_lo(s);
-    for (int idx = tid; idx < items; idx += kTT) {
-      if (idx < kTK * ma) {
-        const int kk = idx / ma, m = idx - (idx / ma) * ma;
-        float2 a = make_float2(0.f, 0.f);
-        if (full) a = raw_a(s)[kk * ma + m];
-        else if (kk < rows) a = g.A[(r0 + kk) * ma + m];
-        put_split(ah, al, m, kk, a.x);
-        put_split(ah, al, ma + m, kk, a.y);
-      } else {
-        const int j = idx - kTK * ma;
-        const int kk = j / mb, n = j - (j / mb) * mb;
-        float2 b = make_float2(0.f, 0.f);
-        float wt = 1.f;
-        if (full) {
-          b = g.same_ab ? raw_a(s)[kk * nb + n] : raw_b(s)[kk * nb + n];
-          if (g.w) wt = raw_w(s)[kk];
-        } else if (kk < rows) {
-          b = g.same_ab ? g.A[(r0 + kk) * nb + n] : g.B[(r0 + kk) * nb + n];
-          if (g.w) wt = g.w[r0 + kk];
+    for (int u = warp; u < units; u += kTT / 32) {
+      if (u < 4 * ga) {
+        const int m = 8 * (u >> 2) + ml, kk = 4 * (u & 3) + kl;
+        if (m < ma) {
+          float2 a = make_float2(0.f, 0.f);
+          if (full) a = raw_a(s)[kk * ma + m];
+          else if (kk < rows) a = g.A[(r0 + kk) * ma + m];
+          put_split(ah, al, m, kk, a.x);
+          put_split(ah, al, ma + m, kk, a.y);
         }
-        put_split(bh, bl, n, kk, wt * b.x);
-        put_split(bh, bl, mb + n, kk, wt * b.y);
+      } else {
+        const int v = u - 4 * ga;
+        const int n = 8 * (v >> 2) + ml, kk = 4 * (v & 3) + kl;
+        if (n < mb) {
+          float2 b = make_float2(0.f, 0.f);
+          float wt = 1.f;
+          if (full) {
+            b = g.same_ab ? raw_a(s)[kk * nb + n] : raw_b(s)[kk * nb + n];
+            if (g.w) wt = raw_w(s)[kk];
+          } else if (kk < rows) {
+            b = g.same_ab ? g.A[(r0 + kk) * nb + n] : g.B[(r0 + kk) * nb + n];
+            if (g.w) wt = g.w[r0 + kk];
+          }
+          put_split(bh, bl, n, kk, wt * b.x);
+          put_split(bh, bl, mb + n, kk, wt * b.y);
+        }
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -307,12 +325,13 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
     }
     // ---- end of a segment: add the FP32 accumulator into this CTA's float64 partial block
     if (c % kFlush == kFlush - 1 || c == nchunks - 1) {
-      const bool ok = mbar_wait(op_free + s, (uint32_t)((c >> 1) & 1));
+      const bool ok = tid == 0 ? mbar_wait(op_free + s, (uint32_t)((c >> 1) & 1)) : true;
       if (__syncthreads_or(!ok)) {
         failed = true;
         ++c;  // chunk c was consumed
         break;
       }
+      if (tid != 0) mbar_wait(op_free + s, (uint32_t)((c >> 1) & 1));  // completed: returns at once
       tc_fence_after();
       flush(c < kFlush);
       tc_fence_before();
@@ -337,7 +356,7 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
 }
 
 // G[i][j] = sum over the CTAs of (P[i][j] + P[ma+i][mb+j]) + i (P[i][mb+j] - P[ma+i][j]), float64,
-// CTAs in order
+// CTAs in order; a CTA's block P is stored [column][row]
 __global__ void gram_tc_reduce_kernel(const double* __restrict__ part, int nblk, int ma, int mb, int mpad, int npad,
                                       double2* __restrict__ G, int64_t ldg) {
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < ma * mb; idx += gridDim.x * blockDim.x) {
@@ -345,8 +364,8 @@ __global__ void gram_tc_reduce_kernel(const double* __restrict__ part, int nblk,
     double re = 0.0, im = 0.0;
     for (int b = 0; b < nblk; ++b) {
       const double* P = part + (size_t)b * mpad * npad;
-      re += P[(size_t)i * npad + j] + P[(size_t)(ma + i) * npad + mb + j];
-      im += P[(size_t)i * npad + mb + j] - P[(size_t)(ma + i) * npad + j];
+      re += P[(size_t)j * mpad + i] + P[(size_t)(mb + j) * mpad + ma + i];
+      im += P[(size_t)(mb + j) * mpad + i] - P[(size_t)j * mpad + ma + i];
     }
     G[(size_t)i * ldg + j] = make_double2(re, im);
   }

@@ -254,7 +254,7 @@ size_t sweep_fp64_bytes_per_system(int r, bool matrix_in_smem);
 cudaError_t sweep_fp64_configure(int cfg, size_t smem_bytes);
 cudaError_t launch_sweep_fp64(int cfg, const RomDev* objs, const SweepTask* tasks, int n_tasks, int* counter,
                               const double* omega, int omega_stride, const double* s_sigma,
-                              double* R, double* I, double* Delta, int* status, int n_w, int grid,
+                              double* R, double* I, double* Delta, double* eig, int* status, int n_w, int grid,
                               size_t smem_bytes, double2* workspace, size_t ws_elems, cudaStream_t stream);
 
 // Same sweep with the task list replaced by a compact per-object table (see
@@ -268,8 +268,8 @@ cudaError_t launch_sweep_fp64_implicit(int cfg, const RomDev* objs, const SweepT
 // task count (table[0].w0); s_sigma as in launch_sweep_fp64.
 cudaError_t launch_sweep_fp64_routed(int cfg, const RomDev* objs, const SweepTask* table, int* counter,
                                      const double* omega, int omega_stride, const double* s_sigma, double* R,
-                                     double* I, double* Delta, int* status, int n_w, int grid, size_t smem_bytes,
-                                     double2* workspace, size_t ws_elems, cudaStream_t stream);
+                                     double* I, double* Delta, double* eig, int* status, int n_w, int grid,
+                                     size_t smem_bytes, double2* workspace, size_t ws_elems, cudaStream_t stream);
 
 // Pencil route (pencil.cu).
 size_t pencil_sweep_smem_bytes(int r, int F);
@@ -293,8 +293,8 @@ cudaError_t launch_pencil_vjp(const RomDev* objs, const PencilDev* pens, const S
                               double* I, int* status, int n_w, int grid, size_t smem_bytes, cudaStream_t stream);
 cudaError_t launch_pencil_sweep(const RomDev* objs, const PencilDev* pens, const SweepTask* table, int* counter,
                                 const double* omega, int omega_stride, const double* s_sigma, double* R,
-                                double* I, double* Delta, int* status, int n_w, int grid, size_t smem_bytes,
-                                cudaStream_t stream);
+                                double* I, double* Delta, double* eig, int* status, int n_w, int grid,
+                                size_t smem_bytes, cudaStream_t stream);
 
 // Builds the RomDev record of an object (api.cu).
 RomDev rom_record(const mrom_rom* m);

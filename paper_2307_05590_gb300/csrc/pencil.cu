@@ -20,6 +20,7 @@
 // exceeds the gate, whose C is not numerically positive definite, or whose QL iteration
 // does not converge are routed to the LU kernel instead (device-side routing, no host sync).
 #include "mrom_internal.h"
+#include "eig3.cuh"
 #include "herm_tridiag.cuh"
 
 #include <algorithm>
@@ -633,8 +634,9 @@ template <bool CERT, bool HAS_E>
 __device__ __forceinline__ void pencil_task(const RomDev& ob, const PencilDev& pd, const SweepTask& task,
                                             const double* __restrict__ omega, int omega_stride, double ssig,
                                             double* __restrict__ Rout, double* __restrict__ Iout,
-                                            double* __restrict__ Dout, int* __restrict__ status, int n_w,
-                                            unsigned char* smem_raw, double* Ws) {
+                                            double* __restrict__ Dout, double* __restrict__ Eout,
+                                            int* __restrict__ status, int n_w, unsigned char* smem_raw,
+                                            double* Ws) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double2* zs = reinterpret_cast<double2*>(smem_raw);
   double* rbuf = reinterpret_cast<double*>(smem_raw);
@@ -731,6 +733,30 @@ __device__ __forceinline__ void pencil_task(const RomDev& ob, const PencilDev& p
       }
     }
   }
+  // ---- rotation invariants: eigenvalues of the symmetric parts of R~ and I (one thread per
+  // frequency and matrix, from the same totals)
+  if (Eout) {
+    for (int idx = tid; idx < 2 * S; idx += kPT) {
+      const int s = idx >> 1, is_i = idx & 1;
+      const double* tot = rbuf + (size_t)(s >> 5) * kNQ * 32 + (s & 31);
+      auto t = [tot](int q) { return tot[q * 32]; };
+      const double wv = Ws[s];
+      double Mp[6];  // packed (00, 01, 02, 11, 12, 22)
+#pragma unroll
+      for (int sym = 0; sym < 6; ++sym) {
+        const int i = sym < 3 ? 0 : (sym < 5 ? 1 : 2), j = sym < 3 ? sym : (sym < 5 ? sym - 2 : 2);
+        if (is_i) {
+          Mp[sym] = 0.25 * ob.alpha3 * wv * (0.5 * (ob.c00[i * 3 + j] + ob.c00[j * 3 + i]) + t(33 + sym));
+        } else {
+          double kf = t(27 + sym);
+          if constexpr (HAS_E) kf -= t(18 + i * 3 + j) + t(18 + j * 3 + i);
+          Mp[sym] = fma(-0.25 * ob.alpha3, kf, 0.5 * (ob.N0[i * 3 + j] + ob.N0[j * 3 + i]));
+        }
+      }
+      double* e = Eout + ((size_t)task.obj * n_w + task.w0 + s) * 6 + 3 * is_i;
+      sym3_eig(Mp[0], Mp[3], Mp[5], Mp[1], Mp[2], Mp[4], e[0], e[1], e[2]);
+    }
+  }
   // the next task's first barrier orders these reads before the space is rewritten
 }
 
@@ -739,7 +765,7 @@ pencil_sweep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict
                     const SweepTask* __restrict__ table, int* __restrict__ counter,
                     const double* __restrict__ omega, int omega_stride, const double* __restrict__ s_sigma,
                     double* __restrict__ Rout, double* __restrict__ Iout, double* __restrict__ Dout,
-                    int* __restrict__ status, int n_w) {
+                    double* __restrict__ Eout, int* __restrict__ status, int n_w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_task;
   __shared__ double Ws[kPT];
@@ -763,15 +789,15 @@ pencil_sweep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict
     const double ssig = s_sigma ? s_sigma[task.obj] : 1.0;
     if (cert) {
       if (has_e)
-        pencil_task<true, true>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, status, n_w, smem_raw, Ws);
+        pencil_task<true, true>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, Eout, status, n_w, smem_raw, Ws);
       else
-        pencil_task<true, false>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, status, n_w, smem_raw, Ws);
+        pencil_task<true, false>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, Eout, status, n_w, smem_raw, Ws);
     } else {
       if (has_e)
-        pencil_task<false, true>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, status, n_w, smem_raw, Ws);
+        pencil_task<false, true>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, Eout, status, n_w, smem_raw, Ws);
       else
-        pencil_task<false, false>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, status, n_w, smem_raw,
-                                  Ws);
+        pencil_task<false, false>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, Eout, status, n_w,
+                                  smem_raw, Ws);
     }
   }
 }
@@ -1109,13 +1135,13 @@ cudaError_t launch_pencil_vjp(const RomDev* objs, const PencilDev* pens, const S
 
 cudaError_t launch_pencil_sweep(const RomDev* objs, const PencilDev* pens, const SweepTask* table, int* counter,
                                 const double* omega, int omega_stride, const double* s_sigma, double* R,
-                                double* I, double* Delta, int* status, int n_w, int grid, size_t smem_bytes,
-                                cudaStream_t stream) {
+                                double* I, double* Delta, double* eig, int* status, int n_w, int grid,
+                                size_t smem_bytes, cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(pencil_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes);
   if (e != cudaSuccess) return e;
   pencil_sweep_kernel<<<grid, kPT, smem_bytes, stream>>>(objs, pens, table, counter, omega, omega_stride, s_sigma,
-                                                         R, I, Delta, status, n_w);
+                                                         R, I, Delta, eig, status, n_w);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@
 // work into tasks of equal cost.  CTAs pull tasks from a cost-sorted list
 // through an atomic counter (no waits).
 #include "mrom_internal.h"
+#include "eig3.cuh"
 
 namespace mrom {
 namespace {
@@ -79,8 +80,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
 sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__ tasks, int n_tasks,
                   int* __restrict__ counter, const double* __restrict__ omega, int omega_stride,
                   const double* __restrict__ s_sigma, double* __restrict__ Rout,
-                  double* __restrict__ Iout, double* __restrict__ Dout, int* __restrict__ status,
-                  int n_w, double2* __restrict__ workspace, size_t ws_elems) {
+                  double* __restrict__ Iout, double* __restrict__ Dout, double* __restrict__ Eout,
+                  int* __restrict__ status, int n_w, double2* __restrict__ workspace, size_t ws_elems) {
   constexpr int kWarps = THREADS / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_task;
@@ -357,6 +358,32 @@ sweep_fp64_kernel(const RomDev* __restrict__ objs, const SweepTask* __restrict__
         }
       }
     }
+    // ---- rotation invariants: eigenvalues of the symmetric parts of R~ and I (one thread per
+    // frequency and matrix)
+    if (Eout) {
+      for (int idx = tid; idx < 2 * S; idx += THREADS) {
+        const int s = idx >> 1, is_i = idx & 1;
+        const double* rp = Red + (size_t)s * kRed * kSplit;
+        auto red = [rp](int q) {
+          double v = 0.0;
+#pragma unroll
+          for (int k = 0; k < kSplit; ++k) v += rp[q * kSplit + k];
+          return v;
+        };
+        const double w = Ws[s];
+        double Mp[6];  // packed (00, 01, 02, 11, 12, 22)
+#pragma unroll
+        for (int sym = 0; sym < 6; ++sym) {
+          const int i = sym < 3 ? 0 : (sym < 5 ? 1 : 2), j = sym < 3 ? sym : (sym < 5 ? sym - 2 : 2);
+          const int ij = i * 3 + j, ji = j * 3 + i;
+          Mp[sym] = is_i ? 0.25 * ob.alpha3 * w *
+                               (0.5 * (ob.c00[ij] + ob.c00[ji]) + red(9 + ij) + red(9 + ji) + red(27 + ij) + red(27 + ji))
+                         : fma(-0.25 * ob.alpha3, red(ij) + red(ji), 0.5 * (ob.N0[ij] + ob.N0[ji]));
+        }
+        double* e = Eout + ((size_t)task.obj * n_w + task.w0 + s) * 6 + 3 * is_i;
+        sym3_eig(Mp[0], Mp[3], Mp[5], Mp[1], Mp[2], Mp[4], e[0], e[1], e[2]);
+      }
+    }
     // the next iteration's first barrier orders these reads before the buffers are reused
   }
 }
@@ -384,34 +411,36 @@ cudaError_t launch_sweep_fp64_implicit(int cfg, const RomDev* objs, const SweepT
                              (int)smem_bytes);
     if (e != cudaSuccess) return e;
     sweep_fp64_kernel<256, 2, true><<<grid, 256, smem_bytes, stream>>>(
-        objs, table, n_tasks, counter, omega, omega_stride, nullptr, R, I, Delta, status, n_w, workspace, ws_elems);
+        objs, table, n_tasks, counter, omega, omega_stride, nullptr, R, I, Delta, nullptr, status, n_w, workspace,
+        ws_elems);
   } else {
     e = cudaFuncSetAttribute(sweep_fp64_kernel<128, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes);
     if (e != cudaSuccess) return e;
     sweep_fp64_kernel<128, 4, true><<<grid, 128, smem_bytes, stream>>>(
-        objs, table, n_tasks, counter, omega, omega_stride, nullptr, R, I, Delta, status, n_w, workspace, ws_elems);
+        objs, table, n_tasks, counter, omega, omega_stride, nullptr, R, I, Delta, nullptr, status, n_w, workspace,
+        ws_elems);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_sweep_fp64_routed(int cfg, const RomDev* objs, const SweepTask* table, int* counter,
                                      const double* omega, int omega_stride, const double* s_sigma, double* R,
-                                     double* I, double* Delta, int* status, int n_w, int grid, size_t smem_bytes,
-                                     double2* workspace, size_t ws_elems, cudaStream_t stream) {
+                                     double* I, double* Delta, double* eig, int* status, int n_w, int grid,
+                                     size_t smem_bytes, double2* workspace, size_t ws_elems, cudaStream_t stream) {
   cudaError_t e;
   if (cfg == 0) {
     e = cudaFuncSetAttribute(sweep_fp64_kernel<256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes);
     if (e != cudaSuccess) return e;
     sweep_fp64_kernel<256, 2, true><<<grid, 256, smem_bytes, stream>>>(
-        objs, table, -1, counter, omega, omega_stride, s_sigma, R, I, Delta, status, n_w, workspace, ws_elems);
+        objs, table, -1, counter, omega, omega_stride, s_sigma, R, I, Delta, eig, status, n_w, workspace, ws_elems);
   } else {
     e = cudaFuncSetAttribute(sweep_fp64_kernel<128, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes);
     if (e != cudaSuccess) return e;
     sweep_fp64_kernel<128, 4, true><<<grid, 128, smem_bytes, stream>>>(
-        objs, table, -1, counter, omega, omega_stride, s_sigma, R, I, Delta, status, n_w, workspace, ws_elems);
+        objs, table, -1, counter, omega, omega_stride, s_sigma, R, I, Delta, eig, status, n_w, workspace, ws_elems);
   }
   return cudaGetLastError();
 }
@@ -437,15 +466,15 @@ cudaError_t sweep_fp64_configure(int cfg, size_t smem_bytes) {
 
 cudaError_t launch_sweep_fp64(int cfg, const RomDev* objs, const SweepTask* tasks, int n_tasks, int* counter,
                               const double* omega, int omega_stride, const double* s_sigma,
-                              double* R, double* I, double* Delta, int* status, int n_w, int grid,
+                              double* R, double* I, double* Delta, double* eig, int* status, int n_w, int grid,
                               size_t smem_bytes, double2* workspace, size_t ws_elems, cudaStream_t stream) {
   if (cfg == 0)
     sweep_fp64_kernel<256, 2><<<grid, 256, smem_bytes, stream>>>(objs, tasks, n_tasks, counter, omega,
-                                                                omega_stride, s_sigma, R, I, Delta, status,
+                                                                omega_stride, s_sigma, R, I, Delta, eig, status,
                                                                 n_w, workspace, ws_elems);
   else
     sweep_fp64_kernel<128, 4><<<grid, 128, smem_bytes, stream>>>(objs, tasks, n_tasks, counter, omega,
-                                                                omega_stride, s_sigma, R, I, Delta, status,
+                                                                omega_stride, s_sigma, R, I, Delta, eig, status,
                                                                 n_w, workspace, ws_elems);
   return cudaGetLastError();
 }

@@ -68,3 +68,44 @@ def test_invariants_of_degenerate_and_random_matrices(mrom):
                          torch.empty((0, 3), dtype=torch.float64, device="cuda"))
     with pytest.raises(mrom.MromError):
         mrom._abi.check(mrom.lib().mrom_invariants(h.ptr, None, -1, None), h.ptr)
+
+
+@pytest.mark.parametrize("lu", [False, True], ids=["pencil", "lu"])
+def test_invariants_fused_into_the_sweep(mrom, lu):
+    """mrom_plan_sweep_invariants: the eigenvalues of R~ and I computed in the sweep kernels'
+    epilogue equal those of the R and I outputs (oracle.invariants on the same values) at 1e-13
+    of the matrix scale, on both routes, with an object that carries N0 and Me; with R and I
+    omitted the same invariants are written."""
+    import torch
+    from oracle import invariants
+    from workloads import log_omegas, reduced_object
+    h = mrom.Handle(0)
+    h.set_solver(lu=lu)
+    objs = [reduced_object(13, k, r) for k, r in enumerate([6, 33, 90])]
+    roms = [mrom.ReducedObject.from_workload(h, o) for o in objs]
+    o = reduced_object(14, 0, 20)
+    rng = np.random.default_rng(4)
+    Z = (rng.standard_normal((20, 20)) + 1j * rng.standard_normal((20, 20))) * 1e-3
+    N0 = np.array([[0.3, 0.01, 0.0], [0.01, 0.3, 0.02], [0.0, 0.02, 0.25]])
+    roms.append(mrom.ReducedObject(h, 20, o.K, o.C, o.B, o.c00, G=o.G, Me=Z @ Z.conj().T, N0=N0))
+    n_w = 257
+    wo = log_omegas(1e1, 1e8, n_w)
+    om = torch.as_tensor(wo, device="cuda")
+    plan = mrom.Plan(h, roms, n_w)
+    R = torch.empty((len(roms), n_w, 3, 3), dtype=torch.float64, device="cuda")
+    I = torch.empty_like(R)
+    E = torch.full((len(roms), n_w, 6), float("nan"), dtype=torch.float64, device="cuda")
+    plan.sweep(om, R, I, eig=E)
+    h.synchronize()
+    if not lu:
+        assert plan.solver_counts()[0] > 0
+    got = E.cpu().numpy()
+    for k, M in enumerate((R.cpu().numpy(), I.cpu().numpy())):
+        ref = invariants.mpt_invariants(M)
+        scale = np.maximum(np.abs(ref).max(axis=-1, keepdims=True), 1e-300)
+        assert np.all(np.abs(got[..., 3 * k:3 * k + 3] - ref) <= 1e-13 * scale), k
+    E2 = torch.full_like(E, float("nan"))
+    plan.sweep(om, None, None, eig=E2)
+    h.synchronize()
+    assert np.array_equal(E2.cpu().numpy(), got)
+    plan.close()
