@@ -71,15 +71,12 @@ struct PencilDev {
 };
 
 // Per-object scratch of the pencil preparation: W = L^-H Q1 D (r x r), the tridiagonal's
-// off-diagonal e (r), and the QL rotation log (sweeps {m, rotations}, rotations (c, s)).
+// off-diagonal e (r), and the tridiagonal eigen-decomposition's workspace (3 r x r float64
+// blocks; the first holds the eigenvectors Z2 afterwards).
 struct PencilScratch {
   double2* W;
   double* e;
-  double2* rot;
-  int2* sweeps;
-  int* nsw;
-  int cap_rot;
-  int cap_sw;
+  double* work;
 };
 
 // One unit of work: S consecutive frequencies of one object.

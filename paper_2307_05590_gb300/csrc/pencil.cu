@@ -4,7 +4,7 @@
 // Hermitian positive semi-definite and C Hermitian positive definite, is diagonalised once
 // per object by the generalised eigenproblem K' V = C V Lambda, V^H C V = I:
 //   C = L L^H (Cholesky), H = L^-1 K' L^-H = Z Lambda Z^H (Householder tridiagonalisation,
-//   then implicit QL on the real symmetric tridiagonal matrix), V = L^-H Z.
+//   then divide and conquer on the real symmetric tridiagonal matrix), V = L^-H Z.
 // Then for every frequency, with z_i = V^-1 p_i,
 //   z_ki = i omega beta_ki / (lambda_k - i omega),  beta = V^H B,
 // and the quadratic forms of Eq. (18), Eq. (19) and of the certificate (Lemma 4.2) become
@@ -17,11 +17,12 @@
 // error of the pencil route is about eps ||H|| / omega (the eigen-decomposition is backward
 // stable in H, and |lambda - i omega| >= omega), which the preparation kernel estimates per
 // object from ||H||_F and the smallest frequency of the sweep.  Objects whose estimate
-// exceeds the gate, whose C is not numerically positive definite, or whose QL iteration
-// does not converge are routed to the LU kernel instead (device-side routing, no host sync).
+// exceeds the gate, whose C is not numerically positive definite, or whose tridiagonal
+// eigen-decomposition meets a non-finite value are routed to the LU kernel instead (device-side routing, no host sync).
 #include "mrom_internal.h"
 #include "eig3.cuh"
 #include "herm_tridiag.cuh"
+#include "tridiag_dc.cuh"
 
 #include <algorithm>
 #include <cfloat>
@@ -34,8 +35,6 @@ namespace {
 
 constexpr int kPT = 256;        // threads per CTA in the preparation and sweep kernels
 constexpr int kPW = kPT / 32;   // warps per CTA
-constexpr int kQlMaxIter = 60;  // QL iterations per eigenvalue before giving up
-constexpr int kQlLanes = 1;     // objects per warp in the QL kernel (MROM_QL_LANES overrides)
 
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 cmac(double2 c, double2 a, double2 b) {  // c + a b
@@ -71,8 +70,8 @@ __device__ double block_min(double v, double* red) {
 
 // ------------------------------------------------------------------ preparation
 //
-// Three kernels per sweep: tridiagonalisation (one CTA per object), implicit QL (one lane
-// per object) and finishing (one CTA per object).
+// Three kernels per sweep: tridiagonalisation, the tridiagonal eigenproblem (divide and
+// conquer) and finishing, each with one CTA per object.
 //
 // Tridiagonalisation: persistent CTAs, objects in descending r.  Three r x r complex
 // matrices in the CTA's slice of a global workspace (L2-resident): W0, W1, W2.
@@ -80,7 +79,7 @@ __device__ double block_min(double v, double* red) {
 //   W1: K' -> H (full Hermitian) -> Householder vectors below the subdiagonal
 //   W2: L^-1 (lower)
 // Output per object: the real tridiagonal D^H Q1^H H Q1 D (diagonal in lam, off-diagonal
-// in the scratch e) and W = L^-H Z; V = W Q2 once QL has diagonalised the tridiagonal.
+// in the scratch e) and W = L^-H Z; V = W Q2 once the tridiagonal is diagonalised (Q2 = Z2).
 __global__ void __launch_bounds__(kPT, 2)
 pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__ pens,
                       const PencilScratch* __restrict__ scr, const int* __restrict__ order, int n_elig,
@@ -235,7 +234,7 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
       hq::herm_tridiag<kPT>(W1, r, W0, sd, se, stau, salpha, sph, W0, red);
 
       // ---- 8. W = L^-H Z (per-object buffer): W[i][j] = sum_{k >= i} conj(Linv[k][i]) Z[k][j];
-      // the real tridiagonal (sd, se) goes to the QL kernel, W to the finishing kernel
+      // the real tridiagonal (sd, se) goes to the eigenproblem kernel, W to the finishing kernel
       for (int i = warp; i < r; i += kPW) {  // one warp per row i, lanes along j
         for (int j = lane; j < r; j += 32) {
           double2 acc = make_double2(0.0, 0.0);
@@ -253,105 +252,48 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
   }
 }
 
-// ------------------------------------------------------------------ implicit QL
+// ------------------------------------------------------------------ tridiagonal eigenproblem
 //
-// One lane per object (objects of a warp have similar r): implicit QL with Wilkinson-type
-// shifts on the real symmetric tridiagonal (d, e), e[i] coupling i and i+1.  Each chase is
-// recorded as a sweep {m, rotations} with the rotations (c, s) on columns (i, i+1),
-// i = m-1, m-2, ...; the finishing kernel applies them.  d becomes the eigenvalues.  A log
-// that would overflow its capacity, or an eigenvalue that needs more than kQlMaxIter
-// chases, clears the object's pencil flag (it then takes the LU route).
-__global__ void __launch_bounds__(32)
-pencil_ql_kernel(const int* __restrict__ order, int n_elig, const RomDev* __restrict__ objs,
+// One CTA per object (atomic work counter): the real symmetric tridiagonal (d, e) left by the
+// tridiagonalisation kernel is diagonalised by divide and conquer (tridiag_dc.cuh), which keeps
+// every thread busy (independent secular roots, a GEMM per merge) where the implicit QL method is
+// one chain of dependent rotations.  d becomes the eigenvalues; the orthonormal eigenvectors Z2
+// (r x r, row-major) are left at the start of the object's workspace (ps.work: three r x r
+// float64 blocks).  A non-finite value
+// clears the object's pencil flag (it then takes the LU route).
+__global__ void __launch_bounds__(kPT)
+pencil_dc_kernel(const int* __restrict__ order, int n_elig, const RomDev* __restrict__ objs,
                  const PencilDev* __restrict__ pens, const PencilScratch* __restrict__ scr,
-                 int* __restrict__ pen_ok, int lpw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sdd = reinterpret_cast<double*>(smem_raw);  // d[k][lane], then e[k][lane]
-  double* see = sdd + MROM_MAX_R * lpw;
-  const int lane = threadIdx.x;
-  const int t = blockIdx.x * lpw + lane;
-  if (lane >= lpw || t >= n_elig) return;
-  const int o = order[t];
-  if (!pen_ok[o]) return;
-  const int r = objs[o].r;
-  const PencilDev pd = pens[o];
-  const PencilScratch ps = scr[o];
-  double* d = sdd + lane;  // d[k * lpw]
-  double* e = see + lane;
-  for (int k = 0; k < r; ++k) {
-    d[k * lpw] = pd.lam[k];
-    e[k * lpw] = ps.e[k];
+                 int* __restrict__ pen_ok, int* __restrict__ counter) {
+  __shared__ dc::DcShared S;
+  __shared__ int s_task;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();
+    if (t >= n_elig) break;
+    const int o = order[t];
+    if (!pen_ok[o]) continue;  // uniform across the CTA
+    const int r = objs[o].r, rr = r * r;
+    const PencilDev& pd = pens[o];
+    const PencilScratch& ps = scr[o];
+    double* A = ps.work;
+    double* Z = dc::tridiag_dc<kPT>(pd.lam, ps.e, r, A, A + rr, A + 2 * rr, S);
+    const bool bad = S.bad != 0;
+    for (int k = tid; k < r; k += kPT) pd.lam[k] = S.lam[k];
+    if (Z != A)
+      for (int idx = tid; idx < rr; idx += kPT) A[idx] = Z[idx];
+    if (bad && tid == 0) pen_ok[o] = 0;
+    __syncthreads();
   }
-  double tn = 0.0;  // max_i |d_i| + |e_i|
-  for (int k = 0; k < r; ++k) tn = fmax(tn, fabs(d[k * lpw]) + fabs(e[k * lpw]));
-  int nsw = 0, nrot_total = 0;
-  bool fail = false;
-  for (int l = 0; l < r && !fail; ++l) {
-    int iter = 0;
-    for (;;) {
-      int m = l;
-      while (m < r - 1 && !hq::ql_split(e[m * lpw], d[m * lpw], d[(m + 1) * lpw], tn)) ++m;
-      if (m == l) break;
-      if (++iter > kQlMaxIter || nsw >= ps.cap_sw || nrot_total + (m - l) > ps.cap_rot) {
-        fail = true;
-        break;
-      }
-      double g = (d[(l + 1) * lpw] - d[l * lpw]) / (2.0 * e[l * lpw]);
-      double h = fabs(g) < 1e150 ? sqrt(fma(g, g, 1.0)) : fabs(g);
-      g = d[m * lpw] - d[l * lpw] + e[l * lpw] / (g + (g >= 0.0 ? h : -h));
-      double sn = 1.0, cs = 1.0, p = 0.0;
-      int nrot = 0;
-      bool underflow = false;
-      double2* rot = ps.rot + nrot_total;
-      for (int i = m - 1; i >= l; --i) {
-        const double ei = e[i * lpw];
-        const double f = sn * ei, b = cs * ei;
-        const double h2 = fma(f, f, g * g);
-        if (h2 > 1e-280 && h2 < 1e280) {
-          const double rh = rsqrt(h2);
-          h = h2 * rh;
-          sn = f * rh;
-          cs = g * rh;
-        } else {
-          h = hypot(f, g);
-          if (h == 0.0) {
-            e[(i + 1) * lpw] = 0.0;
-            d[(i + 1) * lpw] -= p;
-            e[m * lpw] = 0.0;
-            underflow = true;
-            break;
-          }
-          sn = f / h;
-          cs = g / h;
-        }
-        e[(i + 1) * lpw] = h;
-        g = d[(i + 1) * lpw] - p;
-        h = fma(d[i * lpw] - g, sn, 2.0 * cs * b);
-        p = sn * h;
-        d[(i + 1) * lpw] = g + p;
-        g = fma(cs, h, -b);
-        rot[nrot++] = make_double2(cs, sn);
-      }
-      if (!underflow) {
-        d[l * lpw] -= p;
-        e[l * lpw] = g;
-        e[m * lpw] = 0.0;
-      }
-      if (nrot > 0) {
-        ps.sweeps[nsw++] = make_int2(m, nrot);
-        nrot_total += nrot;
-      }
-    }
-  }
-  for (int k = 0; k < r; ++k) pd.lam[k] = d[k * lpw];
-  *ps.nsw = nsw;
-  if (fail) pen_ok[o] = 0;
 }
 
 // ------------------------------------------------------------------ finishing
 //
-// One CTA per object.  Q2 (real r x r, shared memory, odd row stride) = the product of the
-// logged rotations, one row per thread (rows are independent); V = W Q2 (the generalised
+// One CTA per object.  Q2 (real r x r, shared memory, odd row stride) = the tridiagonal's
+// eigenvectors Z2 from the divide-and-conquer kernel; V = W Q2 (the generalised
 // eigenvectors, V^H C V = I); then beta = V^H B, gs V and the transformed Gram blocks.
 // Workspace per CTA: V and Y (r x r complex each).
 __global__ void __launch_bounds__(kPT, 1)
@@ -378,30 +320,12 @@ pencil_finish_kernel(const RomDev* __restrict__ objs, const PencilDev* __restric
     const int r = ob.r, rr = r * r;
     const int ldq = r | 1;
     double2* W0 = W1 + rr;
-    for (int idx = tid; idx < r * ldq; idx += kPT) {
-      const int i = idx / ldq, j = idx - (idx / ldq) * ldq;
-      Q2[idx] = i == j ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    // rotation q of a sweep acts on columns (i, i+1), i = m-1-q:
-    //   Q[:, i+1] <- s Q[:, i] + c Q[:, i+1],  Q[:, i] <- c Q[:, i] - s Q[:, i+1]
-    const int nsw = *ps.nsw;
-    for (int row = tid; row < r; row += kPT) {
-      double* q = Q2 + (size_t)row * ldq;
-      const double2* rot = ps.rot;
-      for (int k = 0; k < nsw; ++k) {
-        const int2 sw = ps.sweeps[k];
-        const int m = sw.x, nrot = sw.y;
-        double hi = q[m];
-        for (int u = 0; u < nrot; ++u) {
-          const int i = m - 1 - u;
-          const double2 cs = rot[u];
-          const double lo = q[i];
-          q[i + 1] = fma(cs.y, lo, cs.x * hi);
-          hi = fma(cs.x, lo, -cs.y * hi);
-        }
-        q[m - nrot] = hi;
-        rot += nrot;
+    // the tridiagonal's eigenvectors from the divide-and-conquer kernel (odd row stride)
+    {
+      const double* Z2 = ps.work;
+      for (int idx = tid; idx < rr; idx += kPT) {
+        const int i = idx / r, j = idx - (idx / r) * r;
+        Q2[i * ldq + j] = Z2[idx];
       }
     }
     __syncthreads();
@@ -1086,19 +1010,8 @@ cudaError_t launch_pencil_prep(const RomDev* objs, const PencilDev* pens, const 
                                                   s_sigma, s_mu, pen_ok, ws, ws_elems, gate, kappa_max);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // objects per warp (lanes in use): one object per warp spreads the chases over all SMs
-  // (masked lanes shorten the FP64 issue time of a warp instruction)
-  int lpw = kQlLanes;
-  if (const char* v = std::getenv("MROM_QL_LANES")) lpw = std::max(1, std::min(32, std::atoi(v)));
-  // at most one QL warp per SM sub-partition: a chase is a chain of dependent FP64
-  // operations, and two chases on one sub-partition slow each other down
-  int dev = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  const size_t ql_smem = std::max<size_t>(2 * (size_t)MROM_MAX_R * lpw * sizeof(double), (size_t)per_sm / 4 - 2048);
-  e = cudaFuncSetAttribute(pencil_ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ql_smem);
-  if (e != cudaSuccess) return e;
-  pencil_ql_kernel<<<(n_elig + lpw - 1) / lpw, 32, ql_smem, stream>>>(order, n_elig, objs, pens, scr, pen_ok, lpw);
+  // the tridiagonal eigenproblems, one CTA per object (work counter: counters[6])
+  pencil_dc_kernel<<<grid, kPT, 0, stream>>>(order, n_elig, objs, pens, scr, pen_ok, counters + 6);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = pencil_finish_smem_bytes(rmax);
@@ -1153,10 +1066,8 @@ namespace {
 // kPencilKappaMax; other objects take the LU route.
 constexpr double kPencilGate = 1e-11;
 constexpr double kPencilKappaMax = 1e6;
-// QL rotation log per object (complex slots): rotations and sweep records (QL takes about r^2
-// rotations in 2 r sweeps)
-constexpr size_t rot_cap(int r) { return 3 * (size_t)r * r + 64; }
-constexpr size_t sweep_cap(int r) { return 16 * (size_t)r + 16; }
+// workspace of the tridiagonal eigen-decomposition per object (complex slots): 3 r x r float64
+constexpr size_t dc_work(int r) { return (3 * (size_t)r * r + 1) / 2; }
 
 }  // namespace
 
@@ -1198,7 +1109,7 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
     if (objs[o].Me) data_elems += tri;                                    // Eh
     if (kin && objs[o].Kin) data_elems += tri;                            // Fh
     if (objs[o].dB) data_elems += 3 * (size_t)r;                          // dbeta
-    data_elems += (size_t)r * r + (size_t)(r + 1) / 2 + rot_cap(r) + (sweep_cap(r) + 1) / 2;  // scratch
+    data_elems += (size_t)r * r + (size_t)(r + 1) / 2 + dc_work(r);  // scratch
   }
   t->prep_grid = std::min<int>((int)elig.size(), 2 * h->num_sms);
   t->prep_ws_elems = 3 * (size_t)rmax * rmax;
@@ -1207,21 +1118,20 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
   t->pen_smem_vjp = smem_vjp;
   t->rmax = rmax;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t b_scr = al(n_obj * sizeof(PencilScratch)), b_nsw = al(elig.size() * sizeof(int));
+  const size_t b_scr = al(n_obj * sizeof(PencilScratch));
   const size_t b_pens = al(n_obj * sizeof(PencilDev)), b_op = al(elig.size() * sizeof(int)),
                b_sp = al(elig.size() * sizeof(int)), b_ol = al(n_obj * sizeof(int)),
                b_li = al(n_obj * sizeof(int2)), b_tab = al((n_obj + 1) * sizeof(SweepTask)),
                b_ok = al(n_obj * sizeof(int)), b_cnt = al(8 * sizeof(int)),
                b_data = al(data_elems * sizeof(double2)),
                b_ws = al(t->prep_ws_elems * t->prep_grid * sizeof(double2));
-  const size_t total = b_scr + b_nsw + b_pens + b_op + b_sp + b_ol + b_li + 2 * b_tab + b_ok + b_cnt + b_data + b_ws;
+  const size_t total = b_scr + b_pens + b_op + b_sp + b_ol + b_li + 2 * b_tab + b_ok + b_cnt + b_data + b_ws;
   void* blk = nullptr;
   cudaError_t e = cudaMallocAsync(&blk, total, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "pencil route: allocation");
   t->block = blk;
   char* p = static_cast<char*>(blk);
   t->d_scr = reinterpret_cast<PencilScratch*>(p); p += b_scr;
-  int* d_nsw = reinterpret_cast<int*>(p); p += b_nsw;
   t->d_pens = reinterpret_cast<PencilDev*>(p); p += b_pens;
   t->d_order_pen = reinterpret_cast<int*>(p); p += b_op;
   t->d_spen = reinterpret_cast<int*>(p); p += b_sp;
@@ -1258,11 +1168,7 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
     }
     scr[o].W = q; q += (size_t)r * r;
     scr[o].e = reinterpret_cast<double*>(q); q += (r + 1) / 2;
-    scr[o].rot = q; q += rot_cap(r);
-    scr[o].sweeps = reinterpret_cast<int2*>(q);
-    scr[o].cap_rot = (int)rot_cap(r);
-    scr[o].cap_sw = (int)sweep_cap(r);
-    scr[o].nsw = d_nsw + k;
+    scr[o].work = reinterpret_cast<double*>(q); q += dc_work(r);
   }
   t->n_pen = (int)elig.size();
   cudaStream_t st = h->stream;
@@ -1288,7 +1194,7 @@ void pencil_tables_destroy(PencilTables* t, cudaStream_t stream) {
 
 cudaError_t pencil_tables_prepare(mrom_ctx* h, const PencilTables& t, const RomDev* objs, const double* omega,
                                   int omega_stride, const double* s_sigma, const double* s_mu) {
-  cudaError_t e = cudaMemsetAsync(t.d_counters, 0, 4 * sizeof(int), h->stream);
+  cudaError_t e = cudaMemsetAsync(t.d_counters, 0, 8 * sizeof(int), h->stream);
   if (e == cudaSuccess)
     e = launch_pencil_prep(objs, t.d_pens, t.d_scr, t.d_order_pen, t.n_pen, t.d_counters, omega, omega_stride, t.n_w,
                            s_sigma, s_mu, t.d_pen_ok, t.d_prep_ws, t.prep_ws_elems, t.prep_grid, t.rmax, kPencilGate,
