@@ -35,6 +35,7 @@ import sys
 import time
 
 import numpy as np
+import scipy.linalg as sla
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -44,9 +45,9 @@ UNIT = "evals/s"
 SM_COUNT_NOMINAL = 152
 DFMA_PER_CLK_PER_SM = 2           # GB300 DFMA rate: 4 flop/clk/SM (mrom_fp64_peak measures it in every run)
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one pencil_sweep_kernel launch on
-# this workload, from a --set full ncu capture of the current kernel (97,853,696 + 373,272,320 bytes);
-# None once the kernel changes until it is captured again
-SWEEP_DRAM_BYTES_PER_LAUNCH = 97_853_696 + 373_272_320
+# this workload, from an ncu capture of the current kernel; None once the kernel changes until it
+# is captured again
+SWEEP_DRAM_BYTES_PER_LAUNCH = None
 
 
 def flops_per_eval(r: int, cert: bool = True) -> float:
@@ -71,21 +72,22 @@ def flops_per_eval(r: int, cert: bool = True) -> float:
     return float(elim + back + form + forms + red)
 
 
-def pencil_sweep_flops(r: int, cert: bool = True) -> float:
-    """FP64 flops of one (object, frequency) evaluation in the pencil sweep kernel.
+def pencil_sweep_flops(r: int, m_sum: int, n_w: int, cert: bool = True) -> float:
+    """FP64 flops of one object's pencil sweep over n_w frequencies (pole-split forms), with
+    m_sum = sum over the frequencies of m = #{lambda_k < w}:
 
-      z_kj = u_k beta_kj, u_k = i w / (lambda_k - i w)         26 per k
-      R and I: (-lambda Re u, Re u) x Re(beta_i^* beta_j)      25 per k
-      certificate source terms X_ij and form sums U_ij          90 per row
-      certificate form: G~_ab(w) (4 FMA) and three complex
-        multiply-adds for every b < a                          32 per pair
-      diagonal b = a (stored halved)                           32 per row
-      outputs R, I, Delta                                      225
+      a_k = 1 / (lambda_k + i w), u_k (one division)            12 per k
+      R and I: (-lambda Re u, Re u) x Re(beta_i^* beta_j)       24 per k
+      a_k conj(beta_ki)                                         18 per k
+      certificate polynomial Y_kj(w): full suffix (k >= m)      30 per k
+        or Horner over five tables (k < m)                      48 per k
+      Re(a_k conj(beta_ki) Y_kj), nine (i, j)                    36 per k
+      outputs R, I, Delta with the leading-block sums C0(m)     306 per frequency
     """
     r = int(r)
     if not cert:
-        return float(51 * r + 100)
-    return float(16 * r * (r - 1) + 51 * r + 90 * r + 32 * r + 225)
+        return float(n_w * (36 * r + 100))
+    return float(n_w * (117 * r + 306) + 18 * m_sum)
 
 
 def pencil_prep_flops(r: int) -> float:
@@ -704,7 +706,9 @@ def main():
     wo = log_omegas(1e1, 1e8, args.n_w)
     rs = np.array([o.r for o in objs])
     flops_lu = float(sum(flops_per_eval(r) for r in rs)) * args.n_w
-    flops_pen = float(sum(pencil_sweep_flops(r) for r in rs)) * args.n_w
+    # m = #{lambda_k < omega} per object and frequency (host eigenvalues of the pencil (K, C))
+    m_sums = [int(np.searchsorted(np.sort(sla.eigh(o.K, o.C, eigvals_only=True)), wo).sum()) for o in objs]
+    flops_pen = float(sum(pencil_sweep_flops(r, ms, args.n_w) for r, ms in zip(rs, m_sums)))
     flops_prep = float(sum(pencil_prep_flops(r) for r in rs))
 
     stream = torch.cuda.Stream(dev)

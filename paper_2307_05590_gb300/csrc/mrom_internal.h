@@ -51,12 +51,12 @@ struct RomDev {
 };
 
 // Per-object data of the pencil route (pencil.cu), computed on the device by the
-// preparation kernel of every sweep: eigenvalues lam (r), beta = V^H B (r x 3),
+// preparation kernel of every sweep: eigenvalues lam (r, ascending), beta = V^H B (r x 3),
 // gsh[k][q] = (gs_q V)[k] for the certificate rows of G (r x 6, or null), the transformed
 // Gram blocks V^H G_X V for X = KK, CC, S interleaved per entry of the packed lower
 // triangle with the diagonal halved (3 r (r+1)/2, or null) and V^H Me V (packed lower, or
-// null).  F: frequency
-// groups of 32 per sweep task.
+// null), and for the sweep the pole-split tables of those Hermitian forms (pt, tb0, c0; null
+// in adjoint tables; layout in pencil.cu).  F: frequency groups of 32 per sweep task.
 struct PencilDev {
   double* lam;
   double2* beta;
@@ -66,6 +66,9 @@ struct PencilDev {
   double2* Eh;
   double2* Fh;  // V^H K_in V (packed lower, or null): the permeability gradient
   double2* dbeta;  // r x 3: V^H dB/ds_mu (or null)
+  double2* pt;     // r (r+1)/2 entries x 21: per (m, k < m) the prefix/suffix polynomial tables
+  double2* tb0;    // r x 12: per k the full suffix sums (KK, CC, iS, E) x 3
+  double* c0;      // (r+1) x 24: per m the leading-block sums Re sum_{k,l<m} (KK, CC, iS, E) x 6
   int F;
   int pad;
 };
@@ -269,15 +272,15 @@ cudaError_t launch_sweep_fp64_routed(int cfg, const RomDev* objs, const SweepTas
                                      size_t smem_bytes, double2* workspace, size_t ws_elems, cudaStream_t stream);
 
 // Pencil route (pencil.cu).
-size_t pencil_sweep_smem_bytes(int r, int F);
-// Tables for objs (host records; the device copy is passed to the kernels).  gram: transform
-// the certificate blocks of objects that have them; kin: transform K_in (permeability
-// gradient).  order_lu / lu_info: every object in the LU kernel's cost order with its task
+size_t pencil_sweep_smem_bytes();
+// Tables for objs (host records; the device copy is passed to the kernels).  gram: tables of
+// the forward sweep (certificate blocks of objects that have them, pole-split tables); kin:
+// tables of the adjoint sweep with K_in transformed (permeability gradient).  order_lu / lu_info: every object in the LU kernel's cost order with its task
 // shape {S, matrices-in-global}.  No eligible object: t->n_pen = 0 and nothing allocated.
 mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, int n_w, bool gram, bool kin,
                                  const std::vector<int>& order_lu, const std::vector<int2>& lu_info, PencilTables* t);
 void pencil_tables_destroy(PencilTables* t, cudaStream_t stream);
-// Preparation (tridiagonalisation, QL, finishing) for one sweep; s_mu scales K_in as
+// Preparation (tridiagonalisation, divide and conquer, finishing) for one sweep; s_mu scales K_in as
 // K + (1/s_mu - 1) K_in (NULL: no scale).  Resets the counters.  Then the routing kernel
 // (pencil_tables_route) fills the pencil and LU task tables.
 cudaError_t pencil_tables_prepare(mrom_ctx* h, const PencilTables& t, const RomDev* objs, const double* omega,

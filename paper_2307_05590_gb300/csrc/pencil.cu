@@ -68,6 +68,29 @@ __device__ double block_min(double v, double* red) {
   return s;
 }
 
+__device__ __forceinline__ double2 herm_packed(const double2* __restrict__ M, int a, int b) {  // M[a][b]
+  if (b <= a) return M[(size_t)a * (a + 1) / 2 + b];
+  const double2 v = M[(size_t)b * (b + 1) / 2 + a];
+  return make_double2(v.x, -v.y);
+}
+
+// Entry (a, b) of the certificate's Hermitian block x in eigen-coordinates, from the
+// interleaved packed lower triangles with the diagonal halved: x = 0 (KK), 1 (CC), 2 (i S, S
+// skew-Hermitian, so that G~(w) = KK + w^2 CC + w (i S)).
+__device__ __forceinline__ double2 gram_herm(const double2* __restrict__ Gh, int x, int a, int b) {
+  double2 v;
+  if (a == b) {
+    v = Gh[((size_t)a * (a + 1) / 2 + a) * 3 + x];
+    v = make_double2(2.0 * v.x, 2.0 * v.y);
+  } else if (b < a) {
+    v = Gh[((size_t)a * (a + 1) / 2 + b) * 3 + x];
+  } else {
+    v = Gh[((size_t)b * (b + 1) / 2 + a) * 3 + x];
+    v = x == 2 ? make_double2(-v.x, v.y) : make_double2(v.x, -v.y);  // -conj (skew) or conj
+  }
+  return x == 2 ? make_double2(-v.y, v.x) : v;
+}
+
 // ------------------------------------------------------------------ preparation
 //
 // Three kernels per sweep: tridiagonalisation, the tridiagonal eigenproblem (divide and
@@ -290,19 +313,153 @@ pencil_dc_kernel(const int* __restrict__ order, int n_elig, const RomDev* __rest
   }
 }
 
+// ------------------------------------------------------------------ pole-split tables
+//
+// The sweep's Hermitian forms z_i^H M z_j (M = V^H Me V, and the certificate's
+// G~(w) = KK + w^2 CC + w (i S)) in O(r) per frequency.  With eigenvalues ascending,
+// a_k = 1 / (lambda_k + i w) and z_kj = u_k beta_kj, u_k = i w / (lambda_k - i w) = i w conj(a_k),
+// every pair (k, l) has conj(u_k) u_l = w^2 a_k conj(a_l), split in partial fractions as
+//   w^2 (a_k + conj(a_l)) / (lambda_k + lambda_l)                 if max(lambda_k, lambda_l) >= w,
+//   1 - (a_k lambda_k^2 + conj(a_l) lambda_l^2) / (lambda_k + lambda_l)   if both are below w
+// (the second from u = -1 + lambda conj(a)).  Neither cancels more than the direct sum: every
+// term is bounded by |u_k| |u_l| up to a factor two.  Gathering the a_k terms per k (the conj(a_l)
+// terms are their conjugate transposes, M being Hermitian), with m = #{lambda_k < w}:
+//   z_i^H M z_j = C0_ij(m) + X_ij + conj(X_ji),   X_ij = sum_k a_k conj(beta_ki) Y_kj,
+//   Y_kj = -TA_kj(m) + w^2 TB_kj(m) for k < m,    Y_kj = w^2 TB_kj(0) for k >= m,
+//   TA_kj(m) = sum_{l<m} M_kl beta_lj lambda_k^2 / (lambda_k + lambda_l),
+//   TB_kj(m) = sum_{l>=m} M_kl beta_lj / (lambda_k + lambda_l),
+//   C0_ij(m) = sum_{k,l<m} conj(beta_ki) M_kl beta_lj.
+// (The coefficients a table entry never uses are set to zero where lambda_k + lambda_l = 0.)
+// For G~(w) the three blocks fold into one polynomial in w per entry,
+//   Y = P0 + w P1 + w^2 P2 + w^3 P3 + w^4 P4,
+//   P0 = -TA_KK, P1 = -TA_iS, P2 = TB_KK - TA_CC - conj(gsK_jk), P3 = TB_iS - i conj(gsC_jk),
+//   P4 = TB_CC,
+// where the gs terms carry the certificate's source rows: with c_jk = i w gsK_jk + w^2 gsC_jk,
+//   Re sum_k c_jk z_ki = Re sum_k a_k conj(beta_ki) (-i w conj(c_jk))   (u_k = i w conj(a_k)),
+// so that sum_k a_k conj(beta_ki) Y_kj = (form)_ij + (source term)_ji, and only the symmetric
+// sums of both enter the certificate.  The full-suffix entries fold them alike.
+// Layout: pt[(m (m - 1) / 2 + k) * 21 + 3 p + j] for 1 <= m <= r, k < m, with p = 0..4 the
+// polynomial, 5: -TA_E, 6: TB_E; tb0[k * 12 + 3 x + j] = TB_kj(0) of block x = KK, CC, iS, E
+// (KK and iS with the gs terms);
+// c0[m * 24 + 6 x + q] = Re C0(m) of block x at the packed symmetric index q (00 01 02 11 12 22).
+// Blocks the object does not have are zero.
+constexpr int kPtEntry = 21;
+
+__device__ __forceinline__ double2 split_block(const PencilDev& pd, int x, int a, int b) {
+  if (x < 3) return pd.Gh ? gram_herm(pd.Gh, x, a, b) : make_double2(0.0, 0.0);
+  return pd.Eh ? herm_packed(pd.Eh, a, b) : make_double2(0.0, 0.0);
+}
+
+__device__ __forceinline__ double2 cscale(double c, double2 v) { return make_double2(c * v.x, c * v.y); }
+__device__ __forceinline__ double2 cneg(double2 v) { return make_double2(-v.x, -v.y); }
+
+// All threads of the CTA; pd.lam ascending, pd.beta, pd.Gh / pd.Eh complete.  rs: shared scratch.
+__device__ void pencil_split_tables(const PencilDev& pd, int r, double2 (*rs)[3 * MROM_MAX_R]) {
+  const int tid = threadIdx.x;
+  // prefix (TA) and suffix (TB) sums, one thread per (k, j)
+  for (int idx = tid; idx < 3 * r; idx += kPT) {
+    const int k = idx / 3, j = idx - (idx / 3) * 3;
+    const double lk = pd.lam[k];
+    double2 sa[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) sa[x] = make_double2(0.0, 0.0);
+    for (int l = 0; l <= r; ++l) {
+      if (l > k) {  // entry (m = l, k): sums over l' < m
+        double2* P = pd.pt + ((size_t)l * (l - 1) / 2 + k) * kPtEntry;
+        P[j] = cneg(sa[0]);
+        P[3 + j] = cneg(sa[2]);
+        P[6 + j] = cneg(sa[1]);  // TB_KK is added below
+        P[15 + j] = cneg(sa[3]);
+      }
+      if (l == r) break;
+      const double den = lk + pd.lam[l];
+      const double c = den > 0.0 ? lk * lk / den : 0.0;
+      const double2 b = pd.beta[l * 3 + j];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) sa[x] = cmac(sa[x], cscale(c, split_block(pd, x, k, l)), b);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) sa[x] = make_double2(0.0, 0.0);
+    // the source rows: -conj(gsK_jk) with w^2, -i conj(gsC_jk) with w^3
+    double2 dK = make_double2(0.0, 0.0), dS = make_double2(0.0, 0.0);
+    if (pd.gsh) {
+      const double2 gk = pd.gsh[k * 6 + j], gc = pd.gsh[k * 6 + 3 + j];
+      dK = make_double2(-gk.x, gk.y);
+      dS = make_double2(-gc.y, -gc.x);
+    }
+    for (int l = r - 1; l >= 0; --l) {
+      const int m = l + 1;  // here sa = sums over l' >= m
+      if (m > k) {
+        double2* P = pd.pt + ((size_t)m * (m - 1) / 2 + k) * kPtEntry;
+        P[6 + j] = cadd(P[6 + j], cadd(sa[0], dK));
+        P[9 + j] = cadd(sa[2], dS);
+        P[12 + j] = sa[1];
+        P[18 + j] = sa[3];
+      }
+      const double den = lk + pd.lam[l];
+      const double c = den > 0.0 ? 1.0 / den : 0.0;
+      const double2 b = pd.beta[l * 3 + j];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) sa[x] = cmac(sa[x], cscale(c, split_block(pd, x, k, l)), b);
+    }
+    double2* T = pd.tb0 + (size_t)k * 12;
+    T[j] = cadd(sa[0], dK);
+    T[3 + j] = sa[1];
+    T[6 + j] = cadd(sa[2], dS);
+    T[9 + j] = sa[3];
+  }
+  // C0(m): row sums S_m(j) = sum_{l<m} M_ml beta_lj, then the increments
+  //   C0(m+1) - C0(m) = conj(beta_m)^T S_m + S_m^H beta_m + M_mm conj(beta_m)^T beta_m
+  for (int idx = tid; idx < 3 * r; idx += kPT) {
+    const int m = idx / 3, j = idx - (idx / 3) * 3;
+    double2 sa[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) sa[x] = make_double2(0.0, 0.0);
+    for (int l = 0; l < m; ++l) {
+      const double2 b = pd.beta[l * 3 + j];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) sa[x] = cmac(sa[x], split_block(pd, x, m, l), b);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) rs[x][idx] = sa[x];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < 24; idx += kPT) {
+    const int x = idx / 6, q = idx - (idx / 6) * 6;
+    const int i = q < 3 ? 0 : (q < 5 ? 1 : 2), j = q < 3 ? q : (q < 5 ? q - 2 : 2);
+    double acc = 0.0;
+    for (int m = 0; m <= r; ++m) {
+      pd.c0[(size_t)m * 24 + idx] = acc;
+      if (m == r) break;
+      const double2 bi = pd.beta[m * 3 + i], bj = pd.beta[m * 3 + j];
+      const double2 si = rs[x][m * 3 + i], sj = rs[x][m * 3 + j];
+      const double mm = split_block(pd, x, m, m).x;  // real diagonal
+      acc += fma(bi.x, sj.x, bi.y * sj.y) + fma(si.x, bj.x, si.y * bj.y) + mm * fma(bi.x, bj.x, bi.y * bj.y);
+    }
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------------------------ finishing
 //
-// One CTA per object.  Q2 (real r x r, shared memory, odd row stride) = the tridiagonal's
-// eigenvectors Z2 from the divide-and-conquer kernel; V = W Q2 (the generalised
-// eigenvectors, V^H C V = I); then beta = V^H B, gs V and the transformed Gram blocks.
+// One CTA per object.  The eigenvalues are put in ascending order (and clamped at zero: K' is
+// positive semi-definite, so a negative eigenvalue within a few eps ||H|| of zero is rounding; a
+// clearly negative one sends the object to the LU route).  Q2 (real r x r, shared memory, odd
+// row stride) = the tridiagonal's eigenvectors Z2 from the divide-and-conquer kernel, columns
+// in the same order; V = W Q2 (the generalised eigenvectors, V^H C V = I); then beta = V^H B,
+// gs V, the transformed Gram blocks and, for the forward sweep, the pole-split tables.
 // Workspace per CTA: V and Y (r x r complex each).
 __global__ void __launch_bounds__(kPT, 1)
 pencil_finish_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__ pens,
                      const PencilScratch* __restrict__ scr, const int* __restrict__ order, int n_elig,
-                     int* __restrict__ counter, const int* __restrict__ pen_ok, double2* __restrict__ ws,
+                     int* __restrict__ counter, int* __restrict__ pen_ok, double2* __restrict__ ws,
                      size_t ws_elems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_task;
+  __shared__ double s_lam[MROM_MAX_R];
+  __shared__ int s_rank[MROM_MAX_R];
+  __shared__ double red[kPW];
+  __shared__ double2 s_rs[4][3 * MROM_MAX_R];
   double* Q2 = reinterpret_cast<double*>(smem_raw);
   const int tid = threadIdx.x;
   double2* W1 = ws + (size_t)blockIdx.x * ws_elems;
@@ -320,13 +477,36 @@ pencil_finish_kernel(const RomDev* __restrict__ objs, const PencilDev* __restric
     const int r = ob.r, rr = r * r;
     const int ldq = r | 1;
     double2* W0 = W1 + rr;
-    // the tridiagonal's eigenvectors from the divide-and-conquer kernel (odd row stride)
+    // ascending order of the eigenvalues (rank by counting, ties by index)
+    for (int j = tid; j < r; j += kPT) s_lam[j] = pd.lam[j];
+    __syncthreads();
+    double vmin = INFINITY, vabs = 0.0;
+    for (int j = tid; j < r; j += kPT) {
+      const double l = s_lam[j];
+      int rk = 0;
+      for (int i = 0; i < r; ++i) {
+        const double li = s_lam[i];
+        rk += (li < l || (li == l && i < j)) ? 1 : 0;
+      }
+      s_rank[j] = rk;
+      vmin = fmin(vmin, l);
+      vabs = fmax(vabs, fabs(l));
+    }
+    vmin = block_min(vmin, red);
+    vabs = -block_min(-vabs, red);
+    if (!(vmin >= -64.0 * r * DBL_EPSILON * vabs)) {  // not semi-definite (uniform across the CTA)
+      if (tid == 0) pen_ok[o] = 0;
+      continue;
+    }
+    // the tridiagonal's eigenvectors from the divide-and-conquer kernel (odd row stride), columns
+    // in ascending order of their eigenvalues
     {
       const double* Z2 = ps.work;
       for (int idx = tid; idx < rr; idx += kPT) {
         const int i = idx / r, j = idx - (idx / r) * r;
-        Q2[i * ldq + j] = Z2[idx];
+        Q2[i * ldq + s_rank[j]] = Z2[idx];
       }
+      for (int j = tid; j < r; j += kPT) pd.lam[s_rank[j]] = fmax(s_lam[j], 0.0);
     }
     __syncthreads();
     // V = W Q2 (W1)
@@ -396,13 +576,14 @@ pencil_finish_kernel(const RomDev* __restrict__ objs, const PencilDev* __restric
         tri_rc(e, a, b);
         double2 acc = make_double2(0.0, 0.0);
         for (int c = 0; c < r; ++c) acc = cmacc(acc, W1[c * r + a], W0[c * r + b]);
-        if (gram)  // the sweep's Hermitian forms use the diagonal halved
+        if (gram)  // stored with the diagonal halved
           pd.Gh[(size_t)e * 3 + x] = a == b ? make_double2(0.5 * acc.x, 0.5 * acc.y) : acc;
         else
           dst[e] = acc;
       }
       __syncthreads();
     }
+    if (pd.pt) pencil_split_tables(pd, r, s_rs);
   }
 }
 
@@ -455,7 +636,7 @@ __device__ __forceinline__ SweepTask table_task(const SweepTask* __restrict__ ta
 
 // ------------------------------------------------------------------ sweep
 
-// Dynamic shared memory of a sweep or adjoint task: the z tile (32 F frequencies x 3 columns x r
+// Dynamic shared memory of an adjoint task: the z tile (32 F frequencies x 3 columns x r
 // complex), then, reusing it, nq partial sums per lane of every warp.
 __host__ __device__ inline size_t pencil_task_smem(int r, int F, int nq) {
   const size_t z = (size_t)32 * F * 3 * r * sizeof(double2);
@@ -470,149 +651,121 @@ __device__ __forceinline__ unsigned dynamic_smem_bytes() {
   return v;
 }
 
-constexpr int kNQ = 39;  // partial sums per lane: U 0..8, X 9..17, E 18..26, R 27..32, I 33..38
+constexpr int kNQ = 30;  // partial sums per lane: U 0..8, E 9..17, R 18..23, I 24..29
+// dynamic shared memory of a sweep task: the partial sums per lane of every warp
+constexpr size_t kSweepSmem = (size_t)kPW * kNQ * 32 * sizeof(double);
 
-// Row pairs (a, r-1-a) of one warp, lane = one frequency: accumulates, over its rows a,
-//   U_ij = Re(z_ai^* y_aj), y = (L + D/2) G~(w) z   (certificate form, halved; the diagonal
-//          of the stored blocks is already halved)
-//   X_ij = Re((i w gsK_ia + w^2 gsC_ia) z_aj)
-//   E_ij = Re(z_ai^* ye_aj), ye = (L + D/2) (V^H Me V) z
-// (R and I need only O(1) per row and frequency; the z phase accumulates them.)
-template <bool CERT, bool HAS_E>
-__device__ __forceinline__ void pencil_rows(const PencilDev& pd, int r, const double2* __restrict__ zg, double w,
-                                            int q0, int wpg, double (&acc)[kNQ]) {
-  const double w2 = w * w;
-  const int half = (r + 1) / 2;
-  for (int pr = q0; pr < half; pr += wpg) {
-    for (int side = 0; side < 2; ++side) {
-      const int a = side == 0 ? pr : r - 1 - pr;
-      if (side == 1 && a == pr) break;
-      double2 za[3];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) za[j] = zg[(a * 3 + j) * 32];
-      if constexpr (CERT) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const double2 gk = pd.gsh[a * 6 + i], gc = pd.gsh[a * 6 + 3 + i];
-          // coefficient i w gk + w^2 gc; the real part of its product with z_j
-          const double cx = fma(-w, gk.y, w2 * gc.x), cy = fma(w, gk.x, w2 * gc.y);
-#pragma unroll
-          for (int j = 0; j < 3; ++j) acc[9 + i * 3 + j] = fma(cx, za[j].x, fma(-cy, za[j].y, acc[9 + i * 3 + j]));
-        }
-      }
-      if constexpr (CERT || HAS_E) {
-        double2 y[3], ye[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) y[j] = ye[j] = make_double2(0.0, 0.0);
-        const size_t row0 = (size_t)a * (a + 1) / 2;
-        const double2* gh = CERT ? pd.Gh + row0 * 3 : nullptr;
-        const double2* eh = HAS_E ? pd.Eh + row0 : nullptr;
-        for (int b = 0; b < a; ++b) {
-          double2 zb[3];
-#pragma unroll
-          for (int j = 0; j < 3; ++j) zb[j] = zg[(b * 3 + j) * 32];
-          if constexpr (CERT) {
-            const double2 kk = gh[3 * b], cc = gh[3 * b + 1], sk = gh[3 * b + 2];
-            // G~_ab = KK + w^2 CC + i w S
-            const double2 gt = make_double2(fma(w2, cc.x, fma(-w, sk.y, kk.x)), fma(w2, cc.y, fma(w, sk.x, kk.y)));
-#pragma unroll
-            for (int j = 0; j < 3; ++j) y[j] = cmac(y[j], gt, zb[j]);
-          }
-          if constexpr (HAS_E) {
-            const double2 e = eh[b];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) ye[j] = cmac(ye[j], e, zb[j]);
-          }
-        }
-        if constexpr (CERT) {  // diagonal term (stored halved)
-          const double2 kk = gh[3 * a], cc = gh[3 * a + 1], sk = gh[3 * a + 2];
-          const double2 gt = make_double2(fma(w2, cc.x, fma(-w, sk.y, kk.x)), fma(w2, cc.y, fma(w, sk.x, kk.y)));
-#pragma unroll
-          for (int j = 0; j < 3; ++j) y[j] = cmac(y[j], gt, za[j]);
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) acc[i * 3 + j] = fma(za[i].x, y[j].x, fma(za[i].y, y[j].y, acc[i * 3 + j]));
-        }
-        if constexpr (HAS_E) {  // diagonal term, halved here
-          const double2 e = eh[a];
-#pragma unroll
-          for (int j = 0; j < 3; ++j) ye[j] = cmac(ye[j], make_double2(0.5 * e.x, 0.5 * e.y), za[j]);
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-              acc[18 + i * 3 + j] = fma(za[i].x, ye[j].x, fma(za[i].y, ye[j].y, acc[18 + i * 3 + j]));
-        }
-      }
-    }
-  }
-}
-
-// A task is 32 F consecutive frequencies of one object (F frequency groups of 32, one
-// frequency per lane).  Warp w serves group w % F and the row pairs (a, r-1-a) with pair
-// index = w / F (mod 8 / F), so that every pair costs r + 1 row steps.  Shared memory:
-// z[g][b][j][lane] (the solutions in eigen-coordinates), then, after a barrier, the
-// per-warp partial sums, reduced once per (group, quantity, lane) into warp g's slot.
+// A task is 32 F consecutive frequencies of one object (F frequency groups of 32, one frequency
+// per lane).  Warp w serves group g = w % F and the rows k = w / F (mod 8 / F), accumulating per
+// lane, with a_k = 1 / (lambda_k + i w) and z_kj = u_k beta_kj (pole-split tables above):
+//   U_ij = Re sum_k a_k conj(beta_ki) Y_kj       (certificate: the form of G~(w) plus the
+//          source terms is U_ij + U_ji + Re C0_ij(m))
+//   E_ij = Re sum_k a_k conj(beta_ki) YE_kj      (V^H Me V likewise)
+//   and the diagonal parts Re(z_i^H Lambda z_j), Re(z_i^H z_j + beta_i^H z_j + z_i^H beta_j),
+//   which need one term per row.
+// Then the per-warp partial sums go to shared memory, reduced once per (group, quantity, lane)
+// into warp g's slot.
 template <bool CERT, bool HAS_E>
 __device__ __forceinline__ void pencil_task(const RomDev& ob, const PencilDev& pd, const SweepTask& task,
                                             const double* __restrict__ omega, int omega_stride, double ssig,
                                             double* __restrict__ Rout, double* __restrict__ Iout,
                                             double* __restrict__ Dout, double* __restrict__ Eout,
                                             int* __restrict__ status, int n_w, unsigned char* smem_raw,
-                                            double* Ws) {
+                                            double* Ws, int* Ms) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double2* zs = reinterpret_cast<double2*>(smem_raw);
   double* rbuf = reinterpret_cast<double*>(smem_raw);
   const int r = ob.r, S = task.nw;
   const int F = pd.F;       // frequency groups of 32
   const int wpg = kPW / F;  // warps per group
 
-  // ---- frequencies and z_kj = i w beta_kj / (lambda_k - i w) = u_k beta_kj,
-  //      u = i w (lambda + i w) / (lambda^2 + w^2)
+  // ---- frequencies and m = #{lambda_k < w} (binary search in the ascending eigenvalues)
   for (int s = tid; s < 32 * F; s += kPT) {
     double w = __longlong_as_double(0x7ff8000000000000LL);
+    int m = 0;
     if (s < S) {
       w = omega[(size_t)task.obj * omega_stride + task.w0 + s] * ssig;
       if (!(w > 0.0) || !isfinite(w)) {
         atomicOr(status, kStatusBadOmega);
         w = __longlong_as_double(0x7ff8000000000000LL);
+      } else {
+        int lo = 0, hi = r;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (pd.lam[mid] < w) lo = mid + 1; else hi = mid;
+        }
+        m = lo;
       }
     }
     Ws[s] = w;
+    Ms[s] = m;
   }
   __syncthreads();
-  // Warp w serves group g = w % F and rows k = w / F (mod 8 / F).  Per row, with
-  // bb_ij = Re(beta_ki^* beta_kj): Re(z_i^H Lambda z_j) gets lambda |u|^2 bb = -lambda Re(u) bb and
+  // Per row, with bb_ij = Re(beta_ki^* beta_kj) and u = i w (lambda + i w) / (lambda^2 + w^2):
+  // Re(z_i^H Lambda z_j) gets lambda |u|^2 bb = -lambda Re(u) bb and
   // Re(z_i^H z_j + beta_i^H z_j + beta_j^H z_i) gets (|u|^2 + 2 Re u) bb = Re(u) bb.
   double acc[kNQ];
 #pragma unroll
   for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
   const int g = warp % F;
-  const double wl = Ws[g * 32 + lane];
+  const double wl = Ws[g * 32 + lane], w2 = wl * wl;
+  const int ml = Ms[g * 32 + lane];
   for (int k = warp / F; k < r; k += wpg) {
     const double lam = pd.lam[k];
-    const double den = 1.0 / fma(lam, lam, wl * wl);
-    const double2 u = make_double2(-wl * wl * den, wl * lam * den);
-    double2* zk = zs + ((size_t)(g * r + k) * 3) * 32 + lane;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const double2 b = pd.beta[k * 3 + j];
-      zk[j * 32] = make_double2(fma(u.x, b.x, -u.y * b.y), fma(u.x, b.y, u.y * b.x));
-    }
+    const double den = 1.0 / fma(lam, lam, w2);
+    const double2 u = make_double2(-w2 * den, wl * lam * den);
     const double wr = -lam * u.x;
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
       const double bb = pd.bbr[k * 6 + q];
-      acc[27 + q] = fma(wr, bb, acc[27 + q]);
-      acc[33 + q] = fma(u.x, bb, acc[33 + q]);
+      acc[18 + q] = fma(wr, bb, acc[18 + q]);
+      acc[24 + q] = fma(u.x, bb, acc[24 + q]);
+    }
+    if constexpr (CERT || HAS_E) {
+      double2 ba[3];  // a_k conj(beta_k)
+      const double2 a = make_double2(lam * den, -wl * den);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double2 bt = pd.beta[k * 3 + i];
+        ba[i] = make_double2(fma(a.x, bt.x, a.y * bt.y), fma(a.y, bt.x, -a.x * bt.y));
+      }
+      double2 Y[3], YE[3];
+      if (k < ml) {
+        const double2* P = pd.pt + ((size_t)ml * (ml - 1) / 2 + k) * kPtEntry;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if constexpr (CERT) {  // Horner in w
+            double2 y = P[12 + j];
+            y = make_double2(fma(wl, y.x, P[9 + j].x), fma(wl, y.y, P[9 + j].y));
+            y = make_double2(fma(wl, y.x, P[6 + j].x), fma(wl, y.y, P[6 + j].y));
+            y = make_double2(fma(wl, y.x, P[3 + j].x), fma(wl, y.y, P[3 + j].y));
+            Y[j] = make_double2(fma(wl, y.x, P[j].x), fma(wl, y.y, P[j].y));
+          }
+          if constexpr (HAS_E) {
+            const double2 ta = P[15 + j], tb = P[18 + j];
+            YE[j] = make_double2(fma(w2, tb.x, ta.x), fma(w2, tb.y, ta.y));
+          }
+        }
+      } else {
+        const double2* T = pd.tb0 + (size_t)k * 12;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if constexpr (CERT) {
+            const double2 kk = T[j], cc = T[3 + j], ss = T[6 + j];
+            Y[j] = make_double2(w2 * fma(w2, cc.x, fma(wl, ss.x, kk.x)), w2 * fma(w2, cc.y, fma(wl, ss.y, kk.y)));
+          }
+          if constexpr (HAS_E) YE[j] = cscale(w2, T[9 + j]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if constexpr (CERT) acc[i * 3 + j] = fma(ba[i].x, Y[j].x, fma(-ba[i].y, Y[j].y, acc[i * 3 + j]));
+          if constexpr (HAS_E)
+            acc[9 + i * 3 + j] = fma(ba[i].x, YE[j].x, fma(-ba[i].y, YE[j].y, acc[9 + i * 3 + j]));
+        }
     }
   }
-  __syncthreads();
-
-  // ---- row pairs
-  pencil_rows<CERT, HAS_E>(pd, r, zs + (size_t)g * r * 3 * 32 + lane, wl, warp / F, wpg, acc);
-  __syncthreads();  // z is no longer read: its space takes the partial sums
   {
     double* rb = rbuf + (size_t)warp * kNQ * 32 + lane;
 #pragma unroll
@@ -629,7 +782,7 @@ __device__ __forceinline__ void pencil_task(const RomDev& ob, const PencilDev& p
     }
     __syncthreads();
   }
-  // ---- outputs
+  // ---- outputs (the leading-block sums C0(m) join here)
   for (int idx = tid; idx < S * 9; idx += kPT) {
     const int s = idx / 9, ij = idx - (idx / 9) * 9;
     const int i = ij / 3, j = ij - (ij / 3) * 3;
@@ -638,19 +791,22 @@ __device__ __forceinline__ void pencil_task(const RomDev& ob, const PencilDev& p
     const int lo = i < j ? i : j, hi = i < j ? j : i;
     const int sym = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);  // packed index of (lo, hi)
     const double wv = Ws[s];
+    const double* c0 = pd.c0 ? pd.c0 + (size_t)Ms[s] * 24 : nullptr;
     const size_t o = ((size_t)task.obj * n_w + task.w0 + s) * 9 + ij;
     if (Rout) {
-      double kf = t(27 + sym);
-      if constexpr (HAS_E) kf -= t(18 + i * 3 + j) + t(18 + j * 3 + i);
+      double kf = t(18 + sym);
+      if constexpr (HAS_E) kf -= t(9 + i * 3 + j) + t(9 + j * 3 + i) + c0[18 + sym];
       Rout[o] = fma(-0.25 * ob.alpha3, kf, ob.N0[ij]);
     }
-    if (Iout) Iout[o] = 0.25 * ob.alpha3 * wv * (ob.c00[ij] + t(33 + sym));
+    if (Iout) Iout[o] = 0.25 * ob.alpha3 * wv * (ob.c00[ij] + t(24 + sym));
     if (Dout) {
       if constexpr (CERT) {
         const double ww = wv * wv;
-        const double cij = fma(ww, ob.gss[ij], t(i * 3 + j) + t(j * 3 + i) + t(9 + i * 3 + j) + t(9 + j * 3 + i));
-        const double ni = fma(ww, ob.gss[i * 4], 2.0 * (t(i * 4) + t(9 + i * 4)));
-        const double nj = fma(ww, ob.gss[j * 4], 2.0 * (t(j * 4) + t(9 + j * 4)));
+        auto cg = [c0, wv, ww](int q) { return fma(ww, c0[6 + q], fma(wv, c0[12 + q], c0[q])); };
+        const int si = i == 0 ? 0 : (i == 1 ? 3 : 5), sj = j == 0 ? 0 : (j == 1 ? 3 : 5);
+        const double cij = fma(ww, ob.gss[ij], t(i * 3 + j) + t(j * 3 + i) + cg(sym));
+        const double ni = fma(ww, ob.gss[i * 4], 2.0 * t(i * 4) + cg(si));
+        const double nj = fma(ww, ob.gss[j * 4], 2.0 * t(j * 4) + cg(sj));
         Dout[o] = ob.cert_scale * (ni + nj - cij);
       } else {
         Dout[o] = __longlong_as_double(0x7ff8000000000000LL);
@@ -665,15 +821,16 @@ __device__ __forceinline__ void pencil_task(const RomDev& ob, const PencilDev& p
       const double* tot = rbuf + (size_t)(s >> 5) * kNQ * 32 + (s & 31);
       auto t = [tot](int q) { return tot[q * 32]; };
       const double wv = Ws[s];
+      const double* c0 = pd.c0 ? pd.c0 + (size_t)Ms[s] * 24 : nullptr;
       double Mp[6];  // packed (00, 01, 02, 11, 12, 22)
 #pragma unroll
       for (int sym = 0; sym < 6; ++sym) {
         const int i = sym < 3 ? 0 : (sym < 5 ? 1 : 2), j = sym < 3 ? sym : (sym < 5 ? sym - 2 : 2);
         if (is_i) {
-          Mp[sym] = 0.25 * ob.alpha3 * wv * (0.5 * (ob.c00[i * 3 + j] + ob.c00[j * 3 + i]) + t(33 + sym));
+          Mp[sym] = 0.25 * ob.alpha3 * wv * (0.5 * (ob.c00[i * 3 + j] + ob.c00[j * 3 + i]) + t(24 + sym));
         } else {
-          double kf = t(27 + sym);
-          if constexpr (HAS_E) kf -= t(18 + i * 3 + j) + t(18 + j * 3 + i);
+          double kf = t(18 + sym);
+          if constexpr (HAS_E) kf -= t(9 + i * 3 + j) + t(9 + j * 3 + i) + c0[18 + sym];
           Mp[sym] = fma(-0.25 * ob.alpha3, kf, 0.5 * (ob.N0[i * 3 + j] + ob.N0[j * 3 + i]));
         }
       }
@@ -693,6 +850,7 @@ pencil_sweep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_task;
   __shared__ double Ws[kPT];
+  __shared__ int Ms[kPT];
   const int tid = threadIdx.x;
   const int n_tasks = table[0].w0;
   for (;;) {
@@ -704,24 +862,29 @@ pencil_sweep_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict
     const SweepTask task = table_task(table, n_w, t);
     const RomDev& ob = objs[task.obj];
     const PencilDev& pd = pens[task.obj];
-    if (pencil_task_smem(ob.r, pd.F, kNQ) > dynamic_smem_bytes()) {  // launch smaller than the task
+    const bool cert = Dout != nullptr && ob.has_cert;
+    const bool has_e = pd.Eh != nullptr;
+    // a launch smaller than the task, or forward-sweep tables missing (internal errors)
+    if (kSweepSmem > dynamic_smem_bytes() || 32 * pd.F > kPT || ((cert || has_e) && pd.pt == nullptr) ||
+        (cert && pd.gsh == nullptr)) {
       if (tid == 0) atomicOr(status, kStatusConfig);
       continue;
     }
-    const bool cert = Dout != nullptr && ob.has_cert;
-    const bool has_e = pd.Eh != nullptr;
     const double ssig = s_sigma ? s_sigma[task.obj] : 1.0;
     if (cert) {
       if (has_e)
-        pencil_task<true, true>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, Eout, status, n_w, smem_raw, Ws);
+        pencil_task<true, true>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, Eout, status, n_w,
+                                smem_raw, Ws, Ms);
       else
-        pencil_task<true, false>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, Eout, status, n_w, smem_raw, Ws);
+        pencil_task<true, false>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, Eout, status, n_w,
+                                 smem_raw, Ws, Ms);
     } else {
       if (has_e)
-        pencil_task<false, true>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, Eout, status, n_w, smem_raw, Ws);
+        pencil_task<false, true>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, Eout, status, n_w,
+                                 smem_raw, Ws, Ms);
       else
         pencil_task<false, false>(ob, pd, task, omega, omega_stride, ssig, Rout, Iout, Dout, Eout, status, n_w,
-                                  smem_raw, Ws);
+                                  smem_raw, Ws, Ms);
     }
   }
 }
@@ -743,12 +906,6 @@ constexpr int kNQV = 42;  // partial sums per lane: R 0..5, I 6..11, B 12..20, R
 // with the PODP in mu_r (dbeta = V^H dB/ds_mu): Re(dbeta_i^H z_j) 42..50, Im tr(dbeta^H Y) 51, and
 //   dL/ds_mu += w' a^3/4 sum_ij Re(db_i^H p_j) G_I,ij + w' Im tr(dbeta^H Y) + w' a^3/4 gI.dc00 + gR.dN0
 constexpr int kNQVB = 52;
-
-__device__ __forceinline__ double2 herm_packed(const double2* __restrict__ M, int a, int b) {  // M[a][b]
-  if (b <= a) return M[(size_t)a * (a + 1) / 2 + b];
-  const double2 v = M[(size_t)b * (b + 1) / 2 + a];
-  return make_double2(v.x, -v.y);
-}
 
 template <bool HAS_E, bool HAS_F, bool HAS_DB, int NQ>
 __device__ __forceinline__ void pencil_vjp_rows(const PencilDev& pd, int r, const double2* __restrict__ zg, double w,
@@ -995,7 +1152,7 @@ pencil_vjp_kernel(const RomDev* __restrict__ objs, const PencilDev* __restrict__
 
 }  // namespace
 
-size_t pencil_sweep_smem_bytes(int r, int F) { return pencil_task_smem(r, F, kNQ); }
+size_t pencil_sweep_smem_bytes() { return kSweepSmem; }
 
 size_t pencil_finish_smem_bytes(int rmax) { return (size_t)rmax * (size_t)(rmax | 1) * sizeof(double); }
 
@@ -1095,12 +1252,15 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
   std::vector<size_t> off(n_obj, 0);
   for (size_t k = 0; k < elig.size(); ++k) {
     const int o = elig[k], r = objs[o].r;
+    // the forward sweep's task needs only its partial sums; the adjoint's holds the z tile too
     int F = 8;
-    while (F > 1 && (F > need || pencil_sweep_smem_bytes(r, F) > budget)) F /= 2;
+    while (F > 1 && (F > need || (!gram && pencil_vjp_smem_bytes(r, F) > budget))) F /= 2;
     spen[k] = 32 * F;
     pens[o].F = F;
-    smem = std::max(smem, pencil_sweep_smem_bytes(r, F));
-    smem_vjp = std::max(smem_vjp, pencil_vjp_smem_bytes(r, F));  // more partial sums per lane
+    if (gram)
+      smem = std::max(smem, pencil_sweep_smem_bytes());
+    else
+      smem_vjp = std::max(smem_vjp, pencil_vjp_smem_bytes(r, F));
     rmax = std::max(rmax, r);
     off[o] = data_elems;
     const size_t tri = (size_t)r * (r + 1) / 2;
@@ -1109,6 +1269,8 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
     if (objs[o].Me) data_elems += tri;                                    // Eh
     if (kin && objs[o].Kin) data_elems += tri;                            // Fh
     if (objs[o].dB) data_elems += 3 * (size_t)r;                          // dbeta
+    if (gram && (objs[o].has_cert || objs[o].Me))                         // pt, tb0, c0
+      data_elems += kPtEntry * tri + 12 * (size_t)r + 12 * (size_t)(r + 1);
     data_elems += (size_t)r * r + (size_t)(r + 1) / 2 + dc_work(r);  // scratch
   }
   t->prep_grid = std::min<int>((int)elig.size(), 2 * h->num_sms);
@@ -1165,6 +1327,11 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
     }
     if (objs[o].dB) {
       pens[o].dbeta = q; q += 3 * (size_t)r;
+    }
+    if (gram && (objs[o].has_cert || objs[o].Me)) {
+      pens[o].pt = q; q += kPtEntry * tri;
+      pens[o].tb0 = q; q += 12 * (size_t)r;
+      pens[o].c0 = reinterpret_cast<double*>(q); q += 12 * (size_t)(r + 1);
     }
     scr[o].W = q; q += (size_t)r * r;
     scr[o].e = reinterpret_cast<double*>(q); q += (r + 1) / 2;

@@ -12,9 +12,10 @@ import numpy as np
 
 def sweep_cost(r, n_w: int) -> np.ndarray:
     """Relative cost of sweeping objects of basis size r over n_w frequencies on the pencil
-    route: the O(r^3) preparation once plus the O(r^2) certificate form per frequency."""
+    route, in float64 flops: the O(r^3) preparation once plus O(r) per frequency (the
+    pole-split forms)."""
     r = np.asarray(r, dtype=np.float64)
-    return 40.0 * r ** 3 + 8.0 * n_w * r * r
+    return 60.0 * r ** 3 + 130.0 * n_w * r
 
 
 def balanced_split(costs, n_parts: int) -> list:

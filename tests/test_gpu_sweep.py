@@ -210,6 +210,32 @@ def test_routing_of_dictionary_and_ill_conditioned_objects(mrom, handle):
         assert max(errs) <= TOL, (obj.r, errs)
 
 
+def test_pole_split_spectra(mrom, handle):
+    """The pencil sweep splits its Hermitian forms at m = #{lambda_k < omega}: objects whose
+    eigenvalues include an exact null space of K (lambda = 0, clamped rounding), one r-fold
+    eigenvalue (K = 3 C) crossed by the sweep and met exactly at omega = 3, all eigenvalues above
+    the frequencies (m = 0) and all below (m = r); every one on the pencil route and at parity."""
+    from workloads import log_omegas, reduced_object
+    from gpu_common import oracle_sweep, rel_errors
+    a = reduced_object(51, 0, 24, k_range=(-2.0, 0.0), c_range=(-0.5, 0.0))
+    lam, Q = np.linalg.eigh(a.K)
+    lam[:2] = 0.0
+    a.K_out = (Q * lam[None, :]) @ Q.conj().T
+    a.K_out = 0.5 * (a.K_out + a.K_out.conj().T)
+    a.K_in = np.zeros_like(a.K_out)
+    b = reduced_object(51, 1, 16)
+    b.K_out, b.K_in = 3.0 * b.C, np.zeros_like(b.C)
+    c = reduced_object(51, 2, 20, k_range=(1.0, 2.0), c_range=(-0.5, 0.0))
+    d = reduced_object(51, 3, 33, k_range=(-3.0, -2.0), c_range=(-0.5, 0.0))
+    objs = [a, b, c, d]
+    wo = np.append(log_omegas(1e-1, 5.0, 64), 3.0)
+    (n_pen, n_lu), (Rg, Ig, Dg) = _plan_sweep(mrom, handle, objs, wo)
+    assert (n_pen, n_lu) == ((0, 4) if handle.solver == "lu" else (4, 0))
+    for k, obj in enumerate(objs):
+        errs = rel_errors(Rg[k], Ig[k], Dg[k], *oracle_sweep(obj, wo))
+        assert max(errs) <= TOL, (k, obj.r, errs)
+
+
 def test_pencil_route_with_stiffness_regularisation(mrom, handle):
     """An object with Me = U^H (eps M) U (added to the system only, not to R): the pencil
     route carries V^H Me V as a separate Hermitian form."""
