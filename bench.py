@@ -45,9 +45,9 @@ UNIT = "evals/s"
 SM_COUNT_NOMINAL = 152
 DFMA_PER_CLK_PER_SM = 2           # GB300 DFMA rate: 4 flop/clk/SM (mrom_fp64_peak measures it in every run)
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one pencil_sweep_kernel launch on
-# this workload, from an ncu capture of the current kernel; None once the kernel changes until it
-# is captured again
-SWEEP_DRAM_BYTES_PER_LAUNCH = None
+# this workload, from a one-pass ncu capture of the current kernel at full size (350.77 MB read +
+# 370.79 MB written); None once the kernel changes until it is captured again
+SWEEP_DRAM_BYTES_PER_LAUNCH = 350_770_000 + 370_790_000
 
 
 def flops_per_eval(r: int, cert: bool = True) -> float:

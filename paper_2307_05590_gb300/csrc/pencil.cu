@@ -356,72 +356,66 @@ __device__ __forceinline__ double2 cneg(double2 v) { return make_double2(-v.x, -
 // All threads of the CTA; pd.lam ascending, pd.beta, pd.Gh / pd.Eh complete.  rs: shared scratch.
 __device__ void pencil_split_tables(const PencilDev& pd, int r, double2 (*rs)[3 * MROM_MAX_R]) {
   const int tid = threadIdx.x;
-  // prefix (TA) and suffix (TB) sums, one thread per (k, j)
-  for (int idx = tid; idx < 3 * r; idx += kPT) {
-    const int k = idx / 3, j = idx - (idx / 3) * 3;
+  const int nb = 3 * r;  // (k, j) pairs per block
+  // (x, k, j) work items: block x of the present ones, row k, column j
+  auto present = [&pd](int x) { return x < 3 ? pd.Gh != nullptr : pd.Eh != nullptr; };
+  // prefix sums TA (one thread per (x, k, j)): P0 = -TA_KK, P1 = -TA_iS, P2 = -TA_CC (TB_KK and
+  // the source row join in the second pass), slot 5 = -TA_E
+  for (int idx = tid; idx < 4 * nb; idx += kPT) {
+    const int x = idx / nb, rem = idx - (idx / nb) * nb;
+    const int k = rem / 3, j = rem - (rem / 3) * 3;
+    const int slot = x == 0 ? 0 : (x == 1 ? 6 : (x == 2 ? 3 : 15));
     const double lk = pd.lam[k];
-    double2 sa[4];
-#pragma unroll
-    for (int x = 0; x < 4; ++x) sa[x] = make_double2(0.0, 0.0);
+    const bool on = present(x);
+    double2 sa = make_double2(0.0, 0.0);
     for (int l = 0; l <= r; ++l) {
-      if (l > k) {  // entry (m = l, k): sums over l' < m
-        double2* P = pd.pt + ((size_t)l * (l - 1) / 2 + k) * kPtEntry;
-        P[j] = cneg(sa[0]);
-        P[3 + j] = cneg(sa[2]);
-        P[6 + j] = cneg(sa[1]);  // TB_KK is added below
-        P[15 + j] = cneg(sa[3]);
-      }
-      if (l == r) break;
+      if (l > k) pd.pt[((size_t)l * (l - 1) / 2 + k) * kPtEntry + slot + j] = cneg(sa);  // entry (m = l, k)
+      if (l == r || !on) continue;
       const double den = lk + pd.lam[l];
       const double c = den > 0.0 ? lk * lk / den : 0.0;
-      const double2 b = pd.beta[l * 3 + j];
-#pragma unroll
-      for (int x = 0; x < 4; ++x) sa[x] = cmac(sa[x], cscale(c, split_block(pd, x, k, l)), b);
+      sa = cmac(sa, cscale(c, split_block(pd, x, k, l)), pd.beta[l * 3 + j]);
     }
-#pragma unroll
-    for (int x = 0; x < 4; ++x) sa[x] = make_double2(0.0, 0.0);
-    // the source rows: -conj(gsK_jk) with w^2, -i conj(gsC_jk) with w^3
-    double2 dK = make_double2(0.0, 0.0), dS = make_double2(0.0, 0.0);
-    if (pd.gsh) {
-      const double2 gk = pd.gsh[k * 6 + j], gc = pd.gsh[k * 6 + 3 + j];
-      dK = make_double2(-gk.x, gk.y);
-      dS = make_double2(-gc.y, -gc.x);
+  }
+  __syncthreads();
+  // suffix sums TB: P2 += TB_KK - conj(gsK_jk), P3 = TB_iS - i conj(gsC_jk), P4 = TB_CC, slot 6 =
+  // TB_E; the full suffix (m = 0) into tb0
+  for (int idx = tid; idx < 4 * nb; idx += kPT) {
+    const int x = idx / nb, rem = idx - (idx / nb) * nb;
+    const int k = rem / 3, j = rem - (rem / 3) * 3;
+    const int slot = x == 0 ? 6 : (x == 1 ? 12 : (x == 2 ? 9 : 18));
+    const double lk = pd.lam[k];
+    const bool on = present(x);
+    double2 d = make_double2(0.0, 0.0);  // the certificate's source row
+    if (pd.gsh && x == 0) {
+      const double2 gk = pd.gsh[k * 6 + j];
+      d = make_double2(-gk.x, gk.y);
+    } else if (pd.gsh && x == 2) {
+      const double2 gc = pd.gsh[k * 6 + 3 + j];
+      d = make_double2(-gc.y, -gc.x);
     }
+    double2 sa = make_double2(0.0, 0.0);
     for (int l = r - 1; l >= 0; --l) {
       const int m = l + 1;  // here sa = sums over l' >= m
       if (m > k) {
-        double2* P = pd.pt + ((size_t)m * (m - 1) / 2 + k) * kPtEntry;
-        P[6 + j] = cadd(P[6 + j], cadd(sa[0], dK));
-        P[9 + j] = cadd(sa[2], dS);
-        P[12 + j] = sa[1];
-        P[18 + j] = sa[3];
+        double2* P = pd.pt + ((size_t)m * (m - 1) / 2 + k) * kPtEntry + slot + j;
+        *P = x == 0 ? cadd(*P, cadd(sa, d)) : cadd(sa, d);
       }
+      if (!on) continue;
       const double den = lk + pd.lam[l];
       const double c = den > 0.0 ? 1.0 / den : 0.0;
-      const double2 b = pd.beta[l * 3 + j];
-#pragma unroll
-      for (int x = 0; x < 4; ++x) sa[x] = cmac(sa[x], cscale(c, split_block(pd, x, k, l)), b);
+      sa = cmac(sa, cscale(c, split_block(pd, x, k, l)), pd.beta[l * 3 + j]);
     }
-    double2* T = pd.tb0 + (size_t)k * 12;
-    T[j] = cadd(sa[0], dK);
-    T[3 + j] = sa[1];
-    T[6 + j] = cadd(sa[2], dS);
-    T[9 + j] = sa[3];
+    pd.tb0[(size_t)k * 12 + 3 * x + j] = cadd(sa, d);
   }
   // C0(m): row sums S_m(j) = sum_{l<m} M_ml beta_lj, then the increments
   //   C0(m+1) - C0(m) = conj(beta_m)^T S_m + S_m^H beta_m + M_mm conj(beta_m)^T beta_m
-  for (int idx = tid; idx < 3 * r; idx += kPT) {
-    const int m = idx / 3, j = idx - (idx / 3) * 3;
-    double2 sa[4];
-#pragma unroll
-    for (int x = 0; x < 4; ++x) sa[x] = make_double2(0.0, 0.0);
-    for (int l = 0; l < m; ++l) {
-      const double2 b = pd.beta[l * 3 + j];
-#pragma unroll
-      for (int x = 0; x < 4; ++x) sa[x] = cmac(sa[x], split_block(pd, x, m, l), b);
-    }
-#pragma unroll
-    for (int x = 0; x < 4; ++x) rs[x][idx] = sa[x];
+  for (int idx = tid; idx < 4 * nb; idx += kPT) {
+    const int x = idx / nb, rem = idx - (idx / nb) * nb;
+    const int m = rem / 3, j = rem - (rem / 3) * 3;
+    double2 sa = make_double2(0.0, 0.0);
+    if (present(x))
+      for (int l = 0; l < m; ++l) sa = cmac(sa, split_block(pd, x, m, l), pd.beta[l * 3 + j]);
+    rs[x][rem] = sa;
   }
   __syncthreads();
   for (int idx = tid; idx < 24; idx += kPT) {
