@@ -24,7 +24,7 @@ __all__ = [
     "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune", "mrom_sweep_noalloc",
     "FullOrder", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "MromSweep", "signature",
     "mrom_sweep_mixed", "mrom_project_dirs", "mrom_invariants", "mrom_fp64_peak", "mrom_static_solve", "static_solver_for", "PermeabilityData", "mrom_project_mu",
-    "mrom_rom_mu_state", "mrom_fom_solve", "PackedDictionary",
+    "mrom_rom_mu_state", "mrom_fom_solve", "PackedDictionary", "mrom_sweep_host",
 ]
 
 
@@ -262,6 +262,25 @@ class PackedDictionary:
         for o, a in parts:
             view[o:o + a.nbytes] = a.view(np.uint8).ravel()
         self.buffer = host
+
+
+def mrom_sweep_host(handle: Handle, packed: PackedDictionary, omega, R, I, Delta=None, n_chunks: int = 2):
+    """mrom_sweep_host: the sweep of a PackedDictionary from host memory (omega: n_w float64) into
+    host outputs R, I, Delta ([n_obj][n_w][3][3] float64, pinned for overlapped copies; Delta may
+    be None), in n_chunks groups pipelined over two streams.  Synchronous."""
+    n_w = int(np.asarray(omega.shape)[0]) if hasattr(omega, "shape") else len(omega)
+    for x in (omega, R, I, Delta):
+        if x is None:
+            continue
+        if isinstance(x, np.ndarray):
+            ok = x.dtype == np.float64
+        else:
+            ok = x.device.type == "cpu" and str(x.dtype) == "torch.float64"
+        if not ok:
+            raise ValueError("mrom_sweep_host takes float64 host arrays")
+    _abi.check(lib().mrom_sweep_host(handle.ptr, len(packed.entries), packed.entries, _ptr(packed.buffer),
+                                     int(packed.nbytes), _ptr(omega), n_w, _ptr(R), _ptr(I), _ptr(Delta),
+                                     int(n_chunks)), handle.ptr)
 
 
 class Plan:

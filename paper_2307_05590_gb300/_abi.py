@@ -20,7 +20,7 @@ EXPORTS = [
     "mrom_project_dirs", "mrom_set_projection_precision", "mrom_set_solver", "mrom_plan_solver_counts",
     "mrom_plan_timing", "mrom_rom_from_reduced_batch", "mrom_invariants", "mrom_project_mu",
     "mrom_rom_static_rank", "mrom_rom_mu_state", "mrom_fom_solve", "mrom_rom_from_packed", "mrom_rom_free_batch",
-    "mrom_fp64_peak", "mrom_static_solve", "mrom_plan_sweep_invariants",
+    "mrom_fp64_peak", "mrom_static_solve", "mrom_plan_sweep_invariants", "mrom_sweep_host",
 ]
 
 
@@ -143,6 +143,8 @@ def _declare(L):
         "mrom_rom_free_batch": (None, [ctypes.POINTER(vp), i32]),
         "mrom_rom_from_packed": (ctypes.c_int, [vp, i32, ctypes.POINTER(mrom_packed_obj), vp, ctypes.c_size_t,
                                                 ctypes.POINTER(vp)]),
+        "mrom_sweep_host": (ctypes.c_int, [vp, i32, ctypes.POINTER(mrom_packed_obj), vp, ctypes.c_size_t, vp, i32,
+                                           vp, vp, vp, i32]),
         "mrom_fom_solve": (ctypes.c_int, [vp, ctypes.POINTER(mrom_fom), ctypes.POINTER(ctypes.c_double), i32,
                                           ctypes.c_double, i32, vp, i64, ctypes.POINTER(i32),
                                           ctypes.POINTER(ctypes.c_double)]),

@@ -72,6 +72,11 @@ extern "C" mrom_status mrom_destroy(mrom_handle h) {
   if (!h) return MROM_EINVAL;
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
+  for (cudaStream_t s : h->aux)
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
   if (h->d_status) cudaFree(h->d_status);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;

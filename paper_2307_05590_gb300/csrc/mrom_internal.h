@@ -128,6 +128,7 @@ struct mrom_ctx {
   int solver = 0;                 // MROM_SOLVER_AUTO or MROM_SOLVER_LU for plans and sweeps
   mrom_status pending = MROM_OK;  // host-detected asynchronous error
   std::string last_error;
+  cudaStream_t aux[2] = {nullptr, nullptr};  // the pipelined host-buffer sweep's streams (lazily created)
 };
 
 namespace mrom {

@@ -236,6 +236,37 @@ def test_pole_split_spectra(mrom, handle):
         assert max(errs) <= TOL, (k, obj.r, errs)
 
 
+def test_sweep_host_pipeline(mrom, handle):
+    """mrom_sweep_host (host buffers in and out, groups pipelined over two streams) gives the
+    device plan sweep's values on a batch with pencil- and LU-routed objects, for 1, 3 and more
+    groups than objects, with and without the certificate; bad arguments are refused."""
+    import torch
+    from workloads import log_omegas, reduced_object
+    from gpu_common import oracle_sweep, rel_errors
+    objs = [reduced_object(61, k, r) for k, r in enumerate([12, 40, 7, 96, 33, 1, 64, 20])]
+    objs.append(reduced_object(61, 9, 40, k_range=(-4.0, 4.0)))   # LU route under "auto"
+    wo = log_omegas(1e1, 1e8, 70)
+    packed = mrom.PackedDictionary([dict(r=o.r, K=o.K, C=o.C, B=o.B, c00=o.c00, G=o.G, K_in=o.K_in,
+                                         alpha=o.alpha, alpha_lb=o.alpha_lb, vol_B=o.vol_B) for o in objs])
+    _, (Rp, Ip, Dp) = _plan_sweep(mrom, handle, objs, wo)
+    shape = (len(objs), wo.size, 3, 3)
+    om = torch.from_numpy(wo.copy()).pin_memory()
+    for n_chunks, cert in ((1, True), (3, True), (16, False)):
+        R, I = (torch.full(shape, np.nan, dtype=torch.float64).pin_memory() for _ in range(2))
+        D = torch.full(shape, np.nan, dtype=torch.float64).pin_memory() if cert else None
+        mrom.mrom_sweep_host(handle, packed, om, R, I, D, n_chunks=n_chunks)
+        assert np.array_equal(R.numpy(), Rp) and np.array_equal(I.numpy(), Ip), n_chunks
+        if cert:
+            assert np.array_equal(D.numpy(), Dp), n_chunks
+    for k in (1, 3, 8):
+        errs = rel_errors(R.numpy()[k], I.numpy()[k], Dp[k], *oracle_sweep(objs[k], wo))
+        assert max(errs) <= TOL, (k, errs)
+    with pytest.raises(mrom.MromError):
+        mrom.mrom_sweep_host(handle, packed, om, R, I, None, n_chunks=0)
+    with pytest.raises(mrom.MromError):
+        mrom.mrom_sweep_host(handle, packed, om, R, I, None, n_chunks=17)
+
+
 def test_pencil_route_with_stiffness_regularisation(mrom, handle):
     """An object with Me = U^H (eps M) U (added to the system only, not to R): the pencil
     route carries V^H Me V as a separate Hermitian form."""
