@@ -8,8 +8,10 @@
 //   K_r = U^H Y, C_r = U^H diag(c) U, Me = U^H diag(eps m) U,
 //   b_i = U^H (c o_i), c00 = o^T diag(c) o                             (Eqs. (17)-(19))
 //   G   = Phi^H diag(1/x) Phi, Phi = [c o_i | Y + eps m U | c U]      (Lemma 4.2)
-// Everything is float64 / complex128, except that the mixed projection mode forms K U and the
-// products K_r, C_r, eps M_r and b in complex64 (TSVD and certificate Gram stay float64).
+// Everything is float64 / complex128, except that the mixed projection mode forms the basis U
+// (without a certificate, which needs U in float64), K U and the products K_r, C_r, eps M_r and b
+// in complex64 (the snapshot Gram of the TSVD and the certificate Gram stay float64: TOL_Sigma
+// down to 1e-6 needs the Gram's eigenvalues to 1e-12 of the largest).
 // The float64 kernels are FP64-pipe bound on GB300
 // (the snapshot and basis streams are re-read from L2), so they are written for
 // full FP64 utilisation with register tiles rather than for HBM streaming.
@@ -206,44 +208,62 @@ herm_eig_kernel(double2* __restrict__ A, int m, double2* __restrict__ Z, double*
 }
 
 // ------------------------------------------------------------- basis apply
-// U[row][k] = sum_c D(row, c) W[c][k]; D(row, c) = D[row * rsD + c * csD]; U row-major (ldu).
-constexpr int kAR = 32;   // rows per CTA
-constexpr int kAC = 32;   // output columns per pass
-__global__ void __launch_bounds__(256)
-apply_basis_kernel(const double2* __restrict__ D, int64_t rsD, int64_t csD, int m, int64_t n,
-                   const double2* __restrict__ W, int r, double2* __restrict__ U, int64_t ldu) {
+// U[row][off + k] = sum_c D(row, c) W[c][k] for k < r; D(row, c) = D[c * ldd + row] (complex128
+// columns), W (m x r, row-major) in shared memory, U row-major (ldu).  One thread per row, 16
+// output columns per pass with the accumulators in registers; each pass is staged in shared
+// memory and written row segment by row segment (coalesced).  T = double2 (float64, the float64
+// projection) or float2 (the mixed projection's complex64 basis, float32 accumulation over the
+// m snapshot columns).
+constexpr int kAR = 128;  // rows per CTA (one per thread)
+constexpr int kAC = 16;   // output columns per pass
+
+template <class T>
+__device__ __forceinline__ T cplx_mac(T c, T a, T b) {  // c + a b
+  c.x = fma(a.x, b.x, fma(-a.y, b.y, c.x));
+  c.y = fma(a.x, b.y, fma(a.y, b.x, c.y));
+  return c;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kAR)
+apply_basis_kernel(const double2* __restrict__ D, int64_t ldd, int m, int64_t n, const T* __restrict__ W, int r,
+                   T* __restrict__ U, int64_t ldu) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* Dt = reinterpret_cast<double2*>(smem_raw);   // kAR x (m + 1)
-  double2* Wt = Dt + (size_t)kAR * (m + 1);             // m x kAC
+  T* Wt = reinterpret_cast<T*>(smem_raw);  // m x kAC: the pass's columns of W
+  T* St = Wt + (size_t)m * kAC;            // kAR x (kAC + 1): the pass's outputs
   const int tid = threadIdx.x;
-  const int64_t row0 = (int64_t)blockIdx.x * kAR;
-  for (int idx = tid; idx < kAR * m; idx += 256) {
-    int rr, c;
-    if (rsD == 1) { c = idx / kAR; rr = idx % kAR; } else { rr = idx / m; c = idx % m; }
-    const int64_t nr = row0 + rr;
-    Dt[rr * (m + 1) + c] = nr < n ? D[nr * rsD + c * csD] : make_double2(0.0, 0.0);
-  }
-  const int rr = tid % kAR, kq = tid / kAR;  // 8 groups of 4 columns
+  const int64_t row0 = (int64_t)blockIdx.x * kAR, row = row0 + tid;
   for (int k0 = 0; k0 < r; k0 += kAC) {
-    __syncthreads();
-    for (int idx = tid; idx < m * kAC; idx += 256) {
-      const int c = idx / kAC, kk = idx % kAC;
-      Wt[idx] = (k0 + kk < r) ? W[(size_t)c * r + k0 + kk] : make_double2(0.0, 0.0);
+    const int kc = min(kAC, r - k0);
+    __syncthreads();  // the previous pass's stage written out
+    for (int idx = tid; idx < m * kAC; idx += kAR) {
+      const int c = idx / kAC, k = idx - (idx / kAC) * kAC;
+      T w;
+      w.x = w.y = 0;
+      if (k < kc) w = W[(size_t)c * r + k0 + k];
+      Wt[idx] = w;
     }
     __syncthreads();
-    double2 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int c = 0; c < m; ++c) {
-      const double2 d = Dt[rr * (m + 1) + c];
+    T acc[kAC];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j] = c_mac(acc[j], d, Wt[c * kAC + kq * 4 + j]);
-    }
-    const int64_t nr = row0 + rr;
-    if (nr < n) {
+    for (int k = 0; k < kAC; ++k) acc[k].x = acc[k].y = 0;
+    if (row < n) {
+      for (int c = 0; c < m; ++c) {
+        const double2 d64 = D[(int64_t)c * ldd + row];
+        T d;
+        d.x = d64.x;
+        d.y = d64.y;
+        const T* w = Wt + (size_t)c * kAC;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int k = k0 + kq * 4 + j;
-        if (k < r) U[nr * ldu + k] = acc[j];
+        for (int k = 0; k < kAC; ++k) acc[k] = cplx_mac(acc[k], d, w[k]);
       }
+    }
+#pragma unroll
+    for (int k = 0; k < kAC; ++k) St[tid * (kAC + 1) + k] = acc[k];
+    __syncthreads();
+    for (int idx = tid; idx < kAR * kc; idx += kAR) {
+      const int rr = idx / kc, k = idx - (idx / kc) * kc;
+      if (row0 + rr < n) U[(row0 + rr) * ldu + k0 + k] = St[rr * (kAC + 1) + k];
     }
   }
 }
@@ -524,19 +544,40 @@ mrom_status gram_eig(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, int
   return MROM_OK;
 }
 
-// U[:, off : off + r] (row-major, leading dimension ldu) = D W
+// U[:, off : off + r] (row-major, leading dimension ldu) = D W, in float64 (U64) or complex64 (U32)
 mrom_status apply_basis(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, int m, const std::vector<double2>& wh,
-                        int r, double2* U, int ldu) {
+                        int r, double2* U64, int ldu, float2* U32 = nullptr) {
   DevBuf wbuf;
-  cudaError_t e = cudaMalloc(&wbuf.p, wh.size() * sizeof(double2));
-  if (e == cudaSuccess) e = cudaMemcpyAsync(wbuf.p, wh.data(), wh.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream);
-  const size_t smem = ((size_t)kAR * (m + 1) + (size_t)m * kAC) * sizeof(double2);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply_basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const bool f32 = U32 != nullptr;
+  const size_t esz = f32 ? sizeof(float2) : sizeof(double2);
+  std::vector<float2> w32;
+  if (f32) {
+    w32.resize(wh.size());
+    for (size_t k = 0; k < wh.size(); ++k) w32[k] = make_float2((float)wh[k].x, (float)wh[k].y);
+  }
+  const size_t smem = ((size_t)m * kAC + (size_t)kAR * (kAC + 1)) * esz;
+  if (smem > h->smem_optin) return fail(h, MROM_EINVAL, "mrom_project: snapshot count too large for the basis apply");
+  cudaError_t e = cudaMalloc(&wbuf.p, wh.size() * esz);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(wbuf.p, f32 ? static_cast<const void*>(w32.data()) : static_cast<const void*>(wh.data()),
+                        wh.size() * esz, cudaMemcpyHostToDevice, h->stream);
+  const unsigned grid = (unsigned)((n + kAR - 1) / kAR);
+  if (f32) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(apply_basis_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      apply_basis_kernel<float2><<<grid, kAR, smem, h->stream>>>(Dp, ldd, m, n, static_cast<float2*>(wbuf.p), r, U32,
+                                                                 ldu);
+  } else {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(apply_basis_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      apply_basis_kernel<double2><<<grid, kAR, smem, h->stream>>>(Dp, ldd, m, n, static_cast<double2*>(wbuf.p), r,
+                                                                  U64, ldu);
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: basis");
-  apply_basis_kernel<<<(unsigned)((n + kAR - 1) / kAR), 256, smem, h->stream>>>(Dp, 1, ldd, m, n,
-                                                                                 static_cast<double2*>(wbuf.p), r, U, ldu);
   ++h->launches;
-  e = cudaStreamSynchronize(h->stream);
+  e = cudaStreamSynchronize(h->stream);  // wbuf is freed on scope exit
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: basis");
   return MROM_OK;
 }
@@ -544,7 +585,7 @@ mrom_status apply_basis(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, 
 // Galerkin projection onto the basis U (n x Rt row-major; r_dirs = per-direction column
 // blocks, or all zero for one shared basis) and creation of the reduced object.
 mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, int r, const int32_t* r_dirs,
-                          mrom_rom_t* out, const double2* Kin_r = nullptr) {
+                          mrom_rom_t* out, const double2* Kin_r = nullptr, const float2* U32in = nullptr) {
   const int64_t n = fom->n;
   cudaStream_t st = h->stream;
   auto launch_grid = [](int64_t work) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(65535 * 4, (work + 255) / 256)); };
@@ -580,15 +621,16 @@ mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, in
     DevBuf U32, Y32, O32, K32, c32, m32;
     int32_t nnz_host = 0;
     e = cudaMemcpy(&nnz_host, fom->K_rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMalloc(&U32.p, (size_t)n * r * sizeof(float2));
+    if (e == cudaSuccess && !U32in) e = cudaMalloc(&U32.p, (size_t)n * r * sizeof(float2));
     if (e == cudaSuccess) e = cudaMalloc(&Y32.p, (size_t)n * r * sizeof(float2));
     if (e == cudaSuccess) e = cudaMalloc(&O32.p, (size_t)n * 3 * sizeof(float2));
     if (e == cudaSuccess) e = cudaMalloc(&K32.p, (size_t)nnz_host * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&c32.p, (size_t)n * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&m32.p, (size_t)n * sizeof(float));
     if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: single-precision buffers");
-    to_f32_kernel<<<launch_grid(2 * n * r), 256, 0, st>>>(reinterpret_cast<const double*>(U), 2 * n * r, 1.0,
-                                                          static_cast<float*>(U32.p));
+    if (!U32in)
+      to_f32_kernel<<<launch_grid(2 * n * r), 256, 0, st>>>(reinterpret_cast<const double*>(U), 2 * n * r, 1.0,
+                                                            static_cast<float*>(U32.p));
     to_f32_kernel<<<launch_grid(6 * n), 256, 0, st>>>(reinterpret_cast<const double*>(Op), 6 * n, 1.0,
                                                       static_cast<float*>(O32.p));
     to_f32_kernel<<<launch_grid(nnz_host), 256, 0, st>>>(fom->K_val, nnz_host, 1.0, static_cast<float*>(K32.p));
@@ -596,11 +638,11 @@ mrom_status project_basis(mrom_ctx* h, const mrom_fom* fom, const double2* U, in
     if (has_me)
       to_f32_kernel<<<launch_grid(n), 256, 0, st>>>(fom->M_diag, n, fom->eps, static_cast<float*>(m32.p));
     spmm_csr_f32_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(
-        fom->K_rowptr, fom->K_col, static_cast<float*>(K32.p), n, static_cast<float2*>(U32.p), r,
+        fom->K_rowptr, fom->K_col, static_cast<float*>(K32.p), n, U32in ? U32in : static_cast<float2*>(U32.p), r,
         static_cast<float2*>(Y32.p));
-    h->launches += has_me ? 6 : 5;
+    h->launches += (has_me ? 6 : 5) - (U32in ? 1 : 0);
     e = cudaGetLastError();
-    const auto* u32 = static_cast<const float2*>(U32.p);
+    const auto* u32 = U32in ? U32in : static_cast<const float2*>(U32.p);
     // the Gram products on the tensor cores (tcgen05, 3 x TF32 split, FP32 accumulation per CTA)
     if (e == cudaSuccess) e = tall_gram_tc(h, u32, r, static_cast<float2*>(Y32.p), r, nullptr, n, Kr, r);
     if (e == cudaSuccess) {
@@ -762,9 +804,15 @@ extern "C" mrom_status mrom_project(mrom_handle h, const mrom_fom* fom, const vo
   if (st != MROM_OK) return st;
   if (sigma_out) std::copy(s.begin(), s.end(), sigma_out);
   if (r_out) *r_out = r;
+  const bool b32 = h->projection_precision == MROM_MIXED && !fom_has_certificate(fom);
   DevBuf Ubuf;
-  e = cudaMalloc(&Ubuf.p, (size_t)n * r * sizeof(double2));
+  e = cudaMalloc(&Ubuf.p, (size_t)n * r * (b32 ? sizeof(float2) : sizeof(double2)));
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: basis allocation");
+  if (b32) {
+    st = apply_basis(h, Dp, ldd, n, n_cols, wh, r, nullptr, r, static_cast<float2*>(Ubuf.p));
+    if (st != MROM_OK) return st;
+    return project_basis(h, fom, nullptr, r, nullptr, out, nullptr, static_cast<const float2*>(Ubuf.p));
+  }
   st = apply_basis(h, Dp, ldd, n, n_cols, wh, r, static_cast<double2*>(Ubuf.p), r);
   if (st != MROM_OK) return st;
   return project_basis(h, fom, static_cast<const double2*>(Ubuf.p), r, nullptr, out);
@@ -811,15 +859,21 @@ extern "C" mrom_status mrom_project_dirs(mrom_handle h, const mrom_fom* fom, con
   const int rt = rd[0] + rd[1] + rd[2];
   if (rt > MROM_MAX_R) return fail(h, MROM_EINVAL, "mrom_project_dirs: r_1 + r_2 + r_3 exceeds MROM_MAX_R");
   if (r_dirs_out) std::copy(rd, rd + 3, r_dirs_out);
+  // the mixed mode without a certificate needs the basis only in complex64
+  const bool b32 = h->projection_precision == MROM_MIXED && !fom_has_certificate(fom);
   DevBuf Ubuf;
-  e = cudaMalloc(&Ubuf.p, (size_t)n * rt * sizeof(double2));
+  e = cudaMalloc(&Ubuf.p, (size_t)n * rt * (b32 ? sizeof(float2) : sizeof(double2)));
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project_dirs: basis allocation");
   int off = 0;
   for (int i = 0; i < 3; ++i) {
-    st = apply_basis(h, Dp + (size_t)i * n_s * ldd, ldd, n, n_s, wh[i], rd[i], static_cast<double2*>(Ubuf.p) + off, rt);
+    st = b32 ? apply_basis(h, Dp + (size_t)i * n_s * ldd, ldd, n, n_s, wh[i], rd[i], nullptr, rt,
+                           static_cast<float2*>(Ubuf.p) + off)
+             : apply_basis(h, Dp + (size_t)i * n_s * ldd, ldd, n, n_s, wh[i], rd[i],
+                           static_cast<double2*>(Ubuf.p) + off, rt);
     if (st != MROM_OK) return st;
     off += rd[i];
   }
+  if (b32) return project_basis(h, fom, nullptr, rt, rd, out, nullptr, static_cast<const float2*>(Ubuf.p));
   return project_basis(h, fom, static_cast<const double2*>(Ubuf.p), rt, rd, out);
 }
 
