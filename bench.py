@@ -717,6 +717,7 @@ def main():
     h = m.Handle(local_rank, stream.cuda_stream)
     roms = [m.ReducedObject.from_workload(h, o) for o in objs]
     sweep_cfg = m.mrom_tune(h, roms, args.n_w)
+    pencil_groups = m.mrom_tune_pencil(h, roms, args.n_w)
     plan = m.Plan(h, roms, args.n_w)
     plan.enable_timing()
     om = torch.as_tensor(wo, dtype=torch.float64, device=dev)
@@ -948,6 +949,7 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
             "roofline": roofline, "cpu_baseline": cpu, "accuracy_vs_oracle": accuracy, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "wall_s_timed": wall, "per_launch_ms": per_launch_ms, "sweep_config": sweep_cfg,
+            "pencil_groups_per_task": pencil_groups,
             "stages": stage_info, "lu_route": lu_route, "mixed_precision": mixed, "projection": proj,
             "gradients": grads, "invariants": inv, "c1_latency": c1, "podp_mu": pmu,
         }

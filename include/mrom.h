@@ -530,6 +530,17 @@ mrom_status mrom_plan_timing(mrom_plan plan, int32_t enable, float* stage_ms);
  * configuration index. */
 mrom_status mrom_tune(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int32_t n_w, int32_t* chosen);
 
+/* The pencil route's launch mapping, picked by timing like mrom_tune: a plan sweep of a sample
+ * of the objects (up to 2000 spread over the batch, up to 2048 log-spaced frequencies in
+ * [1e1, 1e8]; the faster of two timed sweeps) with at most 8, 4, 2 or 1 frequency groups of 32
+ * per sweep task (8 groups: one warp
+ * per group runs every row of the object; fewer groups split the rows over the warps of a group
+ * and reduce across them).  The fastest becomes the handle's cap for later plans (default 8);
+ * *groups (may be NULL) receives it.  Results do not depend on the choice beyond rounding.
+ * Blocks until done; allocates and frees a scratch buffer; device errors of the timed sweeps
+ * are returned (mrom_synchronize). */
+mrom_status mrom_tune_pencil(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int32_t n_w, int32_t* groups);
+
 /* ------------------------------------------------- rotation invariants */
 
 /* Rotation-invariant features of a signature (Sect. 1: under a rotation Q of

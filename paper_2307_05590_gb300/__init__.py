@@ -24,7 +24,7 @@ __all__ = [
     "mrom_plan_create", "mrom_plan_sweep", "mrom_plan_destroy", "mrom_tune", "mrom_sweep_noalloc",
     "FullOrder", "mrom_project", "mrom_rom_get", "mrom_adapt", "mrom_sweep_vjp", "MromSweep", "signature",
     "mrom_sweep_mixed", "mrom_project_dirs", "mrom_invariants", "mrom_fp64_peak", "mrom_static_solve", "static_solver_for", "PermeabilityData", "mrom_project_mu",
-    "mrom_rom_mu_state", "mrom_fom_solve", "PackedDictionary", "mrom_sweep_host",
+    "mrom_rom_mu_state", "mrom_fom_solve", "PackedDictionary", "mrom_sweep_host", "mrom_tune_pencil",
 ]
 
 
@@ -395,6 +395,14 @@ def mrom_tune(h: Handle, objs, n_w: int) -> int:
     """Pick the fastest sweep launch configuration for this batch; returns its index."""
     chosen = ctypes.c_int32(-1)
     _abi.check(lib().mrom_tune(h.ptr, _rom_array(objs), len(objs), int(n_w), ctypes.byref(chosen)), h.ptr)
+    return int(chosen.value)
+
+
+def mrom_tune_pencil(h: Handle, objs, n_w: int) -> int:
+    """mrom_tune_pencil: picks the pencil sweep's frequency groups per task (8, 4, 2 or 1) by
+    timing; returns the choice (the handle's cap for later plans)."""
+    chosen = ctypes.c_int32(0)
+    _abi.check(lib().mrom_tune_pencil(h.ptr, _rom_array(objs), len(objs), int(n_w), ctypes.byref(chosen)), h.ptr)
     return int(chosen.value)
 
 

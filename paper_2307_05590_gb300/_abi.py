@@ -21,6 +21,7 @@ EXPORTS = [
     "mrom_plan_timing", "mrom_rom_from_reduced_batch", "mrom_invariants", "mrom_project_mu",
     "mrom_rom_static_rank", "mrom_rom_mu_state", "mrom_fom_solve", "mrom_rom_from_packed", "mrom_rom_free_batch",
     "mrom_fp64_peak", "mrom_static_solve", "mrom_plan_sweep_invariants", "mrom_sweep_host",
+    "mrom_tune_pencil",
 ]
 
 
@@ -159,6 +160,7 @@ def _declare(L):
         "mrom_plan_sweep": (ctypes.c_int, [vp, dp, i32, dp, dp, dp]),
         "mrom_plan_destroy": (ctypes.c_int, [vp]),
         "mrom_tune": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, i32, ctypes.POINTER(i32)]),
+        "mrom_tune_pencil": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, i32, ctypes.POINTER(i32)]),
         "mrom_sweep_noalloc": (ctypes.c_int, [vp, ctypes.POINTER(vp), i32, dp, i32, i32, dp, dp, dp]),
         "mrom_project": (ctypes.c_int, [vp, ctypes.POINTER(mrom_fom), vp, i64, i32, ctypes.c_double, i32, vp, i32,
                                         ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),

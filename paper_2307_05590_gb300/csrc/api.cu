@@ -539,6 +539,71 @@ extern "C" mrom_status mrom_certificate(mrom_handle h, const mrom_rom_t* roms, i
   return mrom_sweep(h, roms, n_obj, omega, n_w, omega_stride, nullptr, nullptr, nullptr, nullptr, Delta);
 }
 
+extern "C" mrom_status mrom_tune_pencil(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int32_t n_w,
+                                        int32_t* groups) {
+  if (!h) return MROM_EINVAL;
+  if (!roms || n_obj < 1 || n_w < 1) return fail(h, MROM_EINVAL, "mrom_tune_pencil: bad arguments");
+  for (int o = 0; o < n_obj; ++o)
+    if (!roms[o] || roms[o]->ctx != h) return fail(h, MROM_EINVAL, "mrom_tune_pencil: invalid object");
+  cudaSetDevice(h->device);
+  // a sample spread over the batch: up to 2000 objects and 2048 frequencies (the sweep's balance
+  // over the SMs depends on the batch, so a small sample can prefer a mapping that loses on the
+  // whole batch)
+  const int ns = std::min<int>(n_obj, 2000), nw = std::min<int>(n_w, 2048);
+  std::vector<mrom_rom_t> sample(ns);
+  for (int k = 0; k < ns; ++k) sample[k] = roms[(int64_t)k * n_obj / ns];
+  std::vector<double> om(nw);
+  for (int k = 0; k < nw; ++k) om[k] = std::pow(10.0, 1.0 + 7.0 * k / std::max(1, nw - 1));
+  const size_t out = (size_t)ns * nw * 9;
+  double* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, (3 * out + nw) * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(h, e, "mrom_tune_pencil: scratch allocation");
+  double* d_om = buf + 3 * out;
+  e = cudaMemcpyAsync(d_om, om.data(), nw * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  bool cert = true;
+  for (auto* r : sample) cert = cert && r->has_cert;
+  const int saved = h->pencil_fmax, saved_solver = h->solver;
+  h->solver = MROM_SOLVER_AUTO;
+  int best = -1;
+  float best_ms = 0.f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int F = 8; F >= 1 && e == cudaSuccess; F /= 2) {
+    h->pencil_fmax = F;
+    mrom_plan plan = nullptr;
+    if (mrom_plan_create(h, sample.data(), ns, nw, &plan) != MROM_OK) continue;
+    mrom_plan_sweep(plan, d_om, 0, buf, buf + out, cert ? buf + 2 * out : nullptr);  // warm-up
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the faster of two
+      cudaEventRecord(e0, h->stream);
+      mrom_plan_sweep(plan, d_om, 0, buf, buf + out, cert ? buf + 2 * out : nullptr);
+      cudaEventRecord(e1, h->stream);
+      e = cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      ms = rep == 0 ? t : std::min(ms, t);
+    }
+    if (best < 0 || ms < best_ms) {
+      best = F;
+      best_ms = ms;
+    }
+    mrom_plan_destroy(plan);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(h->stream);
+  cudaFree(buf);
+  h->solver = saved_solver;
+  if (e != cudaSuccess) {
+    h->pencil_fmax = saved;
+    return cuda_fail(h, e, "mrom_tune_pencil");
+  }
+  h->pencil_fmax = best < 0 ? saved : best;
+  if (groups) *groups = h->pencil_fmax;
+  return mrom_synchronize(h);
+}
+
 extern "C" mrom_status mrom_tune(mrom_handle h, const mrom_rom_t* roms, int32_t n_obj, int32_t n_w,
                                  int32_t* chosen) {
   if (!h) return MROM_EINVAL;

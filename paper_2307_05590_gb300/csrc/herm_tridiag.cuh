@@ -46,10 +46,11 @@ __device__ __forceinline__ void tri_rc(int e, int& i, int& j) {
 // phases D_0 = 1, D_{k+1} = D_k e_k / |e_k|, which make D^H T D real with off-diagonal
 // |e_k|.  Output: Q = Q1 D (r x r row-major), sd = diagonal of T, se = |e| (se[r-1] = 0).
 // Scratch: stau, salpha, sph (shared, r entries each), pv (r entries, any memory; may
-// alias Q's first row), red (NT/32 doubles).  All threads of the CTA call it.
+// alias Q's first row), red (NT/32 doubles), part (shared, NT entries).  All threads of the CTA
+// call it.
 template <int NT>
 __device__ void herm_tridiag(double2* H, int r, double2* Q, double* sd, double* se, double* stau, double2* salpha,
-                             double2* sph, double2* pv, double* red) {
+                             double2* sph, double2* pv, double* red, double2* part) {
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   for (int k = 0; k + 2 < r; ++k) {
@@ -142,11 +143,29 @@ __device__ void herm_tridiag(double2* H, int r, double2* Q, double* sd, double* 
     const double tau = stau[k];
     if (tau == 0.0) continue;
     const int m = r - k - 1;
-    // u_j = sum_i conj(v_i) Q[k+1+i][k+1+j], then Q_sub -= tau v u
-    for (int j = tid; j < m; j += NT) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int i = 0; i < m; ++i) s = cmacc(s, H[(k + 1 + i) * r + k], Q[(k + 1 + i) * r + (k + 1 + j)]);
-      sph[j] = make_double2(tau * s.x, tau * s.y);
+    // u_j = sum_i conj(v_i) Q[k+1+i][k+1+j], then Q_sub -= tau v u; with fewer columns than
+    // threads the i range is split into G slices summed separately, then in a fixed order
+    const int G = m <= NT ? min(8, NT / m) : 1;
+    if (G > 1) {
+      for (int idx = tid; idx < m * G; idx += NT) {
+        const int j = idx % m, g = idx / m;
+        const int i1 = (g + 1) * m / G;
+        double2 s = make_double2(0.0, 0.0);
+        for (int i = g * m / G; i < i1; ++i) s = cmacc(s, H[(k + 1 + i) * r + k], Q[(k + 1 + i) * r + (k + 1 + j)]);
+        part[idx] = s;
+      }
+      __syncthreads();
+      for (int j = tid; j < m; j += NT) {
+        double2 s = part[j];
+        for (int g = 1; g < G; ++g) s = make_double2(s.x + part[g * m + j].x, s.y + part[g * m + j].y);
+        sph[j] = make_double2(tau * s.x, tau * s.y);
+      }
+    } else {
+      for (int j = tid; j < m; j += NT) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int i = 0; i < m; ++i) s = cmacc(s, H[(k + 1 + i) * r + k], Q[(k + 1 + i) * r + (k + 1 + j)]);
+        sph[j] = make_double2(tau * s.x, tau * s.y);
+      }
     }
     __syncthreads();
     for (int idx = tid; idx < m * m; idx += NT) {

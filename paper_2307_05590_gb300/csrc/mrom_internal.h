@@ -126,6 +126,7 @@ struct mrom_ctx {
   int sweep_cfg = -1;             // launch configuration for sweeps (-1: default)
   int projection_precision = 0;   // MROM_FP64 or MROM_MIXED for mrom_project's K U and Gram products
   int solver = 0;                 // MROM_SOLVER_AUTO or MROM_SOLVER_LU for plans and sweeps
+  int pencil_fmax = 8;            // largest frequency-group count per pencil sweep task (1, 2, 4, 8)
   mrom_status pending = MROM_OK;  // host-detected asynchronous error
   std::string last_error;
   cudaStream_t aux[2] = {nullptr, nullptr};  // the pipelined host-buffer sweep's streams (lazily created)

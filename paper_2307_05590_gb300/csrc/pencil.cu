@@ -111,10 +111,10 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
                    const double* __restrict__ s_sigma, const double* __restrict__ s_mu, int* __restrict__ pen_ok,
                    double2* __restrict__ ws, size_t ws_elems, double gate, double kappa_max) {
   __shared__ double sd[MROM_MAX_R], se[MROM_MAX_R], stau[MROM_MAX_R];
-  __shared__ double2 salpha[MROM_MAX_R], sph[MROM_MAX_R];
+  __shared__ double2 salpha[MROM_MAX_R], sph[MROM_MAX_R], spart[kPT];
   __shared__ double red[kPW];
   __shared__ int s_task;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   double2* W0 = ws + (size_t)blockIdx.x * ws_elems;
 
   for (;;) {
@@ -225,27 +225,32 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
     // ---- 3. X = L^-1 K' (W0)  and  4. H = X L^-H (W1, lower then mirrored)
     double hn = 0.0;
     if (ok) {
-      // X = L^-1 K', stored conjugate-transposed: W0[j][i] = conj(X[i][j]); one warp per row i
-      // (one trip count per warp), lanes along j
-      for (int i = warp; i < r; i += kPW) {
-        for (int j = lane; j < r; j += 32) {
-          double2 s = make_double2(0.0, 0.0);
-          for (int k = 0; k <= i; ++k) s = cmac(s, W2[i * r + k], W1[k * r + j]);
-          W0[j * r + i] = make_double2(s.x, -s.y);
-        }
+      // X = L^-1 K', stored conjugate-transposed: W0[j][i] = conj(X[i][j]); one thread per (i, j),
+      // row by row (the threads of a warp share a row, so their trip counts agree)
+      for (int idx = tid; idx < rr; idx += kPT) {
+        const int i = idx / r, j = idx - (idx / r) * r;
+        double2 s = make_double2(0.0, 0.0);
+        for (int k = 0; k <= i; ++k) s = cmac(s, W2[i * r + k], W1[k * r + j]);
+        W0[j * r + i] = make_double2(s.x, -s.y);
       }
       __syncthreads();
       // H[i][j] = sum_{k <= j} X[i][k] conj(L^-1[j][k]) = conj(sum_k W0[k][i] L^-1[j][k]) for
-      // i >= j: one warp per column j, lanes along i; mirrored into the upper triangle
-      for (int j = warp; j < r; j += kPW) {
-        for (int i = j + lane; i < r; i += 32) {
-          double2 s = make_double2(0.0, 0.0);
-          for (int k = 0; k <= j; ++k) s = cmac(s, W0[k * r + i], W2[j * r + k]);
-          if (i == j) s.y = 0.0;
-          W1[i * r + j] = make_double2(s.x, -s.y);
-          W1[j * r + i] = s;
-          hn += (i == j ? 1.0 : 2.0) * (s.x * s.x + s.y * s.y);
-        }
+      // i >= j: one thread per entry of the lower triangle taken column by column (trip count
+      // j + 1 shared along a column); mirrored into the upper triangle
+      const int ntri = r * (r + 1) / 2;
+      for (int e = tid; e < ntri; e += kPT) {
+        // column j holds entries S(j) .. S(j + 1) - 1, S(j) = j r - j (j - 1) / 2
+        int j = (int)((2.0 * r + 1.0 - sqrt((2.0 * r + 1.0) * (2.0 * r + 1.0) - 8.0 * e)) * 0.5);
+        j = max(0, min(r - 1, j));
+        while (j > 0 && j * r - j * (j - 1) / 2 > e) --j;
+        while (j + 1 < r && (j + 1) * r - (j + 1) * j / 2 <= e) ++j;
+        const int i = j + (e - (j * r - j * (j - 1) / 2));
+        double2 s = make_double2(0.0, 0.0);
+        for (int k = 0; k <= j; ++k) s = cmac(s, W0[k * r + i], W2[j * r + k]);
+        if (i == j) s.y = 0.0;
+        W1[i * r + j] = make_double2(s.x, -s.y);
+        W1[j * r + i] = s;
+        hn += (i == j ? 1.0 : 2.0) * (s.x * s.x + s.y * s.y);
       }
     }
     hn = block_sum(hn, red);
@@ -254,16 +259,15 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
     // ---- 5.-7. Householder tridiagonalisation of H (W1), Z = Q1 D (W0), real tridiagonal (sd, se);
     // p of each Householder step lives in W0's first row (W0 is free until Q1 is formed)
     if (ok) {
-      hq::herm_tridiag<kPT>(W1, r, W0, sd, se, stau, salpha, sph, W0, red);
+      hq::herm_tridiag<kPT>(W1, r, W0, sd, se, stau, salpha, sph, W0, red, spart);
 
       // ---- 8. W = L^-H Z (per-object buffer): W[i][j] = sum_{k >= i} conj(Linv[k][i]) Z[k][j];
       // the real tridiagonal (sd, se) goes to the eigenproblem kernel, W to the finishing kernel
-      for (int i = warp; i < r; i += kPW) {  // one warp per row i, lanes along j
-        for (int j = lane; j < r; j += 32) {
-          double2 acc = make_double2(0.0, 0.0);
-          for (int k = i; k < r; ++k) acc = cmacc(acc, W2[k * r + i], W0[k * r + j]);
-          ps.W[i * r + j] = acc;
-        }
+      for (int idx = tid; idx < rr; idx += kPT) {  // one thread per (i, j), row by row
+        const int i = idx / r, j = idx - (idx / r) * r;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = i; k < r; ++k) acc = cmacc(acc, W2[k * r + i], W0[k * r + j]);
+        ps.W[i * r + j] = acc;
       }
       for (int k = tid; k < r; k += kPT) {
         pd.lam[k] = sd[k];
@@ -284,7 +288,7 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
 // (r x r, row-major) are left at the start of the object's workspace (ps.work: three r x r
 // float64 blocks).  A non-finite value
 // clears the object's pencil flag (it then takes the LU route).
-__global__ void __launch_bounds__(kPT)
+__global__ void __launch_bounds__(kPT, 3)
 pencil_dc_kernel(const int* __restrict__ order, int n_elig, const RomDev* __restrict__ objs,
                  const PencilDev* __restrict__ pens, const PencilScratch* __restrict__ scr,
                  int* __restrict__ pen_ok, int* __restrict__ counter) {
@@ -1161,8 +1165,9 @@ cudaError_t launch_pencil_prep(const RomDev* objs, const PencilDev* pens, const 
                                                   s_sigma, s_mu, pen_ok, ws, ws_elems, gate, kappa_max);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // the tridiagonal eigenproblems, one CTA per object (work counter: counters[6])
-  pencil_dc_kernel<<<grid, kPT, 0, stream>>>(order, n_elig, objs, pens, scr, pen_ok, counters + 6);
+  // the tridiagonal eigenproblems, one CTA per object (work counter: counters[6]); three CTAs per
+  // SM fill each other's barrier waits (the grid is two per SM for the other kernels)
+  pencil_dc_kernel<<<std::max(1, 3 * grid / 2), kPT, 0, stream>>>(order, n_elig, objs, pens, scr, pen_ok, counters + 6);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = pencil_finish_smem_bytes(rmax);
@@ -1247,7 +1252,7 @@ mrom_status pencil_tables_create(mrom_ctx* h, const std::vector<RomDev>& objs, i
   for (size_t k = 0; k < elig.size(); ++k) {
     const int o = elig[k], r = objs[o].r;
     // the forward sweep's task needs only its partial sums; the adjoint's holds the z tile too
-    int F = 8;
+    int F = std::max(1, std::min(8, h->pencil_fmax));
     while (F > 1 && (F > need || (!gram && pencil_vjp_smem_bytes(r, F) > budget))) F /= 2;
     spen[k] = 32 * F;
     pens[o].F = F;

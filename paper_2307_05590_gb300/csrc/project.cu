@@ -198,10 +198,11 @@ herm_eig_kernel(double2* __restrict__ A, int m, double2* __restrict__ Z, double*
   __shared__ double rc[MROM_MAX_SNAPSHOTS], rs[MROM_MAX_SNAPSHOTS];
   __shared__ double2 salpha[MROM_MAX_SNAPSHOTS], sph[MROM_MAX_SNAPSHOTS], pv[MROM_MAX_SNAPSHOTS];
   __shared__ double red[kEigThreads / 32];
+  __shared__ double2 part[kEigThreads];
   __shared__ int flags[4];
   if (threadIdx.x < 4) flags[threadIdx.x] = 0;
   __syncthreads();
-  hq::herm_tridiag<kEigThreads>(A, m, Z, sd, se, stau, salpha, sph, pv, red);
+  hq::herm_tridiag<kEigThreads>(A, m, Z, sd, se, stau, salpha, sph, pv, red, part);
   const bool ok = hq::ql_single<kEigThreads>(sd, se, m, Z, rc, rs, flags, 60);
   for (int i = threadIdx.x; i < m; i += kEigThreads) lam[i] = sd[i];
   if (threadIdx.x == 0 && !ok) atomicOr(status, kStatusTimeout);

@@ -304,6 +304,8 @@ def test_autotuner_picks_a_valid_configuration(mrom, handle):
     roms = [mrom.ReducedObject.from_workload(handle, o) for o in objs]
     cfg = mrom.mrom_tune(handle, roms, 60)
     assert cfg in (0, 1)
+    groups = mrom.mrom_tune_pencil(handle, roms, 300)
+    assert groups in (1, 2, 4, 8)
     wo = log_omegas(1e1, 1e8, 60)
     om = torch.as_tensor(wo, device="cuda")
     R = torch.empty((3, 60, 3, 3), dtype=torch.float64, device="cuda")
