@@ -5,10 +5,11 @@
 // A complex product is four real ones: with A = Ar + i Ai and B' = diag(w) B = Br + i Bi,
 //   Re G = Ar^T Br + Ai^T Bi,   Im G = Ar^T Bi - Ai^T Br,
 // so one real GEMM of [Ar Ai]^T (2 ma x rows) by [Br Bi] (rows x 2 mb) gives all four blocks.
-// Each real operand is split into two TF32 parts, x = x_hi + x_lo (x_hi = tf32(x),
-// x_lo = tf32(x - x_hi)), and a_hi b_hi + a_hi b_lo + a_lo b_hi is accumulated in FP32 in tensor
-// memory (three tcgen05.mma of kind::tf32 per product tile): products accurate to FP32's level
-// instead of TF32's 1e-3.  The rows are the reduction dimension (K of the MMA).
+// Each real operand is split into two parts, x = x_hi + x_lo (x_hi = tf32(x) rounded, x_lo =
+// x - x_hi exactly, of which the MMA reads the TF32 part), and a_hi b_hi + a_hi b_lo + a_lo b_hi
+// is accumulated in FP32 in tensor memory (three tcgen05.mma of kind::tf32 per product tile):
+// products accurate to about 2^-20 instead of TF32's 1e-3.  The rows are the reduction
+// dimension (K of the MMA).
 //
 // Per CTA (one per SM, 16 warps, a contiguous range of rows): chunks of 16 rows of A, B and w are copied
 // into shared memory by the bulk-copy engine (cp.async.bulk, completion on an mbarrier), two raw
@@ -36,10 +37,8 @@ namespace mrom {
 namespace {
 
 constexpr int kTT = 512;           // threads per CTA (16 warps)
-constexpr int kTK = 16;            // rows (MMA K) per chunk
 constexpr int kMaxHalf = 112;      // ma, mb <= 112, so 2 ma, 2 mb <= 224
 constexpr long long kSpinLimit = 1LL << 26;  // try_wait polls before a wait gives up
-constexpr int kFlush = 8;          // chunks (128 rows) per FP32 accumulation segment
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -85,19 +84,14 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return r;
 }
 
-// x = hi + lo with both parts TF32
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = to_tf32(x);
-  lo = to_tf32(x - __uint_as_float(hi));
-}
-
-// Shared-memory matrix descriptor of a K-major operand without swizzle (see the file comment).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  constexpr uint64_t kLbo = 128, kSbo = 512;
+// Shared-memory matrix descriptor of a K-major operand without swizzle (see the file comment):
+// leading byte offset 128 (next core matrix along K), stride byte offset sbo (next 8-row group).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo) {
+  constexpr uint64_t kLbo = 128;
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);
   d |= (uint64_t)((kLbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((kSbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;  // descriptor version of this architecture
   return d;                // base offset 0, layout: no swizzle
 }
@@ -142,40 +136,43 @@ struct TcGramArgs {
   const float2* B;   // n x mb, row-major (unused when same_ab)
   const float* w;    // n weights of B's rows, or null
   int64_t n;
-  int ma, mb, mpad, npad, same_ab;
+  int ma, mb, mpad, npad, same_ab, nraw;  // nraw: raw stages (bulk copies in flight), 2 or 3
   int64_t rows_per_cta;
   double* part;      // [gridDim.x][mpad][npad]
   int* status;
 };
 
-// byte offset of element (row, k) in a K-major operand tile of K = 16 (see the file comment)
+constexpr int kMaxRaw = 3;  // raw stages at most
+
+// byte offset of element (row, k) in a K-major operand tile of K = KT (see the file comment:
+// core matrices of 8 rows x 4 k, KT / 4 of them side by side per 8-row group)
+template <int KT>
 __device__ __forceinline__ uint32_t op_off(int row, int k) {
-  return (uint32_t)((row >> 3) * 512 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+  return (uint32_t)((row >> 3) * (32 * KT) + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
 }
 
-__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, int row, int k, float x) {
-  uint32_t h, l;
-  split_tf32(x, h, l);
-  const uint32_t o = op_off(row, k);
-  *reinterpret_cast<uint32_t*>(hi + o) = h;
-  *reinterpret_cast<uint32_t*>(lo + o) = l;
-}
-
+// KT rows (the MMA's K) per chunk; g.nraw chunks' bulk copies in flight, two operand stages.
+// NB > 0 (one M tile, npad <= 32 NB): each thread keeps its share of the float64 partial block
+// in registers (NB blocks of 8 columns) and stores it once at the end; NB = 0: the partial
+// block is accumulated in global memory at every flush.
+template <int KT, int NB>
 __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
+  constexpr int kFlush = 128 / KT;  // chunks per FP32 accumulation segment (128 rows)
+  constexpr int kKG = KT / 4;       // core matrices along K per 8-row group
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ma = g.ma, mb = g.mb, mpad = g.mpad, npad = g.npad;
+  const int ma = g.ma, mb = g.mb, mpad = g.mpad, npad = g.npad, NR = g.nraw;
   const int mtiles = mpad / 128;
   // ---- shared memory carve-up
-  uint64_t* raw_full = reinterpret_cast<uint64_t*>(smem);       // 2 barriers
-  uint64_t* op_free = raw_full + 2;                              // 2 barriers
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 32);
-  const uint32_t a_raw_b = 128u * ma, b_raw_b = g.same_ab ? 0u : 128u * mb, w_raw_b = 64u;
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(smem);       // kMaxRaw barriers
+  uint64_t* op_free = raw_full + kMaxRaw;                        // 2 barriers
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 64);
+  const uint32_t a_raw_b = 8u * KT * ma, b_raw_b = g.same_ab ? 0u : 8u * KT * mb, w_raw_b = 4u * KT;
   const uint32_t raw_stage_b = (a_raw_b + b_raw_b + w_raw_b + 127u) & ~127u;
   unsigned char* raw0 = smem + 128;
-  const uint32_t a_op_b = 64u * mpad, b_op_b = 64u * npad;
+  const uint32_t a_op_b = 4u * KT * mpad, b_op_b = 4u * KT * npad;
   const uint32_t op_stage_b = 2u * a_op_b + 2u * b_op_b;
-  unsigned char* op0 = raw0 + 2 * raw_stage_b;
+  unsigned char* op0 = raw0 + NR * raw_stage_b;
   auto raw_a = [&](int s) { return reinterpret_cast<float2*>(raw0 + s * raw_stage_b); };
   auto raw_b = [&](int s) { return reinterpret_cast<float2*>(raw0 + s * raw_stage_b + a_raw_b); };
   auto raw_w = [&](int s) { return reinterpret_cast<float*>(raw0 + s * raw_stage_b + a_raw_b + b_raw_b); };
@@ -186,13 +183,13 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
 
   const int64_t row0 = (int64_t)blockIdx.x * g.rows_per_cta;
   const int64_t row1 = min(g.n, row0 + g.rows_per_cta);
-  const int nchunks = row1 > row0 ? (int)((row1 - row0 + kTK - 1) / kTK) : 0;
-  auto chunk_rows = [&](int c) { return (int)min((int64_t)kTK, row1 - (row0 + (int64_t)c * kTK)); };
+  const int nchunks = row1 > row0 ? (int)((row1 - row0 + KT - 1) / KT) : 0;
+  auto chunk_rows = [&](int c) { return (int)min((int64_t)KT, row1 - (row0 + (int64_t)c * KT)); };
   const int ncols = mtiles * npad <= 256 ? 256 : 512;
 
   // ---- set-up: barriers, tensor memory, zeroed operand tiles (their padding rows stay zero)
   if (tid == 0) {
-    for (int k = 0; k < 4; ++k) mbar_init(raw_full + k, 1);
+    for (int k = 0; k < kMaxRaw + 2; ++k) mbar_init(raw_full + k, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -212,9 +209,9 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
   // thread 0's view of the asynchronous work in flight (for the error path)
   int tma_issued = -1;     // highest chunk whose bulk copies were issued
   int mma_last = -1;       // highest chunk whose MMAs were committed
-  auto issue_copy = [&](int c) {  // thread 0: bulk copies of a full chunk into raw stage c & 1
-    const int s = c & 1;
-    const int64_t r = row0 + (int64_t)c * kTK;
+  auto issue_copy = [&](int c) {  // thread 0: bulk copies of a full chunk into raw stage c % NR
+    const int s = c % NR;
+    const int64_t r = row0 + (int64_t)c * KT;
     mbar_expect_tx(raw_full + s, a_raw_b + b_raw_b + (g.w ? w_raw_b : 0u));
     bulk_g2s(raw_a(s), g.A + r * ma, a_raw_b, raw_full + s);
     if (!g.same_ab) bulk_g2s(raw_b(s), g.B + r * mb, b_raw_b, raw_full + s);
@@ -222,28 +219,44 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
     tma_issued = c;
   };
   if (tid == 0) {
-    for (int c = 0; c < 2 && c < nchunks; ++c)
-      if (chunk_rows(c) == kTK) issue_copy(c);
+    for (int c = 0; c < NR && c < nchunks; ++c)
+      if (chunk_rows(c) == KT) issue_copy(c);
   }
 
   // this CTA's partial block (float64) += (or, on the first segment, =) the accumulator; every
-  // warp reads its lane quarter (warp % 4) of each M tile, the two warp halves alternate 8-column
+  // warp reads its lane quarter (warp % 4) of each M tile, the warp sets alternate 8-column
   // blocks.  With no chunk the block is set to zero without touching tensor memory.
   const int nchunks_cta = nchunks;
+  double racc[NB > 0 ? 8 * NB : 1];
+#pragma unroll
+  for (int k = 0; k < (NB > 0 ? 8 * NB : 1); ++k) racc[k] = 0.0;
   auto flush = [&](bool first) {
     const int q = warp & 3, cg = warp >> 2;
     constexpr int kCG = kTT / 128;  // warp sets sharing the lane quarters
     double* out = g.part + (size_t)blockIdx.x * mpad * npad;
-    for (int t = 0; t < mtiles; ++t) {
-      const int m = t * 128 + q * 32 + lane;
-      for (int cb = cg * 8; cb < npad; cb += 8 * kCG) {
-        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (nchunks_cta > 0) tmem_ld8(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * npad + cb), v);
-        // partial block stored [column][row]: the 32 lanes of a warp write 32 consecutive rows
+    if constexpr (NB > 0) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          double* o = out + (size_t)(cb + k) * mpad + m;
-          *o = first ? (double)v[k] : *o + (double)v[k];
+      for (int b = 0; b < NB; ++b) {
+        const int cb = cg * 8 + b * 8 * kCG;
+        if (cb < npad && nchunks_cta > 0) {
+          float v[8];
+          tmem_ld8(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)cb, v);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) racc[b * 8 + k] += (double)v[k];
+        }
+      }
+    } else {
+      for (int t = 0; t < mtiles; ++t) {
+        const int m = t * 128 + q * 32 + lane;
+        for (int cb = cg * 8; cb < npad; cb += 8 * kCG) {
+          float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          if (nchunks_cta > 0) tmem_ld8(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * npad + cb), v);
+          // partial block stored [column][row]: the 32 lanes of a warp write 32 consecutive rows
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            double* o = out + (size_t)(cb + k) * mpad + m;
+            *o = first ? (double)v[k] : *o + (double)v[k];
+          }
         }
       }
     }
@@ -252,72 +265,79 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
   bool failed = false;
   int c = 0;
   for (; c < nchunks; ++c) {
-    const int s = c & 1;
+    const int s = c & 1, sr = c % NR;
+    const uint32_t raw_par = (uint32_t)((c / NR) & 1);
     const int rows = chunk_rows(c);
-    const bool full = rows == kTK;
+    const bool full = rows == KT;
     // thread 0 polls (bounded); after the barrier every other thread observes the completed
     // phases with one try_wait each, which makes the copied bytes visible to it
     bool ok = true;
     if (tid == 0) {
-      if (full) ok = mbar_wait(raw_full + s, (uint32_t)((c >> 1) & 1));
+      if (full) ok = mbar_wait(raw_full + sr, raw_par);
       if (c >= 2 && ok) ok = mbar_wait(op_free + s, (uint32_t)(((c - 2) >> 1) & 1));
     }
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
     }
-    if (tid != 0 && full) mbar_wait(raw_full + s, (uint32_t)((c >> 1) & 1));
-    // ---- convert chunk c into the operand tiles of stage s
-    const int64_t r0 = row0 + (int64_t)c * kTK;
-    const int nb = g.same_ab ? ma : mb;
-    // one core matrix (8 operand rows x 4 k) per warp step: lane -> (row 8 g + lane / 4,
-    // k = 4 q + lane % 4), so the 32 lanes store one contiguous 128-byte core matrix (no bank
-    // conflicts); A's units first, then B's
-    const int ga = (ma + 7) >> 3, gb = (mb + 7) >> 3;
-    const int units = 4 * (ga + gb);
-    const int ml = lane >> 2, kl = lane & 3;
+    if (tid != 0 && full) mbar_wait(raw_full + sr, raw_par);
+    // ---- convert chunk c into the operand tiles of stage s: one item per (complex column,
+    // quad of 4 rows k), A's items first, then B's; an item reads 4 raw values (lanes along the
+    // columns: conflict-free) and stores the hi and lo parts of its real and imaginary rows as
+    // 16-byte vectors (4 consecutive k of one core-matrix row)
+    const int64_t r0 = row0 + (int64_t)c * KT;
+    const float2* ra = raw_a(sr);
+    const float2* rb = g.same_ab ? ra : raw_b(sr);
+    const float* rw = raw_w(sr);
     unsigned char *ah = a_hi(s), *al = a_lo(s), *bh = b_hi(s), *bl = b_lo(s);
-    for (int u = warp; u < units; u += kTT / 32) {
-      if (u < 4 * ga) {
-        const int m = 8 * (u >> 2) + ml, kk = 4 * (u & 3) + kl;
-        if (m < ma) {
-          float2 a = make_float2(0.f, 0.f);
-          if (full) a = raw_a(s)[kk * ma + m];
-          else if (kk < rows) a = g.A[(r0 + kk) * ma + m];
-          put_split(ah, al, m, kk, a.x);
-          put_split(ah, al, ma + m, kk, a.y);
+    const int na = ma * kKG, nitems = na + mb * kKG;
+    for (int it = tid; it < nitems; it += kTT) {
+      const bool isA = it < na;
+      const int jt = isA ? it : it - na;
+      const int mc = isA ? ma : mb;
+      const int m = jt % mc, k0 = 4 * (jt / mc);
+      const float2* src = isA ? ra : rb;
+      const float2* gsrc = (isA || g.same_ab) ? g.A : g.B;
+      uint32_t hre[4], lre[4], him[4], lim[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int kk = k0 + j;
+        float2 v = make_float2(0.f, 0.f);
+        float wt = 1.f;
+        if (full) {
+          v = src[kk * mc + m];
+          if (!isA && g.w) wt = rw[kk];
+        } else if (kk < rows) {
+          v = gsrc[(r0 + kk) * mc + m];
+          if (!isA && g.w) wt = g.w[r0 + kk];
         }
-      } else {
-        const int v = u - 4 * ga;
-        const int n = 8 * (v >> 2) + ml, kk = 4 * (v & 3) + kl;
-        if (n < mb) {
-          float2 b = make_float2(0.f, 0.f);
-          float wt = 1.f;
-          if (full) {
-            b = g.same_ab ? raw_a(s)[kk * nb + n] : raw_b(s)[kk * nb + n];
-            if (g.w) wt = raw_w(s)[kk];
-          } else if (kk < rows) {
-            b = g.same_ab ? g.A[(r0 + kk) * nb + n] : g.B[(r0 + kk) * nb + n];
-            if (g.w) wt = g.w[r0 + kk];
-          }
-          put_split(bh, bl, n, kk, wt * b.x);
-          put_split(bh, bl, mb + n, kk, wt * b.y);
-        }
+        const float x = wt * v.x, y = wt * v.y;
+        hre[j] = to_tf32(x);  // hi: rounded to TF32; lo: the exact remainder (the MMA reads
+        him[j] = to_tf32(y);  // its TF32 part)
+        lre[j] = __float_as_uint(x - __uint_as_float(hre[j]));
+        lim[j] = __float_as_uint(y - __uint_as_float(him[j]));
       }
+      unsigned char* hi = isA ? ah : bh;
+      unsigned char* lo = isA ? al : bl;
+      const uint32_t ore = op_off<KT>(m, k0), oim = op_off<KT>(mc + m, k0);
+      *reinterpret_cast<uint4*>(hi + ore) = make_uint4(hre[0], hre[1], hre[2], hre[3]);
+      *reinterpret_cast<uint4*>(lo + ore) = make_uint4(lre[0], lre[1], lre[2], lre[3]);
+      *reinterpret_cast<uint4*>(hi + oim) = make_uint4(him[0], him[1], him[2], him[3]);
+      *reinterpret_cast<uint4*>(lo + oim) = make_uint4(lim[0], lim[1], lim[2], lim[3]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();  // raw stage s consumed, operand stage s written
+    __syncthreads();  // raw stage sr consumed, operand stage s written
     if (tid == 0) {
-      if (c + 2 < nchunks && chunk_rows(c + 2) == kTK) issue_copy(c + 2);
+      if (c + NR < nchunks && chunk_rows(c + NR) == KT) issue_copy(c + NR);
       tc_fence_after();
       const uint32_t idesc = instr_desc(128, npad);
       const uint32_t pa[3] = {smem_u32(ah), smem_u32(ah), smem_u32(al)};
       const uint32_t pb[3] = {smem_u32(bh), smem_u32(bl), smem_u32(bh)};
-      for (int ks = 0; ks < kTK / 8; ++ks)
+      for (int ks = 0; ks < KT / 8; ++ks)
         for (int t = 0; t < mtiles; ++t)
           for (int p = 0; p < 3; ++p) {
-            const uint64_t ad = smem_desc(pa[p] + (uint32_t)t * 8192u + (uint32_t)ks * 256u);
-            const uint64_t bd = smem_desc(pb[p] + (uint32_t)ks * 256u);
+            const uint64_t ad = smem_desc(pa[p] + (uint32_t)t * (512u * KT) + (uint32_t)ks * 256u, 32u * KT);
+            const uint64_t bd = smem_desc(pb[p] + (uint32_t)ks * 256u, 32u * KT);
             mma_tf32(taddr + (uint32_t)(t * npad), ad, bd, idesc, (c % kFlush > 0 || ks > 0 || p > 0) ? 1u : 0u);
           }
       mma_commit(op_free + s);
@@ -339,11 +359,24 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
     }
   }
   if (!failed && nchunks == 0) flush(true);  // zeros for an empty range
+  if constexpr (NB > 0) {  // the register block, once ([column][row] as above)
+    const int q = warp & 3, cg = warp >> 2;
+    constexpr int kCG = kTT / 128;
+    double* out = g.part + (size_t)blockIdx.x * mpad * npad;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int cb = cg * 8 + b * 8 * kCG;
+      if (cb < npad) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) out[(size_t)(cb + k) * mpad + q * 32 + lane] = racc[b * 8 + k];
+      }
+    }
+  }
   if (failed) {
     if (tid == 0) {
       atomicOr(g.status, kStatusTimeout);
       // bounded waits for this CTA's own copies and MMAs still in flight
-      for (int k = c; k <= tma_issued; ++k) mbar_wait(raw_full + (k & 1), (uint32_t)((k >> 1) & 1));
+      for (int k = c; k <= tma_issued; ++k) mbar_wait(raw_full + (k % NR), (uint32_t)((k / NR) & 1));
       if (mma_last >= 0) mbar_wait(op_free + (mma_last & 1), (uint32_t)((mma_last >> 1) & 1));
     }
   }
@@ -373,10 +406,11 @@ __global__ void gram_tc_reduce_kernel(const double* __restrict__ part, int nblk,
 
 }  // namespace
 
-size_t tall_gram_tc_smem(int ma, int mb, bool same_ab) {
+// dynamic shared memory of a launch with KT rows per chunk and nraw raw stages
+size_t tall_gram_tc_smem(int ma, int mb, bool same_ab, int kt, int nraw) {
   const int mpad = 128 * ((2 * ma + 127) / 128), npad = 16 * ((2 * mb + 15) / 16);
-  const size_t raw_stage = ((size_t)128 * ma + (same_ab ? 0 : (size_t)128 * mb) + 64 + 127) & ~(size_t)127;
-  return 128 + 2 * raw_stage + 2 * (2 * (size_t)64 * mpad + 2 * (size_t)64 * npad);
+  const size_t raw_stage = ((size_t)8 * kt * ma + (same_ab ? 0 : (size_t)8 * kt * mb) + 4 * kt + 127) & ~(size_t)127;
+  return 128 + nraw * raw_stage + 2 * (2 * (size_t)4 * kt * mpad + 2 * (size_t)4 * kt * npad);
 }
 
 cudaError_t tall_gram_tc(mrom_ctx* h, const float2* A, int ma, const float2* B, int mb, const float* w, int64_t n,
@@ -384,20 +418,44 @@ cudaError_t tall_gram_tc(mrom_ctx* h, const float2* A, int ma, const float2* B, 
   if (ma < 1 || mb < 1 || ma > kMaxHalf || mb > kMaxHalf || n < 1) return cudaErrorInvalidValue;
   const bool same = (A == B) && (ma == mb);
   const int mpad = 128 * ((2 * ma + 127) / 128), npad = 16 * ((2 * mb + 15) / 16);
-  // at least 116 KB so that one CTA runs per SM (each holds up to 512 tensor-memory columns)
-  const size_t smem = std::max<size_t>(tall_gram_tc_smem(ma, mb, same), 116 * 1024);
-  if (smem > h->smem_optin) return cudaErrorInvalidValue;
-  const int64_t chunks = (n + kTK - 1) / kTK;
+  // the largest chunk and the most copies in flight that fit: 32 rows and three raw stages keep
+  // enough bytes in flight per SM to cover the memory latency at the HBM rate
+  int kt = 0, nraw = 0;
+  size_t smem = 0;
+  for (int cand = 0; cand < 4 && kt == 0; ++cand) {
+    const int k = cand < 2 ? 32 : 16, nr = (cand & 1) ? 2 : 3;
+    const size_t b = std::max<size_t>(tall_gram_tc_smem(ma, mb, same, k, nr), 116 * 1024);
+    if (b <= h->smem_optin) {
+      kt = k;
+      nraw = nr;
+      smem = b;  // at least 116 KB so that one CTA runs per SM (each holds up to 512 tensor-memory columns)
+    }
+  }
+  if (kt == 0) return cudaErrorInvalidValue;
+  const int64_t chunks = (n + kt - 1) / kt;
   const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(h->num_sms, chunks));
-  const int64_t per = (chunks + nblk - 1) / nblk * kTK;
+  const int64_t per = (chunks + nblk - 1) / nblk * kt;
   DevBuf part;
   cudaError_t e = cudaMalloc(&part.p, (size_t)nblk * mpad * npad * sizeof(double));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  TcGramArgs a{A, same ? nullptr : B, w, n, ma, mb, mpad, npad, same ? 1 : 0, per, static_cast<double*>(part.p),
+  TcGramArgs a{A, same ? nullptr : B, w, n, ma, mb, mpad, npad, same ? 1 : 0, nraw, per, static_cast<double*>(part.p),
                h->d_status};
-  gram_tc_kernel<<<nblk, kTT, smem, h->stream>>>(a);
-  e = cudaGetLastError();
+  // the float64 partial block in registers when it is one M tile of at most 128 columns
+  const int nb = mpad == 128 ? (npad + 31) / 32 : 0;
+  auto launch = [&](auto kernel) {
+    cudaError_t x = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (x == cudaSuccess) kernel<<<nblk, kTT, smem, h->stream>>>(a);
+    return x;
+  };
+  if (kt == 32)
+    e = nb == 1 ? launch(gram_tc_kernel<32, 1>) : nb == 2 ? launch(gram_tc_kernel<32, 2>)
+        : nb == 3 ? launch(gram_tc_kernel<32, 3>) : nb == 4 ? launch(gram_tc_kernel<32, 4>)
+                  : launch(gram_tc_kernel<32, 0>);
+  else
+    e = nb == 1 ? launch(gram_tc_kernel<16, 1>) : nb == 2 ? launch(gram_tc_kernel<16, 2>)
+        : nb == 3 ? launch(gram_tc_kernel<16, 3>) : nb == 4 ? launch(gram_tc_kernel<16, 4>)
+                  : launch(gram_tc_kernel<16, 0>);
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   gram_tc_reduce_kernel<<<std::max(1, std::min(1024, (ma * mb + 255) / 256)), 256, 0, h->stream>>>(
       static_cast<double*>(part.p), nblk, ma, mb, mpad, npad, G, ldg);

@@ -125,6 +125,54 @@ gram_partial_kernel(const double2* __restrict__ A, int64_t rsA, int64_t csA, int
     }
 }
 
+// Gram of at most 4 x 4 columns (e.g. c00 = O^T C O): per thread a register block over a
+// grid-stride range of rows, then a fixed-order reduction over the CTA into part[block][ma x mb].
+constexpr int kGS = 4;
+__global__ void __launch_bounds__(256)
+gram_small_kernel(const double2* __restrict__ A, int64_t rsA, int64_t csA, int ma, const double2* __restrict__ B,
+                  int64_t rsB, int64_t csB, int mb, const double* __restrict__ w, int wmode, int64_t n,
+                  double2* __restrict__ part) {
+  __shared__ double2 red[8][kGS * kGS];
+  double2 acc[kGS][kGS];
+#pragma unroll
+  for (int i = 0; i < kGS; ++i)
+#pragma unroll
+    for (int j = 0; j < kGS; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (int64_t row = (int64_t)blockIdx.x * 256 + threadIdx.x; row < n; row += (int64_t)gridDim.x * 256) {
+    double2 a[kGS], b[kGS];
+    const double s = wmode == 0 ? 1.0 : (wmode == 1 ? w[row] : 1.0 / w[row]);
+#pragma unroll
+    for (int i = 0; i < kGS; ++i) {
+      a[i] = i < ma ? A[row * rsA + i * csA] : make_double2(0.0, 0.0);
+      const double2 v = i < mb ? B[row * rsB + i * csB] : make_double2(0.0, 0.0);
+      b[i] = make_double2(s * v.x, s * v.y);
+    }
+#pragma unroll
+    for (int i = 0; i < kGS; ++i)
+#pragma unroll
+      for (int j = 0; j < kGS; ++j) acc[i][j] = c_conj_mac(acc[i][j], a[i], b[j]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < kGS; ++i)
+#pragma unroll
+    for (int j = 0; j < kGS; ++j) {
+      double2 v = acc[i][j];
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      }
+      if (lane == 0) red[warp][i * kGS + j] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < ma * mb) {
+    const int i = threadIdx.x / mb, j = threadIdx.x - (threadIdx.x / mb) * mb;
+    double2 v = make_double2(0.0, 0.0);
+    for (int k = 0; k < 8; ++k) v = make_double2(v.x + red[k][i * kGS + j].x, v.y + red[k][i * kGS + j].y);
+    part[(size_t)blockIdx.x * ma * mb + threadIdx.x] = v;
+  }
+}
+
 __global__ void __launch_bounds__(256)
 spmm_csr_f32_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                     const float* __restrict__ val, int64_t n, const float2* __restrict__ U, int r,
@@ -456,6 +504,22 @@ int gram_tile(int m) {
 cudaError_t tall_gram(mrom_ctx* h, const double2* A, int64_t rsA, int64_t csA, int ma, const double2* B,
                       int64_t rsB, int64_t csB, int mb, const double* w, int wmode, int64_t n, bool hermitian,
                       double2* G, int64_t ldg) {
+  if (ma <= kGS && mb <= kGS) {  // a few columns: one register block per thread
+    const int64_t nb = std::max<int64_t>(1, std::min<int64_t>(4LL * h->num_sms, (n + 255) / 256));
+    DevBuf part;
+    cudaError_t e = cudaMalloc(&part.p, (size_t)nb * ma * mb * sizeof(double2));
+    if (e != cudaSuccess) return e;
+    gram_small_kernel<<<(unsigned)nb, 256, 0, h->stream>>>(A, rsA, csA, ma, B, rsB, csB, mb, w, wmode, n,
+                                                          static_cast<double2*>(part.p));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    gram_reduce_kernel<<<1, 256, 0, h->stream>>>(static_cast<double2*>(part.p), (int)nb, ma, mb, hermitian ? 1 : 0, 1,
+                                                G, ldg);
+    e = cudaGetLastError();
+    h->launches += 2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // part is freed on return
+    return e;
+  }
   const int Ta = gram_tile(hermitian ? std::max(ma, mb) : ma), Tb = hermitian ? Ta : gram_tile(mb);
   const int ta = (ma + Ta - 1) / Ta, tb = (mb + Tb - 1) / Tb;
   std::vector<int2> tl;
