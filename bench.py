@@ -227,7 +227,7 @@ def project_flops(n: int, nnz: int, m: int, r: int, cert: bool = True, per_dir: 
     return fl
 
 
-def measure_projection(m, h, n_grid: int = 96, n_s: int = 32, n_out: int = 10000):
+def measure_projection(m, h, n_grid: int = 96, n_s: int = 32, n_out: int = 10000, snapshots: str = "device"):
     """The 96^3 plain-vs-mixed configuration: a mu_r = 32, sigma = 1.5e6 cube on the n_grid^3 FIT
     grid (N = 2.6M) with the static correction theta~^(0) solved on the device (mrom_static_solve),
     n_s full-order snapshots per direction at log-spaced omega in [1e1, 1e8] solved on the device
@@ -241,24 +241,35 @@ def measure_projection(m, h, n_grid: int = 96, n_s: int = 32, n_out: int = 10000
     from workloads import CUBE_C2, fit_problem, log_omegas
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    solver = m.static_solver_for(h, n_grid)
-    p = fit_problem(n_grid, CUBE_C2, static_solver=solver)
+    if snapshots == "device":
+        solver = m.static_solver_for(h, n_grid)
+        p = fit_problem(n_grid, CUBE_C2, static_solver=solver)
+    else:  # synthetic snapshot columns: the projection alone (no static or full-order solves)
+        solver = None
+        p = fit_problem(n_grid, CUBE_C2, static=False)
     t_static = time.perf_counter() - t0
     fom = m.FullOrder.from_fit(p)
     ws = log_omegas(1e1, 1e8, n_s)
     per_call = max(1, 48 // 3)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    Qs, its = [], []
-    for k in range(0, n_s, per_call):
-        Q, it, _ = m.mrom_fom_solve(h, fom, ws[k:k + per_call], tol=1e-12)
-        Qs.append(Q)
-        its.append(int(it.max()))
-    Q = torch.cat(Qs)
+    its = []
+    if snapshots == "device":
+        Qs = []
+        for k in range(0, n_s, per_call):
+            Q, it, _ = m.mrom_fom_solve(h, fom, ws[k:k + per_call], tol=1e-12)
+            Qs.append(Q)
+            its.append(int(it.max()))
+        Q = torch.cat(Qs)
+        Dd = Q.view(n_s, 3, p.N).transpose(0, 1).reshape(3 * n_s, p.N).contiguous()  # direction-major
+        del Q, Qs
+    else:
+        from workloads.snapshots import synthetic_snapshot_matrix
+        Dsyn = synthetic_snapshot_matrix(p.N, n_s, 7, decay=0.42)  # singular values 0.42^k: r = 16 at 1e-6
+        Dd = torch.as_tensor(np.ascontiguousarray(Dsyn.transpose(0, 2, 1).reshape(3 * n_s, p.N)), device="cuda")
+        del Dsyn
     torch.cuda.synchronize()
     t_fom = time.perf_counter() - t0
-    Dd = Q.view(n_s, 3, p.N).transpose(0, 1).reshape(3 * n_s, p.N).contiguous()  # direction-major columns
-    del Q, Qs
     res = {}
     for mixed in (False, True):
         h.set_projection_precision(mixed)
@@ -292,10 +303,14 @@ def measure_projection(m, h, n_grid: int = 96, n_s: int = 32, n_out: int = 10000
     dt = res[False][1]
     for mixed in (False, True):
         res[mixed][0].close()
-    return {"workload": f"{n_grid}^3 FIT grid (N = {p.N}, {p.K.nnz} nnz), mu_r = 32 cube with the static "
-                        f"correction, {n_s} device-solved snapshots per direction in [1e1, 1e8], one TSVD per "
-                        f"direction (TOL_Sigma 1e-6 -> r = {list(res[False][2])}), {n_out} outputs",
-            "static_solve_seconds_with_assembly": t_static, "static_iterations": list(solver.iters),
+    desc = (f"{n_s} device-solved snapshots per direction in [1e1, 1e8]" if snapshots == "device" else
+            f"{n_s} synthetic snapshot columns per direction (singular values 0.42^k)")
+    return {"workload": f"{n_grid}^3 FIT grid (N = {p.N}, {p.K.nnz} nnz), mu_r = 32 cube"
+                        + (" with the static correction, " if snapshots == "device" else ", ")
+                        + f"{desc}, one TSVD per direction (TOL_Sigma 1e-6 -> r = {list(res[False][2])}), "
+                        f"{n_out} outputs",
+            "static_solve_seconds_with_assembly": t_static,
+            "static_iterations": list(solver.iters) if solver is not None else None,
             "snapshot_solve_seconds": t_fom, "snapshot_iterations_max": its,
             "project_seconds": {"fp64": dt, "mixed": res[True][1]}, "r_dirs_mixed": list(res[True][2]),
             "sweep_ms": {"fp64": out[False][2], "mixed": out[True][2]},
@@ -621,6 +636,8 @@ def main():
     ap.add_argument("--projection-only", action="store_true",
                     help="time mrom_project alone (float64 and complex64 products) and print its record")
     ap.add_argument("--projection-grid", type=int, default=96)
+    ap.add_argument("--projection-snapshots", default="device", choices=["device", "synthetic"],
+                    help="snapshot columns of the projection section: solved on the device, or synthetic")
     ap.add_argument("--adaptive-only", action="store_true",
                     help="time mrom_adapt (Algorithm 1) on the two-material grid and print its record")
     ap.add_argument("--adaptive-grid", type=int, default=128)
@@ -693,7 +710,8 @@ def main():
         stream = torch.cuda.Stream(dev)
         h = m.Handle(local_rank, stream.cuda_stream)
         if rank == 0:
-            print(json.dumps({"projection": measure_projection(m, h, n_grid=args.projection_grid)}), flush=True)
+            print(json.dumps({"projection": measure_projection(m, h, n_grid=args.projection_grid,
+                                                               snapshots=args.projection_snapshots)}), flush=True)
         h.close()
         return
 

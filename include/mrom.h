@@ -169,6 +169,9 @@ mrom_status mrom_rom_from_packed(mrom_handle h, int32_t n_obj, const mrom_packed
                                  size_t bytes, mrom_rom_t* out);
 /* Basis size r of an object (per direction); 0 on a null object. */
 int32_t mrom_rom_rank(mrom_rom_t rom);
+/* Releases an object (stream-ordered on the stream the handle had when the object was created,
+ * so that stream -- and the handle -- must still exist: release objects and plans before the
+ * handle and before destroying that stream, also at process exit). */
 void mrom_rom_free(mrom_rom_t rom);
 
 /* mrom_rom_free of n objects (host array, entries set to NULL; NULL entries are skipped). */
@@ -468,6 +471,7 @@ mrom_status mrom_plan_create(mrom_handle h, const mrom_rom_t* roms, int32_t n_ob
                              mrom_plan* out);
 mrom_status mrom_plan_sweep(mrom_plan plan, const double* omega, int32_t omega_stride,
                             double* R, double* I, double* Delta);
+/* Releases a plan (stream-ordered on its handle's stream; before the handle is destroyed). */
 mrom_status mrom_plan_destroy(mrom_plan plan);
 /* mrom_plan_sweep that also writes the rotation invariants of every evaluation (Sect. 1: the
  * eigenvalues of R~ = N0 + R and of I do not depend on the object's orientation), computed in the
