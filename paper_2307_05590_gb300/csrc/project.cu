@@ -17,6 +17,7 @@
 // full FP64 utilisation with register tiles rather than for HBM streaming.
 #include "mrom_internal.h"
 #include "herm_tridiag.cuh"
+#include "tridiag_dc.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -233,15 +234,16 @@ __global__ void gram_reduce_kernel(const double2* __restrict__ part, int nsplit,
   }
 }
 
-// ------------------------------------------------ Householder + QL eigensolver
-// Hermitian m x m A = Z Lambda Z^H (A overwritten): Householder tridiagonalisation, then
-// implicit QL with the rotations accumulated into Z (columns = eigenvectors).  One CTA.
-// *status gets kStatusTimeout if QL did not converge.
+// ------------------------------------------------ Householder + tridiagonal eigensolver
+// Hermitian m x m A = Z Lambda Z^H (A overwritten): Householder tridiagonalisation, then the real
+// tridiagonal by divide and conquer (m <= MROM_MAX_R, with `work`: 3 m^2 float64) and Z = Q1 D Z2,
+// or else implicit QL with the rotations accumulated into Z (columns = eigenvectors).  One CTA.
+// *status gets kStatusTimeout if QL did not converge or divide and conquer met a non-finite value.
 constexpr int kEigThreads = 512;
 
 __global__ void __launch_bounds__(kEigThreads)
 herm_eig_kernel(double2* __restrict__ A, int m, double2* __restrict__ Z, double* __restrict__ lam,
-                int* __restrict__ status) {
+                int* __restrict__ status, double* __restrict__ work) {
   __shared__ double sd[MROM_MAX_SNAPSHOTS], se[MROM_MAX_SNAPSHOTS], stau[MROM_MAX_SNAPSHOTS];
   __shared__ double rc[MROM_MAX_SNAPSHOTS], rs[MROM_MAX_SNAPSHOTS];
   __shared__ double2 salpha[MROM_MAX_SNAPSHOTS], sph[MROM_MAX_SNAPSHOTS], pv[MROM_MAX_SNAPSHOTS];
@@ -251,6 +253,28 @@ herm_eig_kernel(double2* __restrict__ A, int m, double2* __restrict__ Z, double*
   if (threadIdx.x < 4) flags[threadIdx.x] = 0;
   __syncthreads();
   hq::herm_tridiag<kEigThreads>(A, m, Z, sd, se, stau, salpha, sph, pv, red, part);
+  if (work != nullptr && m <= dc::kDcMaxN) {
+    __shared__ dc::DcShared S;
+    const int mm = m * m;
+    const double* Z2 = dc::tridiag_dc<kEigThreads>(sd, se, m, work, work + mm, work + 2 * mm, S);
+    // Z Z2 into A (the Householder vectors are no longer needed), then back into Z
+    for (int idx = threadIdx.x; idx < mm; idx += kEigThreads) {
+      const int i = idx / m, j = idx - (idx / m) * m;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = 0; k < m; ++k) {
+        const double2 zk = Z[i * m + k];
+        const double q = Z2[k * m + j];
+        acc.x = fma(zk.x, q, acc.x);
+        acc.y = fma(zk.y, q, acc.y);
+      }
+      A[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < mm; idx += kEigThreads) Z[idx] = A[idx];
+    for (int i = threadIdx.x; i < m; i += kEigThreads) lam[i] = S.lam[i];
+    if (threadIdx.x == 0 && S.bad) atomicOr(status, kStatusTimeout);
+    return;
+  }
   const bool ok = hq::ql_single<kEigThreads>(sd, se, m, Z, rc, rs, flags, 60);
   for (int i = threadIdx.x; i < m; i += kEigThreads) lam[i] = sd[i];
   if (threadIdx.x == 0 && !ok) atomicOr(status, kStatusTimeout);
@@ -566,15 +590,16 @@ namespace {
 mrom_status gram_eig(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, int m, double tol_sigma, int r_cap,
                      int* r_out, std::vector<double>& s, std::vector<double2>& wh) {
   cudaStream_t st = h->stream;
-  DevBuf g, vbuf, lam;
+  DevBuf g, vbuf, lam, work;
   cudaError_t e = cudaMalloc(&g.p, (size_t)m * m * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc(&vbuf.p, (size_t)m * m * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc(&lam.p, (size_t)m * sizeof(double));
+  if (e == cudaSuccess && m <= dc::kDcMaxN) e = cudaMalloc(&work.p, 3 * (size_t)m * m * sizeof(double));
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: allocation");
   e = tall_gram(h, Dp, 1, ldd, m, Dp, 1, ldd, m, nullptr, 0, n, true, static_cast<double2*>(g.p), m);
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: snapshot Gram");
   herm_eig_kernel<<<1, kEigThreads, 0, st>>>(static_cast<double2*>(g.p), m, static_cast<double2*>(vbuf.p),
-                                             static_cast<double*>(lam.p), h->d_status);
+                                             static_cast<double*>(lam.p), h->d_status, static_cast<double*>(work.p));
   ++h->launches;
   std::vector<double> lh(m);
   std::vector<double2> vh((size_t)m * m);
@@ -586,7 +611,7 @@ mrom_status gram_eig(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, int
   cudaMemcpy(&stw, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (stw & kStatusTimeout) {
     cudaMemset(h->d_status, 0, sizeof(int));
-    return fail(h, MROM_ENOTCONVERGED, "mrom_project: the snapshot eigensolver did not converge");
+    return fail(h, MROM_ENOTCONVERGED, "mrom_project: the snapshot eigensolver did not converge (or met a non-finite value)");
   }
   std::vector<int> order(m);
   std::iota(order.begin(), order.end(), 0);
