@@ -357,10 +357,17 @@ __device__ __forceinline__ double2 split_block(const PencilDev& pd, int x, int a
 __device__ __forceinline__ double2 cscale(double c, double2 v) { return make_double2(c * v.x, c * v.y); }
 __device__ __forceinline__ double2 cneg(double2 v) { return make_double2(-v.x, -v.y); }
 
-// All threads of the CTA; pd.lam ascending, pd.beta, pd.Gh / pd.Eh complete.  rs: shared scratch.
-__device__ void pencil_split_tables(const PencilDev& pd, int r, double2 (*rs)[3 * MROM_MAX_R]) {
+// All threads of the CTA; pd.lam ascending, pd.beta, pd.Gh / pd.Eh complete.  rs: shared scratch;
+// cb: shared scratch of r^2 float64 for the coefficients 1 / (lambda_k + lambda_l).
+__device__ void pencil_split_tables(const PencilDev& pd, int r, double2 (*rs)[3 * MROM_MAX_R], double* cb) {
   const int tid = threadIdx.x;
   const int nb = 3 * r;  // (k, j) pairs per block
+  for (int idx = tid; idx < r * r; idx += kPT) {  // one division per pair, shared by all the tables
+    const int k = idx / r, l = idx - (idx / r) * r;
+    const double den = pd.lam[k] + pd.lam[l];
+    cb[idx] = den > 0.0 ? 1.0 / den : 0.0;
+  }
+  __syncthreads();
   // (x, k, j) work items: block x of the present ones, row k, column j
   auto present = [&pd](int x) { return x < 3 ? pd.Gh != nullptr : pd.Eh != nullptr; };
   // prefix sums TA (one thread per (x, k, j)): P0 = -TA_KK, P1 = -TA_iS, P2 = -TA_CC (TB_KK and
@@ -375,8 +382,7 @@ __device__ void pencil_split_tables(const PencilDev& pd, int r, double2 (*rs)[3 
     for (int l = 0; l <= r; ++l) {
       if (l > k) pd.pt[((size_t)l * (l - 1) / 2 + k) * kPtEntry + slot + j] = cneg(sa);  // entry (m = l, k)
       if (l == r || !on) continue;
-      const double den = lk + pd.lam[l];
-      const double c = den > 0.0 ? lk * lk / den : 0.0;
+      const double c = lk * lk * cb[k * r + l];
       sa = cmac(sa, cscale(c, split_block(pd, x, k, l)), pd.beta[l * 3 + j]);
     }
   }
@@ -405,9 +411,7 @@ __device__ void pencil_split_tables(const PencilDev& pd, int r, double2 (*rs)[3 
         *P = x == 0 ? cadd(*P, cadd(sa, d)) : cadd(sa, d);
       }
       if (!on) continue;
-      const double den = lk + pd.lam[l];
-      const double c = den > 0.0 ? 1.0 / den : 0.0;
-      sa = cmac(sa, cscale(c, split_block(pd, x, k, l)), pd.beta[l * 3 + j]);
+      sa = cmac(sa, cscale(cb[k * r + l], split_block(pd, x, k, l)), pd.beta[l * 3 + j]);
     }
     pd.tb0[(size_t)k * 12 + 3 * x + j] = cadd(sa, d);
   }
@@ -581,7 +585,7 @@ pencil_finish_kernel(const RomDev* __restrict__ objs, const PencilDev* __restric
       }
       __syncthreads();
     }
-    if (pd.pt) pencil_split_tables(pd, r, s_rs);
+    if (pd.pt) pencil_split_tables(pd, r, s_rs, Q2);  // Q2's space is free again
   }
 }
 
