@@ -152,9 +152,9 @@ __device__ __forceinline__ uint32_t op_off(int row, int k) {
 }
 
 // KT rows (the MMA's K) per chunk; g.nraw chunks' bulk copies in flight, two operand stages.
-// NB > 0 (one M tile, npad <= 32 NB): each thread keeps its share of the float64 partial block
-// in registers (NB blocks of 8 columns) and stores it once at the end; NB = 0: the partial
-// block is accumulated in global memory at every flush.
+// NB > 0 (one M tile, npad <= 32 NB): each thread keeps its share of the partial block in
+// registers (NB blocks of 8 columns, compensated float32 pairs) and stores it once at the end;
+// NB = 0: the float64 partial block is accumulated in global memory at every flush.
 template <int KT, int NB>
 __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -227,10 +227,17 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
   // warp reads its lane quarter (warp % 4) of each M tile, the warp sets alternate 8-column
   // blocks.  With no chunk the block is set to zero without touching tensor memory.
   const int nchunks_cta = nchunks;
-  double racc[NB > 0 ? 8 * NB : 1];
+  // the register block as an unevaluated float32 pair hi + lo, added to by compensated (two-sum)
+  // steps on the FP32 pipe: float64 adds would cost the scarce FP64 pipe 8 NB per thread and flush
+  float rhi[NB > 0 ? 8 * NB : 1], rlo[NB > 0 ? 8 * NB : 1];
 #pragma unroll
-  for (int k = 0; k < (NB > 0 ? 8 * NB : 1); ++k) racc[k] = 0.0;
-  auto flush = [&](bool first) {
+  for (int k = 0; k < (NB > 0 ? 8 * NB : 1); ++k) rhi[k] = rlo[k] = 0.f;
+  // With NB > 0 the accumulator of segment g (kFlush chunks) lives at tensor-memory column
+  // 128 (g & 1): the MMAs of segment g + 1 run into the other half while segment g is read, two
+  // chunks after its last chunk, whose MMAs the wait for its operand stage has then seen complete.
+  constexpr bool kDefer = NB > 0;
+  auto acc_col = [](int gseg) { return kDefer ? (uint32_t)((gseg & 1) * 128) : 0u; };
+  auto flush = [&](bool first, uint32_t col) {
     const int q = warp & 3, cg = warp >> 2;
     constexpr int kCG = kTT / 128;  // warp sets sharing the lane quarters
     double* out = g.part + (size_t)blockIdx.x * mpad * npad;
@@ -240,9 +247,13 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
         const int cb = cg * 8 + b * 8 * kCG;
         if (cb < npad && nchunks_cta > 0) {
           float v[8];
-          tmem_ld8(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)cb, v);
+          tmem_ld8(taddr + ((uint32_t)(q * 32) << 16) + col + (uint32_t)cb, v);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) racc[b * 8 + k] += (double)v[k];
+          for (int k = 0; k < 8; ++k) {  // two-sum of hi and v, the rounding error into lo
+            const float a = rhi[b * 8 + k], sum = a + v[k], bv = sum - a;
+            rlo[b * 8 + k] += (a - (sum - bv)) + (v[k] - bv);
+            rhi[b * 8 + k] = sum;
+          }
         }
       }
     } else {
@@ -262,6 +273,27 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
     }
   };
 
+  // operand descriptors of the two stages (thread 0), advanced per K step and M tile by adding
+  // to the 14-bit address field (shared addresses stay below 256 KB)
+  uint64_t dA0[3], dA1[3], dB0[3], dB1[3];
+  {
+    const uint32_t sbo = 32u * KT;
+    const uint32_t pa0[3] = {smem_u32(a_hi(0)), smem_u32(a_hi(0)), smem_u32(a_lo(0))};
+    const uint32_t pb0[3] = {smem_u32(b_hi(0)), smem_u32(b_lo(0)), smem_u32(b_hi(0))};
+    const uint32_t pa1[3] = {smem_u32(a_hi(1)), smem_u32(a_hi(1)), smem_u32(a_lo(1))};
+    const uint32_t pb1[3] = {smem_u32(b_hi(1)), smem_u32(b_lo(1)), smem_u32(b_hi(1))};
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      dA0[p] = smem_desc(pa0[p], sbo);
+      dB0[p] = smem_desc(pb0[p], sbo);
+      dA1[p] = smem_desc(pa1[p], sbo);
+      dB1[p] = smem_desc(pb1[p], sbo);
+    }
+  }
+  const uint32_t idesc = instr_desc(128, npad);
+  const int nseg = (nchunks + kFlush - 1) / kFlush;
+  int flushed = 0;  // segments added into the float64 block so far (deferred mode)
+
   bool failed = false;
   int c = 0;
   for (; c < nchunks; ++c) {
@@ -269,6 +301,9 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
     const uint32_t raw_par = (uint32_t)((c / NR) & 1);
     const int rows = chunk_rows(c);
     const bool full = rows == KT;
+    // the deferred flush of the previous segment: chunk c - 2 ended it, and its MMAs are complete
+    // once the wait below for operand stage s has returned
+    const bool dflush = kDefer && c % kFlush == 1 && c / kFlush >= 1 && flushed == c / kFlush - 1;
     // thread 0 polls (bounded); after the barrier every other thread observes the completed
     // phases with one try_wait each, which makes the copied bytes visible to it
     bool ok = true;
@@ -281,24 +316,31 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
       break;
     }
     if (tid != 0 && full) mbar_wait(raw_full + sr, raw_par);
+    if (dflush) {
+      if (tid != 0) mbar_wait(op_free + s, (uint32_t)(((c - 2) >> 1) & 1));  // completed: returns at once
+      tc_fence_after();
+      flush(false, acc_col(flushed));
+      tc_fence_before();
+      ++flushed;
+    }
     // ---- convert chunk c into the operand tiles of stage s: one item per (complex column,
     // quad of 4 rows k), A's items first, then B's; an item reads 4 raw values (lanes along the
     // columns: conflict-free) and stores the hi and lo parts of its real and imaginary rows as
-    // 16-byte vectors (4 consecutive k of one core-matrix row)
+    // 16-byte vectors (4 consecutive k of one core-matrix row); two items per thread and pass,
+    // their loads first
     const int64_t r0 = row0 + (int64_t)c * KT;
     const float2* ra = raw_a(sr);
     const float2* rb = g.same_ab ? ra : raw_b(sr);
     const float* rw = raw_w(sr);
     unsigned char *ah = a_hi(s), *al = a_lo(s), *bh = b_hi(s), *bl = b_lo(s);
     const int na = ma * kKG, nitems = na + mb * kKG;
-    for (int it = tid; it < nitems; it += kTT) {
+    auto load_item = [&](int it, float (&x)[4], float (&y)[4]) {
       const bool isA = it < na;
       const int jt = isA ? it : it - na;
       const int mc = isA ? ma : mb;
       const int m = jt % mc, k0 = 4 * (jt / mc);
       const float2* src = isA ? ra : rb;
       const float2* gsrc = (isA || g.same_ab) ? g.A : g.B;
-      uint32_t hre[4], lre[4], him[4], lim[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int kk = k0 + j;
@@ -311,11 +353,22 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
           v = gsrc[(r0 + kk) * mc + m];
           if (!isA && g.w) wt = g.w[r0 + kk];
         }
-        const float x = wt * v.x, y = wt * v.y;
-        hre[j] = to_tf32(x);  // hi: rounded to TF32; lo: the exact remainder (the MMA reads
-        him[j] = to_tf32(y);  // its TF32 part)
-        lre[j] = __float_as_uint(x - __uint_as_float(hre[j]));
-        lim[j] = __float_as_uint(y - __uint_as_float(him[j]));
+        x[j] = wt * v.x;
+        y[j] = wt * v.y;
+      }
+    };
+    auto store_item = [&](int it, const float (&x)[4], const float (&y)[4]) {
+      const bool isA = it < na;
+      const int jt = isA ? it : it - na;
+      const int mc = isA ? ma : mb;
+      const int m = jt % mc, k0 = 4 * (jt / mc);
+      uint32_t hre[4], lre[4], him[4], lim[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        hre[j] = to_tf32(x[j]);  // hi: rounded to TF32; lo: the exact remainder (the MMA reads
+        him[j] = to_tf32(y[j]);  // its TF32 part)
+        lre[j] = __float_as_uint(x[j] - __uint_as_float(hre[j]));
+        lim[j] = __float_as_uint(y[j] - __uint_as_float(him[j]));
       }
       unsigned char* hi = isA ? ah : bh;
       unsigned char* lo = isA ? al : bl;
@@ -324,27 +377,38 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
       *reinterpret_cast<uint4*>(lo + ore) = make_uint4(lre[0], lre[1], lre[2], lre[3]);
       *reinterpret_cast<uint4*>(hi + oim) = make_uint4(him[0], him[1], him[2], him[3]);
       *reinterpret_cast<uint4*>(lo + oim) = make_uint4(lim[0], lim[1], lim[2], lim[3]);
+    };
+    for (int it = tid; it < nitems; it += 2 * kTT) {
+      float x0[4], y0[4], x1[4], y1[4];
+      const bool two = it + kTT < nitems;
+      load_item(it, x0, y0);
+      if (two) load_item(it + kTT, x1, y1);
+      store_item(it, x0, y0);
+      if (two) store_item(it + kTT, x1, y1);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();  // raw stage sr consumed, operand stage s written
+    const int gseg = c / kFlush;
+    const bool seg_end = c % kFlush == kFlush - 1 || c == nchunks - 1;
     if (tid == 0) {
       if (c + NR < nchunks && chunk_rows(c + NR) == KT) issue_copy(c + NR);
       tc_fence_after();
-      const uint32_t idesc = instr_desc(128, npad);
-      const uint32_t pa[3] = {smem_u32(ah), smem_u32(ah), smem_u32(al)};
-      const uint32_t pb[3] = {smem_u32(bh), smem_u32(bl), smem_u32(bh)};
+      const uint32_t dcol = taddr + acc_col(gseg);
+#pragma unroll
       for (int ks = 0; ks < KT / 8; ++ks)
         for (int t = 0; t < mtiles; ++t)
+#pragma unroll
           for (int p = 0; p < 3; ++p) {
-            const uint64_t ad = smem_desc(pa[p] + (uint32_t)t * (512u * KT) + (uint32_t)ks * 256u, 32u * KT);
-            const uint64_t bd = smem_desc(pb[p] + (uint32_t)ks * 256u, 32u * KT);
-            mma_tf32(taddr + (uint32_t)(t * npad), ad, bd, idesc, (c % kFlush > 0 || ks > 0 || p > 0) ? 1u : 0u);
+            const uint64_t ad = (s ? dA1[p] : dA0[p]) + (uint64_t)((ks * 256u + (uint32_t)t * 512u * KT) >> 4);
+            const uint64_t bd = (s ? dB1[p] : dB0[p]) + (uint64_t)((ks * 256u) >> 4);
+            mma_tf32(dcol + (uint32_t)(t * npad), ad, bd, idesc, (c % kFlush > 0 || ks > 0 || p > 0) ? 1u : 0u);
           }
       mma_commit(op_free + s);
       mma_last = c;
     }
-    // ---- end of a segment: add the FP32 accumulator into this CTA's float64 partial block
-    if (c % kFlush == kFlush - 1 || c == nchunks - 1) {
+    // ---- end of a segment (float64 block in global memory): wait for the MMAs and add the FP32
+    // accumulator into this CTA's partial block
+    if (!kDefer && seg_end) {
       const bool ok = tid == 0 ? mbar_wait(op_free + s, (uint32_t)((c >> 1) & 1)) : true;
       if (__syncthreads_or(!ok)) {
         failed = true;
@@ -353,12 +417,27 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
       }
       if (tid != 0) mbar_wait(op_free + s, (uint32_t)((c >> 1) & 1));  // completed: returns at once
       tc_fence_after();
-      flush(c < kFlush);
+      flush(c < kFlush, 0u);
       tc_fence_before();
       __syncthreads();
     }
   }
-  if (!failed && nchunks == 0) flush(true);  // zeros for an empty range
+  // deferred mode: the segments not yet added (the last one or two), once every MMA is complete
+  if (kDefer && !failed && flushed < nseg) {
+    const int last = nchunks - 1;  // the last chunk's MMAs (every thread knows it; mma_last is thread 0's)
+    const uint32_t par = (uint32_t)((last >> 1) & 1);
+    const bool ok = tid == 0 ? mbar_wait(op_free + (last & 1), par) : true;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+    } else {
+      if (tid != 0) mbar_wait(op_free + (last & 1), par);  // completed: returns at once
+      tc_fence_after();
+      for (; flushed < nseg; ++flushed) flush(false, acc_col(flushed));
+      tc_fence_before();
+      __syncthreads();
+    }
+  }
+  if (!failed && nchunks == 0) flush(true, 0u);  // zeros for an empty range
   if constexpr (NB > 0) {  // the register block, once ([column][row] as above)
     const int q = warp & 3, cg = warp >> 2;
     constexpr int kCG = kTT / 128;
@@ -368,7 +447,8 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
       const int cb = cg * 8 + b * 8 * kCG;
       if (cb < npad) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) out[(size_t)(cb + k) * mpad + q * 32 + lane] = racc[b * 8 + k];
+        for (int k = 0; k < 8; ++k)
+          out[(size_t)(cb + k) * mpad + q * 32 + lane] = (double)rhi[b * 8 + k] + (double)rlo[b * 8 + k];
       }
     }
   }
