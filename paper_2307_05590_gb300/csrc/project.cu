@@ -29,9 +29,6 @@ namespace {
 __device__ __forceinline__ double2 c_conj_mac(double2 c, double2 a, double2 b) {  // c + conj(a) b
   return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
 }
-__device__ __forceinline__ double2 c_mac(double2 c, double2 a, double2 b) {  // c + a b
-  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
-}
 
 // ------------------------------------------------------------------ tall Gram
 // part[split][a][b] = sum_{n in split} conj(A[n][a]) * wgt(n) * B[n][b]
@@ -241,9 +238,14 @@ __global__ void gram_reduce_kernel(const double2* __restrict__ part, int nsplit,
 // *status gets kStatusTimeout if QL did not converge or divide and conquer met a non-finite value.
 constexpr int kEigThreads = 512;
 
+// One CTA per matrix: CTA b takes A + b m^2, Z + b m^2, lam + b m (and work + 3 b m^2).
 __global__ void __launch_bounds__(kEigThreads)
 herm_eig_kernel(double2* __restrict__ A, int m, double2* __restrict__ Z, double* __restrict__ lam,
                 int* __restrict__ status, double* __restrict__ work) {
+  A += (size_t)blockIdx.x * m * m;
+  Z += (size_t)blockIdx.x * m * m;
+  lam += (size_t)blockIdx.x * m;
+  if (work) work += (size_t)blockIdx.x * 3 * m * m;
   __shared__ double sd[MROM_MAX_SNAPSHOTS], se[MROM_MAX_SNAPSHOTS], stau[MROM_MAX_SNAPSHOTS];
   __shared__ double rc[MROM_MAX_SNAPSHOTS], rs[MROM_MAX_SNAPSHOTS];
   __shared__ double2 salpha[MROM_MAX_SNAPSHOTS], sph[MROM_MAX_SNAPSHOTS], pv[MROM_MAX_SNAPSHOTS];
@@ -587,24 +589,33 @@ namespace {
 // Snapshot Gram, eigensolver and truncation for the m columns of D (column c at
 // D + c * ldd): returns the rank r, the singular values (host) and W = V_r diag(1/s_r)
 // (host, m x r, row-major) such that U = D W.
-mrom_status gram_eig(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, int m, double tol_sigma, int r_cap,
-                     int* r_out, std::vector<double>& s, std::vector<double2>& wh) {
+// Truncated SVD of nb snapshot sets of m columns each (set b at Dp + b * m * ldd): their Grams,
+// one eigensolver launch with one CTA per set, then per set the singular values s[b], the rank
+// r_out[b] (s_k / s_1 >= tol_sigma, at most r_cap) and W = V_r diag(1/s_r) in wh[b] (m x r).
+mrom_status gram_eig_many(mrom_ctx* h, int nb, const double2* Dp, int64_t ldd, int64_t n, int m, double tol_sigma,
+                          int r_cap, int* r_out, std::vector<double>* s, std::vector<double2>* wh) {
   cudaStream_t st = h->stream;
+  const size_t mm = (size_t)m * m;
   DevBuf g, vbuf, lam, work;
-  cudaError_t e = cudaMalloc(&g.p, (size_t)m * m * sizeof(double2));
-  if (e == cudaSuccess) e = cudaMalloc(&vbuf.p, (size_t)m * m * sizeof(double2));
-  if (e == cudaSuccess) e = cudaMalloc(&lam.p, (size_t)m * sizeof(double));
-  if (e == cudaSuccess && m <= dc::kDcMaxN) e = cudaMalloc(&work.p, 3 * (size_t)m * m * sizeof(double));
+  cudaError_t e = cudaMalloc(&g.p, nb * mm * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&vbuf.p, nb * mm * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&lam.p, nb * (size_t)m * sizeof(double));
+  if (e == cudaSuccess && m <= dc::kDcMaxN) e = cudaMalloc(&work.p, 3 * nb * mm * sizeof(double));
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: allocation");
-  e = tall_gram(h, Dp, 1, ldd, m, Dp, 1, ldd, m, nullptr, 0, n, true, static_cast<double2*>(g.p), m);
+  for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+    const double2* D = Dp + (size_t)b * m * ldd;
+    e = tall_gram(h, D, 1, ldd, m, D, 1, ldd, m, nullptr, 0, n, true, static_cast<double2*>(g.p) + b * mm, m);
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: snapshot Gram");
-  herm_eig_kernel<<<1, kEigThreads, 0, st>>>(static_cast<double2*>(g.p), m, static_cast<double2*>(vbuf.p),
-                                             static_cast<double*>(lam.p), h->d_status, static_cast<double*>(work.p));
+  herm_eig_kernel<<<nb, kEigThreads, 0, st>>>(static_cast<double2*>(g.p), m, static_cast<double2*>(vbuf.p),
+                                              static_cast<double*>(lam.p), h->d_status,
+                                              static_cast<double*>(work.p));
   ++h->launches;
-  std::vector<double> lh(m);
-  std::vector<double2> vh((size_t)m * m);
-  e = cudaMemcpyAsync(lh.data(), lam.p, m * sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(vh.data(), vbuf.p, vh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st);
+  std::vector<double> lh_all(nb * (size_t)m);
+  std::vector<double2> vh_all(nb * mm);
+  e = cudaMemcpyAsync(lh_all.data(), lam.p, lh_all.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(vh_all.data(), vbuf.p, vh_all.size() * sizeof(double2), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(h, e, "mrom_project: eigensolver");
   int stw = 0;
@@ -613,25 +624,35 @@ mrom_status gram_eig(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, int
     cudaMemset(h->d_status, 0, sizeof(int));
     return fail(h, MROM_ENOTCONVERGED, "mrom_project: the snapshot eigensolver did not converge (or met a non-finite value)");
   }
-  std::vector<int> order(m);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lh[a] > lh[b]; });
-  s.assign(m, 0.0);
-  for (int k = 0; k < m; ++k) s[k] = std::sqrt(std::max(lh[order[k]], 0.0));
-  // truncation rule (Eq. (15) reading): keep s_k / s_1 >= TOL_Sigma, at most r_cap
-  int r = 0;
-  for (int k = 0; k < m; ++k)
-    if (s[0] > 0 && s[k] > 0 && s[k] / s[0] >= tol_sigma) r = k + 1;
-  r = std::min(r, r_cap);
-  if (r < 1) return fail(h, MROM_EINVAL, "mrom_project: snapshots have no nonzero singular value");
-  wh.assign((size_t)m * r, make_double2(0.0, 0.0));
-  for (int c = 0; c < m; ++c)
-    for (int k = 0; k < r; ++k) {
-      const double2 v = vh[(size_t)c * m + order[k]];
-      wh[(size_t)c * r + k] = make_double2(v.x / s[k], v.y / s[k]);
-    }
-  *r_out = r;
+  for (int b = 0; b < nb; ++b) {
+    const double* lh = lh_all.data() + (size_t)b * m;
+    const double2* vh = vh_all.data() + b * mm;
+    std::vector<int> order(m);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lh[x] > lh[y]; });
+    std::vector<double>& sb = s[b];
+    sb.assign(m, 0.0);
+    for (int k = 0; k < m; ++k) sb[k] = std::sqrt(std::max(lh[order[k]], 0.0));
+    // truncation rule (Eq. (15) reading): keep s_k / s_1 >= TOL_Sigma, at most r_cap
+    int r = 0;
+    for (int k = 0; k < m; ++k)
+      if (sb[0] > 0 && sb[k] > 0 && sb[k] / sb[0] >= tol_sigma) r = k + 1;
+    r = std::min(r, r_cap);
+    if (r < 1) return fail(h, MROM_EINVAL, "mrom_project: snapshots have no nonzero singular value");
+    wh[b].assign((size_t)m * r, make_double2(0.0, 0.0));
+    for (int c = 0; c < m; ++c)
+      for (int k = 0; k < r; ++k) {
+        const double2 v = vh[(size_t)c * m + order[k]];
+        wh[b][(size_t)c * r + k] = make_double2(v.x / sb[k], v.y / sb[k]);
+      }
+    r_out[b] = r;
+  }
   return MROM_OK;
+}
+
+mrom_status gram_eig(mrom_ctx* h, const double2* Dp, int64_t ldd, int64_t n, int m, double tol_sigma, int r_cap,
+                     int* r_out, std::vector<double>& s, std::vector<double2>& wh) {
+  return gram_eig_many(h, 1, Dp, ldd, n, m, tol_sigma, r_cap, r_out, &s, &wh);
 }
 
 // U[:, off : off + r] (row-major, leading dimension ldu) = D W, in float64 (U64) or complex64 (U32)
@@ -939,12 +960,13 @@ extern "C" mrom_status mrom_project_dirs(mrom_handle h, const mrom_fom* fom, con
     return fail(h, MROM_EINVAL, "mrom_project_dirs: tol_sigma must be finite and >= 0");
   const auto* Dp = static_cast<const double2*>(D);
   std::vector<double2> wh[3];
-  for (int i = 0; i < 3; ++i) {
-    std::vector<double> s;
+  {
+    std::vector<double> sv[3];
     const int cap = std::min<int>(r_max > 0 ? r_max : MROM_MAX_R, MROM_MAX_R);
-    st = gram_eig(h, Dp + (size_t)i * n_s * ldd, ldd, n, n_s, tol_sigma, cap, &rd[i], s, wh[i]);
+    st = gram_eig_many(h, 3, Dp, ldd, n, n_s, tol_sigma, cap, rd, sv, wh);  // the three directions
     if (st != MROM_OK) return st;
-    if (sigma_out) std::copy(s.begin(), s.end(), sigma_out + (size_t)i * n_s);
+    if (sigma_out)
+      for (int i = 0; i < 3; ++i) std::copy(sv[i].begin(), sv[i].end(), sigma_out + (size_t)i * n_s);
   }
   const int rt = rd[0] + rd[1] + rd[2];
   if (rt > MROM_MAX_R) return fail(h, MROM_EINVAL, "mrom_project_dirs: r_1 + r_2 + r_3 exceeds MROM_MAX_R");
