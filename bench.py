@@ -78,8 +78,8 @@ def pencil_sweep_flops(r: int, m_sum: int, n_w: int, cert: bool = True) -> float
     """FP64 flops of one object's pencil sweep over n_w frequencies (pole-split forms), with
     m_sum = sum over the frequencies of m = #{lambda_k < w}:
 
-      a_k = 1 / (lambda_k + i w), u_k (one division)            12 per k
-      R and I: (-lambda Re u, Re u) x Re(beta_i^* beta_j)       24 per k
+      a_k = 1 / (lambda_k + i w) (one division)                 8 per k
+      R and I: (lambda den, den) x Re(beta_i^* beta_j)          24 per k
       a_k conj(beta_ki)                                         18 per k
       certificate polynomial Y_kj(w): full suffix (k >= m)      30 per k
         or Horner over five tables (k < m)                      48 per k
@@ -88,8 +88,8 @@ def pencil_sweep_flops(r: int, m_sum: int, n_w: int, cert: bool = True) -> float
     """
     r = int(r)
     if not cert:
-        return float(n_w * (36 * r + 100))
-    return float(n_w * (117 * r + 306) + 18 * m_sum)
+        return float(n_w * (32 * r + 100))
+    return float(n_w * (113 * r + 306) + 18 * m_sum)
 
 
 def pencil_prep_flops(r: int) -> float:

@@ -702,9 +702,10 @@ __device__ __forceinline__ void pencil_task(const RomDev& ob, const PencilDev& p
     Ms[s] = m;
   }
   __syncthreads();
-  // Per row, with bb_ij = Re(beta_ki^* beta_kj) and u = i w (lambda + i w) / (lambda^2 + w^2):
-  // Re(z_i^H Lambda z_j) gets lambda |u|^2 bb = -lambda Re(u) bb and
-  // Re(z_i^H z_j + beta_i^H z_j + beta_j^H z_i) gets (|u|^2 + 2 Re u) bb = Re(u) bb.
+  // Per row, with bb_ij = Re(beta_ki^* beta_kj), den = 1 / (lambda^2 + w^2) and
+  // u = i w (lambda + i w) den: Re(z_i^H Lambda z_j) gets lambda |u|^2 bb = w^2 (lambda den) bb and
+  // Re(z_i^H z_j + beta_i^H z_j + beta_j^H z_i) gets (|u|^2 + 2 Re u) bb = Re(u) bb = -w^2 den bb;
+  // the sums over the rows carry lambda den bb and den bb, and w^2 joins at the outputs.
   double acc[kNQ];
 #pragma unroll
   for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
@@ -714,17 +715,15 @@ __device__ __forceinline__ void pencil_task(const RomDev& ob, const PencilDev& p
   for (int k = warp / F; k < r; k += wpg) {
     const double lam = pd.lam[k];
     const double den = 1.0 / fma(lam, lam, w2);
-    const double2 u = make_double2(-w2 * den, wl * lam * den);
-    const double wr = -lam * u.x;
+    const double2 a = make_double2(lam * den, -wl * den);  // 1 / (lambda_k + i w)
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
       const double bb = pd.bbr[k * 6 + q];
-      acc[18 + q] = fma(wr, bb, acc[18 + q]);
-      acc[24 + q] = fma(u.x, bb, acc[24 + q]);
+      acc[18 + q] = fma(a.x, bb, acc[18 + q]);
+      acc[24 + q] = fma(den, bb, acc[24 + q]);
     }
     if constexpr (CERT || HAS_E) {
       double2 ba[3];  // a_k conj(beta_k)
-      const double2 a = make_double2(lam * den, -wl * den);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         const double2 bt = pd.beta[k * 3 + i];
@@ -796,11 +795,11 @@ __device__ __forceinline__ void pencil_task(const RomDev& ob, const PencilDev& p
     const double* c0 = pd.c0 ? pd.c0 + (size_t)Ms[s] * 24 : nullptr;
     const size_t o = ((size_t)task.obj * n_w + task.w0 + s) * 9 + ij;
     if (Rout) {
-      double kf = t(18 + sym);
+      double kf = wv * wv * t(18 + sym);
       if constexpr (HAS_E) kf -= t(9 + i * 3 + j) + t(9 + j * 3 + i) + c0[18 + sym];
       Rout[o] = fma(-0.25 * ob.alpha3, kf, ob.N0[ij]);
     }
-    if (Iout) Iout[o] = 0.25 * ob.alpha3 * wv * (ob.c00[ij] + t(24 + sym));
+    if (Iout) Iout[o] = 0.25 * ob.alpha3 * wv * fma(-wv * wv, t(24 + sym), ob.c00[ij]);
     if (Dout) {
       if constexpr (CERT) {
         const double ww = wv * wv;
@@ -829,9 +828,9 @@ __device__ __forceinline__ void pencil_task(const RomDev& ob, const PencilDev& p
       for (int sym = 0; sym < 6; ++sym) {
         const int i = sym < 3 ? 0 : (sym < 5 ? 1 : 2), j = sym < 3 ? sym : (sym < 5 ? sym - 2 : 2);
         if (is_i) {
-          Mp[sym] = 0.25 * ob.alpha3 * wv * (0.5 * (ob.c00[i * 3 + j] + ob.c00[j * 3 + i]) + t(24 + sym));
+          Mp[sym] = 0.25 * ob.alpha3 * wv * fma(-wv * wv, t(24 + sym), 0.5 * (ob.c00[i * 3 + j] + ob.c00[j * 3 + i]));
         } else {
-          double kf = t(18 + sym);
+          double kf = wv * wv * t(18 + sym);
           if constexpr (HAS_E) kf -= t(9 + i * 3 + j) + t(9 + j * 3 + i) + c0[18 + sym];
           Mp[sym] = fma(-0.25 * ob.alpha3, kf, 0.5 * (ob.N0[i * 3 + j] + ob.N0[j * 3 + i]));
         }
