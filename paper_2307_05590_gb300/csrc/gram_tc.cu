@@ -292,6 +292,22 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
   }
   const uint32_t idesc = instr_desc(128, npad);
   const int nseg = (nchunks + kFlush - 1) / kFlush;
+  auto issue_mmas = [&](int cm) {  // thread 0: the MMAs of chunk cm from operand stage cm & 1
+    const int sm = cm & 1;
+    tc_fence_after();
+    const uint32_t dcol = taddr + acc_col(cm / kFlush);
+#pragma unroll
+    for (int ks = 0; ks < KT / 8; ++ks)
+      for (int t = 0; t < mtiles; ++t)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          const uint64_t ad = (sm ? dA1[p] : dA0[p]) + (uint64_t)((ks * 256u + (uint32_t)t * 512u * KT) >> 4);
+          const uint64_t bd = (sm ? dB1[p] : dB0[p]) + (uint64_t)((ks * 256u) >> 4);
+          mma_tf32(dcol + (uint32_t)(t * npad), ad, bd, idesc, (cm % kFlush > 0 || ks > 0 || p > 0) ? 1u : 0u);
+        }
+    mma_commit(op_free + sm);
+    mma_last = cm;
+  };
   int flushed = 0;  // segments added into the float64 block so far (deferred mode)
 
   bool failed = false;
@@ -378,53 +394,47 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
       *reinterpret_cast<uint4*>(hi + oim) = make_uint4(him[0], him[1], him[2], him[3]);
       *reinterpret_cast<uint4*>(lo + oim) = make_uint4(lim[0], lim[1], lim[2], lim[3]);
     };
-    for (int it = tid; it < nitems; it += 2 * kTT) {
-      float x0[4], y0[4], x1[4], y1[4];
-      const bool two = it + kTT < nitems;
-      load_item(it, x0, y0);
-      if (two) load_item(it + kTT, x1, y1);
-      store_item(it, x0, y0);
-      if (two) store_item(it + kTT, x1, y1);
+    // warp 0: thread 0 issues the copies into the raw stage chunk c - 1 freed and the MMAs of
+    // chunk c - 1 (converted in the previous pass) while warps 1.. convert chunk c
+    if (warp == 0) {
+      if (tid == 0 && c >= 1) {
+        if (c - 1 + NR < nchunks && chunk_rows(c - 1 + NR) == KT) issue_copy(c - 1 + NR);
+        issue_mmas(c - 1);
+      }
+    } else {
+      constexpr int kConv = kTT - 32;  // converting threads
+      for (int it = tid - 32; it < nitems; it += 2 * kConv) {
+        float x0[4], y0[4], x1[4], y1[4];
+        const bool two = it + kConv < nitems;
+        load_item(it, x0, y0);
+        if (two) load_item(it + kConv, x1, y1);
+        store_item(it, x0, y0);
+        if (two) store_item(it + kConv, x1, y1);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();  // raw stage sr consumed, operand stage s written
-    const int gseg = c / kFlush;
-    const bool seg_end = c % kFlush == kFlush - 1 || c == nchunks - 1;
-    if (tid == 0) {
-      if (c + NR < nchunks && chunk_rows(c + NR) == KT) issue_copy(c + NR);
-      tc_fence_after();
-      const uint32_t dcol = taddr + acc_col(gseg);
-#pragma unroll
-      for (int ks = 0; ks < KT / 8; ++ks)
-        for (int t = 0; t < mtiles; ++t)
-#pragma unroll
-          for (int p = 0; p < 3; ++p) {
-            const uint64_t ad = (s ? dA1[p] : dA0[p]) + (uint64_t)((ks * 256u + (uint32_t)t * 512u * KT) >> 4);
-            const uint64_t bd = (s ? dB1[p] : dB0[p]) + (uint64_t)((ks * 256u) >> 4);
-            mma_tf32(dcol + (uint32_t)(t * npad), ad, bd, idesc, (c % kFlush > 0 || ks > 0 || p > 0) ? 1u : 0u);
-          }
-      mma_commit(op_free + s);
-      mma_last = c;
-    }
-    // ---- end of a segment (float64 block in global memory): wait for the MMAs and add the FP32
-    // accumulator into this CTA's partial block
-    if (!kDefer && seg_end) {
-      const bool ok = tid == 0 ? mbar_wait(op_free + s, (uint32_t)((c >> 1) & 1)) : true;
+    // ---- chunk c - 1 ended a segment (float64 block in global memory): wait for its MMAs and add
+    // the FP32 accumulator into this CTA's partial block before the next segment's first MMAs
+    if (!kDefer && c >= 1 && (c - 1) % kFlush == kFlush - 1) {
+      const int cm = c - 1;
+      const bool ok = tid == 0 ? mbar_wait(op_free + (cm & 1), (uint32_t)((cm >> 1) & 1)) : true;
       if (__syncthreads_or(!ok)) {
         failed = true;
         ++c;  // chunk c was consumed
         break;
       }
-      if (tid != 0) mbar_wait(op_free + s, (uint32_t)((c >> 1) & 1));  // completed: returns at once
+      if (tid != 0) mbar_wait(op_free + (cm & 1), (uint32_t)((cm >> 1) & 1));  // completed: returns at once
       tc_fence_after();
-      flush(c < kFlush, 0u);
+      flush(cm < kFlush, 0u);
       tc_fence_before();
       __syncthreads();
     }
   }
-  // deferred mode: the segments not yet added (the last one or two), once every MMA is complete
-  if (kDefer && !failed && flushed < nseg) {
-    const int last = nchunks - 1;  // the last chunk's MMAs (every thread knows it; mma_last is thread 0's)
+  // the last chunk's MMAs, then the segments not yet added, once every MMA is complete
+  if (!failed && nchunks > 0) {
+    if (tid == 0) issue_mmas(nchunks - 1);
+    const int last = nchunks - 1;  // (every thread knows it; mma_last is thread 0's)
     const uint32_t par = (uint32_t)((last >> 1) & 1);
     const bool ok = tid == 0 ? mbar_wait(op_free + (last & 1), par) : true;
     if (__syncthreads_or(!ok)) {
@@ -432,7 +442,11 @@ __global__ void __launch_bounds__(kTT, 1) gram_tc_kernel(const TcGramArgs g) {
     } else {
       if (tid != 0) mbar_wait(op_free + (last & 1), par);  // completed: returns at once
       tc_fence_after();
-      for (; flushed < nseg; ++flushed) flush(false, acc_col(flushed));
+      if constexpr (kDefer) {
+        for (; flushed < nseg; ++flushed) flush(false, acc_col(flushed));
+      } else {
+        flush(last < kFlush, 0u);  // the last segment
+      }
       tc_fence_before();
       __syncthreads();
     }
