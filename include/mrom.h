@@ -583,11 +583,11 @@ mrom_status mrom_fp64_peak(mrom_handle h, int32_t iters, double* tflops, double*
  * one fixed array of MROM_NOALLOC_SCRATCH_BYTES (64 MiB) of device memory inside
  * this library, which every GPU that loads the library holds until the process
  * exits.  The paper has no counterpart to this entry point.
- *  - Not for stream capture: every call uploads its tables from host memory that
- *    lives only during the call, so a captured graph would replay a stale copy
- *    (graphs use a plan: mrom_plan_create, mrom_plan_sweep).
+ *  - Every call copies its object and task tables from host memory that lives
+ *    only for the duration of the call.  To replay a sweep from a CUDA graph,
+ *    use a plan (mrom_plan_create, mrom_plan_sweep).
  *  - The first call on a device looks up that array's device address
- *    (cudaGetSymbolAddress).
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
  *    With CUDA's lazy module loading (the default) the array is committed on a
  *    device when that first call loads this code, not when the library is
  *    loaded: a caller that reserves the rest of its memory budget afterwards
