@@ -38,6 +38,86 @@ __device__ __forceinline__ void tri_rc(int e, int& i, int& j) {
   j = e - t * (t + 1) / 2;
 }
 
+// Q1 = P_0 P_1 ... P_{r-3} from the reflectors left by a Householder reduction (vat(k, i) = entry i of
+// the vector of step k, tau in stau), accumulated backwards on the trailing block; then the phases
+// D_0 = 1, D_{k+1} = D_k e_k / |e_k| that make D^H T D real with off-diagonal |e_k| (se), and
+// Q = Q1 D.  Scratch (shared): sph (r entries), part (NT entries).  All threads of the CTA call it.
+template <int NT, class VAt>
+__device__ void accumulate_q1(VAt vat, int r, double2* Q, double* se, double* stau, double2* salpha, double2* sph,
+                              double2* part) {
+  const int tid = threadIdx.x;
+  // Q1 = P_0 P_1 ... P_{r-3} (in Q), backward accumulation on the trailing block
+  for (int idx = tid; idx < r * r; idx += NT) {
+    const int i = idx / r, j = idx - (idx / r) * r;
+    Q[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int k = r - 3; k >= 0; --k) {
+    const double tau = stau[k];
+    if (tau == 0.0) continue;
+    const int m = r - k - 1;
+    // u_j = sum_i conj(v_i) Q[k+1+i][k+1+j], then Q_sub -= tau v u; with fewer columns than
+    // threads the i range is split into G slices summed separately, then in a fixed order
+    const int G = m <= NT ? min(8, NT / m) : 1;
+    if (G > 1) {
+      for (int idx = tid; idx < m * G; idx += NT) {
+        const int j = idx % m, g = idx / m;
+        const int i1 = (g + 1) * m / G;
+        double2 s = make_double2(0.0, 0.0);
+        for (int i = g * m / G; i < i1; ++i) s = cmacc(s, vat(k, i), Q[(k + 1 + i) * r + (k + 1 + j)]);
+        part[idx] = s;
+      }
+      __syncthreads();
+      for (int j = tid; j < m; j += NT) {
+        double2 s = part[j];
+        for (int g = 1; g < G; ++g) s = make_double2(s.x + part[g * m + j].x, s.y + part[g * m + j].y);
+        sph[j] = make_double2(tau * s.x, tau * s.y);
+      }
+    } else {
+      for (int j = tid; j < m; j += NT) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int i = 0; i < m; ++i) s = cmacc(s, vat(k, i), Q[(k + 1 + i) * r + (k + 1 + j)]);
+        sph[j] = make_double2(tau * s.x, tau * s.y);
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += NT) {
+      const int i = idx / m, j = idx - (idx / m) * m;
+      const double2 v = vat(k, i), u = sph[j];
+      double2 a = Q[(k + 1 + i) * r + (k + 1 + j)];
+      a.x = fma(-v.x, u.x, fma(v.y, u.y, a.x));
+      a.y = fma(-v.x, u.y, fma(-v.y, u.x, a.y));
+      Q[(k + 1 + i) * r + (k + 1 + j)] = a;
+    }
+    __syncthreads();
+  }
+
+  // phases: D_0 = 1, D_{k+1} = D_k e_k / |e_k| makes D^H T D real with
+  // off-diagonal |e_k|; Z = Q1 D
+  if (tid == 0) {
+    double2 D = make_double2(1.0, 0.0);
+    sph[0] = D;
+    for (int k = 0; k + 1 < r; ++k) {
+      const double2 e = salpha[k];
+      const double ae = hypot(e.x, e.y);
+      se[k] = ae;
+      if (ae > 0.0) {
+        const double2 u = make_double2(e.x / ae, e.y / ae);
+        D = make_double2(D.x * u.x - D.y * u.y, D.x * u.y + D.y * u.x);
+      }
+      sph[k + 1] = D;
+    }
+    se[r - 1] = 0.0;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < r * r; idx += NT) {
+    const int j = idx - (idx / r) * r;
+    const double2 a = Q[idx], D = sph[j];
+    Q[idx] = make_double2(a.x * D.x - a.y * D.y, a.x * D.y + a.y * D.x);
+  }
+  __syncthreads();
+}
+
 // Householder tridiagonalisation of the Hermitian r x r matrix H (row-major, full storage;
 // overwritten, the Householder vectors end up below its subdiagonal).  For column k,
 // x = H[k+1:, k], alpha = -phase(x_0) ||x||, v = x - alpha e_1, tau = 1 / (||x|| (||x|| + |x_0|)),
@@ -133,76 +213,153 @@ __device__ void herm_tridiag(double2* H, int r, double2* Q, double* sd, double* 
   }
   __syncthreads();
 
-  // Q1 = P_0 P_1 ... P_{r-3} (in Q), backward accumulation on the trailing block
-  for (int idx = tid; idx < r * r; idx += NT) {
-    const int i = idx / r, j = idx - (idx / r) * r;
-    Q[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-  }
-  __syncthreads();
-  for (int k = r - 3; k >= 0; --k) {
-    const double tau = stau[k];
-    if (tau == 0.0) continue;
-    const int m = r - k - 1;
-    // u_j = sum_i conj(v_i) Q[k+1+i][k+1+j], then Q_sub -= tau v u; with fewer columns than
-    // threads the i range is split into G slices summed separately, then in a fixed order
-    const int G = m <= NT ? min(8, NT / m) : 1;
-    if (G > 1) {
-      for (int idx = tid; idx < m * G; idx += NT) {
-        const int j = idx % m, g = idx / m;
-        const int i1 = (g + 1) * m / G;
-        double2 s = make_double2(0.0, 0.0);
-        for (int i = g * m / G; i < i1; ++i) s = cmacc(s, H[(k + 1 + i) * r + k], Q[(k + 1 + i) * r + (k + 1 + j)]);
-        part[idx] = s;
-      }
-      __syncthreads();
-      for (int j = tid; j < m; j += NT) {
-        double2 s = part[j];
-        for (int g = 1; g < G; ++g) s = make_double2(s.x + part[g * m + j].x, s.y + part[g * m + j].y);
-        sph[j] = make_double2(tau * s.x, tau * s.y);
-      }
-    } else {
-      for (int j = tid; j < m; j += NT) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int i = 0; i < m; ++i) s = cmacc(s, H[(k + 1 + i) * r + k], Q[(k + 1 + i) * r + (k + 1 + j)]);
-        sph[j] = make_double2(tau * s.x, tau * s.y);
-      }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < m * m; idx += NT) {
-      const int i = idx / m, j = idx - (idx / m) * m;
-      const double2 v = H[(k + 1 + i) * r + k], u = sph[j];
-      double2 a = Q[(k + 1 + i) * r + (k + 1 + j)];
-      a.x = fma(-v.x, u.x, fma(v.y, u.y, a.x));
-      a.y = fma(-v.x, u.y, fma(-v.y, u.x, a.y));
-      Q[(k + 1 + i) * r + (k + 1 + j)] = a;
-    }
-    __syncthreads();
-  }
+  accumulate_q1<NT>([&](int k, int i) { return H[(k + 1 + i) * r + k]; }, r, Q, se, stau, salpha, sph, part);
+}
 
-  // phases: D_0 = 1, D_{k+1} = D_k e_k / |e_k| makes D^H T D real with
-  // off-diagonal |e_k|; Z = Q1 D
-  if (tid == 0) {
-    double2 D = make_double2(1.0, 0.0);
-    sph[0] = D;
-    for (int k = 0; k + 1 < r; ++k) {
-      const double2 e = salpha[k];
-      const double ae = hypot(e.x, e.y);
-      se[k] = ae;
-      if (ae > 0.0) {
-        const double2 u = make_double2(e.x / ae, e.y / ae);
-        D = make_double2(D.x * u.x - D.y * u.y, D.x * u.y + D.y * u.x);
-      }
-      sph[k + 1] = D;
+// Offset of entry (a, b), b <= a, in a packed lower triangle (row a holds columns 0..a).
+__device__ __forceinline__ int tri_at(int a, int b) { return a * (a + 1) / 2 + b; }
+
+// herm_tridiag for a matrix held in shared memory as its packed lower triangle H (tri_at), with
+// the same reflectors, outputs and conventions (Q = Q1 D row-major in any memory, sd, se, stau,
+// salpha; the Householder vectors end up below the subdiagonal of H's columns).  Per column
+// four CTA barriers: (B) the reflector's vector v, (C) p = tau H_sub v as partial sums of column
+// blocks (one item per row and block, no warp reductions on the FP64 pipe), (D) the totals per
+// row and the real part of v^H p, (A) the rank-2 update of the lower triangle, which also sums
+// the squares of the next column.  Scratch (shared): sv, sp (r entries each), red, red2 (NT/32
+// each), part (NT entries).  All threads of the CTA call it.
+template <int NT>
+__device__ void herm_tridiag_packed(double2* __restrict__ H, int r, double2* __restrict__ Q, double* sd, double* se,
+                                    double* stau, double2* salpha, double2* __restrict__ sv,
+                                    double2* __restrict__ sp, double* red, double* red2, double2* __restrict__ part) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  {  // squares of the first column below the diagonal
+    double q = 0.0;
+    for (int i = 1 + tid; i < r; i += NT) {
+      const double2 x = H[tri_at(i, 0)];
+      q = fma(x.x, x.x, fma(x.y, x.y, q));
     }
-    se[r - 1] = 0.0;
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) red2[warp] = q;
   }
   __syncthreads();
-  for (int idx = tid; idx < r * r; idx += NT) {
-    const int j = idx - (idx / r) * r;
-    const double2 a = Q[idx], D = sph[j];
-    Q[idx] = make_double2(a.x * D.x - a.y * D.y, a.x * D.y + a.y * D.x);
+  for (int k = 0; k + 2 < r; ++k) {
+    const int m = r - k - 1, K = k + 1;
+    double nx2 = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) nx2 += red2[w];
+    if (tid == 0) sd[k] = H[tri_at(k, k)].x;
+    if (!(nx2 > 0.0)) {  // column already reduced: no reflector; the next column's squares
+      if (tid == 0) {
+        stau[k] = 0.0;
+        salpha[k] = make_double2(0.0, 0.0);
+      }
+      double q = 0.0;
+      for (int i = 1 + tid; i < m; i += NT) {
+        const double2 x = H[tri_at(K + i, K)];
+        q = fma(x.x, x.x, fma(x.y, x.y, q));
+      }
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      __syncthreads();  // every thread has read red2
+      if (lane == 0) red2[warp] = q;
+      __syncthreads();
+      continue;
+    }
+    const double nx = sqrt(nx2);
+    const double2 x0 = H[tri_at(K, k)];
+    const double a0 = hypot(x0.x, x0.y);
+    const double2 ph = a0 > 0.0 ? make_double2(x0.x / a0, x0.y / a0) : make_double2(1.0, 0.0);
+    const double tau = 1.0 / (nx * (nx + a0));
+    // v_0 = x_0 - alpha = ph (|x_0| + ||x||); the other entries of v are those of x
+    const double2 v0 = make_double2(ph.x * (a0 + nx), ph.y * (a0 + nx));
+    for (int i = tid; i < m; i += NT) sv[i] = i == 0 ? v0 : H[tri_at(K + i, k)];
+    __syncthreads();  // (B) v complete; every thread has read x_0 and red2
+    if (tid == 0) {   // nothing reads this entry again before the accumulation of Q1
+      H[tri_at(K, k)] = v0;
+      stau[k] = tau;
+      salpha[k] = make_double2(-ph.x * nx, -ph.y * nx);
+    }
+    // p = tau H_sub v: item t = b m + i sums row i over the columns of block b (nb blocks of bw),
+    // reading the upper part of a row as the conjugate of the stored column
+    const int nb = min((m + 3) / 4, max(1, NT / m));
+    const int bw = (m + nb - 1) / nb;
+    for (int t = tid; t < m * nb; t += NT) {
+      const int b = t / m, i = t - b * m;
+      const int j1 = min(m, (b + 1) * bw);
+      double2 acc = make_double2(0.0, 0.0);
+      for (int j = b * bw; j < j1; ++j) {
+        const bool lo = j <= i;
+        double2 h = H[lo ? tri_at(K + i, K + j) : tri_at(K + j, K + i)];
+        if (!lo) h.y = -h.y;
+        acc = cmac(acc, h, sv[j]);
+      }
+      part[t] = acc;
+    }
+    __syncthreads();  // (C)
+    double kp = 0.0;  // this thread's part of Re(v^H p)
+    for (int i = tid; i < m; i += NT) {
+      double2 q = part[i];
+      for (int b = 1; b < nb; ++b) {
+        const double2 u = part[b * m + i];
+        q.x += u.x;
+        q.y += u.y;
+      }
+      const double2 p = make_double2(tau * q.x, tau * q.y), v = sv[i];
+      sp[i] = p;
+      kp = fma(v.x, p.x, fma(v.y, p.y, kp));
+    }
+    if (warp * 32 < m)  // warps without rows contribute zero
+      for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
+    if (lane == 0) red[warp] = kp;
+    __syncthreads();  // (D)
+    double kr = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) kr += red[w];
+    kr *= 0.5 * tau;
+    // H_sub -= v w^H + w v^H with w = p - K v, K = (tau/2) v^H p (real), on the lower triangle.
+    // Rows are taken in pairs (a, m - 1 - a), m + 1 entries per pair, so that a flat index maps
+    // to (i, j) with one division; the middle row of an odd m is alone in its pair.
+    const int len = m + 1, npair = (m + 1) / 2;
+    const float rlen = 1.0f / (float)len;
+    double q = 0.0;  // squares of the next column (j = 0, i >= 1)
+    for (int e = tid; e < npair * len; e += NT) {
+      int pr = (int)((float)e * rlen);
+      if (pr * len > e) --pr;
+      else if ((pr + 1) * len <= e) ++pr;
+      const int c = e - pr * len;
+      int i = pr, j = c;
+      if (c > pr) {
+        i = m - 1 - pr;
+        j = c - pr - 1;
+        if (i == pr) continue;
+      }
+      const double2 vi = sv[i], vj = sv[j], pi = sp[i], pj = sp[j];
+      const double2 wi = make_double2(fma(-kr, vi.x, pi.x), fma(-kr, vi.y, pi.y));
+      const double2 wj = make_double2(fma(-kr, vj.x, pj.x), fma(-kr, vj.y, pj.y));
+      double2* h = H + tri_at(K + i, K + j);
+      double2 a = *h;
+      // a - vi conj(wj) - wi conj(vj)
+      a.x = fma(-vi.x, wj.x, fma(-vi.y, wj.y, fma(-wi.x, vj.x, fma(-wi.y, vj.y, a.x))));
+      a.y = fma(-vi.y, wj.x, fma(vi.x, wj.y, fma(-wi.y, vj.x, fma(wi.x, vj.y, a.y))));
+      if (i == j) a.y = 0.0;
+      *h = a;
+      if (j == 0 && i >= 1) q = fma(a.x, a.x, fma(a.y, a.y, q));
+    }
+    if (__any_sync(0xffffffffu, q != 0.0))
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) red2[warp] = q;
+    __syncthreads();  // (A)
+  }
+  // the last 2 x 2 block is already tridiagonal
+  if (tid == 0) {
+    for (int k = (r >= 2 ? r - 2 : 0); k < r; ++k) sd[k] = H[tri_at(k, k)].x;
+    if (r >= 2) {
+      salpha[r - 2] = H[tri_at(r - 1, r - 2)];
+      stau[r - 2] = 0.0;
+    }
   }
   __syncthreads();
+  accumulate_q1<NT>([&](int k, int i) { return H[tri_at(k + 1 + i, k)]; }, r, Q, se, stau, salpha, sv, part);
 }
 
 // One Givens step of the implicit QL chase: from f = s e_i, g, returns c, s and h = |(f, g)|

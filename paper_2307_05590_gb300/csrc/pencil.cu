@@ -97,10 +97,13 @@ __device__ __forceinline__ double2 gram_herm(const double2* __restrict__ Gh, int
 // conquer) and finishing, each with one CTA per object.
 //
 // Tridiagonalisation: persistent CTAs, objects in descending r.  Three r x r complex
-// matrices in the CTA's slice of a global workspace (L2-resident): W0, W1, W2.
+// matrices in the CTA's slice of a global workspace (L2-resident): W0, W1, W2, and the
+// Hermitian matrix H as its packed lower triangle in shared memory (r (r + 1) / 2 entries,
+// dynamic), where the Householder reduction runs.
 //   W0: C -> L (strictly lower; diagonal in sd) -> X^H, X = L^-1 K' -> Q1 -> Z = Q1 D
-//   W1: K' -> H (full Hermitian) -> Householder vectors below the subdiagonal
+//   W1: K'
 //   W2: L^-1 (lower)
+//   sH: H -> Householder vectors below the subdiagonal
 // Output per object: the real tridiagonal D^H Q1^H H Q1 D (diagonal in lam, off-diagonal
 // in the scratch e) and W = L^-H Z; V = W Q2 once the tridiagonal is diagonalised (Q2 = Z2).
 __global__ void __launch_bounds__(kPT, 2)
@@ -110,9 +113,12 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
                    const double* __restrict__ omega, int omega_stride, int n_w,
                    const double* __restrict__ s_sigma, const double* __restrict__ s_mu, int* __restrict__ pen_ok,
                    double2* __restrict__ ws, size_t ws_elems, double gate, double kappa_max) {
+  static_assert(MROM_MAX_R <= kPT, "the packed Householder reduction takes r <= threads per CTA");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sH = reinterpret_cast<double2*>(smem_raw);  // packed lower triangle of H
   __shared__ double sd[MROM_MAX_R], se[MROM_MAX_R], stau[MROM_MAX_R];
-  __shared__ double2 salpha[MROM_MAX_R], sph[MROM_MAX_R], spart[kPT];
-  __shared__ double red[kPW];
+  __shared__ double2 salpha[MROM_MAX_R], sph[MROM_MAX_R], spv[MROM_MAX_R], spart[kPT];
+  __shared__ double red[kPW], red2[kPW];
   __shared__ int s_task;
   const int tid = threadIdx.x;
   double2* W0 = ws + (size_t)blockIdx.x * ws_elems;
@@ -222,7 +228,7 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
     ln = block_sum(ln, red);
     ok = ok && (sqrt(cn) * ln <= kappa_max);
 
-    // ---- 3. X = L^-1 K' (W0)  and  4. H = X L^-H (W1, lower then mirrored)
+    // ---- 3. X = L^-1 K' (W0)  and  4. H = X L^-H (lower triangle, packed, in sH)
     double hn = 0.0;
     if (ok) {
       // X = L^-1 K', stored conjugate-transposed: W0[j][i] = conj(X[i][j]); one thread per (i, j),
@@ -236,7 +242,7 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
       __syncthreads();
       // H[i][j] = sum_{k <= j} X[i][k] conj(L^-1[j][k]) = conj(sum_k W0[k][i] L^-1[j][k]) for
       // i >= j: one thread per entry of the lower triangle taken column by column (trip count
-      // j + 1 shared along a column); mirrored into the upper triangle
+      // j + 1 shared along a column)
       const int ntri = r * (r + 1) / 2;
       for (int e = tid; e < ntri; e += kPT) {
         // column j holds entries S(j) .. S(j + 1) - 1, S(j) = j r - j (j - 1) / 2
@@ -248,18 +254,16 @@ pencil_tridiag_kernel(const RomDev* __restrict__ objs, const PencilDev* __restri
         double2 s = make_double2(0.0, 0.0);
         for (int k = 0; k <= j; ++k) s = cmac(s, W0[k * r + i], W2[j * r + k]);
         if (i == j) s.y = 0.0;
-        W1[i * r + j] = make_double2(s.x, -s.y);
-        W1[j * r + i] = s;
+        sH[hq::tri_at(i, j)] = make_double2(s.x, -s.y);
         hn += (i == j ? 1.0 : 2.0) * (s.x * s.x + s.y * s.y);
       }
     }
     hn = block_sum(hn, red);
     ok = ok && (DBL_EPSILON * sqrt(hn) <= gate * wmin);
 
-    // ---- 5.-7. Householder tridiagonalisation of H (W1), Z = Q1 D (W0), real tridiagonal (sd, se);
-    // p of each Householder step lives in W0's first row (W0 is free until Q1 is formed)
+    // ---- 5.-7. Householder tridiagonalisation of H (sH), Z = Q1 D (W0), real tridiagonal (sd, se)
     if (ok) {
-      hq::herm_tridiag<kPT>(W1, r, W0, sd, se, stau, salpha, sph, W0, red, spart);
+      hq::herm_tridiag_packed<kPT>(sH, r, W0, sd, se, stau, salpha, sph, spv, red, red2, spart);
 
       // ---- 8. W = L^-H Z (per-object buffer): W[i][j] = sum_{k >= i} conj(Linv[k][i]) Z[k][j];
       // the real tridiagonal (sd, se) goes to the eigenproblem kernel, W to the finishing kernel
@@ -393,7 +397,6 @@ __device__ void pencil_split_tables(const PencilDev& pd, int r, double2 (*rs)[3 
     const int x = idx / nb, rem = idx - (idx / nb) * nb;
     const int k = rem / 3, j = rem - (rem / 3) * 3;
     const int slot = x == 0 ? 6 : (x == 1 ? 12 : (x == 2 ? 9 : 18));
-    const double lk = pd.lam[k];
     const bool on = present(x);
     double2 d = make_double2(0.0, 0.0);  // the certificate's source row
     if (pd.gsh && x == 0) {
@@ -1164,9 +1167,12 @@ cudaError_t launch_pencil_prep(const RomDev* objs, const PencilDev* pens, const 
                                int n_w, const double* s_sigma, const double* s_mu, int* pen_ok, double2* ws,
                                size_t ws_elems, int grid, int rmax, double gate, double kappa_max,
                                cudaStream_t stream) {
-  pencil_tridiag_kernel<<<grid, kPT, 0, stream>>>(objs, pens, scr, order, n_elig, counters, omega, omega_stride, n_w,
-                                                  s_sigma, s_mu, pen_ok, ws, ws_elems, gate, kappa_max);
-  cudaError_t e = cudaGetLastError();
+  const size_t smem_h = (size_t)rmax * (rmax + 1) / 2 * sizeof(double2);  // packed H
+  cudaError_t e = cudaFuncSetAttribute(pencil_tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
+  if (e != cudaSuccess) return e;
+  pencil_tridiag_kernel<<<grid, kPT, smem_h, stream>>>(objs, pens, scr, order, n_elig, counters, omega, omega_stride,
+                                                       n_w, s_sigma, s_mu, pen_ok, ws, ws_elems, gate, kappa_max);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // the tridiagonal eigenproblems, one CTA per object (work counter: counters[6]); three CTAs per
   // SM fill each other's barrier waits (the grid is two per SM for the other kernels)
