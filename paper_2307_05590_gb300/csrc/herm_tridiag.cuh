@@ -222,11 +222,11 @@ __device__ __forceinline__ int tri_at(int a, int b) { return a * (a + 1) / 2 + b
 // herm_tridiag for a matrix held in shared memory as its packed lower triangle H (tri_at), with
 // the same reflectors, outputs and conventions (Q = Q1 D row-major in any memory, sd, se, stau,
 // salpha; the Householder vectors end up below the subdiagonal of H's columns).  Per column
-// four CTA barriers: (B) the reflector's vector v, (C) p = tau H_sub v as partial sums of column
+// five CTA barriers: (B) the reflector's vector v, (C) p = tau H_sub v as partial sums of column
 // blocks (one item per row and block, no warp reductions on the FP64 pipe), (D) the totals per
-// row and the real part of v^H p, (A) the rank-2 update of the lower triangle, which also sums
-// the squares of the next column.  Scratch (shared): sv, sp (r entries each), red, red2 (NT/32
-// each), part (NT entries).  All threads of the CTA call it.
+// row and the real part of v^H p, (E) w = p - K v, (A) the rank-2 update of the lower triangle,
+// which also sums the squares of the next column.  Scratch (shared): sv, sp (r entries each),
+// red, red2 (NT/32 each), part (NT entries).  All threads of the CTA call it.
 template <int NT>
 __device__ void herm_tridiag_packed(double2* __restrict__ H, int r, double2* __restrict__ Q, double* sd, double* se,
                                     double* stau, double2* salpha, double2* __restrict__ sv,
@@ -312,11 +312,18 @@ __device__ void herm_tridiag_packed(double2* __restrict__ H, int r, double2* __r
       for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
     if (lane == 0) red[warp] = kp;
     __syncthreads();  // (D)
-    double kr = 0.0;
+    {  // w = p - K v in place of p, K = (tau/2) v^H p (real)
+      double kr = 0.0;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) kr += red[w];
-    kr *= 0.5 * tau;
-    // H_sub -= v w^H + w v^H with w = p - K v, K = (tau/2) v^H p (real), on the lower triangle.
+      for (int w = 0; w < NW; ++w) kr += red[w];
+      kr *= 0.5 * tau;
+      for (int i = tid; i < m; i += NT) {
+        const double2 v = sv[i], p = sp[i];
+        sp[i] = make_double2(fma(-kr, v.x, p.x), fma(-kr, v.y, p.y));
+      }
+    }
+    __syncthreads();  // (E)
+    // H_sub -= v w^H + w v^H on the lower triangle.
     // Rows are taken in pairs (a, m - 1 - a), m + 1 entries per pair, so that a flat index maps
     // to (i, j) with one division; the middle row of an odd m is alone in its pair.
     const int len = m + 1, npair = (m + 1) / 2;
@@ -333,9 +340,7 @@ __device__ void herm_tridiag_packed(double2* __restrict__ H, int r, double2* __r
         j = c - pr - 1;
         if (i == pr) continue;
       }
-      const double2 vi = sv[i], vj = sv[j], pi = sp[i], pj = sp[j];
-      const double2 wi = make_double2(fma(-kr, vi.x, pi.x), fma(-kr, vi.y, pi.y));
-      const double2 wj = make_double2(fma(-kr, vj.x, pj.x), fma(-kr, vj.y, pj.y));
+      const double2 vi = sv[i], vj = sv[j], wi = sp[i], wj = sp[j];
       double2* h = H + tri_at(K + i, K + j);
       double2 a = *h;
       // a - vi conj(wj) - wi conj(vj)

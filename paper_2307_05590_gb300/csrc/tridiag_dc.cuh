@@ -20,7 +20,10 @@
 //   - z is recomputed from the roots (Loewner's formula, z^_i^2 = prod_j (lambda_j - d_i) /
 //     (rho prod_{j!=i} (d_j - d_i)), as products of ratios of order one), which makes the
 //     eigenvectors u_j = (z^_i / (d_i - lambda_j))_i / norm orthogonal to working precision;
-//   - Q <- Q P U for the block (one float64 GEMM, n x k x k).
+//   - Q <- Q P U for the block (one float64 GEMM, n x k x k); Q is block diagonal in the two
+//     halves except for columns that a deflation rotation mixed, so a row of the upper half sums
+//     only over the kept columns with entries there (and likewise the lower half): the terms
+//     skipped are exact zeros, and about half of the GEMM's multiplications go.
 // tol = 8 eps max(max|d|, rho max z^2).  Q lives in global memory (L2-resident workspace), per-
 // position data in shared memory.  A non-finite value clears *ok (the caller then routes the
 // object elsewhere); every loop is bounded.
@@ -48,12 +51,17 @@ struct DcShared {
   double rc[kDcMaxN];      // deflation rotations (c, s) per merge, at the merge's offset
   double rs[kDcMaxN];
   int perm[kDcMaxN];       // sorted position -> column offset within the merge
+  int ty[kDcMaxN];         // rows with entries in the column at a sorted position: 1 upper, 2 lower
+  int klist[2 * kDcMaxN];  // per merge at 2 a: kept indices with upper rows, then (at 2 a + nmg) lower
+  int kcol[2 * kDcMaxN];   // their column offsets within the merge
   int keep[kDcMaxN];       // kept sorted positions, per merge at its offset
   int kinv[kDcMaxN];       // sorted position -> kept index (or -1)
   int org[kDcMaxN];        // root origin (kept index of the pole), per kept index
   int rpair[2 * kDcMaxN];  // deflation rotation column pairs (sorted positions)
   int nk[kDcMaxN / 2 + 1]; // kept count per merge
   int nrot[kDcMaxN / 2 + 1];
+  int nk1[kDcMaxN / 2 + 1];  // kept columns with entries in the upper rows, per merge
+  int nk2[kDcMaxN / 2 + 1];  // ... in the lower rows
   double rho[kDcMaxN / 2 + 1];
   int bad;
 };
@@ -315,6 +323,7 @@ __device__ double* tridiag_dc(const double* __restrict__ dg, const double* __res
         zmax = fmax(zmax, fabs(S.zs[p]));
       }
       const double tol = 8.0 * DBL_EPSILON * fmax(dmax, rho * zmax * zmax);
+      for (int p = a; p < a + nmg; ++p) S.ty[p] = S.perm[p] < bs ? 1 : 2;
       int last = -1, nr = 0;
       for (int p = a; p < a + nmg; ++p) {
         S.kinv[p] = 0;
@@ -335,6 +344,7 @@ __device__ double* tridiag_dc(const double* __restrict__ dg, const double* __res
           S.rs[a + nr] = sn;
           S.rpair[2 * (a + nr)] = last;
           S.rpair[2 * (a + nr) + 1] = p;
+          S.ty[last] |= S.ty[p];  // the rotation mixes the two columns' rows
           ++nr;
         } else {
           last = p;
@@ -346,7 +356,21 @@ __device__ double* tridiag_dc(const double* __restrict__ dg, const double* __res
           S.keep[a + k] = p;
           S.kinv[p] = k++;
         }
+      int n1 = 0, n2 = 0;
+      for (int i = 0; i < k; ++i) {
+        const int sp = S.keep[a + i], t = S.ty[sp];
+        if (t & 1) {
+          S.klist[2 * a + n1] = i;
+          S.kcol[2 * a + n1++] = S.perm[sp];
+        }
+        if (t & 2) {
+          S.klist[2 * a + nmg + n2] = i;
+          S.kcol[2 * a + nmg + n2++] = S.perm[sp];
+        }
+      }
       S.nk[mi] = k;
+      S.nk1[mi] = n1;
+      S.nk2[mi] = n2;
       S.nrot[mi] = nr;
       S.rho[mi] = rho;
     }
@@ -430,11 +454,13 @@ __device__ double* tridiag_dc(const double* __restrict__ dg, const double* __res
           v = Q[(size_t)p * n + a + S.perm[sp]];
           lamv = S.ds[sp];
         } else {
-          const int k = S.nk[mi];
           const int* kp = S.keep + a;
           const double* qrow = Q + (size_t)p * n + a;
+          const bool up = p - a < bs;  // the half of the merge that row p lies in
+          const int nl = up ? S.nk1[mi] : S.nk2[mi], l0 = 2 * a + (up ? 0 : nmg);
           double acc = 0.0;
-          for (int i = 0; i < k; ++i) acc = fma(qrow[S.perm[kp[i]]], U[(size_t)(a + i) * n + a + j], acc);
+          for (int t = 0; t < nl; ++t)
+            acc = fma(qrow[S.kcol[l0 + t]], U[(size_t)(a + S.klist[l0 + t]) * n + a + j], acc);
           v = acc * S.cn[a + j];
           lamv = S.ds[kp[S.org[a + j]]] + S.tau[a + j];
         }
