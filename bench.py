@@ -45,9 +45,12 @@ UNIT = "evals/s"
 SM_COUNT_NOMINAL = 152
 DFMA_PER_CLK_PER_SM = 2           # GB300 DFMA rate: 4 flop/clk/SM (mrom_fp64_peak measures it in every run)
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one pencil_sweep_kernel launch on
-# this workload, from a one-pass ncu capture of the current kernel at full size (350.77 MB read +
-# 370.79 MB written); None once the kernel changes until it is captured again
-SWEEP_DRAM_BYTES_PER_LAUNCH = 350_770_000 + 370_790_000
+# this workload, from a one-pass ncu capture of the current kernel at full size; None once the kernel
+# changes until it is captured again.  The last capture (350.77 MB read + 370.79 MB written) was of
+# the kernel before its R and I row sums were regrouped and its frequency groups per task tuned.
+SWEEP_DRAM_BYTES_PER_LAUNCH = None
+SWEEP_DRAM_NOTE = ("not recaptured since the kernel last changed; the previous version's one-pass "
+                   "capture read 350.77 MB and wrote 370.79 MB per launch")
 # object groups of the end-to-end leg (mrom_sweep_host)
 E2E_CHUNKS = 2
 
@@ -957,6 +960,8 @@ def main():
                              + (", below this kernel's own rate, so the derived figure is the denominator"
                                 if fp64_measured < achieved else ""),
                 "fp64_probe_in_run": fp64_measured}
+    if SWEEP_DRAM_BYTES_PER_LAUNCH is None:
+        roofline["traffic_note"] = SWEEP_DRAM_NOTE
     stage_info = {"prep_ms": st[0], "route_ms": st[1], "pencil_sweep_ms": st[2], "lu_sweep_ms": st[3],
                   "prep_flops": flops_prep, "prep_tflops": flops_prep / (st[0] * 1e-3) / 1e12 if st[0] > 0 else None,
                   "objects_pencil": n_pen, "objects_lu": n_lu}
