@@ -1,5 +1,8 @@
-// Hermitian tridiagonalisation (Householder) and implicit QL, shared by the pencil
-// preparation and the snapshot eigensolver.  Device code only; one CTA of NT threads.
+// Hermitian tridiagonalisation (Householder) and implicit QL for the pencil preparation and the
+// snapshot eigensolver: herm_tridiag on a full matrix in any memory (snapshot Grams up to
+// MROM_MAX_SNAPSHOTS), herm_tridiag_packed on a packed lower triangle in shared memory (the
+// pencil's H, r <= MROM_MAX_R), both finished by accumulate_q1.  Device code only; one CTA of NT
+// threads.
 #pragma once
 
 #include <cfloat>
