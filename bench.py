@@ -628,6 +628,8 @@ def main():
     ap.add_argument("--n-obj", type=int, default=1000)
     ap.add_argument("--n-w", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--e2e-chunks", type=int, default=E2E_CHUNKS,
+                    help="object groups of the end-to-end leg (mrom_sweep_host n_chunks)")
     ap.add_argument("--cpu-sample", type=int, default=20)
     ap.add_argument("--ref-sample", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -799,7 +801,7 @@ def main():
 
         def e2e_step():
             # host buffers in and out; the library pipelines upload, sweep and read-back by groups
-            m.mrom_sweep_host(h, packed, om_host, outs[0], outs[1], outs[2], n_chunks=E2E_CHUNKS)
+            m.mrom_sweep_host(h, packed, om_host, outs[0], outs[1], outs[2], n_chunks=args.e2e_chunks)
 
         with torch.cuda.stream(stream):
             e2e_step()
@@ -816,7 +818,7 @@ def main():
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e = {"value": evals_step / float(te.item()), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * float(te.item()),
-               "api": f"mrom_sweep_host, {E2E_CHUNKS} object groups pipelined over two streams"}
+               "api": f"mrom_sweep_host, {args.e2e_chunks} object groups pipelined over two streams"}
 
     # ---- rotation invariants (eigenvalues of R~ and I per frequency) of the step's outputs
     eigs = torch.empty((args.n_obj, args.n_w, 3), dtype=torch.float64, device=dev)
