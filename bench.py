@@ -99,7 +99,7 @@ def pencil_prep_flops(r: int) -> float:
     """FP64 flops of one object's pencil preparation, counting complex multiply-adds (8 flops):
     Cholesky r^3/6, L^-1 r^3/6, X = L^-1 K r^3/2, H (lower) r^3/6, Householder tridiagonalisation
     r^3, Q1 accumulation 2 r^3/3, V = L^-H Z r^3/2, three transformed Gram blocks 3 x 3 r^3/2
-    (the QL rotations, about r^2 of them on 2r real rows, are not counted)."""
+    (the divide-and-conquer eigensolver of the tridiagonal and V = W Q2 are not counted)."""
     r = float(r)
     return 8.0 * r ** 3 * (1 / 6 + 1 / 6 + 1 / 2 + 1 / 6 + 1 + 2 / 3 + 1 / 2 + 4.5) + 8.0 * 9 * r * r
 
