@@ -230,9 +230,9 @@ typedef struct {
  * and Galerkin projection (Sects. 4.2-4.3), producing a reduced object for
  * mrom_sweep.  D holds n_cols complex128 snapshot columns of length n, column c
  * at D + c * ldd (device, ldd >= n, n_cols <= MROM_MAX_SNAPSHOTS).  The SVD is
- * computed from the Hermitian Gram D^H D (Householder tridiagonalisation and
- * implicit QL), so singular
- * values below about 1e-8 s_1 are not resolved; the retained rank is
+ * computed from the Hermitian Gram D^H D (Householder tridiagonalisation, then
+ * divide and conquer on the tridiagonal up to MROM_MAX_R columns and implicit QL
+ * above), so singular values below about 1e-8 s_1 are not resolved; the retained rank is
  * r = #{s_k / s_1 >= tol_sigma}, capped at r_max (if > 0) and MROM_MAX_R.
  * basis_in (device, n x r_in complex128 row-major, or NULL) skips the SVD and
  * projects onto the given basis.  sigma_out (host, n_cols values, or NULL)
@@ -486,12 +486,14 @@ mrom_status mrom_plan_sweep_invariants(mrom_plan plan, const double* omega, int3
  * this call.  MROM_SOLVER_AUTO (default): every object with one basis shared by
  * the directions goes through its Hermitian pencil (K + Me, C) -- per sweep, once
  * per object, C = L L^H, L^-1 (K + Me) L^-H = Z Lambda Z^H (Householder
- * tridiagonalisation and implicit QL) and V = L^-H Z, after which each frequency
- * costs O(r^2) instead of the O(r^3) elimination; same outputs up to rounding.
+ * tridiagonalisation and divide and conquer) and V = L^-H Z, after which each
+ * frequency costs O(r) (the quadratic forms split at the poles into prefix and
+ * suffix tables) instead of the O(r^3) elimination; same outputs up to rounding.
  * An object stays on the LU route when C is not numerically positive definite,
  * when ||C||_F ||L^-1||_F^2 > 1e6, when the error estimate
- * eps ||L^-1 (K + Me) L^-H||_F / omega_min exceeds 1e-11, or when the QL
- * iteration does not converge (decided on the device, per sweep).  Objects with
+ * eps ||L^-1 (K + Me) L^-H||_F / omega_min exceeds 1e-11, when an eigenvalue of
+ * the pencil is clearly negative, or when the eigensolver meets a non-finite
+ * value (decided on the device, per sweep).  Objects with
  * one basis per direction always take the LU route.  MROM_SOLVER_LU: every
  * object takes the LU route. */
 mrom_status mrom_set_solver(mrom_handle h, mrom_solver solver);

@@ -12,8 +12,8 @@
 //   p_i^H C p_j       = z_i^H z_j
 //   b_i^H p_j         = beta_i^H z_j
 //   p_i^H G~(w) p_j   = z_i^H (Gh_KK + w^2 Gh_CC + i w Gh_S) z_j,  Gh_X = V^H G_X V,
-// so a frequency costs O(r^2) (the certificate's Hermitian form, halved) instead of the
-// O(r^3) elimination.  The results are those of the LU path up to rounding: the forward
+// and, with the Hermitian forms split at the poles into prefix and suffix tables built once per
+// object (below), a frequency costs O(r) instead of the O(r^3) elimination.  The results are those of the LU path up to rounding: the forward
 // error of the pencil route is about eps ||H|| / omega (the eigen-decomposition is backward
 // stable in H, and |lambda - i omega| >= omega), which the preparation kernel estimates per
 // object from ||H||_F and the smallest frequency of the sweep.  Objects whose estimate
